@@ -1,0 +1,483 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle:
+published test vectors, hand-derived values, closed forms, brute force on tiny
+inputs, invariants and finite differences. CPU only."""
+import math
+
+import numpy as np
+import pytest
+
+from conftest import read_golden
+from oracle import nbvh_oracle as O
+from paper_2405_16237_b300 import workloads as W
+
+
+# ---------------------------------------------------------------- Philox
+def test_philox_known_answers():
+    for row in read_golden("philox4x32_10_kat.txt"):
+        v = [int(x, 16) for x in row]
+        out = O.philox4x32_10([np.uint64(x) for x in v[0:4]], v[4:6])
+        assert [int(x) for x in out] == v[6:10]
+
+
+def test_uniform24_exact_and_range():
+    x = np.array([0, 255, 256, 0xFFFFFFFF], np.uint32)
+    u = O.u24(x)
+    assert u[0] == 0.0 and u[1] == 0.0 and u[2] == 2.0 ** -24
+    assert u[3] == 1.0 - 2.0 ** -24
+
+
+# ---------------------------------------------------------------- layout / hash
+def test_level_layout_hand_derived():
+    rows = read_golden("level_layout_L16_N16_b1.5_T2p20.txt")
+    lay = O.level_layout(16, 16, 1.5, 20)
+    for r in rows[:-1]:
+        l, n, dense, size = map(int, r)
+        assert lay["res"][l] == n and bool(lay["dense"][l]) == bool(dense) and lay["size"][l] == size
+    assert lay["total"] == int(rows[-1][1])
+    assert lay["offset"][0] == 0 and lay["offset"][5] == 4913 + 15625 + 50653 + 166375 + 551368
+
+
+def test_hash_hand_values():
+    for r in read_golden("hash_index_T2p20.txt"):
+        x, y, z, h = map(int, r)
+        assert O.grid_index(np.array([x, y, z]), 7006, False, 1 << 20) == h
+
+
+def test_dense_index_is_bijective():
+    n = 6
+    g = np.stack(np.meshgrid(np.arange(n + 1), np.arange(n + 1), np.arange(n + 1), indexing="ij"), -1)
+    idx = O.grid_index(g.reshape(-1, 3), n, True, 1 << 20)
+    assert sorted(idx.tolist()) == list(range((n + 1) ** 3))
+    # x is the fastest-varying coordinate
+    assert O.grid_index(np.array([1, 0, 0]), n, True, 0) == 1
+    assert O.grid_index(np.array([0, 1, 0]), n, True, 0) == n + 1
+
+
+def test_hash_buckets_roughly_uniform():
+    rng = np.random.default_rng(1)
+    c = rng.integers(0, 4000, size=(200000, 3))
+    T = 1 << 10
+    h = O.grid_index(c, 4000, False, T)
+    counts = np.bincount(h, minlength=T)
+    exp = len(c) / T
+    chi2 = np.sum((counts - exp) ** 2 / exp)
+    # chi-square with T-1 dof: mean 1023, sd ~45
+    assert chi2 < 1023 + 8 * 45
+
+
+# ---------------------------------------------------------------- encoding
+def _linear_table(layout, F, a, b):
+    """Table whose entry for every dense-level vertex i/N holds a.x + b."""
+    tab = np.zeros((layout["total"], F))
+    for l, n in enumerate(layout["res"]):
+        assert layout["dense"][l]
+        g = np.stack(np.meshgrid(*(np.arange(n + 1),) * 3, indexing="ij"), -1).reshape(-1, 3)
+        idx = O.grid_index(g, int(n), True, layout["T"])
+        for f in range(F):
+            tab[layout["offset"][l] + idx, f] = (g / n) @ a[f] + b[f]
+    return tab
+
+
+def test_trilinear_reproduces_linear_field_on_dense_levels():
+    lay = O.level_layout(3, 4, 2.0, 16)   # N = 4, 8, 16: all dense
+    assert lay["dense"].all()
+    rng = np.random.default_rng(2)
+    F = 2
+    a = rng.normal(size=(F, 3))
+    b = rng.normal(size=F)
+    tab = _linear_table(lay, F, a, b)
+    x = rng.uniform(0, 1, size=(50, 3, 3))
+    x[0, 0] = [1.0, 1.0, 1.0]   # upper corner: clamped cell, frac = 1
+    x[0, 1] = [0.0, 0.5, 1.0]
+    feat = O.encode(x, tab, lay).reshape(50, 3, 3, F)
+    expect = np.einsum("snd,fd->snf", x, a) + b
+    for l in range(3):
+        assert np.max(np.abs(feat[:, :, l, :] - expect)) <= 1e-12
+
+
+def test_trilinear_on_hashed_level_without_collisions():
+    # One hashed level ((128+1)^3 > 2^20); points in a tiny region so the
+    # used vertices do not collide; entries there hold a linear field.
+    lay = O.level_layout(1, 128, 2.0, 20)
+    assert not lay["dense"][0]
+    rng = np.random.default_rng(3)
+    x = 0.3 + 0.03 * rng.uniform(size=(40, 2, 3))
+    cells = np.floor(x * 128).astype(int)
+    verts = np.unique((cells[..., None, :] + np.array(
+        [[(c >> 0) & 1, (c >> 1) & 1, (c >> 2) & 1] for c in range(8)])).reshape(-1, 3), axis=0)
+    h = O.grid_index(verts, 64, False, lay["T"])
+    assert len(np.unique(h)) == len(verts), "choose a region without collisions"
+    a = np.array([[0.3, -1.2, 2.0]])
+    tab = np.zeros((lay["total"], 1))
+    tab[h, 0] = (verts / 128.0) @ a[0] + 0.25
+    feat = O.encode(x, tab, lay).reshape(40, 2)
+    assert np.max(np.abs(feat - (x @ a[0] + 0.25))) <= 1e-12
+
+
+def test_encoding_order_is_sample_level_feature():
+    lay = O.level_layout(2, 2, 2.0, 12)
+    # table entry value encodes (level, feature): level 0 -> 10+f, level 1 -> 20+f
+    tab = np.zeros((lay["total"], 2))
+    for l in range(2):
+        tab[lay["offset"][l]:lay["offset"][l] + lay["size"][l]] = [10 * (l + 1), 10 * (l + 1) + 1]
+    x = np.full((1, 3, 3), 0.4)
+    feat = O.encode(x, tab, lay)[0]
+    assert feat.tolist() == [10, 11, 20, 21] * 3
+
+
+# ---------------------------------------------------------------- slab test / segments
+def test_clip_axis_aligned_closed_form():
+    lo, hi = np.array([1.0, -1.0, -1.0]), np.array([3.0, 1.0, 1.0])
+    keep, t0, t1, _, _ = O.clip_ray_box(np.array([0.0, 0.2, 0.3]), np.array([2.0, 0.0, 0.0]), 0.0,
+                                        np.inf, lo, hi)
+    assert keep and t0 == 0.5 and t1 == 1.5
+    # origin inside the slab of a zero direction component, outside of another
+    keep, _, _, _, _ = O.clip_ray_box(np.array([0.0, 1.5, 0.0]), np.array([1.0, 0.0, 0.0]), 0.0,
+                                      np.inf, lo, hi)
+    assert not keep
+    # ray starting inside the box: t0 = tmin
+    keep, t0, t1, _, _ = O.clip_ray_box(np.array([2.0, 0.0, 0.0]), np.array([-1.0, 0.0, 0.0]), 0.25,
+                                        0.75, lo, hi)
+    assert keep and t0 == 0.25 and t1 == 0.75
+    # interval beyond tmax
+    keep, _, _, _, _ = O.clip_ray_box(np.array([0.0, 0.0, 0.0]), np.array([1.0, 0.0, 0.0]), 0.0, 0.9,
+                                      lo, hi)
+    assert not keep
+
+
+def test_clip_matches_pointwise_membership():
+    rng = np.random.default_rng(4)
+    n = 3000
+    o = rng.uniform(-2, 2, size=(n, 3))
+    d = rng.normal(size=(n, 3))
+    d[::7, 1] = 0.0
+    lo = rng.uniform(-1, 0.5, size=(n, 3))
+    hi = lo + rng.uniform(0.05, 1.0, size=(n, 3))
+    tmin = rng.uniform(0, 0.5, n)
+    tmax = rng.uniform(0.5, 6, n)
+    keep, t0, t1, _, _ = O.clip_ray_box(o, d, tmin, tmax, lo, hi)
+    ts = np.linspace(0, 1, 257)
+    for i in range(n):
+        t = tmin[i] + ts * (tmax[i] - tmin[i])
+        p = o[i] + t[:, None] * d[i]
+        inside = np.all((p >= lo[i] - 1e-9) & (p <= hi[i] + 1e-9), axis=1)
+        if keep[i]:
+            pm = o[i] + 0.5 * (t0[i] + t1[i]) * d[i]
+            assert np.all(pm >= lo[i] - 1e-9) and np.all(pm <= hi[i] + 1e-9)
+            # brute-force samples inside the box lie within [t0, t1]
+            assert np.all((t[inside] >= t0[i] - 1e-9) & (t[inside] <= t1[i] + 1e-9))
+        else:
+            strict = np.all((p > lo[i] + 1e-7) & (p < hi[i] - 1e-7), axis=1)
+            assert not strict.any()
+
+
+def test_segments_sorted_and_complete():
+    tris = W.scene_random_tris(512, seed=5)
+    lv = O.build_leaves(tris, 16)
+    rays = W.camera_rays(24, 24, seed=6)
+    seg = O.ray_segments(rays, lv["leaf_lo"], lv["leaf_hi"])
+    off = seg["offsets"]
+    for r in range(len(rays["ox"])):
+        t0 = seg["t0"][off[r]:off[r + 1]]
+        lf = seg["leaf"][off[r]:off[r + 1]]
+        keys = list(zip(t0, lf))
+        assert keys == sorted(keys)
+        # brute force: every leaf whose box a midpoint sample lies in is listed
+        o, d, tmin, tmax = O.rays_od(rays, r)
+        for leaf in range(16):
+            k, a, b, _, _ = O.clip_ray_box(o, d, tmin, tmax, lv["leaf_lo"][leaf], lv["leaf_hi"][leaf])
+            assert bool(k) == (leaf in lf)
+
+
+# ---------------------------------------------------------------- leaf build
+def test_median_split_tiny_known_partition():
+    # 8 triangles centred at x = 0..7 (y, z spread smaller): 4 leaves of 2 in x order
+    base = np.array([[0, 0, 0], [0.1, 0, 0], [0, 0.1, 0]], np.float64)
+    perm = [3, 0, 6, 1, 7, 2, 5, 4]
+    tris = np.stack([base + [perm[i], 0, 0] for i in range(8)]).astype(np.float32)
+    lv = O.build_leaves(tris, 4, inflate_rel=0.0)
+    xs = [sorted(perm[i] for i in lv["tri_perm"][a:b]) for a, b in lv["leaf_range"]]
+    assert xs == [[0, 1], [2, 3], [4, 5], [6, 7]]
+    assert np.allclose(lv["leaf_lo"][0], [0, 0, 0]) and np.allclose(lv["leaf_hi"][3], [7.1, 0.1, 0])
+
+
+def test_leaf_build_invariants():
+    tris = W.scene_random_tris(4096, seed=7)
+    lv = O.build_leaves(tris, 64)
+    assert sorted(lv["tri_perm"].tolist()) == list(range(4096))
+    sizes = lv["leaf_range"][:, 1] - lv["leaf_range"][:, 0]
+    assert (sizes == 64).all()
+    E = lv["frame"]["extent"]
+    for i, (a, b) in enumerate(lv["leaf_range"]):
+        pts = tris[lv["tri_perm"][a:b]].reshape(-1, 3).astype(np.float64)
+        assert (lv["leaf_lo"][i] <= pts.min(0) - 1e-4 * E).all()
+        assert (lv["leaf_hi"][i] >= pts.max(0) + 1e-4 * E).all()
+        # outward rounding is tight: within one float32 ulp of the exact bound
+        ex_lo = pts.min(0) - 1e-4 * E
+        ex_hi = pts.max(0) + 1e-4 * E
+        assert (lv["leaf_lo"][i] >= ex_lo - np.abs(np.spacing(lv["leaf_lo"][i])).astype(np.float64)).all()
+        assert (lv["leaf_hi"][i] <= ex_hi + np.abs(np.spacing(lv["leaf_hi"][i])).astype(np.float64)).all()
+        assert np.all(np.diff(lv["tri_perm"][a:b]) > 0)
+
+
+# ---------------------------------------------------------------- sampling, MLP
+def test_sample_points_closed_form():
+    o = np.array([[0.0, 0.0, 0.0]])
+    d = np.array([[1.0, 2.0, 0.0]])
+    p = O.sample_points(o, d, np.array([1.0]), np.array([3.0]), 4)
+    assert np.allclose(p[0, :, 0], [1.25, 1.75, 2.25, 2.75], atol=0, rtol=0)
+    p1 = O.sample_points(o, d, np.array([1.0]), np.array([3.0]), 1)
+    assert p1[0, 0, 0] == 2.0 and p1[0, 0, 1] == 4.0
+
+
+def test_mlp_forward_against_loops():
+    rng = np.random.default_rng(8)
+    dims = [5, 4, 3, 2]
+    layers = [(rng.normal(size=(dims[i + 1], dims[i])), rng.normal(size=dims[i + 1])) for i in range(3)]
+    x = rng.normal(size=(6, 5))
+    raw, _, _ = O.mlp_forward(x, layers)
+    for s in range(6):
+        h = list(x[s])
+        for li, (Wm, b) in enumerate(layers):
+            z = [sum(Wm[j][k] * h[k] for k in range(len(h))) + b[j] for j in range(len(b))]
+            h = [max(0.0, v) for v in z] if li < 2 else z
+        assert np.allclose(raw[s], h, rtol=1e-14, atol=1e-14)
+
+
+def test_sigmoid_softplus_closed_forms():
+    assert O.sigmoid(0.0) == 0.5
+    assert abs(O.sigmoid(np.log(3.0)) - 0.75) < 1e-15
+    assert abs(O.softplus(0.0) - math.log(2.0)) < 1e-15
+    assert O.sigmoid(-800.0) == 0.0 and O.sigmoid(800.0) == 1.0
+
+
+# ---------------------------------------------------------------- decode / resolve
+def test_resolve_early_out_equals_all_segments():
+    rng = np.random.default_rng(9)
+    tris = W.scene_random_tris(1024, seed=10)
+    lv = O.build_leaves(tris, 32)
+    rays = W.camera_rays(20, 20, seed=11)
+    seg = O.ray_segments(rays, lv["leaf_lo"], lv["leaf_hi"])
+    S = len(seg["ray"])
+    raw = rng.normal(size=(S, 5))
+    hit, t, nrm = O.decode(raw, seg["t0"], seg["t1"])
+    res = O.resolve(len(rays["ox"]), seg, hit, t, nrm)
+    off = seg["offsets"]
+    for r in range(len(rays["ox"])):
+        best_t, best_leaf = np.inf, -1
+        for j in range(off[r], off[r + 1]):
+            if seg["t0"][j] >= best_t:
+                break       # early out: later segments cannot be closer
+            if hit[j] and t[j] < best_t:
+                best_t, best_leaf = t[j], seg["leaf"][j]
+        assert res["t"][r] == best_t and res["leaf"][r] == best_leaf
+
+
+def test_decode_closed_form():
+    raw = np.array([[0.0, 0.0, 0.0, 0.0, 0.0], [1.0, np.log(3.0), 3.0, 0.0, 4.0]])
+    hit, t, n = O.decode(raw, np.array([1.0, 2.0]), np.array([3.0, 6.0]))
+    assert hit.tolist() == [False, True]
+    assert t[0] == 2.0 and abs(t[1] - 5.0) < 1e-14
+    assert n[0].tolist() == [0, 0, 1] and np.allclose(n[1], [0.6, 0, 0.8], atol=1e-15)
+
+
+# ---------------------------------------------------------------- Moller-Trumbore / labels
+def test_moller_trumbore_plane_closed_form():
+    v0, v1, v2 = np.array([-1.0, -1.0, 0.5]), np.array([3.0, -1.0, 0.5]), np.array([-1.0, 3.0, 0.5])
+    rng = np.random.default_rng(12)
+    o = rng.uniform(-0.5, 0.5, size=(100, 3))
+    o[:, 2] = -1.0
+    d = np.array([0.1, 0.05, 1.0])
+    hit, t, _, _ = O.moller_trumbore(o, d, v0, v1, v2)
+    assert hit.all()
+    assert np.allclose(t, (0.5 - o[:, 2]) / d[2], rtol=1e-14)
+
+
+def test_moller_trumbore_icosphere_vs_analytic_sphere():
+    tris = W.scene_icosphere(level=4, radius=0.4, amplitude=0.0).astype(np.float64)
+    rng = np.random.default_rng(13)
+    o = np.array([0.0, 0.0, -2.0])
+    n = 200
+    d = np.stack([rng.uniform(-0.12, 0.12, n), rng.uniform(-0.12, 0.12, n), np.ones(n)], 1)
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    hit, t, _, _ = O.moller_trumbore(o[None, None], d[:, None], tris[None, :, 0], tris[None, :, 1],
+                                     tris[None, :, 2])
+    tt = np.where(hit & (t > 0), t, np.inf).min(1)
+    b = d @ o
+    disc = b * b - (o @ o - 0.16)
+    t_sphere = -b - np.sqrt(disc)
+    # the polyhedron is inscribed: its faces lie inside the sphere, at most
+    # the largest face-plane depth ``sag`` below it
+    e1 = tris[:, 1] - tris[:, 0]
+    e2 = tris[:, 2] - tris[:, 0]
+    nf = np.cross(e1, e2)
+    nf /= np.linalg.norm(nf, axis=1, keepdims=True)
+    sag = 0.4 - np.min(np.abs(np.sum(nf * tris[:, 0], 1)))
+    assert 0 < sag < 2e-3
+    assert np.all(tt >= t_sphere - 1e-12)
+    cos_inc = np.abs(np.sum(d * (o + t_sphere[:, None] * d), 1)) / 0.4
+    assert np.all(tt - t_sphere <= sag / cos_inc + 1e-12)
+
+
+def test_labels_min_over_leaves_equals_global_closest_hit():
+    tris = W.scene_random_tris(600, seed=14)
+    lv = O.build_leaves(tris, 12)
+    rays = W.camera_rays(14, 14, seed=15)
+    seg = O.ray_segments(rays, lv["leaf_lo"], lv["leaf_hi"])
+    o, d, tmin, tmax = O.rays_od(rays)
+    rr = seg["ray"]
+    lab = O.labels(o[rr], d[rr], seg["leaf"], seg["t0"], seg["t1"], tris, lv["tri_perm"], lv["leaf_range"])
+    tv = tris.astype(np.float64)
+    for r in range(len(o)):
+        hit, t, _, _ = O.moller_trumbore(o[r][None], d[r][None], tv[:, 0], tv[:, 1], tv[:, 2])
+        glob = np.where(hit & (t >= tmin[r]) & (t <= tmax[r]), t, np.inf).min()
+        sel = rr == r
+        per_leaf = np.where(lab["hit"][sel] == 1, lab["t"][sel], np.inf)
+        best = per_leaf.min() if per_leaf.size else np.inf
+        assert best == glob
+    # depths lie in [0, 1], normals face the ray
+    h = lab["hit"] == 1
+    assert np.all((lab["depth"][h] >= 0) & (lab["depth"][h] <= 1))
+    assert np.all(np.sum(lab["normal"][h] * d[rr][h], 1) <= 0)
+
+
+# ---------------------------------------------------------------- loss / gradients / Adam
+def _tiny_problem(seed=16):
+    rng = np.random.default_rng(seed)
+    lay = O.level_layout(3, 4, 2.0, 8)    # mixed dense and hashed levels
+    assert lay["dense"][0] and not lay["dense"][2]
+    F, N = 2, 3
+    tab = rng.uniform(-0.5, 0.5, size=(lay["total"], F))
+    dims = [N * 3 * F, 8, 8, 5]
+    layers = [(rng.normal(0, 1 / math.sqrt(dims[i]), size=(dims[i + 1], dims[i])),
+               rng.normal(0, 0.1, size=dims[i + 1])) for i in range(3)]
+    S = 12
+    o = rng.uniform(-0.3, 0.3, size=(S, 3))
+    d = rng.normal(size=(S, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    t0 = rng.uniform(0, 0.2, S)
+    t1 = t0 + rng.uniform(0.1, 0.4, S)
+    valid = np.ones(S, bool)
+    valid[3] = False
+    yh = (rng.uniform(size=S) < 0.6).astype(float)
+    yd = rng.uniform(size=S)
+    yn = rng.normal(size=(S, 3))
+    return dict(o=o, d=d, t0=t0, t1=t1, valid=valid, yh=yh, yd=yd, yn=yn, tab=tab, layers=layers,
+                lay=lay, N=N)
+
+
+def _loss_of(P, tab=None, layers=None):
+    p = O.sample_points(P["o"], P["d"], P["t0"], P["t1"], P["N"])
+    x = O.normalize_points(p, np.zeros(3), 1.0)
+    feat = O.encode(x, P["tab"] if tab is None else tab, P["lay"])
+    raw, _, _ = O.mlp_forward(feat, P["layers"] if layers is None else layers)
+    return O.loss(raw, P["yh"], P["yd"], P["yn"], P["valid"])[0]
+
+
+def test_loss_special_case_closed_form():
+    raw = np.zeros((2, 5))
+    L, _ = O.loss(raw, [1, 0], [0.25, 0.9], np.array([[0.0, 0.0, 1.0], [1, 1, 1]]), [True, True])
+    expect = (2 * math.log(2) + 2 * 0.25 + 1.0 / 3.0 + 2 * math.log(2)) / 2
+    assert abs(L - expect) < 1e-15
+
+
+def test_gradients_match_central_differences():
+    P = _tiny_problem()
+    L, g_tab, g_layers, raw = O.forward_backward(P["o"], P["d"], P["t0"], P["t1"], P["valid"], P["yh"],
+                                                  P["yd"], P["yn"], P["tab"], P["layers"], P["lay"],
+                                                  np.zeros(3), 1.0, P["N"])
+    # keep away from the L1 kinks so central differences are exact to O(h^2)
+    s1 = O.sigmoid(raw[:, 1])
+    assert np.min(np.abs(s1 - P["yd"])) > 1e-4 and np.min(np.abs(raw[:, 2:5] - P["yn"])) > 1e-4
+    h = 1e-6
+    used = np.nonzero(np.abs(g_tab).sum(1) > 0)[0]
+    rng = np.random.default_rng(17)
+    for e in rng.choice(used, size=12, replace=False):
+        for f in range(2):
+            tp = P["tab"].copy(); tp[e, f] += h
+            tm = P["tab"].copy(); tm[e, f] -= h
+            fd = (_loss_of(P, tab=tp) - _loss_of(P, tab=tm)) / (2 * h)
+            assert abs(fd - g_tab[e, f]) <= 1e-6 * max(1e-3, abs(g_tab[e, f])) + 1e-9
+    for li in range(3):
+        Wm, b = P["layers"][li]
+        for (j, k) in [(0, 0), (1, 2), (Wm.shape[0] - 1, Wm.shape[1] - 1)]:
+            lp = [(w.copy(), bb.copy()) for w, bb in P["layers"]]
+            lm = [(w.copy(), bb.copy()) for w, bb in P["layers"]]
+            lp[li][0][j, k] += h
+            lm[li][0][j, k] -= h
+            fd = (_loss_of(P, layers=lp) - _loss_of(P, layers=lm)) / (2 * h)
+            assert abs(fd - g_layers[li][0][j, k]) <= 1e-6 * max(1e-3, abs(g_layers[li][0][j, k])) + 1e-9
+        lp = [(w.copy(), bb.copy()) for w, bb in P["layers"]]
+        lm = [(w.copy(), bb.copy()) for w, bb in P["layers"]]
+        lp[li][1][0] += h
+        lm[li][1][0] -= h
+        fd = (_loss_of(P, layers=lp) - _loss_of(P, layers=lm)) / (2 * h)
+        assert abs(fd - g_layers[li][1][0]) <= 1e-6 * max(1e-3, abs(g_layers[li][1][0])) + 1e-9
+
+
+def test_invalid_rays_do_not_contribute():
+    P = _tiny_problem()
+    _, g_tab, g_layers, _ = O.forward_backward(P["o"], P["d"], P["t0"], P["t1"], P["valid"], P["yh"],
+                                                P["yd"], P["yn"], P["tab"], P["layers"], P["lay"],
+                                                np.zeros(3), 1.0, P["N"])
+    Q = dict(P)
+    Q["o"] = P["o"].copy(); Q["o"][3] += 0.1   # the invalid ray changes
+    _, g_tab2, _, _ = O.forward_backward(Q["o"], Q["d"], Q["t0"], Q["t1"], Q["valid"], Q["yh"],
+                                          Q["yd"], Q["yn"], Q["tab"], Q["layers"], Q["lay"],
+                                          np.zeros(3), 1.0, Q["N"])
+    assert np.array_equal(g_tab, g_tab2)
+
+
+def test_adam_first_step_closed_form():
+    rng = np.random.default_rng(18)
+    p = rng.normal(size=100)
+    g = rng.normal(size=100)
+    p1, m, v = O.adam(p, g, np.zeros(100), np.zeros(100), 1, lr=1e-2)
+    assert np.allclose(p1, p - 1e-2 * g / (np.abs(g) + 1e-8), rtol=0, atol=1e-15)
+    assert np.allclose(m, 0.1 * g) and np.allclose(v, 0.001 * g * g)
+
+
+# ---------------------------------------------------------------- training rays / bounce
+def test_train_rays_probed_cross_their_leaf_and_chords_on_sphere():
+    tris = W.scene_random_tris(2048, seed=19)
+    lv = O.build_leaves(tris, 32)
+    R = O.train_rays(O.TRAIN_MODE_PROBED_MIX, seed=123, step=7, n=2000, leaves=lv)
+    fr = lv["frame"]
+    assert np.allclose(np.linalg.norm(R["d"], axis=1), 1.0, atol=1e-12)
+    even = np.arange(2000) % 2 == 0
+    assert (R["leaf"][even] >= 0).all()
+    # probed origins lie on the bounding sphere, as do chord origins
+    dist = np.linalg.norm(R["o"] - fr["centre"], axis=1)
+    assert np.allclose(dist, fr["sphere_radius"], rtol=1e-12)
+    # the probed leaf's segment is non-empty and inside the ray
+    assert np.all(R["t1"][even] >= R["t0"][even])
+    # leaf choice uniform-ish over 32 leaves
+    cnt = np.bincount(R["leaf"][even], minlength=32)
+    assert cnt.min() > 10
+    # directions uniform: mean ~ 0, mean z^2 ~ 1/3
+    assert np.all(np.abs(R["d"].mean(0)) < 0.06) and abs((R["d"][:, 2] ** 2).mean() - 1 / 3) < 0.03
+    # chords: the trained leaf is the first one met
+    odd = np.nonzero(~even & (R["leaf"] >= 0))[0][:50]
+    for i in odd:
+        k, t0, _, _, _ = O.clip_ray_box(R["o"][i], R["d"][i], 0.0, R["tmax"][i], lv["leaf_lo"], lv["leaf_hi"])
+        assert R["t0"][i] == np.min(t0[k])
+
+
+def test_bounce_rays_cosine_hemisphere():
+    rng = np.random.default_rng(20)
+    n = 20000
+    nrm = rng.normal(size=(n, 3))
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    d = -nrm + 0.1 * rng.normal(size=(n, 3))
+    o = np.zeros((n, 3))
+    p, dirs = O.bounce_rays(o, d, np.ones(n), nrm, np.arange(n), seed=5)
+    assert np.allclose(np.linalg.norm(dirs, axis=1), 1.0, atol=1e-12)
+    flip = np.sum(nrm * d, 1) > 0
+    nn = np.where(flip[:, None], -nrm, nrm)
+    cos = np.sum(dirs * nn, 1)
+    assert np.all(cos >= -1e-12)
+    # cosine-weighted: E[cos] = 2/3
+    assert abs(cos.mean() - 2 / 3) < 0.01
+    t, b = O.onb(nn)
+    assert np.allclose(np.sum(t * nn, 1), 0, atol=1e-12) and np.allclose(np.sum(t * b, 1), 0, atol=1e-12)
+    assert np.allclose(p, d + 1e-4 * nn)
