@@ -1,0 +1,419 @@
+#!/usr/bin/env python
+"""Neural ray query benchmark on one or more B300s (one process per GPU).
+
+Workload (the full-size configuration): a level-8 displaced icosphere
+(1,310,720 triangles) split into 2,048 median-split leaf boxes; a 16-level
+hash grid (F = 2, 2^20 entries per hashed level, FP16 entries), 16 samples per
+segment, a 3x64 MLP; 1920x1080 pinhole primary rays plus one cosine-weighted
+secondary bounce per predicted hit. One step = primary query -> bounce rays ->
+secondary query, all in the library's kernels. The metric counts primary and
+secondary rays per second.
+
+Printed as one JSON line by rank 0. ``--impl reference`` times the FP64 CPU
+oracle instead (bounded samples of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+# The CPU baseline (the FP64 oracle) runs single-threaded: pin numpy's BLAS
+# before numpy loads. The GPU path does not use numpy arithmetic.
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "neural ray queries Mrays/s (fp16 TC vs fp32 plain, same GPU, same err); train rays/s"
+SEED = 240516237
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--cpu-rays", type=int, default=24576, help="oracle sample size (primary rays)")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--max-segs", type=int, default=48)
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------- distributed
+def dist_init(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def dist_max(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------- workload
+def make_scene():
+    from paper_2405_16237_b300 import workloads as W
+    tris = W.scene_icosphere(level=8)
+    return W.C1, tris, W.camera_rays(1920, 1080)
+
+
+class GpuWorkload:
+    def __init__(self, spec, tris, rays_np, max_segs):
+        import torch
+        from paper_2405_16237_b300 import nbvh as B
+        from paper_2405_16237_b300 import workloads as W
+        self.B = B
+        self.spec = spec
+        self.max_segs = max_segs
+        self.leaves = B.build_leaves(tris, spec.n_leaves, spec.inflate_rel)
+        info = self.leaves["info"]
+        cfg = spec.model
+        self.desc = B.model_desc(cfg, B.FP16, B.FP16, info["centre"], info["extent"])
+        lay = B.level_layout(self.desc)
+        self.table_np = W.init_table(lay["total"], cfg.n_features, SEED + 21, 1e-4).astype(np.float16)
+        self.layers = W.init_mlp(cfg.mlp_dims(), SEED + 22)
+        self.table = torch.as_tensor(self.table_np).cuda()
+        self.mlp = torch.as_tensor(B.pack_mlp(self.layers)).cuda()
+        self.nodes = torch.as_tensor(self.leaves["nodes"]).cuda()
+        self.n = len(rays_np["ox"])
+        self.rays_host = {k: torch.as_tensor(np.ascontiguousarray(rays_np[k])).pin_memory() for k in B.RAY_KEYS}
+        self.rays = {k: v.cuda() for k, v in self.rays_host.items()}
+        self.rays2 = B.new_rays(self.n)
+        self.h1 = B.new_hits(self.n)
+        self.h2 = B.new_hits(self.n)
+        ws = B.query_workspace_size(self.desc, self.n, max_segs)
+        self.ws1 = B.new_workspace(ws)
+        self.ws2 = B.new_workspace(ws)
+        self.h1_host = {k: torch.empty_like(v, device="cpu").pin_memory() for k, v in self.h1.items()}
+        self.h2_host = {k: torch.empty_like(v, device="cpu").pin_memory() for k, v in self.h2.items()}
+        # a buffer larger than L2 (126 MB), rewritten between timed steps
+        self.flush_buf = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def step(self, desc):
+        B = self.B
+        B.query_rays(desc, self.table, self.mlp, self.nodes, self.leaves["n_nodes"], self.rays, self.max_segs,
+                     out=self.h1, workspace=self.ws1)
+        B.bounce_rays(self.rays, self.h1, SEED + 3, out=self.rays2)
+        B.query_rays(desc, self.table, self.mlp, self.nodes, self.leaves["n_nodes"], self.rays2, self.max_segs,
+                     out=self.h2, workspace=self.ws2)
+
+    def step_e2e(self, desc):
+        for k in self.B.RAY_KEYS:
+            self.rays[k].copy_(self.rays_host[k], non_blocking=True)
+        self.step(desc)
+        for k in self.h1:
+            self.h1_host[k].copy_(self.h1[k], non_blocking=True)
+            self.h2_host[k].copy_(self.h2[k], non_blocking=True)
+
+    def rays_per_step(self):
+        return self.n + int(self.h1["hit"].sum().item())
+
+    def flush(self):
+        self.flush_buf.fill_(1)
+
+
+def time_steps(wl, desc, steps, warmup, e2e=False):
+    import torch
+    fn = wl.step_e2e if e2e else wl.step
+    for _ in range(warmup):
+        fn(desc)
+    torch.cuda.synchronize()
+    total = 0.0
+    for _ in range(steps):
+        wl.flush()
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record()
+        fn(desc)
+        e.record()
+        e.synchronize()
+        total += s.elapsed_time(e)
+    torch.cuda.synchronize()
+    return total
+
+
+class ClockSampler:
+    def __init__(self):
+        self.path = os.path.join(tempfile.gettempdir(), f"nbvh_clocks_{os.getpid()}.csv")
+        self.proc = None
+
+    def start(self):
+        try:
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            dev = os.environ.get("LOCAL_RANK", "0")
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", dev, f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2405_16237_b300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, if it was taken on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        t = json.load(open(p))
+    except Exception:
+        return None
+    if t.get("source_hash") != kernel_source_hash():
+        return None
+    return t
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p)), "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------- oracle sample
+def oracle_sample(spec, tris, rays_np, n_sample):
+    """Time the FP64 oracle on a seeded subset of the primary rays plus their
+    bounce rays. Returns (Mrays/s, seconds, sample description, results)."""
+    import contextlib
+    try:
+        from threadpoolctl import threadpool_limits
+    except ImportError:  # BLAS threads are pinned through the environment above
+        def threadpool_limits(limits):
+            return contextlib.nullcontext()
+    from oracle import nbvh_oracle as O
+    from paper_2405_16237_b300 import workloads as W
+    rng = np.random.default_rng(SEED + 5)
+    idx = np.sort(rng.choice(len(rays_np["ox"]), size=n_sample, replace=False))
+    sub = W.subset(rays_np, idx)
+    cfg = spec.model
+    with threadpool_limits(limits=1):
+        leaves = O.build_leaves(tris, spec.n_leaves, spec.inflate_rel)
+        lay = O.level_layout(cfg.n_levels, cfg.base_res, cfg.growth, cfg.log2_table)
+        tab = W.init_table(lay["total"], cfg.n_features, SEED + 21, 1e-4).astype(np.float16)
+        layers = W.init_mlp(cfg.mlp_dims(), SEED + 22)
+        t0 = time.perf_counter()
+        res = O.query(sub, leaves, tab, layers, lay, cfg.n_samples)
+        o, d, _, _ = O.rays_od(sub)
+        hit = res["hit"].astype(bool)
+        p, dirs = O.bounce_rays(o[hit], d[hit], res["t"][hit], res["normal"][hit], idx[hit], SEED + 3)
+        n2 = int(hit.sum())
+        sec = {"ox": p[:, 0], "oy": p[:, 1], "oz": p[:, 2], "dx": dirs[:, 0], "dy": dirs[:, 1], "dz": dirs[:, 2],
+               "tmin": np.zeros(n2), "tmax": np.full(n2, np.inf)}
+        sec = {k: np.asarray(v, np.float32) for k, v in sec.items()}
+        res2 = O.query(sec, leaves, tab, layers, lay, cfg.n_samples)
+        dt = time.perf_counter() - t0
+    n_rays = n_sample + n2
+    return n_rays / dt / 1e6, dt, n_rays, idx, res
+
+
+def accuracy(wl, idx, res):
+    """Hit agreement, depth and normal error of the GPU's primary hits against
+    the oracle's on the sampled rays."""
+    h = {k: v.cpu().numpy() for k, v in wl.h1.items()}
+    g_hit = h["hit"][idx].astype(bool)
+    o_hit = res["hit"].astype(bool)
+    both = g_hit & o_hit & (h["leaf"][idx] == res["leaf"])
+    out = {"rays": int(len(idx)), "hit_agreement": float(np.mean(g_hit == o_hit))}
+    if both.any():
+        out["depth_max_abs"] = float(np.max(np.abs(h["t"][idx][both] - res["t"][both])))
+        gn = np.stack([h["nx"][idx], h["ny"][idx], h["nz"][idx]], 1)[both]
+        c = np.clip(np.sum(gn * res["normal"][both], 1), -1, 1)
+        out["normal_mean_deg"] = float(np.degrees(np.arccos(c)).mean())
+    return out
+
+
+# ---------------------------------------------------------------------------- main
+def main():
+    args = parse()
+    world, rank, local = dist_init(args.gpus)
+    spec, tris, rays_np = make_scene()
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        rates, secs = [], []
+        n = min(args.cpu_rays, 4096)
+        for s in range(args.warmup + args.steps):
+            v, dt, nr, _, _ = oracle_sample(spec, tris, rays_np, n)
+            if s >= args.warmup:
+                rates.append(v)
+                secs.append(dt)
+        val = float(np.mean(rates))
+        line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "Mrays/s", "n_gpus": 1,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(secs) * 1e3),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": spec.name, "sample_primary_rays": n},
+                "cpu_baseline": {"value": val, "unit": "Mrays/s", "cores": 1, "kind": "oracle",
+                                 "sample": f"{n} seeded primary rays of the 1920x1080 image + their bounce rays"},
+                "e2e": {"value": val, "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    import torch
+    from paper_2405_16237_b300 import nbvh as B
+    torch.cuda.set_device(local)
+    wl = GpuWorkload(spec, tris, rays_np, args.max_segs)
+    d16 = B.with_mlp_prec(wl.desc, B.FP16)
+    d32 = B.with_mlp_prec(wl.desc, B.FP32)
+    dbf = B.with_mlp_prec(wl.desc, B.BF16)
+
+    # untimed reference step: statistics of the work one step does
+    wl.step(d16)
+    torch.cuda.synchronize()
+    st = B.device_status()
+    if st != 0:
+        raise RuntimeError(f"device status {st} after the first step")
+    rays_step = wl.rays_per_step()
+    seg1, waves1 = B.query_stats(wl.ws1, wl.n, args.max_segs)
+    seg2, waves2 = B.query_stats(wl.ws2, wl.n, args.max_segs)
+
+    # main measurement: FP16 tensor-core form
+    barrier(world)
+    clocks = ClockSampler()
+    clocks.start()
+    launches0 = B.launch_count()
+    B.set_timing(True)
+    B.get_timing()
+    total_ms = time_steps(wl, d16, args.steps, args.warmup)
+    tr_ms, ev_ms, calls = B.get_timing()
+    B.set_timing(False)
+    launches = B.launch_count() - launches0
+    clk = clocks.stop()
+    total_ms = dist_max(total_ms, world)
+    ms_step = total_ms / args.steps
+    value = world * rays_step / (ms_step * 1e-3) / 1e6
+    per_launch_steps = args.steps + args.warmup  # timing covered warm-up and timed steps
+    eval_ms_step = ev_ms / per_launch_steps
+    tr_ms_step = tr_ms / per_launch_steps
+    launches_per_step = launches / (args.steps + args.warmup)
+
+    # other forms on the same workload
+    ms32 = dist_max(time_steps(wl, d32, max(3, args.steps // 2), 2), world) / max(3, args.steps // 2)
+    msbf = dist_max(time_steps(wl, dbf, max(3, args.steps // 2), 2), world) / max(3, args.steps // 2)
+    wl.step(d16)
+    torch.cuda.synchronize()
+
+    # end to end through the public API with host buffers
+    e2e_ms = dist_max(time_steps(wl, d16, args.steps, args.warmup, e2e=True), world) / args.steps
+    h2d = sum(v.numel() * v.element_size() for v in wl.rays_host.values())
+    d2h = 2 * sum(v.numel() * v.element_size() for v in wl.h1_host.values())
+
+    # roofline of the dominant kernel (the fused encode + MLP waves)
+    cfg = spec.model
+    bytes_seg = cfg.n_samples * cfg.n_levels * 8 * cfg.n_features * 2 + 48
+    seg_step = seg1 + seg2
+    achieved = seg_step * bytes_seg / (eval_ms_step * 1e-3) / 1e9
+    peaks, peak_kind = measured_peaks()
+    traffic = profiled_traffic()
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "peak_source": peak_kind,
+            "kernel": "eval_tc_kernel (wave mode): gather + trilinear + tcgen05 MLP + resolve",
+            "bytes_per_segment": bytes_seg, "segments_per_step": seg_step,
+            "kernel_ms_per_step": eval_ms_step, "traverse_ms_per_step": tr_ms_step,
+            "traffic": (traffic["dram_bytes_per_segment"] * seg_step / max(1, waves1 + waves2)
+                        if traffic else None)}
+
+    line = {"metric": METRIC, "value": value, "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f16", "data": "synthetic",
+            "config": {"workload": spec.name, "rays_per_step": rays_step, "primary_rays": wl.n,
+                       "bounce_rays": rays_step - wl.n, "segments_per_step": seg_step,
+                       "waves": [waves1, waves2], "l2": "flushed (256 MB write) between timed steps",
+                       "parallelism": f"replicas x{world}"},
+            "fp32_plain": {"value": world * rays_step / (ms32 * 1e-3) / 1e6, "ms_per_step": ms32},
+            "bf16_tc": {"value": world * rays_step / (msbf * 1e-3) / 1e6, "ms_per_step": msbf},
+            "roofline": roof,
+            "e2e": {"value": world * rays_step / (e2e_ms * 1e-3) / 1e6, "unit": "Mrays/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+            "gpu_launches": int(round(launches_per_step * args.steps)),
+            "clocks": clk}
+
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        v, dt, nr, idx, res = oracle_sample(spec, tris, rays_np, args.cpu_rays)
+        line["cpu_baseline"] = {"value": v, "unit": "Mrays/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{args.cpu_rays} seeded primary rays of the 1920x1080 image + their "
+                                          f"{nr - args.cpu_rays} bounce rays, {dt:.1f} s"}
+        acc = {}
+        for nm, dsc in (("fp16_tc", d16), ("bf16_tc", dbf), ("fp32_plain", d32)):
+            wl.step(dsc)
+            torch.cuda.synchronize()
+            acc[nm] = accuracy(wl, idx, res)
+        line["accuracy_vs_oracle"] = acc
+    elif rank == 0 and world == 1:
+        line["cpu_baseline"] = None
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,241 @@
+/*
+ * nbvh.h - C ABI of the B300 (sm_103a) neural ray query library.
+ *
+ * Implements the neural ray query of N-BVH (Weier et al., "N-BVH: Neural ray
+ * queries with bounding volume hierarchies", SIGGRAPH 2024) and its training
+ * step. The paper states the problem as: given geometric elements and their
+ * bounding box, train a neural model that answers intersection queries for
+ * rays crossing the box (Sec. 4); a shallow BVH of hollow leaf boxes supplies
+ * the ray-box intervals in which the model is probed (Sec. 3, Sec. 5), and a
+ * neural query returns the same intersection record as a classical one
+ * (Sec. 7).
+ *
+ * Conventions (all entry points):
+ *  - Every buffer is owned by the caller. Device buffers are plain device
+ *    pointers; host buffers are plain host pointers. The library allocates no
+ *    memory: scratch space is a caller-provided workspace whose size the
+ *    matching *_workspace_size call returns.
+ *  - Device work is enqueued on the caller's stream (a cudaStream_t passed as
+ *    void*; NULL = the legacy default stream) and the call returns without
+ *    synchronising, except where a function says otherwise.
+ *  - Every call returns an nbvh_status. Arguments are validated on the host
+ *    before any launch; an invalid argument launches nothing. No exception and
+ *    no process exit crosses this ABI.
+ *  - Conditions found on the device (segment-list overflow, a wait that gave
+ *    up) are recorded in a per-process device status word, read and cleared by
+ *    nbvh_get_device_status. Kernels never trap.
+ *  - Directions need not be unit length; t is measured in units of |d|.
+ *
+ * Precision: slab tests, clipping, sample positions, trilinear weights and
+ * depth reconstruction are FP32. Hash-table entries are stored in
+ * FP32/FP16/BF16. The MLP runs either on CUDA cores in FP32
+ * (mlp_prec = NBVH_FP32) or on the tensor cores (tcgen05) with FP16/BF16
+ * operands and FP32 accumulation (mlp_prec = NBVH_FP16 / NBVH_BF16).
+ */
+#ifndef NBVH_H_
+#define NBVH_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NBVH_MAX_LEVELS 32
+#define NBVH_MAX_SAMPLES 64
+#define NBVH_MAX_INPUTS 2048   /* n_samples * n_levels * n_features */
+
+typedef enum {
+  NBVH_OK = 0,
+  NBVH_ERR_INVALID_ARG = 1,           /* null pointer, negative size, out-of-range field */
+  NBVH_ERR_CUDA = 2,                  /* a CUDA runtime call failed (launch, copy, attribute) */
+  NBVH_ERR_OOM = 3,                   /* reserved: the library itself never allocates */
+  NBVH_ERR_WORKSPACE_TOO_SMALL = 4,   /* ws_bytes below the *_workspace_size result */
+  NBVH_ERR_SEGMENT_OVERFLOW = 5,      /* device: a ray crossed more than max_segs leaves */
+  NBVH_ERR_TIMEOUT = 6,               /* device: a bounded wait gave up */
+  NBVH_ERR_UNSUPPORTED = 7            /* valid but not implemented for this shape/precision */
+} nbvh_status;
+
+typedef enum { NBVH_FP32 = 0, NBVH_FP16 = 1, NBVH_BF16 = 2 } nbvh_precision;
+
+/* Neural model shape (Sec. 4 Fig. 3: samples along the ray-box interval,
+ * multi-resolution hash-grid features concatenated in ray order, MLP decoder;
+ * Sec. 6 "Neural model & training": ReLU hidden layers).
+ * Level l has resolution N_l = floor(base_res * growth^l); it is indexed
+ * densely while (N_l+1)^3 <= 2^log2_table and through the spatial hash
+ * otherwise (nbvh_level_layout). Grid coordinates of a point p are
+ * xhat = (p - frame_centre) / frame_extent + 1/2, clamped to [0,1]^3. */
+typedef struct {
+  int32_t n_levels;      /* L, 1..NBVH_MAX_LEVELS */
+  int32_t n_features;    /* F per level: 1, 2, 4 or 8 */
+  int32_t log2_table;    /* log2 of the hashed-level table size T, 4..26 */
+  int32_t base_res;      /* N_min >= 1 */
+  float growth;          /* b >= 1 */
+  int32_t n_samples;     /* N samples per segment, 1..NBVH_MAX_SAMPLES */
+  int32_t n_hidden;      /* hidden layers, 1..8 */
+  int32_t width;         /* hidden width: 16, 32, 64 or 128 */
+  int32_t n_out;         /* outputs: 5 = hit logit, depth logit, normal xyz */
+  nbvh_precision table_prec;  /* storage type of the hash-table entries */
+  nbvh_precision mlp_prec;    /* FP32: CUDA-core MLP; FP16/BF16: tensor-core MLP */
+  float frame_centre[3];
+  float frame_extent;
+} nbvh_model_desc;
+
+/* Rays, device structure-of-arrays, n entries each. */
+typedef struct {
+  const float *ox, *oy, *oz, *dx, *dy, *dz, *tmin, *tmax;
+  int64_t n;
+} nbvh_rays;
+
+/* Query result per ray, device structure-of-arrays. Rays without a predicted
+ * hit get hit = 0, t = +inf, leaf = -1, normal = 0. */
+typedef struct {
+  uint8_t *hit;
+  float *t, *nx, *ny, *nz;
+  int32_t *leaf;
+} nbvh_hits;
+
+/* One N-BVH node, 64 bytes: the boxes of both children (lo xyz, hi xyz) and
+ * their indices; child >= 0 is an internal node, child < 0 is leaf ~child.
+ * Node 0 is the root. A tree of L leaves has max(1, L-1) nodes. */
+typedef struct {
+  float lo0[3], hi0[3];
+  float lo1[3], hi1[3];
+  int32_t child0, child1;
+  int32_t pad[2];
+} nbvh_node;
+
+/* Scene frame derived from the triangles (host output of the leaf build). */
+typedef struct {
+  float lo[3], hi[3];        /* triangles' AABB */
+  float centre[3];           /* (lo + hi)/2 rounded to float */
+  float extent;              /* largest AABB side */
+  float sphere_radius;       /* 1.01 * half diagonal (training chords) */
+} nbvh_scene_info;
+
+const char* nbvh_status_string(nbvh_status s);
+
+/* Library version and the compute capability it was built for (1030). */
+int32_t nbvh_version(void);
+int32_t nbvh_built_arch(void);
+
+/* Host. Per-level resolution, density flag, entry count and entry offset of
+ * the hash table described by desc (Sec. 3, Sec. 6). Arrays hold
+ * NBVH_MAX_LEVELS entries; *total = sum of sizes. Pure host computation. */
+nbvh_status nbvh_level_layout(const nbvh_model_desc* desc, int32_t* res, int32_t* dense,
+                              int64_t* size, int64_t* offset, int64_t* total);
+
+/* Host. Number of float parameters of the MLP: per layer W [out][in] row-major
+ * then b [out], layers in order input -> hidden ... -> output. */
+nbvh_status nbvh_mlp_param_count(const nbvh_model_desc* desc, int64_t* count);
+
+/* Host. S0 leaf build (Sec. 5: leaves are hollow boxes over geometric
+ * clusters; Sec. 6: nodes are inflated slightly). Median split over triangle
+ * centroids: the leaf with the most triangles (ties: lowest node id) splits
+ * on the axis of largest centroid extent (ties x<y<z), sorting by centroid
+ * then triangle index, the first floor(n/2) going left, until n_leaves exist.
+ * Leaves are numbered left to right; leaf i owns
+ * tri_perm[leaf_range[2i] .. leaf_range[2i+1]) in ascending triangle order.
+ * Leaf boxes are the triangles' AABB pushed out by inflate_rel * extent on
+ * every face, rounded outward to float.
+ *   tris        host, [n_tris][3][3] float (vertex-major xyz)
+ *   nodes       host, node_cap entries (>= max(1, n_leaves-1)); *out_n_nodes set
+ *   tri_perm    host, n_tris int32; leaf_range host, 2*n_leaves int32
+ *   leaf_box    host, [n_leaves][6] float (lo xyz, hi xyz)
+ *   info        host, scene frame
+ * Errors: INVALID_ARG for n_leaves outside [1, n_tris] or node_cap too small. */
+nbvh_status nbvh_build_leaves(const float* tris, int64_t n_tris, int32_t n_leaves, double inflate_rel,
+                              nbvh_node* nodes, int32_t node_cap, int32_t* out_n_nodes,
+                              int32_t* tri_perm, int32_t* leaf_range, float* leaf_box,
+                              nbvh_scene_info* info);
+
+/* Device. S1 traversal + slab test + clip (Sec. 3: probe only inside ray-box
+ * intervals; Sec. 5: traverse the N-BVH and query each leaf reached).
+ * For every ray, every leaf whose box gives a non-empty clip
+ * [max(entry, tmin), min(exit, tmax)] (t0 <= t1 kept), sorted by (t0, leaf).
+ * Output is slot-major: entry s of ray r at [s * n + r], s < seg_count[r].
+ * A ray with more than max_segs segments keeps its first max_segs, and the
+ * device status records NBVH_ERR_SEGMENT_OVERFLOW.
+ *   nodes: device, n_nodes nbvh_node; outputs: device int32/float arrays. */
+nbvh_status nbvh_traverse(const nbvh_node* nodes, int32_t n_nodes, nbvh_rays rays, int32_t max_segs,
+                          int32_t* seg_count, int32_t* seg_leaf, float* seg_t0, float* seg_t1,
+                          void* stream);
+
+/* Device. S2+S3 (Sec. 4 "Sampling & reconstruction quality", Fig. 3):
+ * features of n_seg segments (ray index seg_ray[i], interval [t0[i], t1[i]]):
+ * N stratum-midpoint samples t_k = t0 + (k+1/2)/N (t1-t0), each encoded on
+ * every level by trilinear interpolation of the 8 vertices' entries; written
+ * FP32 to feat[i * K + k*L*F + l*F + f], K = N*L*F. table: device, layout of
+ * nbvh_level_layout, type desc->table_prec. */
+nbvh_status nbvh_encode(const nbvh_model_desc* desc, const void* table, nbvh_rays rays,
+                        const int32_t* seg_ray, const float* t0, const float* t1, int64_t n_seg,
+                        float* feat, void* stream);
+
+/* Device. S2..S4 fused: raw MLP outputs out[i * n_out + j] of n_seg segments
+ * (as nbvh_encode), through the MLP selected by desc->mlp_prec. mlp: device
+ * float parameters (nbvh_mlp_param_count). The FP32 form uses CUDA cores;
+ * the FP16/BF16 form uses tcgen05 tensor-core MMAs with FP32 accumulation. */
+nbvh_status nbvh_eval_segments(const nbvh_model_desc* desc, const void* table, const float* mlp,
+                               nbvh_rays rays, const int32_t* seg_ray, const float* t0,
+                               const float* t1, int64_t n_seg, float* out, void* stream);
+
+/* Host. Workspace bytes of nbvh_query_rays for n_rays rays and at most
+ * max_segs segments per ray. */
+nbvh_status nbvh_query_workspace_size(const nbvh_model_desc* desc, int64_t n_rays, int32_t max_segs,
+                                      size_t* bytes);
+
+/* Device. The neural ray query, S1..S5 (Sec. 5: the number of neural
+ * queries per ray equals the leaves met before an intersection is found).
+ * Traversal lists each ray's segments in (t0, leaf) order; waves then
+ * evaluate segment w of every still-active ray, keeping the closest
+ * predicted hit (hit iff hit logit > 0; t = t0 + sigmoid(depth)(t1 - t0);
+ * normal = normalised normal head) and dropping a ray once its next
+ * segment starts at or beyond its best t. The result equals the closest
+ * predicted hit over all segments, ties to the earlier segment.
+ * workspace: device, >= nbvh_query_workspace_size bytes, 256-byte aligned. */
+nbvh_status nbvh_query_rays(const nbvh_model_desc* desc, const void* table, const float* mlp,
+                            const nbvh_node* nodes, int32_t n_nodes, nbvh_rays rays, int32_t max_segs,
+                            nbvh_hits out, void* workspace, size_t ws_bytes, void* stream);
+
+/* Writable rays, device structure-of-arrays, n entries each. */
+typedef struct {
+  float *ox, *oy, *oz, *dx, *dy, *dz, *tmin, *tmax;
+  int64_t n;
+} nbvh_rays_out;
+
+/* Device. One secondary bounce per ray (Sec. 7: at the intersection a neural
+ * query returns, the path tracer samples the next direction). For a hit:
+ * origin o + t d + 1e-4 n' with n' the predicted normal turned to face -d;
+ * direction cosine-weighted about n' from Philox4x32-10 keyed by seed (low,
+ * high word) with counter (ray low word, ray high word, 0, 2):
+ * r = sqrt(u1), phi = 2 pi u2, u = top 24 bits * 2^-24, in the orthonormal
+ * basis of Duff et al. (JCGT 2017); tmin 0, tmax +inf. A miss gets the primary
+ * ray with the empty interval tmin 0, tmax -1 (no segments).
+ * rays, hits: device inputs of n entries; out: device outputs, out.n == rays.n. */
+nbvh_status nbvh_bounce_rays(nbvh_rays rays, nbvh_hits hits, uint64_t seed, nbvh_rays_out out, void* stream);
+
+/* Device. Reads from a query workspace (after nbvh_query_rays on the same
+ * stream) the number of segments evaluated and the number of waves that had
+ * work. Synchronises the stream. */
+nbvh_status nbvh_query_stats(const void* workspace, int64_t n_rays, int32_t max_segs, int64_t* segments,
+                             int32_t* waves, void* stream);
+
+/* Host. Stage timing: while enabled, nbvh_query_rays records CUDA events on
+ * the caller's stream around its traversal and its evaluation waves;
+ * nbvh_get_timing synchronises on them and returns the summed milliseconds
+ * since the previous nbvh_get_timing, and the number of timed calls. */
+nbvh_status nbvh_set_timing(int32_t enable);
+nbvh_status nbvh_get_timing(double* traverse_ms, double* eval_ms, int64_t* calls);
+
+/* Host. Number of kernels this library has launched in this process. */
+int64_t nbvh_launch_count(void);
+
+/* Device. Reads and clears the device status word (synchronises the stream). */
+nbvh_status nbvh_get_device_status(void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NBVH_H_ */

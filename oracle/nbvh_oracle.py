@@ -72,6 +72,9 @@ def scene_frame(tris: np.ndarray):
     map to the unit cube isotropically: xhat = (p - c)/E + 1/2 with c the centre
     and E the largest extent of the triangles' AABB. Also returns the bounding
     sphere used for chord training rays (centre c, radius 1.01 * half diagonal).
+    The frame is a parameter of the model and is stored in float32
+    (``model_centre``, ``model_extent``: the float64 values rounded to
+    nearest float32); the encoding uses those stored values.
     """
     v = tris.reshape(-1, 3).astype(F64)
     lo = v.min(0)
@@ -79,7 +82,9 @@ def scene_frame(tris: np.ndarray):
     c = (lo + hi) / 2.0
     E = float(np.max(hi - lo))
     R = 1.01 * float(np.linalg.norm(hi - lo)) / 2.0
-    return {"lo": lo, "hi": hi, "centre": c, "extent": E, "sphere_radius": R}
+    return {"lo": lo, "hi": hi, "centre": c, "extent": E, "sphere_radius": R,
+            "model_centre": c.astype(np.float32).astype(F64),
+            "model_extent": float(np.float32(E))}
 
 
 # ============================================================================
@@ -193,7 +198,14 @@ def clip_ray_box(o, d, tmin, tmax, lo, hi):
     b = (hi_i - o_i)/d_i; with d_i == 0 the slab is all of R if
     lo_i <= o_i <= hi_i and empty otherwise. Entry/exit are the max/min over
     axes; the segment is [max(entry, tmin), min(exit, tmax)], kept iff
-    t0 <= t1. Returns (keep, t0, t1, entry, exit)."""
+    t0 <= t1.
+
+    Precision reading: ray-box clipping is float32 arithmetic in this method
+    (inputs, boxes and segment endpoints are float32 data), so every slab
+    value is the float32 value nearest the exact quotient (computed in
+    float64, rounded once to float32); entry, exit, t0, t1 and the keep
+    decision follow from those rounded values. Returns (keep, t0, t1, entry,
+    exit) as float64 arrays holding float32 values."""
     o = np.asarray(o, F64)
     d = np.asarray(d, F64)
     lo = np.asarray(lo, F64)
@@ -205,8 +217,8 @@ def clip_ray_box(o, d, tmin, tmax, lo, hi):
     with np.errstate(divide="ignore", invalid="ignore"):
         for i in range(3):
             oi, di = o[..., i], d[..., i]
-            a = (lo[..., i] - oi) / di
-            b = (hi[..., i] - oi) / di
+            a = ((lo[..., i] - oi) / di).astype(np.float32).astype(F64)
+            b = ((hi[..., i] - oi) / di).astype(np.float32).astype(F64)
             near = np.minimum(a, b)
             far = np.maximum(a, b)
             zero = np.broadcast_to(di == 0, shape)
@@ -216,8 +228,8 @@ def clip_ray_box(o, d, tmin, tmax, lo, hi):
             empty = empty | (zero & ~np.broadcast_to(inside, shape))
             entry = np.maximum(entry, near)
             exit_ = np.minimum(exit_, far)
-    t0 = np.maximum(entry, np.asarray(tmin, F64))
-    t1 = np.minimum(exit_, np.asarray(tmax, F64))
+    t0 = np.maximum(entry, np.asarray(tmin, F64).astype(np.float32).astype(F64))
+    t1 = np.minimum(exit_, np.asarray(tmax, F64).astype(np.float32).astype(F64))
     keep = (~empty) & (t0 <= t1)
     return keep, t0, t1, entry, exit_
 
@@ -431,7 +443,7 @@ def query(rays: dict, leaves: dict, table, layers, layout, n_samples: int, chunk
         e = min(S, s + chunk)
         rr = seg["ray"][s:e]
         f, r = eval_segments(o[rr], d[rr], seg["t0"][s:e], seg["t1"][s:e], table, layers, layout,
-                             fr["centre"], fr["extent"], n_samples)
+                             fr["model_centre"], fr["model_extent"], n_samples)
         raws.append(r)
         feats.append(f)
     raw = np.concatenate(raws) if raws else np.zeros((0, layers[-1][0].shape[0]))
@@ -775,12 +787,14 @@ BOUNCE_OFFSET = 1e-4
 def bounce_rays(o, d, t, nrm, ray_index, seed: int):
     """For hits: origin = o + t d + 1e-4 n' with n' the predicted normal turned
     to face -d; direction cosine-weighted about n' from Philox counter
-    (ray index, 0, 0, 2): r = sqrt(u1), phi = 2 pi u2."""
+    (ray index low word, ray index high word, 0, 2) keyed by the seed's two
+    words: r = sqrt(u1), phi = 2 pi u2."""
     n = np.asarray(nrm, F64).copy()
     flip = np.sum(n * d, -1) > 0
     n[flip] = -n[flip]
     p = o + t[:, None] * d + BOUNCE_OFFSET * n
-    r = philox4x32_10([np.asarray(ray_index, np.uint64), 0, 0, 2], _keys(seed))
+    ri = np.asarray(ray_index, np.uint64)
+    r = philox4x32_10([ri & np.uint64(0xFFFFFFFF), ri >> np.uint64(32), 0, 2], _keys(seed))
     u1, u2 = u24(r[0]), u24(r[1])
     rad = np.sqrt(u1)
     phi = 2.0 * math.pi * u2

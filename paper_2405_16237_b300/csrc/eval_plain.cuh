@@ -1,0 +1,312 @@
+// S2..S5 fused on CUDA cores in FP32: stratified samples (float-float
+// positions), hash-grid gather +
+// trilinear interpolation into shared memory, FP32 MLP, decode and resolve.
+#pragma once
+#include "nbvh_internal.cuh"
+
+namespace nbvh {
+
+constexpr int kPlainTM = 32;        // segments per tile
+constexpr int kPlainThreads = 256;
+
+// Everything a segment-evaluation kernel needs. Two modes:
+//  - list mode  (queue == nullptr): item i is segment (seg_ray[i], t0[i], t1[i]),
+//    raw outputs go to out[i * n_out + j];
+//  - wave mode: item i is ray queue[i] evaluating its segment slot `wave`;
+//    the closest predicted hit is kept in `hits` and the ray is queued for
+//    the next wave while its next segment starts before its best t.
+struct EvalArgs {
+  GridParams gp;
+  const void* table;
+  const float* mlp;
+  int32_t n_hidden, width, n_out;
+  RayPtrs rays;
+  // list mode
+  const int32_t* seg_ray;
+  const float* list_t0;
+  const float* list_t1;
+  int64_t n_items;
+  float* out;
+  // wave mode
+  const int32_t* queue;
+  const int32_t* qlen;
+  int32_t wave;
+  int64_t n_rays;
+  const int32_t* seg_count;
+  const int32_t* seg_leaf;
+  const float* seg_t0;
+  const float* seg_t1;
+  nbvh_hits hits;
+  int32_t* next_queue;
+  int32_t* next_qlen;
+};
+
+// Activation layout in shared memory: [k][TM] with a per-row XOR swizzle of
+// the segment index that keeps float2 pairs together and spreads the rows a
+// warp writes in the dense layers over distinct banks.
+__device__ __forceinline__ int act_idx(int k, int s) { return k * kPlainTM + (s ^ (((k >> 2) & 15) << 1)); }
+
+template <int W, bool RELU>
+__device__ __forceinline__ void dense_plain(const float* __restrict__ in, int K, const float* __restrict__ wt,
+                                            const float* __restrict__ bias, float* __restrict__ out) {
+  constexpr int NPT = W / 16;
+  const int t = threadIdx.x;
+  const int s0 = (t >> 4) * 2;
+  const int n0 = (t & 15) * NPT;
+  float acc0[NPT], acc1[NPT];
+#pragma unroll
+  for (int j = 0; j < NPT; ++j) acc0[j] = acc1[j] = __ldg(bias + n0 + j);
+#pragma unroll 4
+  for (int k = 0; k < K; ++k) {
+    const float2 f = *reinterpret_cast<const float2*>(in + act_idx(k, s0));
+    float w[NPT];
+    if constexpr (NPT % 4 == 0) {
+#pragma unroll
+      for (int j = 0; j < NPT; j += 4) {
+        const float4 q = *reinterpret_cast<const float4*>(wt + k * W + n0 + j);
+        w[j] = q.x; w[j + 1] = q.y; w[j + 2] = q.z; w[j + 3] = q.w;
+      }
+    } else if constexpr (NPT == 2) {
+      const float2 q = *reinterpret_cast<const float2*>(wt + k * W + n0);
+      w[0] = q.x; w[1] = q.y;
+    } else {
+      w[0] = wt[k * W + n0];
+    }
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+      acc0[j] = fmaf(w[j], f.x, acc0[j]);
+      acc1[j] = fmaf(w[j], f.y, acc1[j]);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < NPT; ++j) {
+    float2 v = make_float2(acc0[j], acc1[j]);
+    if (RELU) { v.x = fmaxf(v.x, 0.0f); v.y = fmaxf(v.y, 0.0f); }
+    *reinterpret_cast<float2*>(out + act_idx(n0 + j, s0)) = v;
+  }
+}
+
+// Decoded per-segment result (S5): hit iff logit > 0; t = t0 + sigmoid(o_d) (t1 - t0);
+// normal = o_n / |o_n| or (0,0,1).
+struct SegResult {
+  bool hit;
+  float t, nx, ny, nz;
+};
+
+__device__ __forceinline__ SegResult decode_segment(const float* raw, float t0, float t1) {
+  SegResult r;
+  r.hit = raw[0] > 0.0f;
+  r.t = t0 + sigmoidf_(raw[1]) * (t1 - t0);
+  const float l2 = raw[2] * raw[2] + raw[3] * raw[3] + raw[4] * raw[4];
+  if (l2 > 0.0f) {
+    const float inv = 1.0f / sqrtf(l2);
+    r.nx = raw[2] * inv; r.ny = raw[3] * inv; r.nz = raw[4] * inv;
+  } else {
+    r.nx = 0.0f; r.ny = 0.0f; r.nz = 1.0f;
+  }
+  return r;
+}
+
+// Wave-mode epilogue for one segment of ray `ray` (one lane per item, the
+// whole warp calls it): resolve into the hit record, queue the next segment.
+__device__ __forceinline__ void wave_resolve(const EvalArgs& a, bool valid, int ray, const float* raw, float t0,
+                                             float t1) {
+  bool push = false;
+  if (valid) {
+    const SegResult s = decode_segment(raw, t0, t1);
+    float best = a.hits.t[ray];
+    if (s.hit && s.t < best) {
+      best = s.t;
+      a.hits.t[ray] = s.t;
+      a.hits.hit[ray] = 1;
+      a.hits.nx[ray] = s.nx;
+      a.hits.ny[ray] = s.ny;
+      a.hits.nz[ray] = s.nz;
+      a.hits.leaf[ray] = a.seg_leaf[size_t(a.wave) * size_t(a.n_rays) + size_t(ray)];
+    }
+    const int nxt = a.wave + 1;
+    if (nxt < a.seg_count[ray]) {
+      const float tn = a.seg_t0[size_t(nxt) * size_t(a.n_rays) + size_t(ray)];
+      push = tn < best;
+    }
+  }
+  const unsigned m = __ballot_sync(0xffffffffu, push);
+  if (m) {
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(a.next_qlen, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (push) a.next_queue[base + __popc(m & ((1u << lane) - 1u))] = ray;
+  }
+}
+
+template <typename T, int F, int W, bool WAVE>
+__global__ void __launch_bounds__(kPlainThreads, 1) eval_plain_kernel(EvalArgs a) {
+  extern __shared__ __align__(16) float smem[];
+  const int K = a.gp.n_inputs;
+  const int L = a.gp.n_levels;
+  const int N = a.gp.n_samples;
+  const int n_out = a.n_out;
+  const int hid_w = (a.n_hidden - 1) * W * W + W * n_out;
+  const int feat_floats = max(K * kPlainTM, hid_w);
+  float* sfeat = smem;                      // [K][TM] features, later hidden weights
+  float* sW1 = sfeat + feat_floats;         // [K][W] first-layer weights, transposed
+  float* shA = sW1 + K * W;                 // [W][TM]
+  float* shB = shA + W * kPlainTM;          // [W][TM]
+  float* sout = shB + W * kPlainTM;         // [8][TM]
+  int* sray = reinterpret_cast<int*>(sout + 8 * kPlainTM);
+  float* st0 = reinterpret_cast<float*>(sray + kPlainTM);
+  float* st1 = st0 + kPlainTM;
+
+  const int64_t n_items = WAVE ? int64_t(*a.qlen) : a.n_items;
+  const int64_t n_tiles = (n_items + kPlainTM - 1) / kPlainTM;
+  if (int64_t(blockIdx.x) >= n_tiles) return;
+
+  const float* W1 = a.mlp;            // [W][K]
+  const float* b1 = W1 + W * K;
+  for (int i = threadIdx.x; i < K * W; i += blockDim.x) {
+    const int n = i / K, k = i - n * K;
+    sW1[k * W + n] = __ldg(W1 + i);
+  }
+  const T* table = static_cast<const T*>(a.table);
+
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    if (threadIdx.x < kPlainTM) {
+      const int64_t i = tile * kPlainTM + threadIdx.x;
+      int ray = -1;
+      float t0 = 0.0f, t1 = 0.0f;
+      if (i < n_items) {
+        if (WAVE) {
+          ray = a.queue[i];
+          const size_t q = size_t(a.wave) * size_t(a.n_rays) + size_t(ray);
+          t0 = a.seg_t0[q];
+          t1 = a.seg_t1[q];
+        } else {
+          ray = a.seg_ray[i];
+          t0 = a.list_t0[i];
+          t1 = a.list_t1[i];
+        }
+      }
+      sray[threadIdx.x] = ray;
+      st0[threadIdx.x] = t0;
+      st1[threadIdx.x] = t1;
+    }
+    __syncthreads();
+
+    // Encode: pair p = (segment s, sample k); lanes = consecutive segments.
+    for (int p = threadIdx.x; p < kPlainTM * N; p += blockDim.x) {
+      const int s = p % kPlainTM;
+      const int k = p / kPlainTM;
+      const int ray = sray[s];
+      const int kb = k * L * F;
+      if (ray < 0) {
+        for (int j = 0; j < L * F; ++j) sfeat[act_idx(kb + j, s)] = 0.0f;
+        continue;
+      }
+      FF x, y, z;
+      sample_point_ff(a.gp, a.rays.ox[ray], a.rays.oy[ray], a.rays.oz[ray], a.rays.dx[ray], a.rays.dy[ray],
+                      a.rays.dz[ray], st0[s], st1[s], k, x, y, z);
+      for (int l = 0; l < L; ++l) {
+        float v[F];
+        encode_level<T, F>(a.gp, table, l, x, y, z, v);
+#pragma unroll
+        for (int f = 0; f < F; ++f) sfeat[act_idx(kb + l * F + f, s)] = v[f];
+      }
+    }
+    __syncthreads();
+
+    dense_plain<W, true>(sfeat, K, sW1, b1, shA);
+    __syncthreads();
+
+    // Hidden and output weights, transposed into the (now free) feature area.
+    {
+      const float* src = b1 + W;
+      float* dst = sfeat;
+      for (int h = 1; h < a.n_hidden; ++h) {
+        for (int i = threadIdx.x; i < W * W; i += blockDim.x) {
+          const int n = i / W, k = i - n * W;
+          dst[k * W + n] = __ldg(src + i);
+        }
+        src += W * W + W;
+        dst += W * W;
+      }
+      for (int i = threadIdx.x; i < n_out * W; i += blockDim.x) {
+        const int n = i / W, k = i - n * W;
+        dst[k * n_out + n] = __ldg(src + i);
+      }
+    }
+    __syncthreads();
+
+    const float* bh = b1 + W;  // walks over hidden layers
+    float* hin = shA;
+    float* hout = shB;
+    const float* wt = sfeat;
+    for (int h = 1; h < a.n_hidden; ++h) {
+      const float* bias = bh + W * W;
+      dense_plain<W, true>(hin, W, wt, bias, hout);
+      __syncthreads();
+      float* tmp = hin; hin = hout; hout = tmp;
+      bh += W * W + W;
+      wt += W * W;
+    }
+    {
+      const float* bo = bh + n_out * W;
+      for (int i = threadIdx.x; i < n_out * kPlainTM; i += blockDim.x) {
+        const int j = i / kPlainTM, s = i - j * kPlainTM;
+        float acc = __ldg(bo + j);
+        for (int k = 0; k < W; ++k) acc = fmaf(wt[k * n_out + j], hin[act_idx(k, s)], acc);
+        sout[j * kPlainTM + s] = acc;
+      }
+    }
+    __syncthreads();
+
+    if (threadIdx.x < kPlainTM) {
+      const int s = threadIdx.x;
+      const int ray = sray[s];
+      float raw[8];
+      for (int j = 0; j < n_out; ++j) raw[j] = sout[j * kPlainTM + s];
+      if (WAVE) {
+        wave_resolve(a, ray >= 0, ray, raw, st0[s], st1[s]);
+      } else if (ray >= 0) {
+        const int64_t i = tile * kPlainTM + s;
+        for (int j = 0; j < n_out; ++j) a.out[i * n_out + j] = raw[j];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+inline size_t plain_smem_bytes(int K, int W, int n_hidden, int n_out) {
+  const int hid_w = (n_hidden - 1) * W * W + W * n_out;
+  const int feat_floats = K * kPlainTM > hid_w ? K * kPlainTM : hid_w;
+  return sizeof(float) * (size_t(feat_floats) + size_t(K) * W + 2 * size_t(W) * kPlainTM + 8 * kPlainTM) +
+         3 * sizeof(int) * kPlainTM;
+}
+
+// Encoder only (S2+S3), FP32 features feat[i * K + k*L*F + l*F + f].
+template <typename T, int F>
+__global__ void __launch_bounds__(128) encode_kernel(GridParams gp, const void* table_v, RayPtrs rays,
+                                                     const int32_t* __restrict__ seg_ray,
+                                                     const float* __restrict__ t0, const float* __restrict__ t1,
+                                                     int64_t n_seg, float* __restrict__ feat) {
+  const int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int N = gp.n_samples, L = gp.n_levels;
+  if (p >= n_seg * N) return;
+  const int64_t i = p / N;
+  const int k = int(p - i * N);
+  const int ray = seg_ray[i];
+  FF x, y, z;
+  sample_point_ff(gp, rays.ox[ray], rays.oy[ray], rays.oz[ray], rays.dx[ray], rays.dy[ray], rays.dz[ray], t0[i],
+                  t1[i], k, x, y, z);
+  const T* table = static_cast<const T*>(table_v);
+  float* o = feat + i * int64_t(gp.n_inputs) + int64_t(k) * L * F;
+  for (int l = 0; l < L; ++l) {
+    float v[F];
+    encode_level<T, F>(gp, table, l, x, y, z, v);
+#pragma unroll
+    for (int f = 0; f < F; ++f) o[l * F + f] = v[f];
+  }
+}
+
+}  // namespace nbvh

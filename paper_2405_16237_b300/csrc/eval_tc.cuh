@@ -1,0 +1,494 @@
+// S2..S5 fused with the MLP on the 5th-generation tensor cores (tcgen05):
+// the hash-grid gather writes FP16/BF16 features straight into the MMA's
+// shared-memory operand layout, one elected thread issues tcgen05.mma with the
+// FP32 accumulator in tensor memory (TMEM), and the epilogue reads TMEM back
+// (tcgen05.ld) for bias + ReLU into the next layer's operand, or for decode and
+// resolve after the output layer.
+#pragma once
+#include "nbvh_internal.cuh"
+#include "eval_plain.cuh"
+
+namespace nbvh {
+
+constexpr int kTcM = 128;          // segments per tile = MMA M = TMEM lanes
+constexpr int kTcThreads = 512;    // 16 warps: all gather; 4 lane quarters x 4 column groups in epilogues
+constexpr long long kWaitCycles = 4000000000LL;  // bounded mbarrier wait (~2 s)
+
+// ---------------------------------------------------------------- PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+               "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Bounded wait: gives up after kWaitCycles SM cycles and reports false.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long start = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - start > kWaitCycles) return false;
+  }
+  return true;
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T, kind::f16 (FP16 or BF16 operands, FP32 accumulate).
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// Arrive on `bar` once every tcgen05 operation issued so far by this thread completes.
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+// 32 lanes x 32 bits, 8/16/32 consecutive columns per thread.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+template <int COLS>
+__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, float* v) {
+  if constexpr (COLS == 8) {
+    tmem_ld8(taddr, v);
+  } else {
+#pragma unroll
+    for (int c = 0; c < COLS; c += 16) tmem_ld16(taddr + c, v + c);
+  }
+}
+
+// ---------------------------------------------------------------- operand layout
+// K-major operand without swizzle, built from 8x8 "core matrices" (8 rows x
+// 16 bytes, stored as 128 contiguous bytes). Element (row r, column k) of an
+// operand with Kp columns sits at byte
+//   (r / 8) * SBO + (k / 8) * LBO + (r % 8) * 16 + (k % 8) * 2,
+// LBO = 128 (next core matrix along K), SBO = Kp * 16 (next 8-row group).
+// One MMA covers K = 16, i.e. two core matrices along K: step j starts at
+// base + j * 256.
+__device__ __forceinline__ uint32_t op_offset(int r, int k, int Kp) {
+  return uint32_t((r >> 3) * (Kp * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= uint64_t((addr >> 4) & 0x3FFFu);
+  d |= uint64_t((lbo >> 4) & 0x3FFFu) << 16;
+  d |= uint64_t((sbo >> 4) & 0x3FFFu) << 32;
+  d |= uint64_t(1) << 46;  // descriptor version for tcgen05
+  // base offset 0, absolute LBO mode, layout type 0 = no swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32, A/B = F16 (0) or BF16 (1),
+// both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t idesc_f16(bool bf16, int M, int N) {
+  return (1u << 4) | (uint32_t(bf16) << 7) | (uint32_t(bf16) << 10) | (uint32_t(N >> 3) << 17) |
+         (uint32_t(M >> 4) << 24);
+}
+
+template <bool BF16>
+struct OpType;
+template <>
+struct OpType<false> {
+  using T = __half;
+  using T2 = __half2;
+  static __device__ __forceinline__ T2 pack(float a, float b) { return __floats2half2_rn(a, b); }
+  static __device__ __forceinline__ T one(float a) { return __float2half_rn(a); }
+};
+template <>
+struct OpType<true> {
+  using T = __nv_bfloat16;
+  using T2 = __nv_bfloat162;
+  static __device__ __forceinline__ T2 pack(float a, float b) { return __floats2bfloat162_rn(a, b); }
+  static __device__ __forceinline__ T one(float a) { return __float2bfloat16_rn(a); }
+};
+
+struct TcLayout {
+  int Kp;               // input width padded to 16
+  uint32_t a_off, a_bytes;   // features (128 x Kp); the hidden activations alias it
+  uint32_t w1_off, w1_bytes; // W x Kp
+  uint32_t wh_off, wh_bytes; // (n_hidden - 1) x W x W
+  uint32_t wo_off, wo_bytes; // 16 x W
+  uint32_t row_off;          // per-row ray / t0 / t1
+  uint32_t bar_off;          // mbarrier + TMEM address
+  uint32_t total;
+};
+
+__host__ __device__ inline TcLayout tc_layout(int K, int W, int n_hidden) {
+  TcLayout L;
+  L.Kp = (K + 15) & ~15;
+  uint32_t off = 0;
+  auto take = [&](uint32_t bytes) {
+    const uint32_t o = off;
+    off = (off + bytes + 127u) & ~127u;
+    return o;
+  };
+  L.a_bytes = uint32_t(kTcM) * L.Kp * 2;
+  const uint32_t h_bytes = uint32_t(kTcM) * W * 2;
+  L.a_off = take(L.a_bytes > h_bytes ? L.a_bytes : h_bytes);
+  L.w1_bytes = uint32_t(W) * L.Kp * 2;
+  L.w1_off = take(L.w1_bytes);
+  L.wh_bytes = uint32_t(n_hidden - 1) * W * W * 2;
+  L.wh_off = take(L.wh_bytes);
+  L.wo_bytes = 16u * W * 2;
+  L.wo_off = take(L.wo_bytes);
+  L.row_off = take(kTcM * 12);
+  L.bar_off = take(64);
+  L.total = off + 128;  // slack for base alignment
+  return L;
+}
+
+// Copy an fp32 [rows][K] row-major weight block into the K-major operand layout
+// with Kp columns (zero padding beyond K and rows beyond `rows` up to rows_p).
+template <bool BF16>
+__device__ __forceinline__ void stage_weights(uint8_t* dst, const float* __restrict__ src, int rows, int rows_p,
+                                              int K, int Kp) {
+  using OT = OpType<BF16>;
+  for (int i = threadIdx.x; i < rows_p * Kp; i += blockDim.x) {
+    const int r = i / Kp, k = i - r * Kp;
+    const float v = (r < rows && k < K) ? __ldg(src + size_t(r) * K + k) : 0.0f;
+    *reinterpret_cast<typename OT::T*>(dst + op_offset(r, k, Kp)) = OT::one(v);
+  }
+}
+
+template <typename T, int F, int W, bool WAVE, bool BF16>
+__global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
+  using OT = OpType<BF16>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  const int K = a.gp.n_inputs;
+  const int L = a.gp.n_levels;
+  const int N = a.gp.n_samples;
+  const int n_out = a.n_out;
+  const TcLayout lay = tc_layout(K, W, a.n_hidden);
+  const int Kp = lay.Kp;
+  uint8_t* sA = smem + lay.a_off;
+  uint8_t* sW1 = smem + lay.w1_off;
+  uint8_t* sWh = smem + lay.wh_off;
+  uint8_t* sWo = smem + lay.wo_off;
+  int* sray = reinterpret_cast<int*>(smem + lay.row_off);
+  float* st0 = reinterpret_cast<float*>(sray + kTcM);
+  float* st1 = st0 + kTcM;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + lay.bar_off);
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + lay.bar_off + 8);
+
+  const int64_t n_items = WAVE ? int64_t(*a.qlen) : a.n_items;
+  const int64_t n_tiles = (n_items + kTcM - 1) / kTcM;
+  if (int64_t(blockIdx.x) >= n_tiles) return;
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  constexpr uint32_t kTmemCols = W < 32 ? 32 : W;
+  if (warp == 0) {
+    tmem_alloc(s_tmem, kTmemCols);
+    tmem_relinquish();
+  }
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+
+  // Weights -> operand layouts (converted once per CTA).
+  const float* W1 = a.mlp;
+  const float* b1 = W1 + size_t(W) * K;
+  stage_weights<BF16>(sW1, W1, W, W, K, Kp);
+  const float* p = b1 + W;
+  for (int h = 1; h < a.n_hidden; ++h) {
+    stage_weights<BF16>(sWh + size_t(h - 1) * W * W * 2, p, W, W, W, W);
+    p += W * W + W;
+  }
+  const float* Wo = p;
+  const float* bo = Wo + size_t(n_out) * W;
+  stage_weights<BF16>(sWo, Wo, n_out, 16, W, W);
+  fence_proxy_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *s_tmem;
+
+  const uint32_t a_addr = smem_u32(sA);
+  const uint32_t idesc_h = idesc_f16(BF16, kTcM, W);
+  const uint32_t idesc_o = idesc_f16(BF16, kTcM, 16);
+  const T* table = static_cast<const T*>(a.table);
+  // Epilogue mapping: warp -> TMEM lane quarter (warp % 4) and column group (warp / 4).
+  const int quarter = warp & 3;
+  const int cgroup = warp >> 2;
+  constexpr int kCols = W / 4;  // columns per thread in hidden epilogues
+  const int row = quarter * 32 + lane;
+  const uint32_t t_row = tmem + (uint32_t(quarter * 32) << 16);
+  uint32_t phase = 0;
+  bool failed = false;
+
+  for (int64_t tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
+    if (threadIdx.x < kTcM) {
+      const int64_t i = tile * kTcM + threadIdx.x;
+      int ray = -1;
+      float t0 = 0.0f, t1 = 0.0f;
+      if (i < n_items) {
+        if (WAVE) {
+          ray = a.queue[i];
+          const size_t q = size_t(a.wave) * size_t(a.n_rays) + size_t(ray);
+          t0 = a.seg_t0[q];
+          t1 = a.seg_t1[q];
+        } else {
+          ray = a.seg_ray[i];
+          t0 = a.list_t0[i];
+          t1 = a.list_t1[i];
+        }
+      }
+      sray[threadIdx.x] = ray;
+      st0[threadIdx.x] = t0;
+      st1[threadIdx.x] = t1;
+    }
+    __syncthreads();
+
+    // ---- encode: pair (row m, sample k); lanes = consecutive rows.
+    const bool chunked = ((L * F) & 7) == 0;
+    for (int pidx = threadIdx.x; pidx < kTcM * N; pidx += blockDim.x) {
+      const int m = pidx & (kTcM - 1);
+      const int k = pidx >> 7;
+      const int ray = sray[m];
+      const int kb = k * L * F;
+      if (ray < 0) {
+        for (int j = 0; j < L * F; ++j) *reinterpret_cast<typename OT::T*>(sA + op_offset(m, kb + j, Kp)) = OT::one(0.0f);
+        continue;
+      }
+      float x, y, z;
+      sample_point(a.gp, a.rays.ox[ray], a.rays.oy[ray], a.rays.oz[ray], a.rays.dx[ray], a.rays.dy[ray],
+                   a.rays.dz[ray], st0[m], st1[m], k, x, y, z);
+      if (chunked) {
+        constexpr int LPC = (8 / F) > 0 ? (8 / F) : 1;  // levels per 8-element chunk (F <= 8)
+        for (int l0 = 0; l0 < L; l0 += LPC) {
+          float v[8];
+#pragma unroll
+          for (int q = 0; q < LPC; ++q) encode_level<T, F>(a.gp, table, l0 + q, x, y, z, v + q * F);
+          uint4 pk;
+          typename OT::T2 h0 = OT::pack(v[0], v[1]), h1 = OT::pack(v[2], v[3]);
+          typename OT::T2 h2 = OT::pack(v[4], v[5]), h3 = OT::pack(v[6], v[7]);
+          pk.x = *reinterpret_cast<uint32_t*>(&h0);
+          pk.y = *reinterpret_cast<uint32_t*>(&h1);
+          pk.z = *reinterpret_cast<uint32_t*>(&h2);
+          pk.w = *reinterpret_cast<uint32_t*>(&h3);
+          *reinterpret_cast<uint4*>(sA + op_offset(m, kb + l0 * F, Kp)) = pk;
+        }
+      } else {
+        for (int l = 0; l < L; ++l) {
+          float v[F];
+          encode_level<T, F>(a.gp, table, l, x, y, z, v);
+#pragma unroll
+          for (int f = 0; f < F; ++f)
+            *reinterpret_cast<typename OT::T*>(sA + op_offset(m, kb + l * F + f, Kp)) = OT::one(v[f]);
+        }
+      }
+    }
+    for (int pidx = threadIdx.x; pidx < kTcM * (Kp - K); pidx += blockDim.x) {
+      const int m = pidx % kTcM, k = K + pidx / kTcM;
+      *reinterpret_cast<typename OT::T*>(sA + op_offset(m, k, Kp)) = OT::one(0.0f);
+    }
+    fence_proxy_async_smem();
+    __syncthreads();
+
+    // ---- layer 1: [128 x Kp] x [Kp x W] -> TMEM columns [0, W)
+    if (threadIdx.x == 0) {
+      tc_fence_after();
+      const uint32_t sbo_a = uint32_t(Kp) * 16, w1_addr = smem_u32(sW1);
+      for (int j = 0; j < Kp / 16; ++j) {
+        mma_f16(tmem, smem_desc(a_addr + j * 256, 128, sbo_a), smem_desc(w1_addr + j * 256, 128, sbo_a), idesc_h,
+                j > 0);
+      }
+      mma_commit(bar);
+    }
+    // ---- hidden layers, each: wait, epilogue (bias, ReLU) into H = sA, MMA
+    for (int h = 0; h < a.n_hidden; ++h) {
+      // bias of layer h: b0 follows W0; hidden layer h >= 1 is [W][W] then [W]
+      const float* bias = h == 0 ? b1 : b1 + W + size_t(h - 1) * (W * W + W) + size_t(W) * W;
+      const bool ok = mbar_wait(bar, phase);
+      phase ^= 1u;
+      if (__syncthreads_or(!ok)) {
+        failed = true;
+        break;
+      }
+      tc_fence_after();
+      {
+        float v[kCols];
+        tmem_ld_cols<kCols>(t_row + uint32_t(cgroup * kCols), v);
+        tmem_ld_wait();
+        const int c0 = cgroup * kCols;
+#pragma unroll
+        for (int c = 0; c < kCols; c += 8) {
+          float q[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) q[i] = fmaxf(v[c + i] + __ldg(bias + c0 + c + i), 0.0f);
+          typename OT::T2 h0 = OT::pack(q[0], q[1]), h1 = OT::pack(q[2], q[3]);
+          typename OT::T2 h2 = OT::pack(q[4], q[5]), h3 = OT::pack(q[6], q[7]);
+          uint4 pk;
+          pk.x = *reinterpret_cast<uint32_t*>(&h0);
+          pk.y = *reinterpret_cast<uint32_t*>(&h1);
+          pk.z = *reinterpret_cast<uint32_t*>(&h2);
+          pk.w = *reinterpret_cast<uint32_t*>(&h3);
+          *reinterpret_cast<uint4*>(sA + op_offset(row, c0 + c, W)) = pk;
+        }
+      }
+      tc_fence_before();
+      fence_proxy_async_smem();
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        tc_fence_after();
+        const uint32_t sbo_h = uint32_t(W) * 16;
+        if (h + 1 < a.n_hidden) {
+          const uint32_t wa = smem_u32(sWh + size_t(h) * W * W * 2);
+          for (int j = 0; j < W / 16; ++j)
+            mma_f16(tmem, smem_desc(a_addr + j * 256, 128, sbo_h), smem_desc(wa + j * 256, 128, sbo_h), idesc_h,
+                    j > 0);
+        } else {
+          const uint32_t wa = smem_u32(sWo);
+          for (int j = 0; j < W / 16; ++j)
+            mma_f16(tmem, smem_desc(a_addr + j * 256, 128, sbo_h), smem_desc(wa + j * 256, 128, sbo_h), idesc_o,
+                    j > 0);
+        }
+        mma_commit(bar);
+      }
+    }
+    if (failed) break;
+    // ---- output layer epilogue: warps 0-3 hold rows 0..127, columns 0..15
+    {
+      const bool ok = mbar_wait(bar, phase);
+      phase ^= 1u;
+      if (__syncthreads_or(!ok)) {
+        failed = true;
+        break;
+      }
+      tc_fence_after();
+      if (cgroup == 0) {
+        float v[16];
+        tmem_ld16(t_row, v);
+        tmem_ld_wait();
+        float raw[8];
+        for (int j = 0; j < 8; ++j) raw[j] = j < n_out ? v[j] + __ldg(bo + j) : 0.0f;
+        const int ray = sray[row];
+        if (WAVE) {
+          wave_resolve(a, ray >= 0, ray, raw, st0[row], st1[row]);
+        } else if (ray >= 0) {
+          const int64_t i = tile * kTcM + row;
+          for (int j = 0; j < n_out; ++j) a.out[i * n_out + j] = raw[j];
+        }
+      }
+      tc_fence_before();
+      __syncthreads();
+    }
+  }
+  if (failed) set_status(NBVH_ERR_TIMEOUT);
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+template <typename T, int F, int W, bool WAVE>
+cudaError_t launch_tc_twf(const nbvh_model_desc* d, const EvalArgs& a, int64_t n_items_max, cudaStream_t s) {
+  const TcLayout lay = tc_layout(a.gp.n_inputs, W, a.n_hidden);
+  if (lay.total > 227 * 1024 || W < 16) return cudaErrorInvalidConfiguration;
+  const bool bf16 = d->mlp_prec == NBVH_BF16;
+  auto kern = bf16 ? eval_tc_kernel<T, F, W, WAVE, true> : eval_tc_kernel<T, F, W, WAVE, false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(lay.total));
+  if (e != cudaSuccess) return e;
+  // One CTA per SM: every CTA holds its weights and TMEM columns for the whole launch.
+  int64_t tiles = (n_items_max + kTcM - 1) / kTcM;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int64_t grid = sms;
+  if (tiles < grid) grid = tiles;
+  if (grid < 1) return cudaSuccess;
+  kern<<<unsigned(grid), kTcThreads, lay.total, s>>>(a);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template <typename T, int F, bool WAVE>
+cudaError_t launch_tc_tf(const nbvh_model_desc* d, const EvalArgs& a, int64_t n, cudaStream_t s) {
+  switch (a.width) {
+    case 32: return launch_tc_twf<T, F, 32, WAVE>(d, a, n, s);
+    case 64: return launch_tc_twf<T, F, 64, WAVE>(d, a, n, s);
+    case 128: return launch_tc_twf<T, F, 128, WAVE>(d, a, n, s);
+  }
+  return cudaErrorInvalidConfiguration;
+}
+
+template <typename T, bool WAVE>
+cudaError_t launch_tc_t(const nbvh_model_desc* d, const EvalArgs& a, int64_t n, cudaStream_t s) {
+  switch (d->n_features) {
+    case 1: return launch_tc_tf<T, 1, WAVE>(d, a, n, s);
+    case 2: return launch_tc_tf<T, 2, WAVE>(d, a, n, s);
+    case 4: return launch_tc_tf<T, 4, WAVE>(d, a, n, s);
+    case 8: return launch_tc_tf<T, 8, WAVE>(d, a, n, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <bool WAVE>
+cudaError_t launch_tc(const nbvh_model_desc* d, const EvalArgs& a, int64_t n, cudaStream_t s) {
+  switch (d->table_prec) {
+    case NBVH_FP32: return launch_tc_t<float, WAVE>(d, a, n, s);
+    case NBVH_FP16: return launch_tc_t<__half, WAVE>(d, a, n, s);
+    case NBVH_BF16: return launch_tc_t<__nv_bfloat16, WAVE>(d, a, n, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace nbvh

@@ -1,0 +1,299 @@
+// Host-side parts of the C ABI: status strings, level layout, MLP parameter
+// count and the S0 leaf build (median split over triangle centroids).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <queue>
+#include <vector>
+
+#include "../../include/nbvh.h"
+#include "nbvh_host.h"
+
+extern "C" const char* nbvh_status_string(nbvh_status s) {
+  switch (s) {
+    case NBVH_OK: return "ok";
+    case NBVH_ERR_INVALID_ARG: return "invalid argument";
+    case NBVH_ERR_CUDA: return "CUDA runtime error";
+    case NBVH_ERR_OOM: return "out of memory";
+    case NBVH_ERR_WORKSPACE_TOO_SMALL: return "workspace too small";
+    case NBVH_ERR_SEGMENT_OVERFLOW: return "a ray crossed more leaves than max_segs";
+    case NBVH_ERR_TIMEOUT: return "a bounded device wait gave up";
+    case NBVH_ERR_UNSUPPORTED: return "unsupported shape or precision";
+  }
+  return "unknown status";
+}
+
+extern "C" int32_t nbvh_version(void) { return 1; }
+extern "C" int32_t nbvh_built_arch(void) { return 1030; }
+
+namespace nbvh_host {
+
+bool desc_valid(const nbvh_model_desc* d) {
+  if (!d) return false;
+  if (d->n_levels < 1 || d->n_levels > NBVH_MAX_LEVELS) return false;
+  if (!(d->n_features == 1 || d->n_features == 2 || d->n_features == 4 || d->n_features == 8))
+    return false;
+  if (d->log2_table < 4 || d->log2_table > 26) return false;
+  if (d->base_res < 1 || !(d->growth >= 1.0f) || !std::isfinite(d->growth)) return false;
+  if (d->n_samples < 1 || d->n_samples > NBVH_MAX_SAMPLES) return false;
+  if (d->n_samples * d->n_levels * d->n_features > NBVH_MAX_INPUTS) return false;
+  if (d->n_hidden < 1 || d->n_hidden > 8) return false;
+  if (!(d->width == 16 || d->width == 32 || d->width == 64 || d->width == 128)) return false;
+  if (d->n_out < 5 || d->n_out > 8) return false;
+  if (d->table_prec < NBVH_FP32 || d->table_prec > NBVH_BF16) return false;
+  if (d->mlp_prec < NBVH_FP32 || d->mlp_prec > NBVH_BF16) return false;
+  if (!(d->frame_extent > 0.0f) || !std::isfinite(d->frame_extent)) return false;
+  for (int i = 0; i < 3; ++i)
+    if (!std::isfinite(d->frame_centre[i])) return false;
+  return true;
+}
+
+bool layout(const nbvh_model_desc* d, int32_t* res, int32_t* dense, int64_t* size, int64_t* offset,
+            int64_t* total) {
+  const int64_t T = int64_t(1) << d->log2_table;
+  int64_t acc = 0;
+  for (int l = 0; l < d->n_levels; ++l) {
+    const double n = std::floor(double(d->base_res) * std::pow(double(d->growth), double(l)));
+    if (!(n >= 1.0) || n > 1.0e7) return false;
+    const int64_t N = int64_t(n);
+    const int64_t verts = (N + 1) * (N + 1) * (N + 1);
+    res[l] = int32_t(N);
+    dense[l] = verts <= T ? 1 : 0;
+    size[l] = verts <= T ? verts : T;
+    offset[l] = acc;
+    acc += size[l];
+  }
+  for (int l = d->n_levels; l < NBVH_MAX_LEVELS; ++l) {
+    res[l] = 0; dense[l] = 0; size[l] = 0; offset[l] = acc;
+  }
+  *total = acc;
+  return true;
+}
+
+int64_t mlp_params(const nbvh_model_desc* d) {
+  const int64_t K = int64_t(d->n_samples) * d->n_levels * d->n_features;
+  int64_t n = 0, in = K;
+  for (int h = 0; h < d->n_hidden; ++h) {
+    n += in * d->width + d->width;
+    in = d->width;
+  }
+  n += in * d->n_out + d->n_out;
+  return n;
+}
+
+}  // namespace nbvh_host
+
+extern "C" nbvh_status nbvh_level_layout(const nbvh_model_desc* desc, int32_t* res, int32_t* dense,
+                                         int64_t* size, int64_t* offset, int64_t* total) {
+  if (!nbvh_host::desc_valid(desc) || !res || !dense || !size || !offset || !total)
+    return NBVH_ERR_INVALID_ARG;
+  return nbvh_host::layout(desc, res, dense, size, offset, total) ? NBVH_OK : NBVH_ERR_INVALID_ARG;
+}
+
+extern "C" nbvh_status nbvh_mlp_param_count(const nbvh_model_desc* desc, int64_t* count) {
+  if (!nbvh_host::desc_valid(desc) || !count) return NBVH_ERR_INVALID_ARG;
+  *count = nbvh_host::mlp_params(desc);
+  return NBVH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// S0: median-split leaf clusters.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct SplitNode {
+  int64_t begin, end;  // range in the working index array
+  int left = -1, right = -1;
+};
+
+float round_down(double x) {
+  float f = float(x);
+  if (double(f) > x) f = std::nextafter(f, -INFINITY);
+  return f;
+}
+
+float round_up(double x) {
+  float f = float(x);
+  if (double(f) < x) f = std::nextafter(f, INFINITY);
+  return f;
+}
+
+}  // namespace
+
+extern "C" nbvh_status nbvh_build_leaves(const float* tris, int64_t n_tris, int32_t n_leaves,
+                                         double inflate_rel, nbvh_node* nodes, int32_t node_cap,
+                                         int32_t* out_n_nodes, int32_t* tri_perm, int32_t* leaf_range,
+                                         float* leaf_box, nbvh_scene_info* info) {
+  if (!tris || n_tris < 1 || n_tris > (int64_t(1) << 31) - 1 || n_leaves < 1 ||
+      int64_t(n_leaves) > n_tris || !nodes || !out_n_nodes || !tri_perm || !leaf_range ||
+      !leaf_box || !info || !(inflate_rel >= 0.0) || !std::isfinite(inflate_rel))
+    return NBVH_ERR_INVALID_ARG;
+  const int32_t need_nodes = std::max(1, n_leaves - 1);
+  if (node_cap < need_nodes) return NBVH_ERR_INVALID_ARG;
+
+  // Scene AABB and frame (double from float: exact).
+  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int64_t i = 0; i < n_tris * 9; ++i) {
+    const double v = tris[i];
+    if (!std::isfinite(v)) return NBVH_ERR_INVALID_ARG;
+    lo[i % 3] = std::min(lo[i % 3], v);
+    hi[i % 3] = std::max(hi[i % 3], v);
+  }
+  double E = 0.0, diag2 = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    E = std::max(E, hi[a] - lo[a]);
+    diag2 += (hi[a] - lo[a]) * (hi[a] - lo[a]);
+  }
+  for (int a = 0; a < 3; ++a) {
+    info->lo[a] = float(lo[a]);
+    info->hi[a] = float(hi[a]);
+    info->centre[a] = float((lo[a] + hi[a]) / 2.0);
+  }
+  info->extent = float(E);
+  info->sphere_radius = float(1.01 * std::sqrt(diag2) / 2.0);
+
+  // Centroids ((v0 + v1) + v2) / 3 in double.
+  std::vector<double> cent(size_t(n_tris) * 3);
+  for (int64_t t = 0; t < n_tris; ++t)
+    for (int a = 0; a < 3; ++a)
+      cent[t * 3 + a] = ((double(tris[t * 9 + a]) + double(tris[t * 9 + 3 + a])) +
+                         double(tris[t * 9 + 6 + a])) / 3.0;
+
+  std::vector<int32_t> idx(n_tris);
+  for (int64_t t = 0; t < n_tris; ++t) idx[t] = int32_t(t);
+  std::vector<SplitNode> sn;
+  sn.reserve(size_t(2) * n_leaves);
+  sn.push_back({0, n_tris});
+  // Max-heap on (size, -id): the largest leaf first, ties to the lowest id.
+  auto cmp = [&](int a, int b) {
+    const int64_t sa = sn[a].end - sn[a].begin, sb = sn[b].end - sn[b].begin;
+    if (sa != sb) return sa < sb;
+    return a > b;
+  };
+  std::priority_queue<int, std::vector<int>, decltype(cmp)> heap(cmp);
+  heap.push(0);
+  int32_t leaves = 1;
+  while (leaves < n_leaves) {
+    const int id = heap.top();
+    heap.pop();
+    const int64_t b = sn[id].begin, e = sn[id].end;
+    if (e - b < 2) return NBVH_ERR_INVALID_ARG;
+    double cmin[3] = {INFINITY, INFINITY, INFINITY}, cmax[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = b; i < e; ++i)
+      for (int a = 0; a < 3; ++a) {
+        cmin[a] = std::min(cmin[a], cent[size_t(idx[i]) * 3 + a]);
+        cmax[a] = std::max(cmax[a], cent[size_t(idx[i]) * 3 + a]);
+      }
+    int axis = 0;
+    for (int a = 1; a < 3; ++a)
+      if (cmax[a] - cmin[a] > cmax[axis] - cmin[axis]) axis = a;
+    std::sort(idx.begin() + b, idx.begin() + e, [&](int32_t p, int32_t q) {
+      const double cp = cent[size_t(p) * 3 + axis], cq = cent[size_t(q) * 3 + axis];
+      if (cp != cq) return cp < cq;
+      return p < q;
+    });
+    const int64_t h = (e - b) / 2;
+    const int l = int(sn.size()), r = l + 1;
+    sn.push_back({b, b + h});
+    sn.push_back({b + h, e});
+    sn[id].left = l;
+    sn[id].right = r;
+    heap.push(l);
+    heap.push(r);
+    ++leaves;
+  }
+
+  // Number leaves in order; boxes; internal nodes in preorder.
+  const double pad = inflate_rel * E;
+  std::vector<int> leaf_of(sn.size(), -1), node_of(sn.size(), -1);
+  std::vector<float> box(size_t(6) * n_leaves);
+  int32_t next_leaf = 0, next_node = 0;
+  int64_t perm_pos = 0;
+  std::vector<int> order;  // preorder of split nodes
+  std::vector<int> stack{0};
+  while (!stack.empty()) {
+    const int id = stack.back();
+    stack.pop_back();
+    order.push_back(id);
+    if (sn[id].left >= 0) {
+      stack.push_back(sn[id].right);
+      stack.push_back(sn[id].left);
+    }
+  }
+  for (int id : order) {
+    if (sn[id].left >= 0) {
+      node_of[id] = next_node++;
+      continue;
+    }
+    const int32_t lf = next_leaf++;
+    leaf_of[id] = lf;
+    const int64_t b = sn[id].begin, e = sn[id].end;
+    std::vector<int32_t> mine(idx.begin() + b, idx.begin() + e);
+    std::sort(mine.begin(), mine.end());
+    double blo[3] = {INFINITY, INFINITY, INFINITY}, bhi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int32_t t : mine) {
+      tri_perm[perm_pos++] = t;
+      for (int v = 0; v < 3; ++v)
+        for (int a = 0; a < 3; ++a) {
+          const double x = tris[size_t(t) * 9 + v * 3 + a];
+          blo[a] = std::min(blo[a], x);
+          bhi[a] = std::max(bhi[a], x);
+        }
+    }
+    leaf_range[2 * lf] = int32_t(perm_pos - int64_t(mine.size()));
+    leaf_range[2 * lf + 1] = int32_t(perm_pos);
+    for (int a = 0; a < 3; ++a) {
+      box[size_t(lf) * 6 + a] = round_down(blo[a] - pad);
+      box[size_t(lf) * 6 + 3 + a] = round_up(bhi[a] + pad);
+    }
+  }
+  std::memcpy(leaf_box, box.data(), sizeof(float) * box.size());
+
+  // Bounds of every split node (union of its leaves' boxes, exact in float).
+  std::vector<float> nb(sn.size() * 6);
+  for (auto it = order.rbegin(); it != order.rend(); ++it) {
+    const int id = *it;
+    float* o = &nb[size_t(id) * 6];
+    if (sn[id].left < 0) {
+      std::memcpy(o, &box[size_t(leaf_of[id]) * 6], 6 * sizeof(float));
+    } else {
+      const float* a = &nb[size_t(sn[id].left) * 6];
+      const float* c = &nb[size_t(sn[id].right) * 6];
+      for (int k = 0; k < 3; ++k) {
+        o[k] = std::min(a[k], c[k]);
+        o[3 + k] = std::max(a[3 + k], c[3 + k]);
+      }
+    }
+  }
+  auto child_ref = [&](int id) { return sn[id].left >= 0 ? node_of[id] : ~leaf_of[id]; };
+  if (n_leaves == 1) {
+    nbvh_node& n = nodes[0];
+    std::memset(&n, 0, sizeof(n));
+    for (int k = 0; k < 3; ++k) {
+      n.lo0[k] = nb[k];
+      n.hi0[k] = nb[3 + k];
+      n.lo1[k] = 0.0f;
+      n.hi1[k] = 0.0f;
+    }
+    n.child0 = ~0;
+    n.child1 = 0x7fffffff;
+  } else {
+    for (int id : order) {
+      if (sn[id].left < 0) continue;
+      nbvh_node& n = nodes[node_of[id]];
+      std::memset(&n, 0, sizeof(n));
+      const float* a = &nb[size_t(sn[id].left) * 6];
+      const float* c = &nb[size_t(sn[id].right) * 6];
+      for (int k = 0; k < 3; ++k) {
+        n.lo0[k] = a[k];
+        n.hi0[k] = a[3 + k];
+        n.lo1[k] = c[k];
+        n.hi1[k] = c[3 + k];
+      }
+      n.child0 = child_ref(sn[id].left);
+      n.child1 = child_ref(sn[id].right);
+    }
+  }
+  *out_n_nodes = need_nodes;
+  return NBVH_OK;
+}

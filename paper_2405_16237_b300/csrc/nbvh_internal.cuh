@@ -1,0 +1,337 @@
+// Internal device helpers of the neural ray query library (sm_103a).
+// Single translation unit: nbvh_lib.cu includes every kernel file after this.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/nbvh.h"
+
+namespace nbvh {
+
+constexpr int kMaxLevels = NBVH_MAX_LEVELS;
+constexpr uint32_t kHashP1 = 2654435761u;  // spatial-hash primes of the
+constexpr uint32_t kHashP2 = 805459861u;   // multi-resolution hash encoding
+constexpr int kNodeNone = 0x7fffffff;      // "no child" (single-leaf trees)
+constexpr int kTraverseStack = 64;
+
+// Host-side count of kernel launches made by this library (nbvh_lib.cu).
+void count_launches(int64_t n);
+
+// Per-process device status word (first error wins; read+cleared by the host).
+__device__ int g_status = 0;
+
+__device__ __forceinline__ void set_status(int code) { atomicCAS(&g_status, 0, code); }
+
+// ---------------------------------------------------------------------------
+// Grid description passed by value to kernels.
+// ---------------------------------------------------------------------------
+struct GridParams {
+  int32_t n_levels;
+  int32_t n_features;
+  int32_t n_samples;
+  int32_t n_inputs;         // N * L * F
+  float centre[3];
+  float inv_extent;
+  float extent;
+  uint32_t hash_mask;       // T - 1
+  int32_t res[kMaxLevels];
+  int32_t dense[kMaxLevels];
+  int64_t offset[kMaxLevels];  // entry offset of each level
+};
+
+struct RayPtrs {
+  const float *ox, *oy, *oz, *dx, *dy, *dz, *tmin, *tmax;
+};
+
+// ---------------------------------------------------------------------------
+// Float-float ("double-float") arithmetic from error-free transformations
+// (Knuth's TwoSum, Dekker's product via FMA). The intrinsics keep the compiler
+// from contracting or reassociating the exact steps.
+// ---------------------------------------------------------------------------
+struct FF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ FF two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return FF{s, e};
+}
+
+__device__ __forceinline__ FF fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return FF{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ FF two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return FF{p, fmaf(a, b, -p)};
+}
+
+// ---------------------------------------------------------------------------
+// Table entry loads: F features of one entry, converted to float.
+// ---------------------------------------------------------------------------
+template <typename T, int F>
+struct EntryLoad;
+
+template <int F>
+struct EntryLoad<float, F> {
+  static __device__ __forceinline__ void load(const float* __restrict__ tab, uint64_t e, float* v) {
+    const float* p = tab + e * F;
+    if constexpr (F == 1) {
+      v[0] = __ldg(p);
+    } else if constexpr (F == 2) {
+      float2 a = __ldg(reinterpret_cast<const float2*>(p));
+      v[0] = a.x; v[1] = a.y;
+    } else {
+#pragma unroll
+      for (int i = 0; i < F / 4; ++i) {
+        float4 a = __ldg(reinterpret_cast<const float4*>(p) + i);
+        v[4 * i] = a.x; v[4 * i + 1] = a.y; v[4 * i + 2] = a.z; v[4 * i + 3] = a.w;
+      }
+    }
+  }
+};
+
+template <int F>
+struct EntryLoad<__half, F> {
+  static __device__ __forceinline__ void load(const __half* __restrict__ tab, uint64_t e, float* v) {
+    const __half* p = tab + e * F;
+    if constexpr (F == 1) {
+      v[0] = __half2float(__ldg(p));
+    } else if constexpr (F == 2) {
+      float2 a = __half22float2(__ldg(reinterpret_cast<const __half2*>(p)));
+      v[0] = a.x; v[1] = a.y;
+    } else if constexpr (F == 4) {
+      uint2 raw = __ldg(reinterpret_cast<const uint2*>(p));
+      float2 a = __half22float2(*reinterpret_cast<__half2*>(&raw.x));
+      float2 b = __half22float2(*reinterpret_cast<__half2*>(&raw.y));
+      v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    } else {
+      uint4 raw = __ldg(reinterpret_cast<const uint4*>(p));
+      uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        float2 a = __half22float2(*reinterpret_cast<__half2*>(&w[i]));
+        v[2 * i] = a.x; v[2 * i + 1] = a.y;
+      }
+    }
+  }
+};
+
+template <int F>
+struct EntryLoad<__nv_bfloat16, F> {
+  static __device__ __forceinline__ void load(const __nv_bfloat16* __restrict__ tab, uint64_t e,
+                                              float* v) {
+    const __nv_bfloat16* p = tab + e * F;
+    if constexpr (F == 1) {
+      v[0] = __bfloat162float(__ldg(p));
+    } else if constexpr (F == 2) {
+      float2 a = __bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162*>(p)));
+      v[0] = a.x; v[1] = a.y;
+    } else if constexpr (F == 4) {
+      uint2 raw = __ldg(reinterpret_cast<const uint2*>(p));
+      float2 a = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&raw.x));
+      float2 b = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&raw.y));
+      v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    } else {
+      uint4 raw = __ldg(reinterpret_cast<const uint4*>(p));
+      uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        float2 a = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&w[i]));
+        v[2 * i] = a.x; v[2 * i + 1] = a.y;
+      }
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// S2: stratified sample k of segment [t0, t1] in grid coordinates.
+// t_k = t0 + (k + 1/2)/N (t1 - t0); xhat = (o + t_k d - c) / E + 1/2 in [0,1].
+// ---------------------------------------------------------------------------
+// Plain FP32 form (tensor-core path: its FP16/BF16 features round far above
+// the position error).
+__device__ __forceinline__ void sample_point(const GridParams& gp, float ox, float oy, float oz,
+                                             float dx, float dy, float dz, float t0, float t1, int k,
+                                             float& x, float& y, float& z) {
+  const float u = (static_cast<float>(k) + 0.5f) / static_cast<float>(gp.n_samples);
+  const float t = t0 + u * (t1 - t0);
+  x = __saturatef((ox + t * dx - gp.centre[0]) * gp.inv_extent + 0.5f);
+  y = __saturatef((oy + t * dy - gp.centre[1]) * gp.inv_extent + 0.5f);
+  z = __saturatef((oz + t * dz - gp.centre[2]) * gp.inv_extent + 0.5f);
+}
+
+// Float-float form (FP32 path): the finest level multiplies a position error by
+// its resolution (thousands), so the position is carried to ~2^-44 relative
+// with FP32 operations only. Returns grid coordinates as hi + lo pairs.
+__device__ __forceinline__ FF grid_coord_ff(FF t, float o, float d, float c, float E) {
+  FF q = two_prod(t.hi, d);
+  q.lo = fmaf(t.lo, d, q.lo);
+  FF s = two_sum(o, q.hi);
+  s.lo = __fadd_rn(s.lo, q.lo);
+  FF v = two_sum(s.hi, -c);
+  v.lo = __fadd_rn(v.lo, s.lo);
+  v = fast_two_sum(v.hi, v.lo);
+  const float y_hi = __fdiv_rn(v.hi, E);
+  const float r = __fadd_rn(fmaf(-y_hi, E, v.hi), v.lo);  // v - y_hi * E
+  const float y_lo = __fdiv_rn(r, E);
+  FF w = two_sum(y_hi, 0.5f);
+  w.lo = __fadd_rn(w.lo, y_lo);
+  w = fast_two_sum(w.hi, w.lo);
+  if (w.hi < 0.0f || (w.hi == 0.0f && w.lo < 0.0f)) w = FF{0.0f, 0.0f};
+  if (w.hi > 1.0f || (w.hi == 1.0f && w.lo > 0.0f)) w = FF{1.0f, 0.0f};
+  return w;
+}
+
+__device__ __forceinline__ void sample_point_ff(const GridParams& gp, float ox, float oy, float oz, float dx,
+                                                float dy, float dz, float t0, float t1, int k, FF& x, FF& y,
+                                                FF& z) {
+  const float num = static_cast<float>(k) + 0.5f;
+  const float Nf = static_cast<float>(gp.n_samples);
+  const float u_hi = __fdiv_rn(num, Nf);
+  const float u_lo = __fdiv_rn(fmaf(-u_hi, Nf, num), Nf);
+  const FF dt = two_sum(t1, -t0);
+  FF p = two_prod(u_hi, dt.hi);
+  p.lo = __fadd_rn(p.lo, fmaf(u_hi, dt.lo, __fmul_rn(u_lo, dt.hi)));
+  FF t = two_sum(t0, p.hi);
+  t.lo = __fadd_rn(t.lo, p.lo);
+  t = fast_two_sum(t.hi, t.lo);
+  const float E = gp.extent;
+  x = grid_coord_ff(t, ox, dx, gp.centre[0], E);
+  y = grid_coord_ff(t, oy, dy, gp.centre[1], E);
+  z = grid_coord_ff(t, oz, dz, gp.centre[2], E);
+}
+
+// ---------------------------------------------------------------------------
+// S3: one level of the multi-resolution hash encoding at grid point (x,y,z):
+// the 8 vertex indices of the enclosing cell and their trilinear weights.
+// Corner c selects +1 along x (bit 0), y (bit 1), z (bit 2).
+// ---------------------------------------------------------------------------
+struct Corners {
+  uint32_t idx[8];
+  float w[8];
+};
+
+// Cell index and fraction along one axis: cell = min(floor(x N), N - 1),
+// frac = x N - cell (x in [0, 1]).
+__device__ __forceinline__ void axis_cell(float x, int N, int& c, float& f) {
+  const float p = x * static_cast<float>(N);
+  c = min(static_cast<int>(p), N - 1);  // p >= 0: truncation = floor
+  f = p - static_cast<float>(c);
+}
+
+__device__ __forceinline__ void axis_cell(FF x, int N, int& c, float& f) {
+  const float Nf = static_cast<float>(N);
+  FF p = two_prod(x.hi, Nf);
+  p.lo = fmaf(x.lo, Nf, p.lo);
+  p = fast_two_sum(p.hi, p.lo);
+  float fl = floorf(p.hi);
+  if (p.hi == fl && p.lo < 0.0f) fl -= 1.0f;
+  if (fl > Nf - 1.0f) fl = Nf - 1.0f;
+  if (fl < 0.0f) fl = 0.0f;
+  c = static_cast<int>(fl);
+  f = __fadd_rn(__fsub_rn(p.hi, fl), p.lo);  // p.hi - fl is exact
+}
+
+template <typename P>
+__device__ __forceinline__ void level_corners(const GridParams& gp, int l, P x, P y, P z, Corners& c) {
+  const int N = gp.res[l];
+  int cx, cy, cz;
+  float fx, fy, fz;
+  axis_cell(x, N, cx, fx);
+  axis_cell(y, N, cy, fy);
+  axis_cell(z, N, cz, fz);
+  const float wx[2] = {1.0f - fx, fx};
+  const float wy[2] = {1.0f - fy, fy};
+  const float wz[2] = {1.0f - fz, fz};
+  if (gp.dense[l]) {
+    const uint32_t n1 = static_cast<uint32_t>(N) + 1u;
+    const uint32_t base = static_cast<uint32_t>(cx) + static_cast<uint32_t>(cy) * n1 +
+                          static_cast<uint32_t>(cz) * n1 * n1;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      c.idx[k] = base + (k & 1) + ((k >> 1) & 1) * n1 + ((k >> 2) & 1) * n1 * n1;
+    }
+  } else {
+    const uint32_t hx = static_cast<uint32_t>(cx);
+    const uint32_t hy = static_cast<uint32_t>(cy) * kHashP1;
+    const uint32_t hz = static_cast<uint32_t>(cz) * kHashP2;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const uint32_t a = hx + (k & 1);
+      const uint32_t b = (k & 2) ? hy + kHashP1 : hy;
+      const uint32_t d = (k & 4) ? hz + kHashP2 : hz;
+      c.idx[k] = (a ^ b ^ d) & gp.hash_mask;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 8; ++k) c.w[k] = wx[k & 1] * wy[(k >> 1) & 1] * wz[(k >> 2) & 1];
+}
+
+// Interpolated F features of level l at (x,y,z) (float or float-float coords).
+template <typename T, int F, typename P>
+__device__ __forceinline__ void encode_level(const GridParams& gp, const T* __restrict__ table, int l,
+                                             P x, P y, P z, float* out) {
+  Corners c;
+  level_corners(gp, l, x, y, z, c);
+  const T* tab = table + gp.offset[l] * F;
+  float v[8][F];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) EntryLoad<T, F>::load(tab, c.idx[k], v[k]);
+#pragma unroll
+  for (int f = 0; f < F; ++f) out[f] = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+#pragma unroll
+    for (int f = 0; f < F; ++f) out[f] = fmaf(c.w[k], v[k][f], out[f]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// (b - o) / d rounded once to float: b - o is formed exactly as a float pair,
+// the quotient's remainder comes from an FMA, and the correction is added last.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float slab_t(float b, float o, float d) {
+  const FF a = two_sum(b, -o);
+  const float q = __fdiv_rn(a.hi, d);
+  if (!isfinite(q)) return q;
+  const float r = fmaf(-q, d, a.hi);
+  return __fadd_rn(q, __fdiv_rn(__fadd_rn(r, a.lo), d));
+}
+
+// ---------------------------------------------------------------------------
+// S1: slab test of a ray against a box, FP32 with correctly rounded slabs.
+// A zero direction component keeps the slab unbounded when the origin lies in
+// [lo, hi] and empties it otherwise. Segment = [max(entry, tmin),
+// min(exit, tmax)], non-empty iff t0 <= t1.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool clip_box(float ox, float oy, float oz, float dx, float dy, float dz,
+                                         float tmin, float tmax, float lx, float ly, float lz,
+                                         float hx, float hy, float hz, float& t0, float& t1) {
+  float en = tmin, ex = tmax;
+  bool empty = false;
+  const float o[3] = {ox, oy, oz}, d[3] = {dx, dy, dz}, lo[3] = {lx, ly, lz}, hi[3] = {hx, hy, hz};
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    if (d[i] == 0.0f) {
+      empty |= (o[i] < lo[i]) | (o[i] > hi[i]);
+    } else {
+      const float a = slab_t(lo[i], o[i], d[i]);
+      const float b = slab_t(hi[i], o[i], d[i]);
+      en = fmaxf(en, fminf(a, b));
+      ex = fminf(ex, fmaxf(a, b));
+    }
+  }
+  t0 = en;
+  t1 = ex;
+  return !empty && en <= ex;
+}
+
+__device__ __forceinline__ float sigmoidf_(float x) { return 1.0f / (1.0f + expf(-x)); }
+
+}  // namespace nbvh

@@ -1,0 +1,427 @@
+// Device entry points of the C ABI (include/nbvh.h). Single CUDA translation
+// unit: the kernels live in the included headers.
+#include <atomic>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "nbvh_host.h"
+#include "nbvh_internal.cuh"
+#include "traverse.cuh"
+#include "eval_plain.cuh"
+#include "eval_tc.cuh"
+#include "bounce.cuh"
+
+namespace nbvh {
+
+std::atomic<int64_t> g_launches{0};
+void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+namespace {
+
+cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
+
+bool rays_valid(const nbvh_rays& r) {
+  if (r.n < 0) return false;
+  if (r.n == 0) return true;
+  return r.ox && r.oy && r.oz && r.dx && r.dy && r.dz && r.tmin && r.tmax;
+}
+
+RayPtrs ray_ptrs(const nbvh_rays& r) { return RayPtrs{r.ox, r.oy, r.oz, r.dx, r.dy, r.dz, r.tmin, r.tmax}; }
+
+bool make_grid(const nbvh_model_desc* d, GridParams& gp) {
+  int32_t res[NBVH_MAX_LEVELS], dense[NBVH_MAX_LEVELS];
+  int64_t size[NBVH_MAX_LEVELS], offset[NBVH_MAX_LEVELS], total = 0;
+  if (!nbvh_host::layout(d, res, dense, size, offset, &total)) return false;
+  std::memset(&gp, 0, sizeof(gp));
+  gp.n_levels = d->n_levels;
+  gp.n_features = d->n_features;
+  gp.n_samples = d->n_samples;
+  gp.n_inputs = d->n_samples * d->n_levels * d->n_features;
+  for (int i = 0; i < 3; ++i) gp.centre[i] = d->frame_centre[i];
+  gp.inv_extent = 1.0f / d->frame_extent;
+  gp.extent = d->frame_extent;
+  gp.hash_mask = uint32_t((uint64_t(1) << d->log2_table) - 1);
+  for (int l = 0; l < NBVH_MAX_LEVELS; ++l) {
+    gp.res[l] = res[l];
+    gp.dense[l] = dense[l];
+    gp.offset[l] = offset[l];
+  }
+  return true;
+}
+
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 148;
+  }
+  return n;
+}
+
+// ---------------------------------------------------------------- plain dispatch
+template <typename T, int F, int W, bool WAVE>
+cudaError_t launch_plain_twf(const EvalArgs& a, int64_t n_items_max, cudaStream_t s) {
+  auto kern = eval_plain_kernel<T, F, W, WAVE>;
+  const size_t smem = plain_smem_bytes(a.gp.n_inputs, W, a.n_hidden, a.n_out);
+  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kPlainThreads, smem);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) occ = 1;
+  int64_t tiles = (n_items_max + kPlainTM - 1) / kPlainTM;
+  int64_t grid = int64_t(sm_count()) * occ;
+  if (tiles < grid) grid = tiles;
+  if (grid < 1) return cudaSuccess;
+  kern<<<unsigned(grid), kPlainThreads, smem, s>>>(a);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template <typename T, int F, bool WAVE>
+cudaError_t launch_plain_tf(const EvalArgs& a, int64_t n, cudaStream_t s) {
+  switch (a.width) {
+    case 16: return launch_plain_twf<T, F, 16, WAVE>(a, n, s);
+    case 32: return launch_plain_twf<T, F, 32, WAVE>(a, n, s);
+    case 64: return launch_plain_twf<T, F, 64, WAVE>(a, n, s);
+    case 128: return launch_plain_twf<T, F, 128, WAVE>(a, n, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename T, bool WAVE>
+cudaError_t launch_plain_t(int F, const EvalArgs& a, int64_t n, cudaStream_t s) {
+  switch (F) {
+    case 1: return launch_plain_tf<T, 1, WAVE>(a, n, s);
+    case 2: return launch_plain_tf<T, 2, WAVE>(a, n, s);
+    case 4: return launch_plain_tf<T, 4, WAVE>(a, n, s);
+    case 8: return launch_plain_tf<T, 8, WAVE>(a, n, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <bool WAVE>
+cudaError_t launch_plain(const nbvh_model_desc* d, const EvalArgs& a, int64_t n, cudaStream_t s) {
+  switch (d->table_prec) {
+    case NBVH_FP32: return launch_plain_t<float, WAVE>(d->n_features, a, n, s);
+    case NBVH_FP16: return launch_plain_t<__half, WAVE>(d->n_features, a, n, s);
+    case NBVH_BF16: return launch_plain_t<__nv_bfloat16, WAVE>(d->n_features, a, n, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t launch_encode_t(int F, const GridParams& gp, const void* table, RayPtrs r, const int32_t* seg_ray,
+                            const float* t0, const float* t1, int64_t n_seg, float* feat, cudaStream_t s) {
+  const int64_t work = n_seg * gp.n_samples;
+  const unsigned grid = unsigned((work + 127) / 128);
+  switch (F) {
+    case 1: encode_kernel<T, 1><<<grid, 128, 0, s>>>(gp, table, r, seg_ray, t0, t1, n_seg, feat); break;
+    case 2: encode_kernel<T, 2><<<grid, 128, 0, s>>>(gp, table, r, seg_ray, t0, t1, n_seg, feat); break;
+    case 4: encode_kernel<T, 4><<<grid, 128, 0, s>>>(gp, table, r, seg_ray, t0, t1, n_seg, feat); break;
+    case 8: encode_kernel<T, 8><<<grid, 128, 0, s>>>(gp, table, r, seg_ray, t0, t1, n_seg, feat); break;
+    default: return cudaErrorInvalidValue;
+  }
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+EvalArgs base_args(const nbvh_model_desc* d, const GridParams& gp, const void* table, const float* mlp,
+                   const nbvh_rays& rays) {
+  EvalArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.gp = gp;
+  a.table = table;
+  a.mlp = mlp;
+  a.n_hidden = d->n_hidden;
+  a.width = d->width;
+  a.n_out = d->n_out;
+  a.rays = ray_ptrs(rays);
+  return a;
+}
+
+nbvh_status status_of(cudaError_t e) {
+  if (e == cudaSuccess) return NBVH_OK;
+  if (e == cudaErrorInvalidConfiguration) return NBVH_ERR_UNSUPPORTED;
+  return NBVH_ERR_CUDA;
+}
+
+cudaError_t launch_eval(const nbvh_model_desc* d, const EvalArgs& a, bool wave, int64_t n, cudaStream_t s) {
+  if (d->mlp_prec == NBVH_FP32) return wave ? launch_plain<true>(d, a, n, s) : launch_plain<false>(d, a, n, s);
+  return wave ? launch_tc<true>(d, a, n, s) : launch_tc<false>(d, a, n, s);
+}
+
+// ---------------------------------------------------------------- bookkeeping
+struct StageEvents {
+  cudaEvent_t e0, e1, e2;
+};
+
+std::mutex g_timing_mu;
+bool g_timing = false;
+std::vector<StageEvents> g_pending;
+std::vector<cudaEvent_t> g_free_events;
+
+cudaEvent_t take_event() {
+  if (!g_free_events.empty()) {
+    cudaEvent_t e = g_free_events.back();
+    g_free_events.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+struct QueryWs {
+  int32_t* counters;
+  int32_t* seg_count;
+  int32_t* seg_leaf;
+  float* seg_t0;
+  float* seg_t1;
+  int32_t* queue[2];
+  size_t bytes;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+QueryWs carve_query(void* base, int64_t n, int32_t max_segs) {
+  QueryWs w;
+  char* p = static_cast<char*>(base);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    char* q = p ? p + off : nullptr;
+    off += align256(bytes);
+    return q;
+  };
+  w.counters = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * size_t(max_segs + 2)));
+  w.seg_count = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * size_t(n)));
+  w.seg_leaf = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * size_t(n) * size_t(max_segs)));
+  w.seg_t0 = reinterpret_cast<float*>(take(sizeof(float) * size_t(n) * size_t(max_segs)));
+  w.seg_t1 = reinterpret_cast<float*>(take(sizeof(float) * size_t(n) * size_t(max_segs)));
+  w.queue[0] = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * size_t(n)));
+  w.queue[1] = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * size_t(n)));
+  w.bytes = off;
+  return w;
+}
+
+}  // namespace
+}  // namespace nbvh
+
+using namespace nbvh;
+
+extern "C" nbvh_status nbvh_traverse(const nbvh_node* nodes, int32_t n_nodes, nbvh_rays rays, int32_t max_segs,
+                                     int32_t* seg_count, int32_t* seg_leaf, float* seg_t0, float* seg_t1,
+                                     void* stream) {
+  if (!nodes || n_nodes < 1 || !rays_valid(rays) || max_segs < 1) return NBVH_ERR_INVALID_ARG;
+  if (rays.n == 0) return NBVH_OK;
+  if (!seg_count || !seg_leaf || !seg_t0 || !seg_t1) return NBVH_ERR_INVALID_ARG;
+  if (rays.n > (int64_t(1) << 31) - 1) return NBVH_ERR_INVALID_ARG;
+  TraverseOut out;
+  std::memset(&out, 0, sizeof(out));
+  out.seg_count = seg_count;
+  out.seg_leaf = seg_leaf;
+  out.seg_t0 = seg_t0;
+  out.seg_t1 = seg_t1;
+  out.max_segs = max_segs;
+  const unsigned grid = unsigned((rays.n + 127) / 128);
+  traverse_kernel<<<grid, 128, 0, as_stream(stream)>>>(nodes, ray_ptrs(rays), rays.n, out);
+  count_launches(1);
+  return status_of(cudaGetLastError());
+}
+
+extern "C" nbvh_status nbvh_encode(const nbvh_model_desc* desc, const void* table, nbvh_rays rays,
+                                   const int32_t* seg_ray, const float* t0, const float* t1, int64_t n_seg,
+                                   float* feat, void* stream) {
+  if (!nbvh_host::desc_valid(desc) || !table || !rays_valid(rays) || n_seg < 0) return NBVH_ERR_INVALID_ARG;
+  if (n_seg == 0) return NBVH_OK;
+  if (!seg_ray || !t0 || !t1 || !feat) return NBVH_ERR_INVALID_ARG;
+  GridParams gp;
+  if (!make_grid(desc, gp)) return NBVH_ERR_INVALID_ARG;
+  cudaStream_t s = as_stream(stream);
+  cudaError_t e;
+  switch (desc->table_prec) {
+    case NBVH_FP32: e = launch_encode_t<float>(desc->n_features, gp, table, ray_ptrs(rays), seg_ray, t0, t1, n_seg, feat, s); break;
+    case NBVH_FP16: e = launch_encode_t<__half>(desc->n_features, gp, table, ray_ptrs(rays), seg_ray, t0, t1, n_seg, feat, s); break;
+    default: e = launch_encode_t<__nv_bfloat16>(desc->n_features, gp, table, ray_ptrs(rays), seg_ray, t0, t1, n_seg, feat, s); break;
+  }
+  return status_of(e);
+}
+
+extern "C" nbvh_status nbvh_eval_segments(const nbvh_model_desc* desc, const void* table, const float* mlp,
+                                          nbvh_rays rays, const int32_t* seg_ray, const float* t0,
+                                          const float* t1, int64_t n_seg, float* out, void* stream) {
+  if (!nbvh_host::desc_valid(desc) || !table || !mlp || !rays_valid(rays) || n_seg < 0)
+    return NBVH_ERR_INVALID_ARG;
+  if (n_seg == 0) return NBVH_OK;
+  if (!seg_ray || !t0 || !t1 || !out) return NBVH_ERR_INVALID_ARG;
+  GridParams gp;
+  if (!make_grid(desc, gp)) return NBVH_ERR_INVALID_ARG;
+  EvalArgs a = base_args(desc, gp, table, mlp, rays);
+  a.seg_ray = seg_ray;
+  a.list_t0 = t0;
+  a.list_t1 = t1;
+  a.n_items = n_seg;
+  a.out = out;
+  return status_of(launch_eval(desc, a, false, n_seg, as_stream(stream)));
+}
+
+extern "C" nbvh_status nbvh_query_workspace_size(const nbvh_model_desc* desc, int64_t n_rays, int32_t max_segs,
+                                                 size_t* bytes) {
+  if (!nbvh_host::desc_valid(desc) || n_rays < 0 || max_segs < 1 || !bytes) return NBVH_ERR_INVALID_ARG;
+  *bytes = carve_query(nullptr, n_rays, max_segs).bytes;
+  return NBVH_OK;
+}
+
+extern "C" nbvh_status nbvh_query_rays(const nbvh_model_desc* desc, const void* table, const float* mlp,
+                                       const nbvh_node* nodes, int32_t n_nodes, nbvh_rays rays, int32_t max_segs,
+                                       nbvh_hits out, void* workspace, size_t ws_bytes, void* stream) {
+  if (!nbvh_host::desc_valid(desc) || !table || !mlp || !nodes || n_nodes < 1 || !rays_valid(rays) ||
+      max_segs < 1 || max_segs > 4096)
+    return NBVH_ERR_INVALID_ARG;
+  if (rays.n == 0) return NBVH_OK;
+  if (rays.n > (int64_t(1) << 31) - 1) return NBVH_ERR_INVALID_ARG;
+  if (!out.hit || !out.t || !out.nx || !out.ny || !out.nz || !out.leaf || !workspace) return NBVH_ERR_INVALID_ARG;
+  if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0) return NBVH_ERR_INVALID_ARG;
+  QueryWs w = carve_query(workspace, rays.n, max_segs);
+  if (ws_bytes < w.bytes) return NBVH_ERR_WORKSPACE_TOO_SMALL;
+  GridParams gp;
+  if (!make_grid(desc, gp)) return NBVH_ERR_INVALID_ARG;
+  cudaStream_t s = as_stream(stream);
+  cudaError_t e = cudaMemsetAsync(w.counters, 0, sizeof(int32_t) * size_t(max_segs + 2), s);
+  if (e != cudaSuccess) return NBVH_ERR_CUDA;
+  TraverseOut to;
+  std::memset(&to, 0, sizeof(to));
+  to.seg_count = w.seg_count;
+  to.seg_leaf = w.seg_leaf;
+  to.seg_t0 = w.seg_t0;
+  to.seg_t1 = w.seg_t1;
+  to.max_segs = max_segs;
+  to.queue0 = w.queue[0];
+  to.qlen0 = w.counters;
+  to.hits = out;
+  StageEvents ev{nullptr, nullptr, nullptr};
+  {
+    std::lock_guard<std::mutex> lk(g_timing_mu);
+    if (g_timing) {
+      ev.e0 = take_event();
+      ev.e1 = take_event();
+      ev.e2 = take_event();
+    }
+  }
+  const bool timed = ev.e0 && ev.e1 && ev.e2;
+  if (timed) cudaEventRecord(ev.e0, s);
+  traverse_kernel<<<unsigned((rays.n + 127) / 128), 128, 0, s>>>(nodes, ray_ptrs(rays), rays.n, to);
+  count_launches(1);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return NBVH_ERR_CUDA;
+  if (timed) cudaEventRecord(ev.e1, s);
+  EvalArgs a = base_args(desc, gp, table, mlp, rays);
+  a.n_rays = rays.n;
+  a.seg_count = w.seg_count;
+  a.seg_leaf = w.seg_leaf;
+  a.seg_t0 = w.seg_t0;
+  a.seg_t1 = w.seg_t1;
+  a.hits = out;
+  for (int wv = 0; wv < max_segs; ++wv) {
+    a.wave = wv;
+    a.queue = w.queue[wv & 1];
+    a.qlen = w.counters + wv;
+    a.next_queue = w.queue[(wv + 1) & 1];
+    a.next_qlen = w.counters + wv + 1;
+    e = launch_eval(desc, a, true, rays.n, s);
+    if (e != cudaSuccess) return status_of(e);
+  }
+  if (timed) {
+    cudaEventRecord(ev.e2, s);
+    std::lock_guard<std::mutex> lk(g_timing_mu);
+    g_pending.push_back(ev);
+  }
+  return NBVH_OK;
+}
+
+extern "C" nbvh_status nbvh_query_stats(const void* workspace, int64_t n_rays, int32_t max_segs, int64_t* segments,
+                                       int32_t* waves, void* stream) {
+  if (!workspace || n_rays < 0 || max_segs < 1 || max_segs > 4096 || !segments || !waves)
+    return NBVH_ERR_INVALID_ARG;
+  if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0) return NBVH_ERR_INVALID_ARG;
+  std::vector<int32_t> c(size_t(max_segs) + 2);
+  cudaStream_t s = as_stream(stream);
+  if (cudaMemcpyAsync(c.data(), workspace, sizeof(int32_t) * c.size(), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return NBVH_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return NBVH_ERR_CUDA;
+  int64_t tot = 0;
+  int32_t w = 0;
+  for (int i = 0; i < max_segs; ++i) {
+    tot += c[i];
+    if (c[i] > 0) w = i + 1;
+  }
+  *segments = tot;
+  *waves = w;
+  return NBVH_OK;
+}
+
+extern "C" nbvh_status nbvh_set_timing(int32_t enable) {
+  std::lock_guard<std::mutex> lk(g_timing_mu);
+  g_timing = enable != 0;
+  return NBVH_OK;
+}
+
+extern "C" nbvh_status nbvh_get_timing(double* traverse_ms, double* eval_ms, int64_t* calls) {
+  if (!traverse_ms || !eval_ms || !calls) return NBVH_ERR_INVALID_ARG;
+  std::vector<StageEvents> pend;
+  {
+    std::lock_guard<std::mutex> lk(g_timing_mu);
+    pend.swap(g_pending);
+  }
+  double tr = 0.0, ev = 0.0;
+  nbvh_status st = NBVH_OK;
+  for (auto& p : pend) {
+    float a = 0.0f, b = 0.0f;
+    if (cudaEventSynchronize(p.e2) != cudaSuccess || cudaEventElapsedTime(&a, p.e0, p.e1) != cudaSuccess ||
+        cudaEventElapsedTime(&b, p.e1, p.e2) != cudaSuccess)
+      st = NBVH_ERR_CUDA;
+    tr += a;
+    ev += b;
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_timing_mu);
+    for (auto& p : pend) {
+      g_free_events.push_back(p.e0);
+      g_free_events.push_back(p.e1);
+      g_free_events.push_back(p.e2);
+    }
+  }
+  *traverse_ms = tr;
+  *eval_ms = ev;
+  *calls = int64_t(pend.size());
+  return st;
+}
+
+extern "C" int64_t nbvh_launch_count(void) { return g_launches.load(); }
+
+extern "C" nbvh_status nbvh_bounce_rays(nbvh_rays rays, nbvh_hits hits, uint64_t seed, nbvh_rays_out out,
+                                        void* stream) {
+  if (!rays_valid(rays) || out.n != rays.n) return NBVH_ERR_INVALID_ARG;
+  if (rays.n == 0) return NBVH_OK;
+  if (!hits.hit || !hits.t || !hits.nx || !hits.ny || !hits.nz || !out.ox || !out.oy || !out.oz || !out.dx ||
+      !out.dy || !out.dz || !out.tmin || !out.tmax)
+    return NBVH_ERR_INVALID_ARG;
+  RayOut o{out.ox, out.oy, out.oz, out.dx, out.dy, out.dz, out.tmin, out.tmax};
+  bounce_kernel<<<unsigned((rays.n + 255) / 256), 256, 0, as_stream(stream)>>>(
+      ray_ptrs(rays), hits, rays.n, uint32_t(seed & 0xffffffffu), uint32_t(seed >> 32), o);
+  count_launches(1);
+  return status_of(cudaGetLastError());
+}
+
+extern "C" nbvh_status nbvh_get_device_status(void* stream) {
+  if (cudaStreamSynchronize(as_stream(stream)) != cudaSuccess) return NBVH_ERR_CUDA;
+  int v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_status, sizeof(int)) != cudaSuccess) return NBVH_ERR_CUDA;
+  const int zero = 0;
+  if (cudaMemcpyToSymbol(g_status, &zero, sizeof(int)) != cudaSuccess) return NBVH_ERR_CUDA;
+  return static_cast<nbvh_status>(v);
+}

@@ -1,0 +1,363 @@
+"""Python binding of libnbvh.so (include/nbvh.h): argument marshalling only.
+
+Every step of the neural ray query runs in the library's kernels. PyTorch
+provides device memory and the current CUDA stream. Loading fails loudly when
+the library is missing: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_double, c_float, c_int32, c_int64, c_size_t, c_uint8, c_void_p
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libnbvh.so")
+
+FP32, FP16, BF16 = 0, 1, 2
+MAX_LEVELS = 32
+
+STATUS = {
+    0: "NBVH_OK", 1: "NBVH_ERR_INVALID_ARG", 2: "NBVH_ERR_CUDA", 3: "NBVH_ERR_OOM",
+    4: "NBVH_ERR_WORKSPACE_TOO_SMALL", 5: "NBVH_ERR_SEGMENT_OVERFLOW", 6: "NBVH_ERR_TIMEOUT",
+    7: "NBVH_ERR_UNSUPPORTED",
+}
+
+
+class NBVHError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {STATUS.get(code, code)}")
+        self.code = code
+
+
+class ModelDesc(ctypes.Structure):
+    _fields_ = [("n_levels", c_int32), ("n_features", c_int32), ("log2_table", c_int32),
+                ("base_res", c_int32), ("growth", c_float), ("n_samples", c_int32),
+                ("n_hidden", c_int32), ("width", c_int32), ("n_out", c_int32),
+                ("table_prec", c_int32), ("mlp_prec", c_int32), ("frame_centre", c_float * 3),
+                ("frame_extent", c_float)]
+
+
+class Rays(ctypes.Structure):
+    _fields_ = [(k, c_void_p) for k in ("ox", "oy", "oz", "dx", "dy", "dz", "tmin", "tmax")] + [("n", c_int64)]
+
+
+class Hits(ctypes.Structure):
+    _fields_ = [(k, c_void_p) for k in ("hit", "t", "nx", "ny", "nz", "leaf")]
+
+
+class RaysOut(ctypes.Structure):
+    _fields_ = [(k, c_void_p) for k in ("ox", "oy", "oz", "dx", "dy", "dz", "tmin", "tmax")] + [("n", c_int64)]
+
+
+class Node(ctypes.Structure):
+    _fields_ = [("lo0", c_float * 3), ("hi0", c_float * 3), ("lo1", c_float * 3), ("hi1", c_float * 3),
+                ("child0", c_int32), ("child1", c_int32), ("pad", c_int32 * 2)]
+
+
+class SceneInfo(ctypes.Structure):
+    _fields_ = [("lo", c_float * 3), ("hi", c_float * 3), ("centre", c_float * 3), ("extent", c_float),
+                ("sphere_radius", c_float)]
+
+
+_lib = None
+
+_SIGS = {
+    "nbvh_status_string": (ctypes.c_char_p, [c_int32]),
+    "nbvh_version": (c_int32, []),
+    "nbvh_built_arch": (c_int32, []),
+    "nbvh_level_layout": (c_int32, [POINTER(ModelDesc), POINTER(c_int32), POINTER(c_int32), POINTER(c_int64),
+                                    POINTER(c_int64), POINTER(c_int64)]),
+    "nbvh_mlp_param_count": (c_int32, [POINTER(ModelDesc), POINTER(c_int64)]),
+    "nbvh_build_leaves": (c_int32, [c_void_p, c_int64, c_int32, c_double, c_void_p, c_int32, POINTER(c_int32),
+                                    c_void_p, c_void_p, c_void_p, POINTER(SceneInfo)]),
+    "nbvh_traverse": (c_int32, [c_void_p, c_int32, Rays, c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
+                                c_void_p]),
+    "nbvh_encode": (c_int32, [POINTER(ModelDesc), c_void_p, Rays, c_void_p, c_void_p, c_void_p, c_int64,
+                              c_void_p, c_void_p]),
+    "nbvh_eval_segments": (c_int32, [POINTER(ModelDesc), c_void_p, c_void_p, Rays, c_void_p, c_void_p, c_void_p,
+                                     c_int64, c_void_p, c_void_p]),
+    "nbvh_query_workspace_size": (c_int32, [POINTER(ModelDesc), c_int64, c_int32, POINTER(c_size_t)]),
+    "nbvh_query_rays": (c_int32, [POINTER(ModelDesc), c_void_p, c_void_p, c_void_p, c_int32, Rays, c_int32,
+                                  Hits, c_void_p, c_size_t, c_void_p]),
+    "nbvh_bounce_rays": (c_int32, [Rays, Hits, ctypes.c_uint64, RaysOut, c_void_p]),
+    "nbvh_query_stats": (c_int32, [c_void_p, c_int64, c_int32, POINTER(c_int64), POINTER(c_int32), c_void_p]),
+    "nbvh_set_timing": (c_int32, [c_int32]),
+    "nbvh_get_timing": (c_int32, [POINTER(c_double), POINTER(c_double), POINTER(c_int64)]),
+    "nbvh_launch_count": (c_int64, []),
+    "nbvh_get_device_status": (c_int32, [c_void_p]),
+}
+
+EXPORTED = tuple(_SIGS)
+
+
+def lib():
+    """The loaded library; raises if it is missing (build it with build_lib.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libnbvh.so not built ({LIB_PATH}); run paper_2405_16237_b300.build_lib.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(code: int, what: str):
+    if code != 0:
+        raise NBVHError(code, what)
+
+
+# ---------------------------------------------------------------- torch helpers
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t):
+    return None if t is None else c_void_p(t.data_ptr())
+
+
+def _stream():
+    torch = _torch()
+    return c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+TORCH_DTYPE = {FP32: "float32", FP16: "float16", BF16: "bfloat16"}
+
+
+def table_dtype(prec: int):
+    return getattr(_torch(), TORCH_DTYPE[prec])
+
+
+# ---------------------------------------------------------------- model description
+def model_desc(cfg, table_prec: int, mlp_prec: int, centre, extent) -> ModelDesc:
+    d = ModelDesc()
+    d.n_levels = cfg.n_levels
+    d.n_features = cfg.n_features
+    d.log2_table = cfg.log2_table
+    d.base_res = cfg.base_res
+    d.growth = cfg.growth
+    d.n_samples = cfg.n_samples
+    d.n_hidden = cfg.n_hidden
+    d.width = cfg.width
+    d.n_out = cfg.n_out
+    d.table_prec = table_prec
+    d.mlp_prec = mlp_prec
+    for i in range(3):
+        d.frame_centre[i] = float(centre[i])
+    d.frame_extent = float(extent)
+    return d
+
+
+def with_mlp_prec(desc: ModelDesc, mlp_prec: int) -> ModelDesc:
+    d = ModelDesc()
+    ctypes.pointer(d)[0] = desc
+    d.mlp_prec = mlp_prec
+    return d
+
+
+def level_layout(desc: ModelDesc) -> dict:
+    res = (c_int32 * MAX_LEVELS)()
+    dense = (c_int32 * MAX_LEVELS)()
+    size = (c_int64 * MAX_LEVELS)()
+    off = (c_int64 * MAX_LEVELS)()
+    total = c_int64()
+    _check(lib().nbvh_level_layout(ctypes.byref(desc), res, dense, size, off, ctypes.byref(total)), "level_layout")
+    L = desc.n_levels
+    return {"res": np.array(res[:L], np.int64), "dense": np.array(dense[:L], bool),
+            "size": np.array(size[:L], np.int64), "offset": np.array(off[:L], np.int64), "total": total.value}
+
+
+def mlp_param_count(desc: ModelDesc) -> int:
+    n = c_int64()
+    _check(lib().nbvh_mlp_param_count(ctypes.byref(desc), ctypes.byref(n)), "mlp_param_count")
+    return n.value
+
+
+def pack_mlp(layers) -> np.ndarray:
+    """Flatten [(W [out,in], b [out])] into the library's float parameter order."""
+    return np.concatenate([np.concatenate([np.asarray(w, np.float32).ravel(), np.asarray(b, np.float32)])
+                           for w, b in layers]).astype(np.float32)
+
+
+# ---------------------------------------------------------------- leaf build (host)
+def build_leaves(tris: np.ndarray, n_leaves: int, inflate_rel: float = 1e-4) -> dict:
+    tris = np.ascontiguousarray(tris, np.float32)
+    n = len(tris)
+    cap = max(1, n_leaves - 1)
+    nodes = (Node * cap)()
+    n_nodes = c_int32()
+    perm = np.zeros(n, np.int32)
+    rng = np.zeros(2 * n_leaves, np.int32)
+    box = np.zeros((n_leaves, 6), np.float32)
+    info = SceneInfo()
+    _check(lib().nbvh_build_leaves(tris.ctypes.data_as(c_void_p), n, n_leaves, float(inflate_rel), nodes, cap,
+                                   ctypes.byref(n_nodes), perm.ctypes.data_as(c_void_p),
+                                   rng.ctypes.data_as(c_void_p), box.ctypes.data_as(c_void_p),
+                                   ctypes.byref(info)), "build_leaves")
+    node_bytes = np.frombuffer(bytes(nodes), np.uint8).copy()
+    return {
+        "nodes": node_bytes, "n_nodes": n_nodes.value, "tri_perm": perm, "leaf_range": rng.reshape(-1, 2),
+        "leaf_lo": box[:, :3].copy(), "leaf_hi": box[:, 3:].copy(),
+        "info": {"lo": np.array(info.lo[:]), "hi": np.array(info.hi[:]), "centre": np.array(info.centre[:]),
+                 "extent": info.extent, "sphere_radius": info.sphere_radius},
+    }
+
+
+def node_array(leaves: dict) -> np.ndarray:
+    """Nodes as a structured view (lo0, hi0, lo1, hi1, child0, child1)."""
+    dt = np.dtype([("lo0", "<f4", 3), ("hi0", "<f4", 3), ("lo1", "<f4", 3), ("hi1", "<f4", 3),
+                   ("child0", "<i4"), ("child1", "<i4"), ("pad", "<i4", 2)])
+    return leaves["nodes"].view(dt)
+
+
+# ---------------------------------------------------------------- device calls
+RAY_KEYS = ("ox", "oy", "oz", "dx", "dy", "dz", "tmin", "tmax")
+
+
+def to_device_rays(rays: dict, device="cuda"):
+    torch = _torch()
+    return {k: torch.as_tensor(np.ascontiguousarray(rays[k], np.float32), device=device) for k in RAY_KEYS}
+
+
+def rays_struct(rays: dict) -> Rays:
+    r = Rays()
+    for k in RAY_KEYS:
+        setattr(r, k, rays[k].data_ptr())
+    r.n = rays["ox"].numel()
+    return r
+
+
+def new_hits(n: int, device="cuda") -> dict:
+    torch = _torch()
+    return {"hit": torch.empty(n, dtype=torch.uint8, device=device),
+            "t": torch.empty(n, dtype=torch.float32, device=device),
+            "nx": torch.empty(n, dtype=torch.float32, device=device),
+            "ny": torch.empty(n, dtype=torch.float32, device=device),
+            "nz": torch.empty(n, dtype=torch.float32, device=device),
+            "leaf": torch.empty(n, dtype=torch.int32, device=device)}
+
+
+def hits_struct(h: dict) -> Hits:
+    s = Hits()
+    for k in ("hit", "t", "nx", "ny", "nz", "leaf"):
+        setattr(s, k, h[k].data_ptr())
+    return s
+
+
+def traverse(nodes, n_nodes: int, rays: dict, max_segs: int, out=None):
+    torch = _torch()
+    n = rays["ox"].numel()
+    dev = rays["ox"].device
+    if out is None:
+        out = {"count": torch.empty(n, dtype=torch.int32, device=dev),
+               "leaf": torch.empty(max_segs * n, dtype=torch.int32, device=dev),
+               "t0": torch.empty(max_segs * n, dtype=torch.float32, device=dev),
+               "t1": torch.empty(max_segs * n, dtype=torch.float32, device=dev)}
+    _check(lib().nbvh_traverse(_ptr(nodes), n_nodes, rays_struct(rays), max_segs, _ptr(out["count"]),
+                               _ptr(out["leaf"]), _ptr(out["t0"]), _ptr(out["t1"]), _stream()), "traverse")
+    return out
+
+
+def encode(desc: ModelDesc, table, rays: dict, seg_ray, t0, t1, out=None):
+    torch = _torch()
+    n = seg_ray.numel()
+    K = desc.n_samples * desc.n_levels * desc.n_features
+    if out is None:
+        out = torch.empty((n, K), dtype=torch.float32, device=seg_ray.device)
+    _check(lib().nbvh_encode(ctypes.byref(desc), _ptr(table), rays_struct(rays), _ptr(seg_ray), _ptr(t0), _ptr(t1),
+                             n, _ptr(out), _stream()), "encode")
+    return out
+
+
+def eval_segments(desc: ModelDesc, table, mlp, rays: dict, seg_ray, t0, t1, out=None):
+    torch = _torch()
+    n = seg_ray.numel()
+    if out is None:
+        out = torch.empty((n, desc.n_out), dtype=torch.float32, device=seg_ray.device)
+    _check(lib().nbvh_eval_segments(ctypes.byref(desc), _ptr(table), _ptr(mlp), rays_struct(rays), _ptr(seg_ray),
+                                    _ptr(t0), _ptr(t1), n, _ptr(out), _stream()), "eval_segments")
+    return out
+
+
+def query_workspace_size(desc: ModelDesc, n_rays: int, max_segs: int) -> int:
+    b = c_size_t()
+    _check(lib().nbvh_query_workspace_size(ctypes.byref(desc), n_rays, max_segs, ctypes.byref(b)),
+           "query_workspace_size")
+    return b.value
+
+
+def new_workspace(nbytes: int, device="cuda"):
+    torch = _torch()
+    return torch.empty(max(256, nbytes + 256), dtype=torch.uint8, device=device)
+
+
+def aligned_ptr(ws) -> int:
+    p = ws.data_ptr()
+    return (p + 255) & ~255
+
+
+def query_rays(desc: ModelDesc, table, mlp, nodes, n_nodes: int, rays: dict, max_segs: int, out=None,
+               workspace=None):
+    n = rays["ox"].numel()
+    if out is None:
+        out = new_hits(n, rays["ox"].device)
+    need = query_workspace_size(desc, n, max_segs)
+    if workspace is None:
+        workspace = new_workspace(need, rays["ox"].device)
+    base = aligned_ptr(workspace)
+    avail = workspace.numel() - (base - workspace.data_ptr())
+    _check(lib().nbvh_query_rays(ctypes.byref(desc), _ptr(table), _ptr(mlp), _ptr(nodes), n_nodes,
+                                 rays_struct(rays), max_segs, hits_struct(out), c_void_p(base), avail, _stream()),
+           "query_rays")
+    return out
+
+
+def device_status() -> int:
+    """Reads and clears the device status word (synchronises the current stream)."""
+    return int(lib().nbvh_get_device_status(_stream()))
+
+
+def new_rays(n: int, device="cuda") -> dict:
+    torch = _torch()
+    return {k: torch.empty(n, dtype=torch.float32, device=device) for k in RAY_KEYS}
+
+
+def bounce_rays(rays: dict, hits: dict, seed: int, out=None):
+    n = rays["ox"].numel()
+    if out is None:
+        out = new_rays(n, rays["ox"].device)
+    o = RaysOut()
+    for k in RAY_KEYS:
+        setattr(o, k, out[k].data_ptr())
+    o.n = n
+    _check(lib().nbvh_bounce_rays(rays_struct(rays), hits_struct(hits), ctypes.c_uint64(seed), o, _stream()),
+           "bounce_rays")
+    return out
+
+
+def query_stats(workspace, n_rays: int, max_segs: int):
+    segs = c_int64()
+    waves = c_int32()
+    _check(lib().nbvh_query_stats(c_void_p(aligned_ptr(workspace)), n_rays, max_segs, ctypes.byref(segs),
+                                  ctypes.byref(waves), _stream()), "query_stats")
+    return segs.value, waves.value
+
+
+def set_timing(enable: bool):
+    _check(lib().nbvh_set_timing(1 if enable else 0), "set_timing")
+
+
+def get_timing():
+    a, b, c = c_double(), c_double(), c_int64()
+    _check(lib().nbvh_get_timing(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "get_timing")
+    return a.value, b.value, c.value
+
+
+def launch_count() -> int:
+    return int(lib().nbvh_launch_count())

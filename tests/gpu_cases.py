@@ -1,0 +1,139 @@
+"""Shared set-up of the GPU parity tests: seeded scenes, models and the
+comparison helpers. Inputs come from the workloads module only; expected
+values come from the oracle only."""
+from dataclasses import dataclass, replace
+
+import numpy as np
+
+from oracle import nbvh_oracle as O
+from paper_2405_16237_b300 import nbvh as B
+from paper_2405_16237_b300 import workloads as W
+
+
+@dataclass
+class Case:
+    name: str
+    tris: np.ndarray
+    n_leaves: int
+    model: W.ModelConfig
+    table_prec: int
+    rays: dict
+    table_scale: float = 1e-4
+    mlp_gain: float = 1.0
+    seed: int = 0
+
+
+def small_icosphere_model():
+    # The 16-level, F=2, 2^20-entry, 16-sample, 3x64 model of the full-size
+    # icosphere workload, on a smaller mesh.
+    return replace(W.C1.model)
+
+
+def make_case(name: str, table_scale: float = 1e-4, mlp_gain: float = 1.0) -> Case:
+    if name == "random_tris_c0":
+        return Case(name, W.scene_random_tris(4096, seed=W.SEED_BASE), 64, W.C0.model, B.FP32,
+                    W.camera_rays(64, 64, seed=W.SEED_BASE + 7), table_scale, mlp_gain, 11)
+    if name == "icosphere_l6":
+        return Case(name, W.scene_icosphere(level=6), 256, small_icosphere_model(), B.FP16,
+                    W.camera_rays(96, 96, seed=W.SEED_BASE + 8), table_scale, mlp_gain, 12)
+    if name == "clusters_small":
+        tris = W.scene_sphere_clusters(n_clusters=12, min_tris=200, max_tris=4000, seed=W.SEED_BASE + 5)
+        return Case(name, tris, 512, W.C0.model, B.FP32, W.mixed_rays(3000, seed=W.SEED_BASE + 9),
+                    table_scale, mlp_gain, 13)
+    raise KeyError(name)
+
+
+class Built:
+    """Device copies of one case plus the oracle's own leaf build."""
+
+    def __init__(self, case: Case, mlp_prec: int = B.FP32):
+        import torch
+        self.case = case
+        self.leaves = B.build_leaves(case.tris, case.n_leaves, 1e-4)
+        self.oleaves = O.build_leaves(case.tris, case.n_leaves, 1e-4)
+        info = self.leaves["info"]
+        self.desc = B.model_desc(case.model, case.table_prec, mlp_prec, info["centre"], info["extent"])
+        self.layout = B.level_layout(self.desc)
+        self.olayout = O.level_layout(case.model.n_levels, case.model.base_res, case.model.growth,
+                                      case.model.log2_table)
+        tab = W.init_table(self.layout["total"], case.model.n_features, case.seed, case.table_scale)
+        tdt = {B.FP32: np.float32, B.FP16: np.float16, B.BF16: None}[case.table_prec]
+        if case.table_prec == B.BF16:
+            t = torch.as_tensor(tab).to(torch.bfloat16)
+            self.table_host = t.float().numpy()
+            self.table = t.cuda()
+        else:
+            self.table_host = tab.astype(tdt)
+            self.table = torch.as_tensor(self.table_host).cuda()
+        self.layers = W.init_mlp(case.model.mlp_dims(), case.seed + 1, gain=case.mlp_gain)
+        self.mlp = torch.as_tensor(B.pack_mlp(self.layers)).cuda()
+        self.nodes = torch.as_tensor(self.leaves["nodes"]).cuda()
+        self.rays = B.to_device_rays(case.rays)
+
+    def with_prec(self, mlp_prec: int):
+        return B.with_mlp_prec(self.desc, mlp_prec)
+
+    def oracle_query(self):
+        return O.query(self.case.rays, self.oleaves, self.table_host, self.layers, self.olayout,
+                       self.case.model.n_samples)
+
+
+def segments_by_ray(seg, n_rays):
+    off = seg["offsets"]
+    return [(seg["leaf"][off[r]:off[r + 1]], seg["t0"][off[r]:off[r + 1]], seg["t1"][off[r]:off[r + 1]])
+            for r in range(n_rays)]
+
+
+def compare_segment_lists(count, leaf, t0, t1, n, seg):
+    """GPU slot-major lists vs the oracle's CSR lists. Exact leaf sequence,
+    except (a) grazing (ray, leaf) pairs, dropped on both sides, and (b)
+    neighbours whose oracle t0 differ by <= 1e-6, which may swap. Returns
+    (n_pairs_checked, n_excepted)."""
+    graz = {(int(r), int(l)) for r, l in seg["grazing_pairs"]}
+    ref = segments_by_ray(seg, n)
+    checked = excepted = exact = 0
+    for r in range(n):
+        c = int(count[r])
+        g_leaf = [int(leaf[s * n + r]) for s in range(c)]
+        g_t = {int(leaf[s * n + r]): (float(t0[s * n + r]), float(t1[s * n + r])) for s in range(c)}
+        o_leaf, o_t0, o_t1 = ref[r]
+        o_map = {int(l): (a, b) for l, a, b in zip(o_leaf, o_t0, o_t1)}
+        gl = [l for l in g_leaf if (r, l) not in graz]
+        ol = [int(l) for l in o_leaf if (r, int(l)) not in graz]
+        excepted += (len(g_leaf) - len(gl)) + (len(o_leaf) - len(ol))
+        assert sorted(gl) == sorted(ol), f"ray {r}: leaf sets differ {gl} vs {ol}"
+        keys = [o_map[l][0] for l in gl]
+        for i in range(len(keys) - 1):
+            if keys[i + 1] < keys[i]:
+                assert keys[i] - keys[i + 1] <= 1e-6, f"ray {r}: order {gl}"
+                excepted += 1
+        for l in gl:
+            a, b = o_map[l]
+            ga, gb = g_t[l]
+            assert abs(ga - a) <= 1e-6 * max(1.0, abs(a)) and abs(gb - b) <= 1e-6 * max(1.0, abs(b)), (r, l)
+            exact += int(ga == a) + int(gb == b)
+        checked += len(gl)
+    # both sides round each slab value once to float32: endpoints agree bit for bit
+    assert exact >= 2 * checked - max(2, checked // 1000), (exact, 2 * checked)
+    return checked, excepted
+
+
+def ambiguous_rays(res, n_rays, rel=1e-5):
+    """Rays whose resolved result depends on rounding: a segment's hit logit
+    within rel * RMS(logits) of 0, or two hit candidates within rel * |t|."""
+    seg = res["segments"]
+    raw = res["raw"]
+    scale = float(np.sqrt(np.mean(raw[:, 0] ** 2))) if len(raw) else 1.0
+    amb = np.zeros(n_rays, bool)
+    near0 = np.abs(raw[:, 0]) <= rel * scale
+    amb[seg["ray"][near0]] = True
+    off = seg["offsets"]
+    for r in range(n_rays):
+        t = res["seg_t"][off[r]:off[r + 1]][res["seg_hit"][off[r]:off[r + 1]]]
+        if len(t) > 1:
+            ts = np.sort(t)
+            if ts[1] - ts[0] <= rel * max(1.0, abs(ts[0])):
+                amb[r] = True
+    for r, _ in seg["grazing_pairs"]:
+        amb[int(r)] = True
+    return amb

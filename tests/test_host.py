@@ -1,0 +1,130 @@
+"""Host-side checks of the C-ABI library (no GPU needed): it loads, exports every
+function the headers declare, and its host computations (level layout, MLP
+parameter count, S0 leaf build) agree exactly with the oracle."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import nbvh_oracle as O
+from paper_2405_16237_b300 import nbvh as B
+from paper_2405_16237_b300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?\w+\s*\**\s*(nbvh_\w+)\s*\(", src, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_function():
+    L = B.lib()
+    names = declared_functions()
+    assert "nbvh_query_rays" in names and "nbvh_build_leaves" in names
+    for n in names:
+        assert hasattr(L, n), n
+    assert L.nbvh_built_arch() == 1030
+
+
+def test_binding_covers_declared_functions():
+    assert set(declared_functions()) <= set(B.EXPORTED) | {"nbvh_status_string"}
+
+
+def test_status_strings():
+    for code in range(8):
+        assert B.lib().nbvh_status_string(code)
+
+
+def _desc(cfg, tp=B.FP16, mp=B.FP32):
+    return B.model_desc(cfg, tp, mp, (0.0, 0.0, 0.0), 1.0)
+
+
+@pytest.mark.parametrize("cfg", [W.C0.model, W.C1.model])
+def test_level_layout_matches_oracle(cfg):
+    got = B.level_layout(_desc(cfg))
+    ref = O.level_layout(cfg.n_levels, cfg.base_res, cfg.growth, cfg.log2_table)
+    for k in ("res", "dense", "size", "offset"):
+        assert np.array_equal(got[k], ref[k]), k
+    assert got["total"] == ref["total"]
+
+
+def test_mlp_param_count():
+    cfg = W.C1.model
+    n = B.mlp_param_count(_desc(cfg))
+    dims = cfg.mlp_dims()
+    assert n == sum(dims[i] * dims[i + 1] + dims[i + 1] for i in range(len(dims) - 1))
+    assert len(B.pack_mlp(W.init_mlp(dims, 1))) == n
+
+
+def test_invalid_descriptors_rejected():
+    cfg = W.C0.model
+    d = _desc(cfg)
+    d.n_features = 3
+    with pytest.raises(B.NBVHError):
+        B.level_layout(d)
+    d = _desc(cfg)
+    d.frame_extent = 0.0
+    with pytest.raises(B.NBVHError):
+        B.mlp_param_count(d)
+
+
+@pytest.mark.parametrize("n_tris,n_leaves,seed", [(4096, 64, 1), (3000, 37, 2), (500, 1, 3), (777, 200, 4)])
+def test_leaf_build_matches_oracle_exactly(n_tris, n_leaves, seed):
+    tris = W.scene_random_tris(n_tris, seed=seed)
+    got = B.build_leaves(tris, n_leaves, 1e-4)
+    ref = O.build_leaves(tris, n_leaves, 1e-4)
+    assert np.array_equal(got["tri_perm"], ref["tri_perm"])
+    assert np.array_equal(got["leaf_range"], ref["leaf_range"])
+    assert np.array_equal(got["leaf_lo"], ref["leaf_lo"])
+    assert np.array_equal(got["leaf_hi"], ref["leaf_hi"])
+    fr = ref["frame"]
+    assert np.array_equal(got["info"]["centre"], fr["centre"].astype(np.float32))
+    assert got["info"]["extent"] == np.float32(fr["extent"])
+    assert got["info"]["sphere_radius"] == np.float32(fr["sphere_radius"])
+
+
+def test_leaf_build_icosphere_matches_oracle():
+    tris = W.scene_icosphere(level=5)
+    got = B.build_leaves(tris, 256, 1e-4)
+    ref = O.build_leaves(tris, 256, 1e-4)
+    assert np.array_equal(got["tri_perm"], ref["tri_perm"])
+    assert np.array_equal(got["leaf_lo"], ref["leaf_lo"]) and np.array_equal(got["leaf_hi"], ref["leaf_hi"])
+
+
+def test_node_tree_is_consistent():
+    tris = W.scene_random_tris(2000, seed=5)
+    lv = B.build_leaves(tris, 50)
+    nodes = B.node_array(lv)
+    assert len(nodes) == lv["n_nodes"] == 49
+    seen = []
+
+    def walk(i, lo, hi):
+        nd = nodes[i]
+        for c, l, h in ((nd["child0"], nd["lo0"], nd["hi0"]), (nd["child1"], nd["lo1"], nd["hi1"])):
+            assert np.all(l >= lo) and np.all(h <= hi)       # children nest in the parent
+            if c < 0:
+                leaf = ~c
+                seen.append(leaf)
+                assert np.array_equal(l, lv["leaf_lo"][leaf]) and np.array_equal(h, lv["leaf_hi"][leaf])
+            else:
+                walk(c, l, h)
+
+    walk(0, np.full(3, -np.inf), np.full(3, np.inf))
+    assert sorted(seen) == list(range(50))
+
+
+def test_build_leaves_rejects_bad_arguments():
+    tris = W.scene_random_tris(10, seed=6)
+    with pytest.raises(B.NBVHError):
+        B.build_leaves(tris, 11)
+    with pytest.raises(B.NBVHError):
+        B.build_leaves(tris, 0)

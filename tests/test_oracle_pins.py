@@ -161,14 +161,43 @@ def test_clip_matches_pointwise_membership():
         t = tmin[i] + ts * (tmax[i] - tmin[i])
         p = o[i] + t[:, None] * d[i]
         inside = np.all((p >= lo[i] - 1e-9) & (p <= hi[i] + 1e-9), axis=1)
+        # endpoints are float32 values: within one float32 ulp of the exact ones
+        eps = 2.0 ** -23 * max(1.0, abs(t0[i]), abs(t1[i]))
         if keep[i]:
             pm = o[i] + 0.5 * (t0[i] + t1[i]) * d[i]
-            assert np.all(pm >= lo[i] - 1e-9) and np.all(pm <= hi[i] + 1e-9)
+            tol = eps * np.abs(d[i]) + 1e-9
+            assert np.all(pm >= lo[i] - tol) and np.all(pm <= hi[i] + tol)
             # brute-force samples inside the box lie within [t0, t1]
-            assert np.all((t[inside] >= t0[i] - 1e-9) & (t[inside] <= t1[i] + 1e-9))
+            assert np.all((t[inside] >= t0[i] - eps) & (t[inside] <= t1[i] + eps))
         else:
             strict = np.all((p > lo[i] + 1e-7) & (p < hi[i] - 1e-7), axis=1)
             assert not strict.any()
+
+
+def test_clip_endpoints_are_nearest_float32_of_exact_quotients():
+    from fractions import Fraction
+    rng = np.random.default_rng(21)
+    for _ in range(300):
+        o = rng.uniform(-2, 2, 3).astype(np.float32)
+        d = rng.normal(size=3).astype(np.float32)
+        lo = rng.uniform(-1, 0.5, 3).astype(np.float32)
+        hi = (lo + rng.uniform(0.05, 1.0, 3)).astype(np.float32)
+        keep, t0, t1, en, ex = O.clip_ray_box(o.astype(np.float64), d.astype(np.float64), 0.0, np.inf,
+                                              lo.astype(np.float64), hi.astype(np.float64))
+        near, far = [], []
+        for i in range(3):
+            qa = (Fraction(float(lo[i])) - Fraction(float(o[i]))) / Fraction(float(d[i]))
+            qb = (Fraction(float(hi[i])) - Fraction(float(o[i]))) / Fraction(float(d[i]))
+            near.append(min(qa, qb))
+            far.append(max(qa, qb))
+
+        def nearest_f32(q):
+            f = np.float32(float(q))
+            cands = [np.nextafter(f, np.float32(-np.inf)), f, np.nextafter(f, np.float32(np.inf))]
+            return min(cands, key=lambda c: abs(Fraction(float(c)) - q))
+
+        assert en == float(nearest_f32(max(near))) and ex == float(nearest_f32(min(far)))
+        assert bool(keep) == (max(float(en), 0.0) <= float(ex))
 
 
 def test_segments_sorted_and_complete():
