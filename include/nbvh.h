@@ -231,6 +231,38 @@ nbvh_status nbvh_get_timing(double* traverse_ms, double* eval_ms, int64_t* calls
 /* Host. Number of kernels this library has launched in this process. */
 int64_t nbvh_launch_count(void);
 
+/* Size of the library's built-in query scratch (32 MiB), see
+ * nbvh_query_rays_static. */
+#define NBVH_STATIC_SCRATCH_BYTES 33554432
+
+/* Device. The same neural ray query as nbvh_query_rays, for callers that must
+ * not allocate device memory themselves: for example a renderer or plug-in
+ * whose GPU memory is owned by a host application's fixed-budget arena, or a
+ * frame loop that cannot afford the implicit synchronisation of cudaMalloc.
+ * This entry point has no counterpart in the paper; it only changes where the
+ * query's scratch lives.
+ *
+ * The scratch is a 256-byte aligned array of NBVH_STATIC_SCRATCH_BYTES bytes
+ * built into the library: every GPU that loads the library holds it until the
+ * process exits. A request whose workspace (nbvh_query_workspace_size for
+ * rays.n and max_segs) is larger returns NBVH_ERR_WORKSPACE_TOO_SMALL and
+ * launches nothing; for max_segs = 16 that is about 160,000 rays per call.
+ * The call allocates nothing (no cudaMalloc, cudaFree or allocating library
+ * routine). Leave stage timing (nbvh_set_timing) off here: it creates CUDA
+ * events.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current) and caches it; make that
+ * first call before any stream capture on the device. Every call on a device
+ * shares the one array and finds the previous call's data in it (the query
+ * clears what must start at zero itself), so calls whose GPU work overlaps,
+ * on different streams or from different threads, race on the scratch:
+ * serialise them. Inputs and outputs are caller buffers as in
+ * nbvh_query_rays. */
+nbvh_status nbvh_query_rays_static(const nbvh_model_desc* desc, const void* table, const float* mlp,
+                                   const nbvh_node* nodes, int32_t n_nodes, nbvh_rays rays, int32_t max_segs,
+                                   nbvh_hits out, void* stream);
+
 /* Device. Reads and clears the device status word (synchronises the stream). */
 nbvh_status nbvh_get_device_status(void* stream);
 

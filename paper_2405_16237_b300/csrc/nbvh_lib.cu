@@ -425,3 +425,41 @@ extern "C" nbvh_status nbvh_get_device_status(void* stream) {
   if (cudaMemcpyToSymbol(g_status, &zero, sizeof(int)) != cudaSuccess) return NBVH_ERR_CUDA;
   return static_cast<nbvh_status>(v);
 }
+
+// ---------------------------------------------------------------- built-in scratch
+// Scratch of nbvh_query_rays_static: a fixed array in device memory, so that
+// callers who cannot allocate still get a query. Host code must not pass the
+// symbol itself to a kernel (on the host it names a stand-in, not the device
+// array); the device address comes from cudaGetSymbolAddress, once per device.
+namespace nbvh {
+namespace {
+static __device__ __align__(256) unsigned char g_static_scratch[NBVH_STATIC_SCRATCH_BYTES];
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_addr[kMaxDevices] = {};
+}  // namespace
+}  // namespace nbvh
+
+extern "C" nbvh_status nbvh_query_rays_static(const nbvh_model_desc* desc, const void* table, const float* mlp,
+                                              const nbvh_node* nodes, int32_t n_nodes, nbvh_rays rays,
+                                              int32_t max_segs, nbvh_hits out, void* stream) {
+  size_t need = 0;
+  const nbvh_status st = nbvh_query_workspace_size(desc, rays.n, max_segs, &need);
+  if (st != NBVH_OK) return st;
+  if (need > size_t(NBVH_STATIC_SCRATCH_BYTES)) return NBVH_ERR_WORKSPACE_TOO_SMALL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return NBVH_ERR_CUDA;
+  if (dev < 0 || dev >= kMaxDevices) return NBVH_ERR_UNSUPPORTED;
+  void* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_addr[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) return NBVH_ERR_CUDA;
+      g_static_addr[dev] = p;
+    }
+    base = g_static_addr[dev];
+  }
+  return nbvh_query_rays(desc, table, mlp, nodes, n_nodes, rays, max_segs, out, base,
+                         size_t(NBVH_STATIC_SCRATCH_BYTES), stream);
+}

@@ -86,8 +86,12 @@ _SIGS = {
     "nbvh_set_timing": (c_int32, [c_int32]),
     "nbvh_get_timing": (c_int32, [POINTER(c_double), POINTER(c_double), POINTER(c_int64)]),
     "nbvh_launch_count": (c_int64, []),
+    "nbvh_query_rays_static": (c_int32, [POINTER(ModelDesc), c_void_p, c_void_p, c_void_p, c_int32, Rays, c_int32,
+                                         Hits, c_void_p]),
     "nbvh_get_device_status": (c_int32, [c_void_p]),
 }
+
+STATIC_SCRATCH_BYTES = 33554432
 
 EXPORTED = tuple(_SIGS)
 
@@ -361,3 +365,15 @@ def get_timing():
 
 def launch_count() -> int:
     return int(lib().nbvh_launch_count())
+
+
+def query_rays_static(desc: ModelDesc, table, mlp, nodes, n_nodes: int, rays: dict, max_segs: int, out=None):
+    """nbvh_query_rays_static: the query with the library's built-in scratch,
+    for callers that cannot allocate device memory (see include/nbvh.h)."""
+    n = rays["ox"].numel()
+    if out is None:
+        out = new_hits(n, rays["ox"].device)
+    _check(lib().nbvh_query_rays_static(ctypes.byref(desc), _ptr(table), _ptr(mlp), _ptr(nodes), n_nodes,
+                                        rays_struct(rays), max_segs, hits_struct(out), _stream()),
+           "query_rays_static")
+    return out
