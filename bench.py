@@ -46,6 +46,8 @@ def parse():
     p.add_argument("--cpu-rays", type=int, default=24576, help="oracle sample size (primary rays)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--max-segs", type=int, default=48)
+    p.add_argument("--quick", action="store_true",
+                   help="time the FP16 tensor-core form only (no other forms, no e2e, no CPU baseline)")
     return p.parse_args()
 
 
@@ -353,6 +355,13 @@ def main():
     eval_ms_step = ev_ms / per_launch_steps
     tr_ms_step = tr_ms / per_launch_steps
     launches_per_step = launches / (args.steps + args.warmup)
+
+    if args.quick:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "Mrays/s", "ms_per_step": ms_step,
+                              "quick": True, "segments_per_step": seg1 + seg2, "eval_ms_per_step": eval_ms_step,
+                              "traverse_ms_per_step": tr_ms_step, "clocks": clk}), flush=True)
+        return
 
     # other forms on the same workload
     ms32 = dist_max(time_steps(wl, d32, max(3, args.steps // 2), 2), world) / max(3, args.steps // 2)

@@ -11,7 +11,7 @@
 namespace nbvh {
 
 constexpr int kTcM = 128;          // segments per tile = MMA M = TMEM lanes
-constexpr int kTcThreads = 512;    // 16 warps: all gather; 4 lane quarters x 4 column groups in epilogues
+constexpr int kTcThreads = 1024;   // 32 warps: all gather; 4 lane quarters x 8 column groups in epilogues
 constexpr long long kWaitCycles = 4000000000LL;  // bounded mbarrier wait (~2 s)
 
 // ---------------------------------------------------------------- PTX wrappers
@@ -99,11 +99,21 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v) {
+  uint32_t r[4];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+}
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 template <int COLS>
 __device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, float* v) {
-  if constexpr (COLS == 8) {
+  if constexpr (COLS == 4) {
+    tmem_ld4(taddr, v);
+  } else if constexpr (COLS == 8) {
     tmem_ld8(taddr, v);
   } else {
 #pragma unroll
@@ -157,39 +167,89 @@ struct OpType<true> {
   static __device__ __forceinline__ T one(float a) { return __float2bfloat16_rn(a); }
 };
 
+// TMEM column plan (one 32-bit column holds two 16-bit operand elements):
+//   [0, W)                 FP32 accumulator D of the current layer (the output
+//                          layer uses its first 16 columns)
+//   [W, W + W/2)           hidden activations H, the next layer's A operand
+//   [2W, 2W + Kp/2)        encoded features, the first layer's A operand
+// Only the weights live in shared memory, so L1 keeps most of its capacity
+// for the hash-table gather.
 struct TcLayout {
-  int Kp;               // input width padded to 16
-  uint32_t a_off, a_bytes;   // features (128 x Kp); the hidden activations alias it
-  uint32_t w1_off, w1_bytes; // W x Kp
-  uint32_t wh_off, wh_bytes; // (n_hidden - 1) x W x W
-  uint32_t wo_off, wo_bytes; // 16 x W
+  int Kp;                    // input width padded to 16
+  uint32_t col_h, col_a, ncols;
+  uint32_t w1_off;           // W x Kp operand
+  uint32_t wh_off;           // (n_hidden - 1) x W x W
+  uint32_t wo_off;           // 16 x W
   uint32_t row_off;          // per-row ray / t0 / t1
-  uint32_t bar_off;          // mbarrier + TMEM address
+  uint32_t bar_off;          // mbarrier + TMEM base address
   uint32_t total;
 };
 
 __host__ __device__ inline TcLayout tc_layout(int K, int W, int n_hidden) {
   TcLayout L;
   L.Kp = (K + 15) & ~15;
+  L.col_h = uint32_t(W);
+  L.col_a = uint32_t(2 * W);
+  const uint32_t used = L.col_a + uint32_t(L.Kp / 2);
+  uint32_t nc = 32;
+  while (nc < used) nc <<= 1;
+  L.ncols = nc;
   uint32_t off = 0;
   auto take = [&](uint32_t bytes) {
     const uint32_t o = off;
     off = (off + bytes + 127u) & ~127u;
     return o;
   };
-  L.a_bytes = uint32_t(kTcM) * L.Kp * 2;
-  const uint32_t h_bytes = uint32_t(kTcM) * W * 2;
-  L.a_off = take(L.a_bytes > h_bytes ? L.a_bytes : h_bytes);
-  L.w1_bytes = uint32_t(W) * L.Kp * 2;
-  L.w1_off = take(L.w1_bytes);
-  L.wh_bytes = uint32_t(n_hidden - 1) * W * W * 2;
-  L.wh_off = take(L.wh_bytes);
-  L.wo_bytes = 16u * W * 2;
-  L.wo_off = take(L.wo_bytes);
+  L.w1_off = take(uint32_t(W) * L.Kp * 2);
+  L.wh_off = take(uint32_t(n_hidden - 1) * W * W * 2);
+  L.wo_off = take(16u * W * 2);
   L.row_off = take(kTcM * 12);
   L.bar_off = take(64);
   L.total = off + 128;  // slack for base alignment
   return L;
+}
+
+// D[tmem] (+)= A[tmem] * B[smem]^T (A from tensor memory, kind::f16).
+__device__ __forceinline__ void mma_f16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                           uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// 32 lanes x 32 bits stores of 1/2/4/8 consecutive columns per thread.
+__device__ __forceinline__ void tmem_st1(uint32_t taddr, uint32_t a) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};" ::"r"(taddr), "r"(a) : "memory");
+}
+__device__ __forceinline__ void tmem_st2(uint32_t taddr, uint32_t a, uint32_t b) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1,%2};" ::"r"(taddr), "r"(a), "r"(b) : "memory");
+}
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, const uint32_t* v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr), "r"(v[0]), "r"(v[1]),
+               "r"(v[2]), "r"(v[3])
+               : "memory");
+}
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(v[0]),
+               "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+               : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+template <int NC>
+__device__ __forceinline__ void tmem_st_cols(uint32_t taddr, const uint32_t* v) {
+  if constexpr (NC == 1) {
+    tmem_st1(taddr, v[0]);
+  } else if constexpr (NC == 2) {
+    tmem_st2(taddr, v[0], v[1]);
+  } else if constexpr (NC == 4) {
+    tmem_st4(taddr, v);
+  } else {
+#pragma unroll
+    for (int c = 0; c < NC; c += 8) tmem_st8(taddr + c, v + c);
+  }
 }
 
 // Copy an fp32 [rows][K] row-major weight block into the K-major operand layout
@@ -205,9 +265,14 @@ __device__ __forceinline__ void stage_weights(uint8_t* dst, const float* __restr
   }
 }
 
+template <bool BF16>
+__device__ __forceinline__ uint32_t pack2(float a, float b) {
+  typename OpType<BF16>::T2 h = OpType<BF16>::pack(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
 template <typename T, int F, int W, bool WAVE, bool BF16>
 __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
-  using OT = OpType<BF16>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   const int K = a.gp.n_inputs;
@@ -216,7 +281,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
   const int n_out = a.n_out;
   const TcLayout lay = tc_layout(K, W, a.n_hidden);
   const int Kp = lay.Kp;
-  uint8_t* sA = smem + lay.a_off;
   uint8_t* sW1 = smem + lay.w1_off;
   uint8_t* sWh = smem + lay.wh_off;
   uint8_t* sWo = smem + lay.wo_off;
@@ -232,9 +296,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  constexpr uint32_t kTmemCols = W < 32 ? 32 : W;
   if (warp == 0) {
-    tmem_alloc(s_tmem, kTmemCols);
+    tmem_alloc(s_tmem, lay.ncols);
     tmem_relinquish();
   }
   if (threadIdx.x == 0) {
@@ -260,18 +323,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
   tc_fence_after();
   const uint32_t tmem = *s_tmem;
 
-  const uint32_t a_addr = smem_u32(sA);
   const uint32_t idesc_h = idesc_f16(BF16, kTcM, W);
   const uint32_t idesc_o = idesc_f16(BF16, kTcM, 16);
   const T* table = static_cast<const T*>(a.table);
-  // Epilogue mapping: warp -> TMEM lane quarter (warp % 4) and column group (warp / 4).
+  // Warp -> TMEM lane quarter (warp % 4); in epilogues also a column group (warp / 4).
   const int quarter = warp & 3;
   const int cgroup = warp >> 2;
-  constexpr int kCols = W / 4;  // columns per thread in hidden epilogues
+  constexpr int kGroups = kTcThreads / 128;
+  constexpr int kCols = W / kGroups;  // accumulator columns per thread in hidden epilogues
   const int row = quarter * 32 + lane;
   const uint32_t t_row = tmem + (uint32_t(quarter * 32) << 16);
+  const uint32_t t_a = t_row + lay.col_a;
   uint32_t phase = 0;
   bool failed = false;
+  constexpr int LPC = 8 / F;  // levels per 8-feature chunk (4 TMEM columns)
+  const bool chunked = (L % LPC) == 0;
 
   for (int64_t tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
     if (threadIdx.x < kTcM) {
@@ -296,63 +362,81 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
     }
     __syncthreads();
 
-    // ---- encode: pair (row m, sample k); lanes = consecutive rows.
-    const bool chunked = ((L * F) & 7) == 0;
-    for (int pidx = threadIdx.x; pidx < kTcM * N; pidx += blockDim.x) {
-      const int m = pidx & (kTcM - 1);
-      const int k = pidx >> 7;
-      const int ray = sray[m];
-      const int kb = k * L * F;
-      if (ray < 0) {
-        for (int j = 0; j < L * F; ++j) *reinterpret_cast<typename OT::T*>(sA + op_offset(m, kb + j, Kp)) = OT::one(0.0f);
-        continue;
-      }
-      float x, y, z;
-      sample_point(a.gp, a.rays.ox[ray], a.rays.oy[ray], a.rays.oz[ray], a.rays.dx[ray], a.rays.dy[ray],
-                   a.rays.dz[ray], st0[m], st1[m], k, x, y, z);
+    // ---- encode into TMEM: warp w owns rows 32 (w % 4) + lane and samples
+    // w / 4, w / 4 + 8, ...; lanes = consecutive rows (consecutive queue items).
+    for (int k = cgroup; k < N; k += kGroups) {
+      const int ray = sray[row];
+      const bool valid = ray >= 0;
+      float x = 0.0f, y = 0.0f, z = 0.0f;
+      if (valid)
+        sample_point(a.gp, a.rays.ox[ray], a.rays.oy[ray], a.rays.oz[ray], a.rays.dx[ray], a.rays.dy[ray],
+                     a.rays.dz[ray], st0[row], st1[row], k, x, y, z);
+      const uint32_t col0 = uint32_t(k * L * F) / 2u;
       if (chunked) {
-        constexpr int LPC = (8 / F) > 0 ? (8 / F) : 1;  // levels per 8-element chunk (F <= 8)
         for (int l0 = 0; l0 < L; l0 += LPC) {
           float v[8];
+          if (valid) {
+            if constexpr (LPC % 2 == 0) {
 #pragma unroll
-          for (int q = 0; q < LPC; ++q) encode_level<T, F>(a.gp, table, l0 + q, x, y, z, v + q * F);
-          uint4 pk;
-          typename OT::T2 h0 = OT::pack(v[0], v[1]), h1 = OT::pack(v[2], v[3]);
-          typename OT::T2 h2 = OT::pack(v[4], v[5]), h3 = OT::pack(v[6], v[7]);
-          pk.x = *reinterpret_cast<uint32_t*>(&h0);
-          pk.y = *reinterpret_cast<uint32_t*>(&h1);
-          pk.z = *reinterpret_cast<uint32_t*>(&h2);
-          pk.w = *reinterpret_cast<uint32_t*>(&h3);
-          *reinterpret_cast<uint4*>(sA + op_offset(m, kb + l0 * F, Kp)) = pk;
+              for (int q = 0; q < LPC; q += 2) encode_levels<T, F, 2>(a.gp, table, l0 + q, x, y, z, v + q * F);
+            } else {
+              encode_levels<T, F, LPC>(a.gp, table, l0, x, y, z, v);
+            }
+          } else {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) v[i] = 0.0f;
+          }
+          uint32_t pk[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) pk[i] = pack2<BF16>(v[2 * i], v[2 * i + 1]);
+          __syncwarp();
+          tmem_st4(t_a + col0 + uint32_t(l0 * F) / 2u, pk);
         }
-      } else {
+      } else if constexpr (F >= 2) {  // level by level: F/2 columns each
         for (int l = 0; l < L; ++l) {
           float v[F];
-          encode_level<T, F>(a.gp, table, l, x, y, z, v);
+          if (valid) {
+            encode_level<T, F>(a.gp, table, l, x, y, z, v);
+          } else {
 #pragma unroll
-          for (int f = 0; f < F; ++f)
-            *reinterpret_cast<typename OT::T*>(sA + op_offset(m, kb + l * F + f, Kp)) = OT::one(v[f]);
+            for (int i = 0; i < F; ++i) v[i] = 0.0f;
+          }
+          uint32_t pk[F / 2];
+#pragma unroll
+          for (int i = 0; i < F / 2; ++i) pk[i] = pack2<BF16>(v[2 * i], v[2 * i + 1]);
+          __syncwarp();
+          tmem_st_cols<F / 2>(t_a + col0 + uint32_t(l * F) / 2u, pk);
+        }
+      } else {  // F = 1 (even level count): one column per two levels
+        for (int l = 0; l < L; l += 2) {
+          float v[2] = {0.0f, 0.0f};
+          if (valid) {
+            encode_level<T, F>(a.gp, table, l, x, y, z, v);
+            encode_level<T, F>(a.gp, table, l + 1, x, y, z, v + 1);
+          }
+          __syncwarp();
+          tmem_st1(t_a + col0 + uint32_t(l) / 2u, pack2<BF16>(v[0], v[1]));
         }
       }
     }
-    for (int pidx = threadIdx.x; pidx < kTcM * (Kp - K); pidx += blockDim.x) {
-      const int m = pidx % kTcM, k = K + pidx / kTcM;
-      *reinterpret_cast<typename OT::T*>(sA + op_offset(m, k, Kp)) = OT::one(0.0f);
+    if (Kp > K) {  // zero padding columns (K is even, so padding starts on a column)
+      if (cgroup == 0) {
+        for (int c = K / 2; c < Kp / 2; ++c) tmem_st1(t_a + uint32_t(c), 0u);
+      }
     }
-    fence_proxy_async_smem();
+    tmem_st_wait();
+    tc_fence_before();
     __syncthreads();
 
-    // ---- layer 1: [128 x Kp] x [Kp x W] -> TMEM columns [0, W)
+    // ---- layer 1: A = features (TMEM) x W1 (smem) -> D
     if (threadIdx.x == 0) {
       tc_fence_after();
-      const uint32_t sbo_a = uint32_t(Kp) * 16, w1_addr = smem_u32(sW1);
-      for (int j = 0; j < Kp / 16; ++j) {
-        mma_f16(tmem, smem_desc(a_addr + j * 256, 128, sbo_a), smem_desc(w1_addr + j * 256, 128, sbo_a), idesc_h,
-                j > 0);
-      }
+      const uint32_t sbo = uint32_t(Kp) * 16, w1_addr = smem_u32(sW1);
+      for (int j = 0; j < Kp / 16; ++j)
+        mma_f16_ts(tmem, tmem + lay.col_a + uint32_t(8 * j), smem_desc(w1_addr + j * 256, 128, sbo), idesc_h, j > 0);
       mma_commit(bar);
     }
-    // ---- hidden layers, each: wait, epilogue (bias, ReLU) into H = sA, MMA
+    // ---- each hidden layer: wait, bias + ReLU into H (TMEM), next MMA
     for (int h = 0; h < a.n_hidden; ++h) {
       // bias of layer h: b0 follows W0; hidden layer h >= 1 is [W][W] then [W]
       const float* bias = h == 0 ? b1 : b1 + W + size_t(h - 1) * (W * W + W) + size_t(W) * W;
@@ -368,38 +452,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
         tmem_ld_cols<kCols>(t_row + uint32_t(cgroup * kCols), v);
         tmem_ld_wait();
         const int c0 = cgroup * kCols;
+        uint32_t pk[kCols / 2];
 #pragma unroll
-        for (int c = 0; c < kCols; c += 8) {
-          float q[8];
-#pragma unroll
-          for (int i = 0; i < 8; ++i) q[i] = fmaxf(v[c + i] + __ldg(bias + c0 + c + i), 0.0f);
-          typename OT::T2 h0 = OT::pack(q[0], q[1]), h1 = OT::pack(q[2], q[3]);
-          typename OT::T2 h2 = OT::pack(q[4], q[5]), h3 = OT::pack(q[6], q[7]);
-          uint4 pk;
-          pk.x = *reinterpret_cast<uint32_t*>(&h0);
-          pk.y = *reinterpret_cast<uint32_t*>(&h1);
-          pk.z = *reinterpret_cast<uint32_t*>(&h2);
-          pk.w = *reinterpret_cast<uint32_t*>(&h3);
-          *reinterpret_cast<uint4*>(sA + op_offset(row, c0 + c, W)) = pk;
-        }
+        for (int i = 0; i < kCols / 2; ++i)
+          pk[i] = pack2<BF16>(fmaxf(v[2 * i] + __ldg(bias + c0 + 2 * i), 0.0f),
+                              fmaxf(v[2 * i + 1] + __ldg(bias + c0 + 2 * i + 1), 0.0f));
+        tmem_st_cols<kCols / 2>(t_row + lay.col_h + uint32_t(c0 / 2), pk);
+        tmem_st_wait();
       }
       tc_fence_before();
-      fence_proxy_async_smem();
       __syncthreads();
       if (threadIdx.x == 0) {
         tc_fence_after();
-        const uint32_t sbo_h = uint32_t(W) * 16;
-        if (h + 1 < a.n_hidden) {
-          const uint32_t wa = smem_u32(sWh + size_t(h) * W * W * 2);
-          for (int j = 0; j < W / 16; ++j)
-            mma_f16(tmem, smem_desc(a_addr + j * 256, 128, sbo_h), smem_desc(wa + j * 256, 128, sbo_h), idesc_h,
-                    j > 0);
-        } else {
-          const uint32_t wa = smem_u32(sWo);
-          for (int j = 0; j < W / 16; ++j)
-            mma_f16(tmem, smem_desc(a_addr + j * 256, 128, sbo_h), smem_desc(wa + j * 256, 128, sbo_h), idesc_o,
-                    j > 0);
-        }
+        const uint32_t sbo = uint32_t(W) * 16;
+        const uint32_t wa = smem_u32(h + 1 < a.n_hidden ? sWh + size_t(h) * W * W * 2 : sWo);
+        const uint32_t idesc = h + 1 < a.n_hidden ? idesc_h : idesc_o;
+        for (int j = 0; j < W / 16; ++j)
+          mma_f16_ts(tmem, tmem + lay.col_h + uint32_t(8 * j), smem_desc(wa + j * 256, 128, sbo), idesc, j > 0);
         mma_commit(bar);
       }
     }
@@ -435,14 +504,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    tmem_dealloc(tmem, kTmemCols);
+    tmem_dealloc(tmem, lay.ncols);
   }
 }
 
 template <typename T, int F, int W, bool WAVE>
 cudaError_t launch_tc_twf(const nbvh_model_desc* d, const EvalArgs& a, int64_t n_items_max, cudaStream_t s) {
   const TcLayout lay = tc_layout(a.gp.n_inputs, W, a.n_hidden);
-  if (lay.total > 227 * 1024 || W < 16) return cudaErrorInvalidConfiguration;
+  if (lay.total > 227 * 1024 || W < 32 || lay.ncols > 512 || (a.gp.n_inputs & 1) ||
+      (F == 1 && (a.gp.n_levels & 1)))
+    return cudaErrorInvalidConfiguration;
   const bool bf16 = d->mlp_prec == NBVH_BF16;
   auto kern = bf16 ? eval_tc_kernel<T, F, W, WAVE, true> : eval_tc_kernel<T, F, W, WAVE, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(lay.total));

@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "../../include/nbvh.h"
 
 namespace nbvh {
@@ -273,6 +275,35 @@ __device__ __forceinline__ void level_corners(const GridParams& gp, int l, P x, 
   for (int k = 0; k < 8; ++k) c.w[k] = wx[k & 1] * wy[(k >> 1) & 1] * wz[(k >> 2) & 1];
 }
 
+// Corner indices (table-relative) and cell fractions of level l at (x,y,z).
+template <typename P>
+__device__ __forceinline__ void level_index(const GridParams& gp, int l, P x, P y, P z, uint32_t* idx,
+                                            float* fr) {
+  const int N = gp.res[l];
+  int cx, cy, cz;
+  axis_cell(x, N, cx, fr[0]);
+  axis_cell(y, N, cy, fr[1]);
+  axis_cell(z, N, cz, fr[2]);
+  if (gp.dense[l]) {
+    const uint32_t n1 = static_cast<uint32_t>(N) + 1u;
+    const uint32_t base = static_cast<uint32_t>(cx) + static_cast<uint32_t>(cy) * n1 +
+                          static_cast<uint32_t>(cz) * n1 * n1;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) idx[k] = base + (k & 1) + ((k >> 1) & 1) * n1 + ((k >> 2) & 1) * n1 * n1;
+  } else {
+    const uint32_t hx = static_cast<uint32_t>(cx);
+    const uint32_t hy = static_cast<uint32_t>(cy) * kHashP1;
+    const uint32_t hz = static_cast<uint32_t>(cz) * kHashP2;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const uint32_t a = hx + (k & 1);
+      const uint32_t b = (k & 2) ? hy + kHashP1 : hy;
+      const uint32_t d = (k & 4) ? hz + kHashP2 : hz;
+      idx[k] = (a ^ b ^ d) & gp.hash_mask;
+    }
+  }
+}
+
 // Interpolated F features of level l at (x,y,z) (float or float-float coords).
 template <typename T, int F, typename P>
 __device__ __forceinline__ void encode_level(const GridParams& gp, const T* __restrict__ table, int l,
@@ -291,6 +322,51 @@ __device__ __forceinline__ void encode_level(const GridParams& gp, const T* __re
     for (int f = 0; f < F; ++f) out[f] = fmaf(c.w[k], v[k][f], out[f]);
   }
 }
+
+// NL consecutive levels from l0 with every corner load issued before any is
+// consumed (memory-level parallelism for the latency-bound gather). Entries of
+// 4 bytes (two FP16/BF16 features) stay as raw words until the interpolation.
+template <typename T, int F, int NL, typename P>
+__device__ __forceinline__ void encode_levels(const GridParams& gp, const T* __restrict__ table, int l0, P x,
+                                              P y, P z, float* out) {
+  if constexpr (F * sizeof(T) == 4 && sizeof(T) == 2) {
+    uint32_t raw[NL][8];
+    float fr[NL][3];
+#pragma unroll
+    for (int q = 0; q < NL; ++q) {
+      uint32_t idx[8];
+      level_index(gp, l0 + q, x, y, z, idx, fr[q]);
+      const uint32_t* tab = reinterpret_cast<const uint32_t*>(table + gp.offset[l0 + q] * F);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) raw[q][k] = __ldg(tab + idx[k]);
+    }
+#pragma unroll
+    for (int q = 0; q < NL; ++q) {
+      const float wx[2] = {1.0f - fr[q][0], fr[q][0]};
+      const float wy[2] = {1.0f - fr[q][1], fr[q][1]};
+      const float wz[2] = {1.0f - fr[q][2], fr[q][2]};
+      float a0 = 0.0f, a1 = 0.0f;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const float w = wx[k & 1] * wy[(k >> 1) & 1] * wz[(k >> 2) & 1];
+        float2 v;
+        if constexpr (sizeof(T) == 2 && std::is_same<T, __half>::value) {
+          v = __half22float2(*reinterpret_cast<const __half2*>(&raw[q][k]));
+        } else {
+          v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&raw[q][k]));
+        }
+        a0 = fmaf(w, v.x, a0);
+        a1 = fmaf(w, v.y, a1);
+      }
+      out[q * 2] = a0;
+      out[q * 2 + 1] = a1;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < NL; ++q) encode_level<T, F>(gp, table, l0 + q, x, y, z, out + q * F);
+  }
+}
+
 
 // ---------------------------------------------------------------------------
 // (b - o) / d rounded once to float: b - o is formed exactly as a float pair,
