@@ -231,6 +231,114 @@ nbvh_status nbvh_get_timing(double* traverse_ms, double* eval_ms, int64_t* calls
 /* Host. Number of kernels this library has launched in this process. */
 int64_t nbvh_launch_count(void);
 
+/* ------------------------------------------------------------------------
+ * Training (S7, S8): Sec. 4 "Encoding, inference & training", Sec. 5.2
+ * (ray distribution, visibility / distance / normal losses, combined loss),
+ * Sec. 6 "Neural model & training" (batches of rays, Adam, lr 1e-2).
+ * ------------------------------------------------------------------------ */
+
+typedef enum {
+  NBVH_TRAIN_PROBED_MIX = 0, /* even rays: leaf chosen uniformly, point uniform in its box, uniform
+                                direction, origin on the bounding sphere, trains that leaf; odd rays:
+                                bounding-sphere chords, train the first leaf met */
+  NBVH_TRAIN_PAPER = 1       /* origin uniform in the 50%-inflated scene box, uniform direction,
+                                trains the first leaf met (Sec. 4, Sec. 5.2) */
+} nbvh_train_mode;
+
+/* Device geometry the training step reads. */
+typedef struct {
+  const nbvh_node* nodes;
+  int32_t n_nodes;
+  const float* leaf_box;     /* device [n_leaves][6] lo xyz, hi xyz */
+  int32_t n_leaves;
+  const float* tris;         /* device [n_tris][9] */
+  const int32_t* tri_perm;   /* device, as nbvh_build_leaves */
+  const int32_t* leaf_range; /* device [n_leaves][2] */
+  nbvh_scene_info info;      /* by value */
+} nbvh_train_scene;
+
+/* Training labels, device structure-of-arrays. */
+typedef struct {
+  uint8_t* hit;
+  float *depth, *nx, *ny, *nz;
+} nbvh_labels;
+
+/* Device. S7 rays of one training step. Randomness: Philox4x32-10 keyed by
+ * seed (low, high word), counter (ray, step low, step high, block 0 or 1);
+ * uniforms are the top 24 bits times 2^-24; a uniform direction is
+ * z = 1 - 2u, phi = 2 pi u'. Probed rays: leaf = floor(u32 * n_leaves / 2^32)
+ * of the first word, point = lo + u (hi - lo), origin moved back along -d to
+ * the bounding sphere (centre = scene centre, radius = info.sphere_radius).
+ * Output: rays (tmin 0; tmax +inf, or the chord length), the trained leaf
+ * (-1: the ray meets no leaf and does not train), its segment [t0, t1], and
+ * *n_valid (device) incremented by the number of training rays. */
+nbvh_status nbvh_train_rays(int32_t mode, uint64_t seed, int64_t step, const nbvh_train_scene* scene,
+                            nbvh_rays_out rays, int32_t* leaf, float* t0, float* t1, int32_t* n_valid,
+                            void* stream);
+
+/* Device. S7 labels: closest Moller-Trumbore intersection (edges inclusive,
+ * det == 0 a miss) among the trained leaf's own triangles with t in
+ * [t0, t1]; hit, local depth (t - t0)/(t1 - t0), geometric normal turned to
+ * face -d. Rays with leaf < 0 get hit 0. */
+nbvh_status nbvh_train_labels(nbvh_rays rays, const int32_t* leaf, const float* t0, const float* t1,
+                              const nbvh_train_scene* scene, nbvh_labels out, void* stream);
+
+/* Host. Workspace of nbvh_forward_train / nbvh_backward / nbvh_train_step for
+ * batches of up to n rays. */
+nbvh_status nbvh_train_workspace_size(const nbvh_model_desc* desc, int64_t n, size_t* bytes);
+
+/* Device. Forward of n training segments (segment i belongs to ray i and to
+ * leaf[i]; leaf < 0 does not train) storing the activations in the workspace.
+ * raw_out: device [n][n_out] raw MLP outputs. With labels (labels.hit != NULL)
+ * it also evaluates the combined loss L = mean over training segments of
+ * 2 BCE(sigmoid(o_hit), y) + y (2 |sigmoid(o_d) - d| + (1/3) sum_j |o_nj - n_j|)
+ * (Sec. 5.2), keeps dL/d(raw) times the loss scale for nbvh_backward, and
+ * writes L (FP64 reduction) to *loss_out (device, may be NULL).
+ * n_valid: device count of training segments (nbvh_train_rays). The loss
+ * scale is *loss_scale_dev when that is not NULL, else loss_scale. */
+nbvh_status nbvh_forward_train(const nbvh_model_desc* desc, const void* table, const float* mlp,
+                               nbvh_rays rays, const int32_t* leaf, const float* t0, const float* t1,
+                               nbvh_labels labels, const int32_t* n_valid, float loss_scale,
+                               const float* loss_scale_dev, float* raw_out, double* loss_out, void* workspace,
+                               size_t ws_bytes, void* stream);
+
+/* Device. Backward of the last nbvh_forward_train on the same workspace:
+ * from grad_out (device [n][n_out], dL/d(raw); NULL = the loss gradient the
+ * forward kept) through the MLP into grad_mlp (FP32, parameter order of
+ * nbvh_mlp_param_count) and through the encoding into grad_table (FP32,
+ * [entries][F]): every (sample, level, corner) adds its trilinear weight times
+ * dL/dfeature (Sec. 3, Sec. 4). Both gradients accumulate (callers zero them). */
+nbvh_status nbvh_backward(const nbvh_model_desc* desc, const void* table, const float* mlp, nbvh_rays rays,
+                          const int32_t* leaf, const float* t0, const float* t1, const float* grad_out,
+                          float* grad_table, float* grad_mlp, void* workspace, size_t ws_bytes, void* stream);
+
+/* Optimiser state, all device. The table is optimised in FP32 (table_master);
+ * table_work is the copy the kernels read in desc->table_prec (NULL when
+ * that is FP32 and the master is read directly). */
+typedef struct {
+  float* table_master;
+  void* table_work;
+  float *table_m, *table_v, *grad_table;
+  float* mlp;
+  float *mlp_m, *mlp_v, *grad_mlp;
+  float* loss_scale;   /* device scalar */
+  int32_t* counters;   /* device [4]: good steps, bad flag, applied flag, spare */
+} nbvh_optim;
+
+/* Device. Adam (bias-corrected; step counts from 1) on the FP32 masters with
+ * the gradients divided by the loss scale, then the gradients are zeroed. A
+ * step whose gradients are not all finite is skipped; with dynamic_scale the
+ * scale halves on such a step and doubles after 2000 clean ones. */
+nbvh_status nbvh_adam(const nbvh_model_desc* desc, const nbvh_optim* opt, int64_t step, float lr, float beta1,
+                      float beta2, float eps, int32_t dynamic_scale, void* stream);
+
+/* Device. One whole training step: rays (nbvh_train_rays), labels, forward
+ * with loss, backward, Adam (lr, beta 0.9 / 0.999, eps 1e-8, Sec. 6). FP16 /
+ * BF16 MLPs use dynamic loss scaling. *loss_out (device) receives the loss. */
+nbvh_status nbvh_train_step(const nbvh_model_desc* desc, const nbvh_optim* opt, const nbvh_train_scene* scene,
+                            int32_t mode, int64_t batch, uint64_t seed, int64_t step, float lr, double* loss_out,
+                            void* workspace, size_t ws_bytes, void* stream);
+
 /* Size of the library's built-in query scratch (32 MiB), see
  * nbvh_query_rays_static. */
 #define NBVH_STATIC_SCRATCH_BYTES 33554432

@@ -1,6 +1,7 @@
 // Device entry points of the C ABI (include/nbvh.h). Single CUDA translation
 // unit: the kernels live in the included headers.
 #include <atomic>
+#include <cmath>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -11,6 +12,7 @@
 #include "eval_plain.cuh"
 #include "eval_tc.cuh"
 #include "bounce.cuh"
+#include "train.cuh"
 
 namespace nbvh {
 
@@ -462,4 +464,342 @@ extern "C" nbvh_status nbvh_query_rays_static(const nbvh_model_desc* desc, const
   }
   return nbvh_query_rays(desc, table, mlp, nodes, n_nodes, rays, max_segs, out, base,
                          size_t(NBVH_STATIC_SCRATCH_BYTES), stream);
+}
+
+// ---------------------------------------------------------------- training
+namespace nbvh {
+namespace {
+
+struct TrainWs {
+  int32_t* n_valid;
+  double* loss;
+  float* rays[8];
+  int32_t* leaf;
+  float *t0, *t1;
+  uint8_t* hit;
+  float *depth, *nx, *ny, *nz;
+  TrainBuffers buf;
+  size_t bytes;
+};
+
+TrainWs carve_train(void* base, const nbvh_model_desc* d, int64_t n) {
+  TrainWs w;
+  std::memset(&w, 0, sizeof(w));
+  char* p = static_cast<char*>(base);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    char* q = p ? p + off : nullptr;
+    off += align256(bytes);
+    return q;
+  };
+  const size_t K = size_t(d->n_samples) * d->n_levels * d->n_features;
+  const size_t Wd = size_t(d->width), nh = size_t(d->n_hidden), no = size_t(d->n_out), N = size_t(n);
+  char* small = take(256);
+  w.n_valid = reinterpret_cast<int32_t*>(small);
+  w.loss = reinterpret_cast<double*>(small ? small + 16 : nullptr);
+  for (int k = 0; k < 8; ++k) w.rays[k] = reinterpret_cast<float*>(take(4 * N));
+  w.leaf = reinterpret_cast<int32_t*>(take(4 * N));
+  w.t0 = reinterpret_cast<float*>(take(4 * N));
+  w.t1 = reinterpret_cast<float*>(take(4 * N));
+  w.hit = reinterpret_cast<uint8_t*>(take(N));
+  w.depth = reinterpret_cast<float*>(take(4 * N));
+  w.nx = reinterpret_cast<float*>(take(4 * N));
+  w.ny = reinterpret_cast<float*>(take(4 * N));
+  w.nz = reinterpret_cast<float*>(take(4 * N));
+  w.buf.X = reinterpret_cast<float*>(take(4 * N * K));
+  w.buf.H = reinterpret_cast<float*>(take(4 * nh * N * Wd));
+  w.buf.O = reinterpret_cast<float*>(take(4 * N * no));
+  w.buf.G = reinterpret_cast<float*>(take(4 * N * no));
+  w.buf.loss_seg = reinterpret_cast<float*>(take(4 * N));
+  w.buf.dZ = reinterpret_cast<float*>(take(4 * nh * N * Wd));
+  w.bytes = off;
+  return w;
+}
+
+template <typename T, int F, int W>
+cudaError_t launch_train_plain(bool backward, const TrainArgs& a, cudaStream_t s) {
+  const size_t smem = backward ? train_bwd_smem(a.gp.n_inputs, W, a.n_hidden, a.n_out)
+                               : train_fwd_smem(a.gp.n_inputs, W, a.n_hidden, a.n_out);
+  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+  auto kern = backward ? train_backward_plain<T, F, W> : train_forward_plain<T, F, W>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kPlainThreads, smem);
+  if (e != cudaSuccess) return e;
+  const int64_t tiles = (a.n + kPlainTM - 1) / kPlainTM;
+  int64_t grid = int64_t(sm_count()) * (occ < 1 ? 1 : occ);
+  if (tiles < grid) grid = tiles;
+  if (grid < 1) return cudaSuccess;
+  kern<<<unsigned(grid), kPlainThreads, smem, s>>>(a);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template <typename T, int F>
+cudaError_t launch_train_tf(bool bwd, int W, const TrainArgs& a, cudaStream_t s) {
+  switch (W) {
+    case 16: return launch_train_plain<T, F, 16>(bwd, a, s);
+    case 32: return launch_train_plain<T, F, 32>(bwd, a, s);
+    case 64: return launch_train_plain<T, F, 64>(bwd, a, s);
+    case 128: return launch_train_plain<T, F, 128>(bwd, a, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t launch_train_t(bool bwd, const nbvh_model_desc* d, const TrainArgs& a, cudaStream_t s) {
+  switch (d->n_features) {
+    case 1: return launch_train_tf<T, 1>(bwd, d->width, a, s);
+    case 2: return launch_train_tf<T, 2>(bwd, d->width, a, s);
+    case 4: return launch_train_tf<T, 4>(bwd, d->width, a, s);
+    case 8: return launch_train_tf<T, 8>(bwd, d->width, a, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_train(bool bwd, const nbvh_model_desc* d, const TrainArgs& a, cudaStream_t s) {
+  switch (d->table_prec) {
+    case NBVH_FP32: return launch_train_t<float>(bwd, d, a, s);
+    case NBVH_FP16: return launch_train_t<__half>(bwd, d, a, s);
+    case NBVH_BF16: return launch_train_t<__nv_bfloat16>(bwd, d, a, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+bool scene_valid(const nbvh_train_scene* sc) {
+  return sc && sc->nodes && sc->n_nodes >= 1 && sc->leaf_box && sc->n_leaves >= 1 && sc->tris && sc->tri_perm &&
+         sc->leaf_range;
+}
+
+TrainArgs train_args(const nbvh_model_desc* d, const GridParams& gp, const void* table, const float* mlp,
+                     const nbvh_rays& rays, const int32_t* leaf, const float* t0, const float* t1,
+                     const TrainWs& w) {
+  TrainArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.gp = gp;
+  a.table = table;
+  a.mlp = mlp;
+  a.n_hidden = d->n_hidden;
+  a.width = d->width;
+  a.n_out = d->n_out;
+  a.rays = ray_ptrs(rays);
+  a.leaf = leaf;
+  a.t0 = t0;
+  a.t1 = t1;
+  a.n = rays.n;
+  a.buf = w.buf;
+  a.loss_scale = 1.0f;
+  return a;
+}
+
+cudaError_t launch_weight_grad(const float* dZ, int n_o, const float* A, int n_j, int64_t n, float* dW, float* db,
+                               cudaStream_t s) {
+  dim3 grid(unsigned((n_o + kWgTile - 1) / kWgTile), unsigned((n_j + kWgTile - 1) / kWgTile),
+            unsigned((n + kWgChunk - 1) / kWgChunk));
+  weight_grad_kernel<<<grid, 256, 0, s>>>(dZ, n_o, A, n_j, n, dW, db);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace nbvh
+
+extern "C" nbvh_status nbvh_train_rays(int32_t mode, uint64_t seed, int64_t step, const nbvh_train_scene* scene,
+                                       nbvh_rays_out rays, int32_t* leaf, float* t0, float* t1, int32_t* n_valid,
+                                       void* stream) {
+  if ((mode != NBVH_TRAIN_PROBED_MIX && mode != NBVH_TRAIN_PAPER) || !scene_valid(scene) || rays.n < 0 ||
+      step < 0)
+    return NBVH_ERR_INVALID_ARG;
+  if (rays.n == 0) return NBVH_OK;
+  if (!rays.ox || !rays.oy || !rays.oz || !rays.dx || !rays.dy || !rays.dz || !rays.tmin || !rays.tmax || !leaf ||
+      !t0 || !t1 || !n_valid || rays.n > (int64_t(1) << 31) - 1)
+    return NBVH_ERR_INVALID_ARG;
+  TrainRayArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.mode = mode;
+  a.k0 = uint32_t(seed & 0xffffffffu);
+  a.k1 = uint32_t(seed >> 32);
+  a.step_lo = uint32_t(uint64_t(step) & 0xffffffffu);
+  a.step_hi = uint32_t(uint64_t(step) >> 32);
+  a.n = rays.n;
+  a.nodes = scene->nodes;
+  a.leaf_box = scene->leaf_box;
+  a.n_leaves = scene->n_leaves;
+  for (int i = 0; i < 3; ++i) {
+    a.centre[i] = scene->info.centre[i];
+    a.lo[i] = scene->info.lo[i];
+    a.hi[i] = scene->info.hi[i];
+  }
+  a.radius = scene->info.sphere_radius;
+  a.out = RayOut{rays.ox, rays.oy, rays.oz, rays.dx, rays.dy, rays.dz, rays.tmin, rays.tmax};
+  a.leaf = leaf;
+  a.t0 = t0;
+  a.t1 = t1;
+  a.n_valid = n_valid;
+  train_rays_kernel<<<unsigned((rays.n + 127) / 128), 128, 0, as_stream(stream)>>>(a);
+  count_launches(1);
+  return status_of(cudaGetLastError());
+}
+
+extern "C" nbvh_status nbvh_train_labels(nbvh_rays rays, const int32_t* leaf, const float* t0, const float* t1,
+                                         const nbvh_train_scene* scene, nbvh_labels out, void* stream) {
+  if (!rays_valid(rays) || !scene_valid(scene)) return NBVH_ERR_INVALID_ARG;
+  if (rays.n == 0) return NBVH_OK;
+  if (!leaf || !t0 || !t1 || !out.hit || !out.depth || !out.nx || !out.ny || !out.nz) return NBVH_ERR_INVALID_ARG;
+  labels_kernel<<<unsigned((rays.n + 127) / 128), 128, 0, as_stream(stream)>>>(
+      ray_ptrs(rays), leaf, t0, t1, rays.n, scene->tris, scene->tri_perm, scene->leaf_range, out.hit, out.depth,
+      out.nx, out.ny, out.nz);
+  count_launches(1);
+  return status_of(cudaGetLastError());
+}
+
+extern "C" nbvh_status nbvh_train_workspace_size(const nbvh_model_desc* desc, int64_t n, size_t* bytes) {
+  if (!nbvh_host::desc_valid(desc) || n < 0 || !bytes) return NBVH_ERR_INVALID_ARG;
+  *bytes = carve_train(nullptr, desc, n).bytes;
+  return NBVH_OK;
+}
+
+extern "C" nbvh_status nbvh_forward_train(const nbvh_model_desc* desc, const void* table, const float* mlp,
+                                          nbvh_rays rays, const int32_t* leaf, const float* t0, const float* t1,
+                                          nbvh_labels labels, const int32_t* n_valid, float loss_scale,
+                                          const float* loss_scale_dev, float* raw_out, double* loss_out,
+                                          void* workspace, size_t ws_bytes, void* stream) {
+  if (!nbvh_host::desc_valid(desc) || !table || !mlp || !rays_valid(rays)) return NBVH_ERR_INVALID_ARG;
+  if (rays.n == 0) return NBVH_OK;
+  if (!leaf || !t0 || !t1 || !workspace || (reinterpret_cast<uintptr_t>(workspace) & 255) ||
+      (labels.hit && (!labels.depth || !labels.nx || !labels.ny || !labels.nz || !n_valid)) ||
+      !(loss_scale > 0.0f))
+    return NBVH_ERR_INVALID_ARG;
+  TrainWs w = carve_train(workspace, desc, rays.n);
+  if (ws_bytes < w.bytes) return NBVH_ERR_WORKSPACE_TOO_SMALL;
+  if (desc->mlp_prec != NBVH_FP32) return NBVH_ERR_UNSUPPORTED;
+  GridParams gp;
+  if (!make_grid(desc, gp)) return NBVH_ERR_INVALID_ARG;
+  cudaStream_t s = as_stream(stream);
+  TrainArgs a = train_args(desc, gp, table, mlp, rays, leaf, t0, t1, w);
+  a.lab = Labels{labels.hit, labels.depth, labels.nx, labels.ny, labels.nz};
+  a.n_valid = n_valid;
+  a.loss_scale = loss_scale;
+  a.loss_scale_dev = loss_scale_dev;
+  cudaError_t e = launch_train(false, desc, a, s);
+  if (e != cudaSuccess) return status_of(e);
+  if (raw_out) {
+    e = cudaMemcpyAsync(raw_out, w.buf.O, sizeof(float) * size_t(rays.n) * desc->n_out, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return NBVH_ERR_CUDA;
+  }
+  if (labels.hit && loss_out) {
+    loss_reduce_kernel<<<1, 256, 0, s>>>(w.buf.loss_seg, rays.n, n_valid, loss_out);
+    count_launches(1);
+    e = cudaGetLastError();
+  }
+  return status_of(e);
+}
+
+extern "C" nbvh_status nbvh_backward(const nbvh_model_desc* desc, const void* table, const float* mlp,
+                                     nbvh_rays rays, const int32_t* leaf, const float* t0, const float* t1,
+                                     const float* grad_out, float* grad_table, float* grad_mlp, void* workspace,
+                                     size_t ws_bytes, void* stream) {
+  if (!nbvh_host::desc_valid(desc) || !table || !mlp || !rays_valid(rays)) return NBVH_ERR_INVALID_ARG;
+  if (rays.n == 0) return NBVH_OK;
+  if (!leaf || !t0 || !t1 || !grad_table || !grad_mlp || !workspace ||
+      (reinterpret_cast<uintptr_t>(workspace) & 255))
+    return NBVH_ERR_INVALID_ARG;
+  TrainWs w = carve_train(workspace, desc, rays.n);
+  if (ws_bytes < w.bytes) return NBVH_ERR_WORKSPACE_TOO_SMALL;
+  if (desc->mlp_prec != NBVH_FP32) return NBVH_ERR_UNSUPPORTED;
+  GridParams gp;
+  if (!make_grid(desc, gp)) return NBVH_ERR_INVALID_ARG;
+  cudaStream_t s = as_stream(stream);
+  TrainArgs a = train_args(desc, gp, table, mlp, rays, leaf, t0, t1, w);
+  if (grad_out) a.buf.G = const_cast<float*>(grad_out);
+  a.grad_table = grad_table;
+  cudaError_t e = launch_train(true, desc, a, s);
+  if (e != cudaSuccess) return status_of(e);
+  // weight gradients, parameter order: W0 [W][K], b0, (W_h [W][W], b_h)*, Wo [n_out][W], bo
+  const int K = gp.n_inputs, Wd = desc->width, nh = desc->n_hidden, no = desc->n_out;
+  const int64_t n = rays.n;
+  size_t off = 0;
+  e = launch_weight_grad(w.buf.dZ, Wd, w.buf.X, K, n, grad_mlp + off, grad_mlp + off + size_t(Wd) * K, s);
+  off += size_t(Wd) * K + Wd;
+  for (int h = 1; h < nh && e == cudaSuccess; ++h) {
+    e = launch_weight_grad(w.buf.dZ + size_t(h) * n * Wd, Wd, w.buf.H + size_t(h - 1) * n * Wd, Wd, n,
+                           grad_mlp + off, grad_mlp + off + size_t(Wd) * Wd, s);
+    off += size_t(Wd) * Wd + Wd;
+  }
+  if (e == cudaSuccess)
+    e = launch_weight_grad(a.buf.G, no, w.buf.H + size_t(nh - 1) * n * Wd, Wd, n, grad_mlp + off,
+                           grad_mlp + off + size_t(no) * Wd, s);
+  return status_of(e);
+}
+
+extern "C" nbvh_status nbvh_adam(const nbvh_model_desc* desc, const nbvh_optim* opt, int64_t step, float lr,
+                                 float beta1, float beta2, float eps, int32_t dynamic_scale, void* stream) {
+  if (!nbvh_host::desc_valid(desc) || !opt || step < 1 || !(lr > 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) ||
+      !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps > 0.0f))
+    return NBVH_ERR_INVALID_ARG;
+  if (!opt->table_master || !opt->table_m || !opt->table_v || !opt->grad_table || !opt->mlp || !opt->mlp_m ||
+      !opt->mlp_v || !opt->grad_mlp || !opt->loss_scale || !opt->counters)
+    return NBVH_ERR_INVALID_ARG;
+  int32_t res[NBVH_MAX_LEVELS], dense[NBVH_MAX_LEVELS];
+  int64_t size[NBVH_MAX_LEVELS], offset[NBVH_MAX_LEVELS], total = 0;
+  if (!nbvh_host::layout(desc, res, dense, size, offset, &total)) return NBVH_ERR_INVALID_ARG;
+  const int64_t nt = total * desc->n_features;
+  const int64_t nm = nbvh_host::mlp_params(desc);
+  cudaStream_t s = as_stream(stream);
+  AdamState st{opt->loss_scale, opt->counters, opt->counters + 1, opt->counters + 2};
+  const unsigned g = unsigned(sm_count()) * 8;
+  grad_check_kernel<<<g, 256, 0, s>>>(opt->grad_table, nt, st.bad);
+  grad_check_kernel<<<g, 256, 0, s>>>(opt->grad_mlp, nm, st.bad);
+  const double c1 = 1.0 - std::pow(double(beta1), double(step));
+  const double c2 = 1.0 - std::pow(double(beta2), double(step));
+  switch (desc->table_prec) {
+    case NBVH_FP16:
+      adam_kernel<__half><<<g, 256, 0, s>>>(opt->table_master, static_cast<__half*>(opt->table_work),
+                                           opt->grad_table, opt->table_m, opt->table_v, nt, lr, beta1, beta2, eps,
+                                           float(c1), float(c2), st);
+      break;
+    case NBVH_BF16:
+      adam_kernel<__nv_bfloat16><<<g, 256, 0, s>>>(opt->table_master, static_cast<__nv_bfloat16*>(opt->table_work),
+                                                   opt->grad_table, opt->table_m, opt->table_v, nt, lr, beta1, beta2,
+                                                   eps, float(c1), float(c2), st);
+      break;
+    default:
+      adam_kernel<float><<<g, 256, 0, s>>>(opt->table_master, static_cast<float*>(opt->table_work), opt->grad_table,
+                                          opt->table_m, opt->table_v, nt, lr, beta1, beta2, eps, float(c1), float(c2),
+                                          st);
+  }
+  adam_kernel<float><<<g, 256, 0, s>>>(opt->mlp, nullptr, opt->grad_mlp, opt->mlp_m, opt->mlp_v, nm, lr, beta1,
+                                      beta2, eps, float(c1), float(c2), st);
+  loss_scale_update_kernel<<<1, 1, 0, s>>>(st, dynamic_scale);
+  count_launches(5);
+  return status_of(cudaGetLastError());
+}
+
+extern "C" nbvh_status nbvh_train_step(const nbvh_model_desc* desc, const nbvh_optim* opt,
+                                       const nbvh_train_scene* scene, int32_t mode, int64_t batch, uint64_t seed,
+                                       int64_t step, float lr, double* loss_out, void* workspace, size_t ws_bytes,
+                                       void* stream) {
+  if (!nbvh_host::desc_valid(desc) || !opt || !scene_valid(scene) || batch < 1 || step < 1 || !workspace ||
+      (reinterpret_cast<uintptr_t>(workspace) & 255) || batch > (int64_t(1) << 31) - 1)
+    return NBVH_ERR_INVALID_ARG;
+  TrainWs w = carve_train(workspace, desc, batch);
+  if (ws_bytes < w.bytes) return NBVH_ERR_WORKSPACE_TOO_SMALL;
+  cudaStream_t s = as_stream(stream);
+  if (cudaMemsetAsync(w.n_valid, 0, 256, s) != cudaSuccess) return NBVH_ERR_CUDA;
+  nbvh_rays_out ro{w.rays[0], w.rays[1], w.rays[2], w.rays[3], w.rays[4], w.rays[5], w.rays[6], w.rays[7], batch};
+  nbvh_status st = nbvh_train_rays(mode, seed, step - 1, scene, ro, w.leaf, w.t0, w.t1, w.n_valid, stream);
+  if (st != NBVH_OK) return st;
+  nbvh_rays ri{w.rays[0], w.rays[1], w.rays[2], w.rays[3], w.rays[4], w.rays[5], w.rays[6], w.rays[7], batch};
+  nbvh_labels lab{w.hit, w.depth, w.nx, w.ny, w.nz};
+  st = nbvh_train_labels(ri, w.leaf, w.t0, w.t1, scene, lab, stream);
+  if (st != NBVH_OK) return st;
+  const void* table = opt->table_work ? opt->table_work : opt->table_master;
+  st = nbvh_forward_train(desc, table, opt->mlp, ri, w.leaf, w.t0, w.t1, lab, w.n_valid, 1.0f, opt->loss_scale,
+                          nullptr, loss_out ? loss_out : w.loss, workspace, ws_bytes, stream);
+  if (st != NBVH_OK) return st;
+  st = nbvh_backward(desc, table, opt->mlp, ri, w.leaf, w.t0, w.t1, nullptr, opt->grad_table, opt->grad_mlp,
+                     workspace, ws_bytes, stream);
+  if (st != NBVH_OK) return st;
+  return nbvh_adam(desc, opt, step, lr, 0.9f, 0.999f, 1e-8f, desc->mlp_prec != NBVH_FP32 ? 1 : 0, stream);
 }

@@ -1,0 +1,692 @@
+// S7 + S8: training rays, brute-force labels, forward with stored activations
+// and fused loss, backward into the MLP and (trilinear scatter-add) into the
+// hash table, weight-gradient reduction, Adam with dynamic loss scaling.
+#pragma once
+#include "bounce.cuh"
+#include "eval_plain.cuh"
+#include "nbvh_internal.cuh"
+
+namespace nbvh {
+
+// ---------------------------------------------------------------------------
+// S7a: training rays (Sec. 4 "Encoding, inference & training": rays through
+// the scene that meet a node; Sec. 5.2 "Ray distribution": a ray trains the
+// first leaf it meets). Philox4x32-10 keyed by the seed, counter
+// (ray, step low, step high, draw block 0/1).
+//   mode 0 (probed mix): even rays pick a leaf uniformly, a point uniform in
+//     its box and a uniform direction, start on the bounding sphere and train
+//     that leaf; odd rays are chords of the bounding sphere and train the first
+//     leaf they meet.
+//   mode 1 (paper): origin uniform in the scene box inflated by 50%, uniform
+//     direction, train the first leaf met.
+// ---------------------------------------------------------------------------
+struct TrainRayArgs {
+  int32_t mode;
+  uint32_t k0, k1;
+  uint32_t step_lo, step_hi;
+  int64_t n;
+  const nbvh_node* nodes;
+  const float* leaf_box;  // [L][6]
+  int32_t n_leaves;
+  float centre[3], lo[3], hi[3], radius;
+  RayOut out;
+  int32_t* leaf;
+  float* t0;
+  float* t1;
+  int32_t* n_valid;  // incremented per ray with a trained leaf
+};
+
+__device__ __forceinline__ void sphere_dir_f(float u1, float u2, float& x, float& y, float& z) {
+  z = 1.0f - 2.0f * u1;
+  float s, c;
+  sincosf(kTwoPi * u2, &s, &c);
+  const float r = sqrtf(fmaxf(0.0f, 1.0f - z * z));
+  x = r * c;
+  y = r * s;
+}
+
+// Closest leaf by (t0, leaf id) along a ray: the traversal of S1 keeping only
+// the minimum key.
+__device__ __forceinline__ int first_leaf_dev(const nbvh_node* __restrict__ nodes, float ox, float oy, float oz,
+                                              float dx, float dy, float dz, float tmin, float tmax, float& bt0,
+                                              float& bt1) {
+  int best = -1;
+  bt0 = 0.0f;
+  bt1 = 0.0f;
+  int stack[kTraverseStack];
+  int sp = 0, cur = 0;
+  for (int guard = 0; guard < (1 << 26); ++guard) {
+    const float4* np = reinterpret_cast<const float4*>(nodes + cur);
+    const float4 a = __ldg(np), b = __ldg(np + 1), c = __ldg(np + 2);
+    const int4 e = __ldg(reinterpret_cast<const int4*>(np + 3));
+    float a0, a1, b0, b1;
+    bool h0 = clip_box(ox, oy, oz, dx, dy, dz, tmin, tmax, a.x, a.y, a.z, a.w, b.x, b.y, a0, a1);
+    bool h1 = (e.y != kNodeNone) && clip_box(ox, oy, oz, dx, dy, dz, tmin, tmax, b.z, b.w, c.x, c.y, c.z, c.w, b0, b1);
+    // a subtree whose box starts after the best leaf cannot hold a smaller key
+    if (best >= 0) {
+      h0 = h0 && a0 <= bt0;
+      h1 = h1 && b0 <= bt0;
+    }
+    auto take = [&](int leaf, float s0, float s1) {
+      if (best < 0 || s0 < bt0 || (s0 == bt0 && leaf < best)) {
+        best = leaf;
+        bt0 = s0;
+        bt1 = s1;
+      }
+    };
+    if (h0 && e.x < 0) take(~e.x, a0, a1);
+    if (h1 && e.y < 0) take(~e.y, b0, b1);
+    const bool g0 = h0 && e.x >= 0, g1 = h1 && e.y >= 0;
+    if (g0 && g1) {
+      const bool first0 = a0 <= b0;
+      if (sp < kTraverseStack) stack[sp++] = first0 ? e.y : e.x;
+      else set_status(NBVH_ERR_UNSUPPORTED);
+      cur = first0 ? e.x : e.y;
+    } else if (g0) {
+      cur = e.x;
+    } else if (g1) {
+      cur = e.y;
+    } else {
+      if (sp == 0) break;
+      cur = stack[--sp];
+    }
+  }
+  return best;
+}
+
+__global__ void __launch_bounds__(128) train_rays_kernel(TrainRayArgs a) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  const uint4 r = philox4x32_10(make_uint4(uint32_t(i), a.step_lo, a.step_hi, 0u), a.k0, a.k1);
+  const uint4 q = philox4x32_10(make_uint4(uint32_t(i), a.step_lo, a.step_hi, 1u), a.k0, a.k1);
+  float ox, oy, oz, dx, dy, dz, tmax = __int_as_float(0x7f800000);
+  int leaf = -1;
+  float s0 = 0.0f, s1 = 0.0f;
+  if (a.mode == 0 && (i & 1) == 0) {
+    const int lf = int((uint64_t(r.x) * uint64_t(a.n_leaves)) >> 32);
+    const float* bx = a.leaf_box + size_t(lf) * 6;
+    const float px = bx[0] + u24(r.y) * (bx[3] - bx[0]);
+    const float py = bx[1] + u24(r.z) * (bx[4] - bx[1]);
+    const float pz = bx[2] + u24(r.w) * (bx[5] - bx[2]);
+    sphere_dir_f(u24(q.x), u24(q.y), dx, dy, dz);
+    const float wx = px - a.centre[0], wy = py - a.centre[1], wz = pz - a.centre[2];
+    const float bb = wx * dx + wy * dy + wz * dz;
+    const float cc = wx * wx + wy * wy + wz * wz - a.radius * a.radius;
+    const float tb = bb + sqrtf(fmaxf(0.0f, bb * bb - cc));
+    ox = px - tb * dx;
+    oy = py - tb * dy;
+    oz = pz - tb * dz;
+    if (clip_box(ox, oy, oz, dx, dy, dz, 0.0f, tmax, bx[0], bx[1], bx[2], bx[3], bx[4], bx[5], s0, s1)) leaf = lf;
+  } else {
+    if (a.mode == 0) {  // chord of the bounding sphere
+      float ax, ay, az, ex, ey, ez;
+      sphere_dir_f(u24(r.x), u24(r.y), ax, ay, az);
+      sphere_dir_f(u24(r.z), u24(r.w), ex, ey, ez);
+      ox = a.centre[0] + a.radius * ax;
+      oy = a.centre[1] + a.radius * ay;
+      oz = a.centre[2] + a.radius * az;
+      const float vx = a.centre[0] + a.radius * ex - ox;
+      const float vy = a.centre[1] + a.radius * ey - oy;
+      const float vz = a.centre[2] + a.radius * ez - oz;
+      const float ln = sqrtf(vx * vx + vy * vy + vz * vz);
+      if (ln > 0.0f) {
+        dx = vx / ln; dy = vy / ln; dz = vz / ln;
+      } else {
+        dx = 0.0f; dy = 0.0f; dz = 1.0f;
+      }
+      tmax = ln;
+    } else {  // origin uniform in the 1.5x scene box, uniform direction
+      ox = a.centre[0] + (u24(r.x) - 0.5f) * (1.5f * (a.hi[0] - a.lo[0]));
+      oy = a.centre[1] + (u24(r.y) - 0.5f) * (1.5f * (a.hi[1] - a.lo[1]));
+      oz = a.centre[2] + (u24(r.z) - 0.5f) * (1.5f * (a.hi[2] - a.lo[2]));
+      sphere_dir_f(u24(r.w), u24(q.x), dx, dy, dz);
+    }
+    leaf = first_leaf_dev(a.nodes, ox, oy, oz, dx, dy, dz, 0.0f, tmax, s0, s1);
+  }
+  a.out.ox[i] = ox; a.out.oy[i] = oy; a.out.oz[i] = oz;
+  a.out.dx[i] = dx; a.out.dy[i] = dy; a.out.dz[i] = dz;
+  a.out.tmin[i] = 0.0f;
+  a.out.tmax[i] = tmax;
+  a.leaf[i] = leaf;
+  a.t0[i] = leaf >= 0 ? s0 : 0.0f;
+  a.t1[i] = leaf >= 0 ? s1 : 0.0f;
+  const unsigned m = __ballot_sync(__activemask(), leaf >= 0);
+  if ((threadIdx.x & 31) == __ffs(__activemask()) - 1 && m) atomicAdd(a.n_valid, __popc(m));
+}
+
+// ---------------------------------------------------------------------------
+// S7b: labels, the closest Moller-Trumbore hit among the trained leaf's own
+// triangles with t in [t0, t1] (Sec. 4: ground truth by intersecting the
+// actual geometry). Equal t keeps the earlier triangle of the leaf's list.
+// Local depth (t - t0)/(t1 - t0) (0 for t1 == t0); geometric normal turned
+// to face -d (Sec. 5.2).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) labels_kernel(RayPtrs rays, const int32_t* __restrict__ leaf,
+                                                     const float* __restrict__ t0, const float* __restrict__ t1,
+                                                     int64_t n, const float* __restrict__ tris,
+                                                     const int32_t* __restrict__ tri_perm,
+                                                     const int32_t* __restrict__ leaf_range, uint8_t* hit,
+                                                     float* depth, float* nx, float* ny, float* nz) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int lf = leaf[i];
+  uint8_t h = 0;
+  float dep = 0.0f, gx = 0.0f, gy = 0.0f, gz = 0.0f;
+  if (lf >= 0) {
+    const float ox = rays.ox[i], oy = rays.oy[i], oz = rays.oz[i];
+    const float dx = rays.dx[i], dy = rays.dy[i], dz = rays.dz[i];
+    const float a0 = t0[i], a1 = t1[i];
+    const int b = leaf_range[2 * lf], e = leaf_range[2 * lf + 1];
+    float best = __int_as_float(0x7f800000);
+    int bj = -1;
+    for (int j = b; j < e; ++j) {
+      const float* T = tris + size_t(tri_perm[j]) * 9;
+      const float v0x = __ldg(T), v0y = __ldg(T + 1), v0z = __ldg(T + 2);
+      const float e1x = __ldg(T + 3) - v0x, e1y = __ldg(T + 4) - v0y, e1z = __ldg(T + 5) - v0z;
+      const float e2x = __ldg(T + 6) - v0x, e2y = __ldg(T + 7) - v0y, e2z = __ldg(T + 8) - v0z;
+      const float px = dy * e2z - dz * e2y, py = dz * e2x - dx * e2z, pz = dx * e2y - dy * e2x;
+      const float det = e1x * px + e1y * py + e1z * pz;
+      if (det == 0.0f) continue;
+      const float inv = 1.0f / det;
+      const float sx = ox - v0x, sy = oy - v0y, sz = oz - v0z;
+      const float u = (sx * px + sy * py + sz * pz) * inv;
+      if (u < 0.0f || u > 1.0f) continue;
+      const float qx = sy * e1z - sz * e1y, qy = sz * e1x - sx * e1z, qz = sx * e1y - sy * e1x;
+      const float v = (dx * qx + dy * qy + dz * qz) * inv;
+      if (v < 0.0f || u + v > 1.0f) continue;
+      const float t = (e2x * qx + e2y * qy + e2z * qz) * inv;
+      if (t < a0 || t > a1) continue;
+      if (t < best) {
+        best = t;
+        bj = j;
+      }
+    }
+    if (bj >= 0) {
+      h = 1;
+      const float span = a1 - a0;
+      dep = span > 0.0f ? (best - a0) / span : 0.0f;
+      const float* T = tris + size_t(tri_perm[bj]) * 9;
+      const float e1x = T[3] - T[0], e1y = T[4] - T[1], e1z = T[5] - T[2];
+      const float e2x = T[6] - T[0], e2y = T[7] - T[1], e2z = T[8] - T[2];
+      gx = e1y * e2z - e1z * e2y;
+      gy = e1z * e2x - e1x * e2z;
+      gz = e1x * e2y - e1y * e2x;
+      const float ln = sqrtf(gx * gx + gy * gy + gz * gz);
+      if (ln > 0.0f) { gx /= ln; gy /= ln; gz /= ln; }
+      if (gx * dx + gy * dy + gz * dz > 0.0f) { gx = -gx; gy = -gy; gz = -gz; }
+    }
+  }
+  hit[i] = h;
+  depth[i] = dep;
+  nx[i] = gx;
+  ny[i] = gy;
+  nz[i] = gz;
+}
+
+// ---------------------------------------------------------------------------
+// S8 loss (Sec. 5.2 "Combined loss"): per valid segment
+//   2 BCE(sigmoid(o_hit), y) + y (2 |sigmoid(o_d) - d| + (1/3) sum |o_n - n|),
+// mean over valid segments; BCE from the logit. Returns the term and writes
+// dL/do (times `scale`, divided by the valid count) to g[0..4].
+// ---------------------------------------------------------------------------
+struct Labels {
+  const uint8_t* hit;
+  const float *depth, *nx, *ny, *nz;
+};
+
+__device__ __forceinline__ float sgnf(float x) { return x > 0.0f ? 1.0f : (x < 0.0f ? -1.0f : 0.0f); }
+
+__device__ __forceinline__ float loss_terms(const float* o, float y, float d, float n0, float n1, float n2,
+                                            float gscale, float* g) {
+  const float x = o[0];
+  const float bce = fmaxf(x, 0.0f) + log1pf(expf(-fabsf(x))) - y * x;
+  const float s0 = sigmoidf_(x);
+  const float s1 = sigmoidf_(o[1]);
+  const float dd = s1 - d;
+  const float e0 = o[2] - n0, e1 = o[3] - n1, e2 = o[4] - n2;
+  const float term = 2.0f * bce + y * (2.0f * fabsf(dd) + (fabsf(e0) + fabsf(e1) + fabsf(e2)) * (1.0f / 3.0f));
+  g[0] = gscale * 2.0f * (s0 - y);
+  g[1] = gscale * y * 2.0f * sgnf(dd) * s1 * (1.0f - s1);
+  g[2] = gscale * y * (1.0f / 3.0f) * sgnf(e0);
+  g[3] = gscale * y * (1.0f / 3.0f) * sgnf(e1);
+  g[4] = gscale * y * (1.0f / 3.0f) * sgnf(e2);
+  return term;
+}
+
+// Stored forward of one training batch (row i = segment of ray i).
+struct TrainBuffers {
+  float* X;         // [S][K] features
+  float* H;         // [n_hidden][S][W] hidden activations (after ReLU)
+  float* O;         // [S][n_out] raw outputs
+  float* G;         // [S][n_out] dL/dO (scaled) or the caller's output gradient
+  float* loss_seg;  // [S] per-segment loss term (0 for invalid)
+  float* dZ;        // [n_hidden][S][W] pre-activation gradients
+};
+
+struct TrainArgs {
+  GridParams gp;
+  const void* table;
+  const float* mlp;
+  int32_t n_hidden, width, n_out;
+  RayPtrs rays;
+  const int32_t* leaf;   // < 0: the segment does not train
+  const float* t0;
+  const float* t1;
+  int64_t n;
+  Labels lab;            // null hit pointer: no loss (plain forward)
+  const int32_t* n_valid;
+  float loss_scale;
+  const float* loss_scale_dev;  // if set, overrides loss_scale (dynamic scaling)
+  TrainBuffers buf;
+  float* grad_table;     // FP32 [entries][F]
+};
+
+// Forward (FP32, CUDA cores): 32 segments per tile, float-float positions,
+// activations stored for the backward; with labels, loss and dL/dO fused.
+template <typename T, int F, int W>
+__global__ void __launch_bounds__(kPlainThreads, 1) train_forward_plain(TrainArgs a) {
+  extern __shared__ __align__(16) float smem[];
+  const int K = a.gp.n_inputs;
+  const int L = a.gp.n_levels;
+  const int N = a.gp.n_samples;
+  const int n_out = a.n_out;
+  const int hid_w = (a.n_hidden - 1) * W * W + W * n_out;
+  const int feat_floats = max(K * kPlainTM, hid_w);
+  float* sfeat = smem;
+  float* sW1 = sfeat + feat_floats;
+  float* shA = sW1 + K * W;
+  float* shB = shA + W * kPlainTM;
+  float* sout = shB + W * kPlainTM;
+  int* sray = reinterpret_cast<int*>(sout + 8 * kPlainTM);
+  float* st0 = reinterpret_cast<float*>(sray + kPlainTM);
+  float* st1 = st0 + kPlainTM;
+
+  const int64_t n_tiles = (a.n + kPlainTM - 1) / kPlainTM;
+  if (int64_t(blockIdx.x) >= n_tiles) return;
+  const float* W1 = a.mlp;
+  const float* b1 = W1 + W * K;
+  for (int i = threadIdx.x; i < K * W; i += blockDim.x) {
+    const int n = i / K, k = i - n * K;
+    sW1[k * W + n] = __ldg(W1 + i);
+  }
+  const T* table = static_cast<const T*>(a.table);
+  const float inv_valid = a.n_valid ? 1.0f / float(max(1, *a.n_valid)) : 1.0f;
+  const float lscale = a.loss_scale_dev ? *a.loss_scale_dev : a.loss_scale;
+
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    if (threadIdx.x < kPlainTM) {
+      const int64_t i = tile * kPlainTM + threadIdx.x;
+      int ray = -1;
+      float t0 = 0.0f, t1 = 0.0f;
+      if (i < a.n && a.leaf[i] >= 0) {
+        ray = int(i);
+        t0 = a.t0[i];
+        t1 = a.t1[i];
+      }
+      sray[threadIdx.x] = ray;
+      st0[threadIdx.x] = t0;
+      st1[threadIdx.x] = t1;
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < kPlainTM * N; p += blockDim.x) {
+      const int s = p % kPlainTM;
+      const int k = p / kPlainTM;
+      const int ray = sray[s];
+      const int kb = k * L * F;
+      if (ray < 0) {
+        for (int j = 0; j < L * F; ++j) sfeat[act_idx(kb + j, s)] = 0.0f;
+        continue;
+      }
+      FF x, y, z;
+      sample_point_ff(a.gp, a.rays.ox[ray], a.rays.oy[ray], a.rays.oz[ray], a.rays.dx[ray], a.rays.dy[ray],
+                      a.rays.dz[ray], st0[s], st1[s], k, x, y, z);
+      for (int l = 0; l < L; ++l) {
+        float v[F];
+        encode_level<T, F>(a.gp, table, l, x, y, z, v);
+#pragma unroll
+        for (int f = 0; f < F; ++f) sfeat[act_idx(kb + l * F + f, s)] = v[f];
+      }
+    }
+    __syncthreads();
+    // store features [S][K]
+    for (int idx = threadIdx.x; idx < kPlainTM * K; idx += blockDim.x) {
+      const int s = idx / K, k = idx - s * K;
+      const int64_t i = tile * kPlainTM + s;
+      if (i < a.n) a.buf.X[i * K + k] = sfeat[act_idx(k, s)];
+    }
+    dense_plain<W, true>(sfeat, K, sW1, b1, shA);
+    __syncthreads();
+    auto store_h = [&](const float* h, int layer) {
+      for (int idx = threadIdx.x; idx < kPlainTM * W; idx += blockDim.x) {
+        const int s = idx / W, j = idx - s * W;
+        const int64_t i = tile * kPlainTM + s;
+        if (i < a.n) a.buf.H[(size_t(layer) * a.n + i) * W + j] = h[act_idx(j, s)];
+      }
+    };
+    store_h(shA, 0);
+    {
+      const float* src = b1 + W;
+      float* dst = sfeat;
+      for (int h = 1; h < a.n_hidden; ++h) {
+        for (int i = threadIdx.x; i < W * W; i += blockDim.x) {
+          const int n = i / W, k = i - n * W;
+          dst[k * W + n] = __ldg(src + i);
+        }
+        src += W * W + W;
+        dst += W * W;
+      }
+      for (int i = threadIdx.x; i < n_out * W; i += blockDim.x) {
+        const int n = i / W, k = i - n * W;
+        dst[k * n_out + n] = __ldg(src + i);
+      }
+    }
+    __syncthreads();
+    const float* bh = b1 + W;
+    float* hin = shA;
+    float* hout = shB;
+    const float* wt = sfeat;
+    for (int h = 1; h < a.n_hidden; ++h) {
+      dense_plain<W, true>(hin, W, wt, bh + W * W, hout);
+      __syncthreads();
+      store_h(hout, h);
+      float* tmp = hin; hin = hout; hout = tmp;
+      bh += W * W + W;
+      wt += W * W;
+    }
+    {
+      const float* bo = bh + n_out * W;
+      for (int i = threadIdx.x; i < n_out * kPlainTM; i += blockDim.x) {
+        const int j = i / kPlainTM, s = i - j * kPlainTM;
+        float acc = __ldg(bo + j);
+        for (int k = 0; k < W; ++k) acc = fmaf(wt[k * n_out + j], hin[act_idx(k, s)], acc);
+        sout[j * kPlainTM + s] = acc;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < kPlainTM) {
+      const int s = threadIdx.x;
+      const int64_t i = tile * kPlainTM + s;
+      if (i < a.n) {
+        float o[8], g[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int j = 0; j < n_out; ++j) o[j] = sout[j * kPlainTM + s];
+        float term = 0.0f;
+        if (a.lab.hit && sray[s] >= 0) {
+          term = loss_terms(o, float(a.lab.hit[i]), a.lab.depth[i], a.lab.nx[i], a.lab.ny[i], a.lab.nz[i],
+                            lscale * inv_valid, g);
+        }
+        for (int j = 0; j < n_out; ++j) a.buf.O[i * n_out + j] = o[j];
+        if (a.lab.hit) {
+          for (int j = 0; j < n_out; ++j) a.buf.G[i * n_out + j] = g[j];
+          a.buf.loss_seg[i] = term;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Backward (FP32, CUDA cores): from G = dL/dO through the MLP (dZ stored for
+// the weight gradients) to dL/dfeatures, then the adjoint of the encoding:
+// every (sample, level, corner) adds weight * dL/dfeature into its table
+// entry's FP32 gradient with a vector atomic (collisions accumulate).
+template <typename T, int F, int W>
+__global__ void __launch_bounds__(kPlainThreads, 1) train_backward_plain(TrainArgs a) {
+  extern __shared__ __align__(16) float smem[];
+  const int K = a.gp.n_inputs;
+  const int L = a.gp.n_levels;
+  const int N = a.gp.n_samples;
+  const int n_out = a.n_out;
+  const int nh = a.n_hidden;
+  float* sdX = smem;                       // [K][TM] dL/dfeatures
+  float* sWh = sdX + K * kPlainTM;         // [(nh - 1)][W][W] hidden weights, row-major
+  float* sWo = sWh + (nh - 1) * W * W;     // [n_out][W]
+  float* sdA = sWo + n_out * W;            // [W][TM]
+  float* sdB = sdA + W * kPlainTM;         // [W][TM]
+  float* sH = sdB + W * kPlainTM;          // [W][TM] stored activation of the current layer
+  float* sG = sH + W * kPlainTM;           // [8][TM]
+  int* sray = reinterpret_cast<int*>(sG + 8 * kPlainTM);
+  float* st0 = reinterpret_cast<float*>(sray + kPlainTM);
+  float* st1 = st0 + kPlainTM;
+
+  const int64_t n_tiles = (a.n + kPlainTM - 1) / kPlainTM;
+  if (int64_t(blockIdx.x) >= n_tiles) return;
+  const float* W1 = a.mlp;  // [W][K]; dX reads it at warp-uniform addresses (L1 broadcast)
+  {
+    const float* p = a.mlp + W * K + W;
+    for (int h = 1; h < nh; ++h) {
+      for (int i = threadIdx.x; i < W * W; i += blockDim.x) sWh[(h - 1) * W * W + i] = __ldg(p + i);
+      p += W * W + W;
+    }
+    for (int i = threadIdx.x; i < n_out * W; i += blockDim.x) sWo[i] = __ldg(p + i);
+  }
+  __syncthreads();
+
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    if (threadIdx.x < kPlainTM) {
+      const int64_t i = tile * kPlainTM + threadIdx.x;
+      int ray = -1;
+      float t0 = 0.0f, t1 = 0.0f;
+      if (i < a.n && a.leaf[i] >= 0) {
+        ray = int(i);
+        t0 = a.t0[i];
+        t1 = a.t1[i];
+      }
+      sray[threadIdx.x] = ray;
+      st0[threadIdx.x] = t0;
+      st1[threadIdx.x] = t1;
+    }
+    for (int idx = threadIdx.x; idx < n_out * kPlainTM; idx += blockDim.x) {
+      const int j = idx / kPlainTM, s = idx - j * kPlainTM;
+      const int64_t i = tile * kPlainTM + s;
+      sG[j * kPlainTM + s] = i < a.n ? a.buf.G[i * n_out + j] : 0.0f;
+    }
+    __syncthreads();
+    // layer by layer from the top: dH = (dZ_above) W_above; dZ = dH * (H > 0)
+    float* dz = sdA;
+    for (int h = nh - 1; h >= 0; --h) {
+      for (int idx = threadIdx.x; idx < W * kPlainTM; idx += blockDim.x) {
+        const int j = idx / kPlainTM, s = idx - j * kPlainTM;
+        const int64_t i = tile * kPlainTM + s;
+        sH[j * kPlainTM + s] = i < a.n ? a.buf.H[(size_t(h) * a.n + i) * W + j] : 0.0f;
+      }
+      __syncthreads();
+      float* out = (h == nh - 1) ? sdA : (dz == sdA ? sdB : sdA);
+      for (int idx = threadIdx.x; idx < W * kPlainTM; idx += blockDim.x) {
+        const int j = idx / kPlainTM, s = idx - j * kPlainTM;
+        float acc = 0.0f;
+        if (h == nh - 1) {
+          for (int o = 0; o < n_out; ++o) acc = fmaf(sG[o * kPlainTM + s], sWo[o * W + j], acc);
+        } else {
+          const float* Wa = sWh + h * W * W;  // layer h+1 weights [W][W]
+          for (int o = 0; o < W; ++o) acc = fmaf(dz[o * kPlainTM + s], Wa[o * W + j], acc);
+        }
+        const float g = sH[j * kPlainTM + s] > 0.0f ? acc : 0.0f;
+        out[j * kPlainTM + s] = g;
+      }
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < W * kPlainTM; idx += blockDim.x) {
+        const int s = idx / W, j = idx - s * W;
+        const int64_t i = tile * kPlainTM + s;
+        if (i < a.n) a.buf.dZ[(size_t(h) * a.n + i) * W + j] = out[j * kPlainTM + s];
+      }
+      dz = out;
+      __syncthreads();
+    }
+    // dX = dZ1 W1
+    for (int idx = threadIdx.x; idx < K * kPlainTM; idx += blockDim.x) {
+      const int k = idx / kPlainTM, s = idx - k * kPlainTM;
+      float acc = 0.0f;
+      for (int o = 0; o < W; ++o) acc = fmaf(dz[o * kPlainTM + s], __ldg(W1 + o * K + k), acc);
+      sdX[k * kPlainTM + s] = acc;
+    }
+    __syncthreads();
+    // adjoint of the encoding: scatter into the table gradient
+    for (int p = threadIdx.x; p < kPlainTM * N; p += blockDim.x) {
+      const int s = p % kPlainTM;
+      const int k = p / kPlainTM;
+      const int ray = sray[s];
+      if (ray < 0) continue;
+      FF x, y, z;
+      sample_point_ff(a.gp, a.rays.ox[ray], a.rays.oy[ray], a.rays.oz[ray], a.rays.dx[ray], a.rays.dy[ray],
+                      a.rays.dz[ray], st0[s], st1[s], k, x, y, z);
+      for (int l = 0; l < L; ++l) {
+        Corners c;
+        level_corners(a.gp, l, x, y, z, c);
+        float gf[F];
+#pragma unroll
+        for (int f = 0; f < F; ++f) gf[f] = sdX[(k * L * F + l * F + f) * kPlainTM + s];
+        float* gt = a.grad_table + a.gp.offset[l] * F;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          float* dst = gt + size_t(c.idx[q]) * F;
+          if constexpr (F == 2) {
+            atomicAdd(reinterpret_cast<float2*>(dst), make_float2(c.w[q] * gf[0], c.w[q] * gf[1]));
+          } else if constexpr (F % 4 == 0) {
+#pragma unroll
+            for (int f = 0; f < F; f += 4)
+              atomicAdd(reinterpret_cast<float4*>(dst + f),
+                        make_float4(c.w[q] * gf[f], c.w[q] * gf[f + 1], c.w[q] * gf[f + 2], c.w[q] * gf[f + 3]));
+          } else {
+            atomicAdd(dst, c.w[q] * gf[0]);
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+inline size_t train_fwd_smem(int K, int W, int nh, int n_out) { return plain_smem_bytes(K, W, nh, n_out); }
+
+inline size_t train_bwd_smem(int K, int W, int nh, int n_out) {
+  return sizeof(float) * (size_t(K) * kPlainTM + size_t(nh - 1) * W * W + size_t(n_out) * W +
+                          3 * size_t(W) * kPlainTM + 8 * kPlainTM) +
+         3 * sizeof(int) * kPlainTM;
+}
+
+// ---------------------------------------------------------------------------
+// Weight gradients: dW_l[o][j] = sum_i dZ_l[i][o] A_{l-1}[i][j] and
+// db_l[o] = sum_i dZ_l[i][o] over the batch (A_0 = features, A_l = H_l; the
+// output layer uses G). Split-K over segment chunks: each block reduces a
+// 32 x 32 output block over one chunk in FP32 and adds it with atomics.
+// ---------------------------------------------------------------------------
+constexpr int kWgTile = 32;
+constexpr int kWgChunk = 2048;
+
+__global__ void __launch_bounds__(256) weight_grad_kernel(const float* __restrict__ dZ, int n_o,
+                                                          const float* __restrict__ A, int n_j, int64_t n,
+                                                          float* __restrict__ dW, float* __restrict__ db) {
+  __shared__ float sz[32][kWgTile + 1];
+  __shared__ float sa[32][kWgTile + 1];
+  const int o0 = blockIdx.x * kWgTile;
+  const int j0 = blockIdx.y * kWgTile;
+  const int64_t i0 = int64_t(blockIdx.z) * kWgChunk;
+  const int64_t i1 = min(n, i0 + kWgChunk);
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 8 rows of 4 outputs
+  float acc[4] = {0, 0, 0, 0};
+  float bacc = 0.0f;
+  for (int64_t ib = i0; ib < i1; ib += 32) {
+    for (int idx = threadIdx.x; idx < 32 * kWgTile; idx += blockDim.x) {
+      const int r = idx / kWgTile, c = idx - r * kWgTile;
+      const int64_t i = ib + r;
+      sz[r][c] = (i < i1 && o0 + c < n_o) ? dZ[i * n_o + o0 + c] : 0.0f;
+      sa[r][c] = (i < i1 && j0 + c < n_j) ? A[i * n_j + j0 + c] : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int r = 0; r < 32; ++r) {
+      const float av = sa[r][tx];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] = fmaf(sz[r][ty * 4 + q], av, acc[q]);
+      if (blockIdx.y == 0 && ty == 0) bacc += sz[r][tx];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int o = o0 + ty * 4 + q, j = j0 + tx;
+    if (o < n_o && j < n_j) atomicAdd(dW + size_t(o) * n_j + j, acc[q]);
+  }
+  if (blockIdx.y == 0 && ty == 0 && o0 + tx < n_o) atomicAdd(db + o0 + tx, bacc);
+}
+
+// ---------------------------------------------------------------------------
+// Adam (Kingma & Ba 2015, bias-corrected) on FP32 masters with the gradient
+// unscaled by the loss scale; a step whose gradients hold inf/NaN is skipped
+// and halves the scale; 2000 clean steps double it. The working copy of the
+// table (the precision the kernels read) is refreshed from the master.
+// ---------------------------------------------------------------------------
+struct AdamState {
+  float* loss_scale;   // device scalar
+  int32_t* good_steps; // device scalar
+  int32_t* bad;        // device scalar: set when a gradient is not finite
+  int32_t* applied;    // device scalar: 1 when the last step was applied
+};
+
+__global__ void grad_check_kernel(const float* __restrict__ g, int64_t n, int32_t* bad) {
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  bool ok = true;
+  for (; i < n; i += stride) ok &= isfinite(g[i]);
+  if (!__all_sync(0xffffffffu, ok) && (threadIdx.x & 31) == 0) atomicExch(bad, 1);
+}
+
+template <typename T>
+__global__ void adam_kernel(float* __restrict__ master, T* __restrict__ work, float* __restrict__ grad,
+                            float* __restrict__ m, float* __restrict__ v, int64_t n, float lr, float b1, float b2,
+                            float eps, float c1, float c2, AdamState st) {
+  const bool skip = *st.bad != 0;
+  const float inv_scale = 1.0f / *st.loss_scale;
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (; i < n; i += stride) {
+    if (!skip) {
+      const float g = grad[i] * inv_scale;
+      const float mi = b1 * m[i] + (1.0f - b1) * g;
+      const float vi = b2 * v[i] + (1.0f - b2) * g * g;
+      m[i] = mi;
+      v[i] = vi;
+      const float p = master[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+      master[i] = p;
+      if (work) {
+        if constexpr (std::is_same<T, __half>::value) work[i] = __float2half_rn(p);
+        else if constexpr (std::is_same<T, __nv_bfloat16>::value) work[i] = __float2bfloat16_rn(p);
+        else work[i] = p;
+      }
+    }
+    grad[i] = 0.0f;
+  }
+}
+
+__global__ void loss_scale_update_kernel(AdamState st, int32_t dynamic) {
+  const bool bad = *st.bad != 0;
+  *st.applied = bad ? 0 : 1;
+  if (dynamic) {
+    if (bad) {
+      *st.loss_scale = fmaxf(1.0f, *st.loss_scale * 0.5f);
+      *st.good_steps = 0;
+    } else if (++*st.good_steps >= 2000) {
+      *st.loss_scale = *st.loss_scale * 2.0f;
+      *st.good_steps = 0;
+    }
+  }
+  *st.bad = 0;
+}
+
+// Sum of per-segment loss terms in FP64 divided by the valid count (the batch
+// loss); also used by the finite-difference gradient check.
+__global__ void loss_reduce_kernel(const float* __restrict__ term, int64_t n, const int32_t* n_valid,
+                                   double* out) {
+  __shared__ double sm[256];
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) acc += double(term[i]);
+  sm[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = sm[0] / double(max(1, *n_valid));
+}
+
+}  // namespace nbvh

@@ -61,6 +61,22 @@ class SceneInfo(ctypes.Structure):
                 ("sphere_radius", c_float)]
 
 
+class TrainScene(ctypes.Structure):
+    _fields_ = [("nodes", c_void_p), ("n_nodes", c_int32), ("leaf_box", c_void_p), ("n_leaves", c_int32),
+                ("tris", c_void_p), ("tri_perm", c_void_p), ("leaf_range", c_void_p), ("info", SceneInfo)]
+
+
+class Labels(ctypes.Structure):
+    _fields_ = [(k, c_void_p) for k in ("hit", "depth", "nx", "ny", "nz")]
+
+
+class Optim(ctypes.Structure):
+    _fields_ = [(k, c_void_p) for k in ("table_master", "table_work", "table_m", "table_v", "grad_table", "mlp",
+                                        "mlp_m", "mlp_v", "grad_mlp", "loss_scale", "counters")]
+
+
+TRAIN_PROBED_MIX, TRAIN_PAPER = 0, 1
+
 _lib = None
 
 _SIGS = {
@@ -88,6 +104,19 @@ _SIGS = {
     "nbvh_launch_count": (c_int64, []),
     "nbvh_query_rays_static": (c_int32, [POINTER(ModelDesc), c_void_p, c_void_p, c_void_p, c_int32, Rays, c_int32,
                                          Hits, c_void_p]),
+    "nbvh_train_rays": (c_int32, [c_int32, ctypes.c_uint64, c_int64, POINTER(TrainScene), RaysOut, c_void_p,
+                                  c_void_p, c_void_p, c_void_p, c_void_p]),
+    "nbvh_train_labels": (c_int32, [Rays, c_void_p, c_void_p, c_void_p, POINTER(TrainScene), Labels, c_void_p]),
+    "nbvh_train_workspace_size": (c_int32, [POINTER(ModelDesc), c_int64, POINTER(c_size_t)]),
+    "nbvh_forward_train": (c_int32, [POINTER(ModelDesc), c_void_p, c_void_p, Rays, c_void_p, c_void_p, c_void_p,
+                                     Labels, c_void_p, c_float, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t,
+                                     c_void_p]),
+    "nbvh_backward": (c_int32, [POINTER(ModelDesc), c_void_p, c_void_p, Rays, c_void_p, c_void_p, c_void_p,
+                                c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "nbvh_adam": (c_int32, [POINTER(ModelDesc), POINTER(Optim), c_int64, c_float, c_float, c_float, c_float, c_int32,
+                            c_void_p]),
+    "nbvh_train_step": (c_int32, [POINTER(ModelDesc), POINTER(Optim), POINTER(TrainScene), c_int32, c_int64,
+                                  ctypes.c_uint64, c_int64, c_float, c_void_p, c_void_p, c_size_t, c_void_p]),
     "nbvh_get_device_status": (c_int32, [c_void_p]),
 }
 
@@ -377,3 +406,152 @@ def query_rays_static(desc: ModelDesc, table, mlp, nodes, n_nodes: int, rays: di
                                         rays_struct(rays), max_segs, hits_struct(out), _stream()),
            "query_rays_static")
     return out
+
+
+# ---------------------------------------------------------------- training
+class DeviceScene:
+    """Device copies of the geometry the training step reads."""
+
+    def __init__(self, tris: np.ndarray, leaves: dict, device="cuda"):
+        torch = _torch()
+        self.tris = torch.as_tensor(np.ascontiguousarray(tris, np.float32).reshape(-1, 9), device=device)
+        self.nodes = torch.as_tensor(leaves["nodes"], device=device)
+        box = np.concatenate([leaves["leaf_lo"], leaves["leaf_hi"]], 1).astype(np.float32)
+        self.leaf_box = torch.as_tensor(np.ascontiguousarray(box), device=device)
+        self.tri_perm = torch.as_tensor(leaves["tri_perm"], device=device)
+        self.leaf_range = torch.as_tensor(np.ascontiguousarray(leaves["leaf_range"], np.int32), device=device)
+        self.n_nodes = leaves["n_nodes"]
+        self.n_leaves = len(leaves["leaf_lo"])
+        sc = TrainScene()
+        sc.nodes = self.nodes.data_ptr()
+        sc.n_nodes = self.n_nodes
+        sc.leaf_box = self.leaf_box.data_ptr()
+        sc.n_leaves = self.n_leaves
+        sc.tris = self.tris.data_ptr()
+        sc.tri_perm = self.tri_perm.data_ptr()
+        sc.leaf_range = self.leaf_range.data_ptr()
+        inf = leaves["info"]
+        for i in range(3):
+            sc.info.lo[i] = float(inf["lo"][i])
+            sc.info.hi[i] = float(inf["hi"][i])
+            sc.info.centre[i] = float(inf["centre"][i])
+        sc.info.extent = float(inf["extent"])
+        sc.info.sphere_radius = float(inf["sphere_radius"])
+        self.struct = sc
+
+
+def train_rays(mode: int, seed: int, step: int, scene: DeviceScene, n: int):
+    torch = _torch()
+    dev = scene.nodes.device
+    rays = new_rays(n, dev)
+    leaf = torch.empty(n, dtype=torch.int32, device=dev)
+    t0 = torch.empty(n, dtype=torch.float32, device=dev)
+    t1 = torch.empty(n, dtype=torch.float32, device=dev)
+    n_valid = torch.zeros(1, dtype=torch.int32, device=dev)
+    o = RaysOut()
+    for k in RAY_KEYS:
+        setattr(o, k, rays[k].data_ptr())
+    o.n = n
+    _check(lib().nbvh_train_rays(mode, ctypes.c_uint64(seed), step, ctypes.byref(scene.struct), o, _ptr(leaf),
+                                 _ptr(t0), _ptr(t1), _ptr(n_valid), _stream()), "train_rays")
+    return rays, leaf, t0, t1, n_valid
+
+
+def new_labels(n: int, device="cuda") -> dict:
+    torch = _torch()
+    return {"hit": torch.empty(n, dtype=torch.uint8, device=device),
+            **{k: torch.empty(n, dtype=torch.float32, device=device) for k in ("depth", "nx", "ny", "nz")}}
+
+
+def labels_struct(lab) -> Labels:
+    s = Labels()
+    if lab is not None:
+        for k in ("hit", "depth", "nx", "ny", "nz"):
+            setattr(s, k, lab[k].data_ptr())
+    return s
+
+
+def train_labels(rays: dict, leaf, t0, t1, scene: DeviceScene, out=None):
+    n = rays["ox"].numel()
+    if out is None:
+        out = new_labels(n, rays["ox"].device)
+    _check(lib().nbvh_train_labels(rays_struct(rays), _ptr(leaf), _ptr(t0), _ptr(t1), ctypes.byref(scene.struct),
+                                   labels_struct(out), _stream()), "train_labels")
+    return out
+
+
+def train_workspace_size(desc: ModelDesc, n: int) -> int:
+    b = c_size_t()
+    _check(lib().nbvh_train_workspace_size(ctypes.byref(desc), n, ctypes.byref(b)), "train_workspace_size")
+    return b.value
+
+
+def forward_train(desc: ModelDesc, table, mlp, rays: dict, leaf, t0, t1, workspace, labels=None, n_valid=None,
+                  loss_scale: float = 1.0, loss_scale_dev=None, raw_out=None, loss_out=None):
+    torch = _torch()
+    n = rays["ox"].numel()
+    if raw_out is None:
+        raw_out = torch.empty((n, desc.n_out), dtype=torch.float32, device=rays["ox"].device)
+    base = aligned_ptr(workspace)
+    avail = workspace.numel() - (base - workspace.data_ptr())
+    _check(lib().nbvh_forward_train(ctypes.byref(desc), _ptr(table), _ptr(mlp), rays_struct(rays), _ptr(leaf),
+                                    _ptr(t0), _ptr(t1), labels_struct(labels), _ptr(n_valid), float(loss_scale),
+                                    _ptr(loss_scale_dev), _ptr(raw_out), _ptr(loss_out), c_void_p(base), avail,
+                                    _stream()), "forward_train")
+    return raw_out
+
+
+def backward(desc: ModelDesc, table, mlp, rays: dict, leaf, t0, t1, workspace, grad_table, grad_mlp,
+             grad_out=None):
+    base = aligned_ptr(workspace)
+    avail = workspace.numel() - (base - workspace.data_ptr())
+    _check(lib().nbvh_backward(ctypes.byref(desc), _ptr(table), _ptr(mlp), rays_struct(rays), _ptr(leaf), _ptr(t0),
+                               _ptr(t1), _ptr(grad_out), _ptr(grad_table), _ptr(grad_mlp), c_void_p(base), avail,
+                               _stream()), "backward")
+
+
+class Optimizer:
+    """FP32 master parameters, Adam moments, gradients and the loss scale, all
+    device tensors owned here and handed to the library as plain pointers."""
+
+    def __init__(self, desc: ModelDesc, table_master, mlp, loss_scale: float = 1.0):
+        torch = _torch()
+        self.desc = desc
+        self.table_master = table_master.contiguous()
+        dev = self.table_master.device
+        self.table_work = None
+        if desc.table_prec != FP32:
+            self.table_work = self.table_master.to(table_dtype(desc.table_prec))
+        self.table_m = torch.zeros_like(self.table_master)
+        self.table_v = torch.zeros_like(self.table_master)
+        self.grad_table = torch.zeros_like(self.table_master)
+        self.mlp = mlp.contiguous()
+        self.mlp_m = torch.zeros_like(self.mlp)
+        self.mlp_v = torch.zeros_like(self.mlp)
+        self.grad_mlp = torch.zeros_like(self.mlp)
+        self.loss_scale = torch.tensor([loss_scale], dtype=torch.float32, device=dev)
+        self.counters = torch.zeros(4, dtype=torch.int32, device=dev)
+        o = Optim()
+        for k in ("table_master", "table_m", "table_v", "grad_table", "mlp", "mlp_m", "mlp_v", "grad_mlp",
+                  "loss_scale", "counters"):
+            setattr(o, k, getattr(self, k).data_ptr())
+        o.table_work = self.table_work.data_ptr() if self.table_work is not None else None
+        self.struct = o
+
+    @property
+    def table(self):
+        return self.table_work if self.table_work is not None else self.table_master
+
+    def adam(self, step: int, lr: float = 1e-2, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
+             dynamic_scale: bool = False):
+        _check(lib().nbvh_adam(ctypes.byref(self.desc), ctypes.byref(self.struct), step, lr, beta1, beta2, eps,
+                               1 if dynamic_scale else 0, _stream()), "adam")
+
+
+def train_step(desc: ModelDesc, opt: Optimizer, scene: DeviceScene, mode: int, batch: int, seed: int, step: int,
+               lr: float, workspace, loss_out=None):
+    base = aligned_ptr(workspace)
+    avail = workspace.numel() - (base - workspace.data_ptr())
+    _check(lib().nbvh_train_step(ctypes.byref(desc), ctypes.byref(opt.struct), ctypes.byref(scene.struct), mode,
+                                 batch, ctypes.c_uint64(seed), step, lr, _ptr(loss_out), c_void_p(base), avail,
+                                 _stream()), "train_step")

@@ -1,0 +1,307 @@
+"""GPU parity of the training path (S7, S8) against the FP64 oracle through the
+C ABI: training rays, labels, loss, analytic gradients (table and MLP), the
+autograd.Function, Adam, a finite-difference check with FP64 reductions on the
+GPU, and a learning test against brute-force ground truth."""
+import math
+
+import numpy as np
+import pytest
+
+from gpu_cases import Built, make_case
+from oracle import nbvh_oracle as O
+from paper_2405_16237_b300 import nbvh as B
+from paper_2405_16237_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _torch():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    return torch
+
+
+_CACHE = {}
+
+
+def built(scale=0.5, gain=2.0):
+    key = (scale, gain)
+    if key not in _CACHE:
+        _torch()
+        b = Built(make_case("random_tris_c0", scale, gain))
+        b.scene = B.DeviceScene(b.case.tris, b.leaves)
+        _CACHE[key] = b
+    return _CACHE[key]
+
+
+# ---------------------------------------------------------------- S7 rays
+@pytest.mark.parametrize("mode", [B.TRAIN_PROBED_MIX, B.TRAIN_PAPER])
+def test_train_rays_parity(mode):
+    b = built()
+    n, seed, step = 4096, (3 << 32) | 977, 5
+    rays, leaf, t0, t1, nv = B.train_rays(mode, seed, step, b.scene, n)
+    g = {k: v.cpu().numpy().astype(np.float64) for k, v in rays.items()}
+    gl = leaf.cpu().numpy()
+    ref = O.train_rays(mode, seed, step, n, b.oleaves)
+    go = np.stack([g["ox"], g["oy"], g["oz"]], 1)
+    gd = np.stack([g["dx"], g["dy"], g["dz"]], 1)
+    assert np.max(np.abs(gd - ref["d"])) <= 2e-6
+    assert np.max(np.abs(go - ref["o"])) <= 5e-6
+    assert int(nv.item()) == int((gl >= 0).sum())
+    same = gl == ref["leaf"]
+    assert same.mean() >= 0.998
+    # the rest are near ties of the first leaf (t0 within 1e-5) or marginal clips
+    for i in np.nonzero(~same)[0]:
+        k, a0, _, _, _ = O.clip_ray_box(ref["o"][i], ref["d"][i], 0.0, ref["tmax"][i], b.oleaves["leaf_lo"],
+                                        b.oleaves["leaf_hi"])
+        if gl[i] >= 0 and ref["leaf"][i] >= 0:
+            assert abs(a0[gl[i]] - ref["t0"][i]) <= 1e-5
+    ok = same & (gl >= 0)
+    assert np.max(np.abs(t0.cpu().numpy()[ok] - ref["t0"][ok])) <= 1e-5
+    assert np.max(np.abs(t1.cpu().numpy()[ok] - ref["t1"][ok])) <= 1e-5
+
+
+def _segments(b, n=3000, seed=41):
+    """Input rays (workloads module) with the oracle's first-leaf segments."""
+    rays = W.mixed_rays(n, seed=seed, radius=0.8)
+    o, d, tmin, tmax = O.rays_od(rays)
+    leaf, t0, t1 = O.first_leaf(o, d, tmin, tmax, b.oleaves["leaf_lo"], b.oleaves["leaf_hi"])
+    return rays, o, d, leaf.astype(np.int32), t0.astype(np.float32), t1.astype(np.float32)
+
+
+def _dev(torch, *arrs):
+    return [torch.as_tensor(np.ascontiguousarray(a)).cuda() for a in arrs]
+
+
+# ---------------------------------------------------------------- S7 labels
+def test_labels_parity():
+    torch = _torch()
+    b = built()
+    rays, o, d, leaf, t0, t1 = _segments(b)
+    dl, dt0, dt1 = _dev(torch, leaf, t0, t1)
+    lab = B.train_labels(B.to_device_rays(rays), dl, dt0, dt1, b.scene)
+    got = {k: v.cpu().numpy() for k, v in lab.items()}
+    ref = O.labels(o, d, leaf, t0.astype(np.float64), t1.astype(np.float64), b.case.tris, b.oleaves["tri_perm"],
+                   b.oleaves["leaf_range"])
+    ok = ref["margin"] > 1e-5
+    assert ok.mean() > 0.97 and (ref["hit"][ok] == 1).sum() > 50
+    assert np.array_equal(got["hit"][ok], ref["hit"][ok])
+    h = ok & (ref["hit"] == 1)
+    assert np.max(np.abs(got["depth"][h] - ref["depth"][h])) <= 1e-4
+    gn = np.stack([got["nx"], got["ny"], got["nz"]], 1)
+    assert np.max(np.abs(gn[h] - ref["normal"][h])) <= 1e-5
+    assert np.all(got["hit"][leaf < 0] == 0)
+
+
+# ---------------------------------------------------------------- S8 forward, loss, gradients
+def _batch(b, n=2000, seed=43):
+    torch = _torch()
+    rays, o, d, leaf, t0, t1 = _segments(b, n, seed)
+    lab = W.random_labels(n, seed=seed + 1, hit_fraction=0.6)
+    valid = leaf >= 0
+    dev = dict(rays=B.to_device_rays(rays), leaf=_dev(torch, leaf)[0], t0=_dev(torch, t0)[0],
+               t1=_dev(torch, t1)[0], lab={k: _dev(torch, v)[0] for k, v in lab.items()},
+               n_valid=torch.tensor([int(valid.sum())], dtype=torch.int32, device="cuda"))
+    host = dict(o=o, d=d, leaf=leaf, t0=t0.astype(np.float64), t1=t1.astype(np.float64), valid=valid,
+                yh=lab["hit"].astype(np.float64), yd=lab["depth"].astype(np.float64),
+                yn=np.stack([lab["nx"], lab["ny"], lab["nz"]], 1).astype(np.float64))
+    return dev, host
+
+
+def _oracle_fb(b, h):
+    fr = b.oleaves["frame"]
+    return O.forward_backward(h["o"], h["d"], h["t0"], h["t1"], h["valid"], h["yh"], h["yd"], h["yn"],
+                              b.table_host, b.layers, b.olayout, fr["model_centre"], fr["model_extent"],
+                              b.case.model.n_samples)
+
+
+def test_forward_loss_and_gradients_fp32():
+    torch = _torch()
+    b = built()
+    dv, h = _batch(b)
+    n = len(h["leaf"])
+    ws = B.new_workspace(B.train_workspace_size(b.desc, n))
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    raw = B.forward_train(b.desc, b.table, b.mlp, dv["rays"], dv["leaf"], dv["t0"], dv["t1"], ws,
+                          labels=dv["lab"], n_valid=dv["n_valid"], loss_out=loss)
+    g_tab = torch.zeros((b.layout["total"], b.case.model.n_features), dtype=torch.float32, device="cuda")
+    g_mlp = torch.zeros_like(b.mlp)
+    B.backward(b.desc, b.table, b.mlp, dv["rays"], dv["leaf"], dv["t0"], dv["t1"], ws, g_tab, g_mlp)
+    assert B.device_status() == 0
+    L, ref_tab, ref_layers, ref_raw = _oracle_fb(b, h)
+    v = h["valid"]
+    r = raw.cpu().numpy()[v]
+    scale_j = np.sqrt(np.mean(ref_raw[v] ** 2, axis=0))
+    assert np.max(np.abs(r - ref_raw[v]) / (np.abs(ref_raw[v]) + scale_j)) <= 1e-5
+    assert abs(float(loss.item()) - L) <= 1e-5 * abs(L)
+    gt = g_tab.cpu().numpy()
+    assert np.max(np.abs(gt - ref_tab)) <= 1e-5 * np.max(np.abs(ref_tab))
+    gm = g_mlp.cpu().numpy()
+    ref_m = B.pack_mlp([(dw, db) for dw, db in ref_layers])
+    assert np.max(np.abs(gm - ref_m)) <= 1e-5 * np.max(np.abs(ref_m))
+
+
+def test_autograd_function_matches_oracle_adjoint():
+    torch = _torch()
+    from paper_2405_16237_b300.autograd import NBVHQueryFn
+    b = built()
+    dv, h = _batch(b, n=1200, seed=51)
+    n = len(h["leaf"])
+    ws = B.new_workspace(B.train_workspace_size(b.desc, n))
+    table = b.table.clone().requires_grad_(True)
+    mlp = b.mlp.clone().requires_grad_(True)
+    raw = NBVHQueryFn.apply(table, mlp, b.desc, dv["rays"], dv["leaf"], dv["t0"], dv["t1"], ws)
+    R = torch.as_tensor(np.random.default_rng(52).normal(size=(n, 5)).astype(np.float32)).cuda()
+    valid = torch.as_tensor(h["valid"]).cuda()
+    (raw * R * valid[:, None]).sum().backward()
+    fr = b.oleaves["frame"]
+    p = O.sample_points(h["o"], h["d"], h["t0"], h["t1"], b.case.model.n_samples)
+    x = O.normalize_points(p, fr["model_centre"], fr["model_extent"])
+    feat = O.encode(x, b.table_host, b.olayout)
+    _, acts, pre = O.mlp_forward(feat, b.layers)
+    Rv = R.cpu().numpy().astype(np.float64) * h["valid"][:, None]
+    g_feat, g_layers = O.mlp_backward(Rv, acts, pre, b.layers)
+    g_tab = O.encode_backward(x, g_feat, b.table_host.shape[0], b.table_host.shape[1], b.olayout)
+    assert np.max(np.abs(table.grad.cpu().numpy() - g_tab)) <= 1e-5 * np.max(np.abs(g_tab))
+    ref_m = B.pack_mlp(g_layers)
+    assert np.max(np.abs(mlp.grad.cpu().numpy() - ref_m)) <= 1e-5 * np.max(np.abs(ref_m))
+
+
+def test_fd_gradient_check_fp64_reduction():
+    """Central differences of the GPU loss (per-segment FP32 terms, FP64
+    reduction) on a 256-ray batch against the GPU's analytic gradient."""
+    torch = _torch()
+    b = built()
+    dv, h = _batch(b, n=256, seed=61)
+    n = 256
+    ws = B.new_workspace(B.train_workspace_size(b.desc, n))
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+
+    def L_of(table, mlp):
+        B.forward_train(b.desc, table, mlp, dv["rays"], dv["leaf"], dv["t0"], dv["t1"], ws, labels=dv["lab"],
+                        n_valid=dv["n_valid"], loss_out=loss)
+        return float(loss.item())
+
+    L_of(b.table, b.mlp)
+    g_tab = torch.zeros((b.layout["total"], 2), dtype=torch.float32, device="cuda")
+    g_mlp = torch.zeros_like(b.mlp)
+    B.backward(b.desc, b.table, b.mlp, dv["rays"], dv["leaf"], dv["t0"], dv["t1"], ws, g_tab, g_mlp)
+    gt = g_tab.cpu().numpy().ravel()
+    gm = g_mlp.cpu().numpy()
+    checked = 0
+    for idx in np.argsort(-np.abs(gm))[:6]:
+        hstep = 1e-3
+        mp, mm = b.mlp.clone(), b.mlp.clone()
+        mp[idx] += hstep
+        mm[idx] -= hstep
+        fd = (L_of(b.table, mp) - L_of(b.table, mm)) / (2 * hstep)
+        assert abs(fd - gm[idx]) <= 3e-2 * abs(gm[idx]) + 1e-6, (idx, fd, gm[idx])
+        checked += 1
+    # Table: the largest-gradient entries one at a time (h = 1e-3; an entry
+    # next to a ReLU or L1 kink can still be off, so the median is held to 1%
+    # and every entry to 10%), then one unit-norm direction over every entry
+    # the batch touches (a +-1 direction over thousands of entries would be a
+    # large move that crosses kinks).
+    rel = []
+    for idx in np.argsort(-np.abs(gt))[:6]:
+        hstep = 1e-3
+        tp, tm = b.table.clone().view(-1), b.table.clone().view(-1)
+        tp[idx] += hstep
+        tm[idx] -= hstep
+        fd = (L_of(tp.view_as(b.table), b.mlp) - L_of(tm.view_as(b.table), b.mlp)) / (2 * hstep)
+        rel.append(abs(fd - gt[idx]) / abs(gt[idx]))
+        checked += 1
+    assert np.median(rel) <= 1e-2 and max(rel) <= 0.1, rel
+    rng = np.random.default_rng(62)
+    used = np.abs(gt) > 0
+    delta = np.where(used, rng.choice([-1.0, 1.0], size=gt.shape), 0.0) / math.sqrt(used.sum())
+    dv_ = torch.as_tensor(delta.astype(np.float32)).cuda().view_as(b.table)
+    hstep = 2e-3
+    fd = (L_of(b.table + hstep * dv_, b.mlp) - L_of(b.table - hstep * dv_, b.mlp)) / (2 * hstep)
+    an = float(np.dot(gt.astype(np.float64), delta))
+    assert abs(fd - an) <= 2e-2 * abs(an), (fd, an)
+    checked += 1
+    assert checked == 13
+
+
+# ---------------------------------------------------------------- Adam
+def test_adam_step_matches_oracle_and_skips_nonfinite():
+    torch = _torch()
+    b = built()
+    rng = np.random.default_rng(71)
+    master = torch.as_tensor(b.table_host.astype(np.float32)).cuda()
+    opt = B.Optimizer(b.desc, master.clone(), b.mlp.clone(), loss_scale=4.0)
+    gt = rng.normal(size=opt.grad_table.shape).astype(np.float32)
+    gm = rng.normal(size=opt.grad_mlp.shape).astype(np.float32)
+    opt.grad_table.copy_(torch.as_tensor(gt))
+    opt.grad_mlp.copy_(torch.as_tensor(gm))
+    p0t, p0m = opt.table_master.cpu().numpy(), opt.mlp.cpu().numpy()
+    opt.adam(1, lr=1e-2)
+    ref_t, _, _ = O.adam(p0t, gt / 4.0, np.zeros_like(p0t), np.zeros_like(p0t), 1, lr=1e-2)
+    ref_m, _, _ = O.adam(p0m, gm / 4.0, np.zeros_like(p0m), np.zeros_like(p0m), 1, lr=1e-2)
+    assert np.max(np.abs(opt.table_master.cpu().numpy() - ref_t)) <= 1e-6
+    assert np.max(np.abs(opt.mlp.cpu().numpy() - ref_m)) <= 1e-6
+    assert float(opt.grad_table.abs().max()) == 0.0 and float(opt.grad_mlp.abs().max()) == 0.0
+    # a non-finite gradient skips the step and halves a dynamic scale
+    before = opt.mlp.clone()
+    opt.grad_mlp[3] = float("inf")
+    opt.adam(2, lr=1e-2, dynamic_scale=True)
+    assert torch.equal(before, opt.mlp) and float(opt.loss_scale.item()) == 2.0
+    assert int(opt.counters[2].item()) == 0
+
+
+# ---------------------------------------------------------------- learning
+def _gt_hits(tris, rays):
+    """Closest hit of every ray against every triangle (oracle brute force)."""
+    o, d, tmin, tmax = O.rays_od(rays)
+    tv = tris.astype(np.float64)
+    best = np.full(len(o), np.inf)
+    for s in range(0, len(tv), 512):
+        T = tv[s:s + 512]
+        hit, t, _, _ = O.moller_trumbore(o[:, None], d[:, None], T[None, :, 0], T[None, :, 1], T[None, :, 2])
+        t = np.where(hit & (t >= tmin[:, None]) & (t <= tmax[:, None]), t, np.inf)
+        best = np.minimum(best, t.min(1))
+    return best
+
+
+def test_training_gains_over_untrained_and_box_proxy():
+    """Train on the 4,096-triangle scene and compare hit agreement and depth
+    error against brute-force ground truth: the trained network must beat the
+    untrained one and the box-only proxy (hit = any leaf box hit, t = its t0)."""
+    torch = _torch()
+    b = Built(make_case("random_tris_c0"))
+    scene = B.DeviceScene(b.case.tris, b.leaves)
+    desc = b.desc
+    opt = B.Optimizer(desc, b.table.clone(), b.mlp.clone())
+    batch = 1 << 14
+    ws = B.new_workspace(B.train_workspace_size(desc, batch))
+    rays = W.camera_rays(64, 64, seed=W.SEED_BASE + 77)
+    drays = B.to_device_rays(rays)
+    gt = _gt_hits(b.case.tris, rays)
+    gt_hit = np.isfinite(gt)
+
+    def evaluate(table, mlp):
+        h = B.query_rays(desc, table, mlp, b.nodes, b.leaves["n_nodes"], drays, 32)
+        hit = h["hit"].cpu().numpy().astype(bool)
+        t = h["t"].cpu().numpy()
+        both = hit & gt_hit
+        return np.mean(hit == gt_hit), (np.median(np.abs(t[both] - gt[both])) if both.any() else np.inf)
+
+    untrained = evaluate(b.table, b.mlp)
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for step in range(1, 401):
+        B.train_step(desc, opt, scene, B.TRAIN_PROBED_MIX, batch, 1234, step, 1e-2, ws, loss_out=loss)
+    assert B.device_status() == 0
+    trained = evaluate(opt.table, opt.mlp)
+    seg = O.ray_segments(rays, b.oleaves["leaf_lo"], b.oleaves["leaf_hi"])
+    first = np.full(len(gt), np.inf)
+    off = seg["offsets"]
+    for r in range(len(gt)):
+        if off[r + 1] > off[r]:
+            first[r] = seg["t0"][off[r]]
+    proxy_hit = np.isfinite(first)
+    both = proxy_hit & gt_hit
+    proxy = (np.mean(proxy_hit == gt_hit), np.median(np.abs(first[both] - gt[both])))
+    assert np.isfinite(float(loss.item()))
+    assert trained[0] > untrained[0] + 0.05 and trained[0] > proxy[0] + 0.02, (trained, untrained, proxy)
+    assert trained[1] < proxy[1], (trained, proxy)
