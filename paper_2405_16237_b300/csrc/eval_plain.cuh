@@ -9,6 +9,53 @@ namespace nbvh {
 constexpr int kPlainTM = 32;        // segments per tile
 constexpr int kPlainThreads = 256;
 
+// ---------------------------------------------------------------------------
+// S8 loss (Sec. 5.2 "Combined loss"): per valid segment
+//   2 BCE(sigmoid(o_hit), y) + y (2 |sigmoid(o_d) - d| + (1/3) sum |o_n - n|),
+// mean over valid segments; BCE from the logit. Returns the term and writes
+// dL/do (times `scale`, divided by the valid count) to g[0..4].
+// ---------------------------------------------------------------------------
+struct Labels {
+  const uint8_t* hit;
+  const float *depth, *nx, *ny, *nz;
+};
+
+__device__ __forceinline__ float sgnf(float x) { return x > 0.0f ? 1.0f : (x < 0.0f ? -1.0f : 0.0f); }
+
+__device__ __forceinline__ float loss_terms(const float* o, float y, float d, float n0, float n1, float n2,
+                                            float gscale, float* g) {
+  const float x = o[0];
+  const float bce = fmaxf(x, 0.0f) + log1pf(expf(-fabsf(x))) - y * x;
+  const float s0 = sigmoidf_(x);
+  const float s1 = sigmoidf_(o[1]);
+  const float dd = s1 - d;
+  const float e0 = o[2] - n0, e1 = o[3] - n1, e2 = o[4] - n2;
+  const float term = 2.0f * bce + y * (2.0f * fabsf(dd) + (fabsf(e0) + fabsf(e1) + fabsf(e2)) * (1.0f / 3.0f));
+  g[0] = gscale * 2.0f * (s0 - y);
+  g[1] = gscale * y * 2.0f * sgnf(dd) * s1 * (1.0f - s1);
+  g[2] = gscale * y * (1.0f / 3.0f) * sgnf(e0);
+  g[3] = gscale * y * (1.0f / 3.0f) * sgnf(e1);
+  g[4] = gscale * y * (1.0f / 3.0f) * sgnf(e2);
+  return term;
+}
+
+// Extra outputs of the tensor-core kernel's training forward (segment i =
+// ray i; leaf < 0 does not train): 16-bit copies of the features and hidden
+// activations it fed to the tensor cores, raw outputs, and with labels the
+// loss terms and dL/d(raw) times the loss scale.
+struct TcTrain {
+  const int32_t* leaf;
+  uint16_t* X16;      // [n][Kp]
+  uint16_t* H16;      // [n_hidden][n][W]
+  float* O;           // [n][n_out]
+  float* G;           // [n][n_out]
+  float* loss_seg;    // [n]
+  Labels lab;         // hit == nullptr: no loss
+  const int32_t* n_valid;
+  float loss_scale;
+  const float* loss_scale_dev;
+};
+
 // Everything a segment-evaluation kernel needs. Two modes:
 //  - list mode  (queue == nullptr): item i is segment (seg_ray[i], t0[i], t1[i]),
 //    raw outputs go to out[i * n_out + j];
@@ -39,6 +86,8 @@ struct EvalArgs {
   nbvh_hits hits;
   int32_t* next_queue;
   int32_t* next_qlen;
+  // training forward (tensor-core kernel, list of one segment per ray)
+  TcTrain tr;
 };
 
 // Activation layout in shared memory: [k][TM] with a per-row XOR swizzle of

@@ -271,7 +271,10 @@ __device__ __forceinline__ uint32_t pack2(float a, float b) {
   return *reinterpret_cast<uint32_t*>(&h);
 }
 
-template <typename T, int F, int W, bool WAVE, bool BF16>
+// MODE 0: list of segments -> raw outputs; 1: query wave -> resolve + next
+// queue; 2: training forward (one segment per ray) -> stored 16-bit operands,
+// raw outputs, loss and dL/d(raw).
+template <typename T, int F, int W, int MODE, bool BF16>
 __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
@@ -290,7 +293,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + lay.bar_off);
   uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + lay.bar_off + 8);
 
-  const int64_t n_items = WAVE ? int64_t(*a.qlen) : a.n_items;
+  const int64_t n_items = MODE == 1 ? int64_t(*a.qlen) : a.n_items;
   const int64_t n_tiles = (n_items + kTcM - 1) / kTcM;
   if (int64_t(blockIdx.x) >= n_tiles) return;
 
@@ -345,11 +348,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
       int ray = -1;
       float t0 = 0.0f, t1 = 0.0f;
       if (i < n_items) {
-        if (WAVE) {
+        if constexpr (MODE == 1) {
           ray = a.queue[i];
           const size_t q = size_t(a.wave) * size_t(a.n_rays) + size_t(ray);
           t0 = a.seg_t0[q];
           t1 = a.seg_t1[q];
+        } else if constexpr (MODE == 2) {
+          ray = a.tr.leaf[i] >= 0 ? int(i) : -1;
+          t0 = a.list_t0[i];
+          t1 = a.list_t1[i];
         } else {
           ray = a.seg_ray[i];
           t0 = a.list_t0[i];
@@ -361,6 +368,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
       st1[threadIdx.x] = t1;
     }
     __syncthreads();
+    const int64_t grow = tile * kTcM + row;  // global item of this thread's row
+    uint32_t* x16 = nullptr;                 // training: this row's stored features
+    if constexpr (MODE == 2) {
+      if (grow < n_items) x16 = reinterpret_cast<uint32_t*>(a.tr.X16 + grow * Kp);
+    }
 
     // ---- encode into TMEM: warp w owns rows 32 (w % 4) + lane and samples
     // w / 4, w / 4 + 8, ...; lanes = consecutive rows (consecutive queue items).
@@ -389,6 +401,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
           uint32_t pk[4];
 #pragma unroll
           for (int i = 0; i < 4; ++i) pk[i] = pack2<BF16>(v[2 * i], v[2 * i + 1]);
+          if (x16) *reinterpret_cast<uint4*>(x16 + col0 + (l0 * F) / 2) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
           __syncwarp();
           tmem_st4(t_a + col0 + uint32_t(l0 * F) / 2u, pk);
         }
@@ -404,6 +417,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
           uint32_t pk[F / 2];
 #pragma unroll
           for (int i = 0; i < F / 2; ++i) pk[i] = pack2<BF16>(v[2 * i], v[2 * i + 1]);
+          if (x16) {
+#pragma unroll
+            for (int i = 0; i < F / 2; ++i) x16[col0 + (l * F) / 2 + i] = pk[i];
+          }
           __syncwarp();
           tmem_st_cols<F / 2>(t_a + col0 + uint32_t(l * F) / 2u, pk);
         }
@@ -414,14 +431,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
             encode_level<T, F>(a.gp, table, l, x, y, z, v);
             encode_level<T, F>(a.gp, table, l + 1, x, y, z, v + 1);
           }
+          const uint32_t w = pack2<BF16>(v[0], v[1]);
+          if (x16) x16[col0 + l / 2] = w;
           __syncwarp();
-          tmem_st1(t_a + col0 + uint32_t(l) / 2u, pack2<BF16>(v[0], v[1]));
+          tmem_st1(t_a + col0 + uint32_t(l) / 2u, w);
         }
       }
     }
     if (Kp > K) {  // zero padding columns (K is even, so padding starts on a column)
       if (cgroup == 0) {
-        for (int c = K / 2; c < Kp / 2; ++c) tmem_st1(t_a + uint32_t(c), 0u);
+        for (int c = K / 2; c < Kp / 2; ++c) {
+          tmem_st1(t_a + uint32_t(c), 0u);
+          if (x16) x16[c] = 0u;
+        }
       }
     }
     tmem_st_wait();
@@ -458,6 +480,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
           pk[i] = pack2<BF16>(fmaxf(v[2 * i] + __ldg(bias + c0 + 2 * i), 0.0f),
                               fmaxf(v[2 * i + 1] + __ldg(bias + c0 + 2 * i + 1), 0.0f));
         tmem_st_cols<kCols / 2>(t_row + lay.col_h + uint32_t(c0 / 2), pk);
+        if constexpr (MODE == 2) {
+          if (grow < n_items) {
+            uint32_t* hdst = reinterpret_cast<uint32_t*>(a.tr.H16 + (size_t(h) * size_t(n_items) + size_t(grow)) * W + c0);
+#pragma unroll
+            for (int i = 0; i < kCols / 2; ++i) hdst[i] = pk[i];
+          }
+        }
         tmem_st_wait();
       }
       tc_fence_before();
@@ -489,8 +518,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
         float raw[8];
         for (int j = 0; j < 8; ++j) raw[j] = j < n_out ? v[j] + __ldg(bo + j) : 0.0f;
         const int ray = sray[row];
-        if (WAVE) {
+        if constexpr (MODE == 1) {
           wave_resolve(a, ray >= 0, ray, raw, st0[row], st1[row]);
+        } else if constexpr (MODE == 2) {
+          if (grow < n_items) {
+            float g[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            float term = 0.0f;
+            if (a.tr.lab.hit && ray >= 0) {
+              const float inv_valid = 1.0f / float(max(1, *a.tr.n_valid));
+              const float ls = a.tr.loss_scale_dev ? *a.tr.loss_scale_dev : a.tr.loss_scale;
+              term = loss_terms(raw, float(a.tr.lab.hit[grow]), a.tr.lab.depth[grow], a.tr.lab.nx[grow],
+                                a.tr.lab.ny[grow], a.tr.lab.nz[grow], ls * inv_valid, g);
+            }
+            for (int j = 0; j < n_out; ++j) a.tr.O[grow * n_out + j] = raw[j];
+            if (a.tr.lab.hit) {
+              for (int j = 0; j < n_out; ++j) a.tr.G[grow * n_out + j] = g[j];
+              a.tr.loss_seg[grow] = term;
+            }
+          }
         } else if (ray >= 0) {
           const int64_t i = tile * kTcM + row;
           for (int j = 0; j < n_out; ++j) a.out[i * n_out + j] = raw[j];
@@ -508,14 +553,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
   }
 }
 
-template <typename T, int F, int W, bool WAVE>
+template <typename T, int F, int W, int MODE>
 cudaError_t launch_tc_twf(const nbvh_model_desc* d, const EvalArgs& a, int64_t n_items_max, cudaStream_t s) {
   const TcLayout lay = tc_layout(a.gp.n_inputs, W, a.n_hidden);
   if (lay.total > 227 * 1024 || W < 32 || lay.ncols > 512 || (a.gp.n_inputs & 1) ||
       (F == 1 && (a.gp.n_levels & 1)))
     return cudaErrorInvalidConfiguration;
   const bool bf16 = d->mlp_prec == NBVH_BF16;
-  auto kern = bf16 ? eval_tc_kernel<T, F, W, WAVE, true> : eval_tc_kernel<T, F, W, WAVE, false>;
+  auto kern = bf16 ? eval_tc_kernel<T, F, W, MODE, true> : eval_tc_kernel<T, F, W, MODE, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(lay.total));
   if (e != cudaSuccess) return e;
   // One CTA per SM: every CTA holds its weights and TMEM columns for the whole launch.
@@ -531,33 +576,33 @@ cudaError_t launch_tc_twf(const nbvh_model_desc* d, const EvalArgs& a, int64_t n
   return cudaGetLastError();
 }
 
-template <typename T, int F, bool WAVE>
+template <typename T, int F, int MODE>
 cudaError_t launch_tc_tf(const nbvh_model_desc* d, const EvalArgs& a, int64_t n, cudaStream_t s) {
   switch (a.width) {
-    case 32: return launch_tc_twf<T, F, 32, WAVE>(d, a, n, s);
-    case 64: return launch_tc_twf<T, F, 64, WAVE>(d, a, n, s);
-    case 128: return launch_tc_twf<T, F, 128, WAVE>(d, a, n, s);
+    case 32: return launch_tc_twf<T, F, 32, MODE>(d, a, n, s);
+    case 64: return launch_tc_twf<T, F, 64, MODE>(d, a, n, s);
+    case 128: return launch_tc_twf<T, F, 128, MODE>(d, a, n, s);
   }
   return cudaErrorInvalidConfiguration;
 }
 
-template <typename T, bool WAVE>
+template <typename T, int MODE>
 cudaError_t launch_tc_t(const nbvh_model_desc* d, const EvalArgs& a, int64_t n, cudaStream_t s) {
   switch (d->n_features) {
-    case 1: return launch_tc_tf<T, 1, WAVE>(d, a, n, s);
-    case 2: return launch_tc_tf<T, 2, WAVE>(d, a, n, s);
-    case 4: return launch_tc_tf<T, 4, WAVE>(d, a, n, s);
-    case 8: return launch_tc_tf<T, 8, WAVE>(d, a, n, s);
+    case 1: return launch_tc_tf<T, 1, MODE>(d, a, n, s);
+    case 2: return launch_tc_tf<T, 2, MODE>(d, a, n, s);
+    case 4: return launch_tc_tf<T, 4, MODE>(d, a, n, s);
+    case 8: return launch_tc_tf<T, 8, MODE>(d, a, n, s);
   }
   return cudaErrorInvalidValue;
 }
 
-template <bool WAVE>
+template <int MODE>
 cudaError_t launch_tc(const nbvh_model_desc* d, const EvalArgs& a, int64_t n, cudaStream_t s) {
   switch (d->table_prec) {
-    case NBVH_FP32: return launch_tc_t<float, WAVE>(d, a, n, s);
-    case NBVH_FP16: return launch_tc_t<__half, WAVE>(d, a, n, s);
-    case NBVH_BF16: return launch_tc_t<__nv_bfloat16, WAVE>(d, a, n, s);
+    case NBVH_FP32: return launch_tc_t<float, MODE>(d, a, n, s);
+    case NBVH_FP16: return launch_tc_t<__half, MODE>(d, a, n, s);
+    case NBVH_BF16: return launch_tc_t<__nv_bfloat16, MODE>(d, a, n, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -13,6 +13,7 @@
 #include "eval_tc.cuh"
 #include "bounce.cuh"
 #include "train.cuh"
+#include "train_tc.cuh"
 
 namespace nbvh {
 
@@ -154,7 +155,7 @@ nbvh_status status_of(cudaError_t e) {
 
 cudaError_t launch_eval(const nbvh_model_desc* d, const EvalArgs& a, bool wave, int64_t n, cudaStream_t s) {
   if (d->mlp_prec == NBVH_FP32) return wave ? launch_plain<true>(d, a, n, s) : launch_plain<false>(d, a, n, s);
-  return wave ? launch_tc<true>(d, a, n, s) : launch_tc<false>(d, a, n, s);
+  return wave ? launch_tc<1>(d, a, n, s) : launch_tc<0>(d, a, n, s);
 }
 
 // ---------------------------------------------------------------- bookkeeping
@@ -479,6 +480,7 @@ struct TrainWs {
   uint8_t* hit;
   float *depth, *nx, *ny, *nz;
   TrainBuffers buf;
+  uint16_t *X16, *H16, *dZ16;  // tensor-core path: 16-bit operands
   size_t bytes;
 };
 
@@ -512,6 +514,10 @@ TrainWs carve_train(void* base, const nbvh_model_desc* d, int64_t n) {
   w.buf.G = reinterpret_cast<float*>(take(4 * N * no));
   w.buf.loss_seg = reinterpret_cast<float*>(take(4 * N));
   w.buf.dZ = reinterpret_cast<float*>(take(4 * nh * N * Wd));
+  const size_t Kp = (K + 15) & ~size_t(15);
+  w.X16 = reinterpret_cast<uint16_t*>(take(2 * N * Kp));
+  w.H16 = reinterpret_cast<uint16_t*>(take(2 * nh * N * Wd));
+  w.dZ16 = reinterpret_cast<uint16_t*>(take(2 * nh * N * Wd));
   w.bytes = off;
   return w;
 }
@@ -591,6 +597,76 @@ TrainArgs train_args(const nbvh_model_desc* d, const GridParams& gp, const void*
   a.buf = w.buf;
   a.loss_scale = 1.0f;
   return a;
+}
+
+template <int F, int W>
+cudaError_t launch_bwd_tc_fw(bool bf16, const TcBwdArgs& a, cudaStream_t s) {
+  const TcBwdLayout lay = tc_bwd_layout(a.gp.n_inputs, W, a.n_hidden);
+  if (lay.total > 227 * 1024 || lay.ncols > 512) return cudaErrorInvalidConfiguration;
+  auto kern = bf16 ? train_backward_tc<F, W, true> : train_backward_tc<F, W, false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(lay.total));
+  if (e != cudaSuccess) return e;
+  const int64_t tiles = (a.n + kTcM - 1) / kTcM;
+  int64_t grid = sm_count();
+  if (tiles < grid) grid = tiles;
+  if (grid < 1) return cudaSuccess;
+  kern<<<unsigned(grid), kTcThreads, lay.total, s>>>(a);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template <int F>
+cudaError_t launch_bwd_tc_f(bool bf16, int W, const TcBwdArgs& a, cudaStream_t s) {
+  switch (W) {
+    case 32: return launch_bwd_tc_fw<F, 32>(bf16, a, s);
+    case 64: return launch_bwd_tc_fw<F, 64>(bf16, a, s);
+    case 128: return launch_bwd_tc_fw<F, 128>(bf16, a, s);
+  }
+  return cudaErrorInvalidConfiguration;
+}
+
+cudaError_t launch_bwd_tc(const nbvh_model_desc* d, const TcBwdArgs& a, cudaStream_t s) {
+  const bool bf16 = d->mlp_prec == NBVH_BF16;
+  switch (d->n_features) {
+    case 1: return launch_bwd_tc_f<1>(bf16, d->width, a, s);
+    case 2: return launch_bwd_tc_f<2>(bf16, d->width, a, s);
+    case 4: return launch_bwd_tc_f<4>(bf16, d->width, a, s);
+    case 8: return launch_bwd_tc_f<8>(bf16, d->width, a, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename TZ, typename TA>
+cudaError_t launch_wg_any(const TZ* dZ, int ldz, int n_o, const TA* A, int lda, int n_j, int64_t n, float* dW,
+                          float* db, cudaStream_t s) {
+  dim3 grid(unsigned((n_o + kWgTile - 1) / kWgTile), unsigned((n_j + kWgTile - 1) / kWgTile),
+            unsigned((n + kWgChunk - 1) / kWgChunk));
+  weight_grad_any<TZ, TA><<<grid, 256, 0, s>>>(dZ, ldz, n_o, A, lda, n_j, n, dW, db);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// Weight gradients of the tensor-core path from its 16-bit stored operands.
+template <typename T16>
+cudaError_t weight_grads_16(const nbvh_model_desc* d, const TrainWs& w, const float* G, int64_t n, float* grad_mlp,
+                            cudaStream_t s) {
+  const int K = d->n_samples * d->n_levels * d->n_features, Kp = (K + 15) & ~15;
+  const int Wd = d->width, nh = d->n_hidden, no = d->n_out;
+  const T16* X = reinterpret_cast<const T16*>(w.X16);
+  const T16* H = reinterpret_cast<const T16*>(w.H16);
+  const T16* Z = reinterpret_cast<const T16*>(w.dZ16);
+  size_t off = 0;
+  cudaError_t e = launch_wg_any<T16, T16>(Z, Wd, Wd, X, Kp, K, n, grad_mlp, grad_mlp + size_t(Wd) * K, s);
+  off += size_t(Wd) * K + Wd;
+  for (int h = 1; h < nh && e == cudaSuccess; ++h) {
+    e = launch_wg_any<T16, T16>(Z + size_t(h) * n * Wd, Wd, Wd, H + size_t(h - 1) * n * Wd, Wd, Wd, n,
+                                grad_mlp + off, grad_mlp + off + size_t(Wd) * Wd, s);
+    off += size_t(Wd) * Wd + Wd;
+  }
+  if (e == cudaSuccess)
+    e = launch_wg_any<float, T16>(G, no, no, H + size_t(nh - 1) * n * Wd, Wd, Wd, n, grad_mlp + off,
+                                  grad_mlp + off + size_t(no) * Wd, s);
+  return e;
 }
 
 cudaError_t launch_weight_grad(const float* dZ, int n_o, const float* A, int n_j, int64_t n, float* dW, float* db,
@@ -673,16 +749,34 @@ extern "C" nbvh_status nbvh_forward_train(const nbvh_model_desc* desc, const voi
     return NBVH_ERR_INVALID_ARG;
   TrainWs w = carve_train(workspace, desc, rays.n);
   if (ws_bytes < w.bytes) return NBVH_ERR_WORKSPACE_TOO_SMALL;
-  if (desc->mlp_prec != NBVH_FP32) return NBVH_ERR_UNSUPPORTED;
   GridParams gp;
   if (!make_grid(desc, gp)) return NBVH_ERR_INVALID_ARG;
   cudaStream_t s = as_stream(stream);
-  TrainArgs a = train_args(desc, gp, table, mlp, rays, leaf, t0, t1, w);
-  a.lab = Labels{labels.hit, labels.depth, labels.nx, labels.ny, labels.nz};
-  a.n_valid = n_valid;
-  a.loss_scale = loss_scale;
-  a.loss_scale_dev = loss_scale_dev;
-  cudaError_t e = launch_train(false, desc, a, s);
+  cudaError_t e;
+  if (desc->mlp_prec == NBVH_FP32) {
+    TrainArgs a = train_args(desc, gp, table, mlp, rays, leaf, t0, t1, w);
+    a.lab = Labels{labels.hit, labels.depth, labels.nx, labels.ny, labels.nz};
+    a.n_valid = n_valid;
+    a.loss_scale = loss_scale;
+    a.loss_scale_dev = loss_scale_dev;
+    e = launch_train(false, desc, a, s);
+  } else {
+    EvalArgs a = base_args(desc, gp, table, mlp, rays);
+    a.list_t0 = t0;
+    a.list_t1 = t1;
+    a.n_items = rays.n;
+    a.tr.leaf = leaf;
+    a.tr.X16 = w.X16;
+    a.tr.H16 = w.H16;
+    a.tr.O = w.buf.O;
+    a.tr.G = w.buf.G;
+    a.tr.loss_seg = w.buf.loss_seg;
+    a.tr.lab = Labels{labels.hit, labels.depth, labels.nx, labels.ny, labels.nz};
+    a.tr.n_valid = n_valid;
+    a.tr.loss_scale = loss_scale;
+    a.tr.loss_scale_dev = loss_scale_dev;
+    e = launch_tc<2>(desc, a, rays.n, s);
+  }
   if (e != cudaSuccess) return status_of(e);
   if (raw_out) {
     e = cudaMemcpyAsync(raw_out, w.buf.O, sizeof(float) * size_t(rays.n) * desc->n_out, cudaMemcpyDeviceToDevice, s);
@@ -707,10 +801,31 @@ extern "C" nbvh_status nbvh_backward(const nbvh_model_desc* desc, const void* ta
     return NBVH_ERR_INVALID_ARG;
   TrainWs w = carve_train(workspace, desc, rays.n);
   if (ws_bytes < w.bytes) return NBVH_ERR_WORKSPACE_TOO_SMALL;
-  if (desc->mlp_prec != NBVH_FP32) return NBVH_ERR_UNSUPPORTED;
   GridParams gp;
   if (!make_grid(desc, gp)) return NBVH_ERR_INVALID_ARG;
   cudaStream_t s = as_stream(stream);
+  if (desc->mlp_prec != NBVH_FP32) {
+    TcBwdArgs b;
+    std::memset(&b, 0, sizeof(b));
+    b.gp = gp;
+    b.mlp = mlp;
+    b.n_hidden = desc->n_hidden;
+    b.n_out = desc->n_out;
+    b.rays = ray_ptrs(rays);
+    b.leaf = leaf;
+    b.t0 = t0;
+    b.t1 = t1;
+    b.n = rays.n;
+    b.G = grad_out ? grad_out : w.buf.G;
+    b.H16 = w.H16;
+    b.dZ16 = w.dZ16;
+    b.grad_table = grad_table;
+    cudaError_t e = launch_bwd_tc(desc, b, s);
+    if (e != cudaSuccess) return status_of(e);
+    e = desc->mlp_prec == NBVH_BF16 ? weight_grads_16<__nv_bfloat16>(desc, w, b.G, rays.n, grad_mlp, s)
+                                    : weight_grads_16<__half>(desc, w, b.G, rays.n, grad_mlp, s);
+    return status_of(e);
+  }
   TrainArgs a = train_args(desc, gp, table, mlp, rays, leaf, t0, t1, w);
   if (grad_out) a.buf.G = const_cast<float*>(grad_out);
   a.grad_table = grad_table;

@@ -223,36 +223,6 @@ __global__ void __launch_bounds__(128) labels_kernel(RayPtrs rays, const int32_t
   nz[i] = gz;
 }
 
-// ---------------------------------------------------------------------------
-// S8 loss (Sec. 5.2 "Combined loss"): per valid segment
-//   2 BCE(sigmoid(o_hit), y) + y (2 |sigmoid(o_d) - d| + (1/3) sum |o_n - n|),
-// mean over valid segments; BCE from the logit. Returns the term and writes
-// dL/do (times `scale`, divided by the valid count) to g[0..4].
-// ---------------------------------------------------------------------------
-struct Labels {
-  const uint8_t* hit;
-  const float *depth, *nx, *ny, *nz;
-};
-
-__device__ __forceinline__ float sgnf(float x) { return x > 0.0f ? 1.0f : (x < 0.0f ? -1.0f : 0.0f); }
-
-__device__ __forceinline__ float loss_terms(const float* o, float y, float d, float n0, float n1, float n2,
-                                            float gscale, float* g) {
-  const float x = o[0];
-  const float bce = fmaxf(x, 0.0f) + log1pf(expf(-fabsf(x))) - y * x;
-  const float s0 = sigmoidf_(x);
-  const float s1 = sigmoidf_(o[1]);
-  const float dd = s1 - d;
-  const float e0 = o[2] - n0, e1 = o[3] - n1, e2 = o[4] - n2;
-  const float term = 2.0f * bce + y * (2.0f * fabsf(dd) + (fabsf(e0) + fabsf(e1) + fabsf(e2)) * (1.0f / 3.0f));
-  g[0] = gscale * 2.0f * (s0 - y);
-  g[1] = gscale * y * 2.0f * sgnf(dd) * s1 * (1.0f - s1);
-  g[2] = gscale * y * (1.0f / 3.0f) * sgnf(e0);
-  g[3] = gscale * y * (1.0f / 3.0f) * sgnf(e1);
-  g[4] = gscale * y * (1.0f / 3.0f) * sgnf(e2);
-  return term;
-}
-
 // Stored forward of one training batch (row i = segment of ray i).
 struct TrainBuffers {
   float* X;         // [S][K] features

@@ -1,0 +1,327 @@
+// S8 backward on the tensor cores: the MLP adjoint as tcgen05 MMAs with the
+// gradients in TMEM, then the adjoint of the encoding (trilinear scatter-add
+// into the FP32 table gradient) straight from the dL/dfeatures accumulator.
+#pragma once
+#include "eval_tc.cuh"
+#include "train.cuh"
+
+namespace nbvh {
+
+struct TcBwdArgs {
+  GridParams gp;
+  const float* mlp;
+  int32_t n_hidden, n_out;
+  RayPtrs rays;
+  const int32_t* leaf;
+  const float* t0;
+  const float* t1;
+  int64_t n;
+  const float* G;         // [n][n_out] dL/d(raw), times the loss scale
+  const uint16_t* H16;    // [n_hidden][n][W] hidden activations of the forward
+  uint16_t* dZ16;         // [n_hidden][n][W] pre-activation gradients (out)
+  float* grad_table;      // FP32 [entries][F]
+};
+
+// TMEM columns: [0, W) accumulator of dH; [W, W + W/2) the current A operand
+// (dL/dout padded to 16, then dZ); [2W, 2W + 128) a 128-feature chunk of
+// dL/dfeatures. Shared memory: the transposed weights as B operands.
+struct TcBwdLayout {
+  int Kp;
+  uint32_t col_a, col_x, ncols;
+  uint32_t w0t_off, wht_off, wot_off, row_off, bar_off, total;
+};
+
+__host__ __device__ inline TcBwdLayout tc_bwd_layout(int K, int W, int n_hidden) {
+  TcBwdLayout L;
+  L.Kp = (K + 15) & ~15;
+  L.col_a = uint32_t(W);
+  L.col_x = uint32_t(2 * W);
+  uint32_t nc = 32;
+  while (nc < L.col_x + 128u) nc <<= 1;
+  L.ncols = nc;
+  uint32_t off = 0;
+  auto take = [&](uint32_t bytes) {
+    const uint32_t o = off;
+    off = (off + bytes + 127u) & ~127u;
+    return o;
+  };
+  L.w0t_off = take(uint32_t(L.Kp) * W * 2);
+  L.wht_off = take(uint32_t(n_hidden - 1) * W * W * 2);
+  L.wot_off = take(uint32_t(W) * 16 * 2);
+  L.row_off = take(kTcM * 12);
+  L.bar_off = take(64);
+  L.total = off + 128;
+  return L;
+}
+
+template <bool BF16>
+__device__ __forceinline__ float from16(uint16_t v) {
+  if constexpr (BF16) {
+    return __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(&v));
+  } else {
+    return __half2float(*reinterpret_cast<const __half*>(&v));
+  }
+}
+
+template <int F, int W, bool BF16>
+__global__ void __launch_bounds__(kTcThreads, 1) train_backward_tc(TcBwdArgs a) {
+  using OT = OpType<BF16>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  const int K = a.gp.n_inputs;
+  const int L = a.gp.n_levels;
+  const int nh = a.n_hidden;
+  const int n_out = a.n_out;
+  const TcBwdLayout lay = tc_bwd_layout(K, W, nh);
+  const int Kp = lay.Kp;
+  uint8_t* sW0t = smem + lay.w0t_off;
+  uint8_t* sWht = smem + lay.wht_off;
+  uint8_t* sWot = smem + lay.wot_off;
+  int* sray = reinterpret_cast<int*>(smem + lay.row_off);
+  float* st0 = reinterpret_cast<float*>(sray + kTcM);
+  float* st1 = st0 + kTcM;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + lay.bar_off);
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + lay.bar_off + 8);
+
+  const int64_t n_tiles = (a.n + kTcM - 1) / kTcM;
+  if (int64_t(blockIdx.x) >= n_tiles) return;
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp == 0) {
+    tmem_alloc(s_tmem, lay.ncols);
+    tmem_relinquish();
+  }
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  // B operands (K-major, rows = the MMA's N): W0^T [Kp][W], W_h^T [W][W], Wo^T [W][16]
+  const float* W0 = a.mlp;
+  for (int i = threadIdx.x; i < Kp * W; i += blockDim.x) {
+    const int r = i / W, k = i - r * W;
+    const float v = r < K ? __ldg(W0 + size_t(k) * K + r) : 0.0f;
+    *reinterpret_cast<typename OT::T*>(sW0t + op_offset(r, k, W)) = OT::one(v);
+  }
+  const float* p = W0 + size_t(W) * K + W;
+  for (int h = 1; h < nh; ++h) {
+    uint8_t* dst = sWht + size_t(h - 1) * W * W * 2;
+    for (int i = threadIdx.x; i < W * W; i += blockDim.x) {
+      const int r = i / W, k = i - r * W;
+      *reinterpret_cast<typename OT::T*>(dst + op_offset(r, k, W)) = OT::one(__ldg(p + size_t(k) * W + r));
+    }
+    p += W * W + W;
+  }
+  for (int i = threadIdx.x; i < W * 16; i += blockDim.x) {
+    const int r = i / 16, k = i - r * 16;
+    const float v = k < n_out ? __ldg(p + size_t(k) * W + r) : 0.0f;
+    *reinterpret_cast<typename OT::T*>(sWot + op_offset(r, k, 16)) = OT::one(v);
+  }
+  fence_proxy_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *s_tmem;
+
+  const int quarter = warp & 3;
+  const int cgroup = warp >> 2;
+  constexpr int kGroups = kTcThreads / 128;
+  constexpr int kCols = W / kGroups;
+  const int row = quarter * 32 + lane;
+  const uint32_t t_row = tmem + (uint32_t(quarter * 32) << 16);
+  uint32_t phase = 0;
+  bool failed = false;
+
+  for (int64_t tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
+    if (threadIdx.x < kTcM) {
+      const int64_t i = tile * kTcM + threadIdx.x;
+      const bool v = i < a.n && a.leaf[i] >= 0;
+      sray[threadIdx.x] = v ? int(i) : -1;
+      st0[threadIdx.x] = v ? a.t0[i] : 0.0f;
+      st1[threadIdx.x] = v ? a.t1[i] : 0.0f;
+    }
+    __syncthreads();
+    const int64_t grow = tile * kTcM + row;
+    // dL/d(raw) as the first A operand (16 columns, zero padded)
+    if (cgroup == 0) {
+      float g[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) g[j] = 0.0f;
+      if (grow < a.n)
+        for (int j = 0; j < n_out; ++j) g[j] = a.G[grow * n_out + j];
+      uint32_t pk[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) pk[j] = pack2<BF16>(g[2 * j], g[2 * j + 1]);
+      tmem_st8(t_row + lay.col_a, pk);
+    }
+    tmem_st_wait();
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      tc_fence_after();
+      mma_f16_ts(tmem, tmem + lay.col_a, smem_desc(smem_u32(sWot), 128, 16 * 16), idesc_f16(BF16, kTcM, W), 0u);
+      mma_commit(bar);
+    }
+    for (int h = nh - 1; h >= 0; --h) {
+      const bool ok = mbar_wait(bar, phase);
+      phase ^= 1u;
+      if (__syncthreads_or(!ok)) {
+        failed = true;
+        break;
+      }
+      tc_fence_after();
+      {
+        float v[kCols];
+        tmem_ld_cols<kCols>(t_row + uint32_t(cgroup * kCols), v);
+        tmem_ld_wait();
+        const int c0 = cgroup * kCols;
+        uint32_t pk[kCols / 2];
+        if (grow < a.n) {
+          const uint16_t* hrow = a.H16 + (size_t(h) * size_t(a.n) + size_t(grow)) * W + c0;
+#pragma unroll
+          for (int i = 0; i < kCols; ++i) v[i] = from16<BF16>(hrow[i]) > 0.0f ? v[i] : 0.0f;
+        } else {
+#pragma unroll
+          for (int i = 0; i < kCols; ++i) v[i] = 0.0f;
+        }
+#pragma unroll
+        for (int i = 0; i < kCols / 2; ++i) pk[i] = pack2<BF16>(v[2 * i], v[2 * i + 1]);
+        tmem_st_cols<kCols / 2>(t_row + lay.col_a + uint32_t(c0 / 2), pk);
+        if (grow < a.n) {
+          uint32_t* zdst = reinterpret_cast<uint32_t*>(a.dZ16 + (size_t(h) * size_t(a.n) + size_t(grow)) * W + c0);
+#pragma unroll
+          for (int i = 0; i < kCols / 2; ++i) zdst[i] = pk[i];
+        }
+        tmem_st_wait();
+      }
+      tc_fence_before();
+      __syncthreads();
+      if (h > 0) {
+        if (threadIdx.x == 0) {
+          tc_fence_after();
+          const uint32_t wb = smem_u32(sWht + size_t(h - 1) * W * W * 2);
+          for (int j = 0; j < W / 16; ++j)
+            mma_f16_ts(tmem, tmem + lay.col_a + uint32_t(8 * j), smem_desc(wb + j * 256, 128, uint32_t(W) * 16),
+                       idesc_f16(BF16, kTcM, W), j > 0);
+          mma_commit(bar);
+        }
+        continue;
+      }
+      // dL/dfeatures = dZ0 W0, 128 features at a time, scattered into the table gradient
+      for (int c0 = 0; c0 < Kp && !failed; c0 += 128) {
+        const int cw = min(128, Kp - c0);
+        if (threadIdx.x == 0) {
+          tc_fence_after();
+          const uint32_t wb = smem_u32(sW0t) + uint32_t(c0 / 8) * uint32_t(W) * 16;
+          for (int j = 0; j < W / 16; ++j)
+            mma_f16_ts(tmem + lay.col_x, tmem + lay.col_a + uint32_t(8 * j),
+                       smem_desc(wb + j * 256, 128, uint32_t(W) * 16), idesc_f16(BF16, kTcM, cw), j > 0);
+          mma_commit(bar);
+        }
+        const bool ok2 = mbar_wait(bar, phase);
+        phase ^= 1u;
+        if (__syncthreads_or(!ok2)) {
+          failed = true;
+          break;
+        }
+        tc_fence_after();
+        if (cgroup * 16 < cw) {
+          float gx[16];
+          tmem_ld16(t_row + lay.col_x + uint32_t(cgroup * 16), gx);
+          tmem_ld_wait();
+          const int ray = sray[row];
+          if (ray >= 0) {
+            int kprev = -1;
+            float x = 0.0f, y = 0.0f, z = 0.0f;
+            for (int j = 0; j < 16; j += F) {
+              const int f = c0 + cgroup * 16 + j;
+              if (f >= K) break;
+              const int k = f / (L * F);
+              const int l = (f / F) % L;
+              if (k != kprev) {
+                sample_point(a.gp, a.rays.ox[ray], a.rays.oy[ray], a.rays.oz[ray], a.rays.dx[ray],
+                             a.rays.dy[ray], a.rays.dz[ray], st0[row], st1[row], k, x, y, z);
+                kprev = k;
+              }
+              Corners cr;
+              level_corners(a.gp, l, x, y, z, cr);
+              float* gt = a.grad_table + a.gp.offset[l] * F;
+#pragma unroll
+              for (int q = 0; q < 8; ++q) {
+                float* dst = gt + size_t(cr.idx[q]) * F;
+                if constexpr (F == 2) {
+                  atomicAdd(reinterpret_cast<float2*>(dst), make_float2(cr.w[q] * gx[j], cr.w[q] * gx[j + 1]));
+                } else if constexpr (F % 4 == 0) {
+#pragma unroll
+                  for (int ff = 0; ff < F; ff += 4)
+                    atomicAdd(reinterpret_cast<float4*>(dst + ff),
+                              make_float4(cr.w[q] * gx[j + ff], cr.w[q] * gx[j + ff + 1], cr.w[q] * gx[j + ff + 2],
+                                          cr.w[q] * gx[j + ff + 3]));
+                } else {
+                  atomicAdd(dst, cr.w[q] * gx[j]);
+                }
+              }
+            }
+          }
+        }
+        tc_fence_before();
+        __syncthreads();
+      }
+    }
+  }
+  if (failed) set_status(NBVH_ERR_TIMEOUT);
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, lay.ncols);
+  }
+}
+
+// Weight gradients from stored operands of either precision (FP32 G, 16-bit
+// activations and pre-activation gradients): dW[o][j] += sum_i dZ[i][o] A[i][j],
+// db[o] += sum_i dZ[i][o], FP32 accumulation, split-K over segment chunks.
+template <typename TZ, typename TA>
+__device__ __forceinline__ float ldv(const TZ* p) {
+  if constexpr (std::is_same<TZ, float>::value) return *p;
+  else if constexpr (std::is_same<TZ, __half>::value) return __half2float(*p);
+  else return __bfloat162float(*p);
+}
+
+template <typename TZ, typename TA>
+__global__ void __launch_bounds__(256) weight_grad_any(const TZ* __restrict__ dZ, int ldz, int n_o,
+                                                       const TA* __restrict__ A, int lda, int n_j, int64_t n,
+                                                       float* __restrict__ dW, float* __restrict__ db) {
+  __shared__ float sz[32][kWgTile + 1];
+  __shared__ float sa[32][kWgTile + 1];
+  const int o0 = blockIdx.x * kWgTile;
+  const int j0 = blockIdx.y * kWgTile;
+  const int64_t i0 = int64_t(blockIdx.z) * kWgChunk;
+  const int64_t i1 = min(n, i0 + kWgChunk);
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  float acc[4] = {0, 0, 0, 0};
+  float bacc = 0.0f;
+  for (int64_t ib = i0; ib < i1; ib += 32) {
+    for (int idx = threadIdx.x; idx < 32 * kWgTile; idx += blockDim.x) {
+      const int r = idx / kWgTile, c = idx - r * kWgTile;
+      const int64_t i = ib + r;
+      sz[r][c] = (i < i1 && o0 + c < n_o) ? ldv<TZ, TZ>(dZ + i * ldz + o0 + c) : 0.0f;
+      sa[r][c] = (i < i1 && j0 + c < n_j) ? ldv<TA, TA>(A + i * lda + j0 + c) : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int r = 0; r < 32; ++r) {
+      const float av = sa[r][tx];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] = fmaf(sz[r][ty * 4 + q], av, acc[q]);
+      if (blockIdx.y == 0 && ty == 0) bacc += sz[r][tx];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int o = o0 + ty * 4 + q, j = j0 + tx;
+    if (o < n_o && j < n_j) atomicAdd(dW + size_t(o) * n_j + j, acc[q]);
+  }
+  if (blockIdx.y == 0 && ty == 0 && o0 + tx < n_o) atomicAdd(db + o0 + tx, bacc);
+}
+
+}  // namespace nbvh

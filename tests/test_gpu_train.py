@@ -305,3 +305,67 @@ def test_training_gains_over_untrained_and_box_proxy():
     assert np.isfinite(float(loss.item()))
     assert trained[0] > untrained[0] + 0.05 and trained[0] > proxy[0] + 0.02, (trained, untrained, proxy)
     assert trained[1] < proxy[1], (trained, proxy)
+
+
+# ---------------------------------------------------------------- tensor-core training path
+@pytest.mark.parametrize("mp", [B.FP16, B.BF16])
+def test_tensor_core_gradients_match_oracle(mp):
+    """FP16/BF16 operands with FP32 accumulation and a static loss scale of
+    1024: gradients (divided by the scale) against the oracle's exact ones.
+    16-bit rounding of features, weights, activations and dZ bounds the
+    agreement: relative L2 error <= 2e-2 for FP16; BF16's unit roundoff
+    (2^-8) is 8x FP16's (2^-11), its bound is 1e-1; cosine >= 0.999 (FP16) /
+    0.995 (BF16)."""
+    torch = _torch()
+    b = built()
+    desc = b.with_prec(mp)
+    dv, h = _batch(b, n=2000, seed=81)
+    n = len(h["leaf"])
+    ws = B.new_workspace(B.train_workspace_size(desc, n))
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    scale = 1024.0
+    raw = B.forward_train(desc, b.table, b.mlp, dv["rays"], dv["leaf"], dv["t0"], dv["t1"], ws,
+                          labels=dv["lab"], n_valid=dv["n_valid"], loss_scale=scale, loss_out=loss)
+    g_tab = torch.zeros((b.layout["total"], 2), dtype=torch.float32, device="cuda")
+    g_mlp = torch.zeros_like(b.mlp)
+    B.backward(desc, b.table, b.mlp, dv["rays"], dv["leaf"], dv["t0"], dv["t1"], ws, g_tab, g_mlp)
+    assert B.device_status() == 0
+    L, ref_tab, ref_layers, ref_raw = _oracle_fb(b, h)
+    v = h["valid"]
+    assert abs(float(loss.item()) - L) <= 2e-2 * abs(L)
+    tol_rel, tol_cos = (2e-2, 0.999) if mp == B.FP16 else (1e-1, 0.995)
+    for got, ref in ((g_tab.cpu().numpy().ravel() / scale, ref_tab.ravel()),
+                     (g_mlp.cpu().numpy() / scale, B.pack_mlp(ref_layers).astype(np.float64))):
+        rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        cos = float(np.dot(got, ref) / (np.linalg.norm(got) * np.linalg.norm(ref)))
+        assert rel <= tol_rel and cos >= tol_cos, (rel, cos)
+    r = raw.cpu().numpy()[v]
+    assert np.mean((r[:, 0] > 0) == (ref_raw[v][:, 0] > 0)) >= 0.99
+
+
+def test_tensor_core_training_learns():
+    """The whole FP16 training step (dynamic loss scaling) on the 4,096-triangle
+    scene: the trained FP16 network beats the untrained network."""
+    torch = _torch()
+    b = Built(make_case("random_tris_c0"))
+    scene = B.DeviceScene(b.case.tris, b.leaves)
+    desc = b.with_prec(B.FP16)
+    opt = B.Optimizer(desc, b.table.clone(), b.mlp.clone(), loss_scale=32768.0)
+    batch = 1 << 14
+    ws = B.new_workspace(B.train_workspace_size(desc, batch))
+    rays = W.camera_rays(64, 64, seed=W.SEED_BASE + 77)
+    drays = B.to_device_rays(rays)
+    gt = _gt_hits(b.case.tris, rays)
+    gt_hit = np.isfinite(gt)
+
+    def agreement():
+        hh = B.query_rays(desc, opt.table, opt.mlp, b.nodes, b.leaves["n_nodes"], drays, 32)
+        return np.mean(hh["hit"].cpu().numpy().astype(bool) == gt_hit)
+
+    before = agreement()
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for step in range(1, 401):
+        B.train_step(desc, opt, scene, B.TRAIN_PROBED_MIX, batch, 99, step, 1e-2, ws, loss_out=loss)
+    assert B.device_status() == 0
+    after = agreement()
+    assert np.isfinite(float(loss.item())) and after > before + 0.05, (before, after)
