@@ -46,6 +46,7 @@ def parse():
     p.add_argument("--cpu-rays", type=int, default=24576, help="oracle sample size (primary rays)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--max-segs", type=int, default=48)
+    p.add_argument("--train-steps", type=int, default=20, help="timed training steps (2^18 rays each)")
     p.add_argument("--quick", action="store_true",
                    help="time the FP16 tensor-core form only (no other forms, no e2e, no CPU baseline)")
     return p.parse_args()
@@ -72,6 +73,17 @@ def dist_max(x: float, world: int) -> float:
     t = torch.tensor([x], dtype=torch.float64, device="cuda")
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def dist_max_rate(rate: float, world: int) -> float:
+    """Whole-job rate of per-rank rates: world x the slowest rank's rate."""
+    if world == 1:
+        return rate
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([-rate], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return world * float(-t.item())
 
 
 def barrier(world: int):
@@ -140,6 +152,69 @@ class GpuWorkload:
 
     def flush(self):
         self.flush_buf.fill_(1)
+
+
+def time_training(spec, tris, wl, steps, warmup, batch=1 << 18):
+    """Training steps (2^18 rays each) on the same scene and model, FP16
+    tensor-core compute on FP32 masters, Adam lr 1e-2, dynamic loss scale."""
+    import torch
+    from paper_2405_16237_b300 import nbvh as B
+    scene = B.DeviceScene(tris, wl.leaves)
+    desc = B.with_mlp_prec(wl.desc, B.FP16)
+    opt = B.Optimizer(desc, torch.as_tensor(wl.table_np.astype(np.float32)).cuda(), wl.mlp.clone(),
+                      loss_scale=32768.0)
+    ws = B.new_workspace(B.train_workspace_size(desc, batch))
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    step = 0
+    for _ in range(warmup):
+        step += 1
+        B.train_step(desc, opt, scene, B.TRAIN_PROBED_MIX, batch, SEED + 9, step, 1e-2, ws, loss_out=loss)
+    torch.cuda.synchronize()
+    first = float(loss.item())
+    total = 0.0
+    for _ in range(steps):
+        step += 1
+        wl.flush()
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record()
+        B.train_step(desc, opt, scene, B.TRAIN_PROBED_MIX, batch, SEED + 9, step, 1e-2, ws, loss_out=loss)
+        e.record()
+        e.synchronize()
+        total += s.elapsed_time(e)
+    if B.device_status() != 0:
+        raise RuntimeError("device status after training steps")
+    ms = total / steps
+    return {"value": batch / (ms * 1e-3), "unit": "rays/s", "batch": batch, "ms_per_step": ms, "steps": steps,
+            "dtype": "f16 compute, f32 masters", "loss_after_warmup": first, "loss_last": float(loss.item()),
+            "loss_scale": float(opt.loss_scale.item())}
+
+
+def oracle_train_sample(spec, tris, n=256):
+    """One FP64 oracle training step (rays, labels, loss, gradient, Adam) on n
+    rays of the same scene and model. Returns rays/s and seconds."""
+    import contextlib
+    from oracle import nbvh_oracle as O
+    from paper_2405_16237_b300 import workloads as W
+    cfg = spec.model
+    leaves = O.build_leaves(tris, spec.n_leaves, spec.inflate_rel)
+    lay = O.level_layout(cfg.n_levels, cfg.base_res, cfg.growth, cfg.log2_table)
+    tab = W.init_table(lay["total"], cfg.n_features, SEED + 21, 1e-4).astype(np.float64)
+    layers = W.init_mlp(cfg.mlp_dims(), SEED + 22)
+    fr = leaves["frame"]
+    t0 = time.perf_counter()
+    R = O.train_rays(O.TRAIN_MODE_PROBED_MIX, SEED + 9, 0, n, leaves)
+    valid = R["leaf"] >= 0
+    lab = O.labels(R["o"], R["d"], R["leaf"], R["t0"], R["t1"], tris, leaves["tri_perm"], leaves["leaf_range"])
+    L, g_tab, g_layers, _ = O.forward_backward(R["o"], R["d"], R["t0"], R["t1"], valid, lab["hit"], lab["depth"],
+                                               lab["normal"], tab, layers, lay, fr["model_centre"],
+                                               fr["model_extent"], cfg.n_samples)
+    O.adam(tab, g_tab, np.zeros_like(tab), np.zeros_like(tab), 1)
+    for (w_, b_), (gw, gb) in zip(layers, g_layers):
+        O.adam(w_, gw, np.zeros_like(gw), np.zeros_like(gw), 1)
+        O.adam(b_, gb, np.zeros_like(gb), np.zeros_like(gb), 1)
+    dt = time.perf_counter() - t0
+    return n / dt, dt
 
 
 def time_steps(wl, desc, steps, warmup, e2e=False):
@@ -369,6 +444,11 @@ def main():
     wl.step(d16)
     torch.cuda.synchronize()
 
+    # training throughput (train rays/s)
+    train = time_training(spec, tris, wl, args.train_steps, 3) if args.train_steps > 0 else None
+    if train is not None:
+        train["value"] = dist_max_rate(train["value"], world)
+
     # end to end through the public API with host buffers
     e2e_ms = dist_max(time_steps(wl, d16, args.steps, args.warmup, e2e=True), world) / args.steps
     h2d = sum(v.numel() * v.element_size() for v in wl.rays_host.values())
@@ -396,6 +476,7 @@ def main():
                        "bounce_rays": rays_step - wl.n, "segments_per_step": seg_step,
                        "waves": [waves1, waves2], "l2": "flushed (256 MB write) between timed steps",
                        "parallelism": f"replicas x{world}"},
+            "train": train,
             "fp32_plain": {"value": world * rays_step / (ms32 * 1e-3) / 1e6, "ms_per_step": ms32},
             "bf16_tc": {"value": world * rays_step / (msbf * 1e-3) / 1e6, "ms_per_step": msbf},
             "roofline": roof,
@@ -415,6 +496,9 @@ def main():
             torch.cuda.synchronize()
             acc[nm] = accuracy(wl, idx, res)
         line["accuracy_vs_oracle"] = acc
+        tv, tdt = oracle_train_sample(spec, tris)
+        line["cpu_baseline_train"] = {"value": tv, "unit": "rays/s", "cores": 1, "kind": "oracle",
+                                      "sample": f"one FP64 oracle training step on 256 rays, {tdt:.1f} s"}
     elif rank == 0 and world == 1:
         line["cpu_baseline"] = None
     if rank == 0:
