@@ -371,6 +371,23 @@ nbvh_status nbvh_query_rays_static(const nbvh_model_desc* desc, const void* tabl
                                    const nbvh_node* nodes, int32_t n_nodes, nbvh_rays rays, int32_t max_segs,
                                    nbvh_hits out, void* stream);
 
+/* ------------------------------------------------------------------------
+ * CUDA graphs: record a sequence of this library's calls (for example a
+ * whole query step: query, bounce rays, query) once and replay it with one
+ * launch. Capture needs a created stream (not the legacy default stream);
+ * between nbvh_graph_begin and nbvh_graph_end only enqueueing calls may be
+ * made (no nbvh_get_device_status, nbvh_query_stats or host allocations), and
+ * stage timing is not recorded. The graph replays the recorded pointers and
+ * sizes: rerecord when they change. Empty query waves stay in the graph and
+ * exit after reading their queue length.
+ * ------------------------------------------------------------------------ */
+typedef struct nbvh_graph_s* nbvh_graph;
+
+nbvh_status nbvh_graph_begin(void* stream);
+nbvh_status nbvh_graph_end(void* stream, nbvh_graph* out);
+nbvh_status nbvh_graph_launch(nbvh_graph graph, void* stream);
+nbvh_status nbvh_graph_destroy(nbvh_graph graph);
+
 /* Device. Reads and clears the device status word (synchronises the stream). */
 nbvh_status nbvh_get_device_status(void* stream);
 

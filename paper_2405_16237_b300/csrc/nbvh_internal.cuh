@@ -380,25 +380,54 @@ __device__ __forceinline__ float slab_t(float b, float o, float d) {
   return __fadd_rn(q, __fdiv_rn(__fadd_rn(r, a.lo), d));
 }
 
+// The same value from the ray's reciprocal inv = RN(1/d): q = (b - o) inv, then
+// one correction with the FMA remainder (b - o) - q d, which brings q to the
+// rounded quotient (the traversal computes inv once per ray instead of two
+// divisions per slab).
+__device__ __forceinline__ float slab_t_rcp(float b, float o, float d, float inv) {
+  if (!isfinite(inv)) return slab_t(b, o, d);  // |d| below ~2^-126: divide
+  const FF a = two_sum(b, -o);
+  const float q = __fmul_rn(a.hi, inv);
+  if (!isfinite(q)) return q;
+  const float r = __fadd_rn(fmaf(-q, d, a.hi), a.lo);
+  return fmaf(r, inv, q);
+}
+
 // ---------------------------------------------------------------------------
 // S1: slab test of a ray against a box, FP32 with correctly rounded slabs.
 // A zero direction component keeps the slab unbounded when the origin lies in
 // [lo, hi] and empties it otherwise. Segment = [max(entry, tmin),
 // min(exit, tmax)], non-empty iff t0 <= t1.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ bool clip_box(float ox, float oy, float oz, float dx, float dy, float dz,
-                                         float tmin, float tmax, float lx, float ly, float lz,
-                                         float hx, float hy, float hz, float& t0, float& t1) {
-  float en = tmin, ex = tmax;
+// Ray with per-axis reciprocals for repeated box tests.
+struct RayR {
+  float o[3], d[3], inv[3], tmin, tmax;
+};
+
+__device__ __forceinline__ RayR make_rayr(float ox, float oy, float oz, float dx, float dy, float dz, float tmin,
+                                          float tmax) {
+  RayR r;
+  r.o[0] = ox; r.o[1] = oy; r.o[2] = oz;
+  r.d[0] = dx; r.d[1] = dy; r.d[2] = dz;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) r.inv[i] = __fdiv_rn(1.0f, r.d[i]);
+  r.tmin = tmin;
+  r.tmax = tmax;
+  return r;
+}
+
+__device__ __forceinline__ bool clip_box(const RayR& r, float lx, float ly, float lz, float hx, float hy,
+                                         float hz, float& t0, float& t1) {
+  float en = r.tmin, ex = r.tmax;
   bool empty = false;
-  const float o[3] = {ox, oy, oz}, d[3] = {dx, dy, dz}, lo[3] = {lx, ly, lz}, hi[3] = {hx, hy, hz};
+  const float lo[3] = {lx, ly, lz}, hi[3] = {hx, hy, hz};
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    if (d[i] == 0.0f) {
-      empty |= (o[i] < lo[i]) | (o[i] > hi[i]);
+    if (r.d[i] == 0.0f) {
+      empty |= (r.o[i] < lo[i]) | (r.o[i] > hi[i]);
     } else {
-      const float a = slab_t(lo[i], o[i], d[i]);
-      const float b = slab_t(hi[i], o[i], d[i]);
+      const float a = slab_t_rcp(lo[i], r.o[i], r.d[i], r.inv[i]);
+      const float b = slab_t_rcp(hi[i], r.o[i], r.d[i], r.inv[i]);
       en = fmaxf(en, fminf(a, b));
       ex = fminf(ex, fmaxf(a, b));
     }
@@ -406,6 +435,12 @@ __device__ __forceinline__ bool clip_box(float ox, float oy, float oz, float dx,
   t0 = en;
   t1 = ex;
   return !empty && en <= ex;
+}
+
+__device__ __forceinline__ bool clip_box(float ox, float oy, float oz, float dx, float dy, float dz,
+                                         float tmin, float tmax, float lx, float ly, float lz,
+                                         float hx, float hy, float hz, float& t0, float& t1) {
+  return clip_box(make_rayr(ox, oy, oz, dx, dy, dz, tmin, tmax), lx, ly, lz, hx, hy, hz, t0, t1);
 }
 
 __device__ __forceinline__ float sigmoidf_(float x) { return 1.0f / (1.0f + expf(-x)); }

@@ -307,9 +307,11 @@ extern "C" nbvh_status nbvh_query_rays(const nbvh_model_desc* desc, const void* 
   to.qlen0 = w.counters;
   to.hits = out;
   StageEvents ev{nullptr, nullptr, nullptr};
+  cudaStreamCaptureStatus capturing = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &capturing) != cudaSuccess) return NBVH_ERR_CUDA;
   {
     std::lock_guard<std::mutex> lk(g_timing_mu);
-    if (g_timing) {
+    if (g_timing && capturing == cudaStreamCaptureStatusNone) {
       ev.e0 = take_event();
       ev.e1 = take_event();
       ev.e2 = take_event();
@@ -917,4 +919,43 @@ extern "C" nbvh_status nbvh_train_step(const nbvh_model_desc* desc, const nbvh_o
                      workspace, ws_bytes, stream);
   if (st != NBVH_OK) return st;
   return nbvh_adam(desc, opt, step, lr, 0.9f, 0.999f, 1e-8f, desc->mlp_prec != NBVH_FP32 ? 1 : 0, stream);
+}
+
+// ---------------------------------------------------------------- graphs
+struct nbvh_graph_s {
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+};
+
+extern "C" nbvh_status nbvh_graph_begin(void* stream) {
+  cudaStream_t s = as_stream(stream);
+  if (!s) return NBVH_ERR_INVALID_ARG;
+  return cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess ? NBVH_OK : NBVH_ERR_CUDA;
+}
+
+extern "C" nbvh_status nbvh_graph_end(void* stream, nbvh_graph* out) {
+  cudaStream_t s = as_stream(stream);
+  if (!s || !out) return NBVH_ERR_INVALID_ARG;
+  cudaGraph_t g = nullptr;
+  if (cudaStreamEndCapture(s, &g) != cudaSuccess || !g) return NBVH_ERR_CUDA;
+  cudaGraphExec_t e = nullptr;
+  if (cudaGraphInstantiate(&e, g, 0) != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return NBVH_ERR_CUDA;
+  }
+  *out = new nbvh_graph_s{g, e};
+  return NBVH_OK;
+}
+
+extern "C" nbvh_status nbvh_graph_launch(nbvh_graph graph, void* stream) {
+  if (!graph) return NBVH_ERR_INVALID_ARG;
+  return cudaGraphLaunch(graph->exec, as_stream(stream)) == cudaSuccess ? NBVH_OK : NBVH_ERR_CUDA;
+}
+
+extern "C" nbvh_status nbvh_graph_destroy(nbvh_graph graph) {
+  if (!graph) return NBVH_ERR_INVALID_ARG;
+  cudaGraphExecDestroy(graph->exec);
+  cudaGraphDestroy(graph->graph);
+  delete graph;
+  return NBVH_OK;
 }

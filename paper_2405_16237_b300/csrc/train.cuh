@@ -55,13 +55,14 @@ __device__ __forceinline__ int first_leaf_dev(const nbvh_node* __restrict__ node
   bt1 = 0.0f;
   int stack[kTraverseStack];
   int sp = 0, cur = 0;
+  const RayR ray = make_rayr(ox, oy, oz, dx, dy, dz, tmin, tmax);
   for (int guard = 0; guard < (1 << 26); ++guard) {
     const float4* np = reinterpret_cast<const float4*>(nodes + cur);
     const float4 a = __ldg(np), b = __ldg(np + 1), c = __ldg(np + 2);
     const int4 e = __ldg(reinterpret_cast<const int4*>(np + 3));
     float a0, a1, b0, b1;
-    bool h0 = clip_box(ox, oy, oz, dx, dy, dz, tmin, tmax, a.x, a.y, a.z, a.w, b.x, b.y, a0, a1);
-    bool h1 = (e.y != kNodeNone) && clip_box(ox, oy, oz, dx, dy, dz, tmin, tmax, b.z, b.w, c.x, c.y, c.z, c.w, b0, b1);
+    bool h0 = clip_box(ray, a.x, a.y, a.z, a.w, b.x, b.y, a0, a1);
+    bool h1 = (e.y != kNodeNone) && clip_box(ray, b.z, b.w, c.x, c.y, c.z, c.w, b0, b1);
     // a subtree whose box starts after the best leaf cannot hold a smaller key
     if (best >= 0) {
       h0 = h0 && a0 <= bt0;

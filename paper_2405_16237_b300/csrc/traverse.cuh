@@ -31,6 +31,7 @@ __global__ void __launch_bounds__(128) traverse_kernel(const nbvh_node* __restri
     const float ox = rays.ox[r], oy = rays.oy[r], oz = rays.oz[r];
     const float dx = rays.dx[r], dy = rays.dy[r], dz = rays.dz[r];
     const float tmin = rays.tmin[r], tmax = rays.tmax[r];
+    const RayR ray = make_rayr(ox, oy, oz, dx, dy, dz, tmin, tmax);
     const int max_segs = out.max_segs;
     bool overflow = false;
     auto emit = [&](int leaf, float t0, float t1) {
@@ -72,9 +73,8 @@ __global__ void __launch_bounds__(128) traverse_kernel(const nbvh_node* __restri
       const float4 c = __ldg(np + 2);
       const int4 e = __ldg(reinterpret_cast<const int4*>(np + 3));
       float a0, a1, b0, b1;
-      const bool h0 = clip_box(ox, oy, oz, dx, dy, dz, tmin, tmax, a.x, a.y, a.z, a.w, b.x, b.y, a0, a1);
-      const bool h1 = (e.y != kNodeNone) &&
-                      clip_box(ox, oy, oz, dx, dy, dz, tmin, tmax, b.z, b.w, c.x, c.y, c.z, c.w, b0, b1);
+      const bool h0 = clip_box(ray, a.x, a.y, a.z, a.w, b.x, b.y, a0, a1);
+      const bool h1 = (e.y != kNodeNone) && clip_box(ray, b.z, b.w, c.x, c.y, c.z, c.w, b0, b1);
       if (h0 && e.x < 0) emit(~e.x, a0, a1);
       if (h1 && e.y < 0) emit(~e.y, b0, b1);
       const bool g0 = h0 && e.x >= 0;

@@ -117,6 +117,10 @@ _SIGS = {
                             c_void_p]),
     "nbvh_train_step": (c_int32, [POINTER(ModelDesc), POINTER(Optim), POINTER(TrainScene), c_int32, c_int64,
                                   ctypes.c_uint64, c_int64, c_float, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "nbvh_graph_begin": (c_int32, [c_void_p]),
+    "nbvh_graph_end": (c_int32, [c_void_p, POINTER(c_void_p)]),
+    "nbvh_graph_launch": (c_int32, [c_void_p, c_void_p]),
+    "nbvh_graph_destroy": (c_int32, [c_void_p]),
     "nbvh_get_device_status": (c_int32, [c_void_p]),
 }
 
@@ -555,3 +559,41 @@ def train_step(desc: ModelDesc, opt: Optimizer, scene: DeviceScene, mode: int, b
     _check(lib().nbvh_train_step(ctypes.byref(desc), ctypes.byref(opt.struct), ctypes.byref(scene.struct), mode,
                                  batch, ctypes.c_uint64(seed), step, lr, _ptr(loss_out), c_void_p(base), avail,
                                  _stream()), "train_step")
+
+
+class Graph:
+    """A recorded sequence of library calls replayed with one launch
+    (nbvh_graph_*). Record on a created torch stream:
+
+        with torch.cuda.stream(s):
+            g = Graph.record(lambda: query_rays(...))
+            g.launch()
+    """
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    @classmethod
+    def record(cls, fn):
+        _check(lib().nbvh_graph_begin(_stream()), "graph_begin")
+        try:
+            fn()
+        finally:
+            h = c_void_p()
+            st = lib().nbvh_graph_end(_stream(), ctypes.byref(h))
+        _check(st, "graph_end")
+        return cls(h)
+
+    def launch(self):
+        _check(lib().nbvh_graph_launch(self.handle, _stream()), "graph_launch")
+
+    def destroy(self):
+        if self.handle:
+            lib().nbvh_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
