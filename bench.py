@@ -174,7 +174,7 @@ def time_training(spec, tris, wl, steps, warmup, batch=1 << 18):
     desc = B.with_mlp_prec(wl.desc, B.FP16)
     opt = B.Optimizer(desc, torch.as_tensor(wl.table_np.astype(np.float32)).cuda(), wl.mlp.clone(),
                       loss_scale=32768.0)
-    ws = B.new_workspace(B.train_workspace_size(desc, batch))
+    ws = B.new_workspace(B.train_workspace_size(desc, batch, scene.n_leaves))
     loss = torch.zeros(1, dtype=torch.float64, device="cuda")
     step = 0
     for _ in range(warmup):

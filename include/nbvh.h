@@ -254,6 +254,8 @@ typedef struct {
   const float* tris;         /* device [n_tris][9] */
   const int32_t* tri_perm;   /* device, as nbvh_build_leaves */
   const int32_t* leaf_range; /* device [n_leaves][2] */
+  const float* leaf_tris;    /* optional device [n_tris][9]: the triangles in tri_perm order (each
+                                leaf's triangles contiguous); the labels read them when set */
   nbvh_scene_info info;      /* by value */
 } nbvh_train_scene;
 
@@ -284,8 +286,9 @@ nbvh_status nbvh_train_labels(nbvh_rays rays, const int32_t* leaf, const float* 
                               const nbvh_train_scene* scene, nbvh_labels out, void* stream);
 
 /* Host. Workspace of nbvh_forward_train / nbvh_backward / nbvh_train_step for
- * batches of up to n rays. */
-nbvh_status nbvh_train_workspace_size(const nbvh_model_desc* desc, int64_t n, size_t* bytes);
+ * batches of up to n rays; n_leaves = the scene's leaf count for
+ * nbvh_train_step (its rays are grouped by leaf), 0 for forward/backward only. */
+nbvh_status nbvh_train_workspace_size(const nbvh_model_desc* desc, int64_t n, int32_t n_leaves, size_t* bytes);
 
 /* Device. Forward of n training segments (segment i belongs to ray i and to
  * leaf[i]; leaf < 0 does not train) storing the activations in the workspace.

@@ -45,6 +45,7 @@ __device__ __forceinline__ float loss_terms(const float* o, float y, float d, fl
 // loss terms and dL/d(raw) times the loss scale.
 struct TcTrain {
   const int32_t* leaf;
+  const int32_t* order;  // item -> ray (rays grouped by leaf); nullptr: item = ray
   uint16_t* X16;      // [n][Kp]
   uint16_t* H16;      // [n_hidden][n][W]
   float* O;           // [n][n_out]

@@ -354,9 +354,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
           t0 = a.seg_t0[q];
           t1 = a.seg_t1[q];
         } else if constexpr (MODE == 2) {
-          ray = a.tr.leaf[i] >= 0 ? int(i) : -1;
-          t0 = a.list_t0[i];
-          t1 = a.list_t1[i];
+          const int r = a.tr.order ? a.tr.order[i] : int(i);
+          ray = a.tr.leaf[r] >= 0 ? r : -1;
+          t0 = a.list_t0[r];
+          t1 = a.list_t1[r];
         } else {
           ray = a.seg_ray[i];
           t0 = a.list_t0[i];
@@ -527,8 +528,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
             if (a.tr.lab.hit && ray >= 0) {
               const float inv_valid = 1.0f / float(max(1, *a.tr.n_valid));
               const float ls = a.tr.loss_scale_dev ? *a.tr.loss_scale_dev : a.tr.loss_scale;
-              term = loss_terms(raw, float(a.tr.lab.hit[grow]), a.tr.lab.depth[grow], a.tr.lab.nx[grow],
-                                a.tr.lab.ny[grow], a.tr.lab.nz[grow], ls * inv_valid, g);
+              term = loss_terms(raw, float(a.tr.lab.hit[ray]), a.tr.lab.depth[ray], a.tr.lab.nx[ray],
+                                a.tr.lab.ny[ray], a.tr.lab.nz[ray], ls * inv_valid, g);
             }
             for (int j = 0; j < n_out; ++j) a.tr.O[grow * n_out + j] = raw[j];
             if (a.tr.lab.hit) {

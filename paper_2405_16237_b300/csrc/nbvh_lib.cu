@@ -483,10 +483,11 @@ struct TrainWs {
   float *depth, *nx, *ny, *nz;
   TrainBuffers buf;
   uint16_t *X16, *H16, *dZ16;  // tensor-core path: 16-bit operands
+  int32_t *counts, *cursor, *order;  // rays grouped by trained leaf (training step)
   size_t bytes;
 };
 
-TrainWs carve_train(void* base, const nbvh_model_desc* d, int64_t n) {
+TrainWs carve_train(void* base, const nbvh_model_desc* d, int64_t n, int32_t n_leaves = 0) {
   TrainWs w;
   std::memset(&w, 0, sizeof(w));
   char* p = static_cast<char*>(base);
@@ -520,6 +521,11 @@ TrainWs carve_train(void* base, const nbvh_model_desc* d, int64_t n) {
   w.X16 = reinterpret_cast<uint16_t*>(take(2 * N * Kp));
   w.H16 = reinterpret_cast<uint16_t*>(take(2 * nh * N * Wd));
   w.dZ16 = reinterpret_cast<uint16_t*>(take(2 * nh * N * Wd));
+  if (n_leaves > 0) {
+    w.counts = reinterpret_cast<int32_t*>(take(4 * size_t(n_leaves)));
+    w.cursor = reinterpret_cast<int32_t*>(take(4 * (size_t(n_leaves) + 1)));
+    w.order = reinterpret_cast<int32_t*>(take(4 * N));
+  }
   w.bytes = off;
   return w;
 }
@@ -641,9 +647,9 @@ cudaError_t launch_bwd_tc(const nbvh_model_desc* d, const TcBwdArgs& a, cudaStre
 template <typename TZ, typename TA>
 cudaError_t launch_wg_any(const TZ* dZ, int ldz, int n_o, const TA* A, int lda, int n_j, int64_t n, float* dW,
                           float* db, cudaStream_t s) {
-  dim3 grid(unsigned((n_o + kWgTile - 1) / kWgTile), unsigned((n_j + kWgTile - 1) / kWgTile),
-            unsigned((n + kWgChunk - 1) / kWgChunk));
-  weight_grad_any<TZ, TA><<<grid, 256, 0, s>>>(dZ, ldz, n_o, A, lda, n_j, n, dW, db);
+  dim3 grid(unsigned((n_o + kWgT - 1) / kWgT), unsigned((n_j + kWgT - 1) / kWgT),
+            unsigned((n + kWgChunk2 - 1) / kWgChunk2));
+  weight_grad_tiled<TZ, TA><<<grid, 256, 0, s>>>(dZ, ldz, n_o, A, lda, n_j, n, dW, db);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -673,11 +679,7 @@ cudaError_t weight_grads_16(const nbvh_model_desc* d, const TrainWs& w, const fl
 
 cudaError_t launch_weight_grad(const float* dZ, int n_o, const float* A, int n_j, int64_t n, float* dW, float* db,
                                cudaStream_t s) {
-  dim3 grid(unsigned((n_o + kWgTile - 1) / kWgTile), unsigned((n_j + kWgTile - 1) / kWgTile),
-            unsigned((n + kWgChunk - 1) / kWgChunk));
-  weight_grad_kernel<<<grid, 256, 0, s>>>(dZ, n_o, A, n_j, n, dW, db);
-  count_launches(1);
-  return cudaGetLastError();
+  return launch_wg_any<float, float>(dZ, n_o, n_o, A, n_j, n_j, n, dW, db, s);
 }
 
 }  // namespace
@@ -726,30 +728,64 @@ extern "C" nbvh_status nbvh_train_labels(nbvh_rays rays, const int32_t* leaf, co
   if (rays.n == 0) return NBVH_OK;
   if (!leaf || !t0 || !t1 || !out.hit || !out.depth || !out.nx || !out.ny || !out.nz) return NBVH_ERR_INVALID_ARG;
   labels_kernel<<<unsigned((rays.n + 127) / 128), 128, 0, as_stream(stream)>>>(
-      ray_ptrs(rays), leaf, t0, t1, rays.n, scene->tris, scene->tri_perm, scene->leaf_range, out.hit, out.depth,
-      out.nx, out.ny, out.nz);
+      ray_ptrs(rays), leaf, t0, t1, rays.n, scene->tris, scene->tri_perm, scene->leaf_range, scene->leaf_tris,
+      nullptr, out.hit, out.depth, out.nx, out.ny, out.nz);
   count_launches(1);
   return status_of(cudaGetLastError());
 }
 
-extern "C" nbvh_status nbvh_train_workspace_size(const nbvh_model_desc* desc, int64_t n, size_t* bytes) {
-  if (!nbvh_host::desc_valid(desc) || n < 0 || !bytes) return NBVH_ERR_INVALID_ARG;
-  *bytes = carve_train(nullptr, desc, n).bytes;
+extern "C" nbvh_status nbvh_train_workspace_size(const nbvh_model_desc* desc, int64_t n, int32_t n_leaves,
+                                                 size_t* bytes) {
+  if (!nbvh_host::desc_valid(desc) || n < 0 || n_leaves < 0 || !bytes) return NBVH_ERR_INVALID_ARG;
+  *bytes = carve_train(nullptr, desc, n, n_leaves).bytes;
   return NBVH_OK;
 }
+
+namespace nbvh {
+namespace {
+nbvh_status forward_train_impl(const nbvh_model_desc* desc, const void* table, const float* mlp, nbvh_rays rays,
+                               const int32_t* leaf, const float* t0, const float* t1, nbvh_labels labels,
+                               const int32_t* n_valid, float loss_scale, const float* loss_scale_dev,
+                               float* raw_out, double* loss_out, void* workspace, size_t ws_bytes, void* stream,
+                               const int32_t* order, int32_t n_leaves);
+nbvh_status backward_impl(const nbvh_model_desc* desc, const void* table, const float* mlp, nbvh_rays rays,
+                          const int32_t* leaf, const float* t0, const float* t1, const float* grad_out,
+                          float* grad_table, float* grad_mlp, void* workspace, size_t ws_bytes, void* stream,
+                          const int32_t* order, int32_t n_leaves);
+}  // namespace
+}  // namespace nbvh
 
 extern "C" nbvh_status nbvh_forward_train(const nbvh_model_desc* desc, const void* table, const float* mlp,
                                           nbvh_rays rays, const int32_t* leaf, const float* t0, const float* t1,
                                           nbvh_labels labels, const int32_t* n_valid, float loss_scale,
                                           const float* loss_scale_dev, float* raw_out, double* loss_out,
                                           void* workspace, size_t ws_bytes, void* stream) {
+  return forward_train_impl(desc, table, mlp, rays, leaf, t0, t1, labels, n_valid, loss_scale, loss_scale_dev,
+                            raw_out, loss_out, workspace, ws_bytes, stream, nullptr, 0);
+}
+
+extern "C" nbvh_status nbvh_backward(const nbvh_model_desc* desc, const void* table, const float* mlp,
+                                     nbvh_rays rays, const int32_t* leaf, const float* t0, const float* t1,
+                                     const float* grad_out, float* grad_table, float* grad_mlp, void* workspace,
+                                     size_t ws_bytes, void* stream) {
+  return backward_impl(desc, table, mlp, rays, leaf, t0, t1, grad_out, grad_table, grad_mlp, workspace, ws_bytes,
+                       stream, nullptr, 0);
+}
+
+namespace nbvh {
+namespace {
+nbvh_status forward_train_impl(const nbvh_model_desc* desc, const void* table, const float* mlp, nbvh_rays rays,
+                               const int32_t* leaf, const float* t0, const float* t1, nbvh_labels labels,
+                               const int32_t* n_valid, float loss_scale, const float* loss_scale_dev,
+                               float* raw_out, double* loss_out, void* workspace, size_t ws_bytes, void* stream,
+                               const int32_t* order, int32_t n_leaves) {
   if (!nbvh_host::desc_valid(desc) || !table || !mlp || !rays_valid(rays)) return NBVH_ERR_INVALID_ARG;
   if (rays.n == 0) return NBVH_OK;
   if (!leaf || !t0 || !t1 || !workspace || (reinterpret_cast<uintptr_t>(workspace) & 255) ||
       (labels.hit && (!labels.depth || !labels.nx || !labels.ny || !labels.nz || !n_valid)) ||
       !(loss_scale > 0.0f))
     return NBVH_ERR_INVALID_ARG;
-  TrainWs w = carve_train(workspace, desc, rays.n);
+  TrainWs w = carve_train(workspace, desc, rays.n, n_leaves);
   if (ws_bytes < w.bytes) return NBVH_ERR_WORKSPACE_TOO_SMALL;
   GridParams gp;
   if (!make_grid(desc, gp)) return NBVH_ERR_INVALID_ARG;
@@ -768,6 +804,7 @@ extern "C" nbvh_status nbvh_forward_train(const nbvh_model_desc* desc, const voi
     a.list_t1 = t1;
     a.n_items = rays.n;
     a.tr.leaf = leaf;
+    a.tr.order = order;
     a.tr.X16 = w.X16;
     a.tr.H16 = w.H16;
     a.tr.O = w.buf.O;
@@ -785,23 +822,24 @@ extern "C" nbvh_status nbvh_forward_train(const nbvh_model_desc* desc, const voi
     if (e != cudaSuccess) return NBVH_ERR_CUDA;
   }
   if (labels.hit && loss_out) {
-    loss_reduce_kernel<<<1, 256, 0, s>>>(w.buf.loss_seg, rays.n, n_valid, loss_out);
+    if (cudaMemsetAsync(loss_out, 0, sizeof(double), s) != cudaSuccess) return NBVH_ERR_CUDA;
+    loss_reduce_kernel<<<unsigned(sm_count()), 256, 0, s>>>(w.buf.loss_seg, rays.n, n_valid, loss_out);
     count_launches(1);
     e = cudaGetLastError();
   }
   return status_of(e);
 }
 
-extern "C" nbvh_status nbvh_backward(const nbvh_model_desc* desc, const void* table, const float* mlp,
-                                     nbvh_rays rays, const int32_t* leaf, const float* t0, const float* t1,
-                                     const float* grad_out, float* grad_table, float* grad_mlp, void* workspace,
-                                     size_t ws_bytes, void* stream) {
+nbvh_status backward_impl(const nbvh_model_desc* desc, const void* table, const float* mlp, nbvh_rays rays,
+                          const int32_t* leaf, const float* t0, const float* t1, const float* grad_out,
+                          float* grad_table, float* grad_mlp, void* workspace, size_t ws_bytes, void* stream,
+                          const int32_t* order, int32_t n_leaves) {
   if (!nbvh_host::desc_valid(desc) || !table || !mlp || !rays_valid(rays)) return NBVH_ERR_INVALID_ARG;
   if (rays.n == 0) return NBVH_OK;
   if (!leaf || !t0 || !t1 || !grad_table || !grad_mlp || !workspace ||
       (reinterpret_cast<uintptr_t>(workspace) & 255))
     return NBVH_ERR_INVALID_ARG;
-  TrainWs w = carve_train(workspace, desc, rays.n);
+  TrainWs w = carve_train(workspace, desc, rays.n, n_leaves);
   if (ws_bytes < w.bytes) return NBVH_ERR_WORKSPACE_TOO_SMALL;
   GridParams gp;
   if (!make_grid(desc, gp)) return NBVH_ERR_INVALID_ARG;
@@ -815,6 +853,7 @@ extern "C" nbvh_status nbvh_backward(const nbvh_model_desc* desc, const void* ta
     b.n_out = desc->n_out;
     b.rays = ray_ptrs(rays);
     b.leaf = leaf;
+    b.order = order;
     b.t0 = t0;
     b.t1 = t1;
     b.n = rays.n;
@@ -849,6 +888,9 @@ extern "C" nbvh_status nbvh_backward(const nbvh_model_desc* desc, const void* ta
                            grad_mlp + off + size_t(no) * Wd, s);
   return status_of(e);
 }
+
+}  // namespace
+}  // namespace nbvh
 
 extern "C" nbvh_status nbvh_adam(const nbvh_model_desc* desc, const nbvh_optim* opt, int64_t step, float lr,
                                  float beta1, float beta2, float eps, int32_t dynamic_scale, void* stream) {
@@ -900,23 +942,35 @@ extern "C" nbvh_status nbvh_train_step(const nbvh_model_desc* desc, const nbvh_o
   if (!nbvh_host::desc_valid(desc) || !opt || !scene_valid(scene) || batch < 1 || step < 1 || !workspace ||
       (reinterpret_cast<uintptr_t>(workspace) & 255) || batch > (int64_t(1) << 31) - 1)
     return NBVH_ERR_INVALID_ARG;
-  TrainWs w = carve_train(workspace, desc, batch);
+  TrainWs w = carve_train(workspace, desc, batch, scene->n_leaves);
   if (ws_bytes < w.bytes) return NBVH_ERR_WORKSPACE_TOO_SMALL;
   cudaStream_t s = as_stream(stream);
   if (cudaMemsetAsync(w.n_valid, 0, 256, s) != cudaSuccess) return NBVH_ERR_CUDA;
+  if (cudaMemsetAsync(w.counts, 0, 4 * size_t(scene->n_leaves), s) != cudaSuccess) return NBVH_ERR_CUDA;
   nbvh_rays_out ro{w.rays[0], w.rays[1], w.rays[2], w.rays[3], w.rays[4], w.rays[5], w.rays[6], w.rays[7], batch};
   nbvh_status st = nbvh_train_rays(mode, seed, step - 1, scene, ro, w.leaf, w.t0, w.t1, w.n_valid, stream);
   if (st != NBVH_OK) return st;
   nbvh_rays ri{w.rays[0], w.rays[1], w.rays[2], w.rays[3], w.rays[4], w.rays[5], w.rays[6], w.rays[7], batch};
   nbvh_labels lab{w.hit, w.depth, w.nx, w.ny, w.nz};
-  st = nbvh_train_labels(ri, w.leaf, w.t0, w.t1, scene, lab, stream);
-  if (st != NBVH_OK) return st;
+  // group the rays by trained leaf: labels share a leaf's triangles per warp,
+  // and the forward/backward tiles hold spatially close rays
+  const unsigned g = unsigned((batch + 255) / 256);
+  leaf_hist_kernel<<<g, 256, 0, s>>>(w.leaf, batch, w.counts);
+  leaf_scan_kernel<<<1, 1024, 0, s>>>(w.counts, scene->n_leaves, w.cursor);
+  leaf_scatter_kernel<<<g, 256, 0, s>>>(w.leaf, batch, scene->n_leaves, w.cursor, w.order);
+  labels_kernel<<<unsigned((batch + 127) / 128), 128, 0, s>>>(
+      RayPtrs{ri.ox, ri.oy, ri.oz, ri.dx, ri.dy, ri.dz, ri.tmin, ri.tmax}, w.leaf, w.t0, w.t1, batch, scene->tris,
+      scene->tri_perm, scene->leaf_range, scene->leaf_tris, w.order, lab.hit, lab.depth, lab.nx, lab.ny, lab.nz);
+  count_launches(4);
+  if (cudaGetLastError() != cudaSuccess) return NBVH_ERR_CUDA;
   const void* table = opt->table_work ? opt->table_work : opt->table_master;
-  st = nbvh_forward_train(desc, table, opt->mlp, ri, w.leaf, w.t0, w.t1, lab, w.n_valid, 1.0f, opt->loss_scale,
-                          nullptr, loss_out ? loss_out : w.loss, workspace, ws_bytes, stream);
+  const int32_t* order = desc->mlp_prec != NBVH_FP32 ? w.order : nullptr;
+  st = forward_train_impl(desc, table, opt->mlp, ri, w.leaf, w.t0, w.t1, lab, w.n_valid, 1.0f, opt->loss_scale,
+                          nullptr, loss_out ? loss_out : w.loss, workspace, ws_bytes, stream, order,
+                          scene->n_leaves);
   if (st != NBVH_OK) return st;
-  st = nbvh_backward(desc, table, opt->mlp, ri, w.leaf, w.t0, w.t1, nullptr, opt->grad_table, opt->grad_mlp,
-                     workspace, ws_bytes, stream);
+  st = backward_impl(desc, table, opt->mlp, ri, w.leaf, w.t0, w.t1, nullptr, opt->grad_table, opt->grad_mlp,
+                     workspace, ws_bytes, stream, order, scene->n_leaves);
   if (st != NBVH_OK) return st;
   return nbvh_adam(desc, opt, step, lr, 0.9f, 0.999f, 1e-8f, desc->mlp_prec != NBVH_FP32 ? 1 : 0, stream);
 }

@@ -162,14 +162,20 @@ __global__ void __launch_bounds__(128) train_rays_kernel(TrainRayArgs a) {
 // Local depth (t - t0)/(t1 - t0) (0 for t1 == t0); geometric normal turned
 // to face -d (Sec. 5.2).
 // ---------------------------------------------------------------------------
+// With `order` (rays grouped by leaf) the lanes of a warp mostly share one
+// leaf: the triangle loop is warp-uniform and its loads are broadcasts. With
+// `leaf_tris` the leaf's triangles are read contiguously.
 __global__ void __launch_bounds__(128) labels_kernel(RayPtrs rays, const int32_t* __restrict__ leaf,
                                                      const float* __restrict__ t0, const float* __restrict__ t1,
                                                      int64_t n, const float* __restrict__ tris,
                                                      const int32_t* __restrict__ tri_perm,
-                                                     const int32_t* __restrict__ leaf_range, uint8_t* hit,
+                                                     const int32_t* __restrict__ leaf_range,
+                                                     const float* __restrict__ leaf_tris,
+                                                     const int32_t* __restrict__ order, uint8_t* hit,
                                                      float* depth, float* nx, float* ny, float* nz) {
-  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  const int64_t item = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (item >= n) return;
+  const int64_t i = order ? int64_t(order[item]) : item;
   const int lf = leaf[i];
   uint8_t h = 0;
   float dep = 0.0f, gx = 0.0f, gy = 0.0f, gz = 0.0f;
@@ -181,7 +187,7 @@ __global__ void __launch_bounds__(128) labels_kernel(RayPtrs rays, const int32_t
     float best = __int_as_float(0x7f800000);
     int bj = -1;
     for (int j = b; j < e; ++j) {
-      const float* T = tris + size_t(tri_perm[j]) * 9;
+      const float* T = leaf_tris ? leaf_tris + size_t(j) * 9 : tris + size_t(tri_perm[j]) * 9;
       const float v0x = __ldg(T), v0y = __ldg(T + 1), v0z = __ldg(T + 2);
       const float e1x = __ldg(T + 3) - v0x, e1y = __ldg(T + 4) - v0y, e1z = __ldg(T + 5) - v0z;
       const float e2x = __ldg(T + 6) - v0x, e2y = __ldg(T + 7) - v0y, e2z = __ldg(T + 8) - v0z;
@@ -206,7 +212,7 @@ __global__ void __launch_bounds__(128) labels_kernel(RayPtrs rays, const int32_t
       h = 1;
       const float span = a1 - a0;
       dep = span > 0.0f ? (best - a0) / span : 0.0f;
-      const float* T = tris + size_t(tri_perm[bj]) * 9;
+      const float* T = leaf_tris ? leaf_tris + size_t(bj) * 9 : tris + size_t(tri_perm[bj]) * 9;
       const float e1x = T[3] - T[0], e1y = T[4] - T[1], e1z = T[5] - T[2];
       const float e2x = T[6] - T[0], e2y = T[7] - T[1], e2z = T[8] - T[2];
       gx = e1y * e2z - e1z * e2y;
@@ -646,18 +652,63 @@ __global__ void loss_scale_update_kernel(AdamState st, int32_t dynamic) {
 
 // Sum of per-segment loss terms in FP64 divided by the valid count (the batch
 // loss); also used by the finite-difference gradient check.
+// (*out must be zero before the launch; blocks add their partial sums.)
 __global__ void loss_reduce_kernel(const float* __restrict__ term, int64_t n, const int32_t* n_valid,
                                    double* out) {
   __shared__ double sm[256];
   double acc = 0.0;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) acc += double(term[i]);
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    acc += double(term[i]);
   sm[threadIdx.x] = acc;
   __syncthreads();
   for (int s = blockDim.x / 2; s > 0; s >>= 1) {
     if (threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];
     __syncthreads();
   }
-  if (threadIdx.x == 0) out[0] = sm[0] / double(max(1, *n_valid));
+  if (threadIdx.x == 0) atomicAdd(out, sm[0] / double(max(1, *n_valid)));
+}
+
+// ---------------------------------------------------------------------------
+// Rays grouped by trained leaf (counting sort): order[] lists the training rays
+// leaf by leaf, then the rays that train nothing.
+// ---------------------------------------------------------------------------
+__global__ void leaf_hist_kernel(const int32_t* __restrict__ leaf, int64_t n, int32_t* counts) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n && leaf[i] >= 0) atomicAdd(counts + leaf[i], 1);
+}
+
+// Exclusive scan of n_leaves counts into cursor[0..n_leaves]; cursor[n_leaves]
+// is the number of training rays (where the rays without a leaf start).
+__global__ void __launch_bounds__(1024) leaf_scan_kernel(const int32_t* __restrict__ counts, int n_leaves,
+                                                         int32_t* cursor) {
+  __shared__ int32_t part[1024];
+  const int per = (n_leaves + blockDim.x - 1) / blockDim.x;
+  const int b = threadIdx.x * per, e = min(n_leaves, b + per);
+  int32_t s = 0;
+  for (int i = b; i < e; ++i) s += counts[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 1; off < blockDim.x; off <<= 1) {
+    const int32_t v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int32_t run = part[threadIdx.x] - s;
+  for (int i = b; i < e; ++i) {
+    cursor[i] = run;
+    run += counts[i];
+  }
+  if (threadIdx.x == blockDim.x - 1) cursor[n_leaves] = part[threadIdx.x];
+}
+
+__global__ void leaf_scatter_kernel(const int32_t* __restrict__ leaf, int64_t n, int n_leaves, int32_t* cursor,
+                                    int32_t* order) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int lf = leaf[i];
+  const int pos = atomicAdd(cursor + (lf >= 0 ? lf : n_leaves), 1);
+  order[pos] = int32_t(i);
 }
 
 }  // namespace nbvh

@@ -13,10 +13,11 @@ struct TcBwdArgs {
   int32_t n_hidden, n_out;
   RayPtrs rays;
   const int32_t* leaf;
+  const int32_t* order;   // item -> ray as in the forward; nullptr: item = ray
   const float* t0;
   const float* t1;
   int64_t n;
-  const float* G;         // [n][n_out] dL/d(raw), times the loss scale
+  const float* G;         // [n][n_out] dL/d(raw), times the loss scale (by item)
   const uint16_t* H16;    // [n_hidden][n][W] hidden activations of the forward
   uint16_t* dZ16;         // [n_hidden][n][W] pre-activation gradients (out)
   float* grad_table;      // FP32 [entries][F]
@@ -134,10 +135,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) train_backward_tc(TcBwdArgs a) 
   for (int64_t tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
     if (threadIdx.x < kTcM) {
       const int64_t i = tile * kTcM + threadIdx.x;
-      const bool v = i < a.n && a.leaf[i] >= 0;
-      sray[threadIdx.x] = v ? int(i) : -1;
-      st0[threadIdx.x] = v ? a.t0[i] : 0.0f;
-      st1[threadIdx.x] = v ? a.t1[i] : 0.0f;
+      const int r = i < a.n ? (a.order ? a.order[i] : int(i)) : 0;
+      const bool v = i < a.n && a.leaf[r] >= 0;
+      sray[threadIdx.x] = v ? r : -1;
+      st0[threadIdx.x] = v ? a.t0[r] : 0.0f;
+      st1[threadIdx.x] = v ? a.t1[r] : 0.0f;
     }
     __syncthreads();
     const int64_t grow = tile * kTcM + row;
@@ -228,36 +230,62 @@ __global__ void __launch_bounds__(kTcThreads, 1) train_backward_tc(TcBwdArgs a) 
           float gx[16];
           tmem_ld16(t_row + lay.col_x + uint32_t(cgroup * 16), gx);
           tmem_ld_wait();
+          // Whole warps run this loop (lanes = 32 rows, grouped by leaf in the
+          // training step): when all lanes hit the same entry (coarse levels)
+          // the warp adds one sum instead of 32 atomics.
           const int ray = sray[row];
-          if (ray >= 0) {
-            int kprev = -1;
-            float x = 0.0f, y = 0.0f, z = 0.0f;
-            for (int j = 0; j < 16; j += F) {
-              const int f = c0 + cgroup * 16 + j;
-              if (f >= K) break;
-              const int k = f / (L * F);
-              const int l = (f / F) % L;
-              if (k != kprev) {
+          const bool valid = ray >= 0;
+          int kprev = -1;
+          float x = 0.0f, y = 0.0f, z = 0.0f;
+          for (int j = 0; j < 16; j += F) {
+            const int f = c0 + cgroup * 16 + j;
+            if (f >= K) break;
+            const int k = f / (L * F);
+            const int l = (f / F) % L;
+            if (k != kprev) {
+              if (valid)
                 sample_point(a.gp, a.rays.ox[ray], a.rays.oy[ray], a.rays.oz[ray], a.rays.dx[ray],
                              a.rays.dy[ray], a.rays.dz[ray], st0[row], st1[row], k, x, y, z);
-                kprev = k;
-              }
-              Corners cr;
-              level_corners(a.gp, l, x, y, z, cr);
-              float* gt = a.grad_table + a.gp.offset[l] * F;
+              kprev = k;
+            }
+            Corners cr;
+            level_corners(a.gp, l, x, y, z, cr);
+            float* gt = a.grad_table + a.gp.offset[l] * F;
 #pragma unroll
-              for (int q = 0; q < 8; ++q) {
-                float* dst = gt + size_t(cr.idx[q]) * F;
+            for (int q = 0; q < 8; ++q) {
+              const uint32_t key = valid ? cr.idx[q] : 0xffffffffu;
+              int same = 0;
+              __match_all_sync(0xffffffffu, key, &same);
+              float v[F];
+#pragma unroll
+              for (int ff = 0; ff < F; ++ff) v[ff] = valid ? cr.w[q] * gx[j + ff] : 0.0f;
+              if (same) {
+                if (key != 0xffffffffu) {
+#pragma unroll
+                  for (int ff = 0; ff < F; ++ff) {
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) v[ff] += __shfl_xor_sync(0xffffffffu, v[ff], o);
+                  }
+                  if (lane == 0) {
+                    float* dst = gt + size_t(key) * F;
+                    if constexpr (F == 2) {
+                      atomicAdd(reinterpret_cast<float2*>(dst), make_float2(v[0], v[1]));
+                    } else {
+#pragma unroll
+                      for (int ff = 0; ff < F; ++ff) atomicAdd(dst + ff, v[ff]);
+                    }
+                  }
+                }
+              } else if (valid) {
+                float* dst = gt + size_t(key) * F;
                 if constexpr (F == 2) {
-                  atomicAdd(reinterpret_cast<float2*>(dst), make_float2(cr.w[q] * gx[j], cr.w[q] * gx[j + 1]));
+                  atomicAdd(reinterpret_cast<float2*>(dst), make_float2(v[0], v[1]));
                 } else if constexpr (F % 4 == 0) {
 #pragma unroll
                   for (int ff = 0; ff < F; ff += 4)
-                    atomicAdd(reinterpret_cast<float4*>(dst + ff),
-                              make_float4(cr.w[q] * gx[j + ff], cr.w[q] * gx[j + ff + 1], cr.w[q] * gx[j + ff + 2],
-                                          cr.w[q] * gx[j + ff + 3]));
+                    atomicAdd(reinterpret_cast<float4*>(dst + ff), make_float4(v[ff], v[ff + 1], v[ff + 2], v[ff + 3]));
                 } else {
-                  atomicAdd(dst, cr.w[q] * gx[j]);
+                  atomicAdd(dst, v[0]);
                 }
               }
             }
@@ -279,49 +307,63 @@ __global__ void __launch_bounds__(kTcThreads, 1) train_backward_tc(TcBwdArgs a) 
 // Weight gradients from stored operands of either precision (FP32 G, 16-bit
 // activations and pre-activation gradients): dW[o][j] += sum_i dZ[i][o] A[i][j],
 // db[o] += sum_i dZ[i][o], FP32 accumulation, split-K over segment chunks.
-template <typename TZ, typename TA>
-__device__ __forceinline__ float ldv(const TZ* p) {
-  if constexpr (std::is_same<TZ, float>::value) return *p;
-  else if constexpr (std::is_same<TZ, __half>::value) return __half2float(*p);
-  else return __bfloat162float(*p);
+// Block = 64 x 64 outputs, thread = 4 x 4 (float4 broadcasts from shared memory).
+template <typename T>
+__device__ __forceinline__ float to_f(T v) {
+  if constexpr (std::is_same<T, float>::value) return v;
+  else if constexpr (std::is_same<T, __half>::value) return __half2float(v);
+  else return __bfloat162float(v);
 }
 
+constexpr int kWgT = 64;
+constexpr int kWgRows = 32;
+constexpr int kWgChunk2 = 4096;
+
 template <typename TZ, typename TA>
-__global__ void __launch_bounds__(256) weight_grad_any(const TZ* __restrict__ dZ, int ldz, int n_o,
-                                                       const TA* __restrict__ A, int lda, int n_j, int64_t n,
-                                                       float* __restrict__ dW, float* __restrict__ db) {
-  __shared__ float sz[32][kWgTile + 1];
-  __shared__ float sa[32][kWgTile + 1];
-  const int o0 = blockIdx.x * kWgTile;
-  const int j0 = blockIdx.y * kWgTile;
-  const int64_t i0 = int64_t(blockIdx.z) * kWgChunk;
-  const int64_t i1 = min(n, i0 + kWgChunk);
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  float acc[4] = {0, 0, 0, 0};
-  float bacc = 0.0f;
-  for (int64_t ib = i0; ib < i1; ib += 32) {
-    for (int idx = threadIdx.x; idx < 32 * kWgTile; idx += blockDim.x) {
-      const int r = idx / kWgTile, c = idx - r * kWgTile;
+__global__ void __launch_bounds__(256) weight_grad_tiled(const TZ* __restrict__ dZ, int ldz, int n_o,
+                                                         const TA* __restrict__ A, int lda, int n_j, int64_t n,
+                                                         float* __restrict__ dW, float* __restrict__ db) {
+  __shared__ __align__(16) float sz[kWgRows][kWgT];
+  __shared__ __align__(16) float sa[kWgRows][kWgT];
+  const int o0 = blockIdx.x * kWgT, j0 = blockIdx.y * kWgT;
+  const int64_t i0 = int64_t(blockIdx.z) * kWgChunk2;
+  const int64_t i1 = min(n, i0 + kWgChunk2);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  float acc[4][4] = {};
+  float bacc[4] = {0, 0, 0, 0};
+  for (int64_t ib = i0; ib < i1; ib += kWgRows) {
+    for (int idx = threadIdx.x; idx < kWgRows * kWgT; idx += blockDim.x) {
+      const int r = idx / kWgT, c = idx - r * kWgT;
       const int64_t i = ib + r;
-      sz[r][c] = (i < i1 && o0 + c < n_o) ? ldv<TZ, TZ>(dZ + i * ldz + o0 + c) : 0.0f;
-      sa[r][c] = (i < i1 && j0 + c < n_j) ? ldv<TA, TA>(A + i * lda + j0 + c) : 0.0f;
+      sz[r][c] = (i < i1 && o0 + c < n_o) ? to_f(dZ[i * ldz + o0 + c]) : 0.0f;
+      sa[r][c] = (i < i1 && j0 + c < n_j) ? to_f(A[i * lda + j0 + c]) : 0.0f;
     }
     __syncthreads();
 #pragma unroll 8
-    for (int r = 0; r < 32; ++r) {
-      const float av = sa[r][tx];
+    for (int r = 0; r < kWgRows; ++r) {
+      const float4 zv = *reinterpret_cast<const float4*>(&sz[r][ty * 4]);
+      const float4 av = *reinterpret_cast<const float4*>(&sa[r][tx * 4]);
+      const float z4[4] = {zv.x, zv.y, zv.z, zv.w}, a4[4] = {av.x, av.y, av.z, av.w};
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[q] = fmaf(sz[r][ty * 4 + q], av, acc[q]);
-      if (blockIdx.y == 0 && ty == 0) bacc += sz[r][tx];
+      for (int p = 0; p < 4; ++p) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(z4[p], a4[q], acc[p][q]);
+        bacc[p] += z4[p];
+      }
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int o = o0 + ty * 4 + q, j = j0 + tx;
-    if (o < n_o && j < n_j) atomicAdd(dW + size_t(o) * n_j + j, acc[q]);
+  for (int p = 0; p < 4; ++p) {
+    const int o = o0 + ty * 4 + p;
+    if (o >= n_o) continue;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = j0 + tx * 4 + q;
+      if (j < n_j) atomicAdd(dW + size_t(o) * n_j + j, acc[p][q]);
+    }
+    if (blockIdx.y == 0 && tx == 0) atomicAdd(db + o, bacc[p]);
   }
-  if (blockIdx.y == 0 && ty == 0 && o0 + tx < n_o) atomicAdd(db + o0 + tx, bacc);
 }
 
 }  // namespace nbvh

@@ -63,7 +63,8 @@ class SceneInfo(ctypes.Structure):
 
 class TrainScene(ctypes.Structure):
     _fields_ = [("nodes", c_void_p), ("n_nodes", c_int32), ("leaf_box", c_void_p), ("n_leaves", c_int32),
-                ("tris", c_void_p), ("tri_perm", c_void_p), ("leaf_range", c_void_p), ("info", SceneInfo)]
+                ("tris", c_void_p), ("tri_perm", c_void_p), ("leaf_range", c_void_p), ("leaf_tris", c_void_p),
+                ("info", SceneInfo)]
 
 
 class Labels(ctypes.Structure):
@@ -107,7 +108,7 @@ _SIGS = {
     "nbvh_train_rays": (c_int32, [c_int32, ctypes.c_uint64, c_int64, POINTER(TrainScene), RaysOut, c_void_p,
                                   c_void_p, c_void_p, c_void_p, c_void_p]),
     "nbvh_train_labels": (c_int32, [Rays, c_void_p, c_void_p, c_void_p, POINTER(TrainScene), Labels, c_void_p]),
-    "nbvh_train_workspace_size": (c_int32, [POINTER(ModelDesc), c_int64, POINTER(c_size_t)]),
+    "nbvh_train_workspace_size": (c_int32, [POINTER(ModelDesc), c_int64, c_int32, POINTER(c_size_t)]),
     "nbvh_forward_train": (c_int32, [POINTER(ModelDesc), c_void_p, c_void_p, Rays, c_void_p, c_void_p, c_void_p,
                                      Labels, c_void_p, c_float, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t,
                                      c_void_p]),
@@ -424,6 +425,7 @@ class DeviceScene:
         self.leaf_box = torch.as_tensor(np.ascontiguousarray(box), device=device)
         self.tri_perm = torch.as_tensor(leaves["tri_perm"], device=device)
         self.leaf_range = torch.as_tensor(np.ascontiguousarray(leaves["leaf_range"], np.int32), device=device)
+        self.leaf_tris = self.tris[self.tri_perm.long()].contiguous()
         self.n_nodes = leaves["n_nodes"]
         self.n_leaves = len(leaves["leaf_lo"])
         sc = TrainScene()
@@ -434,6 +436,7 @@ class DeviceScene:
         sc.tris = self.tris.data_ptr()
         sc.tri_perm = self.tri_perm.data_ptr()
         sc.leaf_range = self.leaf_range.data_ptr()
+        sc.leaf_tris = self.leaf_tris.data_ptr()
         inf = leaves["info"]
         for i in range(3):
             sc.info.lo[i] = float(inf["lo"][i])
@@ -484,9 +487,10 @@ def train_labels(rays: dict, leaf, t0, t1, scene: DeviceScene, out=None):
     return out
 
 
-def train_workspace_size(desc: ModelDesc, n: int) -> int:
+def train_workspace_size(desc: ModelDesc, n: int, n_leaves: int = 0) -> int:
     b = c_size_t()
-    _check(lib().nbvh_train_workspace_size(ctypes.byref(desc), n, ctypes.byref(b)), "train_workspace_size")
+    _check(lib().nbvh_train_workspace_size(ctypes.byref(desc), n, n_leaves, ctypes.byref(b)),
+           "train_workspace_size")
     return b.value
 
 

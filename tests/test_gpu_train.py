@@ -274,7 +274,7 @@ def test_training_gains_over_untrained_and_box_proxy():
     desc = b.desc
     opt = B.Optimizer(desc, b.table.clone(), b.mlp.clone())
     batch = 1 << 14
-    ws = B.new_workspace(B.train_workspace_size(desc, batch))
+    ws = B.new_workspace(B.train_workspace_size(desc, batch, scene.n_leaves))
     rays = W.camera_rays(64, 64, seed=W.SEED_BASE + 77)
     drays = B.to_device_rays(rays)
     gt = _gt_hits(b.case.tris, rays)
@@ -352,7 +352,7 @@ def test_tensor_core_training_learns():
     desc = b.with_prec(B.FP16)
     opt = B.Optimizer(desc, b.table.clone(), b.mlp.clone(), loss_scale=32768.0)
     batch = 1 << 14
-    ws = B.new_workspace(B.train_workspace_size(desc, batch))
+    ws = B.new_workspace(B.train_workspace_size(desc, batch, scene.n_leaves))
     rays = W.camera_rays(64, 64, seed=W.SEED_BASE + 77)
     drays = B.to_device_rays(rays)
     gt = _gt_hits(b.case.tris, rays)
