@@ -46,7 +46,8 @@ __device__ __forceinline__ float loss_terms(const float* o, float y, float d, fl
 struct TcTrain {
   const int32_t* leaf;
   const int32_t* order;  // item -> ray (rays grouped by leaf); nullptr: item = ray
-  uint16_t* X16;      // [n][Kp]
+  uint16_t* X16;      // [Kp][ld] feature-major (one row per feature, items along it)
+  int64_t ld;         // row stride of X16 (items, rounded up to 64)
   uint16_t* H16;      // [n_hidden][n][W]
   float* O;           // [n][n_out]
   float* G;           // [n][n_out]

@@ -370,10 +370,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
     }
     __syncthreads();
     const int64_t grow = tile * kTcM + row;  // global item of this thread's row
-    uint32_t* x16 = nullptr;                 // training: this row's stored features
+    uint16_t* x16 = nullptr;                 // training: this item's column of the stored features
     if constexpr (MODE == 2) {
-      if (grow < n_items) x16 = reinterpret_cast<uint32_t*>(a.tr.X16 + grow * Kp);
+      if (grow < n_items) x16 = a.tr.X16 + grow;
     }
+    const int64_t xld = MODE == 2 ? a.tr.ld : 0;
+    // feature-major store of two 16-bit features (one packed word) at feature k2
+    auto store_x = [&](int k2, uint32_t w) {
+      x16[int64_t(k2) * xld] = uint16_t(w & 0xffffu);
+      x16[int64_t(k2 + 1) * xld] = uint16_t(w >> 16);
+    };
 
     // ---- encode into TMEM: warp w owns rows 32 (w % 4) + lane and samples
     // w / 4, w / 4 + 8, ...; lanes = consecutive rows (consecutive queue items).
@@ -402,7 +408,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
           uint32_t pk[4];
 #pragma unroll
           for (int i = 0; i < 4; ++i) pk[i] = pack2<BF16>(v[2 * i], v[2 * i + 1]);
-          if (x16) *reinterpret_cast<uint4*>(x16 + col0 + (l0 * F) / 2) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+          if (x16) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) store_x(2 * int(col0) + l0 * F + 2 * i, pk[i]);
+          }
           __syncwarp();
           tmem_st4(t_a + col0 + uint32_t(l0 * F) / 2u, pk);
         }
@@ -420,7 +429,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
           for (int i = 0; i < F / 2; ++i) pk[i] = pack2<BF16>(v[2 * i], v[2 * i + 1]);
           if (x16) {
 #pragma unroll
-            for (int i = 0; i < F / 2; ++i) x16[col0 + (l * F) / 2 + i] = pk[i];
+            for (int i = 0; i < F / 2; ++i) store_x(2 * int(col0) + l * F + 2 * i, pk[i]);
           }
           __syncwarp();
           tmem_st_cols<F / 2>(t_a + col0 + uint32_t(l * F) / 2u, pk);
@@ -433,7 +442,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
             encode_level<T, F>(a.gp, table, l + 1, x, y, z, v + 1);
           }
           const uint32_t w = pack2<BF16>(v[0], v[1]);
-          if (x16) x16[col0 + l / 2] = w;
+          if (x16) store_x(2 * int(col0) + l, w);
           __syncwarp();
           tmem_st1(t_a + col0 + uint32_t(l) / 2u, w);
         }
@@ -443,7 +452,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
       if (cgroup == 0) {
         for (int c = K / 2; c < Kp / 2; ++c) {
           tmem_st1(t_a + uint32_t(c), 0u);
-          if (x16) x16[c] = 0u;
+          if (x16) store_x(2 * c, 0u);
         }
       }
     }

@@ -482,7 +482,9 @@ struct TrainWs {
   uint8_t* hit;
   float *depth, *nx, *ny, *nz;
   TrainBuffers buf;
-  uint16_t *X16, *H16, *dZ16;  // tensor-core path: 16-bit operands
+  uint16_t *X16, *H16, *dZ16;  // tensor-core path: 16-bit operands (X16 feature-major)
+  uint16_t* dZT0;              // first layer's dZ, neuron-major
+  int64_t ld;                  // row stride of X16 and dZT0
   int32_t *counts, *cursor, *order;  // rays grouped by trained leaf (training step)
   size_t bytes;
 };
@@ -518,7 +520,9 @@ TrainWs carve_train(void* base, const nbvh_model_desc* d, int64_t n, int32_t n_l
   w.buf.loss_seg = reinterpret_cast<float*>(take(4 * N));
   w.buf.dZ = reinterpret_cast<float*>(take(4 * nh * N * Wd));
   const size_t Kp = (K + 15) & ~size_t(15);
-  w.X16 = reinterpret_cast<uint16_t*>(take(2 * N * Kp));
+  w.ld = int64_t((N + 63) & ~size_t(63));
+  w.X16 = reinterpret_cast<uint16_t*>(take(2 * size_t(w.ld) * Kp));
+  w.dZT0 = reinterpret_cast<uint16_t*>(take(2 * size_t(w.ld) * Wd));
   w.H16 = reinterpret_cast<uint16_t*>(take(2 * nh * N * Wd));
   w.dZ16 = reinterpret_cast<uint16_t*>(take(2 * nh * N * Wd));
   if (n_leaves > 0) {
@@ -645,13 +649,49 @@ cudaError_t launch_bwd_tc(const nbvh_model_desc* d, const TcBwdArgs& a, cudaStre
 }
 
 template <typename TZ, typename TA>
-cudaError_t launch_wg_any(const TZ* dZ, int ldz, int n_o, const TA* A, int lda, int n_j, int64_t n, float* dW,
-                          float* db, cudaStream_t s) {
-  dim3 grid(unsigned((n_o + kWgT - 1) / kWgT), unsigned((n_j + kWgT - 1) / kWgT),
-            unsigned((n + kWgChunk2 - 1) / kWgChunk2));
-  weight_grad_tiled<TZ, TA><<<grid, 256, 0, s>>>(dZ, ldz, n_o, A, lda, n_j, n, dW, db);
+cudaError_t launch_wg_strided(const TZ* dZ, int64_t zi, int64_t zo, int n_o, const TA* A, int64_t ai, int64_t aj,
+                              int n_j, int64_t n, float* dW, float* db, cudaStream_t s) {
+  // split the batch so the launch has ~4 blocks per SM whatever the output size
+  const int64_t gxy = int64_t((n_o + kWgT - 1) / kWgT) * ((n_j + kWgT - 1) / kWgT);
+  const int64_t want = int64_t(sm_count()) * 4;
+  int64_t chunk = (n * gxy + want - 1) / want;
+  chunk = ((chunk + kWgRows - 1) / kWgRows) * kWgRows;
+  if (chunk < 256) chunk = 256;
+  dim3 grid(unsigned((n_o + kWgT - 1) / kWgT), unsigned((n_j + kWgT - 1) / kWgT), unsigned((n + chunk - 1) / chunk));
+  weight_grad_tiled<TZ, TA><<<grid, 256, 0, s>>>(dZ, zi, zo, n_o, A, ai, aj, n_j, n, chunk, dW, db);
   count_launches(1);
   return cudaGetLastError();
+}
+
+template <typename TZ, typename TA>
+cudaError_t launch_wg_any(const TZ* dZ, int ldz, int n_o, const TA* A, int lda, int n_j, int64_t n, float* dW,
+                          float* db, cudaStream_t s) {
+  return launch_wg_strided<TZ, TA>(dZ, ldz, 1, n_o, A, lda, 1, n_j, n, dW, db, s);
+}
+
+template <int W>
+cudaError_t launch_wg_tc_w(bool bf16, const WgTcArgs& a, cudaStream_t s) {
+  const uint32_t smem = wg_tc_smem(a.Kp, W);
+  if (smem > 227 * 1024 || wg_tc_tiles(a.Kp) * W > 512) return cudaErrorInvalidConfiguration;
+  auto kern = bf16 ? weight_grad_tc<W, true> : weight_grad_tc<W, false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  const int64_t chunks = (a.n + kWgTcItems - 1) / kWgTcItems;
+  int64_t grid = sm_count();
+  if (chunks < grid) grid = chunks;
+  if (grid < 1) return cudaSuccess;
+  kern<<<unsigned(grid), kWgTcThreads, smem, s>>>(a);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wg_tc(bool bf16, int W, const WgTcArgs& a, cudaStream_t s) {
+  switch (W) {
+    case 32: return launch_wg_tc_w<32>(bf16, a, s);
+    case 64: return launch_wg_tc_w<64>(bf16, a, s);
+    case 128: return launch_wg_tc_w<128>(bf16, a, s);
+  }
+  return cudaErrorInvalidConfiguration;
 }
 
 // Weight gradients of the tensor-core path from its 16-bit stored operands.
@@ -664,7 +704,12 @@ cudaError_t weight_grads_16(const nbvh_model_desc* d, const TrainWs& w, const fl
   const T16* H = reinterpret_cast<const T16*>(w.H16);
   const T16* Z = reinterpret_cast<const T16*>(w.dZ16);
   size_t off = 0;
-  cudaError_t e = launch_wg_any<T16, T16>(Z, Wd, Wd, X, Kp, K, n, grad_mlp, grad_mlp + size_t(Wd) * K, s);
+  // first layer: tensor cores (both operands stored with the batch contiguous);
+  // shapes beyond their TMEM/shared-memory budget use the CUDA-core reduction
+  WgTcArgs ta{w.X16, w.dZT0, n, w.ld, K, Kp, grad_mlp, grad_mlp + size_t(Wd) * K};
+  cudaError_t e = launch_wg_tc(std::is_same<T16, __nv_bfloat16>::value, Wd, ta, s);
+  if (e == cudaErrorInvalidConfiguration)
+    e = launch_wg_strided<T16, T16>(Z, Wd, 1, Wd, X, 1, w.ld, K, n, grad_mlp, grad_mlp + size_t(Wd) * K, s);
   off += size_t(Wd) * K + Wd;
   for (int h = 1; h < nh && e == cudaSuccess; ++h) {
     e = launch_wg_any<T16, T16>(Z + size_t(h) * n * Wd, Wd, Wd, H + size_t(h - 1) * n * Wd, Wd, Wd, n,
@@ -806,6 +851,7 @@ nbvh_status forward_train_impl(const nbvh_model_desc* desc, const void* table, c
     a.tr.leaf = leaf;
     a.tr.order = order;
     a.tr.X16 = w.X16;
+    a.tr.ld = w.ld;
     a.tr.H16 = w.H16;
     a.tr.O = w.buf.O;
     a.tr.G = w.buf.G;
@@ -860,6 +906,8 @@ nbvh_status backward_impl(const nbvh_model_desc* desc, const void* table, const 
     b.G = grad_out ? grad_out : w.buf.G;
     b.H16 = w.H16;
     b.dZ16 = w.dZ16;
+    b.dZT0 = w.dZT0;
+    b.ld = w.ld;
     b.grad_table = grad_table;
     cudaError_t e = launch_bwd_tc(desc, b, s);
     if (e != cudaSuccess) return status_of(e);

@@ -7,6 +7,8 @@
 
 namespace nbvh {
 
+constexpr int kAggMaxRes = 64;  // warp aggregation of scatter atomics up to this level resolution
+
 struct TcBwdArgs {
   GridParams gp;
   const float* mlp;
@@ -20,6 +22,8 @@ struct TcBwdArgs {
   const float* G;         // [n][n_out] dL/d(raw), times the loss scale (by item)
   const uint16_t* H16;    // [n_hidden][n][W] hidden activations of the forward
   uint16_t* dZ16;         // [n_hidden][n][W] pre-activation gradients (out)
+  uint16_t* dZT0;         // [W][ld] the first layer's dZ again, neuron-major (out)
+  int64_t ld;
   float* grad_table;      // FP32 [entries][F]
 };
 
@@ -192,6 +196,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) train_backward_tc(TcBwdArgs a) 
           uint32_t* zdst = reinterpret_cast<uint32_t*>(a.dZ16 + (size_t(h) * size_t(a.n) + size_t(grow)) * W + c0);
 #pragma unroll
           for (int i = 0; i < kCols / 2; ++i) zdst[i] = pk[i];
+          if (h == 0) {
+#pragma unroll
+            for (int i = 0; i < kCols / 2; ++i) {
+              a.dZT0[int64_t(c0 + 2 * i) * a.ld + grow] = uint16_t(pk[i] & 0xffffu);
+              a.dZT0[int64_t(c0 + 2 * i + 1) * a.ld + grow] = uint16_t(pk[i] >> 16);
+            }
+          }
         }
         tmem_st_wait();
       }
@@ -252,10 +263,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) train_backward_tc(TcBwdArgs a) 
             level_corners(a.gp, l, x, y, z, cr);
             float* gt = a.grad_table + a.gp.offset[l] * F;
 #pragma unroll
+            // coarse levels only: there a leaf's rays share entries; finer
+            // levels skip the match instruction
+            const bool coarse = a.gp.res[l] <= kAggMaxRes;
             for (int q = 0; q < 8; ++q) {
               const uint32_t key = valid ? cr.idx[q] : 0xffffffffu;
               int same = 0;
-              __match_all_sync(0xffffffffu, key, &same);
+              if (coarse) __match_all_sync(0xffffffffu, key, &same);
               float v[F];
 #pragma unroll
               for (int ff = 0; ff < F; ++ff) v[ff] = valid ? cr.w[q] * gx[j + ff] : 0.0f;
@@ -319,15 +333,18 @@ constexpr int kWgT = 64;
 constexpr int kWgRows = 32;
 constexpr int kWgChunk2 = 4096;
 
+// Element (i, o) of dZ is dZ[i * zi + o * zo], element (i, j) of A is
+// A[i * ai + j * aj] (row-major or transposed storage).
 template <typename TZ, typename TA>
-__global__ void __launch_bounds__(256) weight_grad_tiled(const TZ* __restrict__ dZ, int ldz, int n_o,
-                                                         const TA* __restrict__ A, int lda, int n_j, int64_t n,
-                                                         float* __restrict__ dW, float* __restrict__ db) {
+__global__ void __launch_bounds__(256) weight_grad_tiled(const TZ* __restrict__ dZ, int64_t zi, int64_t zo, int n_o,
+                                                         const TA* __restrict__ A, int64_t ai, int64_t aj, int n_j,
+                                                         int64_t n, int64_t chunk, float* __restrict__ dW,
+                                                         float* __restrict__ db) {
   __shared__ __align__(16) float sz[kWgRows][kWgT];
   __shared__ __align__(16) float sa[kWgRows][kWgT];
   const int o0 = blockIdx.x * kWgT, j0 = blockIdx.y * kWgT;
-  const int64_t i0 = int64_t(blockIdx.z) * kWgChunk2;
-  const int64_t i1 = min(n, i0 + kWgChunk2);
+  const int64_t i0 = int64_t(blockIdx.z) * chunk;
+  const int64_t i1 = min(n, i0 + chunk);
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   float acc[4][4] = {};
   float bacc[4] = {0, 0, 0, 0};
@@ -335,8 +352,8 @@ __global__ void __launch_bounds__(256) weight_grad_tiled(const TZ* __restrict__ 
     for (int idx = threadIdx.x; idx < kWgRows * kWgT; idx += blockDim.x) {
       const int r = idx / kWgT, c = idx - r * kWgT;
       const int64_t i = ib + r;
-      sz[r][c] = (i < i1 && o0 + c < n_o) ? to_f(dZ[i * ldz + o0 + c]) : 0.0f;
-      sa[r][c] = (i < i1 && j0 + c < n_j) ? to_f(A[i * lda + j0 + c]) : 0.0f;
+      sz[r][c] = (i < i1 && o0 + c < n_o) ? to_f(dZ[i * zi + int64_t(o0 + c) * zo]) : 0.0f;
+      sa[r][c] = (i < i1 && j0 + c < n_j) ? to_f(A[i * ai + int64_t(j0 + c) * aj]) : 0.0f;
     }
     __syncthreads();
 #pragma unroll 8
@@ -363,6 +380,138 @@ __global__ void __launch_bounds__(256) weight_grad_tiled(const TZ* __restrict__ 
       if (j < n_j) atomicAdd(dW + size_t(o) * n_j + j, acc[p][q]);
     }
     if (blockIdx.y == 0 && tx == 0) atomicAdd(db + o, bacc[p]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// First-layer weight gradient on the tensor cores: dW0^T [Kp x W] =
+// X^T [Kp x n] * dZ0 [n x W], K = the batch, split over CTAs. Both operands are
+// stored with the batch contiguous (feature-major features, neuron-major dZ0),
+// so both tiles are K-major. Each CTA accumulates its 128-feature tiles in TMEM
+// over its chunks of 64 items, then adds them into the FP32 gradient.
+// ---------------------------------------------------------------------------
+struct WgTcArgs {
+  const uint16_t* XT;  // [Kp][ld]
+  const uint16_t* ZT;  // [W][ld]
+  int64_t n, ld;
+  int K, Kp;
+  float* dW;           // [W][K]
+  float* db;           // [W]
+};
+
+constexpr int kWgTcItems = 64;
+constexpr int kWgTcThreads = 256;
+
+__host__ __device__ inline int wg_tc_tiles(int Kp) { return (Kp + 127) / 128; }
+__host__ __device__ inline uint32_t wg_tc_smem(int Kp, int W) {
+  return uint32_t(wg_tc_tiles(Kp)) * 128 * kWgTcItems * 2 + uint32_t(W) * kWgTcItems * 2 + 128 + 128;
+}
+
+template <int W, bool BF16>
+__global__ void __launch_bounds__(kWgTcThreads, 1) weight_grad_tc(WgTcArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  const int tiles = wg_tc_tiles(a.Kp);
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + size_t(tiles) * 128 * kWgTcItems * 2;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sB + size_t(W) * kWgTcItems * 2);
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bar + 1);
+  const int64_t n_chunks = (a.n + kWgTcItems - 1) / kWgTcItems;
+  if (int64_t(blockIdx.x) >= n_chunks) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t ncols = 32;
+  while (ncols < uint32_t(tiles * W)) ncols <<= 1;
+  if (warp == 0) {
+    tmem_alloc(s_tmem, ncols);
+    tmem_relinquish();
+  }
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *s_tmem;
+  const uint32_t idesc = idesc_f16(BF16, 128, W);
+  float bsum = 0.0f;  // thread t < W: sum of dZ0 over its neuron
+  uint32_t phase = 0;
+  bool failed = false, first = true;
+  // 16-byte pieces of a [rows][64 items] tile into the K-major core-matrix layout
+  auto stage = [&](uint8_t* dst, const uint16_t* src, int rows, int valid_rows, int64_t c0) {
+    for (int p = threadIdx.x; p < rows * 8; p += blockDim.x) {
+      const int r = p >> 3, q = p & 7;
+      const int64_t col = c0 + 8 * q;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (r < valid_rows) {
+        const uint16_t* g = src + int64_t(r) * a.ld + col;
+        if (col + 8 <= a.n) {
+          v = *reinterpret_cast<const uint4*>(g);
+        } else {
+          uint16_t e[8];
+#pragma unroll
+          for (int t = 0; t < 8; ++t) e[t] = col + t < a.n ? g[t] : uint16_t(0);
+          v = make_uint4(e[0] | (uint32_t(e[1]) << 16), e[2] | (uint32_t(e[3]) << 16), e[4] | (uint32_t(e[5]) << 16),
+                         e[6] | (uint32_t(e[7]) << 16));
+        }
+      }
+      *reinterpret_cast<uint4*>(dst + op_offset(r, 8 * q, kWgTcItems)) = v;
+    }
+  };
+  for (int64_t c = blockIdx.x; c < n_chunks && !failed; c += gridDim.x) {
+    const int64_t c0 = c * kWgTcItems;
+    for (int t = 0; t < tiles; ++t)
+      stage(sA + size_t(t) * 128 * kWgTcItems * 2, a.XT + int64_t(t) * 128 * a.ld, 128, min(128, a.K - 128 * t), c0);
+    stage(sB, a.ZT, W, W, c0);
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (threadIdx.x < W) {
+      for (int q = 0; q < kWgTcItems; ++q) {
+        const uint16_t e = *reinterpret_cast<const uint16_t*>(sB + op_offset(threadIdx.x, q, kWgTcItems));
+        bsum += from16<BF16>(e);
+      }
+    }
+    if (threadIdx.x == 0) {
+      tc_fence_after();
+      const uint32_t sbo = uint32_t(kWgTcItems) * 16;
+      for (int t = 0; t < tiles; ++t) {
+        const uint32_t aa = smem_u32(sA + size_t(t) * 128 * kWgTcItems * 2);
+        for (int kk = 0; kk < kWgTcItems / 16; ++kk)
+          mma_f16(tmem + uint32_t(t * W), smem_desc(aa + kk * 256, 128, sbo), smem_desc(smem_u32(sB) + kk * 256, 128, sbo),
+                  idesc, (first && kk == 0) ? 0u : 1u);
+      }
+      mma_commit(bar);
+    }
+    first = false;
+    const bool ok = mbar_wait(bar, phase);
+    phase ^= 1u;
+    if (__syncthreads_or(!ok)) failed = true;
+    tc_fence_after();
+  }
+  if (!failed && warp < 4) {
+    const int q = warp;  // lane quarter
+    const uint32_t t_row = tmem + (uint32_t(q * 32) << 16);
+    for (int t = 0; t < tiles; ++t) {
+      const int m = 128 * t + 32 * q + lane;  // feature
+#pragma unroll
+      for (int c0 = 0; c0 < W; c0 += 16) {
+        float v[16];
+        tmem_ld16(t_row + uint32_t(t * W + c0), v);
+        tmem_ld_wait();
+        if (m < a.K) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) atomicAdd(a.dW + int64_t(c0 + i) * a.K + m, v[i]);
+        }
+      }
+    }
+  }
+  if (threadIdx.x < W && !failed) atomicAdd(a.db + threadIdx.x, bsum);
+  if (failed) set_status(NBVH_ERR_TIMEOUT);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, ncols);
   }
 }
 
