@@ -359,17 +359,28 @@ def encode(x, table, layout):
 # S4: MLP (Sec. 6: ReLU hidden layers; sigmoid on distance, linear normal)
 # ============================================================================
 
-def mlp_forward(feat, layers):
+def _same(a):
+    return a
+
+
+def mlp_forward(feat, layers, rnd=None):
     """ReLU hidden layers, linear last layer. ``layers`` = [(W [out,in], b)].
     Returns raw outputs [S, n_out] and the list of layer inputs (activations)
-    and pre-activations for the backward pass."""
-    h = np.asarray(feat, F64)
+    and pre-activations for the backward pass.
+
+    ``rnd``: optional rounding of the multiplication operands to a
+    half-precision type (Sec. 6 trains and infers in half precision): each
+    layer's input and weight matrix are rounded, products and sums stay exact
+    and the bias is added unrounded. The layer inputs returned are the rounded
+    ones."""
+    r = rnd or _same
+    h = r(np.asarray(feat, F64))
     acts, pre = [h], []
     for i, (W, b) in enumerate(layers):
-        z = h @ np.asarray(W, F64).T + np.asarray(b, F64)
+        z = h @ r(np.asarray(W, F64)).T + np.asarray(b, F64)
         pre.append(z)
         if i < len(layers) - 1:
-            h = np.maximum(z, 0.0)
+            h = r(np.maximum(z, 0.0))
             acts.append(h)
         else:
             h = z
@@ -705,16 +716,27 @@ def loss_grad(raw, y_hit, y_depth, y_normal, valid):
     return g * (v / nv)[:, None]
 
 
-def mlp_backward(g_out, acts, pre, layers):
-    """Backward of ``mlp_forward``: returns (dfeatures, [(dW, db)])."""
+def mlp_backward(g_out, acts, pre, layers, rnd=None, scale: float = 1.0):
+    """Backward of ``mlp_forward``: returns (dfeatures, [(dW, db)]).
+
+    ``rnd`` (half-precision operands, as in ``mlp_forward``): the gradient that
+    enters each product with a weight matrix is rounded, dL/d(raw) after
+    multiplication by the loss scale ``scale`` (a power of two) so that small
+    values keep their precision; the weights are rounded; the hidden layers'
+    weight gradients take the rounded dZ and the output layer's the unrounded
+    dL/d(raw). The ReLU mask is the stored activation's sign."""
+    r = rnd or _same
     grads = [None] * len(layers)
     g = np.asarray(g_out, F64)
-    for i in range(len(layers) - 1, -1, -1):
-        W = np.asarray(layers[i][0], F64)
-        grads[i] = (g.T @ acts[i], g.sum(0))
-        g = g @ W
+    last = len(layers) - 1
+    for i in range(last, -1, -1):
+        W = r(np.asarray(layers[i][0], F64))
+        gq = g if rnd is None else r(g * scale) / scale
+        gw = g if i == last else gq
+        grads[i] = (gw.T @ acts[i], gw.sum(0))
+        g = gq @ W
         if i > 0:
-            g = g * (pre[i - 1] > 0.0)
+            g = g * (acts[i] > 0.0)
     return g, grads
 
 
@@ -736,16 +758,18 @@ def encode_backward(x, g_feat, n_entries: int, n_features: int, layout):
 
 
 def forward_backward(o, d, t0, t1, valid, y_hit, y_depth, y_normal, table, layers, layout,
-                     centre, extent, n_samples: int):
+                     centre, extent, n_samples: int, rnd=None, scale: float = 1.0):
     """Loss of a batch of segments and its exact gradient with respect to every
-    table entry and MLP weight/bias. Returns (L, dtable, [(dW, db)], raw)."""
+    table entry and MLP weight/bias. Returns (L, dtable, [(dW, db)], raw).
+    ``rnd``/``scale``: half-precision MLP operands (``mlp_forward``,
+    ``mlp_backward``); the encoding and the table gradient stay exact."""
     p = sample_points(o, d, t0, t1, n_samples)
     x = normalize_points(p, centre, extent)
     feat = encode(x, table, layout)
-    raw, acts, pre = mlp_forward(feat, layers)
+    raw, acts, pre = mlp_forward(feat, layers, rnd)
     L, _ = loss(raw, y_hit, y_depth, y_normal, valid)
     g = loss_grad(raw, y_hit, y_depth, y_normal, valid)
-    g_feat, g_layers = mlp_backward(g, acts, pre, layers)
+    g_feat, g_layers = mlp_backward(g, acts, pre, layers, rnd, scale)
     tab = np.asarray(table)
     g_tab = encode_backward(x, g_feat, tab.shape[0], tab.shape[1], layout)
     return L, g_tab, g_layers, raw

@@ -273,6 +273,41 @@ def test_mlp_forward_against_loops():
         assert np.allclose(raw[s], h, rtol=1e-14, atol=1e-14)
 
 
+def test_mlp_half_precision_operands_worked_example():
+    """Operand rounding of the half-precision MLP (Sec. 6), with rounding to
+    integers so every step can be followed by hand. Inputs x = (0.4, 1.6);
+    W0 rows (1.4, 0.6), (-0.7, 2.2), (0.2, -1.4), (0.1, 0.1), b0 = (0.25,
+    -0.3, 0.5, 0.3); Wo = (0.7, -1.2, 0.9, 2.6), bo = 0.1.
+    Forward: x -> (0, 2); W0 -> rows (1, 1), (-1, 2), (0, -1), (0, 0);
+    z0 = (2.25, 3.7, -1.5, 0.3); h0 = relu -> rounded (2, 4, 0, 0);
+    Wo -> (1, -1, 1, 3); raw = 2 - 4 + 0.1 = -1.9.
+    Backward with dL/d(raw) = 0.3 and loss scale 4: the output layer's
+    weight gradient takes the unrounded 0.3: dWo = 0.3 h0 = (0.6, 1.2, 0, 0),
+    dbo = 0.3; the product operand is round(0.3 * 4) / 4 = 0.25, so
+    dH0 = 0.25 (1, -1, 1, 3), masked by the stored activations' sign (the
+    fourth unit had z0 > 0 but rounded to 0): dZ0 = (0.25, -0.25, 0, 0),
+    exact under rounding of dZ0 * 4; dW0 = dZ0 x0^T with x0 = (0, 2);
+    dfeatures = dZ0 W0 = (0.5, -0.25)."""
+    feat = np.array([[0.4, 1.6]])
+    layers = [(np.array([[1.4, 0.6], [-0.7, 2.2], [0.2, -1.4], [0.1, 0.1]]), np.array([0.25, -0.3, 0.5, 0.3])),
+              (np.array([[0.7, -1.2, 0.9, 2.6]]), np.array([0.1]))]
+    raw, acts, pre = O.mlp_forward(feat, layers, rnd=np.round)
+    assert np.allclose(raw, [[-1.9]], rtol=0, atol=1e-15)
+    assert np.array_equal(acts[0], [[0.0, 2.0]]) and np.array_equal(acts[1], [[2.0, 4.0, 0.0, 0.0]])
+    g_feat, grads = O.mlp_backward(np.array([[0.3]]), acts, pre, layers, rnd=np.round, scale=4.0)
+    (dW0, db0), (dWo, dbo) = grads
+    assert np.allclose(dWo, [[0.6, 1.2, 0.0, 0.0]], rtol=0, atol=1e-15) and np.allclose(dbo, [0.3], rtol=0, atol=1e-15)
+    assert np.array_equal(dW0, [[0.0, 0.5], [0.0, -0.5], [0.0, 0.0], [0.0, 0.0]])
+    assert np.array_equal(db0, [0.25, -0.25, 0.0, 0.0])
+    assert np.array_equal(g_feat, [[0.5, -0.25]])
+    # without rounding the same call is the exact backward (mask = pre-activation sign)
+    raw1, acts1, pre1 = O.mlp_forward(feat, layers)
+    g1, _ = O.mlp_backward(np.array([[0.3]]), acts1, pre1, layers)
+    W0, Wo = layers[0][0], layers[1][0]
+    z0 = W0 @ feat[0] + layers[0][1]
+    assert np.allclose(g1[0], ((0.3 * Wo[0]) * (z0 > 0)) @ W0, rtol=1e-15, atol=1e-15)
+
+
 def test_sigmoid_softplus_closed_forms():
     assert O.sigmoid(0.0) == 0.5
     assert abs(O.sigmoid(np.log(3.0)) - 0.75) < 1e-15
