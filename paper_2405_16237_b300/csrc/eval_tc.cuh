@@ -526,6 +526,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
         tmem_ld16(t_row, v);
         tmem_ld_wait();
         float raw[8];
+#pragma unroll
         for (int j = 0; j < 8; ++j) raw[j] = j < n_out ? v[j] + __ldg(bo + j) : 0.0f;
         const int ray = sray[row];
         if constexpr (MODE == 1) {
@@ -540,15 +541,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
               term = loss_terms(raw, float(a.tr.lab.hit[ray]), a.tr.lab.depth[ray], a.tr.lab.nx[ray],
                                 a.tr.lab.ny[ray], a.tr.lab.nz[ray], ls * inv_valid, g);
             }
-            for (int j = 0; j < n_out; ++j) a.tr.O[grow * n_out + j] = raw[j];
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              if (j < n_out) a.tr.O[grow * n_out + j] = raw[j];
             if (a.tr.lab.hit) {
-              for (int j = 0; j < n_out; ++j) a.tr.G[grow * n_out + j] = g[j];
+#pragma unroll
+              for (int j = 0; j < 8; ++j)
+                if (j < n_out) a.tr.G[grow * n_out + j] = g[j];
               a.tr.loss_seg[grow] = term;
             }
           }
         } else if (ray >= 0) {
           const int64_t i = tile * kTcM + row;
-          for (int j = 0; j < n_out; ++j) a.out[i * n_out + j] = raw[j];
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            if (j < n_out) a.out[i * n_out + j] = raw[j];
         }
       }
       tc_fence_before();

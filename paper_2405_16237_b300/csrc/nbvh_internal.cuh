@@ -158,14 +158,24 @@ struct EntryLoad<__nv_bfloat16, F> {
 // ---------------------------------------------------------------------------
 // Plain FP32 form (tensor-core path: its FP16/BF16 features round far above
 // the position error).
-__device__ __forceinline__ void sample_point(const GridParams& gp, float ox, float oy, float oz,
-                                             float dx, float dy, float dz, float t0, float t1, int k,
-                                             float& x, float& y, float& z) {
-  const float u = (static_cast<float>(k) + 0.5f) / static_cast<float>(gp.n_samples);
+__device__ __forceinline__ float sample_u(int k, int n_samples) {
+  return (static_cast<float>(k) + 0.5f) / static_cast<float>(n_samples);
+}
+
+// Sample at fraction u = sample_u(k, N) of the segment.
+__device__ __forceinline__ void sample_point_u(const GridParams& gp, float ox, float oy, float oz, float dx,
+                                               float dy, float dz, float t0, float t1, float u, float& x,
+                                               float& y, float& z) {
   const float t = t0 + u * (t1 - t0);
   x = __saturatef((ox + t * dx - gp.centre[0]) * gp.inv_extent + 0.5f);
   y = __saturatef((oy + t * dy - gp.centre[1]) * gp.inv_extent + 0.5f);
   z = __saturatef((oz + t * dz - gp.centre[2]) * gp.inv_extent + 0.5f);
+}
+
+__device__ __forceinline__ void sample_point(const GridParams& gp, float ox, float oy, float oz,
+                                             float dx, float dy, float dz, float t0, float t1, int k,
+                                             float& x, float& y, float& z) {
+  sample_point_u(gp, ox, oy, oz, dx, dy, dz, t0, t1, sample_u(k, gp.n_samples), x, y, z);
 }
 
 // Float-float form (FP32 path): the finest level multiplies a position error by
@@ -238,6 +248,17 @@ __device__ __forceinline__ void axis_cell(FF x, int N, int& c, float& f) {
   if (fl < 0.0f) fl = 0.0f;
   c = static_cast<int>(fl);
   f = __fadd_rn(__fsub_rn(p.hi, fl), p.lo);  // p.hi - fl is exact
+}
+
+// Table entry of grid vertex (vx, vy, vz) of level l, vertex coordinates in
+// [0, N]: the mapping level_corners applies to a cell's eight corners.
+__device__ __forceinline__ uint32_t vertex_index(const GridParams& gp, int l, uint32_t vx, uint32_t vy,
+                                                 uint32_t vz) {
+  if (gp.dense[l]) {
+    const uint32_t n1 = static_cast<uint32_t>(gp.res[l]) + 1u;
+    return vx + vy * n1 + vz * n1 * n1;
+  }
+  return (vx ^ (vy * kHashP1) ^ (vz * kHashP2)) & gp.hash_mask;
 }
 
 template <typename P>

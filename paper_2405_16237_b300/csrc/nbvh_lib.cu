@@ -1,5 +1,6 @@
 // Device entry points of the C ABI (include/nbvh.h). Single CUDA translation
 // unit: the kernels live in the included headers.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -618,11 +619,18 @@ cudaError_t launch_bwd_tc_fw(bool bf16, const TcBwdArgs& a, cudaStream_t s) {
   auto kern = bf16 ? train_backward_tc<F, W, true> : train_backward_tc<F, W, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(lay.total));
   if (e != cudaSuccess) return e;
+  constexpr int threads = bwd_threads<W>();
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, lay.total);
+  if (e != cudaSuccess) return e;
+  // co-resident CTAs must fit the SM's 512 TMEM columns together
+  per_sm = std::min(per_sm, int(512 / lay.ncols));
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const int64_t tiles = (a.n + kTcM - 1) / kTcM;
-  int64_t grid = sm_count();
+  int64_t grid = int64_t(sm_count()) * per_sm;
   if (tiles < grid) grid = tiles;
   if (grid < 1) return cudaSuccess;
-  kern<<<unsigned(grid), kTcThreads, lay.total, s>>>(a);
+  kern<<<unsigned(grid), threads, lay.total, s>>>(a);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -33,7 +33,7 @@ struct TcBwdArgs {
 struct TcBwdLayout {
   int Kp;
   uint32_t col_a, col_x, ncols;
-  uint32_t w0t_off, wht_off, wot_off, row_off, bar_off, total;
+  uint32_t w0t_off, wht_off, wot_off, row_off, u_off, bar_off, total;
 };
 
 __host__ __device__ inline TcBwdLayout tc_bwd_layout(int K, int W, int n_hidden) {
@@ -53,10 +53,81 @@ __host__ __device__ inline TcBwdLayout tc_bwd_layout(int K, int W, int n_hidden)
   L.w0t_off = take(uint32_t(L.Kp) * W * 2);
   L.wht_off = take(uint32_t(n_hidden - 1) * W * W * 2);
   L.wot_off = take(uint32_t(W) * 16 * 2);
-  L.row_off = take(kTcM * 12);
+  L.row_off = take(kTcM * 36);  // ray index, t0, t1, origin, direction per row
+  L.u_off = take(NBVH_MAX_SAMPLES * 4);
   L.bar_off = take(64);
   L.total = off + 128;
   return L;
+}
+
+// Threads of the backward kernel: 512 lets two CTAs share an SM (2 x 256 TMEM
+// columns) so one CTA's scatter overlaps the other's MMA chain; W = 128 needs
+// 512 columns and runs one 1024-thread CTA per SM.
+template <int W>
+__host__ __device__ constexpr int bwd_threads() {
+  return W >= 128 ? 1024 : 512;
+}
+
+// Level-major dL/dfeatures chunks: the dX MMA takes W0's rows permuted so one
+// level's N*F features are adjacent and a 128-column chunk holds whole levels.
+// The scatter then walks each ray through one level. Up to two features.
+__host__ __device__ inline bool bwd_level_major(int n_samples, int F) {
+  const int nf = n_samples * F;
+  return F <= 2 && nf % 16 == 0 && 128 % nf == 0;
+}
+
+// Adds F gradient values to an FP32 table entry (vector reductions where the
+// entry width allows them).
+template <int F>
+__device__ __forceinline__ void add_entry(float* dst, const float* v) {
+  if constexpr (F == 2) {
+    atomicAdd(reinterpret_cast<float2*>(dst), make_float2(v[0], v[1]));
+  } else if constexpr (F % 4 == 0) {
+#pragma unroll
+    for (int ff = 0; ff < F; ff += 4)
+      atomicAdd(reinterpret_cast<float4*>(dst + ff), make_float4(v[ff], v[ff + 1], v[ff + 2], v[ff + 3]));
+  } else {
+#pragma unroll
+    for (int ff = 0; ff < F; ++ff) atomicAdd(dst + ff, v[ff]);
+  }
+}
+
+// Moves the eight corner sums of a cell to the cell d steps along one axis
+// (BIT = 1, 2, 4 for x, y, z): shared vertices keep their sums, the others
+// (already added to the table) restart at zero.
+template <int F, int BIT>
+__device__ __forceinline__ void shift_corners(float (&acc)[8][F], int d) {
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    if (q & BIT) continue;
+#pragma unroll
+    for (int ff = 0; ff < F; ++ff) {
+      const float a0 = acc[q][ff], a1 = acc[q | BIT][ff];
+      acc[q][ff] = d == 0 ? a0 : (d == 1 ? a1 : 0.0f);
+      acc[q | BIT][ff] = d == 0 ? a1 : (d == -1 ? a0 : 0.0f);
+    }
+  }
+}
+
+// Adds the corner values v of a cell vertex (table entry key; 0xffffffff: none)
+// to the table; when the whole warp holds the same key (coarse levels), one
+// lane adds the warp's sum.
+template <int F>
+__device__ __forceinline__ void add_vertex_warp(float* gt, uint32_t key, float* v, bool aggregate, int lane) {
+  int same = 0;
+  if (aggregate) __match_all_sync(0xffffffffu, key, &same);
+  if (same) {
+    if (key != 0xffffffffu) {
+#pragma unroll
+      for (int ff = 0; ff < F; ++ff) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[ff] += __shfl_xor_sync(0xffffffffu, v[ff], o);
+      }
+      if (lane == 0) add_entry<F>(gt + size_t(key) * F, v);
+    }
+  } else if (key != 0xffffffffu) {
+    add_entry<F>(gt + size_t(key) * F, v);
+  }
 }
 
 template <bool BF16>
@@ -69,22 +140,27 @@ __device__ __forceinline__ float from16(uint16_t v) {
 }
 
 template <int F, int W, bool BF16>
-__global__ void __launch_bounds__(kTcThreads, 1) train_backward_tc(TcBwdArgs a) {
+__global__ void __launch_bounds__(bwd_threads<W>(), 1024 / bwd_threads<W>()) train_backward_tc(TcBwdArgs a) {
   using OT = OpType<BF16>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   const int K = a.gp.n_inputs;
   const int L = a.gp.n_levels;
+  const int NS = a.gp.n_samples;
   const int nh = a.n_hidden;
   const int n_out = a.n_out;
   const TcBwdLayout lay = tc_bwd_layout(K, W, nh);
   const int Kp = lay.Kp;
+  const bool lmaj = bwd_level_major(NS, F);
   uint8_t* sW0t = smem + lay.w0t_off;
   uint8_t* sWht = smem + lay.wht_off;
   uint8_t* sWot = smem + lay.wot_off;
   int* sray = reinterpret_cast<int*>(smem + lay.row_off);
   float* st0 = reinterpret_cast<float*>(sray + kTcM);
   float* st1 = st0 + kTcM;
+  float* sro = st1 + kTcM;       // [3][kTcM] ray origins
+  float* srd = sro + 3 * kTcM;   // [3][kTcM] ray directions
+  float* su = reinterpret_cast<float*>(smem + lay.u_off);  // sample fractions
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + lay.bar_off);
   uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + lay.bar_off + 8);
 
@@ -100,11 +176,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) train_backward_tc(TcBwdArgs a) 
     mbar_init(bar, 1);
     fence_mbar_init();
   }
+  if (threadIdx.x < NS) su[threadIdx.x] = sample_u(threadIdx.x, NS);
   // B operands (K-major, rows = the MMA's N): W0^T [Kp][W], W_h^T [W][W], Wo^T [W][16]
   const float* W0 = a.mlp;
   for (int i = threadIdx.x; i < Kp * W; i += blockDim.x) {
     const int r = i / W, k = i - r * W;
-    const float v = r < K ? __ldg(W0 + size_t(k) * K + r) : 0.0f;
+    int f = r;  // feature of row r: input order k*L*F + l*F + f, or level-major l*N*F + k*F + f
+    if (lmaj && r < K) {
+      const int nf = NS * F;
+      const int l = r / nf, rem = r - l * nf;
+      f = (rem / F) * (L * F) + l * F + rem % F;
+    }
+    const float v = r < K ? __ldg(W0 + size_t(k) * K + f) : 0.0f;
     *reinterpret_cast<typename OT::T*>(sW0t + op_offset(r, k, W)) = OT::one(v);
   }
   const float* p = W0 + size_t(W) * K + W;
@@ -129,8 +212,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) train_backward_tc(TcBwdArgs a) 
 
   const int quarter = warp & 3;
   const int cgroup = warp >> 2;
-  constexpr int kGroups = kTcThreads / 128;
+  constexpr int kGroups = bwd_threads<W>() / 128;
   constexpr int kCols = W / kGroups;
+  static_assert(kCols % 8 == 0, "16-byte activation loads");
   const int row = quarter * 32 + lane;
   const uint32_t t_row = tmem + (uint32_t(quarter * 32) << 16);
   uint32_t phase = 0;
@@ -144,6 +228,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) train_backward_tc(TcBwdArgs a) 
       sray[threadIdx.x] = v ? r : -1;
       st0[threadIdx.x] = v ? a.t0[r] : 0.0f;
       st1[threadIdx.x] = v ? a.t1[r] : 0.0f;
+      sro[threadIdx.x] = v ? a.rays.ox[r] : 0.0f;
+      sro[kTcM + threadIdx.x] = v ? a.rays.oy[r] : 0.0f;
+      sro[2 * kTcM + threadIdx.x] = v ? a.rays.oz[r] : 0.0f;
+      srd[threadIdx.x] = v ? a.rays.dx[r] : 0.0f;
+      srd[kTcM + threadIdx.x] = v ? a.rays.dy[r] : 0.0f;
+      srd[2 * kTcM + threadIdx.x] = v ? a.rays.dz[r] : 0.0f;
     }
     __syncthreads();
     const int64_t grow = tile * kTcM + row;
@@ -152,8 +242,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) train_backward_tc(TcBwdArgs a) 
       float g[16];
 #pragma unroll
       for (int j = 0; j < 16; ++j) g[j] = 0.0f;
-      if (grow < a.n)
-        for (int j = 0; j < n_out; ++j) g[j] = a.G[grow * n_out + j];
+      if (grow < a.n) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if (j < n_out) g[j] = a.G[grow * n_out + j];
+      }
       uint32_t pk[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) pk[j] = pack2<BF16>(g[2 * j], g[2 * j + 1]);
@@ -182,9 +275,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) train_backward_tc(TcBwdArgs a) 
         const int c0 = cgroup * kCols;
         uint32_t pk[kCols / 2];
         if (grow < a.n) {
-          const uint16_t* hrow = a.H16 + (size_t(h) * size_t(a.n) + size_t(grow)) * W + c0;
+          const uint4* hrow = reinterpret_cast<const uint4*>(a.H16 + (size_t(h) * size_t(a.n) + size_t(grow)) * W + c0);
 #pragma unroll
-          for (int i = 0; i < kCols; ++i) v[i] = from16<BF16>(hrow[i]) > 0.0f ? v[i] : 0.0f;
+          for (int q = 0; q < kCols / 8; ++q) {
+            const uint4 hv = __ldg(hrow + q);
+            const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const float hf = from16<BF16>(uint16_t(hw[i >> 1] >> (16 * (i & 1))));
+              v[8 * q + i] = hf > 0.0f ? v[8 * q + i] : 0.0f;
+            }
+          }
         } else {
 #pragma unroll
           for (int i = 0; i < kCols; ++i) v[i] = 0.0f;
@@ -220,6 +321,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) train_backward_tc(TcBwdArgs a) 
         continue;
       }
       // dL/dfeatures = dZ0 W0, 128 features at a time, scattered into the table gradient
+      const int ray = sray[row];
+      const bool valid = ray >= 0;
       for (int c0 = 0; c0 < Kp && !failed; c0 += 128) {
         const int cw = min(128, Kp - c0);
         if (threadIdx.x == 0) {
@@ -237,70 +340,114 @@ __global__ void __launch_bounds__(kTcThreads, 1) train_backward_tc(TcBwdArgs a) 
           break;
         }
         tc_fence_after();
-        if (cgroup * 16 < cw) {
-          float gx[16];
-          tmem_ld16(t_row + lay.col_x + uint32_t(cgroup * 16), gx);
-          tmem_ld_wait();
-          // Whole warps run this loop (lanes = 32 rows, grouped by leaf in the
-          // training step): when all lanes hit the same entry (coarse levels)
-          // the warp adds one sum instead of 32 atomics.
-          const int ray = sray[row];
-          const bool valid = ray >= 0;
-          int kprev = -1;
-          float x = 0.0f, y = 0.0f, z = 0.0f;
-          for (int j = 0; j < 16; j += F) {
-            const int f = c0 + cgroup * 16 + j;
-            if (f >= K) break;
-            const int k = f / (L * F);
-            const int l = (f / F) % L;
-            if (k != kprev) {
-              if (valid)
-                sample_point(a.gp, a.rays.ox[ray], a.rays.oy[ray], a.rays.oz[ray], a.rays.dx[ray],
-                             a.rays.dy[ray], a.rays.dz[ray], st0[row], st1[row], k, x, y, z);
-              kprev = k;
-            }
-            Corners cr;
-            level_corners(a.gp, l, x, y, z, cr);
-            float* gt = a.grad_table + a.gp.offset[l] * F;
+        if constexpr (F <= 2) {
+          if (lmaj) {
+            // Each warp takes one level of the chunk for its 32 rays and walks
+            // the samples in order along the ray. The eight corner sums of the
+            // current cell stay in registers; when the ray moves to another
+            // cell, the vertices the two cells do not share go to the table
+            // and the shared ones carry over. A level with c cells along the
+            // ray costs about 4c + 4 table updates instead of 8 per sample.
+            const int nf = NS * F;
+            constexpr int SP = 8 / F;  // samples per 8-column TMEM load
+            for (int li = cgroup; li < cw / nf; li += kGroups) {
+              const int l = c0 / nf + li;
+              const int N = a.gp.res[l];
+              float* gt = a.grad_table + a.gp.offset[l] * F;
+              float acc[8][F];
 #pragma unroll
-            // coarse levels only: there a leaf's rays share entries; finer
-            // levels skip the match instruction
-            const bool coarse = a.gp.res[l] <= kAggMaxRes;
-            for (int q = 0; q < 8; ++q) {
-              const uint32_t key = valid ? cr.idx[q] : 0xffffffffu;
-              int same = 0;
-              if (coarse) __match_all_sync(0xffffffffu, key, &same);
-              float v[F];
+              for (int q = 0; q < 8; ++q) {
 #pragma unroll
-              for (int ff = 0; ff < F; ++ff) v[ff] = valid ? cr.w[q] * gx[j + ff] : 0.0f;
-              if (same) {
-                if (key != 0xffffffffu) {
+                for (int ff = 0; ff < F; ++ff) acc[q][ff] = 0.0f;
+              }
+              int ccx = -1, ccy = 0, ccz = 0;  // current cell (none yet: ccx < 0)
+              for (int s0 = 0; s0 < NS; s0 += SP) {
+                float g8[8];
+                tmem_ld8(t_row + lay.col_x + uint32_t(li * nf + s0 * F), g8);
+                tmem_ld_wait();
+                if (!valid) continue;
 #pragma unroll
-                  for (int ff = 0; ff < F; ++ff) {
+                for (int si = 0; si < SP; ++si) {
+                  float x, y, z;
+                  sample_point_u(a.gp, sro[row], sro[kTcM + row], sro[2 * kTcM + row], srd[row], srd[kTcM + row],
+                                 srd[2 * kTcM + row], st0[row], st1[row], su[s0 + si], x, y, z);
+                  int cx, cy, cz;
+                  float fx, fy, fz;
+                  axis_cell(x, N, cx, fx);
+                  axis_cell(y, N, cy, fy);
+                  axis_cell(z, N, cz, fz);
+                  if (ccx >= 0 && (cx != ccx || cy != ccy || cz != ccz)) {
+                    const int dx = cx - ccx, dy = cy - ccy, dz = cz - ccz;
 #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) v[ff] += __shfl_xor_sync(0xffffffffu, v[ff], o);
-                  }
-                  if (lane == 0) {
-                    float* dst = gt + size_t(key) * F;
-                    if constexpr (F == 2) {
-                      atomicAdd(reinterpret_cast<float2*>(dst), make_float2(v[0], v[1]));
-                    } else {
-#pragma unroll
-                      for (int ff = 0; ff < F; ++ff) atomicAdd(dst + ff, v[ff]);
+                    for (int q = 0; q < 8; ++q) {
+                      const int bx = q & 1, by = (q >> 1) & 1, bz = q >> 2;
+                      const bool keep =
+                          unsigned(bx - dx) <= 1u && unsigned(by - dy) <= 1u && unsigned(bz - dz) <= 1u;
+                      if (!keep)
+                        add_entry<F>(gt + size_t(vertex_index(a.gp, l, uint32_t(ccx + bx), uint32_t(ccy + by),
+                                                              uint32_t(ccz + bz))) * F,
+                                     acc[q]);
                     }
+                    shift_corners<F, 1>(acc, dx);
+                    shift_corners<F, 2>(acc, dy);
+                    shift_corners<F, 4>(acc, dz);
+                  }
+                  ccx = cx;
+                  ccy = cy;
+                  ccz = cz;
+                  const float wx[2] = {1.0f - fx, fx};
+                  const float wy[2] = {1.0f - fy, fy};
+                  const float wz[2] = {1.0f - fz, fz};
+#pragma unroll
+                  for (int q = 0; q < 8; ++q) {
+                    const float wq = wx[q & 1] * wy[(q >> 1) & 1] * wz[q >> 2];
+#pragma unroll
+                    for (int ff = 0; ff < F; ++ff) acc[q][ff] = fmaf(wq, g8[si * F + ff], acc[q][ff]);
                   }
                 }
-              } else if (valid) {
-                float* dst = gt + size_t(key) * F;
-                if constexpr (F == 2) {
-                  atomicAdd(reinterpret_cast<float2*>(dst), make_float2(v[0], v[1]));
-                } else if constexpr (F % 4 == 0) {
+              }
+              // the last cell's vertices (the whole warp takes part)
 #pragma unroll
-                  for (int ff = 0; ff < F; ff += 4)
-                    atomicAdd(reinterpret_cast<float4*>(dst + ff), make_float4(v[ff], v[ff + 1], v[ff + 2], v[ff + 3]));
-                } else {
-                  atomicAdd(dst, v[0]);
-                }
+              for (int q = 0; q < 8; ++q) {
+                const uint32_t key =
+                    ccx >= 0 ? vertex_index(a.gp, l, uint32_t(ccx + (q & 1)), uint32_t(ccy + ((q >> 1) & 1)),
+                                            uint32_t(ccz + (q >> 2)))
+                             : 0xffffffffu;
+                add_vertex_warp<F>(gt, key, acc[q], N <= kAggMaxRes, lane);
+              }
+            }
+          }
+        }
+        if (!lmaj) {
+          // Sample-major chunks: 16 features (one sample, 16 / F levels) per
+          // pass; eight table updates per sample and level.
+          for (int sub = cgroup * 16; sub < cw; sub += kGroups * 16) {
+            float gx[16];
+            tmem_ld16(t_row + lay.col_x + uint32_t(sub), gx);
+            tmem_ld_wait();
+            int kprev = -1;
+            float x = 0.0f, y = 0.0f, z = 0.0f;
+#pragma unroll
+            for (int j = 0; j < 16; j += F) {
+              const int f = c0 + sub + j;
+              if (f >= K) continue;
+              const int k = f / (L * F);
+              const int l = (f / F) % L;
+              if (k != kprev) {
+                if (valid)
+                  sample_point_u(a.gp, sro[row], sro[kTcM + row], sro[2 * kTcM + row], srd[row], srd[kTcM + row],
+                                 srd[2 * kTcM + row], st0[row], st1[row], su[k], x, y, z);
+                kprev = k;
+              }
+              Corners cr;
+              level_corners(a.gp, l, x, y, z, cr);
+              float* gt = a.grad_table + a.gp.offset[l] * F;
+#pragma unroll
+              for (int q = 0; q < 8; ++q) {
+                float v[F];
+#pragma unroll
+                for (int ff = 0; ff < F; ++ff) v[ff] = valid ? cr.w[q] * gx[j + ff] : 0.0f;
+                add_vertex_warp<F>(gt, valid ? cr.idx[q] : 0xffffffffu, v, a.gp.res[l] <= kAggMaxRes, lane);
               }
             }
           }

@@ -94,10 +94,10 @@ def test_labels_parity():
 
 
 # ---------------------------------------------------------------- S8 forward, loss, gradients
-def _batch(b, n=2000, seed=43):
+def _batch(b, n=2000, seed=43, hit_fraction=0.6):
     torch = _torch()
     rays, o, d, leaf, t0, t1 = _segments(b, n, seed)
-    lab = W.random_labels(n, seed=seed + 1, hit_fraction=0.6)
+    lab = W.random_labels(n, seed=seed + 1, hit_fraction=hit_fraction)
     valid = leaf >= 0
     dev = dict(rays=B.to_device_rays(rays), leaf=_dev(torch, leaf)[0], t0=_dev(torch, t0)[0],
                t1=_dev(torch, t1)[0], lab={k: _dev(torch, v)[0] for k, v in lab.items()},
@@ -341,6 +341,67 @@ def test_tensor_core_gradients_match_oracle(mp):
         assert rel <= tol_rel and cos >= tol_cos, (rel, cos)
     r = raw.cpu().numpy()[v]
     assert np.mean((r[:, 0] > 0) == (ref_raw[v][:, 0] > 0)) >= 0.99
+
+
+def _half_round(prec):
+    """Round-to-nearest-even to the 16-bit operand type (torch conversion)."""
+    import torch
+    dt = torch.float16 if prec == B.FP16 else torch.bfloat16
+    return lambda a: torch.as_tensor(np.asarray(a, np.float64)).to(dt).double().numpy()
+
+
+def _entry_err(got, ref):
+    """Per-entry error |got - ref| / (|ref| + 1e-3 rms(ref)) over the entries
+    either side touches."""
+    nz = (np.abs(ref) > 0) | (np.abs(got) > 0)
+    rms = np.sqrt(np.mean(ref[np.abs(ref) > 0] ** 2))
+    return (np.abs(got - ref) / (np.abs(ref) + 1e-3 * rms))[nz]
+
+
+@pytest.mark.parametrize("mp", [B.FP16, B.BF16])
+@pytest.mark.parametrize("n_samples,n_features", [(8, 2), (16, 1), (12, 2), (8, 4)])
+def test_tensor_core_backward_matches_half_precision_oracle(n_samples, n_features, mp):
+    """The tensor-core forward and backward against the oracle run with the
+    same half-precision operand rounding (features, weights, activations,
+    dL/d(raw) times the loss scale, dZ), so that only FP32-versus-FP64
+    accumulation separates them. Both forms of the table-gradient scatter:
+    walking each ray through one level (N*F = 16 or 32 features per level:
+    (8, 2), (16, 1)) and per sample ((12, 2): N*F = 24; (8, 4): four features).
+    Accumulation differences are ~1e-6 relative, but now and then one moves an
+    operand across a 16-bit rounding boundary or a pre-activation across zero,
+    which changes that ray's whole contribution; such events touch few
+    entries. Bounds: table gradient median per-entry error <= 1e-4 and 90th
+    percentile <= 1e-3 (a wrong corner, weight or level moves whole levels or
+    corner classes), relative L2 error <= 1e-2 for table and MLP, MLP median
+    <= 1e-3."""
+    from dataclasses import replace
+    torch = _torch()
+    base = make_case("random_tris_c0", 0.5, 2.0)
+    model = replace(base.model, n_samples=n_samples, n_features=n_features)
+    b = Built(replace(base, model=model))
+    desc = b.with_prec(mp)
+    dv, h = _batch(b, n=1500, seed=83)
+    n = len(h["leaf"])
+    ws = B.new_workspace(B.train_workspace_size(desc, n))
+    scale = 1024.0
+    B.forward_train(desc, b.table, b.mlp, dv["rays"], dv["leaf"], dv["t0"], dv["t1"], ws,
+                    labels=dv["lab"], n_valid=dv["n_valid"], loss_scale=scale)
+    g_tab = torch.zeros((b.layout["total"], n_features), dtype=torch.float32, device="cuda")
+    g_mlp = torch.zeros_like(b.mlp)
+    B.backward(desc, b.table, b.mlp, dv["rays"], dv["leaf"], dv["t0"], dv["t1"], ws, g_tab, g_mlp)
+    assert B.device_status() == 0
+    fr = b.oleaves["frame"]
+    _, ref_tab, ref_layers, _ = O.forward_backward(h["o"], h["d"], h["t0"], h["t1"], h["valid"], h["yh"], h["yd"],
+                                                   h["yn"], b.table_host, b.layers, b.olayout, fr["model_centre"],
+                                                   fr["model_extent"], n_samples, rnd=_half_round(mp), scale=scale)
+    gt, rt = g_tab.cpu().numpy().ravel() / scale, ref_tab.ravel()
+    gm, rm = g_mlp.cpu().numpy() / scale, B.pack_mlp(ref_layers).astype(np.float64)
+    et, em = _entry_err(gt, rt), _entry_err(gm, rm)
+    l2t = np.linalg.norm(gt - rt) / np.linalg.norm(rt)
+    l2m = np.linalg.norm(gm - rm) / np.linalg.norm(rm)
+    stats = (np.median(et), np.percentile(et, 90), l2t, np.median(em), l2m)
+    assert np.median(et) <= 1e-4 and np.percentile(et, 90) <= 1e-3 and l2t <= 1e-2, stats
+    assert np.median(em) <= 1e-3 and l2m <= 1e-2, stats
 
 
 def test_tensor_core_training_learns():
