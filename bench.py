@@ -261,9 +261,17 @@ class ClockSampler:
             dev = os.environ.get("LOCAL_RANK", "0")
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", dev, f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+                                          "-lms", "50"], stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        # nvidia-smi takes a moment to start: wait (bounded) for its first sample
+        # so that the timed region that follows is sampled from its start
+        t0 = time.time()
+        while time.time() - t0 < 5.0 and self.proc.poll() is None:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.02)
 
     def stop(self):
         if self.proc is None:
@@ -448,13 +456,13 @@ def run_gpu(args, world, rank, spec, tris, rays_np):
     clocks = ClockSampler()
     clocks.start()
     total_ms = time_steps(wl, d16, args.steps, args.warmup)
-    clk = clocks.stop()
     total_ms = dist_max(total_ms, world)
     ms_step = total_ms / args.steps
     value = world * rays_step / (ms_step * 1e-3) / 1e6
     launches_per_step = wl.launches_per_step[(d16.mlp_prec, d16.table_prec)]
 
     if args.quick:
+        clk = clocks.stop()
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": "Mrays/s", "ms_per_step": ms_step,
                               "quick": True, "segments_per_step": seg1 + seg2, "eval_ms_per_step": eval_ms_step,
@@ -474,6 +482,7 @@ def run_gpu(args, world, rank, spec, tris, rays_np):
 
     # end to end through the public API with host buffers (graph step between the copies)
     e2e_ms = dist_max(time_steps(wl, d16, args.steps, args.warmup, e2e=True), world) / args.steps
+    clk = clocks.stop()  # clocks sampled over every timed form above
     h2d = sum(v.numel() * v.element_size() for v in wl.rays_host.values())
     d2h = 2 * sum(v.numel() * v.element_size() for v in wl.h1_host.values())
 
