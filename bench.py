@@ -47,6 +47,10 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--max-segs", type=int, default=48)
     p.add_argument("--train-steps", type=int, default=20, help="timed training steps (2^18 rays each)")
+    p.add_argument("--hybrid-frames", type=int, default=5,
+                   help="timed frames of the hybrid-scene workload (0: skip it)")
+    p.add_argument("--hybrid-size", default="3840x2160")
+    p.add_argument("--hybrid-cpu-rays", type=int, default=128, help="oracle sample of the hybrid workload")
     p.add_argument("--quick", action="store_true",
                    help="time the FP16 tensor-core form only (no other forms, no e2e, no CPU baseline)")
     return p.parse_args()
@@ -385,6 +389,135 @@ def accuracy(wl, idx, res):
     return out
 
 
+# ---------------------------------------------------------------------------- hybrid scene (S9)
+HYBRID_BOUNCES = 4
+HYBRID_MAX_SEGS = 16
+
+
+class HybridWorkload:
+    """16 neural assets (BF16 tables, BF16 tensor-core MLPs) on a 500,000-
+    triangle classical ground, one frame = the primary pass plus 4 bounce
+    passes of nbvh_hybrid_trace + nbvh_bounce_rays, recorded as one graph."""
+
+    def __init__(self, width, height):
+        import torch
+        from paper_2405_16237_b300 import nbvh as B
+        from paper_2405_16237_b300 import workloads as W
+        self.B = B
+        self.ground, self.assets = W.scene_hybrid()
+        self.blas = B.build_tri_blas(self.ground, 4)
+        self.dev_blas = B.DeviceTriBlas(self.ground, self.blas)
+        self.instances = [B.tri_instance(self.dev_blas)]
+        self.keep, self.models = [], []
+        for k, a in enumerate(self.assets):
+            lv = B.build_leaves(a.tris, a.n_leaves, 1e-4)
+            info = lv["info"]
+            desc = B.model_desc(a.model, B.BF16, B.BF16, info["centre"], info["extent"])
+            lay = B.level_layout(desc)
+            tab = torch.as_tensor(W.init_table(lay["total"], a.model.n_features, SEED + 100 + k, 1e-4)).cuda()
+            table = tab.to(torch.bfloat16)
+            layers = W.init_mlp(a.model.mlp_dims(), SEED + 200 + k)
+            mlp = torch.as_tensor(B.pack_mlp(layers)).cuda()
+            nodes = torch.as_tensor(lv["nodes"]).cuda()
+            self.keep += [table, mlp, nodes]
+            self.models.append((a, layers, table))
+            self.instances.append(B.neural_instance(desc, table, mlp, nodes, lv["n_nodes"], HYBRID_MAX_SEGS))
+        self.rays_np = W.hybrid_camera_rays(width, height)
+        self.n = len(self.rays_np["ox"])
+        self.rays = [B.to_device_rays(self.rays_np)] + [B.new_rays(self.n) for _ in range(HYBRID_BOUNCES)]
+        self.hits = [B.new_hits(self.n) for _ in range(HYBRID_BOUNCES + 1)]
+        self.inst = [torch.empty(self.n, dtype=torch.int32, device="cuda") for _ in range(HYBRID_BOUNCES + 1)]
+        self.ws = B.new_workspace(B.hybrid_workspace_size(self.instances, self.n))
+        self.flush_buf = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+        self.graph = None
+        self.launches = 0
+
+    def frame(self):
+        B = self.B
+        for b in range(HYBRID_BOUNCES + 1):
+            B.hybrid_trace(self.instances, self.rays[b], out=self.hits[b], inst_out=self.inst[b], workspace=self.ws)
+            if b < HYBRID_BOUNCES:
+                B.bounce_rays(self.rays[b], self.hits[b], SEED + 30 + b, out=self.rays[b + 1])
+
+    def graph_frame(self):
+        if self.graph is None:
+            n0 = self.B.launch_count()
+            self.graph = self.B.Graph.record(self.frame)
+            self.launches = self.B.launch_count() - n0
+        self.graph.launch()
+
+    def rays_per_frame(self):
+        """Rays traced with a non-empty interval: every primary ray, and each
+        bounce ray spawned from a hit."""
+        return self.n + sum(int(self.hits[b]["hit"].sum().item()) for b in range(HYBRID_BOUNCES))
+
+
+def time_hybrid(args, world):
+    import torch
+    from oracle import nbvh_oracle as O
+    from paper_2405_16237_b300 import workloads as W
+    w, h = (int(x) for x in args.hybrid_size.split("x"))
+    t0 = time.perf_counter()
+    hw = HybridWorkload(w, h)
+    setup_s = time.perf_counter() - t0
+    B = hw.B
+    hw.frame()
+    torch.cuda.synchronize()
+    st = B.device_status()
+    if st != 0:
+        raise RuntimeError(f"device status {st} after the first hybrid frame")
+    rays = hw.rays_per_frame()
+    kinds = {"triangle": int((hw.inst[0] == 0).sum().item()), "neural": int((hw.inst[0] > 0).sum().item())}
+    for _ in range(3):
+        hw.graph_frame()
+    torch.cuda.synchronize()
+    total = 0.0
+    for _ in range(args.hybrid_frames):
+        hw.flush_buf.fill_(1)
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record()
+        hw.graph_frame()
+        e.record()
+        e.synchronize()
+        total += s.elapsed_time(e)
+    if B.device_status() != 0:
+        raise RuntimeError("device status after hybrid frames")
+    ms = dist_max(total, world) / args.hybrid_frames
+    out = {"workload": f"hybrid-16-neural-assets+500000-tri-ground_{w}x{h}_primary+{HYBRID_BOUNCES}-bounces",
+           "value": world * rays / (ms * 1e-3) / 1e6, "unit": "Mrays/s", "ms_per_frame": ms,
+           "rays_per_frame": rays, "primary_hits": kinds, "frames": args.hybrid_frames,
+           "gpu_launches_per_frame": hw.launches, "dtype": "bf16 tables + bf16 tensor-core MLPs, fp32 triangles",
+           "setup_s": setup_s, "l2": "flushed (256 MB write) between timed frames"}
+    if args.hybrid_cpu_rays > 0 and not args.no_cpu_baseline:
+        rng = np.random.default_rng(SEED + 6)
+        idx = np.sort(rng.choice(hw.n, size=args.hybrid_cpu_rays, replace=False))
+        sub = W.subset(hw.rays_np, idx)
+        oinst = [{"kind": "triangles", "tris": hw.ground}]
+        for a, layers, table in hw.models:
+            oinst.append({"kind": "neural", "leaves": O.build_leaves(a.tris, a.n_leaves, 1e-4),
+                          "table": table.float().cpu().numpy().astype(np.float64), "layers": layers,
+                          "layout": O.level_layout(a.model.n_levels, a.model.base_res, a.model.growth,
+                                                   a.model.log2_table), "n_samples": a.model.n_samples})
+        t1 = time.perf_counter()
+        ref = O.hybrid_trace(sub, oinst)
+        dt = time.perf_counter() - t1
+        g_inst = hw.inst[0].cpu().numpy()[idx]
+        g = {k: v.cpu().numpy()[idx] for k, v in hw.hits[0].items()}
+        same = (g_inst == ref["inst"]) & (g["leaf"] == ref["leaf"]) & ref["hit"].astype(bool)
+        acc = {"rays": int(len(idx)), "instance_agreement": float(np.mean(g_inst == ref["inst"]))}
+        if same.any():
+            acc["depth_max_abs"] = float(np.max(np.abs(g["t"][same] - ref["t"][same])))
+            gn = np.stack([g["nx"], g["ny"], g["nz"]], 1)[same]
+            c = np.clip(np.sum(gn * ref["normal"][same], 1), -1, 1)
+            acc["normal_mean_deg"] = float(np.degrees(np.arccos(c)).mean())
+        out["accuracy_vs_oracle"] = acc
+        out["cpu_baseline"] = {"value": len(idx) / dt / 1e6, "unit": "Mrays/s", "cores": 1, "kind": "oracle",
+                               "sample": f"{len(idx)} seeded primary rays of the {w}x{h} image, primary pass only, "
+                                         f"{dt:.1f} s"}
+    return out
+
+
 # ---------------------------------------------------------------------------- main
 def main():
     args = parse()
@@ -480,6 +613,9 @@ def run_gpu(args, world, rank, spec, tris, rays_np):
     if train is not None:
         train["value"] = dist_max_rate(train["value"], world)
 
+    # the hybrid two-level scene (16 neural assets + 500,000 classical triangles)
+    hybrid = time_hybrid(args, world) if args.hybrid_frames > 0 else None
+
     # end to end through the public API with host buffers (graph step between the copies)
     e2e_ms = dist_max(time_steps(wl, d16, args.steps, args.warmup, e2e=True), world) / args.steps
     clk = clocks.stop()  # clocks sampled over every timed form above
@@ -509,6 +645,7 @@ def run_gpu(args, world, rank, spec, tris, rays_np):
                        "waves": [waves1, waves2], "l2": "flushed (256 MB write) between timed steps",
                        "parallelism": f"replicas x{world}"},
             "train": train,
+            "hybrid": hybrid,
             "fp32_plain": {"value": world * rays_step / (ms32 * 1e-3) / 1e6, "ms_per_step": ms32},
             "bf16_tc": {"value": world * rays_step / (msbf * 1e-3) / 1e6, "ms_per_step": msbf},
             "roofline": roof,

@@ -391,6 +391,83 @@ nbvh_status nbvh_graph_end(void* stream, nbvh_graph* out);
 nbvh_status nbvh_graph_launch(nbvh_graph graph, void* stream);
 nbvh_status nbvh_graph_destroy(nbvh_graph graph);
 
+/* ------------------------------------------------------------------------
+ * Hybrid two-level hierarchy (S9; Sec. 7 "Application: Hybrid path
+ * tracing"): a top level holds several bottom-level structures, each either a
+ * classical BVH over triangles or an N-BVH; reaching a BLAS leaf runs a
+ * classical or a neural intersection query, and both return the same hit
+ * record, from which the path tracer samples the next direction.
+ * ------------------------------------------------------------------------ */
+
+/* Host. Classical triangle BLAS: binned surface-area-heuristic BVH over
+ * triangle centroids (32 bins per axis; the base BVH the paper builds on the
+ * CPU is an SAH tree, Sec. 6 "BVH construction"). A node splits where
+ * area(left) n_left + area(right) n_right is smallest; it stays a leaf when it
+ * holds at most max_leaf triangles and no split beats area(node) n (one node
+ * visit counted as one triangle test). Node boxes are the exact float AABBs
+ * of their triangles (no inflation). Nodes use the nbvh_node format (child < 0
+ * is leaf ~child; a single leaf is node 0 with child1 = 0x7fffffff).
+ *   tris        host, [n_tris][3][3] float
+ *   nodes       host, node_cap >= max(1, n_tris - 1) entries; *out_n_nodes set
+ *   tri_perm    host, n_tris int32: the triangles in leaf order (caller indices)
+ *   leaf_range  host, 2 * leaf_cap int32 (leaf_cap >= n_tris): leaf i owns
+ *               tri_perm[leaf_range[2i] .. leaf_range[2i+1]); *out_n_leaves set
+ * Errors: INVALID_ARG for a null pointer, n_tris < 1, max_leaf outside
+ * [1, 64], a non-finite vertex or a capacity below the bounds above. */
+nbvh_status nbvh_build_tri_blas(const float* tris, int64_t n_tris, int32_t max_leaf, nbvh_node* nodes,
+                                int32_t node_cap, int32_t* out_n_nodes, int32_t* tri_perm, int32_t* leaf_range,
+                                int32_t leaf_cap, int32_t* out_n_leaves);
+
+/* A triangle BLAS on the device (all pointers device memory). */
+typedef struct {
+  const nbvh_node* nodes;
+  int32_t n_nodes;
+  const float* tris;          /* [n_tris][9] vertices in leaf order (tris[tri_perm[i]]) */
+  const int32_t* leaf_range;  /* [n_leaves][2] as nbvh_build_tri_blas */
+  const int32_t* tri_id;      /* [n_tris] tri_perm: caller index of each leaf-order triangle */
+} nbvh_tri_blas;
+
+/* Device. Closest triangle hit of every ray with t in [tmin, tmax]
+ * (Moller-Trumbore, edges inclusive, det == 0 a miss, FP32); equal t goes to
+ * the lower caller index. hits: hit 1, t, the geometric normal (unit, turned
+ * to face -d), leaf = the triangle's caller index; a miss gets hit 0,
+ * t +inf, normal 0, leaf -1. rays/hits: device SoA of rays.n entries. */
+nbvh_status nbvh_trace_triangles(const nbvh_tri_blas* blas, nbvh_rays rays, nbvh_hits hits, void* stream);
+
+typedef enum { NBVH_BLAS_TRIANGLES = 0, NBVH_BLAS_NEURAL = 1 } nbvh_blas_kind;
+
+/* One top-level instance (host struct; the pointers inside are device memory).
+ * Instances are placed in world space (no transform). */
+typedef struct {
+  int32_t kind;             /* nbvh_blas_kind */
+  nbvh_tri_blas tri;        /* kind == NBVH_BLAS_TRIANGLES */
+  nbvh_model_desc desc;     /* kind == NBVH_BLAS_NEURAL: the asset's model, */
+  const void* table;        /*   hash table (desc.table_prec), */
+  const float* mlp;         /*   MLP parameters (nbvh_mlp_param_count order), */
+  const nbvh_node* nodes;   /*   N-BVH nodes (nbvh_build_leaves) */
+  int32_t n_nodes;
+  int32_t max_segs;         /*   segment slots per ray for this asset */
+} nbvh_instance;
+
+/* Host. Workspace bytes of nbvh_hybrid_trace for n_rays rays. */
+nbvh_status nbvh_hybrid_workspace_size(const nbvh_instance* inst, int32_t n_inst, int64_t n_rays, size_t* bytes);
+
+/* Device. Closest hit over every instance of the two-level hierarchy. Each
+ * triangle instance answers as nbvh_trace_triangles; each neural instance
+ * answers as nbvh_query_rays on its own N-BVH over the ray's full
+ * [tmin, tmax]. The result is the smallest t over the instances; equal t goes
+ * to the lower instance index. out.leaf is the triangle index or the N-BVH
+ * leaf; out_inst (device, rays.n int32) the instance index, -1 on a miss.
+ * Instances are processed in index order as wavefront passes over all rays,
+ * each keeping the record unless it finds a strictly closer hit; a neural
+ * pass skips the leaves whose segment starts at or beyond the record (their
+ * hits cannot be closer), which leaves the result unchanged.
+ * inst: host array of n_inst (1..64) instances; workspace: device, 256-byte
+ * aligned, >= nbvh_hybrid_workspace_size bytes. Segment overflow of a neural
+ * pass is reported as in nbvh_query_rays. */
+nbvh_status nbvh_hybrid_trace(const nbvh_instance* inst, int32_t n_inst, nbvh_rays rays, nbvh_hits out,
+                              int32_t* out_inst, void* workspace, size_t ws_bytes, void* stream);
+
 /* Device. Reads and clears the device status word (synchronises the stream). */
 nbvh_status nbvh_get_device_status(void* stream);
 

@@ -826,3 +826,89 @@ def bounce_rays(o, d, t, nrm, ray_index, seed: int):
     tt, bb = onb(n)
     dirs = x[:, None] * tt + y[:, None] * bb + z[:, None] * n
     return p, dirs
+
+
+# ============================================================================
+# S9: the hybrid two-level hierarchy (Sec. 7 "Application: Hybrid path
+# tracing"): each bottom-level structure is a classical triangle BVH or an
+# N-BVH, both answer with the same intersection record, and the ray keeps the
+# closest answer over all of them
+# ============================================================================
+
+def closest_triangle_hit(o, d, tmin, tmax, tris, eps: float = 1e-5):
+    """Brute force over every triangle (Moller-Trumbore, edges inclusive,
+    det == 0 a miss): the closest t in [tmin, tmax], equal t to the lowest
+    triangle index; normal = geometric normal turned to face -d.
+    ``margin`` is how close the answer is to flipping: the smallest distance
+    of a candidate's barycentrics to the triangle's edges among triangles
+    within eps of being a hit no farther than the answer, the gap to the next
+    candidate's t, and the answer's distance to tmin / tmax."""
+    o = np.asarray(o, F64)
+    d = np.asarray(d, F64)
+    tv = np.asarray(tris, F64)
+    v0, v1, v2 = tv[:, 0], tv[:, 1], tv[:, 2]
+    n = len(o)
+    hit = np.zeros(n, np.uint8)
+    t_out = np.full(n, np.inf)
+    nrm = np.zeros((n, 3))
+    idx = np.full(n, -1, np.int64)
+    margin = np.full(n, np.inf)
+    for i in range(n):
+        h, t, u, v = moller_trumbore(o[i][None], d[i][None], v0, v1, v2)
+        inside = h & (t >= tmin[i]) & (t <= tmax[i])
+        best = np.inf
+        if np.any(inside):
+            tt = np.where(inside, t, np.inf)
+            best = float(np.min(tt))
+            j = int(np.flatnonzero(tt == best)[0])   # lowest index among equal t
+            hit[i] = 1
+            t_out[i] = best
+            idx[i] = j
+            g = np.cross(v1[j] - v0[j], v2[j] - v0[j])
+            g = g / np.linalg.norm(g)
+            if np.dot(g, d[i]) > 0:
+                g = -g
+            nrm[i] = g
+            srt = np.sort(tt[np.isfinite(tt)])
+            if len(srt) > 1:
+                margin[i] = min(margin[i], srt[1] - srt[0])
+            margin[i] = min(margin[i], best - tmin[i], tmax[i] - best)
+        lim = min(best, tmax[i]) + eps
+        near = (np.isfinite(t) & (u >= -eps) & (v >= -eps) & (u + v <= 1.0 + eps) & (t >= tmin[i] - eps)
+                & (t <= lim))
+        if np.any(near):
+            m = np.minimum.reduce([np.abs(u[near]), np.abs(v[near]), np.abs(1.0 - u[near] - v[near])])
+            margin[i] = min(margin[i], float(np.min(m)))
+    return {"hit": hit, "t": t_out, "normal": nrm, "index": idx, "margin": margin}
+
+
+def hybrid_trace(rays: dict, instances):
+    """Closest hit over the instances, taken in index order: an instance's
+    answer replaces the record only when it is a hit strictly closer than the
+    record (equal t stays with the lower instance index). Instances are dicts:
+    {"kind": "triangles", "tris": [n, 3, 3]} or {"kind": "neural", "leaves",
+    "table", "layers", "layout", "n_samples"} (each neural instance answers
+    with ``query`` over the ray's full [tmin, tmax]). Returns the record
+    (hit, t, normal, leaf = triangle index or N-BVH leaf, inst) and every
+    instance's own answer."""
+    o, d, tmin, tmax = rays_od(rays)
+    n = len(o)
+    out = {"hit": np.zeros(n, np.uint8), "t": np.full(n, np.inf), "normal": np.zeros((n, 3)),
+           "leaf": np.full(n, -1, np.int64), "inst": np.full(n, -1, np.int64)}
+    answers = []
+    for k, x in enumerate(instances):
+        if x["kind"] == "triangles":
+            a = closest_triangle_hit(o, d, tmin, tmax, x["tris"])
+            ans = {"hit": a["hit"], "t": a["t"], "normal": a["normal"], "leaf": a["index"], "margin": a["margin"]}
+        else:
+            q = query(rays, x["leaves"], x["table"], x["layers"], x["layout"], x["n_samples"])
+            ans = {"hit": q["hit"], "t": q["t"], "normal": q["normal"], "leaf": q["leaf"], "query": q}
+        answers.append(ans)
+        better = ans["hit"].astype(bool) & (ans["t"] < out["t"])
+        out["hit"][better] = 1
+        out["t"][better] = ans["t"][better]
+        out["normal"][better] = ans["normal"][better]
+        out["leaf"][better] = ans["leaf"][better]
+        out["inst"][better] = k
+    out["answers"] = answers
+    return out

@@ -88,6 +88,8 @@ struct EvalArgs {
   nbvh_hits hits;
   int32_t* next_queue;
   int32_t* next_qlen;
+  int32_t* inst_out;  // optional (hybrid hierarchy): instance id written with each improved hit
+  int32_t inst_id;
   // training forward (tensor-core kernel, list of one segment per ray)
   TcTrain tr;
 };
@@ -174,6 +176,7 @@ __device__ __forceinline__ void wave_resolve(const EvalArgs& a, bool valid, int 
       a.hits.ny[ray] = s.ny;
       a.hits.nz[ray] = s.nz;
       a.hits.leaf[ray] = a.seg_leaf[size_t(a.wave) * size_t(a.n_rays) + size_t(ray)];
+      if (a.inst_out) a.inst_out[ray] = a.inst_id;
     }
     const int nxt = a.wave + 1;
     if (nxt < a.seg_count[ray]) {

@@ -297,3 +297,212 @@ extern "C" nbvh_status nbvh_build_leaves(const float* tris, int64_t n_tris, int3
   *out_n_nodes = need_nodes;
   return NBVH_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Classical triangle BLAS (Sec. 7: a BLAS of the hybrid hierarchy is either a
+// classical BVH or an N-BVH). Binned surface-area-heuristic build over
+// triangle centroids: at each node, 32 bins per axis over the centroid bounds;
+// the split minimising area(left) * n_left + area(right) * n_right is taken
+// when it beats keeping the node as a leaf of at most max_leaf triangles; a
+// node whose centroids coincide is split at its middle index.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Box3 {
+  float lo[3] = {INFINITY, INFINITY, INFINITY};
+  float hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  void grow(const Box3& b) {
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = std::min(lo[a], b.lo[a]);
+      hi[a] = std::max(hi[a], b.hi[a]);
+    }
+  }
+  double area() const {
+    if (!(hi[0] >= lo[0])) return 0.0;
+    const double x = double(hi[0]) - lo[0], y = double(hi[1]) - lo[1], z = double(hi[2]) - lo[2];
+    return 2.0 * (x * y + y * z + z * x);
+  }
+};
+
+struct BlasNode {
+  int64_t begin, end;
+  Box3 box;
+  int left = -1, right = -1;
+};
+
+constexpr int kSahBins = 32;
+
+}  // namespace
+
+extern "C" nbvh_status nbvh_build_tri_blas(const float* tris, int64_t n_tris, int32_t max_leaf, nbvh_node* nodes,
+                                           int32_t node_cap, int32_t* out_n_nodes, int32_t* tri_perm,
+                                           int32_t* leaf_range, int32_t leaf_cap, int32_t* out_n_leaves) {
+  if (!tris || n_tris < 1 || n_tris > (int64_t(1) << 30) || max_leaf < 1 || max_leaf > 64 || !nodes ||
+      !out_n_nodes || !tri_perm || !leaf_range || !out_n_leaves)
+    return NBVH_ERR_INVALID_ARG;
+  if (int64_t(node_cap) < std::max<int64_t>(1, n_tris - 1) || int64_t(leaf_cap) < n_tris)
+    return NBVH_ERR_INVALID_ARG;
+  std::vector<Box3> tb(static_cast<size_t>(n_tris));
+  std::vector<float> cent(size_t(n_tris) * 3);
+  for (int64_t t = 0; t < n_tris; ++t) {
+    for (int v = 0; v < 3; ++v)
+      for (int a = 0; a < 3; ++a) {
+        const float x = tris[size_t(t) * 9 + v * 3 + a];
+        if (!std::isfinite(x)) return NBVH_ERR_INVALID_ARG;
+        tb[t].lo[a] = std::min(tb[t].lo[a], x);
+        tb[t].hi[a] = std::max(tb[t].hi[a], x);
+      }
+    for (int a = 0; a < 3; ++a) cent[size_t(t) * 3 + a] = 0.5f * (tb[t].lo[a] + tb[t].hi[a]);
+  }
+  std::vector<int32_t> idx(static_cast<size_t>(n_tris));
+  for (int64_t t = 0; t < n_tris; ++t) idx[t] = int32_t(t);
+
+  std::vector<BlasNode> bn;
+  bn.reserve(size_t(2 * n_tris));
+  BlasNode root;
+  root.begin = 0;
+  root.end = n_tris;
+  for (int64_t t = 0; t < n_tris; ++t) root.box.grow(tb[t]);
+  bn.push_back(root);
+  std::vector<int> work{0};
+  while (!work.empty()) {
+    const int id = work.back();
+    work.pop_back();
+    const int64_t b = bn[id].begin, e = bn[id].end, n = e - b;
+    if (n <= 1) continue;
+    float cmin[3] = {INFINITY, INFINITY, INFINITY}, cmax[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = b; i < e; ++i)
+      for (int a = 0; a < 3; ++a) {
+        cmin[a] = std::min(cmin[a], cent[size_t(idx[i]) * 3 + a]);
+        cmax[a] = std::max(cmax[a], cent[size_t(idx[i]) * 3 + a]);
+      }
+    double best_cost = INFINITY;
+    int best_axis = -1, best_bin = -1;
+    for (int a = 0; a < 3; ++a) {
+      const double ext = double(cmax[a]) - cmin[a];
+      if (!(ext > 0.0)) continue;
+      Box3 bb[kSahBins];
+      int64_t cnt[kSahBins] = {};
+      const double scale = kSahBins / ext;
+      for (int64_t i = b; i < e; ++i) {
+        const int32_t t = idx[i];
+        int k = int((double(cent[size_t(t) * 3 + a]) - cmin[a]) * scale);
+        k = std::min(std::max(k, 0), kSahBins - 1);
+        ++cnt[k];
+        bb[k].grow(tb[t]);
+      }
+      double right_area[kSahBins];
+      int64_t right_cnt[kSahBins];
+      Box3 acc;
+      int64_t c = 0;
+      for (int k = kSahBins - 1; k > 0; --k) {
+        acc.grow(bb[k]);
+        c += cnt[k];
+        right_area[k] = acc.area();
+        right_cnt[k] = c;
+      }
+      Box3 lacc;
+      int64_t lc = 0;
+      for (int k = 0; k < kSahBins - 1; ++k) {
+        lacc.grow(bb[k]);
+        lc += cnt[k];
+        if (lc == 0 || right_cnt[k + 1] == 0) continue;
+        const double cost = lacc.area() * double(lc) + right_area[k + 1] * double(right_cnt[k + 1]);
+        if (cost < best_cost) {
+          best_cost = cost;
+          best_axis = a;
+          best_bin = k;
+        }
+      }
+    }
+    // one node visit costs about one triangle test
+    const double area = bn[id].box.area();
+    if (n <= max_leaf && !(best_cost + area < area * double(n))) continue;
+    int64_t mid;
+    if (best_axis >= 0) {
+      const int a = best_axis;
+      const double scale = kSahBins / (double(cmax[a]) - cmin[a]);
+      auto it = std::partition(idx.begin() + b, idx.begin() + e, [&](int32_t t) {
+        int k = int((double(cent[size_t(t) * 3 + a]) - cmin[a]) * scale);
+        k = std::min(std::max(k, 0), kSahBins - 1);
+        return k <= best_bin;
+      });
+      mid = int64_t(it - idx.begin());
+    } else {
+      mid = b + n / 2;  // coincident centroids: split by index
+    }
+    if (mid <= b || mid >= e) mid = b + n / 2;
+    BlasNode l, r;
+    l.begin = b;
+    l.end = mid;
+    r.begin = mid;
+    r.end = e;
+    for (int64_t i = b; i < mid; ++i) l.box.grow(tb[idx[i]]);
+    for (int64_t i = mid; i < e; ++i) r.box.grow(tb[idx[i]]);
+    const int li = int(bn.size());
+    bn.push_back(l);
+    bn.push_back(r);
+    bn[id].left = li;
+    bn[id].right = li + 1;
+    work.push_back(li + 1);
+    work.push_back(li);
+  }
+
+  // Preorder numbering: internal nodes -> node ids, leaves -> leaf ids in
+  // left-to-right order; triangles of leaf i are tri_perm[leaf_range[2i] ..
+  // leaf_range[2i+1]).
+  std::vector<int> order, stack{0};
+  while (!stack.empty()) {
+    const int id = stack.back();
+    stack.pop_back();
+    order.push_back(id);
+    if (bn[id].left >= 0) {
+      stack.push_back(bn[id].right);
+      stack.push_back(bn[id].left);
+    }
+  }
+  std::vector<int> node_of(bn.size(), -1), leaf_of(bn.size(), -1);
+  int32_t nn = 0, nl = 0;
+  int64_t pos = 0;
+  for (int id : order) {
+    if (bn[id].left >= 0) {
+      node_of[id] = nn++;
+      continue;
+    }
+    leaf_of[id] = nl;
+    leaf_range[2 * nl] = int32_t(pos);
+    for (int64_t i = bn[id].begin; i < bn[id].end; ++i) tri_perm[pos++] = idx[i];
+    leaf_range[2 * nl + 1] = int32_t(pos);
+    ++nl;
+  }
+  auto ref = [&](int id) { return bn[id].left >= 0 ? node_of[id] : ~leaf_of[id]; };
+  auto put = [&](nbvh_node& d, int slot, const Box3& bx) {
+    float* lo = slot == 0 ? d.lo0 : d.lo1;
+    float* hi = slot == 0 ? d.hi0 : d.hi1;
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = bx.lo[a];
+      hi[a] = bx.hi[a];
+    }
+  };
+  if (nn == 0) {  // a single leaf: the root holds its box and an empty second slot
+    nbvh_node& d = nodes[0];
+    std::memset(&d, 0, sizeof(d));
+    put(d, 0, bn[0].box);
+    d.child0 = ~0;
+    d.child1 = 0x7fffffff;
+    nn = 1;
+  } else {
+    for (int id : order) {
+      if (bn[id].left < 0) continue;
+      nbvh_node& d = nodes[node_of[id]];
+      std::memset(&d, 0, sizeof(d));
+      put(d, 0, bn[bn[id].left].box);
+      put(d, 1, bn[bn[id].right].box);
+      d.child0 = ref(bn[id].left);
+      d.child1 = ref(bn[id].right);
+    }
+  }
+  *out_n_nodes = nn;
+  *out_n_leaves = nl;
+  return NBVH_OK;
+}

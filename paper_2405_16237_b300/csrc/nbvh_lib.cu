@@ -13,6 +13,7 @@
 #include "eval_plain.cuh"
 #include "eval_tc.cuh"
 #include "bounce.cuh"
+#include "tri_blas.cuh"
 #include "train.cuh"
 #include "train_tc.cuh"
 
@@ -212,6 +213,50 @@ QueryWs carve_query(void* base, int64_t n, int32_t max_segs) {
   return w;
 }
 
+
+// Traversal (S1) then one evaluation wave per segment slot (S2..S5) on the
+// carved query workspace. merge: the hit record holds the closest hit so far
+// (hybrid hierarchy) and records the instance id with every improvement.
+cudaError_t launch_query_stages(const nbvh_model_desc* desc, const GridParams& gp, const void* table,
+                                const float* mlp, const nbvh_node* nodes, const nbvh_rays& rays, int32_t max_segs,
+                                const nbvh_hits& out, const QueryWs& w, bool merge, int32_t* inst_out,
+                                int32_t inst_id, cudaEvent_t after_traverse, cudaStream_t s) {
+  TraverseOut to;
+  std::memset(&to, 0, sizeof(to));
+  to.seg_count = w.seg_count;
+  to.seg_leaf = w.seg_leaf;
+  to.seg_t0 = w.seg_t0;
+  to.seg_t1 = w.seg_t1;
+  to.max_segs = max_segs;
+  to.queue0 = w.queue[0];
+  to.qlen0 = w.counters;
+  to.hits = out;
+  to.merge = merge ? 1 : 0;
+  traverse_kernel<<<unsigned((rays.n + 127) / 128), 128, 0, s>>>(nodes, ray_ptrs(rays), rays.n, to);
+  count_launches(1);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (after_traverse) cudaEventRecord(after_traverse, s);
+  EvalArgs a = base_args(desc, gp, table, mlp, rays);
+  a.n_rays = rays.n;
+  a.seg_count = w.seg_count;
+  a.seg_leaf = w.seg_leaf;
+  a.seg_t0 = w.seg_t0;
+  a.seg_t1 = w.seg_t1;
+  a.hits = out;
+  a.inst_out = inst_out;
+  a.inst_id = inst_id;
+  for (int wv = 0; wv < max_segs; ++wv) {
+    a.wave = wv;
+    a.queue = w.queue[wv & 1];
+    a.qlen = w.counters + wv;
+    a.next_queue = w.queue[(wv + 1) & 1];
+    a.next_qlen = w.counters + wv + 1;
+    e = launch_eval(desc, a, true, rays.n, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
 }  // namespace
 }  // namespace nbvh
 
@@ -297,16 +342,6 @@ extern "C" nbvh_status nbvh_query_rays(const nbvh_model_desc* desc, const void* 
   cudaStream_t s = as_stream(stream);
   cudaError_t e = cudaMemsetAsync(w.counters, 0, sizeof(int32_t) * size_t(max_segs + 2), s);
   if (e != cudaSuccess) return NBVH_ERR_CUDA;
-  TraverseOut to;
-  std::memset(&to, 0, sizeof(to));
-  to.seg_count = w.seg_count;
-  to.seg_leaf = w.seg_leaf;
-  to.seg_t0 = w.seg_t0;
-  to.seg_t1 = w.seg_t1;
-  to.max_segs = max_segs;
-  to.queue0 = w.queue[0];
-  to.qlen0 = w.counters;
-  to.hits = out;
   StageEvents ev{nullptr, nullptr, nullptr};
   cudaStreamCaptureStatus capturing = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(s, &capturing) != cudaSuccess) return NBVH_ERR_CUDA;
@@ -320,27 +355,9 @@ extern "C" nbvh_status nbvh_query_rays(const nbvh_model_desc* desc, const void* 
   }
   const bool timed = ev.e0 && ev.e1 && ev.e2;
   if (timed) cudaEventRecord(ev.e0, s);
-  traverse_kernel<<<unsigned((rays.n + 127) / 128), 128, 0, s>>>(nodes, ray_ptrs(rays), rays.n, to);
-  count_launches(1);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return NBVH_ERR_CUDA;
-  if (timed) cudaEventRecord(ev.e1, s);
-  EvalArgs a = base_args(desc, gp, table, mlp, rays);
-  a.n_rays = rays.n;
-  a.seg_count = w.seg_count;
-  a.seg_leaf = w.seg_leaf;
-  a.seg_t0 = w.seg_t0;
-  a.seg_t1 = w.seg_t1;
-  a.hits = out;
-  for (int wv = 0; wv < max_segs; ++wv) {
-    a.wave = wv;
-    a.queue = w.queue[wv & 1];
-    a.qlen = w.counters + wv;
-    a.next_queue = w.queue[(wv + 1) & 1];
-    a.next_qlen = w.counters + wv + 1;
-    e = launch_eval(desc, a, true, rays.n, s);
-    if (e != cudaSuccess) return status_of(e);
-  }
+  e = launch_query_stages(desc, gp, table, mlp, nodes, rays, max_segs, out, w, false, nullptr, 0,
+                          timed ? ev.e1 : nullptr, s);
+  if (e != cudaSuccess) return status_of(e);
   if (timed) {
     cudaEventRecord(ev.e2, s);
     std::lock_guard<std::mutex> lk(g_timing_mu);
@@ -421,6 +438,113 @@ extern "C" nbvh_status nbvh_bounce_rays(nbvh_rays rays, nbvh_hits hits, uint64_t
       ray_ptrs(rays), hits, rays.n, uint32_t(seed & 0xffffffffu), uint32_t(seed >> 32), o);
   count_launches(1);
   return status_of(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------- hybrid hierarchy (S9)
+namespace nbvh {
+namespace {
+bool tri_blas_valid(const nbvh_tri_blas* b) {
+  return b && b->nodes && b->n_nodes >= 1 && b->tris && b->leaf_range && b->tri_id;
+}
+bool hits_valid(const nbvh_hits& h) { return h.hit && h.t && h.nx && h.ny && h.nz && h.leaf; }
+
+TriBlasArgs tri_args(const nbvh_tri_blas& b, const nbvh_rays& rays, const nbvh_hits& h, int32_t* inst_out,
+                     int32_t inst_id, int32_t merge) {
+  TriBlasArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.nodes = b.nodes;
+  a.tris = b.tris;
+  a.leaf_range = b.leaf_range;
+  a.tri_id = b.tri_id;
+  a.rays = ray_ptrs(rays);
+  a.n = rays.n;
+  a.hits = h;
+  a.inst_out = inst_out;
+  a.inst_id = inst_id;
+  a.merge = merge;
+  return a;
+}
+
+int32_t hybrid_max_segs(const nbvh_instance* inst, int32_t n_inst) {
+  int32_t m = 0;
+  for (int i = 0; i < n_inst; ++i)
+    if (inst[i].kind == NBVH_BLAS_NEURAL) m = std::max(m, inst[i].max_segs);
+  return m;
+}
+
+bool instances_valid(const nbvh_instance* inst, int32_t n_inst) {
+  if (!inst || n_inst < 1 || n_inst > 64) return false;
+  for (int i = 0; i < n_inst; ++i) {
+    const nbvh_instance& x = inst[i];
+    if (x.kind == NBVH_BLAS_TRIANGLES) {
+      if (!tri_blas_valid(&x.tri)) return false;
+    } else if (x.kind == NBVH_BLAS_NEURAL) {
+      if (!nbvh_host::desc_valid(&x.desc) || !x.table || !x.mlp || !x.nodes || x.n_nodes < 1 ||
+          x.max_segs < 1 || x.max_segs > 4096)
+        return false;
+    } else {
+      return false;
+    }
+  }
+  return true;
+}
+}  // namespace
+}  // namespace nbvh
+
+extern "C" nbvh_status nbvh_trace_triangles(const nbvh_tri_blas* blas, nbvh_rays rays, nbvh_hits hits,
+                                            void* stream) {
+  if (!tri_blas_valid(blas) || !rays_valid(rays)) return NBVH_ERR_INVALID_ARG;
+  if (rays.n == 0) return NBVH_OK;
+  if (!hits_valid(hits) || rays.n > (int64_t(1) << 31) - 1) return NBVH_ERR_INVALID_ARG;
+  const TriBlasArgs a = tri_args(*blas, rays, hits, nullptr, 0, 0);
+  tri_trace_kernel<<<unsigned((rays.n + 127) / 128), 128, 0, as_stream(stream)>>>(a);
+  count_launches(1);
+  return status_of(cudaGetLastError());
+}
+
+extern "C" nbvh_status nbvh_hybrid_workspace_size(const nbvh_instance* inst, int32_t n_inst, int64_t n_rays,
+                                                  size_t* bytes) {
+  if (!instances_valid(inst, n_inst) || n_rays < 0 || !bytes) return NBVH_ERR_INVALID_ARG;
+  const int32_t ms = hybrid_max_segs(inst, n_inst);
+  *bytes = ms > 0 ? carve_query(nullptr, n_rays, ms).bytes : 256;
+  return NBVH_OK;
+}
+
+extern "C" nbvh_status nbvh_hybrid_trace(const nbvh_instance* inst, int32_t n_inst, nbvh_rays rays,
+                                         nbvh_hits out, int32_t* out_inst, void* workspace, size_t ws_bytes,
+                                         void* stream) {
+  if (!instances_valid(inst, n_inst) || !rays_valid(rays)) return NBVH_ERR_INVALID_ARG;
+  if (rays.n == 0) return NBVH_OK;
+  if (!hits_valid(out) || !out_inst || !workspace || rays.n > (int64_t(1) << 31) - 1) return NBVH_ERR_INVALID_ARG;
+  if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0) return NBVH_ERR_INVALID_ARG;
+  const int32_t ms = hybrid_max_segs(inst, n_inst);
+  QueryWs w = carve_query(workspace, rays.n, std::max(ms, 1));
+  if (ms > 0 && ws_bytes < w.bytes) return NBVH_ERR_WORKSPACE_TOO_SMALL;
+  std::vector<GridParams> gps(static_cast<size_t>(n_inst));
+  for (int i = 0; i < n_inst; ++i)
+    if (inst[i].kind == NBVH_BLAS_NEURAL && !make_grid(&inst[i].desc, gps[i])) return NBVH_ERR_INVALID_ARG;
+  cudaStream_t s = as_stream(stream);
+  hits_clear_kernel<<<unsigned((rays.n + 255) / 256), 256, 0, s>>>(out, out_inst, rays.n);
+  count_launches(1);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return NBVH_ERR_CUDA;
+  for (int i = 0; i < n_inst; ++i) {
+    const nbvh_instance& x = inst[i];
+    if (x.kind == NBVH_BLAS_TRIANGLES) {
+      const TriBlasArgs a = tri_args(x.tri, rays, out, out_inst, i, 1);
+      tri_trace_kernel<<<unsigned((rays.n + 127) / 128), 128, 0, s>>>(a);
+      count_launches(1);
+      e = cudaGetLastError();
+    } else {
+      e = cudaMemsetAsync(w.counters, 0, sizeof(int32_t) * size_t(x.max_segs + 2), s);
+      if (e != cudaSuccess) return NBVH_ERR_CUDA;
+      QueryWs wi = carve_query(workspace, rays.n, x.max_segs);
+      e = launch_query_stages(&x.desc, gps[i], x.table, x.mlp, x.nodes, rays, x.max_segs, out, wi, true, out_inst,
+                              i, nullptr, s);
+    }
+    if (e != cudaSuccess) return status_of(e);
+  }
+  return NBVH_OK;
 }
 
 extern "C" nbvh_status nbvh_get_device_status(void* stream) {

@@ -14,6 +14,10 @@ struct TraverseOut {
   int32_t* queue0;
   int32_t* qlen0;
   nbvh_hits hits;
+  // Merge mode (hybrid hierarchy): the hit record already holds the closest
+  // hit found so far; it is kept, and leaves whose clipped segment starts at or
+  // beyond it are skipped (a neural hit never lies before its segment's t0).
+  int32_t merge;
 };
 
 // One thread per ray. Depth-first with a short stack; the nearer child is
@@ -33,6 +37,8 @@ __global__ void __launch_bounds__(128) traverse_kernel(const nbvh_node* __restri
     const float tmin = rays.tmin[r], tmax = rays.tmax[r];
     const RayR ray = make_rayr(ox, oy, oz, dx, dy, dz, tmin, tmax);
     const int max_segs = out.max_segs;
+    const bool merge = out.merge != 0;
+    const float best = merge ? out.hits.t[r] : 0.0f;
     bool overflow = false;
     auto emit = [&](int leaf, float t0, float t1) {
       int pos;
@@ -73,8 +79,12 @@ __global__ void __launch_bounds__(128) traverse_kernel(const nbvh_node* __restri
       const float4 c = __ldg(np + 2);
       const int4 e = __ldg(reinterpret_cast<const int4*>(np + 3));
       float a0, a1, b0, b1;
-      const bool h0 = clip_box(ray, a.x, a.y, a.z, a.w, b.x, b.y, a0, a1);
-      const bool h1 = (e.y != kNodeNone) && clip_box(ray, b.z, b.w, c.x, c.y, c.z, c.w, b0, b1);
+      bool h0 = clip_box(ray, a.x, a.y, a.z, a.w, b.x, b.y, a0, a1);
+      bool h1 = (e.y != kNodeNone) && clip_box(ray, b.z, b.w, c.x, c.y, c.z, c.w, b0, b1);
+      if (merge) {
+        h0 = h0 && a0 < best;
+        h1 = h1 && b0 < best;
+      }
       if (h0 && e.x < 0) emit(~e.x, a0, a1);
       if (h1 && e.y < 0) emit(~e.y, b0, b1);
       const bool g0 = h0 && e.x >= 0;
@@ -98,7 +108,7 @@ __global__ void __launch_bounds__(128) traverse_kernel(const nbvh_node* __restri
     }
     out.seg_count[r] = count;
     if (overflow) set_status(NBVH_ERR_SEGMENT_OVERFLOW);
-    if (out.hits.hit) {
+    if (out.hits.hit && !merge) {
       out.hits.hit[r] = 0;
       out.hits.t[r] = __int_as_float(0x7f800000);
       out.hits.nx[r] = 0.0f;

@@ -78,6 +78,19 @@ class Optim(ctypes.Structure):
 
 TRAIN_PROBED_MIX, TRAIN_PAPER = 0, 1
 
+
+class TriBlas(ctypes.Structure):
+    _fields_ = [("nodes", c_void_p), ("n_nodes", c_int32), ("tris", c_void_p), ("leaf_range", c_void_p),
+                ("tri_id", c_void_p)]
+
+
+class Instance(ctypes.Structure):
+    _fields_ = [("kind", c_int32), ("tri", TriBlas), ("desc", ModelDesc), ("table", c_void_p), ("mlp", c_void_p),
+                ("nodes", c_void_p), ("n_nodes", c_int32), ("max_segs", c_int32)]
+
+
+BLAS_TRIANGLES, BLAS_NEURAL = 0, 1
+
 _lib = None
 
 _SIGS = {
@@ -122,6 +135,12 @@ _SIGS = {
     "nbvh_graph_end": (c_int32, [c_void_p, POINTER(c_void_p)]),
     "nbvh_graph_launch": (c_int32, [c_void_p, c_void_p]),
     "nbvh_graph_destroy": (c_int32, [c_void_p]),
+    "nbvh_build_tri_blas": (c_int32, [c_void_p, c_int64, c_int32, c_void_p, c_int32, POINTER(c_int32), c_void_p,
+                                      c_void_p, c_int32, POINTER(c_int32)]),
+    "nbvh_trace_triangles": (c_int32, [POINTER(TriBlas), Rays, Hits, c_void_p]),
+    "nbvh_hybrid_workspace_size": (c_int32, [POINTER(Instance), c_int32, c_int64, POINTER(c_size_t)]),
+    "nbvh_hybrid_trace": (c_int32, [POINTER(Instance), c_int32, Rays, Hits, c_void_p, c_void_p, c_size_t,
+                                    c_void_p]),
     "nbvh_get_device_status": (c_int32, [c_void_p]),
 }
 
@@ -601,3 +620,103 @@ class Graph:
             self.destroy()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------- hybrid hierarchy (S9)
+def build_tri_blas(tris: np.ndarray, max_leaf: int = 4) -> dict:
+    """Host binned-SAH BVH over triangles (nbvh_build_tri_blas)."""
+    tris = np.ascontiguousarray(tris, np.float32)
+    n = len(tris)
+    cap = max(1, n - 1)
+    nodes = np.zeros(cap * 64, np.uint8)
+    n_nodes = c_int32()
+    n_leaves = c_int32()
+    perm = np.zeros(n, np.int32)
+    rng = np.zeros(2 * n, np.int32)
+    _check(lib().nbvh_build_tri_blas(tris.ctypes.data_as(c_void_p), n, max_leaf, nodes.ctypes.data_as(c_void_p),
+                                     cap, ctypes.byref(n_nodes), perm.ctypes.data_as(c_void_p),
+                                     rng.ctypes.data_as(c_void_p), n, ctypes.byref(n_leaves)), "build_tri_blas")
+    return {"nodes": nodes[:n_nodes.value * 64].copy(), "n_nodes": n_nodes.value, "tri_perm": perm,
+            "leaf_range": rng[:2 * n_leaves.value].reshape(-1, 2).copy(), "n_leaves": n_leaves.value}
+
+
+class DeviceTriBlas:
+    """Device copy of a triangle BLAS: nodes, leaf-order triangles, leaf
+    ranges and the caller index of every leaf-order triangle."""
+
+    def __init__(self, tris: np.ndarray, blas: dict, device="cuda"):
+        torch = _torch()
+        t = np.ascontiguousarray(tris, np.float32).reshape(-1, 9)
+        self.nodes = torch.as_tensor(blas["nodes"], device=device)
+        self.tris = torch.as_tensor(np.ascontiguousarray(t[blas["tri_perm"]]), device=device)
+        self.leaf_range = torch.as_tensor(np.ascontiguousarray(blas["leaf_range"], np.int32), device=device)
+        self.tri_id = torch.as_tensor(blas["tri_perm"], device=device)
+        s = TriBlas()
+        s.nodes = self.nodes.data_ptr()
+        s.n_nodes = blas["n_nodes"]
+        s.tris = self.tris.data_ptr()
+        s.leaf_range = self.leaf_range.data_ptr()
+        s.tri_id = self.tri_id.data_ptr()
+        self.struct = s
+
+
+def trace_triangles(blas: DeviceTriBlas, rays: dict, out=None):
+    n = rays["ox"].numel()
+    if out is None:
+        out = new_hits(n, rays["ox"].device)
+    _check(lib().nbvh_trace_triangles(ctypes.byref(blas.struct), rays_struct(rays), hits_struct(out), _stream()),
+           "trace_triangles")
+    return out
+
+
+def tri_instance(blas: DeviceTriBlas) -> Instance:
+    x = Instance()
+    x.kind = BLAS_TRIANGLES
+    x.tri = blas.struct
+    return x
+
+
+def neural_instance(desc: ModelDesc, table, mlp, nodes, n_nodes: int, max_segs: int) -> Instance:
+    x = Instance()
+    x.kind = BLAS_NEURAL
+    x.desc = desc
+    x.table = table.data_ptr()
+    x.mlp = mlp.data_ptr()
+    x.nodes = nodes.data_ptr()
+    x.n_nodes = n_nodes
+    x.max_segs = max_segs
+    return x
+
+
+def instance_array(instances) -> ctypes.Array:
+    arr = (Instance * len(instances))()
+    for i, x in enumerate(instances):
+        arr[i] = x
+    return arr
+
+
+def hybrid_workspace_size(instances, n_rays: int) -> int:
+    arr = instance_array(instances)
+    b = c_size_t()
+    _check(lib().nbvh_hybrid_workspace_size(arr, len(arr), n_rays, ctypes.byref(b)), "hybrid_workspace_size")
+    return b.value
+
+
+def hybrid_trace(instances, rays: dict, out=None, inst_out=None, workspace=None):
+    """Closest hit over the instances of the two-level hierarchy
+    (nbvh_hybrid_trace). Returns (hits, instance index per ray)."""
+    torch = _torch()
+    n = rays["ox"].numel()
+    dev = rays["ox"].device
+    if out is None:
+        out = new_hits(n, dev)
+    if inst_out is None:
+        inst_out = torch.empty(n, dtype=torch.int32, device=dev)
+    arr = instance_array(instances)
+    if workspace is None:
+        workspace = new_workspace(hybrid_workspace_size(instances, n), dev)
+    base = aligned_ptr(workspace)
+    avail = workspace.numel() - (base - workspace.data_ptr())
+    _check(lib().nbvh_hybrid_trace(arr, len(arr), rays_struct(rays), hits_struct(out), _ptr(inst_out),
+                                   c_void_p(base), avail, _stream()), "hybrid_trace")
+    return out, inst_out

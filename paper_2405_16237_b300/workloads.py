@@ -195,16 +195,13 @@ def _pack(o: np.ndarray, d: np.ndarray, tmin, tmax) -> dict:
     }
 
 
-def camera_rays(width: int, height: int, seed: int = SEED_BASE + 7, radius: float = 2.0,
-                fov_deg: float = 40.0) -> dict:
-    """Pinhole primary rays, one per pixel centre, row-major. The camera sits at
-    a seeded point of the sphere of radius ``radius`` and looks at the origin;
-    up is +y (+x if colinear); vertical field of view ``fov_deg``."""
-    rng = np.random.default_rng(seed)
-    u = rng.normal(size=3)
-    u /= np.linalg.norm(u)
-    eye = radius * u
-    fwd = -u
+def look_at_rays(width: int, height: int, eye, target=(0.0, 0.0, 0.0), fov_deg: float = 40.0) -> dict:
+    """Pinhole primary rays, one per pixel centre, row-major, from ``eye``
+    towards ``target``; up is +y (+x if colinear); vertical field of view
+    ``fov_deg``."""
+    eye = np.asarray(eye, np.float64)
+    fwd = np.asarray(target, np.float64) - eye
+    fwd /= np.linalg.norm(fwd)
     up = np.array([0.0, 1.0, 0.0])
     if abs(np.dot(up, fwd)) > 0.999:
         up = np.array([1.0, 0.0, 0.0])
@@ -220,6 +217,17 @@ def camera_rays(width: int, height: int, seed: int = SEED_BASE + 7, radius: floa
     d /= np.linalg.norm(d, axis=1, keepdims=True)
     o = np.broadcast_to(eye, d.shape)
     return _pack(o, d, 0.0, np.inf)
+
+
+def camera_rays(width: int, height: int, seed: int = SEED_BASE + 7, radius: float = 2.0,
+                fov_deg: float = 40.0) -> dict:
+    """Pinhole primary rays, one per pixel centre, row-major. The camera sits at
+    a seeded point of the sphere of radius ``radius`` and looks at the origin;
+    up is +y (+x if colinear); vertical field of view ``fov_deg``."""
+    rng = np.random.default_rng(seed)
+    u = rng.normal(size=3)
+    u /= np.linalg.norm(u)
+    return look_at_rays(width, height, radius * u, (0.0, 0.0, 0.0), fov_deg)
 
 
 def _sphere_dir(rng, n):
@@ -346,3 +354,72 @@ C1 = Workload(
     model=ModelConfig(n_levels=16, n_features=2, log2_table=20, base_res=16, growth=1.5,
                       n_samples=16, n_hidden=3, width=64),
     n_leaves=2048, table_dtype="f16")
+
+
+# ----------------------------------------------------------------------------
+# Hybrid scene: neural assets next to classical triangles (Sec. 7, Table 1:
+# scenes mixing large assets, stored as N-BVHs, with ordinary geometry)
+# ----------------------------------------------------------------------------
+
+def ground_heightfield(n_cells: int = 500, half: float = 1.5, y0: float = -0.35, amplitude: float = 0.03,
+                       seed: int = SEED_BASE + 5) -> np.ndarray:
+    """A displaced ground grid over [-half, half]^2 (xz) at height ``y0``:
+    (n_cells + 1)^2 vertices, 2 n_cells^2 triangles (500 cells: 500,000)."""
+    g = np.linspace(-half, half, n_cells + 1)
+    X, Z = np.meshgrid(g, g, indexing="ij")
+    p = np.stack([X.ravel(), np.zeros(X.size), Z.ravel()], 1)
+    h = fbm(p * 0.5, seed)
+    P = np.stack([X.ravel(), y0 + amplitude * h, Z.ravel()], 1).reshape(n_cells + 1, n_cells + 1, 3)
+    a, b = P[:-1, :-1], P[1:, :-1]
+    c, d = P[:-1, 1:], P[1:, 1:]
+    t1 = np.stack([a, c, b], 2).reshape(-1, 3, 3)
+    t2 = np.stack([b, c, d], 2).reshape(-1, 3, 3)
+    return np.concatenate([t1, t2], 0).astype(np.float32)
+
+
+@dataclass
+class HybridAsset:
+    tris: np.ndarray
+    model: "ModelConfig"
+    n_leaves: int
+
+
+def scene_hybrid(n_assets: int = 16, seed: int = SEED_BASE + 4, asset_level: int = 5, ground_cells: int = 500,
+                 n_leaves: int = 128):
+    """Neural assets on a classical ground. Each asset is a displaced icosphere
+    (20 * 4^asset_level triangles, radius U(0.10, 0.18)) standing on the
+    ground at a jittered 4x4 grid position; its model draws F in {2, 4, 8}
+    and log2 T in {16, ..., 22} (seeded), with n_levels = 32 / F so that
+    N * L * F stays 16 * 32 = 512, base resolution 16 and growth reaching a
+    finest resolution of 1024 (the paper's 8 levels up to 1024 at F = 4).
+    Returns (ground triangles, [HybridAsset])."""
+    rng = np.random.default_rng(seed)
+    ground = ground_heightfield(ground_cells)
+    assets = []
+    side = int(math.ceil(math.sqrt(n_assets)))
+    for k in range(n_assets):
+        gx, gz = k % side, k // side
+        r = rng.uniform(0.10, 0.18)
+        cx = -1.05 + 2.1 * (gx + 0.5) / side + rng.uniform(-0.08, 0.08)
+        cz = -1.05 + 2.1 * (gz + 0.5) / side + rng.uniform(-0.08, 0.08)
+        tris = scene_icosphere(level=asset_level, seed=seed * 7 + k, radius=r, amplitude=0.2 * r)
+        tris = tris + np.array([cx, -0.35 + r, cz], np.float32)
+        F = int(rng.choice([2, 4, 8]))
+        lt = int(rng.integers(16, 23))
+        L = 32 // F
+        # the model descriptor stores the growth factor as float32: use a
+        # float32 value so every consumer derives the same level resolutions
+        growth = float(np.float32((1024.0 / 16.0) ** (1.0 / (L - 1))))
+        model = ModelConfig(n_levels=L, n_features=F, log2_table=lt, base_res=16, growth=growth, n_samples=16,
+                            n_hidden=3, width=64)
+        assets.append(HybridAsset(tris.astype(np.float32), model, n_leaves))
+    return ground, assets
+
+
+def hybrid_camera_rays(width: int, height: int) -> dict:
+    """The hybrid scene's camera: radius 3.2 at 35 degrees elevation, looking
+    at (0, -0.2, 0), 40 degree vertical field of view."""
+    el = math.radians(35.0)
+    az = math.radians(30.0)
+    eye = (3.2 * math.cos(el) * math.sin(az), 3.2 * math.sin(el), 3.2 * math.cos(el) * math.cos(az))
+    return look_at_rays(width, height, eye, (0.0, -0.2, 0.0), 40.0)

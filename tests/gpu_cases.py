@@ -137,3 +137,76 @@ def ambiguous_rays(res, n_rays, rel=1e-5):
     for r, _ in seg["grazing_pairs"]:
         amb[int(r)] = True
     return amb
+
+
+# ---------------------------------------------------------------- hybrid hierarchy (S9)
+def small_hybrid_scene(n_assets: int = 3, seed: int = W.SEED_BASE + 40):
+    """A small version of the hybrid scene: a 40x40-cell ground (3,200
+    triangles) and level-3 icosphere assets (1,280 triangles, 16 leaves) with
+    hashed levels of 2^12..2^14 entries."""
+    ground, assets = W.scene_hybrid(n_assets=n_assets, seed=seed, asset_level=3, ground_cells=40, n_leaves=16)
+    rng = np.random.default_rng(seed + 1)
+    for a in assets:
+        a.model = replace(a.model, log2_table=int(rng.integers(12, 15)))
+    return ground, assets
+
+
+def hybrid_rays(n_side: int = 40, n_chords: int = 800, seed: int = W.SEED_BASE + 41):
+    cam = W.hybrid_camera_rays(n_side, n_side)
+    ch = W.chord_rays(n_chords, seed, centre=(0.0, -0.2, 0.0), radius=1.6)
+    return {k: np.concatenate([cam[k], ch[k]]) for k in W.RAY_KEYS}
+
+
+class HybridBuilt:
+    """Device instances (triangle BLAS first, then the neural assets) and the
+    oracle's description of the same instances."""
+
+    def __init__(self, ground, assets, mlp_prec: int, table_prec: int = B.BF16, table_scale: float = 1.0,
+                 gain: float = 2.0, max_segs: int = 16):
+        import torch
+        self.ground = ground
+        self.blas = B.build_tri_blas(ground, 4)
+        self.dev_blas = B.DeviceTriBlas(ground, self.blas)
+        self.instances = [B.tri_instance(self.dev_blas)]
+        self.oinstances = [{"kind": "triangles", "tris": ground}]
+        self.keep = []
+        for k, a in enumerate(assets):
+            lv = B.build_leaves(a.tris, a.n_leaves, 1e-4)
+            info = lv["info"]
+            desc = B.model_desc(a.model, table_prec, mlp_prec, info["centre"], info["extent"])
+            lay = B.level_layout(desc)
+            tab = W.init_table(lay["total"], a.model.n_features, 500 + k, table_scale)
+            t = torch.as_tensor(tab)
+            t = t.to(torch.bfloat16) if table_prec == B.BF16 else (t.half() if table_prec == B.FP16 else t)
+            table_host = t.float().numpy().astype(np.float64)
+            table = t.cuda()
+            layers = W.init_mlp(a.model.mlp_dims(), 600 + k, gain=gain)
+            mlp = torch.as_tensor(B.pack_mlp(layers)).cuda()
+            nodes = torch.as_tensor(lv["nodes"]).cuda()
+            self.keep += [table, mlp, nodes]
+            self.instances.append(B.neural_instance(desc, table, mlp, nodes, lv["n_nodes"], max_segs))
+            self.oinstances.append({"kind": "neural", "leaves": O.build_leaves(a.tris, a.n_leaves, 1e-4),
+                                    "table": table_host, "layers": layers,
+                                    "layout": O.level_layout(a.model.n_levels, a.model.base_res, a.model.growth,
+                                                             a.model.log2_table),
+                                    "n_samples": a.model.n_samples})
+
+
+def hybrid_ambiguous(ref, n_rays, rel=1e-5):
+    """Rays whose hybrid answer depends on rounding: the triangle answer's
+    margin, an ambiguous neural answer, or two instances' hits within
+    rel * |t| of each other."""
+    amb = np.zeros(n_rays, bool)
+    ts = []
+    for ans in ref["answers"]:
+        if "margin" in ans:
+            amb |= ans["margin"] <= rel
+        else:
+            amb |= ambiguous_rays(ans["query"], n_rays, rel)
+        ts.append(np.where(ans["hit"].astype(bool), ans["t"], np.inf))
+    T = np.sort(np.stack(ts, 1), 1)
+    if T.shape[1] > 1:
+        with np.errstate(invalid="ignore"):
+            close = np.isfinite(T[:, 1]) & (T[:, 1] - T[:, 0] <= rel * np.maximum(1.0, np.abs(T[:, 0])))
+        amb |= close
+    return amb

@@ -1,0 +1,159 @@
+"""GPU parity of the hybrid two-level hierarchy (S9; Sec. 7: classical and
+neural BLASes answer with the same record, the closest one wins) against the
+FP64 oracle, through the C ABI: the triangle BLAS against brute force over
+every triangle, the hybrid trace against the oracle's in-order merge, and the
+graph-captured bounce loop against its eager run."""
+import numpy as np
+import pytest
+
+from gpu_cases import HybridBuilt, hybrid_ambiguous, hybrid_rays, small_hybrid_scene
+from oracle import nbvh_oracle as O
+from paper_2405_16237_b300 import nbvh as B
+from paper_2405_16237_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _torch():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    return torch
+
+
+def _np(h):
+    return {k: v.cpu().numpy() for k, v in h.items()}
+
+
+def _nrm(h):
+    return np.stack([h["nx"], h["ny"], h["nz"]], 1)
+
+
+@pytest.mark.parametrize("max_leaf", [1, 4, 8])
+def test_trace_triangles_matches_brute_force(max_leaf):
+    """Closest triangle hit: hit flag and triangle index exact and t within
+    1e-5 relative wherever the FP64 answer is not within 1e-5 of flipping."""
+    _torch()
+    ground, assets = small_hybrid_scene(2)
+    tris = np.concatenate([ground, assets[0].tris, assets[1].tris])
+    blas = B.build_tri_blas(tris, max_leaf)
+    dev = B.DeviceTriBlas(tris, blas)
+    rays = hybrid_rays(32, 600)
+    h = _np(B.trace_triangles(dev, B.to_device_rays(rays)))
+    assert B.device_status() == 0
+    o, d, tmin, tmax = O.rays_od(rays)
+    ref = O.closest_triangle_hit(o, d, tmin, tmax, tris)
+    ok = ref["margin"] > 1e-5
+    assert ok.mean() > 0.97
+    assert np.array_equal(h["hit"][ok].astype(bool), ref["hit"][ok].astype(bool))
+    assert np.array_equal(h["leaf"][ok], ref["index"][ok])
+    hh = ok & ref["hit"].astype(bool)
+    assert hh.sum() > 500
+    assert np.all(np.abs(h["t"][hh] - ref["t"][hh]) <= 1e-5 * np.abs(ref["t"][hh]))
+    assert np.max(np.abs(_nrm(h)[hh] - ref["normal"][hh])) <= 1e-4
+    miss = ~h["hit"].astype(bool)
+    assert np.all(np.isinf(h["t"][miss])) and np.all(h["leaf"][miss] == -1)
+
+
+def test_hybrid_trace_fp32_matches_oracle():
+    """FP32 neural instances plus the triangle BLAS: instance, hit and leaf
+    exact, t within 1e-5 relative, on every ray whose answer is not within
+    rounding of a flip."""
+    _torch()
+    ground, assets = small_hybrid_scene(3)
+    hb = HybridBuilt(ground, assets, B.FP32, table_prec=B.FP32)
+    rays = hybrid_rays(40, 800)
+    h, inst = B.hybrid_trace(hb.instances, B.to_device_rays(rays))
+    assert B.device_status() == 0
+    h = _np(h)
+    inst = inst.cpu().numpy()
+    ref = O.hybrid_trace(rays, hb.oinstances)
+    n = len(rays["ox"])
+    ok = ~hybrid_ambiguous(ref, n)
+    assert ok.mean() > 0.95
+    assert np.array_equal(inst[ok], ref["inst"][ok])
+    assert np.array_equal(h["hit"][ok].astype(bool), ref["hit"][ok].astype(bool))
+    assert np.array_equal(h["leaf"][ok], ref["leaf"][ok])
+    hh = ok & ref["hit"].astype(bool)
+    assert np.all(np.abs(h["t"][hh] - ref["t"][hh]) <= 1e-5 * np.abs(ref["t"][hh]))
+    # both kinds of instance answer some rays
+    assert np.sum(hh & (ref["inst"] == 0)) > 100 and np.sum(hh & (ref["inst"] > 0)) > 50
+
+
+@pytest.mark.parametrize("mp", [B.FP16, B.BF16])
+def test_hybrid_trace_tensor_core_matches_oracle(mp):
+    """BF16 tables, FP16/BF16 tensor-core MLPs: winning instance agreement
+    >= 99.5%, depth <= 2e-3 and mean normal error <= 1 degree where both sides
+    pick the same instance and leaf."""
+    _torch()
+    ground, assets = small_hybrid_scene(3)
+    hb = HybridBuilt(ground, assets, mp, table_prec=B.BF16)
+    rays = hybrid_rays(40, 800)
+    h, inst = B.hybrid_trace(hb.instances, B.to_device_rays(rays))
+    assert B.device_status() == 0
+    h = _np(h)
+    inst = inst.cpu().numpy()
+    ref = O.hybrid_trace(rays, hb.oinstances)
+    agree = np.mean(inst == ref["inst"])
+    assert agree >= 0.995, agree
+    same = (inst == ref["inst"]) & (h["leaf"] == ref["leaf"]) & ref["hit"].astype(bool)
+    assert same.sum() > 500
+    assert np.max(np.abs(h["t"][same] - ref["t"][same])) <= 2e-3
+    c = np.clip(np.sum(_nrm(h)[same] * ref["normal"][same], 1), -1.0, 1.0)
+    assert np.degrees(np.arccos(c)).mean() <= 1.0
+
+
+def test_hybrid_single_instance_reduces_to_its_query():
+    """One neural instance alone: the hybrid trace equals nbvh_query_rays bit
+    for bit (the merge pass starts from an empty record)."""
+    torch = _torch()
+    ground, assets = small_hybrid_scene(1)
+    hb = HybridBuilt(ground, assets, B.BF16, table_prec=B.BF16)
+    rays = B.to_device_rays(hybrid_rays(40, 800))
+    x = hb.instances[1]
+    h, inst = B.hybrid_trace([x], rays)
+    q = B.query_rays(x.desc, hb.keep[0], hb.keep[1], hb.keep[2], x.n_nodes, rays, x.max_segs)
+    assert B.device_status() == 0
+    for k in h:
+        assert torch.equal(h[k], q[k]), k
+    assert torch.equal(inst, torch.where(q["hit"] > 0, 0, -1).to(torch.int32))
+
+
+def test_hybrid_graph_bounce_loop_equals_eager():
+    """Three bounces of hybrid trace + cosine bounce, recorded as one CUDA
+    graph and replayed, are bit-identical to the eager loop."""
+    torch = _torch()
+    ground, assets = small_hybrid_scene(3)
+    hb = HybridBuilt(ground, assets, B.BF16, table_prec=B.BF16)
+    rays0 = B.to_device_rays(hybrid_rays(40, 0))
+    n = rays0["ox"].numel()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        def buffers():
+            return ([B.new_rays(n) for _ in range(3)], [B.new_hits(n) for _ in range(3)],
+                    [torch.empty(n, dtype=torch.int32, device="cuda") for _ in range(3)],
+                    B.new_workspace(B.hybrid_workspace_size(hb.instances, n)))
+
+        def loop(rb, hits, insts, ws):
+            r = rays0
+            for b in range(3):
+                B.hybrid_trace(hb.instances, r, out=hits[b], inst_out=insts[b], workspace=ws)
+                r = B.bounce_rays(r, hits[b], 17 + b, out=rb[b])
+
+        e = buffers()
+        loop(*e)
+        g_bufs = buffers()
+        g = B.Graph.record(lambda: loop(*g_bufs))
+        for _ in range(2):
+            for hh in g_bufs[1]:
+                for v in hh.values():
+                    v.fill_(3)
+            g.launch()
+        s.synchronize()
+        g.destroy()
+    assert B.device_status() == 0
+    for b in range(3):
+        for k in e[1][b]:
+            assert torch.equal(e[1][b][k], g_bufs[1][b][k]), (b, k)
+        assert torch.equal(e[2][b], g_bufs[2][b])
+    # later bounces still find hits of both kinds
+    assert int((e[2][1] == 0).sum()) > 0 and int((e[2][1] > 0).sum()) > 0

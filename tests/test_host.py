@@ -128,3 +128,57 @@ def test_build_leaves_rejects_bad_arguments():
         B.build_leaves(tris, 11)
     with pytest.raises(B.NBVHError):
         B.build_leaves(tris, 0)
+
+
+@pytest.mark.parametrize("max_leaf", [1, 4, 16])
+def test_tri_blas_build_invariants(max_leaf):
+    """Triangle BLAS (host SAH build): every triangle in exactly one leaf of
+    at most max_leaf triangles, each child box the exact AABB of its
+    subtree's triangles and nested in its parent, a binary tree of
+    n_leaves - 1 internal nodes."""
+    ground = W.ground_heightfield(16, amplitude=0.05)
+    sph = W.scene_icosphere(level=2, radius=0.3)
+    tris = np.concatenate([ground, sph]).astype(np.float32)
+    blas = B.build_tri_blas(tris, max_leaf)
+    nl = blas["n_leaves"]
+    assert blas["n_nodes"] == max(1, nl - 1)
+    assert sorted(blas["tri_perm"].tolist()) == list(range(len(tris)))
+    rng = blas["leaf_range"]
+    assert rng[0, 0] == 0 and rng[-1, 1] == len(tris) and np.all(rng[1:, 0] == rng[:-1, 1])
+    assert np.all(rng[:, 1] - rng[:, 0] >= 1) and np.all(rng[:, 1] - rng[:, 0] <= max_leaf)
+    nodes = B.node_array({"nodes": blas["nodes"]})
+    seen = []
+
+    def walk(i, lo, hi):
+        nd = nodes[i]
+        tri_sets = []
+        for c, l, h in ((nd["child0"], nd["lo0"], nd["hi0"]), (nd["child1"], nd["lo1"], nd["hi1"])):
+            assert np.all(l >= lo) and np.all(h <= hi)
+            if c < 0:
+                seen.append(~c)
+                a, b = rng[~c]
+                ids = blas["tri_perm"][a:b]
+            else:
+                ids = walk(c, l, h)
+            v = tris[ids].reshape(-1, 3)
+            assert np.array_equal(v.min(0), l) and np.array_equal(v.max(0), h)
+            tri_sets.append(ids)
+        return np.concatenate(tri_sets)
+
+    walk(0, np.full(3, -np.inf), np.full(3, np.inf))
+    assert sorted(seen) == list(range(nl))
+
+
+def test_tri_blas_single_leaf_and_bad_arguments():
+    # three copies of one triangle: no split separates them, so one leaf
+    tris = np.repeat(W.scene_random_tris(1, seed=8), 3, axis=0)
+    blas = B.build_tri_blas(tris, 4)
+    assert blas["n_leaves"] == 1 and blas["n_nodes"] == 1
+    nd = B.node_array({"nodes": blas["nodes"]})[0]
+    assert nd["child0"] == ~0 and nd["child1"] == 0x7fffffff
+    with pytest.raises(B.NBVHError):
+        B.build_tri_blas(tris, 0)
+    bad = tris.copy()
+    bad[1, 1, 1] = np.nan
+    with pytest.raises(B.NBVHError):
+        B.build_tri_blas(bad, 4)

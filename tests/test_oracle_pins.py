@@ -545,3 +545,104 @@ def test_bounce_rays_cosine_hemisphere():
     t, b = O.onb(nn)
     assert np.allclose(np.sum(t * nn, 1), 0, atol=1e-12) and np.allclose(np.sum(t * b, 1), 0, atol=1e-12)
     assert np.allclose(p, d + 1e-4 * nn)
+
+
+# ---------------------------------------------------------------- S9 hybrid hierarchy
+def _flat_grid_case(n_cells=20, half=1.0, y0=-0.25, n_rays=400, seed=3):
+    tris = W.ground_heightfield(n_cells, half=half, y0=y0, amplitude=0.0)
+    rng = np.random.default_rng(seed)
+    h = 2 * half / n_cells
+    # targets away from cell edges and diagonals
+    # one cell clear of the border: rays cross a grid raised by 0.2 inside it
+    i = rng.integers(1, n_cells - 1, n_rays)
+    j = rng.integers(1, n_cells - 1, n_rays)
+    fx = rng.uniform(0.1, 0.9, n_rays)
+    fz = rng.uniform(0.1, 0.9, n_rays)
+    keep = np.abs(fx + fz - 1.0) > 0.05
+    i, j, fx, fz = i[keep], j[keep], fx[keep], fz[keep]
+    target = np.stack([-half + (i + fx) * h, np.full(len(i), y0), -half + (j + fz) * h], 1)
+    o = target + np.array([0.0, 1.0, 0.0]) + rng.uniform(-0.3, 0.3, (len(i), 3)) * np.array([1.0, 0.0, 1.0])
+    d = target - o
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    return tris, i, j, fx, fz, o, d, target
+
+
+def test_closest_triangle_hit_flat_grid_closed_form():
+    """A flat grid: t = (y0 - o_y) / d_y, the triangle is the grid cell's
+    lower or upper half (fx + fz < 1 or > 1), the normal is +y (facing -d)."""
+    tris, i, j, fx, fz, o, d, target = _flat_grid_case()
+    n_cells = 20
+    n = len(o)
+    res = O.closest_triangle_hit(o, d, np.zeros(n), np.full(n, np.inf), tris)
+    assert np.all(res["hit"] == 1)
+    t_exact = (-0.25 - o[:, 1]) / d[:, 1]
+    assert np.allclose(res["t"], t_exact, rtol=1e-12, atol=0)
+    idx = np.where(fx + fz < 1.0, i * n_cells + j, n_cells * n_cells + i * n_cells + j)
+    assert np.array_equal(res["index"], idx)
+    assert np.allclose(res["normal"], [0.0, 1.0, 0.0], atol=1e-12)
+    # the interval decides: tmax below the plane's t misses, tmin beyond it misses
+    r2 = O.closest_triangle_hit(o, d, np.zeros(n), t_exact * 0.999, tris)
+    r3 = O.closest_triangle_hit(o, d, t_exact * 1.001, np.full(n, np.inf), tris)
+    assert not r2["hit"].any() and not r3["hit"].any()
+
+
+def test_closest_triangle_hit_nearest_and_lowest_index_on_ties():
+    """Two parallel grids: rays from above take the upper one, from below the
+    lower one; a duplicated triangle set resolves ties to the first copy."""
+    tris, i, j, fx, fz, o, d, target = _flat_grid_case(n_rays=100)
+    upper = tris + np.array([0.0, 0.2, 0.0], np.float32)
+    both = np.concatenate([tris, upper])
+    n = len(o)
+    a = O.closest_triangle_hit(o, d, np.zeros(n), np.full(n, np.inf), both)
+    assert np.all(a["index"] >= len(tris))
+    assert np.allclose(a["t"], (-0.05 - o[:, 1]) / d[:, 1], rtol=1e-12)
+    ob = o * np.array([1.0, -1.0, 1.0]) + np.array([0.0, -0.5, 0.0])
+    db = d * np.array([1.0, -1.0, 1.0])
+    b = O.closest_triangle_hit(ob, db, np.zeros(n), np.full(n, np.inf), both)
+    assert np.all(b["index"] < len(tris))
+    assert np.allclose(b["normal"], [0.0, -1.0, 0.0], atol=1e-12)
+    dup = np.concatenate([tris, tris])
+    c = O.closest_triangle_hit(o, d, np.zeros(n), np.full(n, np.inf), dup)
+    assert np.all(c["index"] < len(tris)) and np.all(c["margin"] == 0.0)
+
+
+def test_hybrid_trace_split_instances_equal_their_union():
+    """Splitting a triangle set into two instances gives the closest hit over
+    the union: same t, and the instance/index that hold the union's answer."""
+    g = W.ground_heightfield(12, half=1.0, y0=-0.3, amplitude=0.05)
+    s = W.scene_icosphere(level=2, radius=0.3) + np.array([0.0, 0.0, 0.0], np.float32)
+    rays = W.chord_rays(300, seed=5, radius=1.2)
+    o, d, tmin, tmax = O.rays_od(rays)
+    union = np.concatenate([g, s])
+    u = O.closest_triangle_hit(o, d, tmin, tmax, union)
+    h = O.hybrid_trace(rays, [{"kind": "triangles", "tris": g}, {"kind": "triangles", "tris": s}])
+    assert np.array_equal(h["hit"], u["hit"])
+    assert np.array_equal(h["t"], u["t"])
+    hit = u["hit"].astype(bool)
+    assert hit.sum() > 50
+    glob = np.where(h["inst"] == 0, h["leaf"], h["leaf"] + len(g))
+    assert np.array_equal(glob[hit], u["index"][hit])
+    assert np.all(h["inst"][~hit] == -1)
+    # reversed order: the same record wherever no two instances tie
+    h2 = O.hybrid_trace(rays, [{"kind": "triangles", "tris": s}, {"kind": "triangles", "tris": g}])
+    assert np.array_equal(h2["t"], h["t"])
+    assert np.array_equal(np.where(hit, 1 - h2["inst"], -1), h["inst"])
+
+
+def test_hybrid_trace_neural_instance_alone_is_its_query():
+    """A single neural instance: the hybrid record is the neural query's."""
+    tris = W.scene_icosphere(level=2, radius=0.35)
+    cfg = W.ModelConfig(n_levels=4, n_features=2, log2_table=10, base_res=4, growth=1.5, n_samples=4,
+                        n_hidden=1, width=16)
+    leaves = O.build_leaves(tris, 8, 1e-4)
+    lay = O.level_layout(cfg.n_levels, cfg.base_res, cfg.growth, cfg.log2_table)
+    tab = W.init_table(lay["total"], cfg.n_features, 3, 1.0).astype(np.float64)
+    layers = W.init_mlp(cfg.mlp_dims(), 4, gain=2.0)
+    rays = W.chord_rays(200, seed=6, radius=0.6)
+    q = O.query(rays, leaves, tab, layers, lay, cfg.n_samples)
+    h = O.hybrid_trace(rays, [{"kind": "neural", "leaves": leaves, "table": tab, "layers": layers, "layout": lay,
+                               "n_samples": cfg.n_samples}])
+    assert q["hit"].sum() > 10
+    assert np.array_equal(h["hit"], q["hit"]) and np.array_equal(h["t"], q["t"])
+    assert np.array_equal(h["leaf"], q["leaf"])
+    assert np.array_equal(h["inst"], np.where(q["hit"] > 0, 0, -1))
