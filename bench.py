@@ -631,7 +631,7 @@ def run_gpu(args, world, rank, spec, tris, rays_np):
     traffic = profiled_traffic()
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "peak_source": peak_kind,
-            "kernel": "eval_tc_kernel (wave mode): gather + trilinear + tcgen05 MLP + resolve",
+            "kernel": "eval_tc_kernel (query mode): gather + trilinear + tcgen05 MLP + resolve",
             "bytes_per_segment": bytes_seg, "segments_per_step": seg_step,
             "kernel_ms_per_step": eval_ms_step, "traverse_ms_per_step": tr_ms_step,
             "traffic": (traffic["dram_bytes_per_segment"] * seg_step / max(1, waves1 + waves2)
@@ -642,7 +642,10 @@ def run_gpu(args, world, rank, spec, tris, rays_np):
             "vs_baseline": None, "dtype": "f16", "data": "synthetic",
             "config": {"workload": spec.name, "rays_per_step": rays_step, "primary_rays": wl.n,
                        "bounce_rays": rays_step - wl.n, "segments_per_step": seg_step,
-                       "waves": [waves1, waves2], "l2": "flushed (256 MB write) between timed steps",
+                       "eval_launches": [waves1, waves2],
+                       "schedule": {"mode": ["waves", "persistent"][B.get_query_schedule()[0]],
+                                    "patience_cycles": B.get_query_schedule()[1]},
+                       "l2": "flushed (256 MB write) between timed steps",
                        "parallelism": f"replicas x{world}"},
             "train": train,
             "hybrid": hybrid,

@@ -187,12 +187,14 @@ nbvh_status nbvh_query_workspace_size(const nbvh_model_desc* desc, int64_t n_ray
 
 /* Device. The neural ray query, S1..S5 (Sec. 5: the number of neural
  * queries per ray equals the leaves met before an intersection is found).
- * Traversal lists each ray's segments in (t0, leaf) order; waves then
- * evaluate segment w of every still-active ray, keeping the closest
- * predicted hit (hit iff hit logit > 0; t = t0 + sigmoid(depth)(t1 - t0);
- * normal = normalised normal head) and dropping a ray once its next
- * segment starts at or beyond its best t. The result equals the closest
- * predicted hit over all segments, ties to the earlier segment.
+ * Traversal lists each ray's segments in (t0, leaf) order; each ray's
+ * segments are then evaluated in that order, keeping the closest predicted
+ * hit (hit iff hit logit > 0; t = t0 + sigmoid(depth)(t1 - t0); normal =
+ * normalised normal head) and dropping the ray once its next segment starts
+ * at or beyond its best t. The result equals the closest predicted hit over
+ * all segments, ties to the earlier segment. The evaluation runs as waves
+ * (one launch per segment slot) or, for FP16/BF16, as one persistent launch
+ * (nbvh_set_query_schedule).
  * workspace: device, >= nbvh_query_workspace_size bytes, 256-byte aligned. */
 nbvh_status nbvh_query_rays(const nbvh_model_desc* desc, const void* table, const float* mlp,
                             const nbvh_node* nodes, int32_t n_nodes, nbvh_rays rays, int32_t max_segs,
@@ -215,9 +217,30 @@ typedef struct {
  * rays, hits: device inputs of n entries; out: device outputs, out.n == rays.n. */
 nbvh_status nbvh_bounce_rays(nbvh_rays rays, nbvh_hits hits, uint64_t seed, nbvh_rays_out out, void* stream);
 
+/* Evaluation schedule of the FP16/BF16 (tensor-core) query; the FP32 form
+ * always runs waves. Both give identical results.
+ *  NBVH_SCHEDULE_WAVES:      one launch per segment slot w evaluates slot w of
+ *                            every ray still active (compacted queue per wave).
+ *  NBVH_SCHEDULE_PERSISTENT: one launch whose CTAs (one per SM) claim tiles of
+ *                            up to 128 (ray, segment) items from a queue that
+ *                            each resolve refills with the ray's next segment,
+ *                            so rays with many segments do not leave a wave
+ *                            tail per slot (Sec. 5: queries per ray = leaves met
+ *                            before a hit). A CTA waits up to patience_cycles
+ *                            SM cycles for a full tile before it takes fewer
+ *                            items. A queue wait that gives up (about a second)
+ *                            records NBVH_ERR_TIMEOUT.
+ * Process-wide setting (default: persistent, 4000 cycles), read when a query
+ * is enqueued (a graph keeps the schedule it was recorded with). */
+#define NBVH_SCHEDULE_WAVES 0
+#define NBVH_SCHEDULE_PERSISTENT 1
+nbvh_status nbvh_set_query_schedule(int32_t schedule, int64_t patience_cycles);
+nbvh_status nbvh_get_query_schedule(int32_t* schedule, int64_t* patience_cycles);
+
 /* Device. Reads from a query workspace (after nbvh_query_rays on the same
- * stream) the number of segments evaluated and the number of waves that had
- * work. Synchronises the stream. */
+ * stream) the number of segments evaluated and the number of evaluation
+ * launches that had work (waves: one per segment slot; the persistent
+ * schedule reports 1). Synchronises the stream. */
 nbvh_status nbvh_query_stats(const void* workspace, int64_t n_rays, int32_t max_segs, int64_t* segments,
                              int32_t* waves, void* stream);
 

@@ -58,6 +58,24 @@ struct TcTrain {
   const float* loss_scale_dev;
 };
 
+// Persistent query queue (tensor-core query kernel, one launch for all
+// segments of all rays). An item is (segment slot << 32 | ray) in a ring of
+// n_rays 64-bit entries (position p at p % n_rays; an empty entry holds all
+// ones). A ray has at most one item queued or in evaluation, so at most
+// n_rays items are ever alive and position p has been taken before p + n_rays
+// is reserved. Producers reserve positions and write each item into its
+// entry; consumers claim positions [head, reserved) and take each item as soon
+// as it is there; a tile retires its items after queueing their successors,
+// so head - retired counts the items in evaluation.
+struct PQueue {
+  unsigned long long* head;      // items claimed
+  unsigned long long* reserved;  // items ever queued (= segments evaluated)
+  unsigned long long* retired;   // items resolved
+  unsigned int* tiles;           // tiles claimed (statistics)
+  long long patience;            // cycles a CTA waits for a full tile before taking a partial one
+  unsigned long long* ring;      // [n_rays] items; nullptr: one launch per segment slot instead
+};
+
 // Everything a segment-evaluation kernel needs. Two modes:
 //  - list mode  (queue == nullptr): item i is segment (seg_ray[i], t0[i], t1[i]),
 //    raw outputs go to out[i * n_out + j];
@@ -88,8 +106,10 @@ struct EvalArgs {
   nbvh_hits hits;
   int32_t* next_queue;
   int32_t* next_qlen;
+  int32_t max_segs;   // segment slots per ray in the seg_* arrays
   int32_t* inst_out;  // optional (hybrid hierarchy): instance id written with each improved hit
   int32_t inst_id;
+  PQueue pq;          // tensor-core query: persistent queue (when pq.ring is set)
   // training forward (tensor-core kernel, list of one segment per ray)
   TcTrain tr;
 };

@@ -203,7 +203,7 @@ __host__ __device__ inline TcLayout tc_layout(int K, int W, int n_hidden) {
   L.w1_off = take(uint32_t(W) * L.Kp * 2);
   L.wh_off = take(uint32_t(n_hidden - 1) * W * W * 2);
   L.wo_off = take(16u * W * 2);
-  L.row_off = take(kTcM * 12);
+  L.row_off = take(kTcM * 24);
   L.bar_off = take(64);
   L.total = off + 128;  // slack for base alignment
   return L;
@@ -271,9 +271,130 @@ __device__ __forceinline__ uint32_t pack2(float a, float b) {
   return *reinterpret_cast<uint32_t*>(&h);
 }
 
-// MODE 0: list of segments -> raw outputs; 1: query wave -> resolve + next
-// queue; 2: training forward (one segment per ray) -> stored 16-bit operands,
-// raw outputs, loss and dL/d(raw).
+// ---------------------------------------------------------------- persistent query queue
+constexpr long long kPqSpinLimit = 1LL << 22;      // bounded waits (~1 s with the back-off below)
+constexpr unsigned long long kPqEmpty = ~0ull;     // an empty ring entry
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long exch_acquire_u64(unsigned long long* p, unsigned long long v) {
+  unsigned long long old;
+  asm volatile("atom.acquire.gpu.global.exch.b64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ unsigned long long cas_release_u64(unsigned long long* p, unsigned long long cmp,
+                                                              unsigned long long v) {
+  unsigned long long old;
+  asm volatile("atom.release.gpu.global.cas.b64 %0, [%1], %2, %3;" : "=l"(old) : "l"(p), "l"(cmp), "l"(v)
+               : "memory");
+  return old;
+}
+__device__ __forceinline__ void red_release_add_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Thread 0 of a CTA: claim up to kTcM queued items. Returns the count (start
+// in *start), 0 when the queue has drained, -1 when the wait gave up. A
+// partial tile is taken only when nothing is in evaluation (no more items can
+// come) or after q.patience cycles of waiting: a tile's latency hardly
+// shrinks with fewer rows, while other CTAs' resolves refill the queue within
+// microseconds. The counters are polled with independent relaxed loads (a
+// stale value only delays a claim; the CAS on head validates it); the drained
+// state is confirmed by reading retired, then head, then reserved in order:
+// equal values mean nothing is in evaluation or queued, so nothing more can
+// be queued.
+__device__ __forceinline__ int pq_claim(const PQueue& q, unsigned long long* start) {
+  const long long t0 = clock64();
+  for (long long spin = 0; spin < kPqSpinLimit; ++spin) {
+    const unsigned long long retired = ld_relaxed_u64(q.retired);
+    const unsigned long long head = ld_relaxed_u64(q.head);
+    const unsigned long long res = ld_relaxed_u64(q.reserved);
+    if (res > head) {
+      const unsigned long long avail = res - head;
+      if (avail >= kTcM || retired == head || clock64() - t0 > q.patience) {
+        const unsigned want = unsigned(avail < kTcM ? avail : kTcM);
+        if (atomicCAS(q.head, head, head + want) == head) {
+          atomicAdd(q.tiles, 1u);
+          *start = head;
+          return int(want);
+        }
+        continue;
+      }
+    } else if (retired == head) {
+      const unsigned long long r2 = ld_acquire_u64(q.retired);
+      const unsigned long long h2 = ld_acquire_u64(q.head);
+      const unsigned long long s2 = ld_acquire_u64(q.reserved);
+      if (r2 == h2 && s2 == h2) return 0;
+      continue;
+    }
+    __nanosleep(64);
+  }
+  return -1;
+}
+
+// Take the item at ring position p (its producer may still be writing it) and
+// leave the entry empty for position p + n; the acquire orders the ray's
+// record reads after it. Returns kPqEmpty if the wait gave up.
+__device__ __forceinline__ unsigned long long pq_take(const PQueue& q, unsigned long long p, unsigned long long n) {
+  unsigned long long* e = q.ring + p % n;
+  for (long long spin = 0; spin < kPqSpinLimit; ++spin) {
+    const unsigned long long v = exch_acquire_u64(e, kPqEmpty);
+    if (v != kPqEmpty) return v;
+    __nanosleep(32);
+  }
+  return kPqEmpty;
+}
+
+// Write an item into the (empty) entry of position p; the release orders this
+// thread's record writes before it. Returns false if the wait gave up.
+__device__ __forceinline__ bool pq_put(const PQueue& q, unsigned long long p, unsigned long long n,
+                                       unsigned long long item) {
+  unsigned long long* e = q.ring + p % n;
+  for (long long spin = 0; spin < kPqSpinLimit; ++spin) {
+    if (cas_release_u64(e, kPqEmpty, item) == kPqEmpty) return true;
+    __nanosleep(32);
+  }
+  return false;
+}
+
+// Resolve one evaluated segment (slot sl of ray `ray`) into the ray's record.
+// best and next_t0 (the ray's best t and its next segment's t0, +inf if none)
+// were read when the item was taken: only this item's evaluation changes the
+// ray's record while it is alive. Returns whether the next segment is queued
+// (it starts before the best t).
+__device__ __forceinline__ bool pq_resolve(const EvalArgs& a, int ray, int sl, float best, float next_t0,
+                                           const float* raw, float t0, float t1) {
+  const SegResult s = decode_segment(raw, t0, t1);
+  if (s.hit && s.t < best) {
+    best = s.t;
+    a.hits.t[ray] = s.t;
+    a.hits.hit[ray] = 1;
+    a.hits.nx[ray] = s.nx;
+    a.hits.ny[ray] = s.ny;
+    a.hits.nz[ray] = s.nz;
+    a.hits.leaf[ray] = a.seg_leaf[size_t(sl) * size_t(a.n_rays) + size_t(ray)];
+    if (a.inst_out) a.inst_out[ray] = a.inst_id;
+  }
+  return next_t0 < best;
+}
+
+// The traversal queued the first items at ring positions [0, *qlen0).
+__global__ void pq_init_kernel(const int32_t* __restrict__ qlen0, PQueue q) {
+  *q.reserved = (unsigned long long)(*qlen0);
+}
+
+// MODE 0: list of segments -> raw outputs; 1: query -> resolve + next segment
+// queued (one launch per segment slot, or with a.pq.ring set one persistent
+// launch draining the queue); 2: training forward (one segment per ray) ->
+// stored 16-bit operands, raw outputs, loss and dL/d(raw).
 template <typename T, int F, int W, int MODE, bool BF16>
 __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
   extern __shared__ uint8_t smem_raw[];
@@ -290,12 +411,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
   int* sray = reinterpret_cast<int*>(smem + lay.row_off);
   float* st0 = reinterpret_cast<float*>(sray + kTcM);
   float* st1 = st0 + kTcM;
+  int* sslot = reinterpret_cast<int*>(st1 + kTcM);  // persistent query: the item's slot,
+  float* sbest = reinterpret_cast<float*>(sslot + kTcM);  // the ray's best t,
+  float* snext = sbest + kTcM;                            // its next segment's t0
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + lay.bar_off);
   uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + lay.bar_off + 8);
+  __shared__ unsigned long long s_start;
+  __shared__ int s_count;
 
-  const int64_t n_items = MODE == 1 ? int64_t(*a.qlen) : a.n_items;
-  const int64_t n_tiles = (n_items + kTcM - 1) / kTcM;
-  if (int64_t(blockIdx.x) >= n_tiles) return;
+  // A persistent query's CTAs claim tiles from the queue until it drains.
+  const bool persistent = MODE == 1 && a.pq.ring != nullptr;
+  const int64_t n_items = MODE == 1 ? (persistent ? 0 : int64_t(*a.qlen)) : a.n_items;
+  const int64_t n_tiles = persistent ? INT64_MAX : (n_items + kTcM - 1) / kTcM;
+  if (!persistent && int64_t(blockIdx.x) >= n_tiles) return;
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -343,16 +471,50 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
   const bool chunked = (L % LPC) == 0;
 
   for (int64_t tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
+    int ccount = 0;  // persistent query: items in this tile
+    if (persistent) {
+      if (threadIdx.x == 0) {
+        unsigned long long st = 0;
+        s_count = pq_claim(a.pq, &st);
+        s_start = st;
+      }
+      __syncthreads();
+      ccount = s_count;
+      if (ccount <= 0) {
+        failed = ccount < 0;
+        break;
+      }
+    }
     if (threadIdx.x < kTcM) {
       const int64_t i = tile * kTcM + threadIdx.x;
       int ray = -1;
       float t0 = 0.0f, t1 = 0.0f;
-      if (i < n_items) {
+      if (persistent ? int(threadIdx.x) < ccount : i < n_items) {
         if constexpr (MODE == 1) {
-          ray = a.queue[i];
-          const size_t q = size_t(a.wave) * size_t(a.n_rays) + size_t(ray);
-          t0 = a.seg_t0[q];
-          t1 = a.seg_t1[q];
+          const size_t nr = size_t(a.n_rays);
+          if (persistent) {
+            const unsigned long long it = pq_take(a.pq, s_start + threadIdx.x, nr);
+            if (it == kPqEmpty) {
+              set_status(NBVH_ERR_TIMEOUT);
+            } else {
+              ray = int(uint32_t(it));
+              const int sl = int(it >> 32);
+              sslot[threadIdx.x] = sl;
+              const size_t q = size_t(sl) * nr + size_t(ray);
+              t0 = a.seg_t0[q];
+              t1 = a.seg_t1[q];
+              sbest[threadIdx.x] = __ldcg(a.hits.t + ray);
+              // the slot after the last holds stale data: load it with the count, use it only below the count
+              const int cnt = a.seg_count[ray];
+              const float tn = sl + 1 < a.max_segs ? a.seg_t0[size_t(sl + 1) * nr + size_t(ray)] : 0.0f;
+              snext[threadIdx.x] = sl + 1 < cnt ? tn : __int_as_float(0x7f800000);
+            }
+          } else {
+            ray = a.queue[i];
+            const size_t q = size_t(a.wave) * nr + size_t(ray);
+            t0 = a.seg_t0[q];
+            t1 = a.seg_t1[q];
+          }
         } else if constexpr (MODE == 2) {
           const int r = a.tr.order ? a.tr.order[i] : int(i);
           ray = a.tr.leaf[r] >= 0 ? r : -1;
@@ -530,7 +692,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
         for (int j = 0; j < 8; ++j) raw[j] = j < n_out ? v[j] + __ldg(bo + j) : 0.0f;
         const int ray = sray[row];
         if constexpr (MODE == 1) {
-          wave_resolve(a, ray >= 0, ray, raw, st0[row], st1[row]);
+          if (persistent) {
+            // the row's ray id stays in sray only if its next segment is queued
+            const bool push = ray >= 0 && pq_resolve(a, ray, sslot[row], sbest[row], snext[row], raw, st0[row],
+                                                     st1[row]);
+            sray[row] = push ? ray : -1;
+          } else {
+            wave_resolve(a, ray >= 0, ray, raw, st0[row], st1[row]);
+          }
         } else if constexpr (MODE == 2) {
           if (grow < n_items) {
             float g[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -560,6 +729,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
       }
       tc_fence_before();
       __syncthreads();
+    }
+    if (persistent) {
+      // Queue the next segments of this tile's rays (one reservation per warp,
+      // each item written into its entry), then retire the tile's items.
+      bool ok = true;
+      if (warp < 4) {
+        const int pray = sray[threadIdx.x];
+        const unsigned m = __ballot_sync(0xffffffffu, pray >= 0);
+        unsigned long long base = 0;
+        if (m && lane == 0) base = atomicAdd(a.pq.reserved, (unsigned long long)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (pray >= 0) {
+          const unsigned long long item = (unsigned long long)(sslot[threadIdx.x] + 1) << 32 | uint32_t(pray);
+          ok = pq_put(a.pq, base + __popc(m & ((1u << lane) - 1u)), (unsigned long long)a.n_rays, item);
+        }
+      }
+      if (__syncthreads_or(!ok)) failed = true;
+      if (threadIdx.x == 0) red_release_add_u64(a.pq.retired, (unsigned long long)ccount);  // after the reservations
     }
   }
   if (failed) set_status(NBVH_ERR_TIMEOUT);

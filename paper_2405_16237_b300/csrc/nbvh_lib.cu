@@ -193,6 +193,11 @@ struct QueryWs {
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// Counter block of a query workspace: per-wave counts [0, max_segs + 2), then
+// at pq_base the persistent queue's counters, one 128-byte line each.
+int32_t pq_base(int32_t max_segs) { return int32_t(align256(sizeof(int32_t) * size_t(max_segs + 2)) / 4); }
+size_t counters_bytes(int32_t max_segs) { return size_t(pq_base(max_segs)) * 4 + 4 * 128; }
+
 QueryWs carve_query(void* base, int64_t n, int32_t max_segs) {
   QueryWs w;
   char* p = static_cast<char*>(base);
@@ -202,21 +207,40 @@ QueryWs carve_query(void* base, int64_t n, int32_t max_segs) {
     off += align256(bytes);
     return q;
   };
-  w.counters = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * size_t(max_segs + 2)));
+  w.counters = reinterpret_cast<int32_t*>(take(counters_bytes(max_segs)));
   w.seg_count = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * size_t(n)));
   w.seg_leaf = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * size_t(n) * size_t(max_segs)));
   w.seg_t0 = reinterpret_cast<float*>(take(sizeof(float) * size_t(n) * size_t(max_segs)));
   w.seg_t1 = reinterpret_cast<float*>(take(sizeof(float) * size_t(n) * size_t(max_segs)));
-  w.queue[0] = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * size_t(n)));
-  w.queue[1] = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * size_t(n)));
+  // the two wave queues, or (persistent query) one ring of n 64-bit items
+  w.queue[0] = reinterpret_cast<int32_t*>(take(2 * sizeof(int32_t) * size_t(n)));
+  w.queue[1] = w.queue[0] ? w.queue[0] + n : nullptr;
   w.bytes = off;
   return w;
 }
 
 
-// Traversal (S1) then one evaluation wave per segment slot (S2..S5) on the
-// carved query workspace. merge: the hit record holds the closest hit so far
-// (hybrid hierarchy) and records the instance id with every improvement.
+
+// Evaluation schedule of the tensor-core query (nbvh_set_query_schedule).
+std::atomic<int32_t> g_schedule{NBVH_SCHEDULE_PERSISTENT};
+std::atomic<int64_t> g_patience{4000};
+
+PQueue pq_of(const QueryWs& w, int32_t max_segs) {
+  int32_t* c = w.counters + pq_base(max_segs);
+  PQueue q;
+  q.head = reinterpret_cast<unsigned long long*>(c);
+  q.reserved = reinterpret_cast<unsigned long long*>(c + 32);
+  q.retired = reinterpret_cast<unsigned long long*>(c + 64);
+  q.tiles = reinterpret_cast<unsigned int*>(c + 96);
+  q.patience = g_patience.load();
+  q.ring = reinterpret_cast<unsigned long long*>(w.queue[0]);
+  return q;
+}
+
+// Traversal (S1) then the evaluation (S2..S5) on the carved query workspace:
+// one wave per segment slot (FP32 form) or one persistent launch (FP16/BF16).
+// merge: the hit record holds the closest hit so far (hybrid hierarchy) and
+// records the instance id with every improvement.
 cudaError_t launch_query_stages(const nbvh_model_desc* desc, const GridParams& gp, const void* table,
                                 const float* mlp, const nbvh_node* nodes, const nbvh_rays& rays, int32_t max_segs,
                                 const nbvh_hits& out, const QueryWs& w, bool merge, int32_t* inst_out,
@@ -232,6 +256,13 @@ cudaError_t launch_query_stages(const nbvh_model_desc* desc, const GridParams& g
   to.qlen0 = w.counters;
   to.hits = out;
   to.merge = merge ? 1 : 0;
+  const bool persistent = desc->mlp_prec != NBVH_FP32 && g_schedule.load() == NBVH_SCHEDULE_PERSISTENT;
+  if (persistent) {
+    to.queue0 = nullptr;
+    to.ring0 = reinterpret_cast<unsigned long long*>(w.queue[0]);
+    cudaError_t me = cudaMemsetAsync(w.queue[0], 0xff, 8 * size_t(rays.n), s);  // empty ring
+    if (me != cudaSuccess) return me;
+  }
   traverse_kernel<<<unsigned((rays.n + 127) / 128), 128, 0, s>>>(nodes, ray_ptrs(rays), rays.n, to);
   count_launches(1);
   cudaError_t e = cudaGetLastError();
@@ -246,6 +277,16 @@ cudaError_t launch_query_stages(const nbvh_model_desc* desc, const GridParams& g
   a.hits = out;
   a.inst_out = inst_out;
   a.inst_id = inst_id;
+  a.max_segs = max_segs;
+  if (persistent) {
+    // one launch drains a queue of (slot, ray) items
+    a.pq = pq_of(w, max_segs);
+    pq_init_kernel<<<1, 1, 0, s>>>(w.counters, a.pq);
+    count_launches(1);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_eval(desc, a, true, rays.n, s);
+  }
   for (int wv = 0; wv < max_segs; ++wv) {
     a.wave = wv;
     a.queue = w.queue[wv & 1];
@@ -340,7 +381,7 @@ extern "C" nbvh_status nbvh_query_rays(const nbvh_model_desc* desc, const void* 
   GridParams gp;
   if (!make_grid(desc, gp)) return NBVH_ERR_INVALID_ARG;
   cudaStream_t s = as_stream(stream);
-  cudaError_t e = cudaMemsetAsync(w.counters, 0, sizeof(int32_t) * size_t(max_segs + 2), s);
+  cudaError_t e = cudaMemsetAsync(w.counters, 0, counters_bytes(max_segs), s);
   if (e != cudaSuccess) return NBVH_ERR_CUDA;
   StageEvents ev{nullptr, nullptr, nullptr};
   cudaStreamCaptureStatus capturing = cudaStreamCaptureStatusNone;
@@ -366,16 +407,40 @@ extern "C" nbvh_status nbvh_query_rays(const nbvh_model_desc* desc, const void* 
   return NBVH_OK;
 }
 
+extern "C" nbvh_status nbvh_set_query_schedule(int32_t schedule, int64_t patience_cycles) {
+  if ((schedule != NBVH_SCHEDULE_WAVES && schedule != NBVH_SCHEDULE_PERSISTENT) || patience_cycles < 0 ||
+      patience_cycles > (int64_t(1) << 40))
+    return NBVH_ERR_INVALID_ARG;
+  g_schedule.store(schedule);
+  g_patience.store(patience_cycles);
+  return NBVH_OK;
+}
+
+extern "C" nbvh_status nbvh_get_query_schedule(int32_t* schedule, int64_t* patience_cycles) {
+  if (!schedule || !patience_cycles) return NBVH_ERR_INVALID_ARG;
+  *schedule = g_schedule.load();
+  *patience_cycles = g_patience.load();
+  return NBVH_OK;
+}
+
 extern "C" nbvh_status nbvh_query_stats(const void* workspace, int64_t n_rays, int32_t max_segs, int64_t* segments,
                                        int32_t* waves, void* stream) {
   if (!workspace || n_rays < 0 || max_segs < 1 || max_segs > 4096 || !segments || !waves)
     return NBVH_ERR_INVALID_ARG;
   if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0) return NBVH_ERR_INVALID_ARG;
-  std::vector<int32_t> c(size_t(max_segs) + 2);
+  std::vector<int32_t> c(counters_bytes(max_segs) / 4);
   cudaStream_t s = as_stream(stream);
   if (cudaMemcpyAsync(c.data(), workspace, sizeof(int32_t) * c.size(), cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return NBVH_ERR_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return NBVH_ERR_CUDA;
+  // persistent query (tensor-core form): one launch, items ever enqueued
+  uint64_t reserved = 0;
+  std::memcpy(&reserved, c.data() + pq_base(max_segs) + 32, sizeof(reserved));
+  if (reserved > 0) {
+    *segments = int64_t(reserved);
+    *waves = 1;
+    return NBVH_OK;
+  }
   int64_t tot = 0;
   int32_t w = 0;
   for (int i = 0; i < max_segs; ++i) {
@@ -536,7 +601,7 @@ extern "C" nbvh_status nbvh_hybrid_trace(const nbvh_instance* inst, int32_t n_in
       count_launches(1);
       e = cudaGetLastError();
     } else {
-      e = cudaMemsetAsync(w.counters, 0, sizeof(int32_t) * size_t(x.max_segs + 2), s);
+      e = cudaMemsetAsync(w.counters, 0, counters_bytes(x.max_segs), s);
       if (e != cudaSuccess) return NBVH_ERR_CUDA;
       QueryWs wi = carve_query(workspace, rays.n, x.max_segs);
       e = launch_query_stages(&x.desc, gps[i], x.table, x.mlp, x.nodes, rays, x.max_segs, out, wi, true, out_inst,

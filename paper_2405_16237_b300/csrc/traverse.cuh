@@ -18,6 +18,8 @@ struct TraverseOut {
   // hit found so far; it is kept, and leaves whose clipped segment starts at or
   // beyond it are skipped (a neural hit never lies before its segment's t0).
   int32_t merge;
+  // Optional (persistent query): the queued rays as 64-bit items (slot 0).
+  unsigned long long* ring0;
 };
 
 // One thread per ray. Depth-first with a short stack; the nearer child is
@@ -117,7 +119,7 @@ __global__ void __launch_bounds__(128) traverse_kernel(const nbvh_node* __restri
       out.hits.leaf[r] = -1;
     }
   }
-  if (out.queue0) {
+  if (out.queue0 || out.ring0) {
     const bool want = active && count > 0;
     const unsigned m = __ballot_sync(0xffffffffu, want);
     if (m) {
@@ -126,7 +128,9 @@ __global__ void __launch_bounds__(128) traverse_kernel(const nbvh_node* __restri
       int base = 0;
       if (lane == leader) base = atomicAdd(out.qlen0, __popc(m));
       base = __shfl_sync(0xffffffffu, base, leader);
-      if (want) out.queue0[base + __popc(m & ((1u << lane) - 1u))] = int32_t(r);
+      const int pos = base + __popc(m & ((1u << lane) - 1u));
+      if (want && out.ring0) out.ring0[pos] = (unsigned long long)r;
+      else if (want) out.queue0[pos] = int32_t(r);
     }
   }
 }

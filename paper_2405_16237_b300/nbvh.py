@@ -112,6 +112,8 @@ _SIGS = {
     "nbvh_query_rays": (c_int32, [POINTER(ModelDesc), c_void_p, c_void_p, c_void_p, c_int32, Rays, c_int32,
                                   Hits, c_void_p, c_size_t, c_void_p]),
     "nbvh_bounce_rays": (c_int32, [Rays, Hits, ctypes.c_uint64, RaysOut, c_void_p]),
+    "nbvh_set_query_schedule": (c_int32, [c_int32, c_int64]),
+    "nbvh_get_query_schedule": (c_int32, [POINTER(c_int32), POINTER(c_int64)]),
     "nbvh_query_stats": (c_int32, [c_void_p, c_int64, c_int32, POINTER(c_int64), POINTER(c_int32), c_void_p]),
     "nbvh_set_timing": (c_int32, [c_int32]),
     "nbvh_get_timing": (c_int32, [POINTER(c_double), POINTER(c_double), POINTER(c_int64)]),
@@ -396,6 +398,19 @@ def bounce_rays(rays: dict, hits: dict, seed: int, out=None):
     _check(lib().nbvh_bounce_rays(rays_struct(rays), hits_struct(hits), ctypes.c_uint64(seed), o, _stream()),
            "bounce_rays")
     return out
+
+
+SCHEDULE_WAVES, SCHEDULE_PERSISTENT = 0, 1
+
+
+def set_query_schedule(schedule: int, patience_cycles: int = 4000):
+    _check(lib().nbvh_set_query_schedule(schedule, patience_cycles), "set_query_schedule")
+
+
+def get_query_schedule():
+    a, b = c_int32(), c_int64()
+    _check(lib().nbvh_get_query_schedule(ctypes.byref(a), ctypes.byref(b)), "get_query_schedule")
+    return a.value, b.value
 
 
 def query_stats(workspace, n_rays: int, max_segs: int):

@@ -157,3 +157,24 @@ def test_hybrid_graph_bounce_loop_equals_eager():
         assert torch.equal(e[2][b], g_bufs[2][b])
     # later bounces still find hits of both kinds
     assert int((e[2][1] == 0).sum()) > 0 and int((e[2][1] > 0).sum()) > 0
+
+
+def test_hybrid_schedules_agree():
+    """Neural passes of the hybrid trace under the persistent queue and under
+    per-slot waves give bit-identical records."""
+    torch = _torch()
+    ground, assets = small_hybrid_scene(3)
+    hb = HybridBuilt(ground, assets, B.BF16, table_prec=B.BF16)
+    rays = B.to_device_rays(hybrid_rays(40, 800))
+    old = B.get_query_schedule()
+    try:
+        B.set_query_schedule(B.SCHEDULE_WAVES, 0)
+        hw, iw = B.hybrid_trace(hb.instances, rays)
+        B.set_query_schedule(B.SCHEDULE_PERSISTENT, 4000)
+        hp, ip = B.hybrid_trace(hb.instances, rays)
+    finally:
+        B.set_query_schedule(*old)
+    assert B.device_status() == 0
+    for k in hw:
+        assert torch.equal(hw[k], hp[k]), k
+    assert torch.equal(iw, ip)

@@ -331,3 +331,30 @@ def test_graph_replay_equals_eager_query():
     for a, c in ((out_e, out_g), (out_e2, out_g2)):
         for k in a:
             assert torch.equal(a[k], c[k]), k
+
+
+@pytest.mark.parametrize("mp", [B.FP16, B.BF16])
+@pytest.mark.parametrize("patience", [0, 4000, 1 << 30])
+def test_persistent_schedule_equals_waves(mp, patience):
+    """The persistent queue (one launch, tiles claimed as resolves refill the
+    queue; patience from eager partial tiles to waiting until drained) gives
+    bit-identical hit records to one launch per segment slot."""
+    torch = _torch()
+    b = built("icosphere_l6", 1.0, 2.0)
+    rays = B.to_device_rays(W.mixed_rays(6000, seed=W.SEED_BASE + 31, radius=0.6))
+    desc = b.with_prec(mp)
+    old = B.get_query_schedule()
+    try:
+        B.set_query_schedule(B.SCHEDULE_WAVES, 0)
+        hw = B.query_rays(desc, b.table, b.mlp, b.nodes, b.leaves["n_nodes"], rays, 24)
+        B.set_query_schedule(B.SCHEDULE_PERSISTENT, patience)
+        ws = B.new_workspace(B.query_workspace_size(desc, rays["ox"].numel(), 24))
+        hp = B.query_rays(desc, b.table, b.mlp, b.nodes, b.leaves["n_nodes"], rays, 24, workspace=ws)
+        segs, launches = B.query_stats(ws, rays["ox"].numel(), 24)
+    finally:
+        B.set_query_schedule(*old)
+    assert B.device_status() == 0
+    for k in hw:
+        assert torch.equal(hw[k], hp[k]), k
+    assert launches == 1 and segs > rays["ox"].numel() // 4
+    assert int(hw["hit"].sum()) > 100
