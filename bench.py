@@ -51,6 +51,8 @@ def parse():
                    help="timed frames of the hybrid-scene workload (0: skip it)")
     p.add_argument("--hybrid-size", default="3840x2160")
     p.add_argument("--hybrid-cpu-rays", type=int, default=128, help="oracle sample of the hybrid workload")
+    p.add_argument("--uneven-steps", type=int, default=5,
+                   help="timed queries of the uneven-segment workload (0: skip it)")
     p.add_argument("--quick", action="store_true",
                    help="time the FP16 tensor-core form only (no other forms, no e2e, no CPU baseline)")
     return p.parse_args()
@@ -389,6 +391,76 @@ def accuracy(wl, idx, res):
     return out
 
 
+# ---------------------------------------------------------------------------- uneven segments (S6)
+def time_uneven(args, world):
+    """64 displaced sphere clusters (1k-200k triangles each) in one 8,192-leaf
+    N-BVH; 4,194,304 rays (60% from a camera, 40% sphere chords) with 1-40
+    segments each; the icosphere model in FP16. The autotuner picks the
+    schedule on this workload; each timed step is one graph-captured query."""
+    import torch
+    from paper_2405_16237_b300 import nbvh as B
+    from paper_2405_16237_b300 import workloads as W
+    spec = W.C3
+    ex = spec.extra
+    t0 = time.perf_counter()
+    tris = W.scene_sphere_clusters(n_clusters=ex["n_clusters"], min_tris=ex["min_tris"], max_tris=ex["max_tris"])
+    rays_np = W.mixed_rays(ex["n_rays"], seed=SEED + 40, camera_fraction=ex["camera_fraction"])
+    leaves = B.build_leaves(tris, spec.n_leaves, spec.inflate_rel)
+    info = leaves["info"]
+    cfg = spec.model
+    desc = B.model_desc(cfg, B.FP16, B.FP16, info["centre"], info["extent"])
+    lay = B.level_layout(desc)
+    table = torch.as_tensor(W.init_table(lay["total"], cfg.n_features, SEED + 41, 1e-4)).cuda().half()
+    mlp = torch.as_tensor(B.pack_mlp(W.init_mlp(cfg.mlp_dims(), SEED + 42))).cuda()
+    nodes = torch.as_tensor(leaves["nodes"]).cuda()
+    rays = B.to_device_rays(rays_np)
+    n = rays["ox"].numel()
+    # segments per ray (traversal only, untimed) with room to spare; the
+    # query then gets exactly the slots the deepest ray needs
+    tr = B.traverse(nodes, leaves["n_nodes"], rays, 160)
+    cnt = tr["count"].cpu().numpy()
+    del tr
+    st = B.device_status()
+    if st != 0:
+        raise RuntimeError(f"device status {st} after the uneven-segment traversal")
+    ms_max = int(cnt.max())
+    out = B.new_hits(n)
+    ws = B.new_workspace(B.query_workspace_size(desc, n, ms_max))
+    setup_s = time.perf_counter() - t0
+    best, table_all = B.autotune_query(desc, table, mlp, nodes, leaves["n_nodes"], rays, ms_max, out=out,
+                                       workspace=ws, reps=3)
+    g = B.Graph.record(lambda: B.query_rays(desc, table, mlp, nodes, leaves["n_nodes"], rays, ms_max, out=out,
+                                            workspace=ws))
+    launches = 0
+    for _ in range(3):
+        g.launch()
+    torch.cuda.synchronize()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    total = 0.0
+    for _ in range(args.uneven_steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.launch()
+        e1.record()
+        e1.synchronize()
+        total += e0.elapsed_time(e1)
+    g.destroy()
+    st = B.device_status()
+    if st != 0:
+        raise RuntimeError(f"device status {st} after the uneven-segment queries")
+    segs, _ = B.query_stats(ws, n, ms_max)
+    ms = dist_max(total, world) / args.uneven_steps
+    hit = cnt > 0
+    return {"workload": spec.name, "value": world * n / (ms * 1e-3) / 1e6, "unit": "Mrays/s", "ms_per_query": ms,
+            "rays": n, "triangles": int(len(tris)), "segments_per_ray": {
+                "max": int(cnt.max()), "mean_of_rays_with_segments": float(cnt[hit].mean()),
+                "rays_with_segments": int(hit.sum()), "p99": float(np.percentile(cnt[hit], 99))},
+            "segments_evaluated": int(segs), "autotuner": {"best": best, "candidates": table_all},
+            "setup_s": setup_s, "l2": "flushed (256 MB write) between timed queries"}
+
+
 # ---------------------------------------------------------------------------- hybrid scene (S9)
 HYBRID_BOUNCES = 4
 HYBRID_MAX_SEGS = 16
@@ -564,6 +636,10 @@ def run_gpu(args, world, rank, spec, tris, rays_np):
     d32 = B.with_mlp_prec(wl.desc, B.FP32)
     dbf = B.with_mlp_prec(wl.desc, B.BF16)
 
+    # autotuner (untimed): pick the query schedule on this workload's primary rays
+    tune_best, tune_all = B.autotune_query(d16, wl.table, wl.mlp, wl.nodes, wl.leaves["n_nodes"], wl.rays,
+                                           args.max_segs, out=wl.h1, workspace=wl.ws1, reps=3)
+
     # untimed reference step: statistics of the work one step does
     wl.step(d16)
     torch.cuda.synchronize()
@@ -613,6 +689,12 @@ def run_gpu(args, world, rank, spec, tris, rays_np):
     if train is not None:
         train["value"] = dist_max_rate(train["value"], world)
 
+    # uneven segment counts (64 sphere clusters, 8,192 leaves, 4M rays)
+    uneven = time_uneven(args, world) if args.uneven_steps > 0 else None
+    # back to the configuration the autotuner chose for the icosphere workload
+    B.set_query_schedule(1 if tune_best["schedule"] == "persistent" else 0, tune_best["patience_cycles"])
+    B.set_traverse_block(tune_best["traverse_block"])
+
     # the hybrid two-level scene (16 neural assets + 500,000 classical triangles)
     hybrid = time_hybrid(args, world) if args.hybrid_frames > 0 else None
 
@@ -644,10 +726,12 @@ def run_gpu(args, world, rank, spec, tris, rays_np):
                        "bounce_rays": rays_step - wl.n, "segments_per_step": seg_step,
                        "eval_launches": [waves1, waves2],
                        "schedule": {"mode": ["waves", "persistent"][B.get_query_schedule()[0]],
-                                    "patience_cycles": B.get_query_schedule()[1]},
+                                    "patience_cycles": B.get_query_schedule()[1],
+                                    "autotuner": {"best": tune_best, "candidates": tune_all}},
                        "l2": "flushed (256 MB write) between timed steps",
                        "parallelism": f"replicas x{world}"},
             "train": train,
+            "uneven": uneven,
             "hybrid": hybrid,
             "fp32_plain": {"value": world * rays_step / (ms32 * 1e-3) / 1e6, "ms_per_step": ms32},
             "bf16_tc": {"value": world * rays_step / (msbf * 1e-3) / 1e6, "ms_per_step": msbf},

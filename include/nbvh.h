@@ -237,6 +237,36 @@ nbvh_status nbvh_bounce_rays(nbvh_rays rays, nbvh_hits hits, uint64_t seed, nbvh
 nbvh_status nbvh_set_query_schedule(int32_t schedule, int64_t patience_cycles);
 nbvh_status nbvh_get_query_schedule(int32_t* schedule, int64_t* patience_cycles);
 
+/* Threads per traversal CTA (64, 128 or 256; default 128), process-wide. */
+nbvh_status nbvh_set_traverse_block(int32_t threads);
+
+/* One configuration of the query and its median time. */
+typedef struct {
+  int32_t schedule;          /* NBVH_SCHEDULE_* */
+  int64_t patience_cycles;
+  int32_t traverse_block;
+  float ms;                  /* median of the timed runs */
+} nbvh_tune_result;
+
+/* Device (synchronises). S6 autotuner: times nbvh_query_rays on the caller's
+ * own inputs under each candidate configuration and keeps the fastest.
+ * Candidates: waves; for FP16/BF16 also the persistent schedule with
+ * patience 0, 1000, 4000, 16000 and 64000 cycles; then traversal CTAs of 64
+ * and 256 threads under the best schedule. Each candidate runs once untimed
+ * and reps times timed (CUDA events on the stream, median). The winner is set
+ * process-wide (nbvh_set_query_schedule, nbvh_set_traverse_block) and
+ * returned in *best; the first all_cap candidates with their times go to
+ * all[], their count to *n_all. Every candidate gives the same hit records
+ * (out holds the last run's). On an error the previous settings are restored.
+ * The tensor-core tile is fixed at 128 rows (the MMA M and the 128 TMEM
+ * lanes), so rows per tile are not a candidate; the patience sets how full a
+ * claimed tile must be. */
+nbvh_status nbvh_autotune_query(const nbvh_model_desc* desc, const void* table, const float* mlp,
+                                const nbvh_node* nodes, int32_t n_nodes, nbvh_rays rays, int32_t max_segs,
+                                nbvh_hits out, void* workspace, size_t ws_bytes, int32_t reps,
+                                nbvh_tune_result* best, nbvh_tune_result* all, int32_t all_cap, int32_t* n_all,
+                                void* stream);
+
 /* Device. Reads from a query workspace (after nbvh_query_rays on the same
  * stream) the number of segments evaluated and the number of evaluation
  * launches that had work (waves: one per segment slot; the persistent

@@ -224,6 +224,7 @@ QueryWs carve_query(void* base, int64_t n, int32_t max_segs) {
 // Evaluation schedule of the tensor-core query (nbvh_set_query_schedule).
 std::atomic<int32_t> g_schedule{NBVH_SCHEDULE_PERSISTENT};
 std::atomic<int64_t> g_patience{4000};
+std::atomic<int32_t> g_traverse_block{128};  // threads per traversal CTA (64, 128 or 256)
 
 PQueue pq_of(const QueryWs& w, int32_t max_segs) {
   int32_t* c = w.counters + pq_base(max_segs);
@@ -263,7 +264,8 @@ cudaError_t launch_query_stages(const nbvh_model_desc* desc, const GridParams& g
     cudaError_t me = cudaMemsetAsync(w.queue[0], 0xff, 8 * size_t(rays.n), s);  // empty ring
     if (me != cudaSuccess) return me;
   }
-  traverse_kernel<<<unsigned((rays.n + 127) / 128), 128, 0, s>>>(nodes, ray_ptrs(rays), rays.n, to);
+  const int tb = g_traverse_block.load();
+  traverse_kernel<<<unsigned((rays.n + tb - 1) / tb), tb, 0, s>>>(nodes, ray_ptrs(rays), rays.n, to);
   count_launches(1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -609,6 +611,93 @@ extern "C" nbvh_status nbvh_hybrid_trace(const nbvh_instance* inst, int32_t n_in
     }
     if (e != cudaSuccess) return status_of(e);
   }
+  return NBVH_OK;
+}
+
+// ---------------------------------------------------------------- autotuner (S6)
+extern "C" nbvh_status nbvh_autotune_query(const nbvh_model_desc* desc, const void* table, const float* mlp,
+                                           const nbvh_node* nodes, int32_t n_nodes, nbvh_rays rays,
+                                           int32_t max_segs, nbvh_hits out, void* workspace, size_t ws_bytes,
+                                           int32_t reps, nbvh_tune_result* best, nbvh_tune_result* all,
+                                           int32_t all_cap, int32_t* n_all, void* stream) {
+  if (!nbvh_host::desc_valid(desc) || !table || !mlp || !nodes || n_nodes < 1 || !rays_valid(rays) ||
+      rays.n < 1 || max_segs < 1 || max_segs > 4096 || !hits_valid(out) || !workspace || reps < 1 ||
+      reps > 100 || !best || (all_cap > 0 && !all) || all_cap < 0 || !n_all)
+    return NBVH_ERR_INVALID_ARG;
+  size_t need = 0;
+  if (nbvh_query_workspace_size(desc, rays.n, max_segs, &need) != NBVH_OK) return NBVH_ERR_INVALID_ARG;
+  if (ws_bytes < need) return NBVH_ERR_WORKSPACE_TOO_SMALL;
+  cudaStream_t s = as_stream(stream);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return NBVH_ERR_CUDA;
+  }
+  const int32_t old_sched = g_schedule.load(), old_block = g_traverse_block.load();
+  const int64_t old_pat = g_patience.load();
+  // one candidate: warm-up, then the median of reps timed queries
+  auto time_it = [&](nbvh_tune_result& r) -> nbvh_status {
+    g_schedule.store(r.schedule);
+    g_patience.store(r.patience_cycles);
+    g_traverse_block.store(r.traverse_block);
+    std::vector<float> ms;
+    for (int i = 0; i <= reps; ++i) {
+      if (cudaEventRecord(e0, s) != cudaSuccess) return NBVH_ERR_CUDA;
+      const nbvh_status st = nbvh_query_rays(desc, table, mlp, nodes, n_nodes, rays, max_segs, out, workspace,
+                                             ws_bytes, stream);
+      if (st != NBVH_OK) return st;
+      if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return NBVH_ERR_CUDA;
+      float t = 0.0f;
+      if (cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) return NBVH_ERR_CUDA;
+      if (i > 0) ms.push_back(t);
+    }
+    std::sort(ms.begin(), ms.end());
+    r.ms = ms[ms.size() / 2];
+    return NBVH_OK;
+  };
+  std::vector<nbvh_tune_result> cand;
+  const bool tc = desc->mlp_prec != NBVH_FP32;
+  cand.push_back({NBVH_SCHEDULE_WAVES, 0, 128, 0.0f});
+  if (tc)
+    for (int64_t p : {int64_t(0), int64_t(1000), int64_t(4000), int64_t(16000), int64_t(64000)})
+      cand.push_back({NBVH_SCHEDULE_PERSISTENT, p, 128, 0.0f});
+  nbvh_status st = NBVH_OK;
+  for (auto& c : cand)
+    if ((st = time_it(c)) != NBVH_OK) break;
+  if (st == NBVH_OK) {
+    nbvh_tune_result b = cand[0];
+    for (const auto& c : cand)
+      if (c.ms < b.ms) b = c;
+    for (int32_t tb : {64, 256}) {  // traversal block size under the best schedule
+      nbvh_tune_result c = b;
+      c.traverse_block = tb;
+      if ((st = time_it(c)) != NBVH_OK) break;
+      cand.push_back(c);
+      if (c.ms < b.ms) b = c;
+    }
+    if (st == NBVH_OK) {
+      *best = b;
+      g_schedule.store(b.schedule);
+      g_patience.store(b.patience_cycles);
+      g_traverse_block.store(b.traverse_block);
+    }
+  }
+  if (st != NBVH_OK) {
+    g_schedule.store(old_sched);
+    g_patience.store(old_pat);
+    g_traverse_block.store(old_block);
+  }
+  const int32_t k = std::min<int32_t>(all_cap, int32_t(cand.size()));
+  for (int32_t i = 0; i < k; ++i) all[i] = cand[size_t(i)];
+  *n_all = int32_t(cand.size());
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return st;
+}
+
+extern "C" nbvh_status nbvh_set_traverse_block(int32_t threads) {
+  if (threads != 64 && threads != 128 && threads != 256) return NBVH_ERR_INVALID_ARG;
+  g_traverse_block.store(threads);
   return NBVH_OK;
 }
 

@@ -28,7 +28,7 @@ struct TraverseOut {
 // of the slab arithmetic is monotone, so an empty clip prunes its subtree.
 // Segments are inserted into the ray's list in (t0, leaf) order; the list is
 // slot-major (slot s of ray r at s * n + r) so a warp's stores coalesce.
-__global__ void __launch_bounds__(128) traverse_kernel(const nbvh_node* __restrict__ nodes,
+__global__ void __launch_bounds__(256) traverse_kernel(const nbvh_node* __restrict__ nodes,
                                                        RayPtrs rays, int64_t n, TraverseOut out) {
   const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const bool active = r < n;

@@ -79,6 +79,10 @@ class Optim(ctypes.Structure):
 TRAIN_PROBED_MIX, TRAIN_PAPER = 0, 1
 
 
+class TuneResult(ctypes.Structure):
+    _fields_ = [("schedule", c_int32), ("patience_cycles", c_int64), ("traverse_block", c_int32), ("ms", c_float)]
+
+
 class TriBlas(ctypes.Structure):
     _fields_ = [("nodes", c_void_p), ("n_nodes", c_int32), ("tris", c_void_p), ("leaf_range", c_void_p),
                 ("tri_id", c_void_p)]
@@ -114,6 +118,10 @@ _SIGS = {
     "nbvh_bounce_rays": (c_int32, [Rays, Hits, ctypes.c_uint64, RaysOut, c_void_p]),
     "nbvh_set_query_schedule": (c_int32, [c_int32, c_int64]),
     "nbvh_get_query_schedule": (c_int32, [POINTER(c_int32), POINTER(c_int64)]),
+    "nbvh_set_traverse_block": (c_int32, [c_int32]),
+    "nbvh_autotune_query": (c_int32, [POINTER(ModelDesc), c_void_p, c_void_p, c_void_p, c_int32, Rays, c_int32, Hits,
+                                      c_void_p, c_size_t, c_int32, POINTER(TuneResult), POINTER(TuneResult), c_int32,
+                                      POINTER(c_int32), c_void_p]),
     "nbvh_query_stats": (c_int32, [c_void_p, c_int64, c_int32, POINTER(c_int64), POINTER(c_int32), c_void_p]),
     "nbvh_set_timing": (c_int32, [c_int32]),
     "nbvh_get_timing": (c_int32, [POINTER(c_double), POINTER(c_double), POINTER(c_int64)]),
@@ -411,6 +419,36 @@ def get_query_schedule():
     a, b = c_int32(), c_int64()
     _check(lib().nbvh_get_query_schedule(ctypes.byref(a), ctypes.byref(b)), "get_query_schedule")
     return a.value, b.value
+
+
+def set_traverse_block(threads: int):
+    _check(lib().nbvh_set_traverse_block(threads), "set_traverse_block")
+
+
+def _tune_dict(r: TuneResult) -> dict:
+    return {"schedule": ["waves", "persistent"][r.schedule], "patience_cycles": r.patience_cycles,
+            "traverse_block": r.traverse_block, "ms": r.ms}
+
+
+def autotune_query(desc: ModelDesc, table, mlp, nodes, n_nodes: int, rays: dict, max_segs: int, out=None,
+                   workspace=None, reps: int = 3):
+    """nbvh_autotune_query: times the query under each candidate schedule and
+    keeps the fastest (process-wide). Returns (best, [all candidates])."""
+    n = rays["ox"].numel()
+    if out is None:
+        out = new_hits(n, rays["ox"].device)
+    if workspace is None:
+        workspace = new_workspace(query_workspace_size(desc, n, max_segs), rays["ox"].device)
+    base = aligned_ptr(workspace)
+    avail = workspace.numel() - (base - workspace.data_ptr())
+    best = TuneResult()
+    cap = 16
+    arr = (TuneResult * cap)()
+    n_all = c_int32()
+    _check(lib().nbvh_autotune_query(ctypes.byref(desc), _ptr(table), _ptr(mlp), _ptr(nodes), n_nodes,
+                                     rays_struct(rays), max_segs, hits_struct(out), c_void_p(base), avail, reps,
+                                     ctypes.byref(best), arr, cap, ctypes.byref(n_all), _stream()), "autotune_query")
+    return _tune_dict(best), [_tune_dict(arr[i]) for i in range(min(cap, n_all.value))]
 
 
 def query_stats(workspace, n_rays: int, max_segs: int):

@@ -423,3 +423,11 @@ def hybrid_camera_rays(width: int, height: int) -> dict:
     az = math.radians(30.0)
     eye = (3.2 * math.cos(el) * math.sin(az), 3.2 * math.sin(el), 3.2 * math.cos(el) * math.cos(az))
     return look_at_rays(width, height, eye, (0.0, -0.2, 0.0), 40.0)
+
+
+C3 = Workload(
+    name="sphere-clusters-64_leaves-8192_L16F2T20-fp16_N16_mlp3x64_4M-mixed-rays",
+    model=ModelConfig(n_levels=16, n_features=2, log2_table=20, base_res=16, growth=1.5,
+                      n_samples=16, n_hidden=3, width=64),
+    n_leaves=8192, table_dtype="f16",
+    extra={"n_clusters": 64, "min_tris": 1000, "max_tris": 200000, "n_rays": 4194304, "camera_fraction": 0.6})

@@ -358,3 +358,32 @@ def test_persistent_schedule_equals_waves(mp, patience):
         assert torch.equal(hw[k], hp[k]), k
     assert launches == 1 and segs > rays["ox"].numel() // 4
     assert int(hw["hit"].sum()) > 100
+
+
+@pytest.mark.parametrize("mp", [B.FP16, B.FP32])
+def test_autotuner_times_candidates_and_keeps_results(mp):
+    """nbvh_autotune_query: every candidate is timed, the fastest is set
+    process-wide and returned, and the hit records equal the untuned query's
+    bit for bit (the schedule changes only the order of evaluation)."""
+    torch = _torch()
+    b = built("icosphere_l6", 1.0, 2.0)
+    desc = b.with_prec(mp)
+    rays = B.to_device_rays(W.mixed_rays(5000, seed=W.SEED_BASE + 32, radius=0.6))
+    old = B.get_query_schedule()
+    try:
+        ref = B.query_rays(desc, b.table, b.mlp, b.nodes, b.leaves["n_nodes"], rays, 24)
+        best, cands = B.autotune_query(desc, b.table, b.mlp, b.nodes, b.leaves["n_nodes"], rays, 24, reps=2)
+        got = B.query_rays(desc, b.table, b.mlp, b.nodes, b.leaves["n_nodes"], rays, 24)
+        now = B.get_query_schedule()
+    finally:
+        B.set_query_schedule(*old)
+        B.set_traverse_block(128)
+    assert B.device_status() == 0
+    n_sched = 6 if mp != B.FP32 else 1
+    assert len(cands) == n_sched + 2
+    assert {c["schedule"] for c in cands} == ({"waves", "persistent"} if mp != B.FP32 else {"waves"})
+    assert all(c["ms"] > 0 for c in cands)
+    assert best["ms"] == min(c["ms"] for c in cands)
+    assert now == (1 if best["schedule"] == "persistent" else 0, best["patience_cycles"])
+    for k in ref:
+        assert torch.equal(ref[k], got[k]), k

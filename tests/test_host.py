@@ -182,3 +182,18 @@ def test_tri_blas_single_leaf_and_bad_arguments():
     bad[1, 1, 1] = np.nan
     with pytest.raises(B.NBVHError):
         B.build_tri_blas(bad, 4)
+
+
+def test_schedule_and_tuner_arguments_checked_on_host():
+    """Invalid schedule settings and autotuner arguments are rejected before
+    any device work (no GPU needed)."""
+    L = B.lib()
+    assert L.nbvh_set_query_schedule(7, 0) == 1
+    assert L.nbvh_set_query_schedule(1, -5) == 1
+    assert L.nbvh_set_traverse_block(100) == 1
+    best = B.TuneResult()
+    n_all = ctypes.c_int32()
+    assert L.nbvh_autotune_query(None, None, None, None, 0, B.Rays(), 8, B.Hits(), None, 0, 1, ctypes.byref(best),
+                                 None, 0, ctypes.byref(n_all), None) == 1
+    s, p = B.get_query_schedule()
+    assert s in (0, 1) and p >= 0
