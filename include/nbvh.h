@@ -511,10 +511,13 @@ nbvh_status nbvh_hybrid_workspace_size(const nbvh_instance* inst, int32_t n_inst
  * [tmin, tmax]. The result is the smallest t over the instances; equal t goes
  * to the lower instance index. out.leaf is the triangle index or the N-BVH
  * leaf; out_inst (device, rays.n int32) the instance index, -1 on a miss.
- * Instances are processed in index order as wavefront passes over all rays,
- * each keeping the record unless it finds a strictly closer hit; a neural
- * pass skips the leaves whose segment starts at or beyond the record (their
- * hits cannot be closer), which leaves the result unchanged.
+ * Instances are processed in index order as wavefront passes, each keeping
+ * the record unless it finds a strictly closer hit. Before the first neural
+ * instance, one top-level pass tests every ray against the root boxes of all
+ * remaining neural instances and lists, per instance, the rays that meet
+ * them before the record; each neural pass then traverses only its list and
+ * skips the leaves whose segment starts at or beyond the record (their hits
+ * cannot be closer), which leaves the result unchanged.
  * inst: host array of n_inst (1..64) instances; workspace: device, 256-byte
  * aligned, >= nbvh_hybrid_workspace_size bytes. Segment overflow of a neural
  * pass is reported as in nbvh_query_rays. */

@@ -245,7 +245,8 @@ PQueue pq_of(const QueryWs& w, int32_t max_segs) {
 cudaError_t launch_query_stages(const nbvh_model_desc* desc, const GridParams& gp, const void* table,
                                 const float* mlp, const nbvh_node* nodes, const nbvh_rays& rays, int32_t max_segs,
                                 const nbvh_hits& out, const QueryWs& w, bool merge, int32_t* inst_out,
-                                int32_t inst_id, cudaEvent_t after_traverse, cudaStream_t s) {
+                                int32_t inst_id, cudaEvent_t after_traverse, cudaStream_t s,
+                                const int32_t* list = nullptr, const int32_t* list_count = nullptr) {
   TraverseOut to;
   std::memset(&to, 0, sizeof(to));
   to.seg_count = w.seg_count;
@@ -265,7 +266,13 @@ cudaError_t launch_query_stages(const nbvh_model_desc* desc, const GridParams& g
     if (me != cudaSuccess) return me;
   }
   const int tb = g_traverse_block.load();
-  traverse_kernel<<<unsigned((rays.n + tb - 1) / tb), tb, 0, s>>>(nodes, ray_ptrs(rays), rays.n, to);
+  if (list) {  // only the listed rays (grid-stride over the device-side count)
+    const int64_t blocks = std::min<int64_t>((rays.n + 255) / 256, int64_t(sm_count()) * 8);
+    traverse_list_kernel<<<unsigned(std::max<int64_t>(blocks, 1)), 256, 0, s>>>(nodes, ray_ptrs(rays), rays.n,
+                                                                                 list, list_count, to);
+  } else {
+    traverse_kernel<<<unsigned((rays.n + tb - 1) / tb), tb, 0, s>>>(nodes, ray_ptrs(rays), rays.n, to);
+  }
   count_launches(1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -569,11 +576,35 @@ extern "C" nbvh_status nbvh_trace_triangles(const nbvh_tri_blas* blas, nbvh_rays
   return status_of(cudaGetLastError());
 }
 
+// Hybrid workspace: the query workspace of the deepest neural instance, then
+// one ray list per neural instance (n_rays entries) and their counts.
+struct HybridWs {
+  QueryWs q;
+  int32_t* lists;
+  int32_t* counts;
+  size_t bytes;
+};
+
+HybridWs carve_hybrid(void* base, const nbvh_instance* inst, int32_t n_inst, int64_t n) {
+  HybridWs h;
+  int32_t n_neural = 0;
+  for (int i = 0; i < n_inst; ++i) n_neural += inst[i].kind == NBVH_BLAS_NEURAL;
+  const int32_t ms = std::max(hybrid_max_segs(inst, n_inst), 1);
+  h.q = carve_query(base, n, ms);
+  char* p = static_cast<char*>(base);
+  size_t off = h.q.bytes;
+  h.lists = p ? reinterpret_cast<int32_t*>(p + off) : nullptr;
+  off += align256(sizeof(int32_t) * size_t(n) * size_t(n_neural));
+  h.counts = p ? reinterpret_cast<int32_t*>(p + off) : nullptr;
+  off += align256(sizeof(int32_t) * kMaxInstances);
+  h.bytes = off;
+  return h;
+}
+
 extern "C" nbvh_status nbvh_hybrid_workspace_size(const nbvh_instance* inst, int32_t n_inst, int64_t n_rays,
                                                   size_t* bytes) {
   if (!instances_valid(inst, n_inst) || n_rays < 0 || !bytes) return NBVH_ERR_INVALID_ARG;
-  const int32_t ms = hybrid_max_segs(inst, n_inst);
-  *bytes = ms > 0 ? carve_query(nullptr, n_rays, ms).bytes : 256;
+  *bytes = carve_hybrid(nullptr, inst, n_inst, n_rays).bytes;
   return NBVH_OK;
 }
 
@@ -584,9 +615,8 @@ extern "C" nbvh_status nbvh_hybrid_trace(const nbvh_instance* inst, int32_t n_in
   if (rays.n == 0) return NBVH_OK;
   if (!hits_valid(out) || !out_inst || !workspace || rays.n > (int64_t(1) << 31) - 1) return NBVH_ERR_INVALID_ARG;
   if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0) return NBVH_ERR_INVALID_ARG;
-  const int32_t ms = hybrid_max_segs(inst, n_inst);
-  QueryWs w = carve_query(workspace, rays.n, std::max(ms, 1));
-  if (ms > 0 && ws_bytes < w.bytes) return NBVH_ERR_WORKSPACE_TOO_SMALL;
+  const HybridWs hw = carve_hybrid(workspace, inst, n_inst, rays.n);
+  if (ws_bytes < hw.bytes) return NBVH_ERR_WORKSPACE_TOO_SMALL;
   std::vector<GridParams> gps(static_cast<size_t>(n_inst));
   for (int i = 0; i < n_inst; ++i)
     if (inst[i].kind == NBVH_BLAS_NEURAL && !make_grid(&inst[i].desc, gps[i])) return NBVH_ERR_INVALID_ARG;
@@ -595,6 +625,8 @@ extern "C" nbvh_status nbvh_hybrid_trace(const nbvh_instance* inst, int32_t n_in
   count_launches(1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return NBVH_ERR_CUDA;
+  int32_t culled_from = -1;  // first instance covered by the top-level cull
+  std::vector<int32_t> cull_slot(static_cast<size_t>(n_inst), -1);
   for (int i = 0; i < n_inst; ++i) {
     const nbvh_instance& x = inst[i];
     if (x.kind == NBVH_BLAS_TRIANGLES) {
@@ -602,13 +634,40 @@ extern "C" nbvh_status nbvh_hybrid_trace(const nbvh_instance* inst, int32_t n_in
       tri_trace_kernel<<<unsigned((rays.n + 127) / 128), 128, 0, s>>>(a);
       count_launches(1);
       e = cudaGetLastError();
-    } else {
-      e = cudaMemsetAsync(w.counters, 0, counters_bytes(x.max_segs), s);
-      if (e != cudaSuccess) return NBVH_ERR_CUDA;
-      QueryWs wi = carve_query(workspace, rays.n, x.max_segs);
-      e = launch_query_stages(&x.desc, gps[i], x.table, x.mlp, x.nodes, rays, x.max_segs, out, wi, true, out_inst,
-                              i, nullptr, s);
+      if (e != cudaSuccess) return status_of(e);
+      continue;
     }
+    if (culled_from < 0) {
+      // Top level: one pass over the rays builds, for every neural instance
+      // from here on, the list of rays whose interval meets its root boxes
+      // before the record so far (the record only shrinks, so each list stays
+      // a superset of the rays its traversal can give a segment).
+      CullArgs c;
+      std::memset(&c, 0, sizeof(c));
+      int32_t k = 0;
+      for (int j = i; j < n_inst; ++j) {
+        if (inst[j].kind != NBVH_BLAS_NEURAL) continue;
+        cull_slot[j] = k;
+        c.root[k] = inst[j].nodes;
+        c.list[k] = hw.lists + size_t(k) * size_t(rays.n);
+        ++k;
+      }
+      c.count = hw.counts;
+      c.n_inst = k;
+      e = cudaMemsetAsync(hw.counts, 0, sizeof(int32_t) * kMaxInstances, s);
+      if (e != cudaSuccess) return NBVH_ERR_CUDA;
+      tlas_cull_kernel<<<unsigned((rays.n + 255) / 256), 256, 0, s>>>(ray_ptrs(rays), rays.n, out.t, c);
+      count_launches(1);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return NBVH_ERR_CUDA;
+      culled_from = i;
+    }
+    const int32_t k = cull_slot[i];
+    e = cudaMemsetAsync(hw.q.counters, 0, counters_bytes(x.max_segs), s);
+    if (e != cudaSuccess) return NBVH_ERR_CUDA;
+    QueryWs wi = carve_query(workspace, rays.n, x.max_segs);
+    e = launch_query_stages(&x.desc, gps[i], x.table, x.mlp, x.nodes, rays, x.max_segs, out, wi, true, out_inst, i,
+                            nullptr, s, hw.lists + size_t(k) * size_t(rays.n), hw.counts + k);
     if (e != cudaSuccess) return status_of(e);
   }
   return NBVH_OK;

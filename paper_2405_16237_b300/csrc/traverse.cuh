@@ -22,116 +22,240 @@ struct TraverseOut {
   unsigned long long* ring0;
 };
 
-// One thread per ray. Depth-first with a short stack; the nearer child is
-// descended first. Child boxes are stored in the parent, so one 64-byte node
-// load tests two boxes. A child box contains all boxes below it and rounding
-// of the slab arithmetic is monotone, so an empty clip prunes its subtree.
-// Segments are inserted into the ray's list in (t0, leaf) order; the list is
-// slot-major (slot s of ray r at s * n + r) so a warp's stores coalesce.
+// Traversal of ray r (S1). Depth-first with a short stack; the nearer child
+// is descended first. Child boxes are stored in the parent, so one 64-byte
+// node load tests two boxes. A child box contains all boxes below it and
+// rounding of the slab arithmetic is monotone, so an empty clip prunes its
+// subtree. Segments are inserted into the ray's list in (t0, leaf) order; the
+// list is slot-major (slot s of ray r at s * n + r) so a warp's stores
+// coalesce. Returns the ray's segment count.
+__device__ __forceinline__ int traverse_ray(const nbvh_node* __restrict__ nodes, const RayPtrs& rays, int64_t n,
+                                            int64_t r, const TraverseOut& out) {
+  int count = 0;
+  const float ox = rays.ox[r], oy = rays.oy[r], oz = rays.oz[r];
+  const float dx = rays.dx[r], dy = rays.dy[r], dz = rays.dz[r];
+  const float tmin = rays.tmin[r], tmax = rays.tmax[r];
+  const RayR ray = make_rayr(ox, oy, oz, dx, dy, dz, tmin, tmax);
+  const int max_segs = out.max_segs;
+  const bool merge = out.merge != 0;
+  const float best = merge ? out.hits.t[r] : 0.0f;
+  bool overflow = false;
+  auto emit = [&](int leaf, float t0, float t1) {
+    int pos;
+    if (count < max_segs) {
+      pos = count++;
+    } else {
+      overflow = true;
+      const size_t q = size_t(max_segs - 1) * size_t(n) + size_t(r);
+      const float lt = out.seg_t0[q];
+      const int ll = out.seg_leaf[q];
+      if (t0 > lt || (t0 == lt && leaf > ll)) return;
+      pos = max_segs - 1;
+    }
+    while (pos > 0) {
+      const size_t q = size_t(pos - 1) * size_t(n) + size_t(r);
+      const float pt = out.seg_t0[q];
+      const int pl = out.seg_leaf[q];
+      if (pt < t0 || (pt == t0 && pl < leaf)) break;
+      const size_t w = size_t(pos) * size_t(n) + size_t(r);
+      out.seg_t0[w] = pt;
+      out.seg_t1[w] = out.seg_t1[q];
+      out.seg_leaf[w] = pl;
+      --pos;
+    }
+    const size_t w = size_t(pos) * size_t(n) + size_t(r);
+    out.seg_t0[w] = t0;
+    out.seg_t1[w] = t1;
+    out.seg_leaf[w] = leaf;
+  };
+
+  int stack[kTraverseStack];
+  int sp = 0;
+  int cur = 0;
+  for (int guard = 0; guard < (1 << 26); ++guard) {
+    const float4* np = reinterpret_cast<const float4*>(nodes + cur);
+    const float4 a = __ldg(np);
+    const float4 b = __ldg(np + 1);
+    const float4 c = __ldg(np + 2);
+    const int4 e = __ldg(reinterpret_cast<const int4*>(np + 3));
+    float a0, a1, b0, b1;
+    bool h0 = clip_box(ray, a.x, a.y, a.z, a.w, b.x, b.y, a0, a1);
+    bool h1 = (e.y != kNodeNone) && clip_box(ray, b.z, b.w, c.x, c.y, c.z, c.w, b0, b1);
+    if (merge) {
+      h0 = h0 && a0 < best;
+      h1 = h1 && b0 < best;
+    }
+    if (h0 && e.x < 0) emit(~e.x, a0, a1);
+    if (h1 && e.y < 0) emit(~e.y, b0, b1);
+    const bool g0 = h0 && e.x >= 0;
+    const bool g1 = h1 && e.y >= 0;
+    if (g0 && g1) {
+      const bool first0 = a0 <= b0;
+      if (sp < kTraverseStack) {
+        stack[sp++] = first0 ? e.y : e.x;
+      } else {
+        set_status(NBVH_ERR_UNSUPPORTED);
+      }
+      cur = first0 ? e.x : e.y;
+    } else if (g0) {
+      cur = e.x;
+    } else if (g1) {
+      cur = e.y;
+    } else {
+      if (sp == 0) break;
+      cur = stack[--sp];
+    }
+  }
+  out.seg_count[r] = count;
+  if (overflow) set_status(NBVH_ERR_SEGMENT_OVERFLOW);
+  if (out.hits.hit && !merge) {
+    out.hits.hit[r] = 0;
+    out.hits.t[r] = __int_as_float(0x7f800000);
+    out.hits.nx[r] = 0.0f;
+    out.hits.ny[r] = 0.0f;
+    out.hits.nz[r] = 0.0f;
+    out.hits.leaf[r] = -1;
+  }
+  return count;
+}
+
+// Warp-aggregated append of the rays with segments to the first queue (the
+// whole warp calls it).
+__device__ __forceinline__ void queue_first(const TraverseOut& out, bool want, int64_t r) {
+  const unsigned m = __ballot_sync(0xffffffffu, want);
+  if (m) {
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(out.qlen0, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    const int pos = base + __popc(m & ((1u << lane) - 1u));
+    if (want && out.ring0) out.ring0[pos] = (unsigned long long)r;
+    else if (want) out.queue0[pos] = int32_t(r);
+  }
+}
+
+// One thread per ray.
 __global__ void __launch_bounds__(256) traverse_kernel(const nbvh_node* __restrict__ nodes,
                                                        RayPtrs rays, int64_t n, TraverseOut out) {
   const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const bool active = r < n;
   int count = 0;
-  if (active) {
-    const float ox = rays.ox[r], oy = rays.oy[r], oz = rays.oz[r];
-    const float dx = rays.dx[r], dy = rays.dy[r], dz = rays.dz[r];
-    const float tmin = rays.tmin[r], tmax = rays.tmax[r];
-    const RayR ray = make_rayr(ox, oy, oz, dx, dy, dz, tmin, tmax);
-    const int max_segs = out.max_segs;
-    const bool merge = out.merge != 0;
-    const float best = merge ? out.hits.t[r] : 0.0f;
-    bool overflow = false;
-    auto emit = [&](int leaf, float t0, float t1) {
-      int pos;
-      if (count < max_segs) {
-        pos = count++;
-      } else {
-        overflow = true;
-        const size_t q = size_t(max_segs - 1) * size_t(n) + size_t(r);
-        const float lt = out.seg_t0[q];
-        const int ll = out.seg_leaf[q];
-        if (t0 > lt || (t0 == lt && leaf > ll)) return;
-        pos = max_segs - 1;
-      }
-      while (pos > 0) {
-        const size_t q = size_t(pos - 1) * size_t(n) + size_t(r);
-        const float pt = out.seg_t0[q];
-        const int pl = out.seg_leaf[q];
-        if (pt < t0 || (pt == t0 && pl < leaf)) break;
-        const size_t w = size_t(pos) * size_t(n) + size_t(r);
-        out.seg_t0[w] = pt;
-        out.seg_t1[w] = out.seg_t1[q];
-        out.seg_leaf[w] = pl;
-        --pos;
-      }
-      const size_t w = size_t(pos) * size_t(n) + size_t(r);
-      out.seg_t0[w] = t0;
-      out.seg_t1[w] = t1;
-      out.seg_leaf[w] = leaf;
-    };
+  if (active) count = traverse_ray(nodes, rays, n, r, out);
+  if (out.queue0 || out.ring0) queue_first(out, active && count > 0, r);
+}
 
-    int stack[kTraverseStack];
-    int sp = 0;
-    int cur = 0;
-    for (int guard = 0; guard < (1 << 26); ++guard) {
-      const float4* np = reinterpret_cast<const float4*>(nodes + cur);
-      const float4 a = __ldg(np);
-      const float4 b = __ldg(np + 1);
-      const float4 c = __ldg(np + 2);
-      const int4 e = __ldg(reinterpret_cast<const int4*>(np + 3));
-      float a0, a1, b0, b1;
-      bool h0 = clip_box(ray, a.x, a.y, a.z, a.w, b.x, b.y, a0, a1);
-      bool h1 = (e.y != kNodeNone) && clip_box(ray, b.z, b.w, c.x, c.y, c.z, c.w, b0, b1);
-      if (merge) {
-        h0 = h0 && a0 < best;
-        h1 = h1 && b0 < best;
-      }
-      if (h0 && e.x < 0) emit(~e.x, a0, a1);
-      if (h1 && e.y < 0) emit(~e.y, b0, b1);
-      const bool g0 = h0 && e.x >= 0;
-      const bool g1 = h1 && e.y >= 0;
-      if (g0 && g1) {
-        const bool first0 = a0 <= b0;
-        if (sp < kTraverseStack) {
-          stack[sp++] = first0 ? e.y : e.x;
-        } else {
-          set_status(NBVH_ERR_UNSUPPORTED);
-        }
-        cur = first0 ? e.x : e.y;
-      } else if (g0) {
-        cur = e.x;
-      } else if (g1) {
-        cur = e.y;
-      } else {
-        if (sp == 0) break;
-        cur = stack[--sp];
-      }
-    }
-    out.seg_count[r] = count;
-    if (overflow) set_status(NBVH_ERR_SEGMENT_OVERFLOW);
-    if (out.hits.hit && !merge) {
-      out.hits.hit[r] = 0;
-      out.hits.t[r] = __int_as_float(0x7f800000);
-      out.hits.nx[r] = 0.0f;
-      out.hits.ny[r] = 0.0f;
-      out.hits.nz[r] = 0.0f;
-      out.hits.leaf[r] = -1;
+// The rays list[0 .. *list_count) only (hybrid hierarchy: the rays whose
+// interval meets the instance's root boxes); grid-stride, warp-uniform loop.
+__global__ void __launch_bounds__(256) traverse_list_kernel(const nbvh_node* __restrict__ nodes, RayPtrs rays,
+                                                            int64_t n, const int32_t* __restrict__ list,
+                                                            const int32_t* __restrict__ list_count,
+                                                            TraverseOut out) {
+  const int64_t cnt = *list_count;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t base = int64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31); base < cnt; base += stride) {
+    const int64_t i = base + (threadIdx.x & 31);
+    const bool active = i < cnt;
+    const int64_t r = active ? int64_t(list[i]) : 0;
+    int count = 0;
+    if (active) count = traverse_ray(nodes, rays, n, r, out);
+    if (out.queue0 || out.ring0) queue_first(out, active && count > 0, r);
+  }
+}
+
+// Top level of the hybrid hierarchy: for every ray, each neural instance whose
+// root boxes the ray's [tmin, tmax] meets before its current record (the
+// traversal's own root test in merge mode, so a ray left out would find no
+// segment there) gets the ray appended to its list. Appends are counted per
+// block in shared memory, then reserved with one atomic per instance.
+constexpr int kMaxInstances = 64;
+struct CullArgs {
+  const nbvh_node* root[kMaxInstances];
+  int32_t* list[kMaxInstances];
+  int32_t* count;  // [n_inst]
+  int32_t n_inst;
+};
+
+__device__ __forceinline__ bool root_meets(const nbvh_node* __restrict__ nodes, const RayR& ray, float best) {
+  const float4* np = reinterpret_cast<const float4*>(nodes);
+  const float4 a = __ldg(np);
+  const float4 b = __ldg(np + 1);
+  const float4 c = __ldg(np + 2);
+  const int4 e = __ldg(reinterpret_cast<const int4*>(np + 3));
+  float a0, a1, b0, b1;
+  const bool h0 = clip_box(ray, a.x, a.y, a.z, a.w, b.x, b.y, a0, a1) && a0 < best;
+  const bool h1 = (e.y != kNodeNone) && clip_box(ray, b.z, b.w, c.x, c.y, c.z, c.w, b0, b1) && b0 < best;
+  return h0 || h1;
+}
+
+// Cheap pre-test: the ray against the root's bounding box grown on every
+// side by g = 1e-3 of its size + 1e-4 (1 + |lo| + |hi|), the interval ends
+// compared with a relative slack of 1e-5. A "false" is conservative: these
+// slab values and the exact ones differ by a few ulps of (b - o) / d, far
+// less than g / |d|, so a ray this rejects fails root_meets too. A direction
+// component too small for a finite reciprocal is passed on to the exact test.
+__device__ __forceinline__ bool root_maybe(const float* __restrict__ box, const RayR& ray, float best) {
+  float en = ray.tmin, ex = fminf(ray.tmax, best);
+  const float slack = 1e-5f;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const float lo = box[i], hi = box[3 + i];
+    const float g = 1e-3f * (hi - lo) + 1e-4f * (1.0f + fabsf(lo) + fabsf(hi));
+    if (ray.d[i] != 0.0f && !isfinite(ray.inv[i])) return true;
+    if (ray.d[i] == 0.0f) {
+      if (ray.o[i] < lo - g || ray.o[i] > hi + g) return false;
+    } else {
+      const float ta = (lo - g - ray.o[i]) * ray.inv[i];
+      const float tb = (hi + g - ray.o[i]) * ray.inv[i];
+      en = fmaxf(en, fminf(ta, tb));
+      ex = fminf(ex, fmaxf(ta, tb));
     }
   }
-  if (out.queue0 || out.ring0) {
-    const bool want = active && count > 0;
-    const unsigned m = __ballot_sync(0xffffffffu, want);
-    if (m) {
-      const int lane = threadIdx.x & 31;
-      const int leader = __ffs(m) - 1;
-      int base = 0;
-      if (lane == leader) base = atomicAdd(out.qlen0, __popc(m));
-      base = __shfl_sync(0xffffffffu, base, leader);
-      const int pos = base + __popc(m & ((1u << lane) - 1u));
-      if (want && out.ring0) out.ring0[pos] = (unsigned long long)r;
-      else if (want) out.queue0[pos] = int32_t(r);
+  return en <= ex + slack * (fabsf(ex) + fabsf(en)) + 1e-30f;
+}
+
+__global__ void __launch_bounds__(256) tlas_cull_kernel(RayPtrs rays, int64_t n, const float* __restrict__ best_t,
+                                                        CullArgs c) {
+  constexpr int kWarps = 256 / 32;
+  __shared__ int s_cnt[kMaxInstances], s_base[kMaxInstances];
+  __shared__ int s_wbase[kWarps][kMaxInstances];  // a warp's offset within the block's share
+  __shared__ float s_box[kMaxInstances][6];       // root bounding boxes
+  for (int k = threadIdx.x; k < c.n_inst; k += blockDim.x) {
+    s_cnt[k] = 0;
+    const nbvh_node* nd = c.root[k];
+    const bool two = nd->child1 != kNodeNone;
+    for (int j = 0; j < 3; ++j) {
+      s_box[k][j] = two ? fminf(nd->lo0[j], nd->lo1[j]) : nd->lo0[j];
+      s_box[k][3 + j] = two ? fmaxf(nd->hi0[j], nd->hi1[j]) : nd->hi0[j];
     }
+  }
+  __syncthreads();
+  const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const bool active = r < n;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint64_t mask = 0;  // instances whose root the ray meets
+  if (active) {
+    const RayR ray = make_rayr(rays.ox[r], rays.oy[r], rays.oz[r], rays.dx[r], rays.dy[r], rays.dz[r],
+                               rays.tmin[r], rays.tmax[r]);
+    const float best = best_t[r];
+    for (int k = 0; k < c.n_inst; ++k)
+      if (root_maybe(s_box[k], ray, best) && root_meets(c.root[k], ray, best)) mask |= uint64_t(1) << k;
+  }
+  // count: one shared-memory increment per warp and instance
+  for (int k = 0; k < c.n_inst; ++k) {
+    const unsigned m = __ballot_sync(0xffffffffu, (mask >> k) & 1);
+    if (m && lane == 0) s_wbase[warp][k] = atomicAdd(&s_cnt[k], __popc(m));
+  }
+  __syncthreads();
+  // reserve: one global increment per block and instance
+  for (int k = threadIdx.x; k < c.n_inst; k += blockDim.x)
+    s_base[k] = s_cnt[k] > 0 ? atomicAdd(c.count + k, s_cnt[k]) : 0;
+  __syncthreads();
+  // write
+  for (int k = 0; k < c.n_inst; ++k) {
+    const unsigned m = __ballot_sync(0xffffffffu, (mask >> k) & 1);
+    if ((mask >> k) & 1)
+      c.list[k][s_base[k] + s_wbase[warp][k] + __popc(m & ((1u << lane) - 1u))] = int32_t(r);
   }
 }
 
