@@ -524,6 +524,18 @@ nbvh_status nbvh_hybrid_workspace_size(const nbvh_instance* inst, int32_t n_inst
 nbvh_status nbvh_hybrid_trace(const nbvh_instance* inst, int32_t n_inst, nbvh_rays rays, nbvh_hits out,
                               int32_t* out_inst, void* workspace, size_t ws_bytes, void* stream);
 
+/* Device (synchronises). Measurement utility, no counterpart in the paper:
+ * the L2 random-gather ceiling that bounds the hash-table gather when the
+ * table is L2-resident. One CTA of 1,024 threads per SM issues independent
+ * 4-byte loads at pseudo-random positions of table (n_entries 4-byte
+ * entries, a power of two in [1024, 2^31]; device memory the caller owns,
+ * any contents; pick 16-64 MB so it stays in L2), 16 in flight per thread.
+ * *gsectors_per_s receives the best of three timed launches in 1e9 loads per
+ * second (each load a distinct 32-byte sector). sink: one device uint32 the
+ * kernel may write. */
+nbvh_status nbvh_probe_l2_gather(const void* table, int64_t n_entries, uint32_t* sink, double* gsectors_per_s,
+                                 void* stream);
+
 /* Device. Reads and clears the device status word (synchronises the stream). */
 nbvh_status nbvh_get_device_status(void* stream);
 

@@ -14,6 +14,7 @@
 #include "eval_tc.cuh"
 #include "bounce.cuh"
 #include "tri_blas.cuh"
+#include "probe.cuh"
 #include "train.cuh"
 #include "train_tc.cuh"
 
@@ -757,6 +758,44 @@ extern "C" nbvh_status nbvh_autotune_query(const nbvh_model_desc* desc, const vo
 extern "C" nbvh_status nbvh_set_traverse_block(int32_t threads) {
   if (threads != 64 && threads != 128 && threads != 256) return NBVH_ERR_INVALID_ARG;
   g_traverse_block.store(threads);
+  return NBVH_OK;
+}
+
+// ---------------------------------------------------------------- measurement utility
+extern "C" nbvh_status nbvh_probe_l2_gather(const void* table, int64_t n_entries, uint32_t* sink,
+                                            double* gsectors_per_s, void* stream) {
+  if (!table || !sink || !gsectors_per_s || n_entries < 1024 || n_entries > (int64_t(1) << 31) ||
+      (n_entries & (n_entries - 1)) != 0)
+    return NBVH_ERR_INVALID_ARG;
+  cudaStream_t s = as_stream(stream);
+  const uint32_t mask = uint32_t(n_entries - 1);
+  const int blocks = sm_count(), threads = 1024, iters = 100;
+  const uint32_t* tab = static_cast<const uint32_t*>(table);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return NBVH_ERR_CUDA;
+  }
+  nbvh_status st = NBVH_OK;
+  float best = 0.0f;
+  for (int rep = 0; rep < 4 && st == NBVH_OK; ++rep) {  // the first launch warms the table into L2
+    cudaEventRecord(e0, s);
+    probe_gather_kernel<<<blocks, threads, 0, s>>>(tab, mask, iters, sink);
+    count_launches(1);
+    cudaEventRecord(e1, s);
+    if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+      st = NBVH_ERR_CUDA;
+      break;
+    }
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && (best == 0.0f || ms < best)) best = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != NBVH_OK) return st;
+  const double loads = double(blocks) * threads * iters * kProbeLoads;
+  *gsectors_per_s = loads / (double(best) * 1e-3) / 1e9;
   return NBVH_OK;
 }
 

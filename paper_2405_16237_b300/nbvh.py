@@ -151,6 +151,7 @@ _SIGS = {
     "nbvh_hybrid_workspace_size": (c_int32, [POINTER(Instance), c_int32, c_int64, POINTER(c_size_t)]),
     "nbvh_hybrid_trace": (c_int32, [POINTER(Instance), c_int32, Rays, Hits, c_void_p, c_void_p, c_size_t,
                                     c_void_p]),
+    "nbvh_probe_l2_gather": (c_int32, [c_void_p, c_int64, c_void_p, POINTER(c_double), c_void_p]),
     "nbvh_get_device_status": (c_int32, [c_void_p]),
 }
 
@@ -773,3 +774,15 @@ def hybrid_trace(instances, rays: dict, out=None, inst_out=None, workspace=None)
     _check(lib().nbvh_hybrid_trace(arr, len(arr), rays_struct(rays), hits_struct(out), _ptr(inst_out),
                                    c_void_p(base), avail, _stream()), "hybrid_trace")
     return out, inst_out
+
+
+def probe_l2_gather(n_entries: int = 1 << 24) -> float:
+    """nbvh_probe_l2_gather: the L2 random-gather ceiling in 1e9 sector loads/s
+    (a measurement utility for the gather's roofline)."""
+    torch = _torch()
+    tab = torch.ones(n_entries, dtype=torch.int32, device="cuda")
+    sink = torch.zeros(1, dtype=torch.int32, device="cuda")
+    g = c_double()
+    _check(lib().nbvh_probe_l2_gather(_ptr(tab), n_entries, _ptr(sink), ctypes.byref(g), _stream()),
+           "probe_l2_gather")
+    return g.value
