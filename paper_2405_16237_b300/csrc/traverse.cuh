@@ -164,10 +164,11 @@ __global__ void __launch_bounds__(256) traverse_list_kernel(const nbvh_node* __r
 }
 
 // Top level of the hybrid hierarchy: for every ray, each neural instance whose
-// root boxes the ray's [tmin, tmax] meets before its current record (the
-// traversal's own root test in merge mode, so a ray left out would find no
-// segment there) gets the ray appended to its list. Appends are counted per
-// block in shared memory, then reserved with one atomic per instance.
+// root bounding box (grown, see root_maybe) the ray's [tmin, tmax] meets
+// before its current record gets the ray appended to its list: a superset of
+// the rays for which the traversal's own root test passes, so a ray left out
+// would find no segment there. Appends are counted per warp in shared memory,
+// then reserved with one atomic per block and instance.
 constexpr int kMaxInstances = 64;
 struct CullArgs {
   const nbvh_node* root[kMaxInstances];
@@ -188,12 +189,13 @@ __device__ __forceinline__ bool root_meets(const nbvh_node* __restrict__ nodes, 
   return h0 || h1;
 }
 
-// Cheap pre-test: the ray against the root's bounding box grown on every
-// side by g = 1e-3 of its size + 1e-4 (1 + |lo| + |hi|), the interval ends
-// compared with a relative slack of 1e-5. A "false" is conservative: these
-// slab values and the exact ones differ by a few ulps of (b - o) / d, far
-// less than g / |d|, so a ray this rejects fails root_meets too. A direction
-// component too small for a finite reciprocal is passed on to the exact test.
+// The ray against the root's bounding box grown on every side by
+// g = 1e-3 of its size + 1e-4 (1 + |lo| + |hi|), the interval ends compared
+// with a relative slack of 1e-5. A "false" is conservative: these slab values
+// and the traversal's exactly rounded ones differ by a few ulps of
+// (b - o) / d, far less than g / |d|, so a ray this rejects fails the
+// traversal's root test (root_meets) too. A direction component too small for
+// a finite reciprocal passes.
 __device__ __forceinline__ bool root_maybe(const float* __restrict__ box, const RayR& ray, float best) {
   float en = ray.tmin, ex = fminf(ray.tmax, best);
   const float slack = 1e-5f;
@@ -239,7 +241,7 @@ __global__ void __launch_bounds__(256) tlas_cull_kernel(RayPtrs rays, int64_t n,
                                rays.tmin[r], rays.tmax[r]);
     const float best = best_t[r];
     for (int k = 0; k < c.n_inst; ++k)
-      if (root_maybe(s_box[k], ray, best) && root_meets(c.root[k], ray, best)) mask |= uint64_t(1) << k;
+      if (root_maybe(s_box[k], ray, best)) mask |= uint64_t(1) << k;
   }
   // count: one shared-memory increment per warp and instance
   for (int k = 0; k < c.n_inst; ++k) {

@@ -41,9 +41,42 @@ __device__ __forceinline__ bool tri_mt(const float* __restrict__ T, float ox, fl
   return true;
 }
 
+// Conservative slab test of the classical BLAS (robust traversal after Ize,
+// "Robust BVH Ray Traversal", JCGT 2013): slab values from the ray's
+// reciprocal, the far end grown by 2 gamma_3 (gamma_n = n eps / (1 - n eps),
+// eps = 2^-24) of its magnitude, so rounding never drops a box the ray meets;
+// a zero direction component keeps the slab iff lo <= o <= hi. The interval's
+// upper end tmax (the best hit so far) is grown the same way, so a box whose
+// entry rounds up onto it is still visited. The boxes only prune:
+// Moller-Trumbore decides every hit.
+constexpr float kRobustGrow = 2.0f * (3.0f * 5.9604645e-8f) / (1.0f - 3.0f * 5.9604645e-8f);
+
+__device__ __forceinline__ bool clip_box_robust(const RayR& r, float tmax, float lx, float ly, float lz, float hx,
+                                                float hy, float hz, float& t0) {
+  constexpr float kGrow = kRobustGrow;
+  float en = r.tmin, ex = tmax + fabsf(tmax) * kGrow;
+  const float lo[3] = {lx, ly, lz}, hi[3] = {hx, hy, hz};
+  bool empty = false;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    if (r.d[i] == 0.0f) {
+      empty |= (r.o[i] < lo[i]) | (r.o[i] > hi[i]);
+    } else {
+      const float a = (lo[i] - r.o[i]) * r.inv[i];
+      const float b = (hi[i] - r.o[i]) * r.inv[i];
+      const float f = fmaxf(a, b);
+      en = fmaxf(en, fminf(a, b));
+      ex = fminf(ex, f + fabsf(f) * kGrow);
+    }
+  }
+  t0 = en;
+  return !empty && en <= ex;
+}
+
 // Closest hit with t in [tmin, tmax]; equal t goes to the lower caller index.
-// The traversal visits the nearer child first and skips boxes whose clip to
-// [tmin, best] is empty (the clip is inclusive, so equal-t candidates survive).
+// The traversal visits the nearer child first and skips boxes whose
+// conservative clip to [tmin, best] is empty (inclusive, so equal-t candidates
+// survive).
 __global__ void __launch_bounds__(128) tri_trace_kernel(TriBlasArgs a) {
   const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (r >= a.n) return;
@@ -67,10 +100,9 @@ __global__ void __launch_bounds__(128) tri_trace_kernel(TriBlasArgs a) {
       const float4 q = __ldg(np + 1);
       const float4 c = __ldg(np + 2);
       const int4 e = __ldg(reinterpret_cast<const int4*>(np + 3));
-      ray.tmax = best;
-      float a0, a1, b0, b1;
-      const bool h0 = clip_box(ray, p.x, p.y, p.z, p.w, q.x, q.y, a0, a1);
-      const bool h1 = (e.y != kNodeNone) && clip_box(ray, q.z, q.w, c.x, c.y, c.z, c.w, b0, b1);
+      float a0, b0;
+      const bool h0 = clip_box_robust(ray, best, p.x, p.y, p.z, p.w, q.x, q.y, a0);
+      const bool h1 = (e.y != kNodeNone) && clip_box_robust(ray, best, q.z, q.w, c.x, c.y, c.z, c.w, b0);
       // leaves are tested at once (they may shrink best before the subtree is chosen)
       for (int s = 0; s < 2; ++s) {
         const bool hs = s == 0 ? h0 : h1;
@@ -90,8 +122,9 @@ __global__ void __launch_bounds__(128) tri_trace_kernel(TriBlasArgs a) {
           }
         }
       }
-      const bool g0 = h0 && e.x >= 0 && a0 <= best;
-      const bool g1 = h1 && e.y >= 0 && b0 <= best;
+      const float reach = best + fabsf(best) * kRobustGrow;
+      const bool g0 = h0 && e.x >= 0 && a0 <= reach;
+      const bool g1 = h1 && e.y >= 0 && b0 <= reach;
       if (g0 && g1) {
         const bool first0 = a0 <= b0;
         if (sp < kTraverseStack) {
