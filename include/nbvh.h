@@ -395,6 +395,49 @@ nbvh_status nbvh_train_step(const nbvh_model_desc* desc, const nbvh_optim* opt, 
                             int32_t mode, int64_t batch, uint64_t seed, int64_t step, float lr, double* loss_out,
                             void* workspace, size_t ws_bytes, void* stream);
 
+/* Per-leaf statistics of training steps (Sec. 5.1 "Node error": a node's error
+ * is its training loss q times the probability p that a training ray hits
+ * it, p estimated by the fraction of training rays that hit it). Device
+ * arrays of n_leaves entries that the steps accumulate into (callers zero
+ * them): hits = rays whose first leaf (the leaf they would train) is the
+ * leaf; trained = those that trained it; loss = the sum of their combined
+ * loss terms (per-ray, before the mean over the batch). */
+typedef struct {
+  uint32_t* hits;
+  uint32_t* trained;
+  double* loss;
+} nbvh_leaf_stats;
+
+/* Device. nbvh_train_step with error-driven ray selection (Sec. 5.2 "Ray
+ * distribution": a ray trains the first leaf it meets only with that leaf's
+ * probability). leaf_prob: device [n_leaves] probabilities in [0, 1] or NULL
+ * (every ray trains); a ray with first leaf l trains iff u < leaf_prob[l],
+ * u from Philox4x32-10 keyed by seed (low, high word) with counter
+ * (ray, step-1 low, step-1 high, 3), top 24 bits * 2^-24. stats: host struct
+ * of device arrays accumulated as nbvh_leaf_stats describes, or NULL. The
+ * loss mean runs over the rays that train. */
+nbvh_status nbvh_train_step_weighted(const nbvh_model_desc* desc, const nbvh_optim* opt,
+                                     const nbvh_train_scene* scene, int32_t mode, int64_t batch, uint64_t seed,
+                                     int64_t step, float lr, const float* leaf_prob, const nbvh_leaf_stats* stats,
+                                     double* loss_out, void* workspace, size_t ws_bytes, void* stream);
+
+/* Host. N-BVH from a cut through a base BVH (Sec. 5.1 "Base-BVH cut
+ * optimization": the nodes along the cut become the N-BVH leaves, inflated
+ * as in nbvh_build_leaves). base_nodes/base_leaf_range: a base BVH in the
+ * format of nbvh_build_tri_blas (host). cut: n_cut base references, ref in
+ * [0, n_base_nodes) = the subtree of that base node (0 = the whole tree),
+ * ref < 0 = base leaf ~ref; every root-to-leaf path must cross exactly one.
+ * Outputs (host): nodes (node_cap >= max(1, n_cut - 1)), *out_n_nodes;
+ * leaf_range [n_cut][2] into the base BVH's triangle order; leaf_box
+ * [n_cut][6], the reference's box pushed out by inflate_rel * extent and
+ * rounded outward; leaf_ref [n_cut], the reference of each N-BVH leaf. Leaves
+ * are numbered depth-first, first child first. Errors: INVALID_ARG for an
+ * invalid base tree or cut. */
+nbvh_status nbvh_build_cut(const nbvh_node* base_nodes, int32_t n_base_nodes, const int32_t* base_leaf_range,
+                           int32_t n_base_leaves, const int32_t* cut, int32_t n_cut, double inflate_rel,
+                           float extent, nbvh_node* nodes, int32_t node_cap, int32_t* out_n_nodes,
+                           int32_t* leaf_range, float* leaf_box, int32_t* leaf_ref);
+
 /* Size of the library's built-in query scratch (32 MiB), see
  * nbvh_query_rays_static. */
 #define NBVH_STATIC_SCRATCH_BYTES 33554432

@@ -912,3 +912,118 @@ def hybrid_trace(rays: dict, instances):
         out["inst"][better] = k
     out["answers"] = answers
     return out
+
+
+# ============================================================================
+# Error-driven construction (Sec. 5.1 "Base-BVH cut optimization", "Node
+# error"; Sec. 5.2 "Ray distribution")
+# ============================================================================
+
+def training_selection(leaf, prob, seed: int, step: int):
+    """Which rays train their first leaf: ray i with first leaf l >= 0 trains
+    iff u < prob[l], u = top 24 bits of the first word of Philox4x32-10 with
+    counter (i, step low, step high, 3) keyed by the seed's words, * 2^-24."""
+    leaf = np.asarray(leaf, np.int64)
+    i = np.arange(len(leaf), dtype=np.uint64)
+    st = np.uint64(step)
+    r = philox4x32_10([i & np.uint64(0xFFFFFFFF), np.full_like(i, st & np.uint64(0xFFFFFFFF)),
+                       np.full_like(i, st >> np.uint64(32)), np.full_like(i, 3)], _keys(seed))
+    u = u24(r[0])
+    p = np.asarray(prob, np.float32).astype(F64)
+    keep = leaf >= 0
+    keep[keep] = u[keep] < p[leaf[keep]]
+    return keep
+
+
+def leaf_statistics(first_leaf, trains, loss_terms, n_leaves: int):
+    """Per leaf: rays whose first leaf it is, the rays among them that train
+    it, and the sum of their loss terms (Sec. 5.1: error = loss q x hit
+    probability p, p estimated from the training rays)."""
+    first_leaf = np.asarray(first_leaf, np.int64)
+    hits = np.zeros(n_leaves, np.int64)
+    trained = np.zeros(n_leaves, np.int64)
+    loss = np.zeros(n_leaves)
+    for i, l in enumerate(first_leaf):
+        if l < 0:
+            continue
+        hits[l] += 1
+        if trains[i]:
+            trained[l] += 1
+            loss[l] += float(loss_terms[i])
+    return hits, trained, loss
+
+
+def node_rank(hits, trained, loss, n_rays: int):
+    """q = mean loss of a leaf's trained rays, p = hits / n_rays, ranking
+    r = 2 ln q + ln p (Sec. 5.1); training probability max(exp(r - r_max),
+    0.005) (Sec. 5.2, read in the linear domain of the ranking). A leaf with
+    no hit ranks -inf; a hit leaf without trained rays takes the mean q of
+    the trained leaves."""
+    n = len(hits)
+    q = np.zeros(n)
+    have = [i for i in range(n) if trained[i] > 0]
+    qm = sum(loss[i] / trained[i] for i in have) / len(have) if have else 1.0
+    for i in range(n):
+        q[i] = loss[i] / trained[i] if trained[i] > 0 else qm
+    p = np.array([hits[i] / max(1, n_rays) for i in range(n)], F64)
+    r = np.array([2.0 * math.log(q[i]) + math.log(p[i]) if hits[i] > 0 and q[i] > 0 else -math.inf
+                  for i in range(n)])
+    finite = [x for x in r if math.isfinite(x)]
+    rmax = max(finite) if finite else 0.0
+    prob = np.array([max(math.exp(x - rmax), 0.005) if math.isfinite(x) else 0.005 for x in r])
+    return q, p, r, prob
+
+
+def split_cut(refs, r, k: int, children):
+    """Replace the k splittable leaves of largest r (ties: lower leaf index)
+    by their children; children(ref) lists a reference's children, empty for
+    a base leaf. Leaf order is kept, children in their order."""
+    cand = sorted([i for i in range(len(refs)) if children(refs[i]) and math.isfinite(r[i])],
+                  key=lambda i: (-r[i], i))[:k]
+    out = []
+    for i, ref in enumerate(refs):
+        out += list(children(ref)) if i in cand else [ref]
+    return out
+
+
+def cut_leaves(tris, base_nodes, base_leaf_range, base_tri_perm, cut, inflate_rel: float, extent: float):
+    """Leaves of the N-BVH of a cut, by brute force over the base tree: walk
+    from the root (first child first); a cut reference becomes a leaf whose
+    triangles are those of every base leaf below it and whose box is their
+    AABB pushed out by inflate_rel * extent (FP64) and rounded outward to
+    float32. base_nodes: records with child0, child1 (leaf = ~index, none =
+    0x7fffffff). Returns (refs in leaf order, triangle index sets, lo, hi)."""
+    cut = set(int(c) for c in cut)
+
+    def leaves_below(ref):
+        if ref < 0:
+            return [~ref]
+        nd = base_nodes[ref]
+        out = []
+        for c in (int(nd["child0"]), int(nd["child1"])):
+            if c != 0x7fffffff:
+                out += leaves_below(c)
+        return out
+
+    refs, sets, lo, hi = [], [], [], []
+    pad = inflate_rel * float(extent)
+
+    def walk(ref):
+        if ref in cut:
+            bl = leaves_below(ref)
+            idx = np.concatenate([base_tri_perm[base_leaf_range[b][0]:base_leaf_range[b][1]] for b in bl])
+            v = np.asarray(tris, F64)[idx].reshape(-1, 3)
+            refs.append(ref)
+            sets.append(np.sort(idx))
+            lo.append(_round_down_f32(v.min(0) - pad))
+            hi.append(_round_up_f32(v.max(0) + pad))
+            return
+        if ref < 0:
+            raise ValueError("a base leaf below no cut reference")
+        nd = base_nodes[ref]
+        for c in (int(nd["child0"]), int(nd["child1"])):
+            if c != 0x7fffffff:
+                walk(c)
+
+    walk(0)
+    return refs, sets, np.array(lo), np.array(hi)

@@ -506,3 +506,199 @@ extern "C" nbvh_status nbvh_build_tri_blas(const float* tris, int64_t n_tris, in
   *out_n_leaves = nl;
   return NBVH_OK;
 }
+
+// ---------------------------------------------------------------------------
+// N-BVH from a cut through a base BVH (Sec. 5.1 "Base-BVH cut optimization":
+// the nodes along the cut become the N-BVH's leaves). The base BVH is in the
+// nbvh_node format of nbvh_build_tri_blas; a cut entry is a base reference:
+// 0 <= ref < n_base_nodes names the subtree of base node ref (0 = the whole
+// tree), ref < 0 names base leaf ~ref. Every root-to-leaf path of the base
+// tree must cross exactly one entry.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct BaseTree {
+  const nbvh_node* nodes;
+  int32_t n_nodes;
+  const int32_t* leaf_range;
+  int32_t n_leaves;
+  std::vector<int> node_parent, node_slot, leaf_parent, leaf_slot;
+
+  bool init() {
+    node_parent.assign(size_t(n_nodes), -1);
+    node_slot.assign(size_t(n_nodes), -1);
+    leaf_parent.assign(size_t(n_leaves), -1);
+    leaf_slot.assign(size_t(n_leaves), -1);
+    for (int i = 0; i < n_nodes; ++i) {
+      const int32_t ch[2] = {nodes[i].child0, nodes[i].child1};
+      for (int s = 0; s < 2; ++s) {
+        const int32_t c = ch[s];
+        if (c == 0x7fffffff) continue;
+        if (c >= 0) {
+          if (c >= n_nodes || c == 0 || node_parent[c] >= 0) return false;
+          node_parent[c] = i;
+          node_slot[c] = s;
+        } else {
+          const int32_t l = ~c;
+          if (l >= n_leaves || leaf_parent[l] >= 0) return false;
+          leaf_parent[l] = i;
+          leaf_slot[l] = s;
+        }
+      }
+    }
+    return true;
+  }
+  // box of a reference: a subtree's box is the union of its node's child boxes
+  void box(int32_t ref, float* lo, float* hi) const {
+    if (ref >= 0) {
+      const nbvh_node& nd = nodes[ref];
+      const bool two = nd.child1 != 0x7fffffff;
+      for (int a = 0; a < 3; ++a) {
+        lo[a] = two ? std::min(nd.lo0[a], nd.lo1[a]) : nd.lo0[a];
+        hi[a] = two ? std::max(nd.hi0[a], nd.hi1[a]) : nd.hi0[a];
+      }
+    } else {
+      const int32_t l = ~ref;
+      const nbvh_node& p = nodes[leaf_parent[l]];
+      const float* slo = leaf_slot[l] == 0 ? p.lo0 : p.lo1;
+      const float* shi = leaf_slot[l] == 0 ? p.hi0 : p.hi1;
+      for (int a = 0; a < 3; ++a) {
+        lo[a] = slo[a];
+        hi[a] = shi[a];
+      }
+    }
+  }
+  // triangle range of a reference (leaves of a subtree are consecutive)
+  void range(int32_t ref, int32_t& b, int32_t& e) const {
+    if (ref < 0) {
+      b = leaf_range[2 * (~ref)];
+      e = leaf_range[2 * (~ref) + 1];
+      return;
+    }
+    int32_t first = ref, last = ref;
+    while (first >= 0) first = nodes[first].child0;
+    for (;;) {
+      const nbvh_node& nd = nodes[last];
+      const int32_t c = nd.child1 == 0x7fffffff ? nd.child0 : nd.child1;
+      if (c < 0) {
+        last = c;
+        break;
+      }
+      last = c;
+    }
+    b = leaf_range[2 * (~first)];
+    e = leaf_range[2 * (~last) + 1];
+  }
+};
+
+}  // namespace
+
+extern "C" nbvh_status nbvh_build_cut(const nbvh_node* base_nodes, int32_t n_base_nodes,
+                                      const int32_t* base_leaf_range, int32_t n_base_leaves, const int32_t* cut,
+                                      int32_t n_cut, double inflate_rel, float extent, nbvh_node* nodes,
+                                      int32_t node_cap, int32_t* out_n_nodes, int32_t* leaf_range, float* leaf_box,
+                                      int32_t* leaf_ref) {
+  if (!base_nodes || n_base_nodes < 1 || !base_leaf_range || n_base_leaves < 1 || !cut || n_cut < 1 || !nodes ||
+      !out_n_nodes || !leaf_range || !leaf_box || !leaf_ref || node_cap < std::max(1, n_cut - 1) ||
+      !(inflate_rel >= 0.0) || !std::isfinite(inflate_rel) || !(extent > 0.0f))
+    return NBVH_ERR_INVALID_ARG;
+  BaseTree bt{base_nodes, n_base_nodes, base_leaf_range, n_base_leaves, {}, {}, {}, {}};
+  if (!bt.init()) return NBVH_ERR_INVALID_ARG;
+  // mark the cut entries
+  std::vector<char> node_cut(size_t(n_base_nodes), 0), leaf_cut(size_t(n_base_leaves), 0);
+  for (int i = 0; i < n_cut; ++i) {
+    const int32_t r = cut[i];
+    if (r >= 0) {
+      if (r >= n_base_nodes || node_cut[r]) return NBVH_ERR_INVALID_ARG;
+      node_cut[r] = 1;
+    } else {
+      if (~r >= n_base_leaves || leaf_cut[~r]) return NBVH_ERR_INVALID_ARG;
+      leaf_cut[~r] = 1;
+    }
+  }
+  // depth-first from the root: references above the cut become internal
+  // N-BVH nodes, cut references leaves (numbered in this order)
+  const double pad = inflate_rel * double(extent);
+  int32_t n_leaf = 0, n_int = 0;
+  struct Item {
+    int32_t ref, parent, slot;
+  };
+  std::vector<Item> stack{{0, -1, 0}};
+  int32_t visited_cut = 0;
+  while (!stack.empty()) {
+    const Item it = stack.back();
+    stack.pop_back();
+    const bool is_cut = it.ref >= 0 ? node_cut[it.ref] != 0 : leaf_cut[~it.ref] != 0;
+    int32_t out_ref;
+    float lo[3], hi[3];
+    bt.box(it.ref, lo, hi);
+    if (is_cut) {
+      const int32_t lf = n_leaf++;
+      if (lf >= n_cut) return NBVH_ERR_INVALID_ARG;
+      int32_t b, e;
+      bt.range(it.ref, b, e);
+      leaf_range[2 * lf] = b;
+      leaf_range[2 * lf + 1] = e;
+      leaf_ref[lf] = it.ref;
+      for (int a = 0; a < 3; ++a) {
+        leaf_box[6 * lf + a] = round_down(double(lo[a]) - pad);
+        leaf_box[6 * lf + 3 + a] = round_up(double(hi[a]) + pad);
+      }
+      ++visited_cut;
+      out_ref = ~lf;
+    } else {
+      if (it.ref < 0) return NBVH_ERR_INVALID_ARG;  // a base leaf below no cut entry
+      const int32_t id = n_int++;
+      if (id >= node_cap) return NBVH_ERR_INVALID_ARG;
+      std::memset(&nodes[id], 0, sizeof(nbvh_node));
+      nodes[id].child1 = 0x7fffffff;
+      const nbvh_node& bn = base_nodes[it.ref];
+      if (bn.child1 != 0x7fffffff) stack.push_back({bn.child1, id, 1});
+      stack.push_back({bn.child0, id, 0});
+      out_ref = id;
+    }
+    if (it.parent >= 0) {
+      nbvh_node& p = nodes[it.parent];
+      float* plo = it.slot == 0 ? p.lo0 : p.lo1;
+      float* phi = it.slot == 0 ? p.hi0 : p.hi1;
+      if (is_cut) {
+        for (int a = 0; a < 3; ++a) {
+          plo[a] = leaf_box[6 * (~out_ref) + a];
+          phi[a] = leaf_box[6 * (~out_ref) + 3 + a];
+        }
+      }
+      if (it.slot == 0) p.child0 = out_ref;
+      else p.child1 = out_ref;
+    }
+  }
+  if (visited_cut != n_cut) return NBVH_ERR_INVALID_ARG;  // some entries lie below others
+  if (n_int == 0) {  // the cut is the root alone: one leaf
+    std::memset(&nodes[0], 0, sizeof(nbvh_node));
+    for (int a = 0; a < 3; ++a) {
+      nodes[0].lo0[a] = leaf_box[a];
+      nodes[0].hi0[a] = leaf_box[3 + a];
+    }
+    nodes[0].child0 = ~0;
+    nodes[0].child1 = 0x7fffffff;
+    n_int = 1;
+  } else {
+    // an internal node's box in its parent: the union of its children's boxes
+    for (int id = n_int - 1; id >= 0; --id) {
+      nbvh_node& nd = nodes[id];
+      for (int s = 0; s < 2; ++s) {
+        const int32_t c = s == 0 ? nd.child0 : nd.child1;
+        if (c < 0 || c == 0x7fffffff) continue;
+        const nbvh_node& ch = nodes[c];
+        float* dlo = s == 0 ? nd.lo0 : nd.lo1;
+        float* dhi = s == 0 ? nd.hi0 : nd.hi1;
+        const bool two = ch.child1 != 0x7fffffff;
+        for (int a = 0; a < 3; ++a) {
+          dlo[a] = two ? std::min(ch.lo0[a], ch.lo1[a]) : ch.lo0[a];
+          dhi[a] = two ? std::max(ch.hi0[a], ch.hi1[a]) : ch.hi0[a];
+        }
+      }
+    }
+  }
+  *out_n_nodes = n_int;
+  return NBVH_OK;
+}

@@ -1371,9 +1371,19 @@ extern "C" nbvh_status nbvh_train_step(const nbvh_model_desc* desc, const nbvh_o
                                        const nbvh_train_scene* scene, int32_t mode, int64_t batch, uint64_t seed,
                                        int64_t step, float lr, double* loss_out, void* workspace, size_t ws_bytes,
                                        void* stream) {
+  return nbvh_train_step_weighted(desc, opt, scene, mode, batch, seed, step, lr, nullptr, nullptr, loss_out,
+                                  workspace, ws_bytes, stream);
+}
+
+extern "C" nbvh_status nbvh_train_step_weighted(const nbvh_model_desc* desc, const nbvh_optim* opt,
+                                                const nbvh_train_scene* scene, int32_t mode, int64_t batch,
+                                                uint64_t seed, int64_t step, float lr, const float* leaf_prob,
+                                                const nbvh_leaf_stats* stats, double* loss_out, void* workspace,
+                                                size_t ws_bytes, void* stream) {
   if (!nbvh_host::desc_valid(desc) || !opt || !scene_valid(scene) || batch < 1 || step < 1 || !workspace ||
       (reinterpret_cast<uintptr_t>(workspace) & 255) || batch > (int64_t(1) << 31) - 1)
     return NBVH_ERR_INVALID_ARG;
+  if (stats && (!stats->hits || !stats->trained || !stats->loss)) return NBVH_ERR_INVALID_ARG;
   TrainWs w = carve_train(workspace, desc, batch, scene->n_leaves);
   if (ws_bytes < w.bytes) return NBVH_ERR_WORKSPACE_TOO_SMALL;
   cudaStream_t s = as_stream(stream);
@@ -1382,6 +1392,14 @@ extern "C" nbvh_status nbvh_train_step(const nbvh_model_desc* desc, const nbvh_o
   nbvh_rays_out ro{w.rays[0], w.rays[1], w.rays[2], w.rays[3], w.rays[4], w.rays[5], w.rays[6], w.rays[7], batch};
   nbvh_status st = nbvh_train_rays(mode, seed, step - 1, scene, ro, w.leaf, w.t0, w.t1, w.n_valid, stream);
   if (st != NBVH_OK) return st;
+  if (leaf_prob || stats) {  // first-leaf hit counts; trained with the leaf's probability
+    const uint64_t st0 = uint64_t(step - 1);
+    leaf_select_kernel<<<unsigned((batch + 255) / 256), 256, 0, s>>>(
+        w.leaf, batch, uint32_t(seed & 0xffffffffu), uint32_t(seed >> 32), uint32_t(st0 & 0xffffffffu),
+        uint32_t(st0 >> 32), leaf_prob, stats ? stats->hits : nullptr, w.n_valid);
+    count_launches(1);
+    if (cudaGetLastError() != cudaSuccess) return NBVH_ERR_CUDA;
+  }
   nbvh_rays ri{w.rays[0], w.rays[1], w.rays[2], w.rays[3], w.rays[4], w.rays[5], w.rays[6], w.rays[7], batch};
   nbvh_labels lab{w.hit, w.depth, w.nx, w.ny, w.nz};
   // group the rays by trained leaf: labels share a leaf's triangles per warp,
@@ -1401,6 +1419,12 @@ extern "C" nbvh_status nbvh_train_step(const nbvh_model_desc* desc, const nbvh_o
                           nullptr, loss_out ? loss_out : w.loss, workspace, ws_bytes, stream, order,
                           scene->n_leaves);
   if (st != NBVH_OK) return st;
+  if (stats) {
+    leaf_loss_kernel<<<unsigned((batch + 255) / 256), 256, 0, s>>>(w.buf.loss_seg, batch, w.leaf, order,
+                                                                    stats->trained, stats->loss);
+    count_launches(1);
+    if (cudaGetLastError() != cudaSuccess) return NBVH_ERR_CUDA;
+  }
   st = backward_impl(desc, table, opt->mlp, ri, w.leaf, w.t0, w.t1, nullptr, opt->grad_table, opt->grad_mlp,
                      workspace, ws_bytes, stream, order, scene->n_leaves);
   if (st != NBVH_OK) return st;

@@ -712,3 +712,47 @@ __global__ void leaf_scatter_kernel(const int32_t* __restrict__ leaf, int64_t n,
 }
 
 }  // namespace nbvh
+
+namespace nbvh {
+
+// ---------------------------------------------------------------------------
+// Error-driven training (Sec. 5.1 "Node error", Sec. 5.2 "Ray distribution"):
+// each ray's first leaf is counted as hit; with leaf probabilities the ray
+// trains that leaf only with its probability (uniform u from Philox4x32-10,
+// key = seed words, counter (ray, step low, step high, 3), u = top 24 bits
+// * 2^-24, trained iff u < prob[leaf]); a rejected ray trains nothing.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) leaf_select_kernel(int32_t* __restrict__ leaf, int64_t n, uint32_t k0,
+                                                          uint32_t k1, uint32_t step_lo, uint32_t step_hi,
+                                                          const float* __restrict__ prob, uint32_t* hits,
+                                                          int32_t* n_valid) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int lf = leaf[i];
+  if (lf < 0) return;
+  if (hits) atomicAdd(hits + lf, 1u);
+  if (prob) {
+    const uint4 r = philox4x32_10(make_uint4(uint32_t(i), step_lo, step_hi, 3u), k0, k1);
+    if (!(u24(r.x) < __ldg(prob + lf))) {
+      leaf[i] = -1;
+      atomicSub(n_valid, 1);
+    }
+  }
+}
+
+// Per-leaf sums of the trained rays' loss terms (entry i of the forward's
+// term buffer belongs to ray order[i], or to ray i without an order).
+__global__ void __launch_bounds__(256) leaf_loss_kernel(const float* __restrict__ term, int64_t n,
+                                                        const int32_t* __restrict__ leaf,
+                                                        const int32_t* __restrict__ order, uint32_t* trained,
+                                                        double* loss) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t r = order ? int64_t(order[i]) : i;
+  const int lf = leaf[r];
+  if (lf < 0) return;
+  atomicAdd(trained + lf, 1u);
+  atomicAdd(loss + lf, double(term[i]));
+}
+
+}  // namespace nbvh

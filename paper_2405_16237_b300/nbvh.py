@@ -7,6 +7,7 @@ the library is missing: there is no fallback path.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 from ctypes import POINTER, c_double, c_float, c_int32, c_int64, c_size_t, c_uint8, c_void_p
 
@@ -79,6 +80,10 @@ class Optim(ctypes.Structure):
 TRAIN_PROBED_MIX, TRAIN_PAPER = 0, 1
 
 
+class LeafStats(ctypes.Structure):
+    _fields_ = [("hits", c_void_p), ("trained", c_void_p), ("loss", c_void_p)]
+
+
 class TuneResult(ctypes.Structure):
     _fields_ = [("schedule", c_int32), ("patience_cycles", c_int64), ("traverse_block", c_int32), ("ms", c_float)]
 
@@ -141,6 +146,11 @@ _SIGS = {
                             c_void_p]),
     "nbvh_train_step": (c_int32, [POINTER(ModelDesc), POINTER(Optim), POINTER(TrainScene), c_int32, c_int64,
                                   ctypes.c_uint64, c_int64, c_float, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "nbvh_train_step_weighted": (c_int32, [POINTER(ModelDesc), POINTER(Optim), POINTER(TrainScene), c_int32,
+                                           c_int64, ctypes.c_uint64, c_int64, c_float, c_void_p, c_void_p, c_void_p,
+                                           c_void_p, c_size_t, c_void_p]),
+    "nbvh_build_cut": (c_int32, [c_void_p, c_int32, c_void_p, c_int32, c_void_p, c_int32, c_double, c_float,
+                                 c_void_p, c_int32, POINTER(c_int32), c_void_p, c_void_p, c_void_p]),
     "nbvh_graph_begin": (c_int32, [c_void_p]),
     "nbvh_graph_end": (c_int32, [c_void_p, POINTER(c_void_p)]),
     "nbvh_graph_launch": (c_int32, [c_void_p, c_void_p]),
@@ -786,3 +796,150 @@ def probe_l2_gather(n_entries: int = 1 << 24) -> float:
     _check(lib().nbvh_probe_l2_gather(_ptr(tab), n_entries, _ptr(sink), ctypes.byref(g), _stream()),
            "probe_l2_gather")
     return g.value
+
+
+# ---------------------------------------------------------------- error-driven cut (Sec. 5.1)
+def build_cut(base: dict, cut, inflate_rel: float, info: dict) -> dict:
+    """nbvh_build_cut: the N-BVH whose leaves are the base-BVH references in
+    ``cut`` (the base BVH from build_tri_blas). Returns a leaves dict in the
+    format of build_leaves (triangle order: the base BVH's) plus leaf_ref."""
+    cut = np.ascontiguousarray(cut, np.int32)
+    n_cut = len(cut)
+    cap = max(1, n_cut - 1)
+    nodes = np.zeros(cap * 64, np.uint8)
+    n_nodes = c_int32()
+    rng = np.zeros(2 * n_cut, np.int32)
+    box = np.zeros((n_cut, 6), np.float32)
+    ref = np.zeros(n_cut, np.int32)
+    base_nodes = np.ascontiguousarray(base["nodes"])
+    base_rng = np.ascontiguousarray(base["leaf_range"], np.int32)
+    _check(lib().nbvh_build_cut(base_nodes.ctypes.data_as(c_void_p), base["n_nodes"], base_rng.ctypes.data_as(c_void_p),
+                                base["n_leaves"], cut.ctypes.data_as(c_void_p), n_cut, float(inflate_rel),
+                                float(info["extent"]), nodes.ctypes.data_as(c_void_p), cap, ctypes.byref(n_nodes),
+                                rng.ctypes.data_as(c_void_p), box.ctypes.data_as(c_void_p),
+                                ref.ctypes.data_as(c_void_p)), "build_cut")
+    return {"nodes": nodes[:n_nodes.value * 64].copy(), "n_nodes": n_nodes.value, "tri_perm": base["tri_perm"],
+            "leaf_range": rng.reshape(-1, 2), "leaf_lo": box[:, :3].copy(), "leaf_hi": box[:, 3:].copy(),
+            "leaf_ref": ref, "info": info}
+
+
+def base_children(base: dict, ref: int):
+    """Child references of an internal base reference (ref >= 0)."""
+    nd = node_array({"nodes": base["nodes"]})[ref]
+    out = [int(nd["child0"])]
+    if int(nd["child1"]) != 0x7fffffff:
+        out.append(int(nd["child1"]))
+    return out
+
+
+def train_step_weighted(desc: ModelDesc, opt, scene, mode: int, batch: int, seed: int, step: int, lr: float,
+                        workspace, leaf_prob=None, stats=None, loss_out=None):
+    """nbvh_train_step_weighted. stats: dict of device tensors hits (int32),
+    trained (int32), loss (float64), n_leaves entries each, accumulated."""
+    base = aligned_ptr(workspace)
+    avail = workspace.numel() - (base - workspace.data_ptr())
+    st = None
+    if stats is not None:
+        st = LeafStats()
+        st.hits, st.trained, st.loss = (stats["hits"].data_ptr(), stats["trained"].data_ptr(),
+                                        stats["loss"].data_ptr())
+    _check(lib().nbvh_train_step_weighted(ctypes.byref(desc), ctypes.byref(opt.struct), ctypes.byref(scene.struct),
+                                          mode, batch, ctypes.c_uint64(seed), step, lr, _ptr(leaf_prob),
+                                          ctypes.byref(st) if st is not None else None, _ptr(loss_out),
+                                          c_void_p(base), avail, _stream()), "train_step_weighted")
+
+
+def node_rank(hits, trained, loss, n_rays):
+    """Sec. 5.1 "Node error": q = mean training loss of the leaf, p = fraction of
+    the training rays that hit it, ranking r = 2 log q + log p; the training
+    probability of Sec. 5.2, read as max(exp(r - r_max), 0.005) (the ranking's
+    linear-domain ratio q^2 p / max q^2 p). A leaf no ray hit gets r = -inf; a
+    leaf hit but never trained takes the mean q of the trained ones."""
+    hits = np.asarray(hits, np.float64)
+    trained = np.asarray(trained, np.float64)
+    loss = np.asarray(loss, np.float64)
+    q = np.where(trained > 0, loss / np.maximum(trained, 1.0), np.nan)
+    qm = np.nanmean(q) if np.any(trained > 0) else 1.0
+    q = np.where(np.isnan(q), qm, q)
+    p = hits / max(1.0, float(n_rays))
+    with np.errstate(divide="ignore"):
+        r = np.where((hits > 0) & (q > 0), 2.0 * np.log(np.maximum(q, 1e-300)) + np.log(np.maximum(p, 1e-300)),
+                     -np.inf)
+    rmax = np.max(r) if np.any(np.isfinite(r)) else 0.0
+    prob = np.where(np.isfinite(r), np.maximum(np.exp(r - rmax), 0.005), 0.005)
+    return q, p, r, prob
+
+
+def optimize_cut(tris, desc: ModelDesc, opt, n_target: int, *, base_max_leaf: int = 16, iters: int = 50,
+                 splits: int = 4, factor: float = 1.5, final_iters: int = 200, batch: int = 1 << 16,
+                 seed: int = 240516237, lr: float = 1e-2, mode: int = TRAIN_PROBED_MIX, inflate_rel: float = 1e-4,
+                 step0: int = 1, max_rounds: int = 1000):
+    """Error-driven cut optimization (Sec. 5.1): start with the root of the
+    base BVH (binned SAH over the triangles); train ``iters`` steps on the
+    current cut's N-BVH with error-weighted ray selection; split the
+    ``splits`` leaves of largest ranking r into their base children; grow
+    both counts by ``factor``; stop at ``n_target`` leaves and train
+    ``final_iters`` more steps. Returns (leaves dict of the final cut, the
+    DeviceScene, per-round history, next step number)."""
+    torch = _torch()
+    base = build_tri_blas(tris, base_max_leaf)
+    info = build_leaves(tris, 1, inflate_rel)["info"]
+    cut = [0]
+    prob = None
+    step = step0
+    history = []
+    ws = None
+    ws_leaves = -1
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+
+    def run(cut, prob, n_iters):
+        nonlocal step, ws, ws_leaves
+        lv = build_cut(base, cut, inflate_rel, info)
+        scene = DeviceScene(tris, lv)
+        if ws is None or ws_leaves < len(cut):
+            ws = new_workspace(train_workspace_size(desc, batch, max(len(cut), n_target)))
+            ws_leaves = max(len(cut), n_target)
+        n = len(cut)
+        stats = {"hits": torch.zeros(n, dtype=torch.int32, device="cuda"),
+                 "trained": torch.zeros(n, dtype=torch.int32, device="cuda"),
+                 "loss": torch.zeros(n, dtype=torch.float64, device="cuda")}
+        pdev = torch.as_tensor(np.asarray(prob, np.float32)).cuda() if prob is not None else None
+        for _ in range(n_iters):
+            train_step_weighted(desc, opt, scene, mode, batch, seed, step, lr, ws, leaf_prob=pdev, stats=stats,
+                                loss_out=loss)
+            step += 1
+        h = stats["hits"].cpu().numpy()
+        t = stats["trained"].cpu().numpy()
+        l = stats["loss"].cpu().numpy()
+        return lv, scene, h, t, l
+
+    rounds = 0
+    while len(cut) < n_target and rounds < max_rounds:
+        rounds += 1
+        lv, scene, h, t, l = run(cut, prob, iters)
+        q, p, r, pr = node_rank(h, t, l, batch * iters)
+        history.append({"leaves": len(cut), "iters": iters, "loss": float(loss.item()),
+                        "mean_q": float(np.sum(l) / max(1, np.sum(t)))})
+        refs = lv["leaf_ref"]
+        cand = [i for i in range(len(refs)) if refs[i] >= 0 and np.isfinite(r[i])]
+        cand.sort(key=lambda i: (-r[i], i))
+        k = min(int(splits), n_target - len(cut), len(cand))
+        if k <= 0:
+            break
+        chosen = set(cand[:k])
+        new_cut, new_prob = [], []
+        for i, ref in enumerate(refs):
+            if i in chosen:
+                ch = base_children(base, int(ref))
+                new_cut += ch
+                new_prob += [1.0] * len(ch)
+            else:
+                new_cut.append(int(ref))
+                new_prob.append(float(pr[i]))
+        cut, prob = new_cut, new_prob
+        iters = int(math.ceil(iters * factor))
+        splits = int(math.ceil(splits * factor))
+    lv, scene, h, t, l = run(cut, prob, final_iters)
+    history.append({"leaves": len(cut), "iters": final_iters, "loss": float(loss.item()),
+                    "mean_q": float(np.sum(l) / max(1, np.sum(t))), "final": True})
+    return lv, scene, history, step

@@ -197,3 +197,76 @@ def test_schedule_and_tuner_arguments_checked_on_host():
                                  None, 0, ctypes.byref(n_all), None) == 1
     s, p = B.get_query_schedule()
     assert s in (0, 1) and p >= 0
+
+
+def _base(tris, max_leaf=8):
+    return B.build_tri_blas(tris, max_leaf)
+
+
+@pytest.mark.parametrize("depths", ["root", "leaves", "mixed"])
+def test_build_cut_matches_oracle(depths):
+    """nbvh_build_cut: leaves in depth-first order, each with the triangles of
+    every base leaf below its reference and their AABB pushed out and rounded
+    outward, exactly as the oracle's brute-force walk gives; the node tree's
+    child boxes nest their descendants' leaf boxes."""
+    tris = np.concatenate([W.ground_heightfield(10, amplitude=0.05), W.scene_icosphere(level=2, radius=0.3)])
+    base = _base(tris)
+    nodes = B.node_array({"nodes": base["nodes"]})
+    info = B.build_leaves(tris, 1)["info"]
+    if depths == "root":
+        cut = [0]
+    elif depths == "leaves":
+        cut = [~i for i in range(base["n_leaves"])]
+    else:
+        rng = np.random.default_rng(4)
+        cut, stack = [], [0]
+        while stack:  # random cut: stop or descend at each internal reference
+            ref = stack.pop()
+            if ref < 0 or rng.uniform() < 0.3:
+                cut.append(ref)
+                continue
+            nd = nodes[ref]
+            kids = [int(nd["child0"])] + ([int(nd["child1"])] if int(nd["child1"]) != 0x7fffffff else [])
+            stack += kids[::-1]
+    lv = B.build_cut(base, cut, 1e-4, info)
+    refs, sets, lo, hi = O.cut_leaves(tris, nodes, base["leaf_range"], base["tri_perm"], cut, 1e-4, info["extent"])
+    assert list(lv["leaf_ref"]) == refs
+    for i, st in enumerate(sets):
+        a, b = lv["leaf_range"][i]
+        assert np.array_equal(np.sort(base["tri_perm"][a:b]), st)
+    assert np.array_equal(lv["leaf_lo"], lo) and np.array_equal(lv["leaf_hi"], hi)
+    assert sum(len(st) for st in sets) == len(tris)
+    # tree consistency
+    nn = B.node_array(lv)
+    seen = []
+
+    def walk(i):
+        nd = nn[i]
+        boxes = []
+        for c, l, h in ((nd["child0"], nd["lo0"], nd["hi0"]), (nd["child1"], nd["lo1"], nd["hi1"])):
+            if c == 0x7fffffff:
+                continue
+            if c < 0:
+                seen.append(~c)
+                assert np.array_equal(l, lv["leaf_lo"][~c]) and np.array_equal(h, lv["leaf_hi"][~c])
+            else:
+                clo, chi = walk(c)
+                assert np.array_equal(l, clo) and np.array_equal(h, chi)
+            boxes.append((l, h))
+        return np.min([b[0] for b in boxes], 0), np.max([b[1] for b in boxes], 0)
+
+    walk(0)
+    assert sorted(seen) == list(range(len(cut)))
+
+
+def test_build_cut_rejects_invalid_cuts():
+    tris = W.ground_heightfield(6, amplitude=0.05)
+    base = _base(tris, 4)
+    info = B.build_leaves(tris, 1)["info"]
+    nd = B.node_array({"nodes": base["nodes"]})[0]
+    with pytest.raises(B.NBVHError):   # overlapping: the root and one of its children
+        B.build_cut(base, [0, int(nd["child0"])], 1e-4, info)
+    with pytest.raises(B.NBVHError):   # incomplete: one child only
+        B.build_cut(base, [int(nd["child0"])], 1e-4, info)
+    with pytest.raises(B.NBVHError):   # out of range
+        B.build_cut(base, [base["n_nodes"] + 5], 1e-4, info)

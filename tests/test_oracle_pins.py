@@ -646,3 +646,53 @@ def test_hybrid_trace_neural_instance_alone_is_its_query():
     assert np.array_equal(h["hit"], q["hit"]) and np.array_equal(h["t"], q["t"])
     assert np.array_equal(h["leaf"], q["leaf"])
     assert np.array_equal(h["inst"], np.where(q["hit"] > 0, 0, -1))
+
+
+# ---------------------------------------------------------------- error-driven construction
+def test_node_rank_worked_example():
+    """q, p, r = 2 ln q + ln p and the training probability
+    max(q^2 p / max q^2 p, 0.005), values derived by hand."""
+    hits = [10, 0, 5, 20]
+    trained = [5, 0, 5, 10]
+    loss = [1.0, 0.0, 2.0, 0.5]
+    q, p, r, prob = O.node_rank(hits, trained, loss, 100)
+    qm = (0.2 + 0.4 + 0.05) / 3.0
+    assert np.allclose(q, [0.2, qm, 0.4, 0.05], rtol=1e-15)
+    assert np.allclose(p, [0.1, 0.0, 0.05, 0.2], rtol=1e-15)
+    assert np.isinf(r[1]) and r[1] < 0
+    assert math.isclose(r[0], 2 * math.log(0.2) + math.log(0.1), rel_tol=1e-14)
+    # q^2 p: 0.004, -, 0.008, 0.0005 -> ratios 0.5, floor, 1, 0.0625
+    assert np.allclose(prob, [0.5, 0.005, 1.0, 0.0625], rtol=1e-12)
+
+
+def test_split_cut_replaces_highest_ranked_splittable_leaves():
+    kids = {0: [1, 2], 1: [3, -1], 2: [-2, -3], 3: [-4, -5]}
+    children = lambda ref: kids.get(ref, [])
+    # leaves: 1 (r=5), 2 (r=7), ~0 (r=9, a base leaf: not splittable)
+    assert O.split_cut([1, 2, -1], [5.0, 7.0, 9.0], 1, children) == [1, -2, -3, -1]
+    assert O.split_cut([1, 2, -1], [5.0, 7.0, 9.0], 2, children) == [3, -1, -2, -3, -1]
+    # ties go to the lower leaf index
+    assert O.split_cut([1, 2], [4.0, 4.0], 1, children) == [3, -1, 2]
+
+
+def test_training_selection_rates_and_extremes():
+    n = 200000
+    leaf = np.arange(n) % 4
+    leaf[::7] = -1
+    prob = np.array([0.0, 1.0, 0.25, 0.6], np.float32)
+    keep = O.training_selection(leaf, prob, seed=11, step=3)
+    assert not keep[leaf < 0].any()
+    assert not keep[leaf == 0].any() and keep[leaf == 1].all()
+    for l, pr in ((2, 0.25), (3, 0.6)):
+        frac = keep[leaf == l].mean()
+        assert abs(frac - pr) < 4 * math.sqrt(pr * (1 - pr) / np.sum(leaf == l))
+    # the selection is a function of (ray, step, seed)
+    assert np.array_equal(keep, O.training_selection(leaf, prob, seed=11, step=3))
+    assert not np.array_equal(keep, O.training_selection(leaf, prob, seed=11, step=4))
+
+
+def test_leaf_statistics_counts_by_hand():
+    hits, trained, loss = O.leaf_statistics([0, 1, 1, -1, 2, 1], [True, False, True, False, True, True],
+                                            [1.0, 9.0, 2.0, 5.0, 0.5, 3.0], 3)
+    assert list(hits) == [1, 3, 1] and list(trained) == [1, 2, 1]
+    assert np.allclose(loss, [1.0, 5.0, 0.5])
