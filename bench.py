@@ -53,6 +53,8 @@ def parse():
     p.add_argument("--hybrid-cpu-rays", type=int, default=128, help="oracle sample of the hybrid workload")
     p.add_argument("--uneven-steps", type=int, default=5,
                    help="timed queries of the uneven-segment workload (0: skip it)")
+    p.add_argument("--cut-steps", type=int, default=1700,
+                   help="training-step budget of the error-driven-cut comparison (0: skip it)")
     p.add_argument("--no-autotune", action="store_true",
                    help="keep the library's default query schedule (no autotuning before the timed region)")
     p.add_argument("--quick", action="store_true",
@@ -381,10 +383,14 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# the sources of the dominant kernel (eval_tc_kernel, its argument struct and device helpers)
+KERNEL_SOURCES = ("eval_tc.cuh", "eval_plain.cuh", "nbvh_internal.cuh")
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2405_16237_b300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in KERNEL_SOURCES:
         h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -531,6 +537,98 @@ def time_uneven(args, world):
                 "rays_with_segments": int(hit.sum()), "p99": float(np.percentile(cnt[hit], 99))},
             "segments_evaluated": int(segs), "autotuner": {"best": best, "candidates": table_all},
             "setup_s": setup_s, "l2": "flushed (256 MB write) between timed queries"}
+
+
+# ---------------------------------------------------------------------------- error-driven cut (NEXT-1)
+def time_cut(args, world):
+    """Error-driven cut optimization (Sec. 5.1) against the median-split N-BVH
+    with the same leaf count (2,048) and the same training budget (steps of
+    2^16 rays, the paper's ray distribution, FP16 tensor cores), on the
+    displaced icosphere. Both models answer 512x512 camera rays; the triangle
+    BLAS of the mesh gives the exact closest hits they are scored against."""
+    import torch
+    from paper_2405_16237_b300 import nbvh as B
+    from paper_2405_16237_b300 import workloads as W
+    spec = W.C1
+    cfg = spec.model
+    tris = W.scene_icosphere(level=8)
+    batch, seed, lr, n_leaves = 1 << 16, SEED + 50, 1e-2, spec.n_leaves
+    info = B.build_leaves(tris, 1)["info"]
+
+    def fresh():
+        desc = B.model_desc(cfg, B.FP16, B.FP16, info["centre"], info["extent"])
+        lay = B.level_layout(desc)
+        tab = torch.as_tensor(W.init_table(lay["total"], cfg.n_features, SEED + 51, 1e-4)).cuda()
+        mlp = torch.as_tensor(B.pack_mlp(W.init_mlp(cfg.mlp_dims(), SEED + 52))).cuda()
+        return desc, B.Optimizer(desc, tab, mlp, loss_scale=32768.0)
+
+    # error-driven: grows from the root; its rounds and final round use the budget
+    desc_e, opt_e = fresh()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lv_e, scene_e, hist, step_e = B.optimize_cut(tris, desc_e, opt_e, n_leaves, base_max_leaf=16, iters=10,
+                                                 splits=16, factor=1.4, final_iters=1, batch=batch, seed=seed,
+                                                 lr=lr, mode=B.TRAIN_PAPER)
+    used = step_e - 1
+    rest = max(0, args.cut_steps - used)
+    ws_e = B.new_workspace(B.train_workspace_size(desc_e, batch, n_leaves))
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    stats = {"hits": torch.zeros(n_leaves, dtype=torch.int32, device="cuda"),
+             "trained": torch.zeros(n_leaves, dtype=torch.int32, device="cuda"),
+             "loss": torch.zeros(n_leaves, dtype=torch.float64, device="cuda")}
+    pdev = None
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(rest):
+        B.train_step_weighted(desc_e, opt_e, scene_e, B.TRAIN_PAPER, batch, seed, step_e, lr, ws_e, leaf_prob=pdev,
+                              stats=stats, loss_out=loss)
+        step_e += 1
+        if i == 50:  # from here on, error-weighted selection from the measured statistics
+            h, t, l = (stats[k].cpu().numpy() for k in ("hits", "trained", "loss"))
+            pdev = torch.as_tensor(B.node_rank(h, t, l, batch * 51)[3].astype(np.float32)).cuda()
+    e1.record()
+    e1.synchronize()
+    weighted_ms = e0.elapsed_time(e1) / max(1, rest)
+    cut_s = time.perf_counter() - t0
+    # median split: the same number of steps
+    desc_m, opt_m = fresh()
+    lv_m = B.build_leaves(tris, n_leaves, spec.inflate_rel)
+    scene_m = B.DeviceScene(tris, lv_m)
+    ws_m = B.new_workspace(B.train_workspace_size(desc_m, batch, n_leaves))
+    for s in range(1, step_e):
+        B.train_step(desc_m, opt_m, scene_m, B.TRAIN_PAPER, batch, seed, s, lr, ws_m, loss_out=loss)
+    torch.cuda.synchronize()
+    # score both on camera rays against the exact closest triangle hits
+    rays_np = W.camera_rays(512, 512)
+    rays = B.to_device_rays(rays_np)
+    blas = B.build_tri_blas(tris, 4)
+    gt = B.trace_triangles(B.DeviceTriBlas(tris, blas), rays)
+
+    def score(desc, opt, lv):
+        nodes = torch.as_tensor(lv["nodes"]).cuda()
+        h = B.query_rays(desc, opt.table, opt.mlp, nodes, lv["n_nodes"], rays, 48)
+        g_hit = gt["hit"].bool()
+        m_hit = h["hit"].bool()
+        both = g_hit & m_hit
+        dt = (h["t"] - gt["t"]).abs()[both]
+        cosang = (h["nx"] * gt["nx"] + h["ny"] * gt["ny"] + h["nz"] * gt["nz"])[both].clamp(-1, 1)
+        return {"hit_agreement": float((g_hit == m_hit).float().mean()),
+                "depth_mean_abs": float(dt.mean()) if both.any() else None,
+                "depth_p95_abs": float(dt.quantile(0.95)) if both.any() else None,
+                "normal_mean_deg": float(torch.rad2deg(torch.arccos(cosang)).mean()) if both.any() else None}
+
+    out = {"workload": "icosphere-l8 2048 leaves, 2^16-ray steps, paper ray distribution, fp16",
+           "steps": step_e - 1, "rays_per_step": batch,
+           "error_driven": {"rounds": len(hist), "leaves": len(lv_e["leaf_ref"]), "construction_steps": used,
+                            "wall_s": cut_s, "weighted_step_ms": weighted_ms,
+                            "weighted_train_rays_s": batch / (weighted_ms * 1e-3) if rest else None,
+                            **score(desc_e, opt_e, lv_e)},
+           "median_split": score(desc_m, opt_m, lv_m),
+           "scored_on": "512x512 camera rays vs the closest triangle hit (triangle BLAS of the mesh)"}
+    if B.device_status() != 0:
+        raise RuntimeError("device status after the cut comparison")
+    return out
 
 
 # ---------------------------------------------------------------------------- hybrid scene (S9)
@@ -772,6 +870,11 @@ def run_gpu(args, world, rank, spec, tris, rays_np):
     B.set_query_schedule(1 if tune_best["schedule"] == "persistent" else 0, tune_best["patience_cycles"])
     B.set_traverse_block(tune_best["traverse_block"])
 
+    # error-driven cut vs median split (same leaves, same training budget)
+    cutcmp = time_cut(args, world) if args.cut_steps > 0 else None
+    B.set_query_schedule(1 if tune_best["schedule"] == "persistent" else 0, tune_best["patience_cycles"])
+    B.set_traverse_block(tune_best["traverse_block"])
+
     # the hybrid two-level scene (16 neural assets + 500,000 classical triangles)
     hybrid = time_hybrid(args, world) if args.hybrid_frames > 0 else None
 
@@ -819,6 +922,7 @@ def run_gpu(args, world, rank, spec, tris, rays_np):
                        "parallelism": f"replicas x{world}"},
             "train": train,
             "uneven": uneven,
+            "cut_optimization": cutcmp,
             "hybrid": hybrid,
             "fp32_plain": {"value": world * rays_step / (ms32 * 1e-3) / 1e6, "ms_per_step": ms32},
             "bf16_tc": {"value": world * rays_step / (msbf * 1e-3) / 1e6, "ms_per_step": msbf},
