@@ -203,7 +203,7 @@ __host__ __device__ inline TcLayout tc_layout(int K, int W, int n_hidden) {
   L.w1_off = take(uint32_t(W) * L.Kp * 2);
   L.wh_off = take(uint32_t(n_hidden - 1) * W * W * 2);
   L.wo_off = take(16u * W * 2);
-  L.row_off = take(kTcM * 24);
+  L.row_off = take(2 * kTcM * 24);  // two row buffers (the persistent query stages the next tile early)
   L.bar_off = take(64);
   L.total = off + 128;  // slack for base alignment
   return L;
@@ -340,6 +340,24 @@ __device__ __forceinline__ int pq_claim(const PQueue& q, unsigned long long* sta
   return -1;
 }
 
+// Non-blocking claim of a full tile for a CTA that is still evaluating one:
+// kTcM items if that many are queued now, else kPqNoTile (the CTA then claims
+// after retiring its tile, with pq_claim's waiting rules).
+constexpr int kPqNoTile = -2147483647 - 1;
+__device__ __forceinline__ int pq_try_claim(const PQueue& q, unsigned long long* start) {
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    const unsigned long long head = ld_relaxed_u64(q.head);
+    const unsigned long long res = ld_relaxed_u64(q.reserved);
+    if (res < head + kTcM) return kPqNoTile;
+    if (atomicCAS(q.head, head, head + kTcM) == head) {
+      atomicAdd(q.tiles, 1u);
+      *start = head;
+      return kTcM;
+    }
+  }
+  return kPqNoTile;
+}
+
 // Take the item at ring position p (its producer may still be writing it) and
 // leave the entry empty for position p + n; the acquire orders the ray's
 // record reads after it. Returns kPqEmpty if the wait gave up.
@@ -363,6 +381,36 @@ __device__ __forceinline__ bool pq_put(const PQueue& q, unsigned long long p, un
     __nanosleep(32);
   }
   return false;
+}
+
+// Stage row r of a claimed tile (item at ring position p): the ray, its
+// segment's interval, its best t and its next segment's t0. Returns the ray
+// (-1 if the wait gave up).
+__device__ __forceinline__ int pq_stage(const EvalArgs& a, unsigned long long p, int r, int* sray, float* st0,
+                                        float* st1, int* sslot, float* sbest, float* snext) {
+  const size_t nr = size_t(a.n_rays);
+  const unsigned long long it = pq_take(a.pq, p, nr);
+  int ray = -1;
+  float t0 = 0.0f, t1 = 0.0f;
+  if (it == kPqEmpty) {
+    set_status(NBVH_ERR_TIMEOUT);
+  } else {
+    ray = int(uint32_t(it));
+    const int sl = int(it >> 32);
+    sslot[r] = sl;
+    const size_t q = size_t(sl) * nr + size_t(ray);
+    t0 = a.seg_t0[q];
+    t1 = a.seg_t1[q];
+    sbest[r] = __ldcg(a.hits.t + ray);
+    // the slot after the last holds stale data: load it with the count, use it only below the count
+    const int cnt = a.seg_count[ray];
+    const float tn = sl + 1 < a.max_segs ? a.seg_t0[size_t(sl + 1) * nr + size_t(ray)] : 0.0f;
+    snext[r] = sl + 1 < cnt ? tn : __int_as_float(0x7f800000);
+  }
+  sray[r] = ray;
+  st0[r] = t0;
+  st1[r] = t1;
+  return ray;
 }
 
 // Resolve one evaluated segment (slot sl of ray `ray`) into the ray's record.
@@ -408,16 +456,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
   uint8_t* sW1 = smem + lay.w1_off;
   uint8_t* sWh = smem + lay.wh_off;
   uint8_t* sWo = smem + lay.wo_off;
-  int* sray = reinterpret_cast<int*>(smem + lay.row_off);
-  float* st0 = reinterpret_cast<float*>(sray + kTcM);
-  float* st1 = st0 + kTcM;
-  int* sslot = reinterpret_cast<int*>(st1 + kTcM);  // persistent query: the item's slot,
-  float* sbest = reinterpret_cast<float*>(sslot + kTcM);  // the ray's best t,
-  float* snext = sbest + kTcM;                            // its next segment's t0
+  // row buffer b: ray, t0, t1 and (persistent query) the item's slot, the
+  // ray's best t and its next segment's t0
+  int *sray, *sslot;
+  float *st0, *st1, *sbest, *snext;
+  auto bind_rows = [&](int b, int*& ry, float*& a0, float*& a1, int*& sl, float*& be, float*& nx) {
+    ry = reinterpret_cast<int*>(smem + lay.row_off + size_t(b) * kTcM * 24);
+    a0 = reinterpret_cast<float*>(ry + kTcM);
+    a1 = a0 + kTcM;
+    sl = reinterpret_cast<int*>(a1 + kTcM);
+    be = reinterpret_cast<float*>(sl + kTcM);
+    nx = be + kTcM;
+  };
+  bind_rows(0, sray, st0, st1, sslot, sbest, snext);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + lay.bar_off);
   uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + lay.bar_off + 8);
-  __shared__ unsigned long long s_start;
-  __shared__ int s_count;
+  __shared__ unsigned long long s_start[2];
+  __shared__ int s_count[2];  // per row buffer: its tile's item count, kPqNoTile when nothing is staged
 
   // A persistent query's CTAs claim tiles from the queue until it drains.
   const bool persistent = MODE == 1 && a.pq.ring != nullptr;
@@ -434,6 +489,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
     fence_mbar_init();
+    s_count[0] = kPqNoTile;
+    s_count[1] = kPqNoTile;
   }
 
   // Weights -> operand layouts (converted once per CTA).
@@ -470,51 +527,54 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
   constexpr int LPC = 8 / F;  // levels per 8-feature chunk (4 TMEM columns)
   const bool chunked = (L % LPC) == 0;
 
+  int cur = 0;  // persistent query: the row buffer of the tile being evaluated
   for (int64_t tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
-    int ccount = 0;  // persistent query: items in this tile
+    int ccount = 0;       // persistent query: items in this tile
+    bool staged = false;  // its rows were staged while the previous tile finished
     if (persistent) {
-      if (threadIdx.x == 0) {
-        unsigned long long st = 0;
-        s_count = pq_claim(a.pq, &st);
-        s_start = st;
-      }
-      __syncthreads();
-      ccount = s_count;
-      if (ccount <= 0) {
-        failed = ccount < 0;
-        break;
+      bind_rows(cur, sray, st0, st1, sslot, sbest, snext);
+      const int pre = s_count[cur];
+      if (pre != kPqNoTile) {
+        ccount = pre;
+        staged = true;
+      } else {
+        __syncthreads();  // every thread has read s_count[cur]; the previous tile is retired
+        if (threadIdx.x == 0) {
+          unsigned long long st = 0;
+          s_count[cur] = pq_claim(a.pq, &st);
+          s_start[cur] = st;
+        }
+        __syncthreads();
+        ccount = s_count[cur];
+        if (ccount <= 0) {
+          failed = ccount < 0;
+          break;
+        }
       }
     }
+    if (persistent && !staged) {
+      if (threadIdx.x < kTcM) {
+        if (int(threadIdx.x) < ccount) {
+          pq_stage(a, s_start[cur] + threadIdx.x, threadIdx.x, sray, st0, st1, sslot, sbest, snext);
+        } else {
+          sray[threadIdx.x] = -1;
+          st0[threadIdx.x] = 0.0f;
+          st1[threadIdx.x] = 0.0f;
+        }
+      }
+      __syncthreads();
+    } else if (!persistent) {
     if (threadIdx.x < kTcM) {
       const int64_t i = tile * kTcM + threadIdx.x;
       int ray = -1;
       float t0 = 0.0f, t1 = 0.0f;
-      if (persistent ? int(threadIdx.x) < ccount : i < n_items) {
+      if (i < n_items) {
         if constexpr (MODE == 1) {
           const size_t nr = size_t(a.n_rays);
-          if (persistent) {
-            const unsigned long long it = pq_take(a.pq, s_start + threadIdx.x, nr);
-            if (it == kPqEmpty) {
-              set_status(NBVH_ERR_TIMEOUT);
-            } else {
-              ray = int(uint32_t(it));
-              const int sl = int(it >> 32);
-              sslot[threadIdx.x] = sl;
-              const size_t q = size_t(sl) * nr + size_t(ray);
-              t0 = a.seg_t0[q];
-              t1 = a.seg_t1[q];
-              sbest[threadIdx.x] = __ldcg(a.hits.t + ray);
-              // the slot after the last holds stale data: load it with the count, use it only below the count
-              const int cnt = a.seg_count[ray];
-              const float tn = sl + 1 < a.max_segs ? a.seg_t0[size_t(sl + 1) * nr + size_t(ray)] : 0.0f;
-              snext[threadIdx.x] = sl + 1 < cnt ? tn : __int_as_float(0x7f800000);
-            }
-          } else {
-            ray = a.queue[i];
-            const size_t q = size_t(a.wave) * nr + size_t(ray);
-            t0 = a.seg_t0[q];
-            t1 = a.seg_t1[q];
-          }
+          ray = a.queue[i];
+          const size_t q = size_t(a.wave) * nr + size_t(ray);
+          t0 = a.seg_t0[q];
+          t1 = a.seg_t1[q];
         } else if constexpr (MODE == 2) {
           const int r = a.tr.order ? a.tr.order[i] : int(i);
           ray = a.tr.leaf[r] >= 0 ? r : -1;
@@ -531,6 +591,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
       st1[threadIdx.x] = t1;
     }
     __syncthreads();
+    }
     const int64_t grow = tile * kTcM + row;  // global item of this thread's row
     uint16_t* x16 = nullptr;                 // training: this item's column of the stored features
     if constexpr (MODE == 2) {
@@ -726,14 +787,29 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
           for (int j = 0; j < 8; ++j)
             if (j < n_out) a.out[i * n_out + j] = raw[j];
         }
+      } else if (persistent && cgroup == 1) {
+        // meanwhile warps 4-7 claim the next tile if a full one is queued and
+        // stage its rows into the other buffer
+        const int nb = cur ^ 1;
+        int *ry, *sl;
+        float *b0, *b1, *be, *nx;
+        bind_rows(nb, ry, b0, b1, sl, be, nx);
+        if (threadIdx.x == 128) {
+          unsigned long long st = 0;
+          s_count[nb] = pq_try_claim(a.pq, &st);
+          s_start[nb] = st;
+        }
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        if (s_count[nb] != kPqNoTile)
+          pq_stage(a, s_start[nb] + (threadIdx.x - 128), threadIdx.x - 128, ry, b0, b1, sl, be, nx);
       }
       tc_fence_before();
       __syncthreads();
     }
     if (persistent) {
-      // Queue the next segments of this tile's rays (one reservation per warp,
-      // each item written into its entry), then retire the tile's items.
-      bool ok = true;
+      // Warps 0-3 queue the next segments of this tile's rays (one reservation
+      // per warp, each item written into its entry) and retire the tile's
+      // items, while the other warps go on to the next tile.
       if (warp < 4) {
         const int pray = sray[threadIdx.x];
         const unsigned m = __ballot_sync(0xffffffffu, pray >= 0);
@@ -742,11 +818,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
         base = __shfl_sync(0xffffffffu, base, 0);
         if (pray >= 0) {
           const unsigned long long item = (unsigned long long)(sslot[threadIdx.x] + 1) << 32 | uint32_t(pray);
-          ok = pq_put(a.pq, base + __popc(m & ((1u << lane) - 1u)), (unsigned long long)a.n_rays, item);
+          if (!pq_put(a.pq, base + __popc(m & ((1u << lane) - 1u)), (unsigned long long)a.n_rays, item))
+            set_status(NBVH_ERR_TIMEOUT);
         }
+        asm volatile("bar.sync 2, 128;" ::: "memory");
+        if (threadIdx.x == 0) red_release_add_u64(a.pq.retired, (unsigned long long)ccount);  // after the reservations
       }
-      if (__syncthreads_or(!ok)) failed = true;
-      if (threadIdx.x == 0) red_release_add_u64(a.pq.retired, (unsigned long long)ccount);  // after the reservations
+      cur ^= 1;
     }
   }
   if (failed) set_status(NBVH_ERR_TIMEOUT);
