@@ -55,6 +55,8 @@ def parse():
                    help="timed queries of the uneven-segment workload (0: skip it)")
     p.add_argument("--cut-steps", type=int, default=1700,
                    help="training-step budget of the error-driven-cut comparison (0: skip it)")
+    p.add_argument("--lod-steps", type=int, default=1200,
+                   help="training steps of the level-of-detail measurement (0: skip it)")
     p.add_argument("--no-autotune", action="store_true",
                    help="keep the library's default query schedule (no autotuning before the timed region)")
     p.add_argument("--quick", action="store_true",
@@ -631,6 +633,75 @@ def time_cut(args, world):
     return out
 
 
+# ---------------------------------------------------------------------------- levels of detail (NEXT-3)
+def time_lod(args, world):
+    """Levels of detail (Sec. 5.3, Sec. 6.1): an error-driven construction on
+    the icosphere registers LoDs every 100 training steps and trains a random
+    one per step. Primary rays (1920x1080) are answered on the finest LoD;
+    their bounce rays once on the finest and once on a coarse LoD (about 1/8
+    of its leaves). Both bounce queries are timed (graph-captured, L2 flushed)
+    and scored against the closest triangle hits of the same bounce rays."""
+    import torch
+    from paper_2405_16237_b300 import nbvh as B
+    from paper_2405_16237_b300 import workloads as W
+    spec = W.C1
+    cfg = spec.model
+    tris = W.scene_icosphere(level=8)
+    info = B.build_leaves(tris, 1)["info"]
+    desc = B.model_desc(cfg, B.FP16, B.FP16, info["centre"], info["extent"])
+    lay = B.level_layout(desc)
+    opt = B.Optimizer(desc, torch.as_tensor(W.init_table(lay["total"], cfg.n_features, SEED + 61, 1e-4)).cuda(),
+                      torch.as_tensor(B.pack_mlp(W.init_mlp(cfg.mlp_dims(), SEED + 62))).cuda(), loss_scale=32768.0)
+    lods = []
+    _, _, hist, step = B.optimize_cut(tris, desc, opt, spec.n_leaves, base_max_leaf=16, iters=10, splits=16,
+                                      factor=1.4, final_iters=max(1, args.lod_steps - 1000), batch=1 << 16,
+                                      seed=SEED + 63, lr=1e-2, mode=B.TRAIN_PAPER, lod_every=100, lods_out=lods)
+    fine = lods[-1][0]
+    target = max(1, len(fine["leaf_ref"]) // 8)
+    coarse = min((x[0] for x in lods), key=lambda lv: abs(len(lv["leaf_ref"]) - target))
+    rays = B.to_device_rays(W.camera_rays(1920, 1080))
+    n = rays["ox"].numel()
+    fine_nodes = torch.as_tensor(fine["nodes"]).cuda()
+    h1 = B.query_rays(desc, opt.table, opt.mlp, fine_nodes, fine["n_nodes"], rays, 48)
+    rays2 = B.bounce_rays(rays, h1, SEED + 64)
+    blas = B.DeviceTriBlas(tris, B.build_tri_blas(tris, 4))
+    gt = B.trace_triangles(blas, rays2)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    out = {"workload": "icosphere-l8, LoDs every 100 steps, 2^16-ray steps, fp16; 1920x1080 primary rays + bounce",
+           "training_steps": step - 1, "lods": [len(x[0]["leaf_ref"]) for x in lods], "bounce_rays": int(h1["hit"].sum())}
+    for name, lv in (("finest", fine), ("coarse", coarse)):
+        nodes = torch.as_tensor(lv["nodes"]).cuda()
+        h2 = B.new_hits(n)
+        ws = B.new_workspace(B.query_workspace_size(desc, n, 48))
+        g = B.Graph.record(lambda: B.query_rays(desc, opt.table, opt.mlp, nodes, lv["n_nodes"], rays2, 48, out=h2,
+                                                workspace=ws))
+        for _ in range(3):
+            g.launch()
+        total = 0.0
+        for _ in range(5):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            g.launch()
+            e1.record()
+            e1.synchronize()
+            total += e0.elapsed_time(e1)
+        g.destroy()
+        segs, _ = B.query_stats(ws, n, 48)
+        gh, mh = gt["hit"].bool(), h2["hit"].bool()
+        live = rays2["tmax"] >= 0  # bounce rays spawned from a hit
+        both = gh & mh
+        dt = (h2["t"] - gt["t"]).abs()[both]
+        out[name] = {"leaves": len(lv["leaf_ref"]), "ms": total / 5, "segments": int(segs),
+                     "hit_agreement": float((gh == mh)[live].float().mean()),
+                     "depth_mean_abs": float(dt.mean()) if both.any() else None}
+    out["speedup_coarse_vs_finest"] = out["finest"]["ms"] / out["coarse"]["ms"]
+    if B.device_status() != 0:
+        raise RuntimeError("device status after the LoD measurement")
+    return out
+
+
 # ---------------------------------------------------------------------------- hybrid scene (S9)
 HYBRID_BOUNCES = 4
 HYBRID_MAX_SEGS = 16
@@ -875,6 +946,11 @@ def run_gpu(args, world, rank, spec, tris, rays_np):
     B.set_query_schedule(1 if tune_best["schedule"] == "persistent" else 0, tune_best["patience_cycles"])
     B.set_traverse_block(tune_best["traverse_block"])
 
+    # levels of detail: bounce rays on a coarse LoD vs the finest
+    lod = time_lod(args, world) if args.lod_steps > 0 else None
+    B.set_query_schedule(1 if tune_best["schedule"] == "persistent" else 0, tune_best["patience_cycles"])
+    B.set_traverse_block(tune_best["traverse_block"])
+
     # the hybrid two-level scene (16 neural assets + 500,000 classical triangles)
     hybrid = time_hybrid(args, world) if args.hybrid_frames > 0 else None
 
@@ -923,6 +999,7 @@ def run_gpu(args, world, rank, spec, tris, rays_np):
             "train": train,
             "uneven": uneven,
             "cut_optimization": cutcmp,
+            "levels_of_detail": lod,
             "hybrid": hybrid,
             "fp32_plain": {"value": world * rays_step / (ms32 * 1e-3) / 1e6, "ms_per_step": ms32},
             "bf16_tc": {"value": world * rays_step / (msbf * 1e-3) / 1e6, "ms_per_step": msbf},

@@ -873,14 +873,22 @@ def node_rank(hits, trained, loss, n_rays):
 def optimize_cut(tris, desc: ModelDesc, opt, n_target: int, *, base_max_leaf: int = 16, iters: int = 50,
                  splits: int = 4, factor: float = 1.5, final_iters: int = 200, batch: int = 1 << 16,
                  seed: int = 240516237, lr: float = 1e-2, mode: int = TRAIN_PROBED_MIX, inflate_rel: float = 1e-4,
-                 step0: int = 1, max_rounds: int = 1000):
+                 step0: int = 1, max_rounds: int = 1000, lod_every: int = 0, lods_out=None):
     """Error-driven cut optimization (Sec. 5.1): start with the root of the
     base BVH (binned SAH over the triangles); train ``iters`` steps on the
     current cut's N-BVH with error-weighted ray selection; split the
     ``splits`` leaves of largest ranking r into their base children; grow
     both counts by ``factor``; stop at ``n_target`` leaves and train
     ``final_iters`` more steps. Returns (leaves dict of the final cut, the
-    DeviceScene, per-round history, next step number)."""
+    DeviceScene, per-round history, next step number).
+
+    Levels of detail (Sec. 5.3): with ``lod_every`` > 0 the current cut is
+    registered as an LoD whenever another ``lod_every`` training steps have
+    passed (at a round's end, before its splits), and from then on every step
+    trains a cut drawn uniformly from the registered LoDs and the current cut
+    (seeded host draws; error weighting applies to the current cut only).
+    ``lods_out`` (a list) receives (leaves, DeviceScene) of every LoD, coarse
+    to fine, the final cut last."""
     torch = _torch()
     base = build_tri_blas(tris, base_max_leaf)
     info = build_leaves(tris, 1, inflate_rel)["info"]
@@ -892,8 +900,13 @@ def optimize_cut(tris, desc: ModelDesc, opt, n_target: int, *, base_max_leaf: in
     ws_leaves = -1
     loss = torch.zeros(1, dtype=torch.float64, device="cuda")
 
+    lods = []  # registered (leaves, scene), coarse to fine
+    lod_rng = np.random.default_rng(seed ^ 0x10D)
+    trained_steps = 0
+    next_lod = lod_every
+
     def run(cut, prob, n_iters):
-        nonlocal step, ws, ws_leaves
+        nonlocal step, ws, ws_leaves, trained_steps
         lv = build_cut(base, cut, inflate_rel, info)
         scene = DeviceScene(tris, lv)
         if ws is None or ws_leaves < len(cut):
@@ -905,9 +918,14 @@ def optimize_cut(tris, desc: ModelDesc, opt, n_target: int, *, base_max_leaf: in
                  "loss": torch.zeros(n, dtype=torch.float64, device="cuda")}
         pdev = torch.as_tensor(np.asarray(prob, np.float32)).cuda() if prob is not None else None
         for _ in range(n_iters):
-            train_step_weighted(desc, opt, scene, mode, batch, seed, step, lr, ws, leaf_prob=pdev, stats=stats,
-                                loss_out=loss)
+            k = int(lod_rng.integers(0, len(lods) + 1)) if lods else len(lods)
+            if k == len(lods):
+                train_step_weighted(desc, opt, scene, mode, batch, seed, step, lr, ws, leaf_prob=pdev,
+                                    stats=stats, loss_out=loss)
+            else:
+                train_step_weighted(desc, opt, lods[k][1], mode, batch, seed, step, lr, ws, loss_out=loss)
             step += 1
+        trained_steps += n_iters
         h = stats["hits"].cpu().numpy()
         t = stats["trained"].cpu().numpy()
         l = stats["loss"].cpu().numpy()
@@ -917,6 +935,10 @@ def optimize_cut(tris, desc: ModelDesc, opt, n_target: int, *, base_max_leaf: in
     while len(cut) < n_target and rounds < max_rounds:
         rounds += 1
         lv, scene, h, t, l = run(cut, prob, iters)
+        if lod_every > 0 and trained_steps >= next_lod:
+            lods.append((lv, scene))
+            while next_lod <= trained_steps:
+                next_lod += lod_every
         q, p, r, pr = node_rank(h, t, l, batch * iters)
         history.append({"leaves": len(cut), "iters": iters, "loss": float(loss.item()),
                         "mean_q": float(np.sum(l) / max(1, np.sum(t)))})
@@ -941,5 +963,9 @@ def optimize_cut(tris, desc: ModelDesc, opt, n_target: int, *, base_max_leaf: in
         splits = int(math.ceil(splits * factor))
     lv, scene, h, t, l = run(cut, prob, final_iters)
     history.append({"leaves": len(cut), "iters": final_iters, "loss": float(loss.item()),
-                    "mean_q": float(np.sum(l) / max(1, np.sum(t))), "final": True})
+                    "mean_q": float(np.sum(l) / max(1, np.sum(t))), "final": True,
+                    "lods": [len(x[0]["leaf_ref"]) for x in lods]})
+    if lods_out is not None:
+        lods_out.extend(lods)
+        lods_out.append((lv, scene))
     return lv, scene, history, step

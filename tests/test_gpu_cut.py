@@ -113,3 +113,34 @@ def test_cut_optimizer_reaches_target_with_a_valid_cut(mp):
     assert hist[0]["leaves"] == 1 and hist[-1].get("final") and len(hist) >= 4
     assert all(np.isfinite(h["loss"]) and h["mean_q"] > 0 for h in hist)
     assert step == 1 + sum(h["iters"] for h in hist)
+
+
+def test_levels_of_detail():
+    """optimize_cut with LoDs registered every 8 training steps: the LoDs are
+    valid cuts of increasing size ending with the final cut; every step trains
+    one of them; a query on each LoD runs, and a coarser LoD evaluates fewer
+    segments for the same rays."""
+    torch = _torch()
+    tris, _, _, cfg, desc, _, _, opt, _ = _setup(mlp_prec=B.FP16)
+    lods = []
+    lv, scene, hist, step = B.optimize_cut(tris, desc, opt, 32, base_max_leaf=8, iters=4, splits=2, factor=1.5,
+                                           final_iters=6, batch=4096, seed=3, lod_every=8, lods_out=lods)
+    assert B.device_status() == 0
+    sizes = [len(x[0]["leaf_ref"]) for x in lods]
+    assert len(lods) >= 3 and sizes == sorted(sizes) and sizes[-1] == 32 and sizes[0] < 32
+    assert lods[-1][0] is lv
+    base = B.build_tri_blas(tris, 8)
+    nodes = B.node_array({"nodes": base["nodes"]})
+    for leaves, _ in lods:
+        _, sets, _, _ = O.cut_leaves(tris, nodes, base["leaf_range"], base["tri_perm"], list(leaves["leaf_ref"]),
+                                     1e-4, leaves["info"]["extent"])
+        assert np.array_equal(np.sort(np.concatenate(sets)), np.arange(len(tris)))
+    rays = B.to_device_rays(W.chord_rays(4000, seed=8, radius=0.6))
+    segs = []
+    for leaves, _ in (lods[0], lods[-1]):
+        ws = B.new_workspace(B.query_workspace_size(desc, 4000, 40))
+        B.query_rays(desc, opt.table, opt.mlp, torch.as_tensor(leaves["nodes"]).cuda(), leaves["n_nodes"], rays, 40,
+                     workspace=ws)
+        segs.append(B.query_stats(ws, 4000, 40)[0])
+    assert B.device_status() == 0
+    assert segs[0] < segs[1]
