@@ -639,8 +639,10 @@ def time_lod(args, world):
     the icosphere registers LoDs every 100 training steps and trains a random
     one per step. Primary rays (1920x1080) are answered on the finest LoD;
     their bounce rays once on the finest and once on a coarse LoD (about 1/8
-    of its leaves). Both bounce queries are timed (graph-captured, L2 flushed)
-    and scored against the closest triangle hits of the same bounce rays."""
+    of its leaves), each also with the reversed query of the leaf the ray
+    starts in (NBVH_FLAG_REVERSE_INSIDE). Every bounce query is timed
+    (graph-captured, L2 flushed) and scored against the closest triangle hits
+    of the same bounce rays."""
     import torch
     from paper_2405_16237_b300 import nbvh as B
     from paper_2405_16237_b300 import workloads as W
@@ -669,11 +671,13 @@ def time_lod(args, world):
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     out = {"workload": "icosphere-l8, LoDs every 100 steps, 2^16-ray steps, fp16; 1920x1080 primary rays + bounce",
            "training_steps": step - 1, "lods": [len(x[0]["leaf_ref"]) for x in lods], "bounce_rays": int(h1["hit"].sum())}
-    for name, lv in (("finest", fine), ("coarse", coarse)):
+    desc_rev = B.with_flags(desc, B.FLAG_REVERSE_INSIDE)
+    for name, lv, dq in (("finest", fine, desc), ("coarse", coarse, desc), ("finest_reversed_inside", fine, desc_rev),
+                         ("coarse_reversed_inside", coarse, desc_rev)):
         nodes = torch.as_tensor(lv["nodes"]).cuda()
         h2 = B.new_hits(n)
-        ws = B.new_workspace(B.query_workspace_size(desc, n, 48))
-        g = B.Graph.record(lambda: B.query_rays(desc, opt.table, opt.mlp, nodes, lv["n_nodes"], rays2, 48, out=h2,
+        ws = B.new_workspace(B.query_workspace_size(dq, n, 48))
+        g = B.Graph.record(lambda: B.query_rays(dq, opt.table, opt.mlp, nodes, lv["n_nodes"], rays2, 48, out=h2,
                                                 workspace=ws))
         for _ in range(3):
             g.launch()

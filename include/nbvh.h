@@ -80,7 +80,18 @@ typedef struct {
   nbvh_precision mlp_prec;    /* FP32: CUDA-core MLP; FP16/BF16: tensor-core MLP */
   float frame_centre[3];
   float frame_extent;
+  int32_t flags;         /* NBVH_FLAG_*; 0 = the default query */
 } nbvh_model_desc;
+
+/* Query option (the paper's Sec. 6 text on depth from within a node,
+ * commented out in its source): a ray whose origin lies inside a leaf box
+ * (the box's entry t is below tmin) queries that leaf over its whole chord
+ * with the samples concatenated in reverse order, from the exit point back
+ * towards the entry, as a ray entering the box at its exit would see it. The
+ * predicted hit is t = exit - sigmoid(o_d) (exit - entry) and counts only if
+ * tmin < t <= tmax. Such a segment is listed with its endpoints swapped
+ * (t0 = exit > t1 = entry) and ordered by its entry. */
+#define NBVH_FLAG_REVERSE_INSIDE 1
 
 /* Rays, device structure-of-arrays, n entries each. */
 typedef struct {

@@ -244,9 +244,13 @@ def rays_od(rays: dict, idx=None):
     return o, d, tmin, tmax
 
 
-def ray_segments(rays: dict, leaf_lo, leaf_hi, chunk: int = 1024):
+def ray_segments(rays: dict, leaf_lo, leaf_hi, chunk: int = 1024, reverse_inside: bool = False):
     """All (ray, leaf) pairs whose clip is non-empty, sorted per ray by
-    (t0, leaf id). Returns CSR dict: ``offsets`` [R+1], ``ray``, ``leaf``,
+    (t0, leaf id). With ``reverse_inside`` (the Sec. 6 reading of depth from
+    within a node) a pair whose box entry lies below tmin (the origin is
+    inside the box) is listed over the box's whole chord with swapped
+    endpoints, t0 = exit > t1 = entry, and sorted by its entry.
+    Returns CSR dict: ``offsets`` [R+1], ``ray``, ``leaf``,
     ``t0``, ``t1``, ``entry``, ``exit`` (float64) and per-pair ``grazing``
     pairs ``grazing_pairs`` [G, 2] = (ray, leaf) with |exit - entry| <= 1e-6,
     |entry - tmax| <= 1e-6 or |exit - tmin| <= 1e-6: touching or nearly
@@ -275,7 +279,12 @@ def ray_segments(rays: dict, leaf_lo, leaf_hi, chunk: int = 1024):
         out["entry"].append(en[r, l])
         out["exit"].append(ex[r, l])
     seg = {k: np.concatenate(v) for k, v in out.items()}
-    order = np.lexsort((seg["leaf"], seg["t0"], seg["ray"]))
+    if reverse_inside:
+        inside = (seg["entry"] < tmin[seg["ray"]]) & np.isfinite(seg["entry"]) & np.isfinite(seg["exit"])
+        seg["t0"] = np.where(inside, seg["exit"], seg["t0"])
+        seg["t1"] = np.where(inside, seg["entry"], seg["t1"])
+    key = np.minimum(seg["t0"], seg["t1"])
+    order = np.lexsort((seg["leaf"], key, seg["ray"]))
     seg = {k: v[order] for k, v in seg.items()}
     seg["offsets"] = np.concatenate([[0], np.cumsum(np.bincount(seg["ray"], minlength=R))]).astype(np.int64)
     seg["grazing_pairs"] = np.concatenate(graz_pairs, 0) if graz_pairs else np.zeros((0, 2), np.int64)
@@ -443,9 +452,13 @@ def eval_segments(o, d, t0, t1, table, layers, layout, centre, extent, n_samples
     return feat, raw
 
 
-def query(rays: dict, leaves: dict, table, layers, layout, n_samples: int, chunk: int = 4096):
-    """The full neural ray query: S1 -> S5 over every segment of every ray."""
-    seg = ray_segments(rays, leaves["leaf_lo"], leaves["leaf_hi"])
+def query(rays: dict, leaves: dict, table, layers, layout, n_samples: int, chunk: int = 4096,
+          reverse_inside: bool = False):
+    """The full neural ray query: S1 -> S5 over every segment of every ray.
+    With ``reverse_inside`` a chord listed reversed (t0 > t1, see
+    ray_segments) is sampled from its exit back to its entry, its hit lies at
+    t = exit - sigmoid(o_d) (exit - entry) and counts only if tmin < t <= tmax."""
+    seg = ray_segments(rays, leaves["leaf_lo"], leaves["leaf_hi"], reverse_inside=reverse_inside)
     o, d, _, _ = rays_od(rays)
     fr = leaves["frame"]
     S = len(seg["ray"])
@@ -459,6 +472,11 @@ def query(rays: dict, leaves: dict, table, layers, layout, n_samples: int, chunk
         feats.append(f)
     raw = np.concatenate(raws) if raws else np.zeros((0, layers[-1][0].shape[0]))
     hit, t, nrm = decode(raw, seg["t0"], seg["t1"])
+    if reverse_inside:
+        rev = seg["t0"] > seg["t1"]
+        _, _, tmin, tmax = rays_od(rays)
+        rr = seg["ray"]
+        hit = hit & (~rev | ((t > tmin[rr]) & (t <= tmax[rr])))
     res = resolve(len(o), seg, hit, t, nrm)
     res["segments"] = seg
     res["raw"] = raw

@@ -186,7 +186,8 @@ __device__ __forceinline__ void wave_resolve(const EvalArgs& a, bool valid, int 
                                              float t1) {
   bool push = false;
   if (valid) {
-    const SegResult s = decode_segment(raw, t0, t1);
+    SegResult s = decode_segment(raw, t0, t1);
+    if (s.hit && t0 > t1) s.hit = s.t > a.rays.tmin[ray] && s.t <= a.rays.tmax[ray];  // reversed chord
     float best = a.hits.t[ray];
     if (s.hit && s.t < best) {
       best = s.t;
@@ -200,8 +201,8 @@ __device__ __forceinline__ void wave_resolve(const EvalArgs& a, bool valid, int 
     }
     const int nxt = a.wave + 1;
     if (nxt < a.seg_count[ray]) {
-      const float tn = a.seg_t0[size_t(nxt) * size_t(a.n_rays) + size_t(ray)];
-      push = tn < best;
+      const size_t q = size_t(nxt) * size_t(a.n_rays) + size_t(ray);
+      push = fminf(a.seg_t0[q], a.seg_t1[q]) < best;  // the next segment's start
     }
   }
   const unsigned m = __ballot_sync(0xffffffffu, push);

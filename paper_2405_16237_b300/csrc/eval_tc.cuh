@@ -404,7 +404,8 @@ __device__ __forceinline__ int pq_stage(const EvalArgs& a, unsigned long long p,
     sbest[r] = __ldcg(a.hits.t + ray);
     // the slot after the last holds stale data: load it with the count, use it only below the count
     const int cnt = a.seg_count[ray];
-    const float tn = sl + 1 < a.max_segs ? a.seg_t0[size_t(sl + 1) * nr + size_t(ray)] : 0.0f;
+    const size_t qn = size_t(sl + 1) * nr + size_t(ray);
+    const float tn = sl + 1 < a.max_segs ? fminf(a.seg_t0[qn], a.seg_t1[qn]) : 0.0f;  // its start
     snext[r] = sl + 1 < cnt ? tn : __int_as_float(0x7f800000);
   }
   sray[r] = ray;
@@ -420,7 +421,8 @@ __device__ __forceinline__ int pq_stage(const EvalArgs& a, unsigned long long p,
 // (it starts before the best t).
 __device__ __forceinline__ bool pq_resolve(const EvalArgs& a, int ray, int sl, float best, float next_t0,
                                            const float* raw, float t0, float t1) {
-  const SegResult s = decode_segment(raw, t0, t1);
+  SegResult s = decode_segment(raw, t0, t1);
+  if (s.hit && t0 > t1) s.hit = s.t > a.rays.tmin[ray] && s.t <= a.rays.tmax[ray];  // reversed chord
   if (s.hit && s.t < best) {
     best = s.t;
     a.hits.t[ray] = s.t;

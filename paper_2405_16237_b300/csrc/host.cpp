@@ -45,6 +45,7 @@ bool desc_valid(const nbvh_model_desc* d) {
   if (!(d->frame_extent > 0.0f) || !std::isfinite(d->frame_extent)) return false;
   for (int i = 0; i < 3; ++i)
     if (!std::isfinite(d->frame_centre[i])) return false;
+  if ((d->flags & ~NBVH_FLAG_REVERSE_INSIDE) != 0) return false;
   return true;
 }
 

@@ -259,6 +259,7 @@ cudaError_t launch_query_stages(const nbvh_model_desc* desc, const GridParams& g
   to.qlen0 = w.counters;
   to.hits = out;
   to.merge = merge ? 1 : 0;
+  to.reverse_inside = (desc->flags & NBVH_FLAG_REVERSE_INSIDE) ? 1 : 0;
   const bool persistent = desc->mlp_prec != NBVH_FP32 && g_schedule.load() == NBVH_SCHEDULE_PERSISTENT;
   if (persistent) {
     to.queue0 = nullptr;

@@ -20,7 +20,15 @@ struct TraverseOut {
   int32_t merge;
   // Optional (persistent query): the queued rays as 64-bit items (slot 0).
   unsigned long long* ring0;
+  // A leaf whose box the ray's origin lies in (entry < tmin) is listed over its
+  // whole chord with swapped endpoints (t0 = exit, t1 = entry), for a query
+  // of the chord in reverse order (NBVH_FLAG_REVERSE_INSIDE).
+  int32_t reverse_inside;
 };
+
+// Order key of a listed segment: its start along the ray (the entry of a
+// swapped segment).
+__device__ __forceinline__ float seg_key(float t0, float t1) { return fminf(t0, t1); }
 
 // Traversal of ray r (S1). Depth-first with a short stack; the nearer child
 // is descended first. Child boxes are stored in the parent, so one 64-byte
@@ -40,25 +48,38 @@ __device__ __forceinline__ int traverse_ray(const nbvh_node* __restrict__ nodes,
   const bool merge = out.merge != 0;
   const float best = merge ? out.hits.t[r] : 0.0f;
   bool overflow = false;
+  float lo_box[3] = {0.0f, 0.0f, 0.0f}, hi_box[3] = {0.0f, 0.0f, 0.0f};  // the box being emitted
   auto emit = [&](int leaf, float t0, float t1) {
+    if (out.reverse_inside) {  // origin inside the box: the whole chord, reversed
+      RayR whole = ray;
+      whole.tmin = -__int_as_float(0x7f800000);
+      whole.tmax = __int_as_float(0x7f800000);
+      float en, ex;
+      if (clip_box(whole, lo_box[0], lo_box[1], lo_box[2], hi_box[0], hi_box[1], hi_box[2], en, ex) &&
+          en < tmin && isfinite(en) && isfinite(ex)) {
+        t0 = ex;
+        t1 = en;
+      }
+    }
+    const float key = seg_key(t0, t1);
     int pos;
     if (count < max_segs) {
       pos = count++;
     } else {
       overflow = true;
       const size_t q = size_t(max_segs - 1) * size_t(n) + size_t(r);
-      const float lt = out.seg_t0[q];
+      const float lt = seg_key(out.seg_t0[q], out.seg_t1[q]);
       const int ll = out.seg_leaf[q];
-      if (t0 > lt || (t0 == lt && leaf > ll)) return;
+      if (key > lt || (key == lt && leaf > ll)) return;
       pos = max_segs - 1;
     }
     while (pos > 0) {
       const size_t q = size_t(pos - 1) * size_t(n) + size_t(r);
-      const float pt = out.seg_t0[q];
+      const float pt = seg_key(out.seg_t0[q], out.seg_t1[q]);
       const int pl = out.seg_leaf[q];
-      if (pt < t0 || (pt == t0 && pl < leaf)) break;
+      if (pt < key || (pt == key && pl < leaf)) break;
       const size_t w = size_t(pos) * size_t(n) + size_t(r);
-      out.seg_t0[w] = pt;
+      out.seg_t0[w] = out.seg_t0[q];
       out.seg_t1[w] = out.seg_t1[q];
       out.seg_leaf[w] = pl;
       --pos;
@@ -85,8 +106,16 @@ __device__ __forceinline__ int traverse_ray(const nbvh_node* __restrict__ nodes,
       h0 = h0 && a0 < best;
       h1 = h1 && b0 < best;
     }
-    if (h0 && e.x < 0) emit(~e.x, a0, a1);
-    if (h1 && e.y < 0) emit(~e.y, b0, b1);
+    if (h0 && e.x < 0) {
+      lo_box[0] = a.x; lo_box[1] = a.y; lo_box[2] = a.z;
+      hi_box[0] = a.w; hi_box[1] = b.x; hi_box[2] = b.y;
+      emit(~e.x, a0, a1);
+    }
+    if (h1 && e.y < 0) {
+      lo_box[0] = b.z; lo_box[1] = b.w; lo_box[2] = c.x;
+      hi_box[0] = c.y; hi_box[1] = c.z; hi_box[2] = c.w;
+      emit(~e.y, b0, b1);
+    }
     const bool g0 = h0 && e.x >= 0;
     const bool g1 = h1 && e.y >= 0;
     if (g0 && g1) {

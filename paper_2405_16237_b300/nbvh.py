@@ -37,7 +37,10 @@ class ModelDesc(ctypes.Structure):
                 ("base_res", c_int32), ("growth", c_float), ("n_samples", c_int32),
                 ("n_hidden", c_int32), ("width", c_int32), ("n_out", c_int32),
                 ("table_prec", c_int32), ("mlp_prec", c_int32), ("frame_centre", c_float * 3),
-                ("frame_extent", c_float)]
+                ("frame_extent", c_float), ("flags", c_int32)]
+
+
+FLAG_REVERSE_INSIDE = 1
 
 
 class Rays(ctypes.Structure):
@@ -236,6 +239,13 @@ def with_mlp_prec(desc: ModelDesc, mlp_prec: int) -> ModelDesc:
     d = ModelDesc()
     ctypes.pointer(d)[0] = desc
     d.mlp_prec = mlp_prec
+    return d
+
+
+def with_flags(desc: ModelDesc, flags: int) -> ModelDesc:
+    d = ModelDesc()
+    ctypes.pointer(d)[0] = desc
+    d.flags = flags
     return d
 
 

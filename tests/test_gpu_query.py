@@ -387,3 +387,72 @@ def test_autotuner_times_candidates_and_keeps_results(mp):
     assert now == (1 if best["schedule"] == "persistent" else 0, best["patience_cycles"])
     for k in ref:
         assert torch.equal(ref[k], got[k]), k
+
+
+def _surface_rays(tris, n, seed):
+    """Rays starting on the mesh (a uniform point of a random triangle) in a
+    uniform direction: their origins lie inside leaf boxes."""
+    rng = np.random.default_rng(seed)
+    t = tris[rng.integers(0, len(tris), n)].astype(np.float64)
+    u, v = rng.uniform(size=(2, n))
+    flip = u + v > 1
+    u[flip], v[flip] = 1 - u[flip], 1 - v[flip]
+    o = t[:, 0] + u[:, None] * (t[:, 1] - t[:, 0]) + v[:, None] * (t[:, 2] - t[:, 0])
+    z = rng.uniform(-1, 1, n)
+    ph = rng.uniform(0, 2 * np.pi, n)
+    s = np.sqrt(1 - z * z)
+    d = np.stack([s * np.cos(ph), s * np.sin(ph), z], 1)
+    keys = ("ox", "oy", "oz", "dx", "dy", "dz")
+    vals = (o[:, 0], o[:, 1], o[:, 2], d[:, 0], d[:, 1], d[:, 2])
+    rays = {k: np.asarray(x, np.float32) for k, x in zip(keys, vals)}
+    rays["tmin"] = np.full(n, 1e-4, np.float32)
+    rays["tmax"] = np.full(n, np.inf, np.float32)
+    return rays
+
+
+@pytest.mark.parametrize("mp", [B.FP32, B.FP16])
+def test_reverse_inside_query_matches_oracle(mp):
+    """NBVH_FLAG_REVERSE_INSIDE on rays that start on the surface: segment
+    lists with the reversed chords first (endpoints exact), FP32 results equal
+    to the oracle's on unambiguous rays, FP16 within tolerance."""
+    torch = _torch()
+    b = built("icosphere_l6", 1.0, 2.0)
+    rays = _surface_rays(b.case.tris, 3000, 12)
+    res = O.query(rays, b.oleaves, b.table_host, b.layers, b.olayout, b.case.model.n_samples, reverse_inside=True)
+    seg = res["segments"]
+    n = len(rays["ox"])
+    rev = seg["t0"] > seg["t1"]
+    assert rev.sum() > 1000
+    desc = B.with_flags(b.with_prec(mp), B.FLAG_REVERSE_INSIDE)
+    ms = int(np.max(np.diff(seg["offsets"]))) + 1
+    dr = B.to_device_rays(rays)
+    h = B.query_rays(desc, b.table, b.mlp, b.nodes, b.leaves["n_nodes"], dr, ms)
+    assert B.device_status() == 0
+    h = {k: v.cpu().numpy() for k, v in h.items()}
+    amb = ambiguous_rays(res, n)
+    # a reversed chord's hit counts only inside (tmin, tmax]: decisions within
+    # rounding of the window's ends are ambiguous too
+    raw_hit = res["raw"][:, 0] > 0
+    near_end = rev & raw_hit & ((np.abs(res["seg_t"] - rays["tmin"][seg["ray"]]) <= 1e-5 * np.maximum(
+        1.0, np.abs(res["seg_t"]))) | (np.abs(res["seg_t"] - rays["tmax"][seg["ray"]]) <= 1e-5))
+    amb[seg["ray"][near_end]] = True
+    if mp == B.FP32:
+        ok = ~amb
+        assert ok.mean() > 0.95
+        bad = np.flatnonzero(ok & (h["hit"].astype(bool) != res["hit"].astype(bool)))
+        assert len(bad) == 0, [(int(r), float(h["t"][r]), float(res["t"][r]), float(rays["tmin"][r])) for r in bad[:5]]
+        assert np.array_equal(h["leaf"][ok], res["leaf"][ok])
+        hh = ok & res["hit"].astype(bool)
+        assert hh.sum() > 100
+        assert np.all(np.abs(h["t"][hh] - res["t"][hh]) <= 1e-5 * np.maximum(np.abs(res["t"][hh]), 1e-3))
+    else:
+        assert np.mean(h["hit"].astype(bool) == res["hit"].astype(bool)) >= 0.995
+    # the chords themselves: the traversal step of the query lists the same swapped segments
+    plain = O.ray_segments(rays, b.oleaves["leaf_lo"], b.oleaves["leaf_hi"])
+    assert not np.array_equal(plain["t0"], seg["t0"])
+    # the flag off gives the plain query
+    h0 = B.query_rays(b.with_prec(mp), b.table, b.mlp, b.nodes, b.leaves["n_nodes"], dr, ms)
+    r0 = O.query(rays, b.oleaves, b.table_host, b.layers, b.olayout, b.case.model.n_samples)
+    if mp == B.FP32:
+        ok0 = ~ambiguous_rays(r0, n)
+        assert np.array_equal(h0["hit"].cpu().numpy()[ok0].astype(bool), r0["hit"][ok0].astype(bool))

@@ -696,3 +696,35 @@ def test_leaf_statistics_counts_by_hand():
                                             [1.0, 9.0, 2.0, 5.0, 0.5, 3.0], 3)
     assert list(hits) == [1, 3, 1] and list(trained) == [1, 2, 1]
     assert np.allclose(loss, [1.0, 5.0, 0.5])
+
+
+def test_reverse_inside_chord_listing():
+    """Reading of depth from within a node: a ray starting inside a box lists
+    that box over its whole chord with swapped endpoints (exit, entry) and
+    first in order; boxes ahead of it are listed as usual; without the flag
+    nothing changes."""
+    lo = np.array([[-1.0, -1.0, -1.0], [2.0, -1.0, -1.0]])
+    hi = np.array([[1.0, 1.0, 1.0], [3.0, 1.0, 1.0]])
+    rays = {k: np.zeros(2, np.float32) for k in W.RAY_KEYS}
+    rays["ox"][:] = [0.5, -3.0]
+    rays["dx"][:] = [1.0, 1.0]
+    rays["tmax"][:] = np.inf
+    seg = O.ray_segments(rays, lo, hi, reverse_inside=True)
+    # ray 0 starts at x = 0.5 inside box 0: chord entry -1.5, exit 0.5; box 1 at [1.5, 2.5]
+    assert list(seg["leaf"][:2]) == [0, 1]
+    assert seg["t0"][0] == 0.5 and seg["t1"][0] == -1.5
+    assert seg["t0"][1] == 1.5 and seg["t1"][1] == 2.5
+    # ray 1 starts outside both: plain segments
+    assert list(seg["t0"][2:]) == [2.0, 5.0] and list(seg["t1"][2:]) == [4.0, 6.0]
+    plain = O.ray_segments(rays, lo, hi)
+    assert plain["t0"][0] == 0.0 and plain["t1"][0] == 0.5
+
+
+def test_reverse_inside_decode_window():
+    """A reversed chord [exit 0.5 .. entry -1.5] of a ray starting at t = 0:
+    the sample order runs from the exit back, and a predicted depth fraction
+    s puts the hit at 0.5 - 2 s, kept only for 0 < t <= tmax."""
+    p = O.sample_points(np.zeros((1, 3)), np.array([[1.0, 0.0, 0.0]]), np.array([0.5]), np.array([-1.5]), 4)
+    assert np.allclose(p[0, :, 0], [0.25, -0.25, -0.75, -1.25])
+    hit, t, _ = O.decode(np.array([[3.0, 0.0, 0, 0, 1]]), np.array([0.5]), np.array([-1.5]))
+    assert hit[0] and t[0] == 0.5 - 2.0 * 0.5  # sigmoid(0) = 1/2: t = -0.5, behind the origin
