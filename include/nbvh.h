@@ -75,7 +75,8 @@ typedef struct {
   int32_t n_samples;     /* N samples per segment, 1..NBVH_MAX_SAMPLES */
   int32_t n_hidden;      /* hidden layers, 1..8 */
   int32_t width;         /* hidden width: 16, 32, 64 or 128 */
-  int32_t n_out;         /* outputs: 5 = hit logit, depth logit, normal xyz */
+  int32_t n_out;         /* outputs: 5 = hit logit, depth logit, normal xyz;
+                            8 = the same plus albedo logits rgb (5..8 accepted) */
   nbvh_precision table_prec;  /* storage type of the hash-table entries */
   nbvh_precision mlp_prec;    /* FP32: CUDA-core MLP; FP16/BF16: tensor-core MLP */
   float frame_centre[3];
@@ -100,11 +101,16 @@ typedef struct {
 } nbvh_rays;
 
 /* Query result per ray, device structure-of-arrays. Rays without a predicted
- * hit get hit = 0, t = +inf, leaf = -1, normal = 0. */
+ * hit get hit = 0, t = +inf, leaf = -1, normal = 0, albedo 0. The albedo
+ * arrays are optional (all three NULL, or all three set): the hit's albedo,
+ * sigmoid of outputs 5-7 for a model with n_out = 8 (Sec. 5.2, auxiliary
+ * intersection data), the triangle's albedo for a triangle BLAS that has one,
+ * else 0. */
 typedef struct {
   uint8_t *hit;
   float *t, *nx, *ny, *nz;
   int32_t *leaf;
+  float *ar, *ag, *ab;
 } nbvh_hits;
 
 /* One N-BVH node, 64 bytes: the boxes of both children (lo xyz, hi xyz) and
@@ -321,12 +327,15 @@ typedef struct {
   const float* leaf_tris;    /* optional device [n_tris][9]: the triangles in tri_perm order (each
                                 leaf's triangles contiguous); the labels read them when set */
   nbvh_scene_info info;      /* by value */
+  const float* tri_albedo;   /* optional device [n_tris][3] RGB in [0, 1] by triangle index, NULL = none */
 } nbvh_train_scene;
 
-/* Training labels, device structure-of-arrays. */
+/* Training labels, device structure-of-arrays. The albedo arrays are optional
+ * (all three NULL or all three set); the loss uses them with n_out = 8. */
 typedef struct {
   uint8_t* hit;
   float *depth, *nx, *ny, *nz;
+  float *ar, *ag, *ab;
 } nbvh_labels;
 
 /* Device. S7 rays of one training step. Randomness: Philox4x32-10 keyed by
@@ -345,7 +354,8 @@ nbvh_status nbvh_train_rays(int32_t mode, uint64_t seed, int64_t step, const nbv
 /* Device. S7 labels: closest Moller-Trumbore intersection (edges inclusive,
  * det == 0 a miss) among the trained leaf's own triangles with t in
  * [t0, t1]; hit, local depth (t - t0)/(t1 - t0), geometric normal turned to
- * face -d. Rays with leaf < 0 get hit 0. */
+ * face -d; with scene->tri_albedo and out.ar set, the hit triangle's albedo
+ * (0 on a miss). Rays with leaf < 0 get hit 0. */
 nbvh_status nbvh_train_labels(nbvh_rays rays, const int32_t* leaf, const float* t0, const float* t1,
                               const nbvh_train_scene* scene, nbvh_labels out, void* stream);
 
@@ -359,7 +369,9 @@ nbvh_status nbvh_train_workspace_size(const nbvh_model_desc* desc, int64_t n, in
  * raw_out: device [n][n_out] raw MLP outputs. With labels (labels.hit != NULL)
  * it also evaluates the combined loss L = mean over training segments of
  * 2 BCE(sigmoid(o_hit), y) + y (2 |sigmoid(o_d) - d| + (1/3) sum_j |o_nj - n_j|)
- * (Sec. 5.2), keeps dL/d(raw) times the loss scale for nbvh_backward, and
+ * (Sec. 5.2), plus, for n_out = 8 with albedo labels, the relative L2 term
+ * y (1/3) sum_c (s_c - a_c)^2 / (s_c^2 + 0.01), s_c = sigmoid(o_{5+c}), the
+ * denominator held constant; keeps dL/d(raw) times the loss scale for nbvh_backward, and
  * writes L (FP64 reduction) to *loss_out (device, may be NULL).
  * n_valid: device count of training segments (nbvh_train_rays). The loss
  * scale is *loss_scale_dev when that is not NULL, else loss_scale. */
@@ -532,6 +544,7 @@ typedef struct {
   const float* tris;          /* [n_tris][9] vertices in leaf order (tris[tri_perm[i]]) */
   const int32_t* leaf_range;  /* [n_leaves][2] as nbvh_build_tri_blas */
   const int32_t* tri_id;      /* [n_tris] tri_perm: caller index of each leaf-order triangle */
+  const float* albedo;        /* optional [n_tris][3] RGB by caller index, NULL = none */
 } nbvh_tri_blas;
 
 /* Device. Closest triangle hit of every ray with t in [tmin, tmax]

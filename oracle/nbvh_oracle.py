@@ -19,7 +19,7 @@ Pipeline (Sec. 4 "Neural ray query", Fig. 3; Sec. 5; Sec. 6 "Implementation"):
   S3 ``encode``            multi-resolution hash-grid features of each point,
                            concatenated in ray order (Sec. 4, Fig. 3).
   S4 ``mlp_forward``       ReLU MLP decoding visibility, distance, normal
-                           (Sec. 5.2, Sec. 6).
+                           and, with 8 outputs, albedo (Sec. 5.2, Sec. 6).
   S5 ``decode``/``resolve``  per-segment hit and depth, closest predicted hit
                            per ray (Sec. 5: queries until an intersection).
   S7 ``train_rays``/``labels``  training rays and brute-force Moller-Trumbore
@@ -421,13 +421,22 @@ def decode(raw, t0, t1):
     return hit, t, nrm
 
 
-def resolve(n_rays: int, seg, hit, t, nrm):
+def decode_albedo(raw):
+    """Albedo of each segment from a model with an albedo head (outputs 5-7):
+    sigmoid of the three logits, so that it lies in [0, 1] like the signal it
+    learns (Sec. 5.2 "Auxiliary intersection data"); None without the head."""
+    raw = np.asarray(raw, F64)
+    return sigmoid(raw[:, 5:8]) if raw.shape[1] >= 8 else None
+
+
+def resolve(n_rays: int, seg, hit, t, nrm, albedo=None):
     """Closest predicted hit per ray over all its segments; equal t goes to the
     segment first in (t0, leaf) order. Rays without a predicted hit get
-    hit = 0, t = +inf, leaf = -1, normal = 0."""
+    hit = 0, t = +inf, leaf = -1, normal = 0 (and albedo 0 when given)."""
     out_hit = np.zeros(n_rays, np.uint8)
     out_t = np.full(n_rays, np.inf)
     out_n = np.zeros((n_rays, 3))
+    out_a = np.zeros((n_rays, 3))
     out_leaf = np.full(n_rays, -1, np.int64)
     off = seg["offsets"]
     for r in range(n_rays):
@@ -440,7 +449,12 @@ def resolve(n_rays: int, seg, hit, t, nrm):
             out_t[r] = t[best]
             out_n[r] = nrm[best]
             out_leaf[r] = seg["leaf"][best]
-    return {"hit": out_hit, "t": out_t, "normal": out_n, "leaf": out_leaf}
+            if albedo is not None:
+                out_a[r] = albedo[best]
+    res = {"hit": out_hit, "t": out_t, "normal": out_n, "leaf": out_leaf}
+    if albedo is not None:
+        res["albedo"] = out_a
+    return res
 
 
 def eval_segments(o, d, t0, t1, table, layers, layout, centre, extent, n_samples: int):
@@ -477,7 +491,7 @@ def query(rays: dict, leaves: dict, table, layers, layout, n_samples: int, chunk
         _, _, tmin, tmax = rays_od(rays)
         rr = seg["ray"]
         hit = hit & (~rev | ((t > tmin[rr]) & (t <= tmax[rr])))
-    res = resolve(len(o), seg, hit, t, nrm)
+    res = resolve(len(o), seg, hit, t, nrm, decode_albedo(raw))
     res["segments"] = seg
     res["raw"] = raw
     res["seg_hit"] = hit
@@ -644,18 +658,20 @@ def moller_trumbore(o, d, v0, v1, v2):
     return hit, t, u, v
 
 
-def labels(o, d, leaf, t0, t1, tris, tri_perm, leaf_range):
+def labels(o, d, leaf, t0, t1, tris, tri_perm, leaf_range, tri_albedo=None):
     """Ground truth of the trained segment: the closest intersection among the
     leaf's own triangles with t in [t0, t1] (Sec. 4: obtained by intersecting
     the actual geometry). Equal t: the lowest position in the leaf's list.
     Returns hit (uint8), local depth (t - t0)/(t1 - t0) (0 for t1 == t0), the
     geometric normal flipped to face -d (Sec. 5.2), the hit t and margins
-    describing how close each decision was (for rounding exceptions)."""
+    describing how close each decision was (for rounding exceptions); with
+    ``tri_albedo`` ([n_tris][3]) also the hit triangle's albedo (0 on a miss)."""
     n = len(o)
     tv = tris.astype(F64)
     hit = np.zeros(n, np.uint8)
     depth = np.zeros(n)
     nrm = np.zeros((n, 3))
+    alb = np.zeros((n, 3))
     thit = np.full(n, np.inf)
     margin = np.full(n, np.inf)
     for i in range(n):
@@ -685,7 +701,12 @@ def labels(o, d, leaf, t0, t1, tris, tri_perm, leaf_range):
         if np.dot(g, d[i]) > 0:
             g = -g
         nrm[i] = g
-    return {"hit": hit, "depth": depth, "normal": nrm, "t": thit, "margin": margin}
+        if tri_albedo is not None:
+            alb[i] = np.asarray(tri_albedo, F64)[tri_perm[a + j]]
+    out = {"hit": hit, "depth": depth, "normal": nrm, "t": thit, "margin": margin}
+    if tri_albedo is not None:
+        out["albedo"] = alb
+    return out
 
 
 # ============================================================================
@@ -693,7 +714,10 @@ def labels(o, d, leaf, t0, t1, tris, tri_perm, leaf_range):
 # Sec. 6 "Neural model & training")
 # ============================================================================
 
-W_VIS, W_DIST, W_NORMAL = 2.0, 2.0, 1.0
+W_VIS, W_DIST, W_NORMAL, W_ALBEDO = 2.0, 2.0, 1.0, 1.0
+# Relative L2 (Sec. 5.2 "Auxiliary intersection data"): the squared error over
+# the prediction's own square plus this constant, the denominator held fixed.
+ALBEDO_EPS = 0.01
 
 
 def softplus(x):
@@ -701,12 +725,15 @@ def softplus(x):
     return np.maximum(x, 0.0) + np.log1p(np.exp(-np.abs(x)))
 
 
-def loss(raw, y_hit, y_depth, y_normal, valid):
+def loss(raw, y_hit, y_depth, y_normal, valid, y_albedo=None):
     """L = (1/n_valid) sum over valid rays of
          2 BCE(sigmoid(o_hit), y) + y (2 |sigmoid(o_d) - d| + (1/3) sum_j |o_nj - n_j|)
     (Sec. 5.2: BCE for visibility, L1 on local distance, L1 on the normal, the
     other losses zeroed without an intersection; combined weights 2, 2, 1).
-    BCE from the logit: softplus(o) - y o. Returns (L, per-ray terms)."""
+    BCE from the logit: softplus(o) - y o. With an albedo head (8 outputs) and
+    albedo labels the term adds, weight 1, y times the relative L2 of the
+    albedo averaged over RGB: (1/3) sum_c (s_c - a_c)^2 / (s_c^2 + 0.01),
+    s_c = sigmoid(o_{5+c}). Returns (L, per-ray terms)."""
     raw = np.asarray(raw, F64)
     y = np.asarray(y_hit, F64)
     v = np.asarray(valid, bool)
@@ -715,12 +742,18 @@ def loss(raw, y_hit, y_depth, y_normal, valid):
     dist = np.abs(sigmoid(raw[:, 1]) - np.asarray(y_depth, F64))
     nl1 = np.sum(np.abs(raw[:, 2:5] - np.asarray(y_normal, F64)), 1) / 3.0
     per = W_VIS * bce + y * (W_DIST * dist + W_NORMAL * nl1)
+    if y_albedo is not None and raw.shape[1] >= 8:
+        s = sigmoid(raw[:, 5:8])
+        rel = np.sum((s - np.asarray(y_albedo, F64)) ** 2 / (s * s + ALBEDO_EPS), 1) / 3.0
+        per = per + y * W_ALBEDO * rel
     per = np.where(v, per, 0.0)
     return float(per.sum() / nv), per
 
 
-def loss_grad(raw, y_hit, y_depth, y_normal, valid):
-    """dL/d(raw outputs) of ``loss`` (sign(0) = 0 at the L1 kinks)."""
+def loss_grad(raw, y_hit, y_depth, y_normal, valid, y_albedo=None):
+    """dL/d(raw outputs) of ``loss`` (sign(0) = 0 at the L1 kinks; the
+    relative L2's denominator is a constant, so its gradient is
+    2 (s - a) / (s^2 + 0.01) times sigmoid's derivative)."""
     raw = np.asarray(raw, F64)
     y = np.asarray(y_hit, F64)
     v = np.asarray(valid, bool).astype(F64)
@@ -731,6 +764,10 @@ def loss_grad(raw, y_hit, y_depth, y_normal, valid):
     s1 = sigmoid(raw[:, 1])
     g[:, 1] = y * W_DIST * np.sign(s1 - np.asarray(y_depth, F64)) * s1 * (1.0 - s1)
     g[:, 2:5] = y[:, None] * (W_NORMAL / 3.0) * np.sign(raw[:, 2:5] - np.asarray(y_normal, F64))
+    if y_albedo is not None and raw.shape[1] >= 8:
+        s = sigmoid(raw[:, 5:8])
+        g[:, 5:8] = (y[:, None] * (W_ALBEDO / 3.0) * 2.0 * (s - np.asarray(y_albedo, F64)) / (s * s + ALBEDO_EPS)
+                     * s * (1.0 - s))
     return g * (v / nv)[:, None]
 
 
@@ -776,7 +813,7 @@ def encode_backward(x, g_feat, n_entries: int, n_features: int, layout):
 
 
 def forward_backward(o, d, t0, t1, valid, y_hit, y_depth, y_normal, table, layers, layout,
-                     centre, extent, n_samples: int, rnd=None, scale: float = 1.0):
+                     centre, extent, n_samples: int, rnd=None, scale: float = 1.0, y_albedo=None):
     """Loss of a batch of segments and its exact gradient with respect to every
     table entry and MLP weight/bias. Returns (L, dtable, [(dW, db)], raw).
     ``rnd``/``scale``: half-precision MLP operands (``mlp_forward``,
@@ -785,8 +822,8 @@ def forward_backward(o, d, t0, t1, valid, y_hit, y_depth, y_normal, table, layer
     x = normalize_points(p, centre, extent)
     feat = encode(x, table, layout)
     raw, acts, pre = mlp_forward(feat, layers, rnd)
-    L, _ = loss(raw, y_hit, y_depth, y_normal, valid)
-    g = loss_grad(raw, y_hit, y_depth, y_normal, valid)
+    L, _ = loss(raw, y_hit, y_depth, y_normal, valid, y_albedo)
+    g = loss_grad(raw, y_hit, y_depth, y_normal, valid, y_albedo)
     g_feat, g_layers = mlp_backward(g, acts, pre, layers, rnd, scale)
     tab = np.asarray(table)
     g_tab = encode_backward(x, g_feat, tab.shape[0], tab.shape[1], layout)
@@ -904,23 +941,30 @@ def hybrid_trace(rays: dict, instances):
     """Closest hit over the instances, taken in index order: an instance's
     answer replaces the record only when it is a hit strictly closer than the
     record (equal t stays with the lower instance index). Instances are dicts:
-    {"kind": "triangles", "tris": [n, 3, 3]} or {"kind": "neural", "leaves",
-    "table", "layers", "layout", "n_samples"} (each neural instance answers
-    with ``query`` over the ray's full [tmin, tmax]). Returns the record
-    (hit, t, normal, leaf = triangle index or N-BVH leaf, inst) and every
-    instance's own answer."""
+    {"kind": "triangles", "tris": [n, 3, 3], optional "albedo": [n, 3]} or
+    {"kind": "neural", "leaves", "table", "layers", "layout", "n_samples"}
+    (each neural instance answers with ``query`` over the ray's full
+    [tmin, tmax]). Returns the record (hit, t, normal, leaf = triangle index
+    or N-BVH leaf, inst, albedo: the triangle's, the albedo head's, or 0 where
+    the answering instance has none) and every instance's own answer."""
     o, d, tmin, tmax = rays_od(rays)
     n = len(o)
     out = {"hit": np.zeros(n, np.uint8), "t": np.full(n, np.inf), "normal": np.zeros((n, 3)),
-           "leaf": np.full(n, -1, np.int64), "inst": np.full(n, -1, np.int64)}
+           "leaf": np.full(n, -1, np.int64), "inst": np.full(n, -1, np.int64), "albedo": np.zeros((n, 3))}
     answers = []
     for k, x in enumerate(instances):
         if x["kind"] == "triangles":
             a = closest_triangle_hit(o, d, tmin, tmax, x["tris"])
             ans = {"hit": a["hit"], "t": a["t"], "normal": a["normal"], "leaf": a["index"], "margin": a["margin"]}
+            alb = np.zeros((n, 3))
+            if x.get("albedo") is not None:
+                h = a["index"] >= 0
+                alb[h] = np.asarray(x["albedo"], F64)[a["index"][h]]
+            ans["albedo"] = alb
         else:
             q = query(rays, x["leaves"], x["table"], x["layers"], x["layout"], x["n_samples"])
-            ans = {"hit": q["hit"], "t": q["t"], "normal": q["normal"], "leaf": q["leaf"], "query": q}
+            ans = {"hit": q["hit"], "t": q["t"], "normal": q["normal"], "leaf": q["leaf"], "query": q,
+                   "albedo": q.get("albedo", np.zeros((n, 3)))}
         answers.append(ans)
         better = ans["hit"].astype(bool) & (ans["t"] < out["t"])
         out["hit"][better] = 1
@@ -928,6 +972,7 @@ def hybrid_trace(rays: dict, instances):
         out["normal"][better] = ans["normal"][better]
         out["leaf"][better] = ans["leaf"][better]
         out["inst"][better] = k
+        out["albedo"][better] = ans["albedo"][better]
     out["answers"] = answers
     return out
 

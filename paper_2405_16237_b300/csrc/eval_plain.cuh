@@ -18,24 +18,41 @@ constexpr int kPlainThreads = 256;
 struct Labels {
   const uint8_t* hit;
   const float *depth, *nx, *ny, *nz;
+  const float *ar, *ag, *ab;  // albedo labels (n_out >= 8), or nullptr
 };
 
 __device__ __forceinline__ float sgnf(float x) { return x > 0.0f ? 1.0f : (x < 0.0f ? -1.0f : 0.0f); }
 
+constexpr float kAlbedoEps = 1e-2f;  // relative L2: (y' - y)^2 / (y'^2 + eps), y' not differentiated
+
+// Sec. 5.2 "Auxiliary intersection data": with an albedo head (outputs 5-7,
+// sigmoid) and albedo labels alb (3 values), the term adds
+// y (1/3) sum_c (s_c - a_c)^2 / (s_c^2 + eps), s_c = sigmoid(o_{5+c}), the
+// denominator taken as a constant (relative L2), weight 1 in the combined loss.
 __device__ __forceinline__ float loss_terms(const float* o, float y, float d, float n0, float n1, float n2,
-                                            float gscale, float* g) {
+                                            const float* alb, float gscale, float* g) {
   const float x = o[0];
   const float bce = fmaxf(x, 0.0f) + log1pf(expf(-fabsf(x))) - y * x;
   const float s0 = sigmoidf_(x);
   const float s1 = sigmoidf_(o[1]);
   const float dd = s1 - d;
   const float e0 = o[2] - n0, e1 = o[3] - n1, e2 = o[4] - n2;
-  const float term = 2.0f * bce + y * (2.0f * fabsf(dd) + (fabsf(e0) + fabsf(e1) + fabsf(e2)) * (1.0f / 3.0f));
+  float term = 2.0f * bce + y * (2.0f * fabsf(dd) + (fabsf(e0) + fabsf(e1) + fabsf(e2)) * (1.0f / 3.0f));
   g[0] = gscale * 2.0f * (s0 - y);
   g[1] = gscale * y * 2.0f * sgnf(dd) * s1 * (1.0f - s1);
   g[2] = gscale * y * (1.0f / 3.0f) * sgnf(e0);
   g[3] = gscale * y * (1.0f / 3.0f) * sgnf(e1);
   g[4] = gscale * y * (1.0f / 3.0f) * sgnf(e2);
+  if (alb) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float sc = sigmoidf_(o[5 + c]);
+      const float den = sc * sc + kAlbedoEps;
+      const float diff = sc - alb[c];
+      term += y * (1.0f / 3.0f) * diff * diff / den;
+      g[5 + c] = gscale * y * (1.0f / 3.0f) * 2.0f * diff / den * sc * (1.0f - sc);
+    }
+  }
   return term;
 }
 
@@ -166,6 +183,10 @@ struct SegResult {
   float t, nx, ny, nz;
 };
 
+// Albedo head (outputs 5-7, sigmoid) of a hit into the record, when both the
+// model and the record have one.
+__device__ __forceinline__ void write_albedo(const EvalArgs& a, int ray, const float* raw);
+
 __device__ __forceinline__ SegResult decode_segment(const float* raw, float t0, float t1) {
   SegResult r;
   r.hit = raw[0] > 0.0f;
@@ -178,6 +199,17 @@ __device__ __forceinline__ SegResult decode_segment(const float* raw, float t0, 
     r.nx = 0.0f; r.ny = 0.0f; r.nz = 1.0f;
   }
   return r;
+}
+
+// Albedo of a new closest hit: sigmoid of outputs 5-7 with an albedo head,
+// 0 without one (the record may have held another instance's albedo).
+__device__ __forceinline__ void write_albedo(const EvalArgs& a, int ray, const float* raw) {
+  if (a.hits.ar) {
+    const bool head = a.n_out >= 8;
+    a.hits.ar[ray] = head ? sigmoidf_(raw[5]) : 0.0f;
+    a.hits.ag[ray] = head ? sigmoidf_(raw[6]) : 0.0f;
+    a.hits.ab[ray] = head ? sigmoidf_(raw[7]) : 0.0f;
+  }
 }
 
 // Wave-mode epilogue for one segment of ray `ray` (one lane per item, the
@@ -198,6 +230,7 @@ __device__ __forceinline__ void wave_resolve(const EvalArgs& a, bool valid, int 
       a.hits.nz[ray] = s.nz;
       a.hits.leaf[ray] = a.seg_leaf[size_t(a.wave) * size_t(a.n_rays) + size_t(ray)];
       if (a.inst_out) a.inst_out[ray] = a.inst_id;
+      write_albedo(a, ray, raw);
     }
     const int nxt = a.wave + 1;
     if (nxt < a.seg_count[ray]) {

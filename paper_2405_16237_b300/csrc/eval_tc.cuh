@@ -432,6 +432,7 @@ __device__ __forceinline__ bool pq_resolve(const EvalArgs& a, int ray, int sl, f
     a.hits.nz[ray] = s.nz;
     a.hits.leaf[ray] = a.seg_leaf[size_t(sl) * size_t(a.n_rays) + size_t(ray)];
     if (a.inst_out) a.inst_out[ray] = a.inst_id;
+    write_albedo(a, ray, raw);
   }
   return next_t0 < best;
 }
@@ -770,8 +771,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
             if (a.tr.lab.hit && ray >= 0) {
               const float inv_valid = 1.0f / float(max(1, *a.tr.n_valid));
               const float ls = a.tr.loss_scale_dev ? *a.tr.loss_scale_dev : a.tr.loss_scale;
+              float alb[3];
+              const bool has_alb = n_out >= 8 && a.tr.lab.ar;
+              if (has_alb) {
+                alb[0] = a.tr.lab.ar[ray];
+                alb[1] = a.tr.lab.ag[ray];
+                alb[2] = a.tr.lab.ab[ray];
+              }
               term = loss_terms(raw, float(a.tr.lab.hit[ray]), a.tr.lab.depth[ray], a.tr.lab.nx[ray],
-                                a.tr.lab.ny[ray], a.tr.lab.nz[ray], ls * inv_valid, g);
+                                a.tr.lab.ny[ray], a.tr.lab.nz[ray], has_alb ? alb : nullptr, ls * inv_valid, g);
             }
 #pragma unroll
             for (int j = 0; j < 8; ++j)

@@ -522,7 +522,9 @@ namespace {
 bool tri_blas_valid(const nbvh_tri_blas* b) {
   return b && b->nodes && b->n_nodes >= 1 && b->tris && b->leaf_range && b->tri_id;
 }
-bool hits_valid(const nbvh_hits& h) { return h.hit && h.t && h.nx && h.ny && h.nz && h.leaf; }
+bool hits_valid(const nbvh_hits& h) {
+  return h.hit && h.t && h.nx && h.ny && h.nz && h.leaf && (!h.ar || (h.ag && h.ab));
+}
 
 TriBlasArgs tri_args(const nbvh_tri_blas& b, const nbvh_rays& rays, const nbvh_hits& h, int32_t* inst_out,
                      int32_t inst_id, int32_t merge) {
@@ -532,6 +534,7 @@ TriBlasArgs tri_args(const nbvh_tri_blas& b, const nbvh_rays& rays, const nbvh_h
   a.tris = b.tris;
   a.leaf_range = b.leaf_range;
   a.tri_id = b.tri_id;
+  a.albedo = b.albedo;
   a.rays = ray_ptrs(rays);
   a.n = rays.n;
   a.hits = h;
@@ -859,6 +862,7 @@ struct TrainWs {
   float *t0, *t1;
   uint8_t* hit;
   float *depth, *nx, *ny, *nz;
+  float *ar, *ag, *ab;  // albedo labels, carved for n_out >= 8 only
   TrainBuffers buf;
   uint16_t *X16, *H16, *dZ16;  // tensor-core path: 16-bit operands (X16 feature-major)
   uint16_t* dZT0;              // first layer's dZ, neuron-major
@@ -891,6 +895,11 @@ TrainWs carve_train(void* base, const nbvh_model_desc* d, int64_t n, int32_t n_l
   w.nx = reinterpret_cast<float*>(take(4 * N));
   w.ny = reinterpret_cast<float*>(take(4 * N));
   w.nz = reinterpret_cast<float*>(take(4 * N));
+  if (no >= 8) {
+    w.ar = reinterpret_cast<float*>(take(4 * N));
+    w.ag = reinterpret_cast<float*>(take(4 * N));
+    w.ab = reinterpret_cast<float*>(take(4 * N));
+  }
   w.buf.X = reinterpret_cast<float*>(take(4 * N * K));
   w.buf.H = reinterpret_cast<float*>(take(4 * nh * N * Wd));
   w.buf.O = reinterpret_cast<float*>(take(4 * N * no));
@@ -1156,10 +1165,12 @@ extern "C" nbvh_status nbvh_train_labels(nbvh_rays rays, const int32_t* leaf, co
                                          const nbvh_train_scene* scene, nbvh_labels out, void* stream) {
   if (!rays_valid(rays) || !scene_valid(scene)) return NBVH_ERR_INVALID_ARG;
   if (rays.n == 0) return NBVH_OK;
-  if (!leaf || !t0 || !t1 || !out.hit || !out.depth || !out.nx || !out.ny || !out.nz) return NBVH_ERR_INVALID_ARG;
+  if (!leaf || !t0 || !t1 || !out.hit || !out.depth || !out.nx || !out.ny || !out.nz ||
+      (out.ar && (!out.ag || !out.ab)))
+    return NBVH_ERR_INVALID_ARG;
   labels_kernel<<<unsigned((rays.n + 127) / 128), 128, 0, as_stream(stream)>>>(
       ray_ptrs(rays), leaf, t0, t1, rays.n, scene->tris, scene->tri_perm, scene->leaf_range, scene->leaf_tris,
-      nullptr, out.hit, out.depth, out.nx, out.ny, out.nz);
+      nullptr, out.hit, out.depth, out.nx, out.ny, out.nz, scene->tri_albedo, out.ar, out.ag, out.ab);
   count_launches(1);
   return status_of(cudaGetLastError());
 }
@@ -1213,6 +1224,7 @@ nbvh_status forward_train_impl(const nbvh_model_desc* desc, const void* table, c
   if (rays.n == 0) return NBVH_OK;
   if (!leaf || !t0 || !t1 || !workspace || (reinterpret_cast<uintptr_t>(workspace) & 255) ||
       (labels.hit && (!labels.depth || !labels.nx || !labels.ny || !labels.nz || !n_valid)) ||
+      (labels.ar && (!labels.ag || !labels.ab)) ||
       !(loss_scale > 0.0f))
     return NBVH_ERR_INVALID_ARG;
   TrainWs w = carve_train(workspace, desc, rays.n, n_leaves);
@@ -1223,7 +1235,7 @@ nbvh_status forward_train_impl(const nbvh_model_desc* desc, const void* table, c
   cudaError_t e;
   if (desc->mlp_prec == NBVH_FP32) {
     TrainArgs a = train_args(desc, gp, table, mlp, rays, leaf, t0, t1, w);
-    a.lab = Labels{labels.hit, labels.depth, labels.nx, labels.ny, labels.nz};
+    a.lab = Labels{labels.hit, labels.depth, labels.nx, labels.ny, labels.nz, labels.ar, labels.ag, labels.ab};
     a.n_valid = n_valid;
     a.loss_scale = loss_scale;
     a.loss_scale_dev = loss_scale_dev;
@@ -1241,7 +1253,7 @@ nbvh_status forward_train_impl(const nbvh_model_desc* desc, const void* table, c
     a.tr.O = w.buf.O;
     a.tr.G = w.buf.G;
     a.tr.loss_seg = w.buf.loss_seg;
-    a.tr.lab = Labels{labels.hit, labels.depth, labels.nx, labels.ny, labels.nz};
+    a.tr.lab = Labels{labels.hit, labels.depth, labels.nx, labels.ny, labels.nz, labels.ar, labels.ag, labels.ab};
     a.tr.n_valid = n_valid;
     a.tr.loss_scale = loss_scale;
     a.tr.loss_scale_dev = loss_scale_dev;
@@ -1402,7 +1414,8 @@ extern "C" nbvh_status nbvh_train_step_weighted(const nbvh_model_desc* desc, con
     if (cudaGetLastError() != cudaSuccess) return NBVH_ERR_CUDA;
   }
   nbvh_rays ri{w.rays[0], w.rays[1], w.rays[2], w.rays[3], w.rays[4], w.rays[5], w.rays[6], w.rays[7], batch};
-  nbvh_labels lab{w.hit, w.depth, w.nx, w.ny, w.nz};
+  const bool alb = desc->n_out >= 8 && scene->tri_albedo;
+  nbvh_labels lab{w.hit, w.depth, w.nx, w.ny, w.nz, alb ? w.ar : nullptr, alb ? w.ag : nullptr, alb ? w.ab : nullptr};
   // group the rays by trained leaf: labels share a leaf's triangles per warp,
   // and the forward/backward tiles hold spatially close rays
   const unsigned g = unsigned((batch + 255) / 256);
@@ -1411,7 +1424,8 @@ extern "C" nbvh_status nbvh_train_step_weighted(const nbvh_model_desc* desc, con
   leaf_scatter_kernel<<<g, 256, 0, s>>>(w.leaf, batch, scene->n_leaves, w.cursor, w.order);
   labels_kernel<<<unsigned((batch + 127) / 128), 128, 0, s>>>(
       RayPtrs{ri.ox, ri.oy, ri.oz, ri.dx, ri.dy, ri.dz, ri.tmin, ri.tmax}, w.leaf, w.t0, w.t1, batch, scene->tris,
-      scene->tri_perm, scene->leaf_range, scene->leaf_tris, w.order, lab.hit, lab.depth, lab.nx, lab.ny, lab.nz);
+      scene->tri_perm, scene->leaf_range, scene->leaf_tris, w.order, lab.hit, lab.depth, lab.nx, lab.ny, lab.nz,
+      scene->tri_albedo, lab.ar, lab.ag, lab.ab);
   count_launches(4);
   if (cudaGetLastError() != cudaSuccess) return NBVH_ERR_CUDA;
   const void* table = opt->table_work ? opt->table_work : opt->table_master;

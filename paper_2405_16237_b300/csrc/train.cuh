@@ -172,13 +172,16 @@ __global__ void __launch_bounds__(128) labels_kernel(RayPtrs rays, const int32_t
                                                      const int32_t* __restrict__ leaf_range,
                                                      const float* __restrict__ leaf_tris,
                                                      const int32_t* __restrict__ order, uint8_t* hit,
-                                                     float* depth, float* nx, float* ny, float* nz) {
+                                                     float* depth, float* nx, float* ny, float* nz,
+                                                     const float* __restrict__ tri_albedo, float* ar, float* ag,
+                                                     float* ab) {
   const int64_t item = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (item >= n) return;
   const int64_t i = order ? int64_t(order[item]) : item;
   const int lf = leaf[i];
   uint8_t h = 0;
   float dep = 0.0f, gx = 0.0f, gy = 0.0f, gz = 0.0f;
+  int hit_j = -1;  // leaf-order position of the hit triangle
   if (lf >= 0) {
     const float ox = rays.ox[i], oy = rays.oy[i], oz = rays.oz[i];
     const float dx = rays.dx[i], dy = rays.dy[i], dz = rays.dz[i];
@@ -210,6 +213,7 @@ __global__ void __launch_bounds__(128) labels_kernel(RayPtrs rays, const int32_t
     }
     if (bj >= 0) {
       h = 1;
+      hit_j = bj;
       const float span = a1 - a0;
       dep = span > 0.0f ? (best - a0) / span : 0.0f;
       const float* T = leaf_tris ? leaf_tris + size_t(bj) * 9 : tris + size_t(tri_perm[bj]) * 9;
@@ -228,6 +232,18 @@ __global__ void __launch_bounds__(128) labels_kernel(RayPtrs rays, const int32_t
   nx[i] = gx;
   ny[i] = gy;
   nz[i] = gz;
+  if (ar) {  // albedo of the hit triangle (0 on a miss)
+    float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f;
+    if (h && tri_albedo) {
+      const int t = tri_perm[hit_j];
+      c0 = tri_albedo[3 * size_t(t)];
+      c1 = tri_albedo[3 * size_t(t) + 1];
+      c2 = tri_albedo[3 * size_t(t) + 2];
+    }
+    ar[i] = c0;
+    ag[i] = c1;
+    ab[i] = c2;
+  }
 }
 
 // Stored forward of one training batch (row i = segment of ray i).
@@ -388,8 +404,15 @@ __global__ void __launch_bounds__(kPlainThreads, 1) train_forward_plain(TrainArg
         for (int j = 0; j < n_out; ++j) o[j] = sout[j * kPlainTM + s];
         float term = 0.0f;
         if (a.lab.hit && sray[s] >= 0) {
+          float alb[3];
+          const bool has_alb = n_out >= 8 && a.lab.ar;
+          if (has_alb) {
+            alb[0] = a.lab.ar[i];
+            alb[1] = a.lab.ag[i];
+            alb[2] = a.lab.ab[i];
+          }
           term = loss_terms(o, float(a.lab.hit[i]), a.lab.depth[i], a.lab.nx[i], a.lab.ny[i], a.lab.nz[i],
-                            lscale * inv_valid, g);
+                            has_alb ? alb : nullptr, lscale * inv_valid, g);
         }
         for (int j = 0; j < n_out; ++j) a.buf.O[i * n_out + j] = o[j];
         if (a.lab.hit) {

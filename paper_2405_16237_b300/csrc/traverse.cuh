@@ -144,6 +144,11 @@ __device__ __forceinline__ int traverse_ray(const nbvh_node* __restrict__ nodes,
     out.hits.ny[r] = 0.0f;
     out.hits.nz[r] = 0.0f;
     out.hits.leaf[r] = -1;
+    if (out.hits.ar) {
+      out.hits.ar[r] = 0.0f;
+      out.hits.ag[r] = 0.0f;
+      out.hits.ab[r] = 0.0f;
+    }
   }
   return count;
 }

@@ -12,6 +12,7 @@ struct TriBlasArgs {
   const float* tris;          // [n_tris][9] vertices, leaf order
   const int32_t* leaf_range;  // [n_leaves][2] begin, end into tris
   const int32_t* tri_id;      // [n_tris] caller's index of each leaf-order triangle
+  const float* albedo;        // optional [n_tris][3] by caller index
   RayPtrs rays;
   int64_t n;
   nbvh_hits hits;
@@ -159,6 +160,12 @@ __global__ void __launch_bounds__(128) tri_trace_kernel(TriBlasArgs a) {
     a.hits.nz[r] = gz;
     a.hits.leaf[r] = bid;
     if (a.inst_out) a.inst_out[r] = a.inst_id;
+    if (a.hits.ar) {
+      const float* c = a.albedo ? a.albedo + 3 * size_t(__ldg(a.tri_id + bj)) : nullptr;
+      a.hits.ar[r] = c ? __ldg(c) : 0.0f;
+      a.hits.ag[r] = c ? __ldg(c + 1) : 0.0f;
+      a.hits.ab[r] = c ? __ldg(c + 2) : 0.0f;
+    }
   } else if (!a.merge) {
     a.hits.hit[r] = 0;
     a.hits.t[r] = __int_as_float(0x7f800000);
@@ -167,6 +174,11 @@ __global__ void __launch_bounds__(128) tri_trace_kernel(TriBlasArgs a) {
     a.hits.nz[r] = 0.0f;
     a.hits.leaf[r] = -1;
     if (a.inst_out) a.inst_out[r] = -1;
+    if (a.hits.ar) {
+      a.hits.ar[r] = 0.0f;
+      a.hits.ag[r] = 0.0f;
+      a.hits.ab[r] = 0.0f;
+    }
   }
 }
 
@@ -181,6 +193,11 @@ __global__ void __launch_bounds__(256) hits_clear_kernel(nbvh_hits h, int32_t* i
   h.nz[r] = 0.0f;
   h.leaf[r] = -1;
   if (inst_out) inst_out[r] = -1;
+  if (h.ar) {
+    h.ar[r] = 0.0f;
+    h.ag[r] = 0.0f;
+    h.ab[r] = 0.0f;
+  }
 }
 
 }  // namespace nbvh

@@ -47,8 +47,12 @@ class Rays(ctypes.Structure):
     _fields_ = [(k, c_void_p) for k in ("ox", "oy", "oz", "dx", "dy", "dz", "tmin", "tmax")] + [("n", c_int64)]
 
 
+HIT_KEYS = ("hit", "t", "nx", "ny", "nz", "leaf")
+ALBEDO_KEYS = ("ar", "ag", "ab")
+
+
 class Hits(ctypes.Structure):
-    _fields_ = [(k, c_void_p) for k in ("hit", "t", "nx", "ny", "nz", "leaf")]
+    _fields_ = [(k, c_void_p) for k in HIT_KEYS + ALBEDO_KEYS]
 
 
 class RaysOut(ctypes.Structure):
@@ -68,11 +72,14 @@ class SceneInfo(ctypes.Structure):
 class TrainScene(ctypes.Structure):
     _fields_ = [("nodes", c_void_p), ("n_nodes", c_int32), ("leaf_box", c_void_p), ("n_leaves", c_int32),
                 ("tris", c_void_p), ("tri_perm", c_void_p), ("leaf_range", c_void_p), ("leaf_tris", c_void_p),
-                ("info", SceneInfo)]
+                ("info", SceneInfo), ("tri_albedo", c_void_p)]
+
+
+LABEL_KEYS = ("hit", "depth", "nx", "ny", "nz")
 
 
 class Labels(ctypes.Structure):
-    _fields_ = [(k, c_void_p) for k in ("hit", "depth", "nx", "ny", "nz")]
+    _fields_ = [(k, c_void_p) for k in LABEL_KEYS + ALBEDO_KEYS]
 
 
 class Optim(ctypes.Structure):
@@ -93,7 +100,7 @@ class TuneResult(ctypes.Structure):
 
 class TriBlas(ctypes.Structure):
     _fields_ = [("nodes", c_void_p), ("n_nodes", c_int32), ("tris", c_void_p), ("leaf_range", c_void_p),
-                ("tri_id", c_void_p)]
+                ("tri_id", c_void_p), ("albedo", c_void_p)]
 
 
 class Instance(ctypes.Structure):
@@ -321,20 +328,28 @@ def rays_struct(rays: dict) -> Rays:
     return r
 
 
-def new_hits(n: int, device="cuda") -> dict:
+def new_hits(n: int, device="cuda", albedo: bool = False) -> dict:
+    """Device hit record of n rays; albedo=True adds the ar/ag/ab arrays."""
     torch = _torch()
-    return {"hit": torch.empty(n, dtype=torch.uint8, device=device),
-            "t": torch.empty(n, dtype=torch.float32, device=device),
-            "nx": torch.empty(n, dtype=torch.float32, device=device),
-            "ny": torch.empty(n, dtype=torch.float32, device=device),
-            "nz": torch.empty(n, dtype=torch.float32, device=device),
-            "leaf": torch.empty(n, dtype=torch.int32, device=device)}
+    h = {"hit": torch.empty(n, dtype=torch.uint8, device=device),
+         "t": torch.empty(n, dtype=torch.float32, device=device),
+         "nx": torch.empty(n, dtype=torch.float32, device=device),
+         "ny": torch.empty(n, dtype=torch.float32, device=device),
+         "nz": torch.empty(n, dtype=torch.float32, device=device),
+         "leaf": torch.empty(n, dtype=torch.int32, device=device)}
+    if albedo:
+        for k in ALBEDO_KEYS:
+            h[k] = torch.empty(n, dtype=torch.float32, device=device)
+    return h
 
 
 def hits_struct(h: dict) -> Hits:
     s = Hits()
-    for k in ("hit", "t", "nx", "ny", "nz", "leaf"):
+    for k in HIT_KEYS:
         setattr(s, k, h[k].data_ptr())
+    if "ar" in h:
+        for k in ALBEDO_KEYS:
+            setattr(s, k, h[k].data_ptr())
     return s
 
 
@@ -394,7 +409,7 @@ def query_rays(desc: ModelDesc, table, mlp, nodes, n_nodes: int, rays: dict, max
                workspace=None):
     n = rays["ox"].numel()
     if out is None:
-        out = new_hits(n, rays["ox"].device)
+        out = new_hits(n, rays["ox"].device, albedo=desc.n_out >= 8)
     need = query_workspace_size(desc, n, max_segs)
     if workspace is None:
         workspace = new_workspace(need, rays["ox"].device)
@@ -499,7 +514,7 @@ def query_rays_static(desc: ModelDesc, table, mlp, nodes, n_nodes: int, rays: di
     for callers that cannot allocate device memory (see include/nbvh.h)."""
     n = rays["ox"].numel()
     if out is None:
-        out = new_hits(n, rays["ox"].device)
+        out = new_hits(n, rays["ox"].device, albedo=desc.n_out >= 8)
     _check(lib().nbvh_query_rays_static(ctypes.byref(desc), _ptr(table), _ptr(mlp), _ptr(nodes), n_nodes,
                                         rays_struct(rays), max_segs, hits_struct(out), _stream()),
            "query_rays_static")
@@ -510,9 +525,13 @@ def query_rays_static(desc: ModelDesc, table, mlp, nodes, n_nodes: int, rays: di
 class DeviceScene:
     """Device copies of the geometry the training step reads."""
 
-    def __init__(self, tris: np.ndarray, leaves: dict, device="cuda"):
+    def __init__(self, tris: np.ndarray, leaves: dict, device="cuda", albedo: np.ndarray = None):
+        """albedo: optional [n_tris][3] RGB in [0, 1]; the labels then carry
+        the hit triangle's albedo (trained by a model with n_out = 8)."""
         torch = _torch()
         self.tris = torch.as_tensor(np.ascontiguousarray(tris, np.float32).reshape(-1, 9), device=device)
+        self.albedo = None if albedo is None else torch.as_tensor(
+            np.ascontiguousarray(albedo, np.float32).reshape(-1, 3), device=device)
         self.nodes = torch.as_tensor(leaves["nodes"], device=device)
         box = np.concatenate([leaves["leaf_lo"], leaves["leaf_hi"]], 1).astype(np.float32)
         self.leaf_box = torch.as_tensor(np.ascontiguousarray(box), device=device)
@@ -530,6 +549,7 @@ class DeviceScene:
         sc.tri_perm = self.tri_perm.data_ptr()
         sc.leaf_range = self.leaf_range.data_ptr()
         sc.leaf_tris = self.leaf_tris.data_ptr()
+        sc.tri_albedo = self.albedo.data_ptr() if self.albedo is not None else None
         inf = leaves["info"]
         for i in range(3):
             sc.info.lo[i] = float(inf["lo"][i])
@@ -557,16 +577,17 @@ def train_rays(mode: int, seed: int, step: int, scene: DeviceScene, n: int):
     return rays, leaf, t0, t1, n_valid
 
 
-def new_labels(n: int, device="cuda") -> dict:
+def new_labels(n: int, device="cuda", albedo: bool = False) -> dict:
     torch = _torch()
+    keys = ("depth", "nx", "ny", "nz") + (ALBEDO_KEYS if albedo else ())
     return {"hit": torch.empty(n, dtype=torch.uint8, device=device),
-            **{k: torch.empty(n, dtype=torch.float32, device=device) for k in ("depth", "nx", "ny", "nz")}}
+            **{k: torch.empty(n, dtype=torch.float32, device=device) for k in keys}}
 
 
 def labels_struct(lab) -> Labels:
     s = Labels()
     if lab is not None:
-        for k in ("hit", "depth", "nx", "ny", "nz"):
+        for k in LABEL_KEYS + (ALBEDO_KEYS if "ar" in lab else ()):
             setattr(s, k, lab[k].data_ptr())
     return s
 
@@ -574,7 +595,7 @@ def labels_struct(lab) -> Labels:
 def train_labels(rays: dict, leaf, t0, t1, scene: DeviceScene, out=None):
     n = rays["ox"].numel()
     if out is None:
-        out = new_labels(n, rays["ox"].device)
+        out = new_labels(n, rays["ox"].device, albedo=scene.albedo is not None)
     _check(lib().nbvh_train_labels(rays_struct(rays), _ptr(leaf), _ptr(t0), _ptr(t1), ctypes.byref(scene.struct),
                                    labels_struct(out), _stream()), "train_labels")
     return out
@@ -718,9 +739,11 @@ class DeviceTriBlas:
     """Device copy of a triangle BLAS: nodes, leaf-order triangles, leaf
     ranges and the caller index of every leaf-order triangle."""
 
-    def __init__(self, tris: np.ndarray, blas: dict, device="cuda"):
+    def __init__(self, tris: np.ndarray, blas: dict, device="cuda", albedo: np.ndarray = None):
         torch = _torch()
         t = np.ascontiguousarray(tris, np.float32).reshape(-1, 9)
+        self.albedo = None if albedo is None else torch.as_tensor(
+            np.ascontiguousarray(albedo, np.float32).reshape(-1, 3), device=device)
         self.nodes = torch.as_tensor(blas["nodes"], device=device)
         self.tris = torch.as_tensor(np.ascontiguousarray(t[blas["tri_perm"]]), device=device)
         self.leaf_range = torch.as_tensor(np.ascontiguousarray(blas["leaf_range"], np.int32), device=device)
@@ -731,13 +754,14 @@ class DeviceTriBlas:
         s.tris = self.tris.data_ptr()
         s.leaf_range = self.leaf_range.data_ptr()
         s.tri_id = self.tri_id.data_ptr()
+        s.albedo = self.albedo.data_ptr() if self.albedo is not None else None
         self.struct = s
 
 
 def trace_triangles(blas: DeviceTriBlas, rays: dict, out=None):
     n = rays["ox"].numel()
     if out is None:
-        out = new_hits(n, rays["ox"].device)
+        out = new_hits(n, rays["ox"].device, albedo=blas.albedo is not None)
     _check(lib().nbvh_trace_triangles(ctypes.byref(blas.struct), rays_struct(rays), hits_struct(out), _stream()),
            "trace_triangles")
     return out
@@ -783,7 +807,9 @@ def hybrid_trace(instances, rays: dict, out=None, inst_out=None, workspace=None)
     n = rays["ox"].numel()
     dev = rays["ox"].device
     if out is None:
-        out = new_hits(n, dev)
+        alb = any((x.kind == BLAS_NEURAL and x.desc.n_out >= 8) or (x.kind == BLAS_TRIANGLES and x.tri.albedo)
+                  for x in instances)
+        out = new_hits(n, dev, albedo=alb)
     if inst_out is None:
         inst_out = torch.empty(n, dtype=torch.int32, device=dev)
     arr = instance_array(instances)

@@ -299,14 +299,28 @@ def init_mlp(dims, seed: int, gain: float = 1.0):
     return layers
 
 
-def random_labels(n: int, seed: int, hit_fraction: float = 0.6) -> dict:
-    """Synthetic training labels: hit bit, local depth in [0, 1], unit normal."""
+def random_labels(n: int, seed: int, hit_fraction: float = 0.6, albedo: bool = False) -> dict:
+    """Synthetic training labels: hit bit, local depth in [0, 1], unit normal,
+    and with albedo=True an RGB albedo in [0, 1] (ar, ag, ab)."""
     rng = np.random.default_rng(seed)
     hit = (rng.uniform(size=n) < hit_fraction).astype(np.uint8)
     depth = rng.uniform(0.0, 1.0, n).astype(np.float32)
     nrm = _sphere_dir(rng, n).astype(np.float32)
-    return {"hit": hit, "depth": depth, "nx": nrm[:, 0].copy(), "ny": nrm[:, 1].copy(),
-            "nz": nrm[:, 2].copy()}
+    out = {"hit": hit, "depth": depth, "nx": nrm[:, 0].copy(), "ny": nrm[:, 1].copy(),
+           "nz": nrm[:, 2].copy()}
+    if albedo:
+        a = rng.uniform(0.0, 1.0, (n, 3)).astype(np.float32)
+        out.update(ar=a[:, 0].copy(), ag=a[:, 1].copy(), ab=a[:, 2].copy())
+    return out
+
+
+def tri_albedo(tris: np.ndarray, seed: int = SEED_BASE + 11) -> np.ndarray:
+    """Per-triangle RGB albedo [n_tris][3] float32 in [0.05, 0.95]: fBm of the
+    triangle's centroid, one seed per channel, so that nearby triangles have
+    similar colours (a texture-like signal the albedo head can learn)."""
+    c = np.asarray(tris, np.float64).reshape(-1, 3, 3).mean(axis=1)
+    rgb = np.stack([fbm(c, seed + k, base_freq=3.0) for k in range(3)], axis=1)
+    return (0.5 + 0.45 * np.clip(rgb * 1.6, -1.0, 1.0)).astype(np.float32)
 
 
 # ----------------------------------------------------------------------------

@@ -728,3 +728,148 @@ def test_reverse_inside_decode_window():
     assert np.allclose(p[0, :, 0], [0.25, -0.25, -0.75, -1.25])
     hit, t, _ = O.decode(np.array([[3.0, 0.0, 0, 0, 1]]), np.array([0.5]), np.array([-1.5]))
     assert hit[0] and t[0] == 0.5 - 2.0 * 0.5  # sigmoid(0) = 1/2: t = -0.5, behind the origin
+
+
+# ---------------------------------------------------------------- albedo head (Sec. 5.2 auxiliary data)
+def _logit(p):
+    return math.log(p / (1.0 - p))
+
+
+def test_albedo_relative_l2_closed_form():
+    """Predicted albedo (0.2, 0.5, 0.8) against labels (0.1, 0.5, 1.0) on a
+    hit ray: (0.01/0.05 + 0 + 0.04/0.65)/3 by hand; a missed ray adds nothing;
+    a five-output model ignores albedo labels."""
+    raw = np.zeros((2, 8))
+    raw[:, 5:8] = [_logit(0.2), 0.0, _logit(0.8)]
+    yn = np.array([[0.0, 0.0, 1.0], [1, 1, 1]])
+    ya = np.array([[0.1, 0.5, 1.0], [0.9, 0.9, 0.9]])
+    L8, per8 = O.loss(raw, [1, 0], [0.25, 0.9], yn, [True, True], ya)
+    L5, per5 = O.loss(raw[:, :5], [1, 0], [0.25, 0.9], yn, [True, True], ya)
+    rel = (0.01 / 0.05 + 0.0 + 0.04 / 0.65) / 3.0
+    assert abs((per8[0] - per5[0]) - rel) < 1e-14
+    assert per8[1] == per5[1]
+    assert abs((L8 - L5) - rel / 2) < 1e-14
+    assert np.all(O.loss_grad(raw[:, :5], [1, 0], [0.25, 0.9], yn, [True, True], ya)
+                  == O.loss_grad(raw[:, :5], [1, 0], [0.25, 0.9], yn, [True, True]))
+
+
+def test_albedo_gradient_near_the_target_matches_differences():
+    """The relative L2 holds its denominator constant. Near s = a the constant
+    and the differentiated denominator agree to first order (their ratio is
+    1 - 2 s (s - a) / (s^2 + 0.01)), so central differences of the full loss
+    pin the gradient's factor 2, sign, 1/3 mean, 1/(s^2 + 0.01) scale and
+    sigmoid derivative there; away from it they differ by that known term. The
+    gradient vanishes at s = a and for rays without a hit."""
+    rng = np.random.default_rng(90)
+    S = 20
+    raw = rng.normal(0, 1.5, (S, 8))
+    y = (rng.uniform(size=S) < 0.7).astype(float)
+    y[0], y[1] = 1.0, 0.0
+    yd = rng.uniform(size=S)
+    yn = rng.normal(size=(S, 3))
+    valid = np.ones(S, bool)
+    s = O.sigmoid(raw[:, 5:8])
+    delta = rng.choice([-1.0, 1.0], (S, 3)) * rng.uniform(5e-5, 2e-4, (S, 3))
+    ya = s + delta
+    g = O.loss_grad(raw, y, yd, yn, valid, ya)
+    h = 1e-6
+    for i in range(S):
+        for c in range(3):
+            rp, rm = raw.copy(), raw.copy()
+            rp[i, 5 + c] += h
+            rm[i, 5 + c] -= h
+            fd = (O.loss(rp, y, yd, yn, valid, ya)[0] - O.loss(rm, y, yd, yn, valid, ya)[0]) / (2 * h)
+            if y[i] == 0:
+                assert g[i, 5 + c] == 0.0
+            else:
+                assert abs(fd - g[i, 5 + c]) <= 2e-3 * abs(g[i, 5 + c]) + 1e-12, (i, c, fd, g[i, 5 + c])
+    # far from the target: the finite difference also sees the denominator
+    ya2 = np.clip(s + 0.3, 0, 1)
+    g2 = O.loss_grad(raw, y, yd, yn, valid, ya2)
+    i, c = 0, 0
+    rp, rm = raw.copy(), raw.copy()
+    rp[i, 5 + c] += h
+    rm[i, 5 + c] -= h
+    fd = (O.loss(rp, y, yd, yn, valid, ya2)[0] - O.loss(rm, y, yd, yn, valid, ya2)[0]) / (2 * h)
+    sc, ac = s[i, c], ya2[i, c]
+    den = sc * sc + O.ALBEDO_EPS
+    denom_term = -(sc - ac) ** 2 * 2 * sc / den ** 2 * sc * (1 - sc) / 3.0 / S
+    assert abs(fd - (g2[i, 5 + c] + denom_term)) <= 1e-7 * abs(fd) + 1e-12
+    # stationary at the target
+    g3 = O.loss_grad(raw, y, yd, yn, valid, s)
+    assert np.all(g3[:, 5:8] == 0.0)
+
+
+def test_labels_albedo_is_the_hit_triangles():
+    """Label albedo encodes the triangle index; decoding it gives a triangle of
+    the trained leaf whose own Moller-Trumbore t is the label's t, and misses
+    carry 0 (brute force per segment)."""
+    tris = W.scene_random_tris(600, seed=14)
+    lv = O.build_leaves(tris, 12)
+    rays = W.camera_rays(14, 14, seed=15)
+    seg = O.ray_segments(rays, lv["leaf_lo"], lv["leaf_hi"])
+    o, d, _, _ = O.rays_od(rays)
+    rr = seg["ray"]
+    n = len(tris)
+    alb = np.stack([(np.arange(n) + 1) / (n + 1), np.full(n, 0.25), np.full(n, 0.75)], 1)
+    lab = O.labels(o[rr], d[rr], seg["leaf"], seg["t0"], seg["t1"], tris, lv["tri_perm"], lv["leaf_range"], alb)
+    h = lab["hit"] == 1
+    assert h.sum() > 15 and np.all(lab["albedo"][~h] == 0.0)
+    tv = tris.astype(np.float64)
+    for k in np.nonzero(h)[0]:
+        j = int(round(lab["albedo"][k, 0] * (n + 1))) - 1
+        a, b = lv["leaf_range"][seg["leaf"][k]]
+        assert j in set(lv["tri_perm"][a:b].tolist())
+        hit, t, _, _ = O.moller_trumbore(o[rr[k]][None], d[rr[k]][None], tv[j:j + 1, 0], tv[j:j + 1, 1],
+                                         tv[j:j + 1, 2])
+        assert hit[0] and t[0] == lab["t"][k]
+        assert np.all(lab["albedo"][k, 1:] == [0.25, 0.75])
+
+
+def test_albedo_head_leaves_geometry_and_resolves_with_the_hit():
+    """Adding three albedo outputs leaves hit, t, normal and leaf unchanged.
+    With the albedo rows of the output layer zero and biases b, every hit ray
+    reads sigmoid(b) and every miss 0 (closed form); with random rows the
+    albedo is that of the segment whose t the ray reports."""
+    tris = W.scene_random_tris(400, seed=21)
+    lv = O.build_leaves(tris, 8)
+    rays = W.camera_rays(12, 12, seed=22)
+    lay = O.level_layout(4, 4, 2.0, 10)
+    rng = np.random.default_rng(23)
+    tab = rng.uniform(-1, 1, (lay["total"], 2))
+    layers5 = W.init_mlp([4 * 4 * 2, 16, 5], 24, gain=2.0)
+    layers5[-1][1][0] += 0.3      # more predicted hits
+    W8 = np.concatenate([layers5[-1][0], np.zeros((3, 16))], 0)
+    b8 = np.concatenate([layers5[-1][1], [-1.0, 0.0, 2.0]])
+    q5 = O.query(rays, lv, tab, layers5, lay, 4)
+    q8 = O.query(rays, lv, tab, layers5[:-1] + [(W8, b8)], lay, 4)
+    for k in ("hit", "t", "normal", "leaf"):
+        assert np.array_equal(q5[k], q8[k]), k
+    h = q8["hit"] == 1
+    assert 10 < h.sum() < len(h)
+    expect = 1.0 / (1.0 + np.exp(-np.array([-1.0, 0.0, 2.0])))
+    assert np.allclose(q8["albedo"][h], expect, rtol=0, atol=1e-15)
+    assert np.all(q8["albedo"][~h] == 0.0)
+    Wr = np.concatenate([layers5[-1][0], rng.normal(0, 1, (3, 16))], 0)
+    qr = O.query(rays, lv, tab, layers5[:-1] + [(Wr, b8)], lay, 4)
+    seg = qr["segments"]
+    for r in np.nonzero(qr["hit"] == 1)[0]:
+        js = [j for j in range(seg["offsets"][r], seg["offsets"][r + 1])
+              if qr["seg_hit"][j] and qr["seg_t"][j] == qr["t"][r]]
+        assert np.array_equal(qr["albedo"][r], O.sigmoid(qr["raw"][js[0], 5:8]))
+
+
+def test_hybrid_albedo_follows_the_answering_instance():
+    """In the two-level trace the record's albedo is the triangle's where a
+    triangle instance answers and 0 where an instance without albedo does."""
+    tris = W.scene_random_tris(300, seed=31, edge=0.25)
+    a = tris[:150]
+    b = tris[150:]
+    alb = np.random.default_rng(32).uniform(0, 1, (150, 3))
+    rays = W.camera_rays(16, 16, seed=33)
+    out = O.hybrid_trace(rays, [{"kind": "triangles", "tris": a, "albedo": alb}, {"kind": "triangles", "tris": b}])
+    ia = out["inst"] == 0
+    ib = out["inst"] == 1
+    assert ia.sum() > 5 and ib.sum() > 5
+    assert np.array_equal(out["albedo"][ia], alb[out["leaf"][ia]])
+    assert np.all(out["albedo"][ib] == 0.0) and np.all(out["albedo"][out["inst"] < 0] == 0.0)
