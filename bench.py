@@ -57,6 +57,7 @@ def parse():
                    help="training-step budget of the error-driven-cut comparison (0: skip it)")
     p.add_argument("--lod-steps", type=int, default=1200,
                    help="training steps of the level-of-detail measurement (0: skip it)")
+    p.add_argument("--no-albedo", action="store_true", help="skip the albedo-head measurement")
     p.add_argument("--no-autotune", action="store_true",
                    help="keep the library's default query schedule (no autotuning before the timed region)")
     p.add_argument("--quick", action="store_true",
@@ -247,15 +248,16 @@ class GpuWorkload:
         self.flush_buf.fill_(1)
 
 
-def time_training(spec, tris, wl, steps, warmup, batch=1 << 18):
+def time_training(spec, tris, wl, steps, warmup, batch=1 << 18, desc=None, mlp=None, scene=None):
     """Training steps (2^18 rays each) on the same scene and model, FP16
-    tensor-core compute on FP32 masters, Adam lr 1e-2, dynamic loss scale."""
+    tensor-core compute on FP32 masters, Adam lr 1e-2, dynamic loss scale.
+    desc/mlp/scene replace the workload's model and the plain scene."""
     import torch
     from paper_2405_16237_b300 import nbvh as B
-    scene = B.DeviceScene(tris, wl.leaves)
-    desc = B.with_mlp_prec(wl.desc, B.FP16)
-    opt = B.Optimizer(desc, torch.as_tensor(wl.table_np.astype(np.float32)).cuda(), wl.mlp.clone(),
-                      loss_scale=32768.0)
+    scene = scene if scene is not None else B.DeviceScene(tris, wl.leaves)
+    desc = B.with_mlp_prec(desc if desc is not None else wl.desc, B.FP16)
+    opt = B.Optimizer(desc, torch.as_tensor(wl.table_np.astype(np.float32)).cuda(),
+                      (mlp if mlp is not None else wl.mlp).clone(), loss_scale=32768.0)
     ws = B.new_workspace(B.train_workspace_size(desc, batch, scene.n_leaves))
     loss = torch.zeros(1, dtype=torch.float64, device="cuda")
     step = 0
@@ -281,6 +283,59 @@ def time_training(spec, tris, wl, steps, warmup, batch=1 << 18):
     return {"value": batch / (ms * 1e-3), "unit": "rays/s", "batch": batch, "ms_per_step": ms, "steps": steps,
             "dtype": "f16 compute, f32 masters", "loss_after_warmup": first, "loss_last": float(loss.item()),
             "loss_scale": float(opt.loss_scale.item())}
+
+
+def time_albedo(args, world, spec, tris, wl):
+    """The icosphere step with the albedo head (8 outputs, FP16 tensor cores):
+    both queries write albedo into their hit records; and training steps with
+    per-triangle albedo labels (smooth fBm colours) and the relative L2 term."""
+    import torch
+    from dataclasses import replace
+    from paper_2405_16237_b300 import nbvh as B
+    from paper_2405_16237_b300 import workloads as W
+    cfg = replace(spec.model, n_out=8)
+    info = wl.leaves["info"]
+    desc = B.model_desc(cfg, B.FP16, B.FP16, info["centre"], info["extent"])
+    mlp = torch.as_tensor(B.pack_mlp(W.init_mlp(cfg.mlp_dims(), SEED + 22))).cuda()
+    h1 = B.new_hits(wl.n, albedo=True)
+    h2 = B.new_hits(wl.n, albedo=True)
+
+    def step():
+        B.query_rays(desc, wl.table, mlp, wl.nodes, wl.leaves["n_nodes"], wl.rays, wl.max_segs, out=h1,
+                     workspace=wl.ws1)
+        B.bounce_rays(wl.rays, h1, SEED + 3, out=wl.rays2)
+        B.query_rays(desc, wl.table, mlp, wl.nodes, wl.leaves["n_nodes"], wl.rays2, wl.max_segs, out=h2,
+                     workspace=wl.ws2)
+
+    step()
+    torch.cuda.synchronize()
+    g = B.Graph.record(step)
+    for _ in range(args.warmup):
+        g.launch()
+    torch.cuda.synchronize()
+    total = 0.0
+    for _ in range(args.steps):
+        wl.flush()
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record()
+        g.launch()
+        e.record()
+        e.synchronize()
+        total += s.elapsed_time(e)
+    if B.device_status() != 0:
+        raise RuntimeError("device status after the albedo query")
+    ms = dist_max(total, world) / args.steps
+    rays = wl.n + int(h1["hit"].sum().item())
+    a = torch.stack([h1["ar"], h1["ag"], h1["ab"]], 1)[h1["hit"] > 0]
+    out = {"query": {"value": world * rays / (ms * 1e-3) / 1e6, "unit": "Mrays/s", "ms_per_step": ms,
+                     "rays_per_step": rays, "albedo_mean_on_hits": a.float().mean(0).tolist()}}
+    if args.train_steps > 0:
+        scene = B.DeviceScene(tris, wl.leaves, albedo=W.tri_albedo(tris))
+        tr = time_training(spec, tris, wl, args.train_steps, 3, desc=desc, mlp=mlp, scene=scene)
+        tr["value"] = dist_max_rate(tr["value"], world)
+        out["train"] = tr
+    return out
 
 
 def oracle_train_sample(spec, tris, n=256):
@@ -958,6 +1013,9 @@ def run_gpu(args, world, rank, spec, tris, rays_np):
     # the hybrid two-level scene (16 neural assets + 500,000 classical triangles)
     hybrid = time_hybrid(args, world) if args.hybrid_frames > 0 else None
 
+    # the same step and training with the albedo head (8 outputs)
+    albedo = time_albedo(args, world, spec, tris, wl) if not args.no_albedo else None
+
     # end to end through the public API with host buffers (graph step between the copies)
     wl.e2e_pipelined(d16, args.warmup)
     e2e_ms = dist_max(wl.e2e_pipelined(d16, args.steps), world) / args.steps
@@ -1005,6 +1063,7 @@ def run_gpu(args, world, rank, spec, tris, rays_np):
             "cut_optimization": cutcmp,
             "levels_of_detail": lod,
             "hybrid": hybrid,
+            "albedo_head": albedo,
             "fp32_plain": {"value": world * rays_step / (ms32 * 1e-3) / 1e6, "ms_per_step": ms32},
             "bf16_tc": {"value": world * rays_step / (msbf * 1e-3) / 1e6, "ms_per_step": msbf},
             "roofline": roof,
