@@ -11,7 +11,7 @@
 namespace nbvh {
 
 constexpr int kTcM = 128;          // segments per tile = MMA M = TMEM lanes
-constexpr int kTcThreads = 1024;   // 32 warps: all gather; 4 lane quarters x 8 column groups in epilogues
+constexpr int kTcThreads = 512;    // 16 warps: all gather; 4 lane quarters x 4 column groups in epilogues
 constexpr long long kWaitCycles = 4000000000LL;  // bounded mbarrier wait (~2 s)
 
 // ---------------------------------------------------------------- PTX wrappers
@@ -442,6 +442,90 @@ __global__ void pq_init_kernel(const int32_t* __restrict__ qlen0, PQueue q) {
   *q.reserved = (unsigned long long)(*qlen0);
 }
 
+// The four corners of the cell of level l at (x, y, z) whose x offset is xb:
+// table indices (level-relative) for (y, z) offsets (0,0), (1,0), (0,1), (1,1)
+// and the matching trilinear weights.
+__device__ __forceinline__ void level_xhalf(const GridParams& gp, int l, const float* p, int xb, uint32_t* idx,
+                                            float* w) {
+  const int N = gp.res[l];
+  int cx, cy, cz;
+  float fx, fy, fz;
+  axis_cell(p[0], N, cx, fx);
+  axis_cell(p[1], N, cy, fy);
+  axis_cell(p[2], N, cz, fz);
+  const float wx = xb ? fx : 1.0f - fx;
+  const float wy[2] = {1.0f - fy, fy};
+  const float wz[2] = {1.0f - fz, fz};
+  if (gp.dense[l]) {
+    const uint32_t n1 = static_cast<uint32_t>(N) + 1u;
+    const uint32_t base = static_cast<uint32_t>(cx + xb) + static_cast<uint32_t>(cy) * n1 +
+                          static_cast<uint32_t>(cz) * n1 * n1;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) idx[k] = base + (k & 1) * n1 + ((k >> 1) & 1) * n1 * n1;
+  } else {
+    const uint32_t hx = static_cast<uint32_t>(cx + xb);
+    const uint32_t hy = static_cast<uint32_t>(cy) * kHashP1;
+    const uint32_t hz = static_cast<uint32_t>(cz) * kHashP2;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint32_t b = (k & 1) ? hy + kHashP1 : hy;
+      const uint32_t d = (k & 2) ? hz + kHashP2 : hz;
+      idx[k] = (hx ^ b ^ d) & gp.hash_mask;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) w[k] = wx * wy[k & 1] * wz[(k >> 1) & 1];
+}
+
+// Partial features (x-offset xb corners only) of NL levels from l0 at two
+// points: all 8 NL corner loads are issued before any is consumed. Invalid
+// points contribute zeros.
+template <typename T, int NL>
+__device__ __forceinline__ void encode_xhalf(const GridParams& gp, const T* __restrict__ table, int l0,
+                                             const float* p0, const float* p1, bool v0, bool v1, int xb,
+                                             float* out0, float* out1) {
+  uint32_t raw[2][NL][4];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const float* p = h ? p1 : p0;
+    const bool v = h ? v1 : v0;
+#pragma unroll
+    for (int q = 0; q < NL; ++q) {
+      uint32_t idx[4];
+      float w[4];
+      level_xhalf(gp, l0 + q, p, xb, idx, w);
+      const uint32_t* tab = reinterpret_cast<const uint32_t*>(table + size_t(gp.offset[l0 + q]) * 2);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) raw[h][q][k] = v ? __ldg(tab + idx[k]) : 0u;
+    }
+  }
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const float* p = h ? p1 : p0;
+    float* out = h ? out1 : out0;
+#pragma unroll
+    for (int q = 0; q < NL; ++q) {
+      uint32_t idx[4];
+      float w[4];
+      level_xhalf(gp, l0 + q, p, xb, idx, w);  // weights recomputed (indices unused)
+      float a0 = 0.0f, a1 = 0.0f;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        float2 v;
+        if constexpr (std::is_same<T, __half>::value) {
+          v = __half22float2(*reinterpret_cast<const __half2*>(&raw[h][q][k]));
+        } else {
+          v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&raw[h][q][k]));
+        }
+        a0 = fmaf(w[k], v.x, a0);
+        a1 = fmaf(w[k], v.y, a1);
+      }
+      out[2 * q] = a0;
+      out[2 * q + 1] = a1;
+    }
+  }
+}
+
 // MODE 0: list of segments -> raw outputs; 1: query -> resolve + next segment
 // queued (one launch per segment slot, or with a.pq.ring set one persistent
 // launch draining the queue); 2: training forward (one segment per ray) ->
@@ -608,8 +692,51 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
     };
 
     // ---- encode into TMEM: warp w owns rows 32 (w % 4) + lane and samples
-    // w / 4, w / 4 + 8, ...; lanes = consecutive rows (consecutive queue items).
-    for (int k = cgroup; k < N; k += kGroups) {
+    // w / 4, w / 4 + kGroups, ...; lanes = consecutive rows (consecutive queue items),
+    // or, for 4-byte entries, pairs of lanes sharing the cells of two rows.
+    constexpr bool kSplitX = F == 2 && sizeof(T) == 2;  // 4-byte entries: x-corner lane split
+    if constexpr (kSplitX) {
+      if (chunked) {
+        // Lanes i and i ^ 16 share cells: lane i loads the four corners with
+        // x bit (i >> 4) of rows 32q + (i & 15) and 32q + 16 + (i & 15), so one
+        // warp request fetches both x-neighbours of 16 cells (one 128-byte
+        // line almost always) instead of 32 cells' corners with one x bit.
+        // Each lane then adds its partner's partial sums for its own row.
+        const int xb = lane >> 4;
+        const int r0 = quarter * 32 + (lane & 15), r1 = r0 + 16;
+        const int ray0 = sray[r0], ray1 = sray[r1];
+        for (int k = cgroup; k < N; k += kGroups) {
+          float p0[3] = {0.0f, 0.0f, 0.0f}, p1[3] = {0.0f, 0.0f, 0.0f};
+          if (ray0 >= 0)
+            sample_point(a.gp, a.rays.ox[ray0], a.rays.oy[ray0], a.rays.oz[ray0], a.rays.dx[ray0],
+                         a.rays.dy[ray0], a.rays.dz[ray0], st0[r0], st1[r0], k, p0[0], p0[1], p0[2]);
+          if (ray1 >= 0)
+            sample_point(a.gp, a.rays.ox[ray1], a.rays.oy[ray1], a.rays.oz[ray1], a.rays.dx[ray1],
+                         a.rays.dy[ray1], a.rays.dz[ray1], st0[r1], st1[r1], k, p1[0], p1[1], p1[2]);
+          const uint32_t col0 = uint32_t(k * L * F) / 2u;
+          for (int l0 = 0; l0 < L; l0 += 4) {
+            float h0[8], h1[8];  // partial features of rows r0 and r1 over this lane's x bit
+            encode_xhalf<T, 4>(a.gp, table, l0, p0, p1, ray0 >= 0, ray1 >= 0, xb, h0, h1);
+            uint32_t pk[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              // send the partner the row it owns (r1 for lanes 0-15, r0 for 16-31)
+              const float s0 = xb ? h0[2 * i] : h1[2 * i], s1 = xb ? h0[2 * i + 1] : h1[2 * i + 1];
+              const float g0 = __shfl_xor_sync(0xffffffffu, s0, 16), g1 = __shfl_xor_sync(0xffffffffu, s1, 16);
+              const float m0 = xb ? h1[2 * i] : h0[2 * i], m1 = xb ? h1[2 * i + 1] : h0[2 * i + 1];
+              pk[i] = pack2<BF16>(m0 + g0, m1 + g1);
+            }
+            if (x16) {
+#pragma unroll
+              for (int i = 0; i < 4; ++i) store_x(2 * int(col0) + l0 * F + 2 * i, pk[i]);
+            }
+            __syncwarp();
+            tmem_st4(t_a + col0 + uint32_t(l0 * F) / 2u, pk);
+          }
+        }
+      }
+    }
+    for (int k = cgroup; k < N && !(kSplitX && chunked); k += kGroups) {
       const int ray = sray[row];
       const bool valid = ray >= 0;
       float x = 0.0f, y = 0.0f, z = 0.0f;
@@ -622,8 +749,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
           float v[8];
           if (valid) {
             if constexpr (LPC % 2 == 0) {
+              if constexpr (LPC == 4) {
+                encode_levels<T, F, 4>(a.gp, table, l0, x, y, z, v);
+              } else {
 #pragma unroll
-              for (int q = 0; q < LPC; q += 2) encode_levels<T, F, 2>(a.gp, table, l0 + q, x, y, z, v + q * F);
+                for (int q = 0; q < LPC; q += 2) encode_levels<T, F, 2>(a.gp, table, l0 + q, x, y, z, v + q * F);
+              }
             } else {
               encode_levels<T, F, LPC>(a.gp, table, l0, x, y, z, v);
             }

@@ -166,10 +166,12 @@ __device__ __forceinline__ float sample_u(int k, int n_samples) {
 __device__ __forceinline__ void sample_point_u(const GridParams& gp, float ox, float oy, float oz, float dx,
                                                float dy, float dz, float t0, float t1, float u, float& x,
                                                float& y, float& z) {
-  const float t = t0 + u * (t1 - t0);
-  x = __saturatef((ox + t * dx - gp.centre[0]) * gp.inv_extent + 0.5f);
-  y = __saturatef((oy + t * dy - gp.centre[1]) * gp.inv_extent + 0.5f);
-  z = __saturatef((oz + t * dz - gp.centre[2]) * gp.inv_extent + 0.5f);
+  // explicit roundings: every inlined copy computes the same bits, so a row's
+  // features do not depend on where the kernel evaluates it
+  const float t = __fmaf_rn(u, __fsub_rn(t1, t0), t0);
+  x = __saturatef(__fmaf_rn(__fsub_rn(__fmaf_rn(t, dx, ox), gp.centre[0]), gp.inv_extent, 0.5f));
+  y = __saturatef(__fmaf_rn(__fsub_rn(__fmaf_rn(t, dy, oy), gp.centre[1]), gp.inv_extent, 0.5f));
+  z = __saturatef(__fmaf_rn(__fsub_rn(__fmaf_rn(t, dz, oz), gp.centre[2]), gp.inv_extent, 0.5f));
 }
 
 __device__ __forceinline__ void sample_point(const GridParams& gp, float ox, float oy, float oz,
@@ -232,9 +234,9 @@ struct Corners {
 // Cell index and fraction along one axis: cell = min(floor(x N), N - 1),
 // frac = x N - cell (x in [0, 1]).
 __device__ __forceinline__ void axis_cell(float x, int N, int& c, float& f) {
-  const float p = x * static_cast<float>(N);
+  const float p = __fmul_rn(x, static_cast<float>(N));  // no contraction: the same bits at every call site
   c = min(static_cast<int>(p), N - 1);  // p >= 0: truncation = floor
-  f = p - static_cast<float>(c);
+  f = __fsub_rn(p, static_cast<float>(c));
 }
 
 __device__ __forceinline__ void axis_cell(FF x, int N, int& c, float& f) {
@@ -352,20 +354,27 @@ __device__ __forceinline__ void encode_levels(const GridParams& gp, const T* __r
                                               P y, P z, float* out) {
   if constexpr (F * sizeof(T) == 4 && sizeof(T) == 2) {
     uint32_t raw[NL][8];
-    float fr[NL][3];
 #pragma unroll
     for (int q = 0; q < NL; ++q) {
       uint32_t idx[8];
-      level_index(gp, l0 + q, x, y, z, idx, fr[q]);
+      float fr[3];
+      level_index(gp, l0 + q, x, y, z, idx, fr);
       const uint32_t* tab = reinterpret_cast<const uint32_t*>(table + gp.offset[l0 + q] * F);
 #pragma unroll
       for (int k = 0; k < 8; ++k) raw[q][k] = __ldg(tab + idx[k]);
     }
 #pragma unroll
     for (int q = 0; q < NL; ++q) {
-      const float wx[2] = {1.0f - fr[q][0], fr[q][0]};
-      const float wy[2] = {1.0f - fr[q][1], fr[q][1]};
-      const float wz[2] = {1.0f - fr[q][2], fr[q][2]};
+      // cell fractions recomputed here rather than held while the loads are in flight
+      const int N = gp.res[l0 + q];
+      int c;
+      float fr[3];
+      axis_cell(x, N, c, fr[0]);
+      axis_cell(y, N, c, fr[1]);
+      axis_cell(z, N, c, fr[2]);
+      const float wx[2] = {1.0f - fr[0], fr[0]};
+      const float wy[2] = {1.0f - fr[1], fr[1]};
+      const float wz[2] = {1.0f - fr[2], fr[2]};
       float a0 = 0.0f, a1 = 0.0f;
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
