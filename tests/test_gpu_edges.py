@@ -157,3 +157,22 @@ def test_one_ray_training_step():
         B.train_step(b.with_prec(B.FP32), opt, scene, B.TRAIN_PROBED_MIX, 1, 21, step, 1e-2, ws, loss_out=loss)
         assert np.isfinite(loss.item())
     assert B.device_status() == 0
+
+
+@pytest.mark.parametrize("mp", [B.FP32, B.FP16])
+def test_inputs_beyond_the_kernels_report_unsupported(mp):
+    """N * L * F = 1024 is a valid descriptor (<= NBVH_MAX_INPUTS) that neither
+    MLP kernel stages (the first layer's weights or features exceed shared
+    memory or TMEM): the query returns NBVH_ERR_UNSUPPORTED without launching
+    and the device status stays clean."""
+    from dataclasses import replace
+    torch = _torch()
+    case = make_case("random_tris_c0", 1.0, 2.0)
+    model = replace(case.model, n_samples=32, n_levels=16, n_features=2, log2_table=12, width=64)
+    b = Built(replace(case, model=model))
+    desc = b.with_prec(mp)
+    with pytest.raises(B.NBVHError) as err:
+        B.query_rays(desc, b.table, b.mlp, b.nodes, b.leaves["n_nodes"], b.rays, 8)
+    assert err.value.code == 7  # NBVH_ERR_UNSUPPORTED
+    torch.cuda.synchronize()
+    assert B.device_status() == 0
