@@ -163,8 +163,8 @@ def test_one_ray_training_step():
 def test_inputs_beyond_the_kernels_report_unsupported(mp):
     """N * L * F = 1024 is a valid descriptor (<= NBVH_MAX_INPUTS) that neither
     MLP kernel stages (the first layer's weights or features exceed shared
-    memory or TMEM): the query returns NBVH_ERR_UNSUPPORTED without launching
-    and the device status stays clean."""
+    memory or TMEM): the query returns NBVH_ERR_UNSUPPORTED and the device
+    status stays clean."""
     from dataclasses import replace
     torch = _torch()
     case = make_case("random_tris_c0", 1.0, 2.0)
