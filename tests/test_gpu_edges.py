@@ -171,8 +171,9 @@ def test_inputs_beyond_the_kernels_report_unsupported(mp):
     model = replace(case.model, n_samples=32, n_levels=16, n_features=2, log2_table=12, width=64)
     b = Built(replace(case, model=model))
     desc = b.with_prec(mp)
+    B.device_status()  # clear the status word
     with pytest.raises(B.NBVHError) as err:
-        B.query_rays(desc, b.table, b.mlp, b.nodes, b.leaves["n_nodes"], b.rays, 8)
+        B.query_rays(desc, b.table, b.mlp, b.nodes, b.leaves["n_nodes"], b.rays, 64)
     assert err.value.code == 7  # NBVH_ERR_UNSUPPORTED
     torch.cuda.synchronize()
     assert B.device_status() == 0
