@@ -478,13 +478,15 @@ __device__ __forceinline__ void level_xhalf(const GridParams& gp, int l, const f
 }
 
 // Partial features (x-offset xb corners only) of NL levels from l0 at two
-// points: all 8 NL corner loads are issued before any is consumed. Invalid
+// points: all 8 NL corner loads are issued before any is consumed, and the
+// weights computed with the indices are kept for the interpolation. Invalid
 // points contribute zeros.
 template <typename T, int NL>
 __device__ __forceinline__ void encode_xhalf(const GridParams& gp, const T* __restrict__ table, int l0,
                                              const float* p0, const float* p1, bool v0, bool v1, int xb,
                                              float* out0, float* out1) {
   uint32_t raw[2][NL][4];
+  float w[2][NL][4];
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     const float* p = h ? p1 : p0;
@@ -492,8 +494,7 @@ __device__ __forceinline__ void encode_xhalf(const GridParams& gp, const T* __re
 #pragma unroll
     for (int q = 0; q < NL; ++q) {
       uint32_t idx[4];
-      float w[4];
-      level_xhalf(gp, l0 + q, p, xb, idx, w);
+      level_xhalf(gp, l0 + q, p, xb, idx, w[h][q]);
       const uint32_t* tab = reinterpret_cast<const uint32_t*>(table + size_t(gp.offset[l0 + q]) * 2);
 #pragma unroll
       for (int k = 0; k < 4; ++k) raw[h][q][k] = v ? __ldg(tab + idx[k]) : 0u;
@@ -501,13 +502,9 @@ __device__ __forceinline__ void encode_xhalf(const GridParams& gp, const T* __re
   }
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
-    const float* p = h ? p1 : p0;
     float* out = h ? out1 : out0;
 #pragma unroll
     for (int q = 0; q < NL; ++q) {
-      uint32_t idx[4];
-      float w[4];
-      level_xhalf(gp, l0 + q, p, xb, idx, w);  // weights recomputed (indices unused)
       float a0 = 0.0f, a1 = 0.0f;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
@@ -517,8 +514,8 @@ __device__ __forceinline__ void encode_xhalf(const GridParams& gp, const T* __re
         } else {
           v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&raw[h][q][k]));
         }
-        a0 = fmaf(w[k], v.x, a0);
-        a1 = fmaf(w[k], v.y, a1);
+        a0 = fmaf(w[h][q][k], v.x, a0);
+        a1 = fmaf(w[h][q][k], v.y, a1);
       }
       out[2 * q] = a0;
       out[2 * q + 1] = a1;
@@ -716,7 +713,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
           const uint32_t col0 = uint32_t(k * L * F) / 2u;
           for (int l0 = 0; l0 < L; l0 += 4) {
             float h0[8], h1[8];  // partial features of rows r0 and r1 over this lane's x bit
-            encode_xhalf<T, 4>(a.gp, table, l0, p0, p1, ray0 >= 0, ray1 >= 0, xb, h0, h1);
+            encode_xhalf<T, 2>(a.gp, table, l0, p0, p1, ray0 >= 0, ray1 >= 0, xb, h0, h1);
+            encode_xhalf<T, 2>(a.gp, table, l0 + 2, p0, p1, ray0 >= 0, ray1 >= 0, xb, h0 + 4, h1 + 4);
             uint32_t pk[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
