@@ -78,12 +78,19 @@ def dist_init(n_gpus):
     return world, rank, local
 
 
+def _reduce_device() -> str:
+    """Where the process group reduces: the GPU under NCCL, the host under gloo."""
+    import torch.distributed as dist
+    return "cuda" if dist.get_backend() == "nccl" else "cpu"
+
+
 def dist_max(x: float, world: int) -> float:
+    """The largest value over the ranks (a time: the slowest rank's)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=_reduce_device())
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -94,7 +101,7 @@ def dist_max_rate(rate: float, world: int) -> float:
         return rate
     import torch
     import torch.distributed as dist
-    t = torch.tensor([-rate], dtype=torch.float64, device="cuda")
+    t = torch.tensor([-rate], dtype=torch.float64, device=_reduce_device())
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return world * float(-t.item())
 
