@@ -711,7 +711,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
             sample_point(a.gp, a.rays.ox[ray1], a.rays.oy[ray1], a.rays.oz[ray1], a.rays.dx[ray1],
                          a.rays.dy[ray1], a.rays.dz[ray1], st0[r1], st1[r1], k, p1[0], p1[1], p1[2]);
           const uint32_t col0 = uint32_t(k * L * F) / 2u;
-          for (int l0 = 0; l0 < L; l0 += 4) {
+          auto chunk = [&](int l0) {
             float h0[8], h1[8];  // partial features of rows r0 and r1 over this lane's x bit
             encode_xhalf<T, 2>(a.gp, table, l0, p0, p1, ray0 >= 0, ray1 >= 0, xb, h0, h1);
             encode_xhalf<T, 2>(a.gp, table, l0 + 2, p0, p1, ray0 >= 0, ray1 >= 0, xb, h0 + 4, h1 + 4);
@@ -730,6 +730,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
             }
             __syncwarp();
             tmem_st4(t_a + col0 + uint32_t(l0 * F) / 2u, pk);
+          };
+          if (L == 16) {  // the common level count: levels unrolled, their parameters at fixed offsets
+#pragma unroll
+            for (int l0 = 0; l0 < 16; l0 += 4) chunk(l0);
+          } else {
+            for (int l0 = 0; l0 < L; l0 += 4) chunk(l0);
           }
         }
       }
