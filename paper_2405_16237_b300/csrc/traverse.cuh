@@ -49,6 +49,8 @@ __device__ __forceinline__ int traverse_ray(const nbvh_node* __restrict__ nodes,
   const float best = merge ? out.hits.t[r] : 0.0f;
   bool overflow = false;
   float lo_box[3] = {0.0f, 0.0f, 0.0f}, hi_box[3] = {0.0f, 0.0f, 0.0f};  // the box being emitted
+  float tail_key = 0.0f;  // order key and leaf of the list's last entry (count > 0)
+  int tail_leaf = 0;
   auto emit = [&](int leaf, float t0, float t1) {
     if (out.reverse_inside) {  // origin inside the box: the whole chord, reversed
       RayR whole = ray;
@@ -62,6 +64,22 @@ __device__ __forceinline__ int traverse_ray(const nbvh_node* __restrict__ nodes,
       }
     }
     const float key = seg_key(t0, t1);
+    // usual case (near-to-far traversal): the segment goes after the list's
+    // last entry, known from registers, so nothing is read back
+    if (count == 0 || tail_key < key || (tail_key == key && tail_leaf < leaf)) {
+      if (count < max_segs) {
+        const size_t w = size_t(count) * size_t(n) + size_t(r);
+        out.seg_t0[w] = t0;
+        out.seg_t1[w] = t1;
+        out.seg_leaf[w] = leaf;
+        ++count;
+        tail_key = key;
+        tail_leaf = leaf;
+      } else {
+        overflow = true;  // beyond the last kept entry of a full list
+      }
+      return;
+    }
     int pos;
     if (count < max_segs) {
       pos = count++;
@@ -88,6 +106,11 @@ __device__ __forceinline__ int traverse_ray(const nbvh_node* __restrict__ nodes,
     out.seg_t0[w] = t0;
     out.seg_t1[w] = t1;
     out.seg_leaf[w] = leaf;
+    if (overflow) {  // a full list dropped its last entry: the new last one
+      const size_t q = size_t(max_segs - 1) * size_t(n) + size_t(r);
+      tail_key = seg_key(out.seg_t0[q], out.seg_t1[q]);
+      tail_leaf = out.seg_leaf[q];
+    }
   };
 
   int stack[kTraverseStack];
