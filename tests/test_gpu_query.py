@@ -456,3 +456,35 @@ def test_reverse_inside_query_matches_oracle(mp):
     if mp == B.FP32:
         ok0 = ~ambiguous_rays(r0, n)
         assert np.array_equal(h0["hit"].cpu().numpy()[ok0].astype(bool), r0["hit"][ok0].astype(bool))
+
+
+@pytest.mark.parametrize("table_prec", [B.FP16, B.BF16])
+@pytest.mark.parametrize("n_levels", [6, 8, 12, 16])
+def test_tensor_core_gather_paths_by_level_count(n_levels, table_prec):
+    """Every form of the tensor-core gather against the oracle on the same
+    segments: 16 levels (unrolled level loop), 8 and 12 (four-level chunks in
+    a loop) and 6 (levels one by one), with FP16 and BF16 tables."""
+    from dataclasses import replace
+    torch = _torch()
+    base = make_case("random_tris_c0", 1.0, 2.0)
+    model = replace(base.model, n_levels=n_levels, growth=1.3)
+    b = Built(replace(base, model=model, table_prec=table_prec))
+    seg = _oracle_segments(b)
+    t0 = seg["t0"].astype(np.float32)
+    t1 = seg["t1"].astype(np.float32)
+    out = B.eval_segments(b.with_prec(B.FP16), b.table, b.mlp, b.rays,
+                          torch.as_tensor(seg["ray"].astype(np.int32)).cuda(), torch.as_tensor(t0).cuda(),
+                          torch.as_tensor(t1).cuda())
+    assert B.device_status() == 0
+    got = out.cpu().numpy()
+    o, d, _, _ = O.rays_od(b.case.rays)
+    rr = seg["ray"]
+    _, ref = O.eval_segments(o[rr], d[rr], t0.astype(np.float64), t1.astype(np.float64), b.table_host,
+                             b.layers, b.olayout, b.oleaves["frame"]["model_centre"], b.oleaves["frame"]["model_extent"],
+                             b.case.model.n_samples)
+    raw_agree, resolved_agree = hit_agreement(got[:, 0], ref[:, 0], B.FP16)
+    assert raw_agree >= RAW_AGREEMENT[B.FP16] and resolved_agree >= 0.999, (raw_agree, resolved_agree)
+    dg = t0 + O.sigmoid(got[:, 1]) * (t1 - t0)
+    dr = t0 + O.sigmoid(ref[:, 1]) * (t1 - t0)
+    assert np.max(np.abs(dg - dr)) <= 2e-3
+    assert np.mean(_angle_deg(got[:, 2:5], ref[:, 2:5])) <= 1.0
