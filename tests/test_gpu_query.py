@@ -488,3 +488,23 @@ def test_tensor_core_gather_paths_by_level_count(n_levels, table_prec):
     dr = t0 + O.sigmoid(ref[:, 1]) * (t1 - t0)
     assert np.max(np.abs(dg - dr)) <= 2e-3
     assert np.mean(_angle_deg(got[:, 2:5], ref[:, 2:5])) <= 1.0
+
+
+@pytest.mark.parametrize("mp", [B.FP16, B.BF16])
+def test_query_independent_of_ray_order(mp):
+    """A ray's result does not depend on where in a tile (or in which lane
+    pair of the gather) it is evaluated: the query of a permuted ray set,
+    mapped back, equals the query of the original order bit for bit."""
+    torch = _torch()
+    b = built("icosphere_l6", 1.0, 2.0)
+    rays = b.case.rays
+    n = len(rays["ox"])
+    perm = np.random.default_rng(5).permutation(n)
+    prays = {k: np.ascontiguousarray(v[perm]) for k, v in rays.items()}
+    h = B.query_rays(b.with_prec(mp), b.table, b.mlp, b.nodes, b.leaves["n_nodes"], b.rays, 24)
+    hp = B.query_rays(b.with_prec(mp), b.table, b.mlp, b.nodes, b.leaves["n_nodes"], B.to_device_rays(prays), 24)
+    assert B.device_status() == 0
+    inv = torch.as_tensor(np.argsort(perm)).cuda()
+    for k in h:
+        assert torch.equal(h[k], hp[k][inv]), k
+    assert int(h["hit"].sum()) > 1000
