@@ -206,16 +206,70 @@ def test_segments_sorted_and_complete():
     rays = W.camera_rays(24, 24, seed=6)
     seg = O.ray_segments(rays, lv["leaf_lo"], lv["leaf_hi"])
     off = seg["offsets"]
+    lo, hi = lv["leaf_lo"].astype(np.float64), lv["leaf_hi"].astype(np.float64)
+    # brute force by pointwise membership: dense points along each ray (the
+    # camera sits at radius 2 and every box lies inside [-1, 1]^3)
+    ts = np.linspace(0.0, 4.0, 8001)
+    n_listed = 0
     for r in range(len(rays["ox"])):
         t0 = seg["t0"][off[r]:off[r + 1]]
+        t1 = seg["t1"][off[r]:off[r + 1]]
         lf = seg["leaf"][off[r]:off[r + 1]]
         keys = list(zip(t0, lf))
         assert keys == sorted(keys)
-        # brute force: every leaf whose box a midpoint sample lies in is listed
         o, d, tmin, tmax = O.rays_od(rays, r)
+        t = ts[(ts >= tmin) & (ts <= tmax)]
+        p = o[None, :] + t[:, None] * d[None, :]
         for leaf in range(16):
-            k, a, b, _, _ = O.clip_ray_box(o, d, tmin, tmax, lv["leaf_lo"][leaf], lv["leaf_hi"][leaf])
-            assert bool(k) == (leaf in lf)
+            strictly = np.all((p > lo[leaf] + 1e-7) & (p < hi[leaf] - 1e-7), axis=1)
+            listed = np.flatnonzero(lf == leaf)
+            if strictly.any():
+                # a point strictly inside the box: the leaf is listed once, and
+                # its interval covers every such point
+                assert len(listed) == 1, (r, leaf)
+                j = listed[0]
+                eps = 2.0 ** -22 * max(1.0, abs(t0[j]), abs(t1[j]))
+                assert t[strictly].min() >= t0[j] - eps and t[strictly].max() <= t1[j] + eps
+            for j in listed:
+                # a listed interval lies in the box: its midpoint is inside
+                pm = o + 0.5 * (t0[j] + t1[j]) * d
+                assert np.all(pm >= lo[leaf] - 1e-6) and np.all(pm <= hi[leaf] + 1e-6), (r, leaf)
+                n_listed += 1
+    assert n_listed > 100
+
+
+def test_scene_frame_hand_made():
+    # the AABB spans x in [-1, 3], y in [0, 1], z in [2, 2.5]; most vertices
+    # sit near one corner, so the vertex mean is far from the box centre
+    tris = np.array([[[-1.0, 0.0, 2.0], [-0.9, 0.0, 2.0], [-1.0, 0.1, 2.0]],
+                     [[-1.0, 0.0, 2.1], [-0.9, 0.1, 2.0], [-1.0, 0.1, 2.1]],
+                     [[3.0, 1.0, 2.5], [-1.0, 0.0, 2.0], [-0.95, 0.05, 2.0]]], np.float32)
+    fr = O.scene_frame(tris)
+    assert fr["lo"].tolist() == [-1.0, 0.0, 2.0] and fr["hi"].tolist() == [3.0, 1.0, 2.5]
+    assert fr["centre"].tolist() == [1.0, 0.5, 2.25]
+    assert fr["extent"] == 4.0
+    assert fr["sphere_radius"] == pytest.approx(1.01 * math.sqrt(16.0 + 1.0 + 0.25) / 2.0, rel=1e-15)
+    # stored frame: nearest float32 of the centre and extent
+    tri2 = tris + np.float32(0.1)
+    fr2 = O.scene_frame(tri2)
+    c = (tri2.reshape(-1, 3).astype(np.float64).min(0) + tri2.reshape(-1, 3).astype(np.float64).max(0)) / 2
+    assert fr2["model_centre"].tolist() == c.astype(np.float32).astype(np.float64).tolist()
+    assert np.abs(fr2["model_centre"] - fr2["centre"]).max() <= 2.0 ** -24 * 3
+
+
+def test_normalize_points_clamp_and_centre():
+    c = np.array([1.0, -2.0, 0.5])
+    E = 4.0
+    p = np.array([c, c + E / 2, c - E / 2, c + E, c - E, c + 0.25 * E, c + [-E, 0.0, 3 * E]])
+    x = O.normalize_points(p, c, E)
+    assert x[0].tolist() == [0.5, 0.5, 0.5]
+    assert x[1].tolist() == [1.0, 1.0, 1.0] and x[2].tolist() == [0.0, 0.0, 0.0]
+    assert x[3].tolist() == [1.0, 1.0, 1.0] and x[4].tolist() == [0.0, 0.0, 0.0]   # clamped
+    assert x[5].tolist() == [0.75, 0.75, 0.75]
+    assert x[6].tolist() == [0.0, 0.5, 1.0]
+    # isotropic: one scale for every axis
+    q = O.normalize_points(np.array([[2.0, -1.0, 1.5]]), c, E)
+    assert q[0].tolist() == [0.75, 0.75, 0.75]
 
 
 # ---------------------------------------------------------------- leaf build
@@ -873,3 +927,66 @@ def test_hybrid_albedo_follows_the_answering_instance():
     assert ia.sum() > 5 and ib.sum() > 5
     assert np.array_equal(out["albedo"][ia], alb[out["leaf"][ia]])
     assert np.all(out["albedo"][ib] == 0.0) and np.all(out["albedo"][out["inst"] < 0] == 0.0)
+
+
+# ---------------------------------------------------------------- cut leaves (Sec. 5.1)
+def _hand_base():
+    """A hand-built base tree: node 0 -> (node 2, node 1) (second child first,
+    so depth-first order differs from node order), node 1 -> (leaf 0, leaf 1),
+    node 2 -> (leaf 2, leaf 3). Triangle i spans x in [i, i + 0.5], y in
+    [0, 1], z in [0, 2]; a permuted triangle order catches index mix-ups."""
+    dt = np.dtype([("child0", "<i4"), ("child1", "<i4")])
+    nodes = np.array([(2, 1), (~0, ~1), (~2, ~3)], dt)
+    tri_perm = np.array([3, 1, 0, 2, 7, 5, 6, 4], np.int32)
+    leaf_range = np.array([[0, 2], [2, 4], [4, 6], [6, 8]], np.int32)
+    tris = np.array([[[i, 0.0, 0.0], [i + 0.5, 1.0, 0.0], [i, 0.0, 2.0]] for i in range(8)], np.float32)
+    return tris, nodes, leaf_range, tri_perm
+
+
+def _is_outward_f32(lo, exact_lo, hi, exact_hi):
+    """lo is the largest float32 <= exact_lo, hi the smallest float32 >= exact_hi."""
+    lo = np.asarray(lo, np.float32)
+    hi = np.asarray(hi, np.float32)
+    up = np.nextafter(lo, np.float32(np.inf)).astype(np.float64)
+    dn = np.nextafter(hi, np.float32(-np.inf)).astype(np.float64)
+    return (np.all(lo.astype(np.float64) <= exact_lo) and np.all(up > exact_lo)
+            and np.all(hi.astype(np.float64) >= exact_hi) and np.all(dn < exact_hi))
+
+
+def test_cut_leaves_root_only_is_one_leaf_of_everything():
+    tris, nodes, rng, perm = _hand_base()
+    refs, sets, lo, hi = O.cut_leaves(tris, nodes, rng, perm, [0], 0.01, 10.0)
+    assert refs == [0]
+    assert sets[0].tolist() == list(range(8))
+    # AABB x [0, 7.5], y [0, 1], z [0, 2], pushed out by 0.01 * 10 = 0.1
+    assert _is_outward_f32(lo[0], np.array([-0.1, -0.1, -0.1]), hi[0], np.array([7.6, 1.1, 2.1]))
+
+
+def test_cut_leaves_all_base_leaves_in_depth_first_order():
+    tris, nodes, rng, perm = _hand_base()
+    cut = [~0, ~1, ~2, ~3]
+    refs, sets, lo, hi = O.cut_leaves(tris, nodes, rng, perm, cut, 0.01, 10.0)
+    # node 0 visits node 2 first: base leaves 2, 3, then 0, 1
+    assert refs == [~2, ~3, ~0, ~1]
+    assert [s.tolist() for s in sets] == [[5, 7], [4, 6], [1, 3], [0, 2]]
+    xs = [(5, 7.5), (4, 6.5), (1, 3.5), (0, 2.5)]
+    for i, (a, b) in enumerate(xs):
+        assert _is_outward_f32(lo[i], np.array([a - 0.1, -0.1, -0.1]), hi[i], np.array([b + 0.1, 1.1, 2.1]))
+
+
+def test_cut_leaves_mixed_cut_unions_the_base_leaves_below():
+    tris, nodes, rng, perm = _hand_base()
+    refs, sets, lo, hi = O.cut_leaves(tris, nodes, rng, perm, [1, ~2, ~3], 0.0, 10.0)
+    assert refs == [~2, ~3, 1]
+    assert [s.tolist() for s in sets] == [[5, 7], [4, 6], [0, 1, 2, 3]]
+    # no inflation: the exact AABB (representable values)
+    assert lo[2].tolist() == [0.0, 0.0, 0.0] and hi[2].tolist() == [3.5, 1.0, 2.0]
+    refs2, sets2, _, _ = O.cut_leaves(tris, nodes, rng, perm, [2, ~0, ~1], 0.0, 10.0)
+    assert refs2 == [2, ~0, ~1]
+    assert [s.tolist() for s in sets2] == [[4, 5, 6, 7], [1, 3], [0, 2]]
+
+
+def test_cut_leaves_rejects_an_incomplete_cut():
+    tris, nodes, rng, perm = _hand_base()
+    with pytest.raises(ValueError):
+        O.cut_leaves(tris, nodes, rng, perm, [2, ~0], 0.0, 10.0)   # base leaf 1 below no reference
