@@ -152,14 +152,15 @@ class GpuWorkload:
         self.flush_buf = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
         self.graphs = {}
         self.launches_per_step = {}
+        self.options = None  # query options (None: the library's defaults), set from the autotuner
 
     def step(self, desc):
         B = self.B
         B.query_rays(desc, self.table, self.mlp, self.nodes, self.leaves["n_nodes"], self.rays, self.max_segs,
-                     out=self.h1, workspace=self.ws1)
+                     out=self.h1, workspace=self.ws1, options=self.options)
         B.bounce_rays(self.rays, self.h1, SEED + 3, out=self.rays2)
         B.query_rays(desc, self.table, self.mlp, self.nodes, self.leaves["n_nodes"], self.rays2, self.max_segs,
-                     out=self.h2, workspace=self.ws2)
+                     out=self.h2, workspace=self.ws2, options=self.options)
 
     def graph_step(self, desc):
         """The step replayed from a CUDA graph recorded on first use."""
@@ -205,10 +206,10 @@ class GpuWorkload:
             if st["graph"] is None:
                 def run(st=st):
                     B.query_rays(desc, self.table, self.mlp, self.nodes, self.leaves["n_nodes"], st["rays"],
-                                 self.max_segs, out=st["h1"], workspace=st["ws1"])
+                                 self.max_segs, out=st["h1"], workspace=st["ws1"], options=self.options)
                     B.bounce_rays(st["rays"], st["h1"], SEED + 3, out=st["rays2"])
                     B.query_rays(desc, self.table, self.mlp, self.nodes, self.leaves["n_nodes"], st["rays2"],
-                                 self.max_segs, out=st["h2"], workspace=st["ws2"])
+                                 self.max_segs, out=st["h2"], workspace=st["ws2"], options=self.options)
                 st["graph"] = B.Graph.record(run)
         start = torch.cuda.Event(enable_timing=True)
         end = torch.cuda.Event(enable_timing=True)
@@ -266,7 +267,7 @@ def time_training(spec, tris, wl, steps, warmup, batch=1 << 18, desc=None, mlp=N
     opt = B.Optimizer(desc, torch.as_tensor(wl.table_np.astype(np.float32)).cuda(),
                       (mlp if mlp is not None else wl.mlp).clone(), loss_scale=32768.0)
     ws = B.new_workspace(B.train_workspace_size(desc, batch, scene.n_leaves))
-    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
     step = 0
     for _ in range(warmup):
         step += 1
@@ -571,8 +572,9 @@ def time_uneven(args, world):
     setup_s = time.perf_counter() - t0
     best, table_all = B.autotune_query(desc, table, mlp, nodes, leaves["n_nodes"], rays, ms_max, out=out,
                                        workspace=ws, reps=3)
+    opts = B.options_from_dict(best)
     g = B.Graph.record(lambda: B.query_rays(desc, table, mlp, nodes, leaves["n_nodes"], rays, ms_max, out=out,
-                                            workspace=ws))
+                                            workspace=ws, options=opts))
     launches = 0
     for _ in range(3):
         g.launch()
@@ -636,10 +638,10 @@ def time_cut(args, world):
     used = step_e - 1
     rest = max(0, args.cut_steps - used)
     ws_e = B.new_workspace(B.train_workspace_size(desc_e, batch, n_leaves))
-    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
     stats = {"hits": torch.zeros(n_leaves, dtype=torch.int32, device="cuda"),
              "trained": torch.zeros(n_leaves, dtype=torch.int32, device="cuda"),
-             "loss": torch.zeros(n_leaves, dtype=torch.float64, device="cuda")}
+             "loss": torch.zeros(n_leaves, dtype=torch.float32, device="cuda")}
     pdev = None
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -945,12 +947,11 @@ def run_gpu(args, world, rank, spec, tris, rays_np):
 
     # autotuner (untimed): pick the query schedule on this workload's primary rays
     if args.no_autotune:
-        sch, pat = B.get_query_schedule()
-        tune_best, tune_all = {"schedule": ["waves", "persistent"][sch], "patience_cycles": pat,
-                               "traverse_block": 128, "ms": None}, []
+        tune_best, tune_all = dict(B.options_dict(B.query_options()), ms=None), []
     else:
         tune_best, tune_all = B.autotune_query(d16, wl.table, wl.mlp, wl.nodes, wl.leaves["n_nodes"], wl.rays,
                                                args.max_segs, out=wl.h1, workspace=wl.ws1, reps=3)
+    wl.options = B.options_from_dict(tune_best)
 
     # untimed reference step: statistics of the work one step does
     wl.step(d16)
@@ -1003,19 +1004,12 @@ def run_gpu(args, world, rank, spec, tris, rays_np):
 
     # uneven segment counts (64 sphere clusters, 8,192 leaves, 4M rays)
     uneven = time_uneven(args, world) if args.uneven_steps > 0 else None
-    # back to the configuration the autotuner chose for the icosphere workload
-    B.set_query_schedule(1 if tune_best["schedule"] == "persistent" else 0, tune_best["patience_cycles"])
-    B.set_traverse_block(tune_best["traverse_block"])
 
     # error-driven cut vs median split (same leaves, same training budget)
     cutcmp = time_cut(args, world) if args.cut_steps > 0 else None
-    B.set_query_schedule(1 if tune_best["schedule"] == "persistent" else 0, tune_best["patience_cycles"])
-    B.set_traverse_block(tune_best["traverse_block"])
 
     # levels of detail: bounce rays on a coarse LoD vs the finest
     lod = time_lod(args, world) if args.lod_steps > 0 else None
-    B.set_query_schedule(1 if tune_best["schedule"] == "persistent" else 0, tune_best["patience_cycles"])
-    B.set_traverse_block(tune_best["traverse_block"])
 
     # the hybrid two-level scene (16 neural assets + 500,000 classical triangles)
     hybrid = time_hybrid(args, world) if args.hybrid_frames > 0 else None
@@ -1063,8 +1057,8 @@ def run_gpu(args, world, rank, spec, tris, rays_np):
             "config": {"workload": spec.name, "rays_per_step": rays_step, "primary_rays": wl.n,
                        "bounce_rays": rays_step - wl.n, "segments_per_step": seg_step,
                        "eval_launches": [waves1, waves2],
-                       "schedule": {"mode": ["waves", "persistent"][B.get_query_schedule()[0]],
-                                    "patience_cycles": B.get_query_schedule()[1],
+                       "schedule": {"options": B.options_dict(wl.options),
+                                    "plan": B.eval_plan(d16, wl.options),
                                     "autotuner": {"best": tune_best, "candidates": tune_all}},
                        "l2": "flushed (256 MB write) between timed steps",
                        "parallelism": f"replicas x{world}"},

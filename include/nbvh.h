@@ -44,7 +44,7 @@ extern "C" {
 
 #define NBVH_MAX_LEVELS 32
 #define NBVH_MAX_SAMPLES 64
-#define NBVH_MAX_INPUTS 2048   /* n_samples * n_levels * n_features */
+#define NBVH_MAX_INPUTS 2048   /* n_samples * n_levels * n_features (queries; training: see nbvh_train_workspace_size) */
 
 typedef enum {
   NBVH_OK = 0,
@@ -189,13 +189,75 @@ nbvh_status nbvh_encode(const nbvh_model_desc* desc, const void* table, nbvh_ray
                         const int32_t* seg_ray, const float* t0, const float* t1, int64_t n_seg,
                         float* feat, void* stream);
 
+/* Evaluation options of a query (S6; Sec. 5: the number of neural queries
+ * per ray equals the leaves met before an intersection, so rays need uneven
+ * amounts of work). Every choice gives the same hit records; they only change
+ * how the work is scheduled and shaped on the GPU. Passed per call (NULL =
+ * nbvh_query_options_default); the library keeps no schedule state.
+ *  schedule         NBVH_SCHEDULE_WAVES: one launch per segment slot w
+ *                   evaluates slot w of every ray still active (compacted
+ *                   queue per wave). NBVH_SCHEDULE_PERSISTENT (FP16/BF16 only;
+ *                   the FP32 form always runs waves): one launch whose CTAs
+ *                   claim tiles of up to 128 (ray, segment) items from a queue
+ *                   that each resolve refills with the ray's next segment, so
+ *                   rays with many segments leave no wave tail per slot. A
+ *                   queue wait that gives up (about a second) records
+ *                   NBVH_ERR_TIMEOUT.
+ *  patience_cycles  persistent schedule: SM cycles a CTA waits for a full
+ *                   tile before it takes fewer items (0 .. 2^40).
+ *  traverse_block   threads per traversal CTA: 64, 128 or 256.
+ *  eval_threads     FP16/BF16 evaluation CTA: 256 (two CTAs per SM, hidden
+ *                   width <= 64), 512 (one CTA per SM), 0 = automatic (256
+ *                   where the width allows).
+ *  w1_mode          FP16/BF16 evaluation: where the first layer's weights
+ *                   live. NBVH_W1_RESIDENT: converted into shared memory once
+ *                   per CTA; NBVH_W1_STREAMED: converted once per call into a
+ *                   16-bit image in the workspace and streamed through two
+ *                   shared-memory buffers, 128 inputs at a time, by bulk
+ *                   copies; NBVH_W1_AUTO: resident when it fits the CTA's
+ *                   shared-memory budget, else streamed. */
+#define NBVH_SCHEDULE_WAVES 0
+#define NBVH_SCHEDULE_PERSISTENT 1
+#define NBVH_W1_AUTO 0
+#define NBVH_W1_RESIDENT 1
+#define NBVH_W1_STREAMED 2
+typedef struct {
+  int32_t schedule;
+  int64_t patience_cycles;
+  int32_t traverse_block;
+  int32_t eval_threads;
+  int32_t w1_mode;
+} nbvh_query_options;
+
+/* Host. The defaults: persistent schedule, patience 4000 cycles, traversal
+ * CTAs of 128 threads, automatic evaluation CTA shape and weight placement. */
+nbvh_status nbvh_query_options_default(nbvh_query_options* opt);
+
+/* Host. The evaluation kernel's launch plan for desc under opt (NULL = the
+ * defaults): threads per CTA, whether the first layer's weights are streamed
+ * (1) or resident (0), dynamic shared memory bytes and TMEM columns per CTA
+ * (0 for the FP32 form, whose CTAs use no TMEM; for it *threads is the CTA
+ * size and *w1_streamed says whether the first layer is taken in chunks).
+ * NBVH_ERR_UNSUPPORTED when the kernels cannot run this combination. */
+nbvh_status nbvh_eval_plan(const nbvh_model_desc* desc, const nbvh_query_options* opt, int32_t* threads,
+                           int32_t* w1_streamed, int32_t* smem_bytes, int32_t* tmem_cols);
+
+/* Host. Workspace bytes of nbvh_eval_segments for desc (the streamed
+ * first-layer image of the FP16/BF16 form; may be 0). */
+nbvh_status nbvh_eval_workspace_size(const nbvh_model_desc* desc, size_t* bytes);
+
 /* Device. S2..S4 fused: raw MLP outputs out[i * n_out + j] of n_seg segments
  * (as nbvh_encode), through the MLP selected by desc->mlp_prec. mlp: device
  * float parameters (nbvh_mlp_param_count). The FP32 form uses CUDA cores;
- * the FP16/BF16 form uses tcgen05 tensor-core MMAs with FP32 accumulation. */
+ * the FP16/BF16 form uses tcgen05 tensor-core MMAs with FP32 accumulation.
+ * Both take the first layer in chunks of inputs, so every descriptor up to
+ * NBVH_MAX_INPUTS inputs runs. opt: NULL or the evaluation shape (schedule,
+ * patience and traverse_block are ignored). workspace: device, 256-byte
+ * aligned, >= nbvh_eval_workspace_size bytes (NULL when that is 0). */
 nbvh_status nbvh_eval_segments(const nbvh_model_desc* desc, const void* table, const float* mlp,
                                nbvh_rays rays, const int32_t* seg_ray, const float* t0,
-                               const float* t1, int64_t n_seg, float* out, void* stream);
+                               const float* t1, int64_t n_seg, float* out, const nbvh_query_options* opt,
+                               void* workspace, size_t ws_bytes, void* stream);
 
 /* Host. Workspace bytes of nbvh_query_rays for n_rays rays and at most
  * max_segs segments per ray. */
@@ -204,6 +266,8 @@ nbvh_status nbvh_query_workspace_size(const nbvh_model_desc* desc, int64_t n_ray
 
 /* Device. The neural ray query, S1..S5 (Sec. 5: the number of neural
  * queries per ray equals the leaves met before an intersection is found).
+ * nbvh_query_rays runs with nbvh_query_options_default; nbvh_query_rays_opt
+ * takes the options (NULL = the defaults).
  * Traversal lists each ray's segments in (t0, leaf) order; each ray's
  * segments are then evaluated in that order, keeping the closest predicted
  * hit (hit iff hit logit > 0; t = t0 + sigmoid(depth)(t1 - t0); normal =
@@ -211,11 +275,17 @@ nbvh_status nbvh_query_workspace_size(const nbvh_model_desc* desc, int64_t n_ray
  * at or beyond its best t. The result equals the closest predicted hit over
  * all segments, ties to the earlier segment. The evaluation runs as waves
  * (one launch per segment slot) or, for FP16/BF16, as one persistent launch
- * (nbvh_set_query_schedule).
- * workspace: device, >= nbvh_query_workspace_size bytes, 256-byte aligned. */
+ * (nbvh_query_options).
+ * workspace: device, >= nbvh_query_workspace_size bytes, 256-byte aligned.
+ * A descriptor or option the kernels cannot run returns NBVH_ERR_UNSUPPORTED
+ * before anything is enqueued. */
 nbvh_status nbvh_query_rays(const nbvh_model_desc* desc, const void* table, const float* mlp,
                             const nbvh_node* nodes, int32_t n_nodes, nbvh_rays rays, int32_t max_segs,
                             nbvh_hits out, void* workspace, size_t ws_bytes, void* stream);
+nbvh_status nbvh_query_rays_opt(const nbvh_model_desc* desc, const void* table, const float* mlp,
+                                const nbvh_node* nodes, int32_t n_nodes, nbvh_rays rays, int32_t max_segs,
+                                nbvh_hits out, void* workspace, size_t ws_bytes, const nbvh_query_options* opt,
+                                void* stream);
 
 /* Writable rays, device structure-of-arrays, n entries each. */
 typedef struct {
@@ -234,50 +304,24 @@ typedef struct {
  * rays, hits: device inputs of n entries; out: device outputs, out.n == rays.n. */
 nbvh_status nbvh_bounce_rays(nbvh_rays rays, nbvh_hits hits, uint64_t seed, nbvh_rays_out out, void* stream);
 
-/* Evaluation schedule of the FP16/BF16 (tensor-core) query; the FP32 form
- * always runs waves. Both give identical results.
- *  NBVH_SCHEDULE_WAVES:      one launch per segment slot w evaluates slot w of
- *                            every ray still active (compacted queue per wave).
- *  NBVH_SCHEDULE_PERSISTENT: one launch whose CTAs (one per SM) claim tiles of
- *                            up to 128 (ray, segment) items from a queue that
- *                            each resolve refills with the ray's next segment,
- *                            so rays with many segments do not leave a wave
- *                            tail per slot (Sec. 5: queries per ray = leaves met
- *                            before a hit). A CTA waits up to patience_cycles
- *                            SM cycles for a full tile before it takes fewer
- *                            items. A queue wait that gives up (about a second)
- *                            records NBVH_ERR_TIMEOUT.
- * Process-wide setting (default: persistent, 4000 cycles), read when a query
- * is enqueued (a graph keeps the schedule it was recorded with). */
-#define NBVH_SCHEDULE_WAVES 0
-#define NBVH_SCHEDULE_PERSISTENT 1
-nbvh_status nbvh_set_query_schedule(int32_t schedule, int64_t patience_cycles);
-nbvh_status nbvh_get_query_schedule(int32_t* schedule, int64_t* patience_cycles);
-
-/* Threads per traversal CTA (64, 128 or 256; default 128), process-wide. */
-nbvh_status nbvh_set_traverse_block(int32_t threads);
-
 /* One configuration of the query and its median time. */
 typedef struct {
-  int32_t schedule;          /* NBVH_SCHEDULE_* */
-  int64_t patience_cycles;
-  int32_t traverse_block;
+  nbvh_query_options opt;
   float ms;                  /* median of the timed runs */
 } nbvh_tune_result;
 
-/* Device (synchronises). S6 autotuner: times nbvh_query_rays on the caller's
- * own inputs under each candidate configuration and keeps the fastest.
- * Candidates: waves; for FP16/BF16 also the persistent schedule with
- * patience 0, 1000, 4000, 16000 and 64000 cycles; then traversal CTAs of 64
- * and 256 threads under the best schedule. Each candidate runs once untimed
- * and reps times timed (CUDA events on the stream, median). The winner is set
- * process-wide (nbvh_set_query_schedule, nbvh_set_traverse_block) and
- * returned in *best; the first all_cap candidates with their times go to
+/* Device (synchronises). S6 autotuner: times nbvh_query_rays_opt on the
+ * caller's own inputs under candidate options and returns the fastest in
+ * *best (nothing is stored in the library). The search runs in stages, each
+ * keeping the best so far: (1) waves, and for FP16/BF16 the persistent
+ * schedule with patience 0, 1000, 4000, 16000 and 64000 cycles; (2) for
+ * FP16/BF16 the evaluation CTA shape, 256 and 512 threads (256 only for
+ * width <= 64) times resident and streamed first-layer weights, where the
+ * model stages them; (3) traversal CTAs of 64, 128 and 256 threads. Each
+ * candidate runs once untimed and reps times timed (CUDA events on the
+ * stream, median). The first all_cap candidates with their times go to
  * all[], their count to *n_all. Every candidate gives the same hit records
- * (out holds the last run's). On an error the previous settings are restored.
- * The tensor-core tile is fixed at 128 rows (the MMA M and the 128 TMEM
- * lanes), so rows per tile are not a candidate; the patience sets how full a
- * claimed tile must be. */
+ * (out holds the last run's). */
 nbvh_status nbvh_autotune_query(const nbvh_model_desc* desc, const void* table, const float* mlp,
                                 const nbvh_node* nodes, int32_t n_nodes, nbvh_rays rays, int32_t max_segs,
                                 nbvh_hits out, void* workspace, size_t ws_bytes, int32_t reps,
@@ -360,9 +404,27 @@ nbvh_status nbvh_train_labels(nbvh_rays rays, const int32_t* leaf, const float* 
                               const nbvh_train_scene* scene, nbvh_labels out, void* stream);
 
 /* Host. Workspace of nbvh_forward_train / nbvh_backward / nbvh_train_step for
- * batches of up to n rays; n_leaves = the scene's leaf count for
- * nbvh_train_step (its rays are grouped by leaf), 0 for forward/backward only. */
+ * batches of n rays that stores the whole batch's activations; n_leaves = the
+ * scene's leaf count for nbvh_train_step (its rays are grouped by leaf), 0 for
+ * forward/backward only.
+ * Recompute mode: a workspace smaller than this (but at least the budget
+ * call's minimum) holds the per-ray outputs of the whole batch and the
+ * activations of one chunk of rays only. The forward then runs chunk by chunk
+ * keeping the raw outputs, dL/d(raw) and loss terms, and the backward runs each
+ * chunk's forward again to rebuild its activations before differentiating it
+ * (the same gradients up to FP32 summation order). The calls choose the mode
+ * from ws_bytes, so a forward and its backward must get the same ws_bytes.
+ * Training supports first layers the kernels stage whole: N * L * F up to
+ * about 768 at width 64 (FP16/BF16) and similar for FP32; larger models
+ * return NBVH_ERR_UNSUPPORTED before anything is enqueued. */
 nbvh_status nbvh_train_workspace_size(const nbvh_model_desc* desc, int64_t n, int32_t n_leaves, size_t* bytes);
+
+/* Host. Memory budget of a training workspace: *bytes = the stored-mode size
+ * when it is at most max_bytes (*chunk = n), else the recompute-mode size of
+ * the largest activation chunk (a multiple of 128 rays, *chunk) that fits.
+ * NBVH_ERR_WORKSPACE_TOO_SMALL when not even a 128-ray chunk fits. */
+nbvh_status nbvh_train_workspace_budget(const nbvh_model_desc* desc, int64_t n, int32_t n_leaves, size_t max_bytes,
+                                        size_t* bytes, int64_t* chunk);
 
 /* Device. Forward of n training segments (segment i belongs to ray i and to
  * leaf[i]; leaf < 0 does not train) storing the activations in the workspace.
@@ -372,14 +434,22 @@ nbvh_status nbvh_train_workspace_size(const nbvh_model_desc* desc, int64_t n, in
  * (Sec. 5.2), plus, for n_out = 8 with albedo labels, the relative L2 term
  * y (1/3) sum_c (s_c - a_c)^2 / (s_c^2 + 0.01), s_c = sigmoid(o_{5+c}), the
  * denominator held constant; keeps dL/d(raw) times the loss scale for nbvh_backward, and
- * writes L (FP64 reduction) to *loss_out (device, may be NULL).
+ * writes L to *loss_out (device, may be NULL): an FP32 sum of the per-segment
+ * terms, compensated per thread and pairwise across threads, without atomics.
  * n_valid: device count of training segments (nbvh_train_rays). The loss
  * scale is *loss_scale_dev when that is not NULL, else loss_scale. */
 nbvh_status nbvh_forward_train(const nbvh_model_desc* desc, const void* table, const float* mlp,
                                nbvh_rays rays, const int32_t* leaf, const float* t0, const float* t1,
                                nbvh_labels labels, const int32_t* n_valid, float loss_scale,
-                               const float* loss_scale_dev, float* raw_out, double* loss_out, void* workspace,
+                               const float* loss_scale_dev, float* raw_out, float* loss_out, void* workspace,
                                size_t ws_bytes, void* stream);
+
+/* Device. The loss of the last nbvh_forward_train on this workspace (n rays,
+ * the same ws_bytes) summed with FP64 accumulation into *loss_out (device).
+ * For finite-difference gradient checks only: central differences subtract
+ * two nearly equal losses. */
+nbvh_status nbvh_loss_fp64(const nbvh_model_desc* desc, int64_t n, const int32_t* n_valid, const void* workspace,
+                           size_t ws_bytes, double* loss_out, void* stream);
 
 /* Device. Backward of the last nbvh_forward_train on the same workspace:
  * from grad_out (device [n][n_out], dL/d(raw); NULL = the loss gradient the
@@ -415,7 +485,7 @@ nbvh_status nbvh_adam(const nbvh_model_desc* desc, const nbvh_optim* opt, int64_
  * with loss, backward, Adam (lr, beta 0.9 / 0.999, eps 1e-8, Sec. 6). FP16 /
  * BF16 MLPs use dynamic loss scaling. *loss_out (device) receives the loss. */
 nbvh_status nbvh_train_step(const nbvh_model_desc* desc, const nbvh_optim* opt, const nbvh_train_scene* scene,
-                            int32_t mode, int64_t batch, uint64_t seed, int64_t step, float lr, double* loss_out,
+                            int32_t mode, int64_t batch, uint64_t seed, int64_t step, float lr, float* loss_out,
                             void* workspace, size_t ws_bytes, void* stream);
 
 /* Per-leaf statistics of training steps (Sec. 5.1 "Node error": a node's error
@@ -424,11 +494,12 @@ nbvh_status nbvh_train_step(const nbvh_model_desc* desc, const nbvh_optim* opt, 
  * arrays of n_leaves entries that the steps accumulate into (callers zero
  * them): hits = rays whose first leaf (the leaf they would train) is the
  * leaf; trained = those that trained it; loss = the sum of their combined
- * loss terms (per-ray, before the mean over the batch). */
+ * loss terms (per-ray, before the mean over the batch; FP32, each step's
+ * per-leaf sum compensated). */
 typedef struct {
   uint32_t* hits;
   uint32_t* trained;
-  double* loss;
+  float* loss;
 } nbvh_leaf_stats;
 
 /* Device. nbvh_train_step with error-driven ray selection (Sec. 5.2 "Ray
@@ -442,7 +513,7 @@ typedef struct {
 nbvh_status nbvh_train_step_weighted(const nbvh_model_desc* desc, const nbvh_optim* opt,
                                      const nbvh_train_scene* scene, int32_t mode, int64_t batch, uint64_t seed,
                                      int64_t step, float lr, const float* leaf_prob, const nbvh_leaf_stats* stats,
-                                     double* loss_out, void* workspace, size_t ws_bytes, void* stream);
+                                     float* loss_out, void* workspace, size_t ws_bytes, void* stream);
 
 /* Host. N-BVH from a cut through a base BVH (Sec. 5.1 "Base-BVH cut
  * optimization": the nodes along the cut become the N-BVH leaves, inflated
@@ -460,6 +531,30 @@ nbvh_status nbvh_build_cut(const nbvh_node* base_nodes, int32_t n_base_nodes, co
                            int32_t n_base_leaves, const int32_t* cut, int32_t n_cut, double inflate_rel,
                            float extent, nbvh_node* nodes, int32_t node_cap, int32_t* out_n_nodes,
                            int32_t* leaf_range, float* leaf_box, int32_t* leaf_ref);
+
+/* Host. Sec. 5.1 "Node error" for the leaves of a cut, from the per-leaf
+ * statistics of training steps (nbvh_leaf_stats, copied to the host):
+ * q = loss / trained, the leaf's mean training loss (a leaf hit but never
+ * trained takes the mean q of the trained leaves, 1 if none trained);
+ * p = hits / n_rays, the fraction of training rays that hit it; ranking
+ * r = 2 ln q + ln p (-inf when hits = 0 or q <= 0, never split). Training
+ * probability of Sec. 5.2, read as the ranking's linear-domain ratio:
+ * prob = max(exp(r - r_max), 0.005) (0.005 for r = -inf), r_max the largest
+ * finite r. All arrays host, n_leaves entries; q, p, r FP64 (host). */
+nbvh_status nbvh_rank_leaves(const uint32_t* hits, const uint32_t* trained, const float* loss, int32_t n_leaves,
+                             int64_t n_rays, double* q, double* p, double* r, float* prob);
+
+/* Host. Sec. 5.1 split step: among the cut's references that are internal
+ * base nodes (cut[i] >= 0) with a finite ranking r[i], the k_splits of
+ * largest r (ties to the lower leaf index) are replaced by their base
+ * children in place (first child first); the leaf order is kept otherwise.
+ * new_prob: prob[i] for a kept leaf, 1 for a new child (no statistics yet).
+ * base_nodes: the base BVH (nbvh_build_tri_blas format), host. new_cut,
+ * new_prob: host, cap entries; *n_new = the new cut's length
+ * (NBVH_ERR_WORKSPACE_TOO_SMALL if above cap). */
+nbvh_status nbvh_refine_cut(const nbvh_node* base_nodes, int32_t n_base_nodes, const int32_t* cut, int32_t n_cut,
+                            const double* r, const float* prob, int32_t k_splits, int32_t* new_cut, float* new_prob,
+                            int32_t cap, int32_t* n_new);
 
 /* Size of the library's built-in query scratch (32 MiB), see
  * nbvh_query_rays_static. */
@@ -482,8 +577,10 @@ nbvh_status nbvh_build_cut(const nbvh_node* base_nodes, int32_t n_base_nodes, co
  * events.
  *
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current) and caches it; make that
- * first call before any stream capture on the device. Every call on a device
+ * (cudaGetSymbolAddress, with that device current) and caches it with the
+ * current context; a call in another context of the device (one created after
+ * cudaDeviceReset, for example) looks it up again. Make the first call of each
+ * context before any stream capture on the device. Every call on a device
  * shares the one array and finds the previous call's data in it (the query
  * clears what must start at zero itself), so calls whose GPU work overlaps,
  * on different streams or from different threads, race on the scratch:
@@ -586,10 +683,12 @@ nbvh_status nbvh_hybrid_workspace_size(const nbvh_instance* inst, int32_t n_inst
  * skips the leaves whose segment starts at or beyond the record (their hits
  * cannot be closer), which leaves the result unchanged.
  * inst: host array of n_inst (1..64) instances; workspace: device, 256-byte
- * aligned, >= nbvh_hybrid_workspace_size bytes. Segment overflow of a neural
- * pass is reported as in nbvh_query_rays. */
+ * aligned, >= nbvh_hybrid_workspace_size bytes. opt: the evaluation options
+ * of the neural passes (NULL = nbvh_query_options_default). Segment overflow
+ * of a neural pass is reported as in nbvh_query_rays. */
 nbvh_status nbvh_hybrid_trace(const nbvh_instance* inst, int32_t n_inst, nbvh_rays rays, nbvh_hits out,
-                              int32_t* out_inst, void* workspace, size_t ws_bytes, void* stream);
+                              int32_t* out_inst, void* workspace, size_t ws_bytes, const nbvh_query_options* opt,
+                              void* stream);
 
 /* Device (synchronises). Measurement utility, no counterpart in the paper:
  * the L2 random-gather ceiling that bounds the hash-table gather when the

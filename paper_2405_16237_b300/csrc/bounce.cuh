@@ -36,7 +36,7 @@ constexpr float kTwoPi = 6.28318530717958647692f;
 // -d), direction cosine-weighted about n' from Philox counter (ray, 0, 0, 2)
 // with r = sqrt(u1), phi = 2 pi u2, expressed in the orthonormal basis of
 // Duff et al. (JCGT 2017). A miss gets an empty interval (tmin 0, tmax -1).
-__global__ void __launch_bounds__(256) bounce_kernel(RayPtrs in, nbvh_hits hits, int64_t n, uint32_t k0,
+static __global__ void __launch_bounds__(256) bounce_kernel(RayPtrs in, nbvh_hits hits, int64_t n, uint32_t k0,
                                                      uint32_t k1, RayOut out) {
   const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (r >= n) return;

@@ -127,6 +127,8 @@ struct EvalArgs {
   int32_t* inst_out;  // optional (hybrid hierarchy): instance id written with each improved hit
   int32_t inst_id;
   PQueue pq;          // tensor-core query: persistent queue (when pq.ring is set)
+  const void* w1_image;  // tensor-core kernel: streamed first-layer weights (nullptr: resident)
+  int32_t chunk_samples; // FP32 kernel: samples per first-layer chunk (0: all, weights resident)
   // training forward (tensor-core kernel, list of one segment per ray)
   TcTrain tr;
 };
@@ -136,44 +138,64 @@ struct EvalArgs {
 // warp writes in the dense layers over distinct banks.
 __device__ __forceinline__ int act_idx(int k, int s) { return k * kPlainTM + (s ^ (((k >> 2) & 15) << 1)); }
 
+// A dense layer over a [K][TM] activation tile (act_idx layout) with the
+// weights transposed to [K][W] in shared memory: thread t owns segments s0,
+// s0 + 1 and outputs n0 .. n0 + W/16 - 1. The accumulators stay in registers
+// across calls, so a layer can be fed in K chunks.
+template <int W>
+struct DenseAcc {
+  static constexpr int NPT = W / 16;
+  float a0[NPT], a1[NPT];
+  __device__ __forceinline__ int s0() const { return (threadIdx.x >> 4) * 2; }
+  __device__ __forceinline__ int n0() const { return (threadIdx.x & 15) * NPT; }
+  __device__ __forceinline__ void init(const float* __restrict__ bias) {
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) a0[j] = a1[j] = __ldg(bias + n0() + j);
+  }
+  __device__ __forceinline__ void accum(const float* __restrict__ in, int K, const float* __restrict__ wt) {
+    const int sa = s0(), na = n0();
+#pragma unroll 4
+    for (int k = 0; k < K; ++k) {
+      const float2 f = *reinterpret_cast<const float2*>(in + act_idx(k, sa));
+      float w[NPT];
+      if constexpr (NPT % 4 == 0) {
+#pragma unroll
+        for (int j = 0; j < NPT; j += 4) {
+          const float4 q = *reinterpret_cast<const float4*>(wt + k * W + na + j);
+          w[j] = q.x; w[j + 1] = q.y; w[j + 2] = q.z; w[j + 3] = q.w;
+        }
+      } else if constexpr (NPT == 2) {
+        const float2 q = *reinterpret_cast<const float2*>(wt + k * W + na);
+        w[0] = q.x; w[1] = q.y;
+      } else {
+        w[0] = wt[k * W + na];
+      }
+#pragma unroll
+      for (int j = 0; j < NPT; ++j) {
+        a0[j] = fmaf(w[j], f.x, a0[j]);
+        a1[j] = fmaf(w[j], f.y, a1[j]);
+      }
+    }
+  }
+  template <bool RELU>
+  __device__ __forceinline__ void store(float* __restrict__ out) const {
+    const int sa = s0(), na = n0();
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+      float2 v = make_float2(a0[j], a1[j]);
+      if (RELU) { v.x = fmaxf(v.x, 0.0f); v.y = fmaxf(v.y, 0.0f); }
+      *reinterpret_cast<float2*>(out + act_idx(na + j, sa)) = v;
+    }
+  }
+};
+
 template <int W, bool RELU>
 __device__ __forceinline__ void dense_plain(const float* __restrict__ in, int K, const float* __restrict__ wt,
                                             const float* __restrict__ bias, float* __restrict__ out) {
-  constexpr int NPT = W / 16;
-  const int t = threadIdx.x;
-  const int s0 = (t >> 4) * 2;
-  const int n0 = (t & 15) * NPT;
-  float acc0[NPT], acc1[NPT];
-#pragma unroll
-  for (int j = 0; j < NPT; ++j) acc0[j] = acc1[j] = __ldg(bias + n0 + j);
-#pragma unroll 4
-  for (int k = 0; k < K; ++k) {
-    const float2 f = *reinterpret_cast<const float2*>(in + act_idx(k, s0));
-    float w[NPT];
-    if constexpr (NPT % 4 == 0) {
-#pragma unroll
-      for (int j = 0; j < NPT; j += 4) {
-        const float4 q = *reinterpret_cast<const float4*>(wt + k * W + n0 + j);
-        w[j] = q.x; w[j + 1] = q.y; w[j + 2] = q.z; w[j + 3] = q.w;
-      }
-    } else if constexpr (NPT == 2) {
-      const float2 q = *reinterpret_cast<const float2*>(wt + k * W + n0);
-      w[0] = q.x; w[1] = q.y;
-    } else {
-      w[0] = wt[k * W + n0];
-    }
-#pragma unroll
-    for (int j = 0; j < NPT; ++j) {
-      acc0[j] = fmaf(w[j], f.x, acc0[j]);
-      acc1[j] = fmaf(w[j], f.y, acc1[j]);
-    }
-  }
-#pragma unroll
-  for (int j = 0; j < NPT; ++j) {
-    float2 v = make_float2(acc0[j], acc1[j]);
-    if (RELU) { v.x = fmaxf(v.x, 0.0f); v.y = fmaxf(v.y, 0.0f); }
-    *reinterpret_cast<float2*>(out + act_idx(n0 + j, s0)) = v;
-  }
+  DenseAcc<W> acc;
+  acc.init(bias);
+  acc.accum(in, K, wt);
+  acc.template store<RELU>(out);
 }
 
 // Decoded per-segment result (S5): hit iff logit > 0; t = t0 + sigmoid(o_d) (t1 - t0);
@@ -249,18 +271,45 @@ __device__ __forceinline__ void wave_resolve(const EvalArgs& a, bool valid, int 
   }
 }
 
+// First-layer chunking of the FP32 kernel: CS samples (CS * L * F features)
+// per chunk, CS = a.chunk_samples, or all N (0) with the first layer's weights
+// staged once per CTA. Chunked, every tile gathers chunk c and multiplies it
+// by the matching rows of the first layer's weights (reloaded per chunk), the
+// accumulators staying in registers.
+inline size_t plain_smem_bytes(int K, int W, int n_hidden, int n_out) {
+  const int hid_w = (n_hidden - 1) * W * W + W * n_out;
+  const int feat_floats = K * kPlainTM > hid_w ? K * kPlainTM : hid_w;
+  return sizeof(float) * (size_t(feat_floats) + size_t(K) * W + 2 * size_t(W) * kPlainTM + 8 * kPlainTM) +
+         3 * sizeof(int) * kPlainTM;
+}
+
+// Samples per chunk for an input width K = N * LF: 0 when the whole first
+// layer fits shared memory, else the most samples whose chunk fits; -1 if not
+// even one sample's chunk fits.
+inline int plain_chunk_samples(int N, int LF, int W, int n_hidden, int n_out) {
+  const size_t limit = 227 * 1024;
+  if (plain_smem_bytes(N * LF, W, n_hidden, n_out) <= limit) return 0;
+  for (int cs = N - 1; cs >= 1; --cs)
+    if (plain_smem_bytes(cs * LF, W, n_hidden, n_out) <= limit) return cs;
+  return -1;
+}
+
 template <typename T, int F, int W, bool WAVE>
 __global__ void __launch_bounds__(kPlainThreads, 1) eval_plain_kernel(EvalArgs a) {
   extern __shared__ __align__(16) float smem[];
   const int K = a.gp.n_inputs;
   const int L = a.gp.n_levels;
   const int N = a.gp.n_samples;
+  const int LF = L * F;
   const int n_out = a.n_out;
+  const int CS = a.chunk_samples > 0 ? a.chunk_samples : N;  // samples per chunk
+  const int KC = CS * LF;                                     // features per chunk
+  const bool resident = CS >= N;
   const int hid_w = (a.n_hidden - 1) * W * W + W * n_out;
-  const int feat_floats = max(K * kPlainTM, hid_w);
-  float* sfeat = smem;                      // [K][TM] features, later hidden weights
-  float* sW1 = sfeat + feat_floats;         // [K][W] first-layer weights, transposed
-  float* shA = sW1 + K * W;                 // [W][TM]
+  const int feat_floats = max(KC * kPlainTM, hid_w);
+  float* sfeat = smem;                      // [KC][TM] features, later hidden weights
+  float* sW1 = sfeat + feat_floats;         // [KC][W] first-layer weights (chunk), transposed
+  float* shA = sW1 + KC * W;                // [W][TM]
   float* shB = shA + W * kPlainTM;          // [W][TM]
   float* sout = shB + W * kPlainTM;         // [8][TM]
   int* sray = reinterpret_cast<int*>(sout + 8 * kPlainTM);
@@ -273,10 +322,14 @@ __global__ void __launch_bounds__(kPlainThreads, 1) eval_plain_kernel(EvalArgs a
 
   const float* W1 = a.mlp;            // [W][K]
   const float* b1 = W1 + W * K;
-  for (int i = threadIdx.x; i < K * W; i += blockDim.x) {
-    const int n = i / K, k = i - n * K;
-    sW1[k * W + n] = __ldg(W1 + i);
-  }
+  // rows [c0, c0 + KC) of the transposed first layer (zero beyond K)
+  auto load_w1 = [&](int c0) {
+    for (int i = threadIdx.x; i < KC * W; i += blockDim.x) {
+      const int n = i / KC, k = i - n * KC;
+      sW1[k * W + n] = c0 + k < K ? __ldg(W1 + size_t(n) * K + c0 + k) : 0.0f;
+    }
+  };
+  if (resident) load_w1(0);
   const T* table = static_cast<const T*>(a.table);
 
   for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
@@ -302,30 +355,36 @@ __global__ void __launch_bounds__(kPlainThreads, 1) eval_plain_kernel(EvalArgs a
     }
     __syncthreads();
 
-    // Encode: pair p = (segment s, sample k); lanes = consecutive segments.
-    for (int p = threadIdx.x; p < kPlainTM * N; p += blockDim.x) {
-      const int s = p % kPlainTM;
-      const int k = p / kPlainTM;
-      const int ray = sray[s];
-      const int kb = k * L * F;
-      if (ray < 0) {
-        for (int j = 0; j < L * F; ++j) sfeat[act_idx(kb + j, s)] = 0.0f;
-        continue;
-      }
-      FF x, y, z;
-      sample_point_ff(a.gp, a.rays.ox[ray], a.rays.oy[ray], a.rays.oz[ray], a.rays.dx[ray], a.rays.dy[ray],
-                      a.rays.dz[ray], st0[s], st1[s], k, x, y, z);
-      for (int l = 0; l < L; ++l) {
-        float v[F];
-        encode_level<T, F>(a.gp, table, l, x, y, z, v);
+    DenseAcc<W> acc;
+    acc.init(b1);
+    for (int ks = 0; ks < N; ks += CS) {
+      const int cs = min(CS, N - ks);
+      if (!resident) load_w1(ks * LF);
+      // Encode: pair p = (segment s, sample k); lanes = consecutive segments.
+      for (int p = threadIdx.x; p < kPlainTM * cs; p += blockDim.x) {
+        const int s = p % kPlainTM;
+        const int k = ks + p / kPlainTM;
+        const int ray = sray[s];
+        const int kb = (k - ks) * LF;
+        if (ray < 0) {
+          for (int j = 0; j < LF; ++j) sfeat[act_idx(kb + j, s)] = 0.0f;
+          continue;
+        }
+        FF x, y, z;
+        sample_point_ff(a.gp, a.rays.ox[ray], a.rays.oy[ray], a.rays.oz[ray], a.rays.dx[ray], a.rays.dy[ray],
+                        a.rays.dz[ray], st0[s], st1[s], k, x, y, z);
+        for (int l = 0; l < L; ++l) {
+          float v[F];
+          encode_level<T, F>(a.gp, table, l, x, y, z, v);
 #pragma unroll
-        for (int f = 0; f < F; ++f) sfeat[act_idx(kb + l * F + f, s)] = v[f];
+          for (int f = 0; f < F; ++f) sfeat[act_idx(kb + l * F + f, s)] = v[f];
+        }
       }
+      __syncthreads();
+      acc.accum(sfeat, cs * LF, sW1);
+      __syncthreads();
     }
-    __syncthreads();
-
-    dense_plain<W, true>(sfeat, K, sW1, b1, shA);
-    __syncthreads();
+    acc.template store<true>(shA);
 
     // Hidden and output weights, transposed into the (now free) feature area.
     {
@@ -362,9 +421,9 @@ __global__ void __launch_bounds__(kPlainThreads, 1) eval_plain_kernel(EvalArgs a
       const float* bo = bh + n_out * W;
       for (int i = threadIdx.x; i < n_out * kPlainTM; i += blockDim.x) {
         const int j = i / kPlainTM, s = i - j * kPlainTM;
-        float acc = __ldg(bo + j);
-        for (int k = 0; k < W; ++k) acc = fmaf(wt[k * n_out + j], hin[act_idx(k, s)], acc);
-        sout[j * kPlainTM + s] = acc;
+        float acc_o = __ldg(bo + j);
+        for (int k = 0; k < W; ++k) acc_o = fmaf(wt[k * n_out + j], hin[act_idx(k, s)], acc_o);
+        sout[j * kPlainTM + s] = acc_o;
       }
     }
     __syncthreads();
@@ -383,13 +442,6 @@ __global__ void __launch_bounds__(kPlainThreads, 1) eval_plain_kernel(EvalArgs a
     }
     __syncthreads();
   }
-}
-
-inline size_t plain_smem_bytes(int K, int W, int n_hidden, int n_out) {
-  const int hid_w = (n_hidden - 1) * W * W + W * n_out;
-  const int feat_floats = K * kPlainTM > hid_w ? K * kPlainTM : hid_w;
-  return sizeof(float) * (size_t(feat_floats) + size_t(K) * W + 2 * size_t(W) * kPlainTM + 8 * kPlainTM) +
-         3 * sizeof(int) * kPlainTM;
 }
 
 // Encoder only (S2+S3), FP32 features feat[i * K + k*L*F + l*F + f].
@@ -415,6 +467,54 @@ __global__ void __launch_bounds__(128) encode_kernel(GridParams gp, const void* 
 #pragma unroll
     for (int f = 0; f < F; ++f) o[l * F + f] = v[f];
   }
+}
+
+// ---------------------------------------------------------------- launch
+template <typename T, int F, int W, bool WAVE>
+cudaError_t launch_plain_twf(const EvalArgs& a0, int64_t n_items_max, cudaStream_t s) {
+  EvalArgs a = a0;
+  const int LF = a.gp.n_levels * F;
+  const int cs = plain_chunk_samples(a.gp.n_samples, LF, W, a.n_hidden, a.n_out);
+  if (cs < 0) return cudaErrorInvalidConfiguration;
+  a.chunk_samples = cs;
+  auto kern = eval_plain_kernel<T, F, W, WAVE>;
+  const size_t smem = plain_smem_bytes((cs > 0 ? cs : a.gp.n_samples) * LF, W, a.n_hidden, a.n_out);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kPlainThreads, smem);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) occ = 1;
+  int64_t tiles = (n_items_max + kPlainTM - 1) / kPlainTM;
+  int64_t grid = int64_t(sm_count()) * occ;
+  if (tiles < grid) grid = tiles;
+  if (grid < 1) return cudaSuccess;
+  kern<<<unsigned(grid), kPlainThreads, smem, s>>>(a);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template <typename T, int F, bool WAVE>
+cudaError_t launch_plain_tf(const EvalArgs& a, int64_t n, cudaStream_t s) {
+  switch (a.width) {
+    case 16: return launch_plain_twf<T, F, 16, WAVE>(a, n, s);
+    case 32: return launch_plain_twf<T, F, 32, WAVE>(a, n, s);
+    case 64: return launch_plain_twf<T, F, 64, WAVE>(a, n, s);
+    case 128: return launch_plain_twf<T, F, 128, WAVE>(a, n, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// The FP32 kernels of one table type and schedule (one translation unit each).
+template <typename T, bool WAVE>
+cudaError_t launch_plain_t(int F, const EvalArgs& a, int64_t n, cudaStream_t s) {
+  switch (F) {
+    case 1: return launch_plain_tf<T, 1, WAVE>(a, n, s);
+    case 2: return launch_plain_tf<T, 2, WAVE>(a, n, s);
+    case 4: return launch_plain_tf<T, 4, WAVE>(a, n, s);
+    case 8: return launch_plain_tf<T, 8, WAVE>(a, n, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace nbvh

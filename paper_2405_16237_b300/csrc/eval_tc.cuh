@@ -8,10 +8,12 @@
 #include "nbvh_internal.cuh"
 #include "eval_plain.cuh"
 
+#include <algorithm>
+#include <cstring>
+
 namespace nbvh {
 
 constexpr int kTcM = 128;          // segments per tile = MMA M = TMEM lanes
-constexpr int kTcThreads = 512;    // 16 warps: all gather; 4 lane quarters x 4 column groups in epilogues
 constexpr long long kWaitCycles = 4000000000LL;  // bounded mbarrier wait (~2 s)
 
 // ---------------------------------------------------------------- PTX wrappers
@@ -167,46 +169,88 @@ struct OpType<true> {
   static __device__ __forceinline__ T one(float a) { return __float2bfloat16_rn(a); }
 };
 
+// ---------------------------------------------------------------- tile geometry
+// The first layer runs over the features in K chunks of kKC = 128 (64 TMEM
+// columns). A sample's L*F features are padded to a multiple of 8 (one
+// "item": 8 features = 4 TMEM columns, one tcgen05.st); the padded input has
+// KP = N * LFp features rounded up to 16 (one MMA K step) and the first
+// layer's weights carry zero rows for the padding. While the tensor cores
+// multiply chunk r, the gather fills chunk r + 1 into the other of two TMEM
+// buffers, so the feature footprint is 128 columns whatever K is.
+constexpr int kKC = 128;
+constexpr int kItemF = 8;
+constexpr int kChunkItems = kKC / kItemF;
+
 // TMEM column plan (one 32-bit column holds two 16-bit operand elements):
-//   [0, W)                 FP32 accumulator D of the current layer (the output
-//                          layer uses its first 16 columns)
-//   [W, W + W/2)           hidden activations H, the next layer's A operand
-//   [2W, 2W + Kp/2)        encoded features, the first layer's A operand
-// Only the weights live in shared memory, so L1 keeps most of its capacity
-// for the hash-table gather.
+//   [0, W)             FP32 accumulator D of the current layer (the output
+//                      layer uses its first 16 columns)
+//   [W, W + W/2)       hidden activations H, the next layer's A operand
+//   [2W, 2W + 128)     two 64-column feature chunk buffers, the first layer's
+//                      A operand
+// Shared memory: the first layer's weights as chunk-sized B operands (all R
+// chunks resident, or two buffers that bulk copies refill from a prepared
+// 16-bit image in global memory), the hidden and output weights, two row
+// buffers and the barriers.
 struct TcLayout {
-  int Kp;                    // input width padded to 16
+  int LFp;                   // features per sample, padded to a multiple of 8
+  int IPS;                   // items per sample (LFp / 8)
+  int NI;                    // items per row (N * IPS)
+  int KP;                    // padded input width (N * LFp rounded up to 16)
+  int R;                     // K chunks
   uint32_t col_h, col_a, ncols;
-  uint32_t w1_off;           // W x Kp operand
+  uint32_t chunk_bytes;      // one W x 128 chunk of the first layer's weights
+  uint32_t w1_off;           // resident: R chunks; streamed: 2 chunk buffers
   uint32_t wh_off;           // (n_hidden - 1) x W x W
   uint32_t wo_off;           // 16 x W
-  uint32_t row_off;          // per-row ray / t0 / t1
-  uint32_t bar_off;          // mbarrier + TMEM base address
+  uint32_t row_off;          // two row buffers
+  uint32_t bar_off;          // mbarriers + TMEM base address
   uint32_t total;
 };
 
-__host__ __device__ inline TcLayout tc_layout(int K, int W, int n_hidden) {
-  TcLayout L;
-  L.Kp = (K + 15) & ~15;
-  L.col_h = uint32_t(W);
-  L.col_a = uint32_t(2 * W);
-  const uint32_t used = L.col_a + uint32_t(L.Kp / 2);
+constexpr uint32_t kRowBytes = 12 * 4;  // per row: ray, t0, t1, slot, best t, next t0, origin, direction
+
+__host__ __device__ inline TcLayout tc_layout(int L, int F, int N, int W, int n_hidden, bool stream) {
+  TcLayout T;
+  T.LFp = (L * F + kItemF - 1) / kItemF * kItemF;
+  T.IPS = T.LFp / kItemF;
+  T.NI = N * T.IPS;
+  T.KP = (N * T.LFp + 15) & ~15;
+  T.R = (T.KP + kKC - 1) / kKC;
+  T.col_h = uint32_t(W);
+  T.col_a = uint32_t(2 * W);
+  const uint32_t used = T.col_a + uint32_t(kKC);
   uint32_t nc = 32;
   while (nc < used) nc <<= 1;
-  L.ncols = nc;
+  T.ncols = nc;
+  T.chunk_bytes = uint32_t(W) * kKC * 2;
   uint32_t off = 0;
   auto take = [&](uint32_t bytes) {
     const uint32_t o = off;
     off = (off + bytes + 127u) & ~127u;
     return o;
   };
-  L.w1_off = take(uint32_t(W) * L.Kp * 2);
-  L.wh_off = take(uint32_t(n_hidden - 1) * W * W * 2);
-  L.wo_off = take(16u * W * 2);
-  L.row_off = take(2 * kTcM * 24);  // two row buffers (the persistent query stages the next tile early)
-  L.bar_off = take(64);
-  L.total = off + 128;  // slack for base alignment
-  return L;
+  T.w1_off = take((stream ? 2u : uint32_t(T.R)) * T.chunk_bytes);
+  T.wh_off = take(uint32_t(n_hidden - 1) * W * W * 2);
+  T.wo_off = take(16u * W * 2);
+  T.row_off = take(2 * kTcM * kRowBytes);
+  T.bar_off = take(64);
+  T.total = off + 128;  // slack for base alignment
+  return T;
+}
+
+// Column c of the padded input: the original feature index, or -1 for padding.
+__host__ __device__ inline int padded_feature(int c, int L, int F, int N, int LFp) {
+  const int k = c / LFp, rem = c - k * LFp;
+  return (k < N && rem < L * F) ? k * L * F + rem : -1;
+}
+
+// Element (row n, padded column c) of the first layer's weights in the chunked
+// B-operand layout: chunk c / 128, then the K-major core-matrix layout of a
+// W x 128 operand.
+__host__ __device__ inline uint32_t w1_chunk_offset(int n, int c, uint32_t chunk_bytes) {
+  const int r = c / kKC, cc = c - r * kKC;
+  return uint32_t(r) * chunk_bytes +
+         uint32_t((n >> 3) * (kKC * 16) + (cc >> 3) * 128 + (n & 7) * 16 + (cc & 7) * 2);
 }
 
 // D[tmem] (+)= A[tmem] * B[smem]^T (A from tensor memory, kind::f16).
@@ -383,11 +427,61 @@ __device__ __forceinline__ bool pq_put(const PQueue& q, unsigned long long p, un
   return false;
 }
 
+// ---------------------------------------------------------------- row buffers
+// One tile's rows in shared memory, structure of arrays.
+struct RowBuf {
+  int* ray;     // -1: an empty row
+  float* t0;
+  float* t1;
+  int* slot;    // persistent query: the item's segment slot
+  float* best;  // persistent query: the ray's best t when the item was taken
+  float* next;  // persistent query: the start of the ray's next segment (+inf: none)
+  float* o[3];
+  float* d[3];
+};
+
+__device__ __forceinline__ RowBuf row_buf(uint8_t* base) {
+  RowBuf b;
+  float* f = reinterpret_cast<float*>(base);
+  b.ray = reinterpret_cast<int*>(f);
+  b.t0 = f + kTcM;
+  b.t1 = f + 2 * kTcM;
+  b.slot = reinterpret_cast<int*>(f + 3 * kTcM);
+  b.best = f + 4 * kTcM;
+  b.next = f + 5 * kTcM;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    b.o[i] = f + (6 + i) * kTcM;
+    b.d[i] = f + (9 + i) * kTcM;
+  }
+  return b;
+}
+
+// Row r holds segment [t0, t1] of ray `ray` (-1: empty): origin and direction
+// are copied next to it so the gather reads them from shared memory.
+__device__ __forceinline__ void put_row(const RowBuf& b, const RayPtrs& rays, int r, int ray, float t0, float t1) {
+  b.ray[r] = ray;
+  b.t0[r] = t0;
+  b.t1[r] = t1;
+  const bool v = ray >= 0;
+  b.o[0][r] = v ? rays.ox[ray] : 0.0f;
+  b.o[1][r] = v ? rays.oy[ray] : 0.0f;
+  b.o[2][r] = v ? rays.oz[ray] : 0.0f;
+  b.d[0][r] = v ? rays.dx[ray] : 0.0f;
+  b.d[1][r] = v ? rays.dy[ray] : 0.0f;
+  b.d[2][r] = v ? rays.dz[ray] : 0.0f;
+}
+
+// Sample k of row r's segment in grid coordinates (S2).
+__device__ __forceinline__ void row_point(const GridParams& gp, const RowBuf& b, int r, int k, float* p) {
+  sample_point(gp, b.o[0][r], b.o[1][r], b.o[2][r], b.d[0][r], b.d[1][r], b.d[2][r], b.t0[r], b.t1[r], k, p[0],
+               p[1], p[2]);
+}
+
 // Stage row r of a claimed tile (item at ring position p): the ray, its
 // segment's interval, its best t and its next segment's t0. Returns the ray
 // (-1 if the wait gave up).
-__device__ __forceinline__ int pq_stage(const EvalArgs& a, unsigned long long p, int r, int* sray, float* st0,
-                                        float* st1, int* sslot, float* sbest, float* snext) {
+__device__ __forceinline__ int pq_stage(const EvalArgs& a, unsigned long long p, int r, const RowBuf& b) {
   const size_t nr = size_t(a.n_rays);
   const unsigned long long it = pq_take(a.pq, p, nr);
   int ray = -1;
@@ -397,20 +491,18 @@ __device__ __forceinline__ int pq_stage(const EvalArgs& a, unsigned long long p,
   } else {
     ray = int(uint32_t(it));
     const int sl = int(it >> 32);
-    sslot[r] = sl;
+    b.slot[r] = sl;
     const size_t q = size_t(sl) * nr + size_t(ray);
     t0 = a.seg_t0[q];
     t1 = a.seg_t1[q];
-    sbest[r] = __ldcg(a.hits.t + ray);
+    b.best[r] = __ldcg(a.hits.t + ray);
     // the slot after the last holds stale data: load it with the count, use it only below the count
     const int cnt = a.seg_count[ray];
     const size_t qn = size_t(sl + 1) * nr + size_t(ray);
     const float tn = sl + 1 < a.max_segs ? fminf(a.seg_t0[qn], a.seg_t1[qn]) : 0.0f;  // its start
-    snext[r] = sl + 1 < cnt ? tn : __int_as_float(0x7f800000);
+    b.next[r] = sl + 1 < cnt ? tn : __int_as_float(0x7f800000);
   }
-  sray[r] = ray;
-  st0[r] = t0;
-  st1[r] = t1;
+  put_row(b, a.rays, r, ray, t0, t1);
   return ray;
 }
 
@@ -438,7 +530,7 @@ __device__ __forceinline__ bool pq_resolve(const EvalArgs& a, int ray, int sl, f
 }
 
 // The traversal queued the first items at ring positions [0, *qlen0).
-__global__ void pq_init_kernel(const int32_t* __restrict__ qlen0, PQueue q) {
+static __global__ void pq_init_kernel(const int32_t* __restrict__ qlen0, PQueue q) {
   *q.reserved = (unsigned long long)(*qlen0);
 }
 
@@ -523,40 +615,139 @@ __device__ __forceinline__ void encode_xhalf(const GridParams& gp, const T* __re
   }
 }
 
+// ---------------------------------------------------------------- bulk copies (TMA unit)
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+// Contiguous global -> shared copy of `bytes` (16-byte aligned ends, a multiple
+// of 16 bytes) that completes on `bar`'s transaction count.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// The first layer's weights (FP32 [W][K] row-major) into the chunked B-operand
+// layout (w1_chunk_offset) with zero rows for the padding: into shared memory
+// by a CTA (resident weights) or into global memory by w1_image_kernel.
+template <bool BF16>
+__device__ __forceinline__ void put_w1(uint8_t* dst, const float* __restrict__ W1, int i, int W, int K, int L, int F,
+                                       int N, const TcLayout& T) {
+  const int cols = T.R * kKC;
+  const int n = i / cols, c = i - n * cols;
+  const int f = padded_feature(c, L, F, N, T.LFp);
+  const float v = f >= 0 ? __ldg(W1 + size_t(n) * K + f) : 0.0f;
+  *reinterpret_cast<typename OpType<BF16>::T*>(dst + w1_chunk_offset(n, c, T.chunk_bytes)) = OpType<BF16>::one(v);
+}
+
+// Streamed first-layer weights: the 16-bit chunked image the kernel's bulk
+// copies read (R * chunk_bytes bytes, 16-byte aligned).
+template <bool BF16>
+__global__ void __launch_bounds__(256) w1_image_kernel(const float* __restrict__ W1, int W, int K, int L, int F, int N,
+                                                       TcLayout T, uint8_t* __restrict__ img) {
+  const int total = W * T.R * kKC;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x)
+    put_w1<BF16>(img, W1, i, W, K, L, F, N, T);
+}
+
+// One item (levels l0 .. l0 + 3 of one sample, F = 2, 4-byte entries) of the
+// two rows a lane pair shares (x-corner lane split): each lane gathers the
+// corners with x bit xb of both rows, then the partners swap partial sums so
+// that lane i returns its own row's 8 features, packed to 16 bits. Levels at
+// or beyond L give zeros.
+template <typename T, bool BF16, bool FULL>
+__device__ __forceinline__ void split_item(const GridParams& gp, const T* __restrict__ table, int l0, int L,
+                                           const float* p0, const float* p1, bool v0, bool v1, int xb,
+                                           uint32_t* pk) {
+  float h0[8], h1[8];  // partial features of rows r0 and r1 over this lane's x bit
+  if constexpr (FULL) {
+    encode_xhalf<T, 2>(gp, table, l0, p0, p1, v0, v1, xb, h0, h1);
+    encode_xhalf<T, 2>(gp, table, l0 + 2, p0, p1, v0, v1, xb, h0 + 4, h1 + 4);
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (l0 + q < L) {
+        encode_xhalf<T, 1>(gp, table, l0 + q, p0, p1, v0, v1, xb, h0 + 2 * q, h1 + 2 * q);
+      } else {
+        h0[2 * q] = h0[2 * q + 1] = h1[2 * q] = h1[2 * q + 1] = 0.0f;
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    // send the partner the row it owns (r1 for lanes 0-15, r0 for 16-31)
+    const float s0 = xb ? h0[2 * i] : h1[2 * i], s1 = xb ? h0[2 * i + 1] : h1[2 * i + 1];
+    const float g0 = __shfl_xor_sync(0xffffffffu, s0, 16), g1 = __shfl_xor_sync(0xffffffffu, s1, 16);
+    const float m0 = xb ? h1[2 * i] : h0[2 * i], m1 = xb ? h1[2 * i + 1] : h0[2 * i + 1];
+    pk[i] = pack2<BF16>(m0 + g0, m1 + g1);
+  }
+}
+
+// One item (8 / F levels from l0 of one sample) of one row; levels at or
+// beyond L give zeros.
+template <typename T, int F>
+__device__ __forceinline__ void row_item(const GridParams& gp, const T* __restrict__ table, int l0, int L,
+                                         const float* p, float* v) {
+  constexpr int LPC = 8 / F;
+  if (l0 + LPC <= L) {
+    if constexpr (LPC == 4) {
+      encode_levels<T, F, 4>(gp, table, l0, p[0], p[1], p[2], v);
+    } else if constexpr (LPC % 2 == 0) {
+#pragma unroll
+      for (int q = 0; q < LPC; q += 2) encode_levels<T, F, 2>(gp, table, l0 + q, p[0], p[1], p[2], v + q * F);
+    } else {
+      encode_levels<T, F, LPC>(gp, table, l0, p[0], p[1], p[2], v);
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < LPC; ++q) {
+      if (l0 + q < L) {
+        encode_level<T, F>(gp, table, l0 + q, p[0], p[1], p[2], v + q * F);
+      } else {
+#pragma unroll
+        for (int f = 0; f < F; ++f) v[q * F + f] = 0.0f;
+      }
+    }
+  }
+}
+
 // MODE 0: list of segments -> raw outputs; 1: query -> resolve + next segment
 // queued (one launch per segment slot, or with a.pq.ring set one persistent
 // launch draining the queue); 2: training forward (one segment per ray) ->
 // stored 16-bit operands, raw outputs, loss and dL/d(raw).
-template <typename T, int F, int W, int MODE, bool BF16>
-__global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
+// NT threads = NT / 128 warp groups; each warp group gathers 16 / (NT / 128)
+// items of every K chunk for all 128 rows of the tile. With W <= 64 the CTA
+// holds 256 TMEM columns, so two 256-thread CTAs share an SM and one CTA's
+// barriers, MMAs and queue claims overlap the other's gather.
+template <typename T, int F, int W, int MODE, bool BF16, int NT>
+__global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) eval_tc_kernel(EvalArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  constexpr int kGroups = NT / 128;
+  constexpr int IPG = kChunkItems / kGroups;  // items per warp group and chunk
+  constexpr int LPC = 8 / F;                  // levels per item
+  constexpr int kCols = W / kGroups;          // accumulator columns per thread in hidden epilogues
+  static_assert(kCols % 8 == 0 || kCols == 4 || kCols == 8, "epilogue column split");
   const int K = a.gp.n_inputs;
   const int L = a.gp.n_levels;
   const int N = a.gp.n_samples;
   const int n_out = a.n_out;
-  const TcLayout lay = tc_layout(K, W, a.n_hidden);
-  const int Kp = lay.Kp;
+  const bool stream = a.w1_image != nullptr;
+  const TcLayout lay = tc_layout(L, F, N, W, a.n_hidden, stream);
   uint8_t* sW1 = smem + lay.w1_off;
   uint8_t* sWh = smem + lay.wh_off;
   uint8_t* sWo = smem + lay.wo_off;
-  // row buffer b: ray, t0, t1 and (persistent query) the item's slot, the
-  // ray's best t and its next segment's t0
-  int *sray, *sslot;
-  float *st0, *st1, *sbest, *snext;
-  auto bind_rows = [&](int b, int*& ry, float*& a0, float*& a1, int*& sl, float*& be, float*& nx) {
-    ry = reinterpret_cast<int*>(smem + lay.row_off + size_t(b) * kTcM * 24);
-    a0 = reinterpret_cast<float*>(ry + kTcM);
-    a1 = a0 + kTcM;
-    sl = reinterpret_cast<int*>(a1 + kTcM);
-    be = reinterpret_cast<float*>(sl + kTcM);
-    nx = be + kTcM;
-  };
-  bind_rows(0, sray, st0, st1, sslot, sbest, snext);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + lay.bar_off);
-  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + lay.bar_off + 8);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + lay.bar_off);  // [0] hidden/output MMAs
+  uint64_t* mma_done = bar + 1;                                      // [2] first-layer chunk MMAs
+  uint64_t* w_full = bar + 3;                                        // [2] streamed weight chunks
+  uint64_t* bar_fin = bar + 5;                                       // exit: every MMA retired
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bar + 6);
+  uint8_t* const rows_base = smem + lay.row_off;  // row buffer b at rows_base + b * kTcM * kRowBytes
   __shared__ unsigned long long s_start[2];
   __shared__ int s_count[2];  // per row buffer: its tile's item count, kPqNoTile when nothing is staged
+  __shared__ int s_fail;
 
   // A persistent query's CTAs claim tiles from the queue until it drains.
   const bool persistent = MODE == 1 && a.pq.ring != nullptr;
@@ -571,16 +762,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
     tmem_relinquish();
   }
   if (threadIdx.x == 0) {
-    mbar_init(bar, 1);
+    for (int i = 0; i < 6; ++i) mbar_init(bar + i, 1);
     fence_mbar_init();
     s_count[0] = kPqNoTile;
     s_count[1] = kPqNoTile;
+    s_fail = 0;
   }
 
-  // Weights -> operand layouts (converted once per CTA).
+  // Weights -> operand layouts (converted once per CTA; the first layer's only
+  // when they stay resident).
   const float* W1 = a.mlp;
   const float* b1 = W1 + size_t(W) * K;
-  stage_weights<BF16>(sW1, W1, W, W, K, Kp);
+  if (!stream)
+    for (int i = threadIdx.x; i < W * lay.R * kKC; i += NT) put_w1<BF16>(sW1, W1, i, W, K, L, F, N, lay);
   const float* p = b1 + W;
   for (int h = 1; h < a.n_hidden; ++h) {
     stage_weights<BF16>(sWh + size_t(h - 1) * W * W * 2, p, W, W, W, W);
@@ -598,25 +792,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
   const uint32_t idesc_h = idesc_f16(BF16, kTcM, W);
   const uint32_t idesc_o = idesc_f16(BF16, kTcM, 16);
   const T* table = static_cast<const T*>(a.table);
-  // Warp -> TMEM lane quarter (warp % 4); in epilogues also a column group (warp / 4).
+  // Warp -> TMEM lane quarter (warp % 4) and column group (warp / 4).
   const int quarter = warp & 3;
   const int cgroup = warp >> 2;
-  constexpr int kGroups = kTcThreads / 128;
-  constexpr int kCols = W / kGroups;  // accumulator columns per thread in hidden epilogues
   const int row = quarter * 32 + lane;
   const uint32_t t_row = tmem + (uint32_t(quarter * 32) << 16);
-  const uint32_t t_a = t_row + lay.col_a;
-  uint32_t phase = 0;
+  uint32_t phase = 0;         // parity of `bar`
+  uint32_t g = 0;             // first-layer chunk rounds so far (buffer g & 1)
+  uint32_t tma_pending[2] = {~0u, ~0u};  // thread 0: round of a streamed copy not yet seen complete
   bool failed = false;
-  constexpr int LPC = 8 / F;  // levels per 8-feature chunk (4 TMEM columns)
-  const bool chunked = (L % LPC) == 0;
+  constexpr bool kSplitX = F == 2 && sizeof(T) == 2;  // 4-byte entries: x-corner lane split
 
   int cur = 0;  // persistent query: the row buffer of the tile being evaluated
   for (int64_t tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
     int ccount = 0;       // persistent query: items in this tile
     bool staged = false;  // its rows were staged while the previous tile finished
+    const RowBuf rb = row_buf(rows_base + size_t(cur) * kTcM * kRowBytes);
     if (persistent) {
-      bind_rows(cur, sray, st0, st1, sslot, sbest, snext);
       const int pre = s_count[cur];
       if (pre != kPqNoTile) {
         ccount = pre;
@@ -638,43 +830,38 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
     }
     if (persistent && !staged) {
       if (threadIdx.x < kTcM) {
-        if (int(threadIdx.x) < ccount) {
-          pq_stage(a, s_start[cur] + threadIdx.x, threadIdx.x, sray, st0, st1, sslot, sbest, snext);
-        } else {
-          sray[threadIdx.x] = -1;
-          st0[threadIdx.x] = 0.0f;
-          st1[threadIdx.x] = 0.0f;
-        }
+        if (int(threadIdx.x) < ccount)
+          pq_stage(a, s_start[cur] + threadIdx.x, threadIdx.x, rb);
+        else
+          put_row(rb, a.rays, threadIdx.x, -1, 0.0f, 0.0f);
       }
       __syncthreads();
     } else if (!persistent) {
-    if (threadIdx.x < kTcM) {
-      const int64_t i = tile * kTcM + threadIdx.x;
-      int ray = -1;
-      float t0 = 0.0f, t1 = 0.0f;
-      if (i < n_items) {
-        if constexpr (MODE == 1) {
-          const size_t nr = size_t(a.n_rays);
-          ray = a.queue[i];
-          const size_t q = size_t(a.wave) * nr + size_t(ray);
-          t0 = a.seg_t0[q];
-          t1 = a.seg_t1[q];
-        } else if constexpr (MODE == 2) {
-          const int r = a.tr.order ? a.tr.order[i] : int(i);
-          ray = a.tr.leaf[r] >= 0 ? r : -1;
-          t0 = a.list_t0[r];
-          t1 = a.list_t1[r];
-        } else {
-          ray = a.seg_ray[i];
-          t0 = a.list_t0[i];
-          t1 = a.list_t1[i];
+      if (threadIdx.x < kTcM) {
+        const int64_t i = tile * kTcM + threadIdx.x;
+        int ray = -1;
+        float t0 = 0.0f, t1 = 0.0f;
+        if (i < n_items) {
+          if constexpr (MODE == 1) {
+            const size_t nr = size_t(a.n_rays);
+            ray = a.queue[i];
+            const size_t q = size_t(a.wave) * nr + size_t(ray);
+            t0 = a.seg_t0[q];
+            t1 = a.seg_t1[q];
+          } else if constexpr (MODE == 2) {
+            const int r = a.tr.order ? a.tr.order[i] : int(i);
+            ray = a.tr.leaf[r] >= 0 ? r : -1;
+            t0 = a.list_t0[r];
+            t1 = a.list_t1[r];
+          } else {
+            ray = a.seg_ray[i];
+            t0 = a.list_t0[i];
+            t1 = a.list_t1[i];
+          }
         }
+        put_row(rb, a.rays, threadIdx.x, ray, t0, t1);
       }
-      sray[threadIdx.x] = ray;
-      st0[threadIdx.x] = t0;
-      st1[threadIdx.x] = t1;
-    }
-    __syncthreads();
+      __syncthreads();
     }
     const int64_t grow = tile * kTcM + row;  // global item of this thread's row
     uint16_t* x16 = nullptr;                 // training: this item's column of the stored features
@@ -682,164 +869,165 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
       if (grow < n_items) x16 = a.tr.X16 + grow;
     }
     const int64_t xld = MODE == 2 ? a.tr.ld : 0;
-    // feature-major store of two 16-bit features (one packed word) at feature k2
-    auto store_x = [&](int k2, uint32_t w) {
-      x16[int64_t(k2) * xld] = uint16_t(w & 0xffffu);
-      x16[int64_t(k2 + 1) * xld] = uint16_t(w >> 16);
+    // feature-major store of the valid features of one item (original order)
+    auto store_item = [&](int k, int l0, const uint32_t* pk) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        if (l0 + j / F < L) x16[int64_t(k * L * F + l0 * F + j) * xld] = uint16_t(pk[j >> 1] >> (16 * (j & 1)));
+      }
     };
 
-    // ---- encode into TMEM: warp w owns rows 32 (w % 4) + lane and samples
-    // w / 4, w / 4 + kGroups, ...; lanes = consecutive rows (consecutive queue items),
-    // or, for 4-byte entries, pairs of lanes sharing the cells of two rows.
-    constexpr bool kSplitX = F == 2 && sizeof(T) == 2;  // 4-byte entries: x-corner lane split
-    if constexpr (kSplitX) {
-      if (chunked) {
+    // ---- layer 1 over K chunks: gather chunk r into buffer g & 1 while the
+    // tensor cores multiply chunk r - 1
+    for (int r = 0; r < lay.R; ++r, ++g) {
+      const int b = int(g & 1u);
+      if (g >= 2) {  // buffer b was read by the MMAs of round g - 2
+        const bool ok = mbar_wait(mma_done + b, ((g - 2) >> 1) & 1u);
+        if (__syncthreads_or(!ok || s_fail)) {
+          failed = true;
+          break;
+        }
+        tc_fence_after();
+      }
+      if (stream && threadIdx.x == 0 && !s_fail) {  // after a failed wait no further copy is issued
+        mbar_expect_tx(w_full + b, lay.chunk_bytes);
+        bulk_g2s(sW1 + size_t(b) * lay.chunk_bytes,
+                 static_cast<const uint8_t*>(a.w1_image) + size_t(r) * lay.chunk_bytes, lay.chunk_bytes, w_full + b);
+        tma_pending[b] = g;
+      }
+      const uint32_t t_buf = t_row + lay.col_a + uint32_t(b * (kKC / 2));
+      const int it_begin = r * kChunkItems + cgroup * IPG;  // this warp group's first item
+      const int c_begin = cgroup * IPG * 4;                   // its first column in the buffer
+      if constexpr (kSplitX) {
         // Lanes i and i ^ 16 share cells: lane i loads the four corners with
         // x bit (i >> 4) of rows 32q + (i & 15) and 32q + 16 + (i & 15), so one
         // warp request fetches both x-neighbours of 16 cells (one 128-byte
         // line almost always) instead of 32 cells' corners with one x bit.
-        // Each lane then adds its partner's partial sums for its own row.
         const int xb = lane >> 4;
         const int r0 = quarter * 32 + (lane & 15), r1 = r0 + 16;
-        const int ray0 = sray[r0], ray1 = sray[r1];
-        for (int k = cgroup; k < N; k += kGroups) {
-          float p0[3] = {0.0f, 0.0f, 0.0f}, p1[3] = {0.0f, 0.0f, 0.0f};
-          if (ray0 >= 0)
-            sample_point(a.gp, a.rays.ox[ray0], a.rays.oy[ray0], a.rays.oz[ray0], a.rays.dx[ray0],
-                         a.rays.dy[ray0], a.rays.dz[ray0], st0[r0], st1[r0], k, p0[0], p0[1], p0[2]);
-          if (ray1 >= 0)
-            sample_point(a.gp, a.rays.ox[ray1], a.rays.oy[ray1], a.rays.oz[ray1], a.rays.dx[ray1],
-                         a.rays.dy[ray1], a.rays.dz[ray1], st0[r1], st1[r1], k, p1[0], p1[1], p1[2]);
-          const uint32_t col0 = uint32_t(k * L * F) / 2u;
-          auto chunk = [&](int l0) {
-            float h0[8], h1[8];  // partial features of rows r0 and r1 over this lane's x bit
-            encode_xhalf<T, 2>(a.gp, table, l0, p0, p1, ray0 >= 0, ray1 >= 0, xb, h0, h1);
-            encode_xhalf<T, 2>(a.gp, table, l0 + 2, p0, p1, ray0 >= 0, ray1 >= 0, xb, h0 + 4, h1 + 4);
-            uint32_t pk[4];
+        const bool v0 = rb.ray[r0] >= 0, v1 = rb.ray[r1] >= 0;
+        float p0[3] = {0.0f, 0.0f, 0.0f}, p1[3] = {0.0f, 0.0f, 0.0f};
+        if (L == 16 && lay.IPS == 4 && IPG % 4 == 0) {
+          // whole samples per warp group, the 16 levels unrolled
+#pragma unroll 1
+          for (int s = 0; s < IPG / 4; ++s) {
+            const int k = it_begin / 4 + s;
+            const uint32_t col = uint32_t(c_begin + 16 * s);
+            if (k < N) {
+              if (v0) row_point(a.gp, rb, r0, k, p0);
+              if (v1) row_point(a.gp, rb, r1, k, p1);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-              // send the partner the row it owns (r1 for lanes 0-15, r0 for 16-31)
-              const float s0 = xb ? h0[2 * i] : h1[2 * i], s1 = xb ? h0[2 * i + 1] : h1[2 * i + 1];
-              const float g0 = __shfl_xor_sync(0xffffffffu, s0, 16), g1 = __shfl_xor_sync(0xffffffffu, s1, 16);
-              const float m0 = xb ? h1[2 * i] : h0[2 * i], m1 = xb ? h1[2 * i + 1] : h0[2 * i + 1];
-              pk[i] = pack2<BF16>(m0 + g0, m1 + g1);
-            }
-            if (x16) {
-#pragma unroll
-              for (int i = 0; i < 4; ++i) store_x(2 * int(col0) + l0 * F + 2 * i, pk[i]);
-            }
-            __syncwarp();
-            tmem_st4(t_a + col0 + uint32_t(l0 * F) / 2u, pk);
-          };
-          if (L == 16) {  // the common level count: levels unrolled, their parameters at fixed offsets
-#pragma unroll
-            for (int l0 = 0; l0 < 16; l0 += 4) chunk(l0);
-          } else {
-            for (int l0 = 0; l0 < L; l0 += 4) chunk(l0);
-          }
-        }
-      }
-    }
-    for (int k = cgroup; k < N && !(kSplitX && chunked); k += kGroups) {
-      const int ray = sray[row];
-      const bool valid = ray >= 0;
-      float x = 0.0f, y = 0.0f, z = 0.0f;
-      if (valid)
-        sample_point(a.gp, a.rays.ox[ray], a.rays.oy[ray], a.rays.oz[ray], a.rays.dx[ray], a.rays.dy[ray],
-                     a.rays.dz[ray], st0[row], st1[row], k, x, y, z);
-      const uint32_t col0 = uint32_t(k * L * F) / 2u;
-      if (chunked) {
-        for (int l0 = 0; l0 < L; l0 += LPC) {
-          float v[8];
-          if (valid) {
-            if constexpr (LPC % 2 == 0) {
-              if constexpr (LPC == 4) {
-                encode_levels<T, F, 4>(a.gp, table, l0, x, y, z, v);
-              } else {
-#pragma unroll
-                for (int q = 0; q < LPC; q += 2) encode_levels<T, F, 2>(a.gp, table, l0 + q, x, y, z, v + q * F);
+              for (int q = 0; q < 4; ++q) {
+                uint32_t pk[4];
+                split_item<T, BF16, true>(a.gp, table, 4 * q, 16, p0, p1, v0, v1, xb, pk);
+                if (x16) store_item(k, 4 * q, pk);
+                __syncwarp();
+                tmem_st4(t_buf + col + 4 * q, pk);
               }
             } else {
-              encode_levels<T, F, LPC>(a.gp, table, l0, x, y, z, v);
-            }
-          } else {
+              const uint32_t z[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
-            for (int i = 0; i < 8; ++i) v[i] = 0.0f;
+              for (int q = 0; q < 4; ++q) tmem_st4(t_buf + col + 4 * q, z);
+            }
+          }
+        } else {
+          int kcur = -1;
+#pragma unroll 1
+          for (int i = 0; i < IPG; ++i) {
+            const int it = it_begin + i;
+            uint32_t pk[4] = {0u, 0u, 0u, 0u};
+            if (it < lay.NI) {
+              const int k = it / lay.IPS, l0 = (it - k * lay.IPS) * 4;
+              if (k != kcur) {
+                if (v0) row_point(a.gp, rb, r0, k, p0);
+                if (v1) row_point(a.gp, rb, r1, k, p1);
+                kcur = k;
+              }
+              if (l0 + 4 <= L)
+                split_item<T, BF16, true>(a.gp, table, l0, L, p0, p1, v0, v1, xb, pk);
+              else
+                split_item<T, BF16, false>(a.gp, table, l0, L, p0, p1, v0, v1, xb, pk);
+              if (x16) store_item(k, l0, pk);
+            }
+            __syncwarp();
+            tmem_st4(t_buf + uint32_t(c_begin + 4 * i), pk);
+          }
+        }
+      } else {
+        const bool valid = rb.ray[row] >= 0;
+        float pt[3] = {0.0f, 0.0f, 0.0f};
+        int kcur = -1;
+#pragma unroll 1
+        for (int i = 0; i < IPG; ++i) {
+          const int it = it_begin + i;
+          float v[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) v[j] = 0.0f;
+          int k = 0, l0 = 0;
+          if (it < lay.NI) {
+            k = it / lay.IPS;
+            l0 = (it - k * lay.IPS) * LPC;
+            if (valid) {
+              if (k != kcur) {
+                row_point(a.gp, rb, row, k, pt);
+                kcur = k;
+              }
+              row_item<T, F>(a.gp, table, l0, L, pt, v);
+            }
           }
           uint32_t pk[4];
 #pragma unroll
-          for (int i = 0; i < 4; ++i) pk[i] = pack2<BF16>(v[2 * i], v[2 * i + 1]);
-          if (x16) {
-#pragma unroll
-            for (int i = 0; i < 4; ++i) store_x(2 * int(col0) + l0 * F + 2 * i, pk[i]);
-          }
+          for (int j = 0; j < 4; ++j) pk[j] = pack2<BF16>(v[2 * j], v[2 * j + 1]);
+          if (x16 && it < lay.NI) store_item(k, l0, pk);
           __syncwarp();
-          tmem_st4(t_a + col0 + uint32_t(l0 * F) / 2u, pk);
-        }
-      } else if constexpr (F >= 2) {  // level by level: F/2 columns each
-        for (int l = 0; l < L; ++l) {
-          float v[F];
-          if (valid) {
-            encode_level<T, F>(a.gp, table, l, x, y, z, v);
-          } else {
-#pragma unroll
-            for (int i = 0; i < F; ++i) v[i] = 0.0f;
-          }
-          uint32_t pk[F / 2];
-#pragma unroll
-          for (int i = 0; i < F / 2; ++i) pk[i] = pack2<BF16>(v[2 * i], v[2 * i + 1]);
-          if (x16) {
-#pragma unroll
-            for (int i = 0; i < F / 2; ++i) store_x(2 * int(col0) + l * F + 2 * i, pk[i]);
-          }
-          __syncwarp();
-          tmem_st_cols<F / 2>(t_a + col0 + uint32_t(l * F) / 2u, pk);
-        }
-      } else {  // F = 1 (even level count): one column per two levels
-        for (int l = 0; l < L; l += 2) {
-          float v[2] = {0.0f, 0.0f};
-          if (valid) {
-            encode_level<T, F>(a.gp, table, l, x, y, z, v);
-            encode_level<T, F>(a.gp, table, l + 1, x, y, z, v + 1);
-          }
-          const uint32_t w = pack2<BF16>(v[0], v[1]);
-          if (x16) store_x(2 * int(col0) + l, w);
-          __syncwarp();
-          tmem_st1(t_a + col0 + uint32_t(l) / 2u, w);
+          tmem_st4(t_buf + uint32_t(c_begin + 4 * i), pk);
         }
       }
-    }
-    if (Kp > K) {  // zero padding columns (K is even, so padding starts on a column)
-      if (cgroup == 0) {
-        for (int c = K / 2; c < Kp / 2; ++c) {
-          tmem_st1(t_a + uint32_t(c), 0u);
-          if (x16) store_x(2 * c, 0u);
+      tmem_st_wait();
+      tc_fence_before();
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        tc_fence_after();
+        bool ok = !s_fail;
+        if (stream && ok) {
+          ok = mbar_wait(w_full + b, (g >> 1) & 1u);
+          if (ok) tma_pending[b] = ~0u;
         }
+        if (ok) {
+          const int steps = min(kKC, lay.KP - r * kKC) / 16;
+          const uint32_t wb = smem_u32(sW1 + size_t(stream ? b : r) * lay.chunk_bytes);
+          for (int j = 0; j < steps; ++j)
+            mma_f16_ts(tmem, tmem + lay.col_a + uint32_t(b * (kKC / 2) + 8 * j),
+                       smem_desc(wb + j * 256, 128, kKC * 16), idesc_h, (r > 0 || j > 0) ? 1u : 0u);
+        } else {
+          s_fail = 1;
+        }
+        mma_commit(mma_done + b);  // also when nothing was issued: keeps the phases in step
       }
     }
-    tmem_st_wait();
-    tc_fence_before();
-    __syncthreads();
-
-    // ---- layer 1: A = features (TMEM) x W1 (smem) -> D
-    if (threadIdx.x == 0) {
-      tc_fence_after();
-      const uint32_t sbo = uint32_t(Kp) * 16, w1_addr = smem_u32(sW1);
-      for (int j = 0; j < Kp / 16; ++j)
-        mma_f16_ts(tmem, tmem + lay.col_a + uint32_t(8 * j), smem_desc(w1_addr + j * 256, 128, sbo), idesc_h, j > 0);
-      mma_commit(bar);
-    }
-    // ---- each hidden layer: wait, bias + ReLU into H (TMEM), next MMA
-    for (int h = 0; h < a.n_hidden; ++h) {
-      // bias of layer h: b0 follows W0; hidden layer h >= 1 is [W][W] then [W]
-      const float* bias = h == 0 ? b1 : b1 + W + size_t(h - 1) * (W * W + W) + size_t(W) * W;
-      const bool ok = mbar_wait(bar, phase);
-      phase ^= 1u;
-      if (__syncthreads_or(!ok)) {
+    if (failed) break;
+    {  // the first layer's last chunk (and with it every earlier one) is done
+      const uint32_t gl = g - 1;
+      const bool ok = mbar_wait(mma_done + (gl & 1u), (gl >> 1) & 1u);
+      if (__syncthreads_or(!ok || s_fail)) {
         failed = true;
         break;
       }
       tc_fence_after();
+    }
+    // ---- each hidden layer: bias + ReLU into H (TMEM), next MMA, wait
+    for (int h = 0; h < a.n_hidden; ++h) {
+      // bias of layer h: b0 follows W0; hidden layer h >= 1 is [W][W] then [W]
+      const float* bias = h == 0 ? b1 : b1 + W + size_t(h - 1) * (W * W + W) + size_t(W) * W;
+      if (h > 0) {
+        const bool ok = mbar_wait(bar, phase);
+        phase ^= 1u;
+        if (__syncthreads_or(!ok)) {
+          failed = true;
+          break;
+        }
+        tc_fence_after();
+      }
       {
         float v[kCols];
         tmem_ld_cols<kCols>(t_row + uint32_t(cgroup * kCols), v);
@@ -889,19 +1077,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
         float raw[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) raw[j] = j < n_out ? v[j] + __ldg(bo + j) : 0.0f;
-        const int ray = sray[row];
+        const int ray = rb.ray[row];
         if constexpr (MODE == 1) {
           if (persistent) {
-            // the row's ray id stays in sray only if its next segment is queued
-            const bool push = ray >= 0 && pq_resolve(a, ray, sslot[row], sbest[row], snext[row], raw, st0[row],
-                                                     st1[row]);
-            sray[row] = push ? ray : -1;
+            // the row's ray id stays in the row buffer only if its next segment is queued
+            const bool push = ray >= 0 && pq_resolve(a, ray, rb.slot[row], rb.best[row], rb.next[row], raw,
+                                                     rb.t0[row], rb.t1[row]);
+            rb.ray[row] = push ? ray : -1;
           } else {
-            wave_resolve(a, ray >= 0, ray, raw, st0[row], st1[row]);
+            wave_resolve(a, ray >= 0, ray, raw, rb.t0[row], rb.t1[row]);
           }
         } else if constexpr (MODE == 2) {
           if (grow < n_items) {
-            float g[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            float gr[8] = {0, 0, 0, 0, 0, 0, 0, 0};
             float term = 0.0f;
             if (a.tr.lab.hit && ray >= 0) {
               const float inv_valid = 1.0f / float(max(1, *a.tr.n_valid));
@@ -914,7 +1102,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
                 alb[2] = a.tr.lab.ab[ray];
               }
               term = loss_terms(raw, float(a.tr.lab.hit[ray]), a.tr.lab.depth[ray], a.tr.lab.nx[ray],
-                                a.tr.lab.ny[ray], a.tr.lab.nz[ray], has_alb ? alb : nullptr, ls * inv_valid, g);
+                                a.tr.lab.ny[ray], a.tr.lab.nz[ray], has_alb ? alb : nullptr, ls * inv_valid, gr);
             }
 #pragma unroll
             for (int j = 0; j < 8; ++j)
@@ -922,7 +1110,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
             if (a.tr.lab.hit) {
 #pragma unroll
               for (int j = 0; j < 8; ++j)
-                if (j < n_out) a.tr.G[grow * n_out + j] = g[j];
+                if (j < n_out) a.tr.G[grow * n_out + j] = gr[j];
               a.tr.loss_seg[grow] = term;
             }
           }
@@ -936,9 +1124,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
         // meanwhile warps 4-7 claim the next tile if a full one is queued and
         // stage its rows into the other buffer
         const int nb = cur ^ 1;
-        int *ry, *sl;
-        float *b0, *b1, *be, *nx;
-        bind_rows(nb, ry, b0, b1, sl, be, nx);
         if (threadIdx.x == 128) {
           unsigned long long st = 0;
           s_count[nb] = pq_try_claim(a.pq, &st);
@@ -946,7 +1131,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
         }
         asm volatile("bar.sync 1, 128;" ::: "memory");
         if (s_count[nb] != kPqNoTile)
-          pq_stage(a, s_start[nb] + (threadIdx.x - 128), threadIdx.x - 128, ry, b0, b1, sl, be, nx);
+          pq_stage(a, s_start[nb] + (threadIdx.x - 128), threadIdx.x - 128,
+                   row_buf(rows_base + size_t(nb) * kTcM * kRowBytes));
       }
       tc_fence_before();
       __syncthreads();
@@ -956,13 +1142,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
       // per warp, each item written into its entry) and retire the tile's
       // items, while the other warps go on to the next tile.
       if (warp < 4) {
-        const int pray = sray[threadIdx.x];
+        const int pray = rb.ray[threadIdx.x];
         const unsigned m = __ballot_sync(0xffffffffu, pray >= 0);
         unsigned long long base = 0;
         if (m && lane == 0) base = atomicAdd(a.pq.reserved, (unsigned long long)__popc(m));
         base = __shfl_sync(0xffffffffu, base, 0);
         if (pray >= 0) {
-          const unsigned long long item = (unsigned long long)(sslot[threadIdx.x] + 1) << 32 | uint32_t(pray);
+          const unsigned long long item = (unsigned long long)(rb.slot[threadIdx.x] + 1) << 32 | uint32_t(pray);
           if (!pq_put(a.pq, base + __popc(m & ((1u << lane) - 1u)), (unsigned long long)a.n_rays, item))
             set_status(NBVH_ERR_TIMEOUT);
         }
@@ -974,64 +1160,138 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_tc_kernel(EvalArgs a) {
   }
   if (failed) set_status(NBVH_ERR_TIMEOUT);
   __syncthreads();
+  if (threadIdx.x == 0) {
+    // before the columns are freed: every MMA this thread issued has retired,
+    // and no bulk copy into shared memory is still in flight (bounded waits)
+    mma_commit(bar_fin);
+    if (!mbar_wait(bar_fin, 0)) set_status(NBVH_ERR_TIMEOUT);
+    for (int b = 0; b < 2; ++b)
+      if (tma_pending[b] != ~0u && !mbar_wait(w_full + b, (tma_pending[b] >> 1) & 1u)) set_status(NBVH_ERR_TIMEOUT);
+  }
+  __syncthreads();
   if (warp == 0) {
     tc_fence_after();
     tmem_dealloc(tmem, lay.ncols);
   }
 }
 
-template <typename T, int F, int W, int MODE>
-cudaError_t launch_tc_twf(const nbvh_model_desc* d, const EvalArgs& a, int64_t n_items_max, cudaStream_t s) {
-  const TcLayout lay = tc_layout(a.gp.n_inputs, W, a.n_hidden);
-  if (lay.total > 227 * 1024 || W < 32 || lay.ncols > 512 || (a.gp.n_inputs & 1) ||
-      (F == 1 && (a.gp.n_levels & 1)))
-    return cudaErrorInvalidConfiguration;
+// ---------------------------------------------------------------- launch plan
+// Threads per CTA and placement of the first layer's weights for a model:
+// 256 threads (two CTAs per SM: 256 TMEM columns and at most ~113 KB of
+// shared memory each) or 512 (one CTA per SM); the weights resident in shared
+// memory, or streamed chunk by chunk from a prepared 16-bit image when they do
+// not fit (or when the caller asks for it).
+struct TcPlan {
+  bool ok;           // stageable (shared memory and TMEM within the SM's limits)
+  int threads;       // 256 or 512
+  bool stream;       // first-layer weights streamed from the image
+  uint32_t smem;     // dynamic shared memory per CTA
+  uint32_t ncols;    // TMEM columns per CTA
+  size_t image_bytes;  // size of the streamed image (R chunks)
+};
+
+constexpr uint32_t kSmemMax = 227 * 1024;       // per CTA
+constexpr uint32_t kSmemHalf = 113 * 1024;      // per CTA with two CTAs on an SM
+
+inline TcPlan tc_plan(const nbvh_model_desc* d, int threads_opt, int w1_mode) {
+  TcPlan p;
+  std::memset(&p, 0, sizeof(p));
+  const int W = d->width;
+  if (W < 32 || W > 128 || d->n_out > 16) return p;
+  const TcLayout res = tc_layout(d->n_levels, d->n_features, d->n_samples, W, d->n_hidden, false);
+  const TcLayout str = tc_layout(d->n_levels, d->n_features, d->n_samples, W, d->n_hidden, true);
+  p.threads = threads_opt != 0 ? threads_opt : (W <= 64 ? 256 : 512);
+  if (p.threads != 256 && p.threads != 512) return p;
+  if (p.threads == 256 && W > 64) return p;
+  const uint32_t budget = p.threads == 256 ? kSmemHalf : kSmemMax;
+  if (w1_mode == NBVH_W1_RESIDENT) p.stream = false;
+  else if (w1_mode == NBVH_W1_STREAMED) p.stream = true;
+  else p.stream = res.total > budget;
+  const TcLayout& T = p.stream ? str : res;
+  p.smem = T.total;
+  p.ncols = T.ncols;
+  p.image_bytes = size_t(T.R) * T.chunk_bytes;
+  p.ok = T.total <= kSmemMax && T.ncols <= 512;
+  return p;
+}
+
+// Bytes of the streamed first-layer image of any plan of this model.
+inline size_t tc_image_bytes(const nbvh_model_desc* d) {
+  const TcLayout T = tc_layout(d->n_levels, d->n_features, d->n_samples, d->width, d->n_hidden, true);
+  return size_t(T.R) * T.chunk_bytes;
+}
+
+template <typename T, int F, int W, int MODE, int NT>
+cudaError_t launch_tc_nt(const nbvh_model_desc* d, const EvalArgs& a, int64_t n_items_max, const TcPlan& pl,
+                         cudaStream_t s) {
   const bool bf16 = d->mlp_prec == NBVH_BF16;
-  auto kern = bf16 ? eval_tc_kernel<T, F, W, MODE, true> : eval_tc_kernel<T, F, W, MODE, false>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(lay.total));
+  auto kern = bf16 ? eval_tc_kernel<T, F, W, MODE, true, NT> : eval_tc_kernel<T, F, W, MODE, false, NT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pl.smem));
   if (e != cudaSuccess) return e;
-  // One CTA per SM: every CTA holds its weights and TMEM columns for the whole launch.
-  int64_t tiles = (n_items_max + kTcM - 1) / kTcM;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, pl.smem);
+  if (e != cudaSuccess) return e;
+  // co-resident CTAs share the SM's 512 TMEM columns
+  occ = std::min(occ, int(512 / pl.ncols));
+  if (occ < 1) return cudaErrorInvalidConfiguration;
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int64_t grid = sms;
+  const int64_t tiles = (n_items_max + kTcM - 1) / kTcM;
+  int64_t grid = int64_t(sms) * occ;
   if (tiles < grid) grid = tiles;
   if (grid < 1) return cudaSuccess;
-  kern<<<unsigned(grid), kTcThreads, lay.total, s>>>(a);
+  kern<<<unsigned(grid), NT, pl.smem, s>>>(a);
   count_launches(1);
   return cudaGetLastError();
 }
 
+template <typename T, int F, int W, int MODE>
+cudaError_t launch_tc_twf(const nbvh_model_desc* d, const EvalArgs& a, int64_t n, const TcPlan& pl, cudaStream_t s) {
+  if (!pl.ok || (pl.stream && !a.w1_image) || (!pl.stream && a.w1_image)) return cudaErrorInvalidConfiguration;
+  if constexpr (W <= 64) {
+    if (pl.threads == 256) return launch_tc_nt<T, F, W, MODE, 256>(d, a, n, pl, s);
+  }
+  if (pl.threads == 512) return launch_tc_nt<T, F, W, MODE, 512>(d, a, n, pl, s);
+  return cudaErrorInvalidConfiguration;
+}
+
 template <typename T, int F, int MODE>
-cudaError_t launch_tc_tf(const nbvh_model_desc* d, const EvalArgs& a, int64_t n, cudaStream_t s) {
+cudaError_t launch_tc_tf(const nbvh_model_desc* d, const EvalArgs& a, int64_t n, const TcPlan& pl, cudaStream_t s) {
   switch (a.width) {
-    case 32: return launch_tc_twf<T, F, 32, MODE>(d, a, n, s);
-    case 64: return launch_tc_twf<T, F, 64, MODE>(d, a, n, s);
-    case 128: return launch_tc_twf<T, F, 128, MODE>(d, a, n, s);
+    case 32: return launch_tc_twf<T, F, 32, MODE>(d, a, n, pl, s);
+    case 64: return launch_tc_twf<T, F, 64, MODE>(d, a, n, pl, s);
+    case 128: return launch_tc_twf<T, F, 128, MODE>(d, a, n, pl, s);
   }
   return cudaErrorInvalidConfiguration;
 }
 
+// The kernels of one table type and mode (one translation unit each).
 template <typename T, int MODE>
-cudaError_t launch_tc_t(const nbvh_model_desc* d, const EvalArgs& a, int64_t n, cudaStream_t s) {
+cudaError_t launch_tc_tm(const nbvh_model_desc* d, const EvalArgs& a, int64_t n, const TcPlan& pl, cudaStream_t s) {
   switch (d->n_features) {
-    case 1: return launch_tc_tf<T, 1, MODE>(d, a, n, s);
-    case 2: return launch_tc_tf<T, 2, MODE>(d, a, n, s);
-    case 4: return launch_tc_tf<T, 4, MODE>(d, a, n, s);
-    case 8: return launch_tc_tf<T, 8, MODE>(d, a, n, s);
+    case 1: return launch_tc_tf<T, 1, MODE>(d, a, n, pl, s);
+    case 2: return launch_tc_tf<T, 2, MODE>(d, a, n, pl, s);
+    case 4: return launch_tc_tf<T, 4, MODE>(d, a, n, pl, s);
+    case 8: return launch_tc_tf<T, 8, MODE>(d, a, n, pl, s);
   }
   return cudaErrorInvalidValue;
 }
 
-template <int MODE>
-cudaError_t launch_tc(const nbvh_model_desc* d, const EvalArgs& a, int64_t n, cudaStream_t s) {
-  switch (d->table_prec) {
-    case NBVH_FP32: return launch_tc_t<float, MODE>(d, a, n, s);
-    case NBVH_FP16: return launch_tc_t<__half, MODE>(d, a, n, s);
-    case NBVH_BF16: return launch_tc_t<__nv_bfloat16, MODE>(d, a, n, s);
-  }
-  return cudaErrorInvalidValue;
+// The prepared image of the first layer's weights (plan with stream set).
+inline cudaError_t launch_w1_image(const nbvh_model_desc* d, const float* mlp, void* img, cudaStream_t s) {
+  const TcLayout T = tc_layout(d->n_levels, d->n_features, d->n_samples, d->width, d->n_hidden, true);
+  const int K = d->n_samples * d->n_levels * d->n_features;
+  const int total = d->width * T.R * kKC;
+  const unsigned grid = unsigned(std::min(1024, (total + 255) / 256));
+  if (d->mlp_prec == NBVH_BF16)
+    w1_image_kernel<true><<<grid, 256, 0, s>>>(mlp, d->width, K, d->n_levels, d->n_features, d->n_samples, T,
+                                               static_cast<uint8_t*>(img));
+  else
+    w1_image_kernel<false><<<grid, 256, 0, s>>>(mlp, d->width, K, d->n_levels, d->n_features, d->n_samples, T,
+                                                static_cast<uint8_t*>(img));
+  count_launches(1);
+  return cudaGetLastError();
 }
 
 }  // namespace nbvh

@@ -703,3 +703,69 @@ extern "C" nbvh_status nbvh_build_cut(const nbvh_node* base_nodes, int32_t n_bas
   *out_n_nodes = n_int;
   return NBVH_OK;
 }
+
+// ---------------------------------------------------------------- error-driven cut (Sec. 5.1, Sec. 5.2)
+extern "C" nbvh_status nbvh_rank_leaves(const uint32_t* hits, const uint32_t* trained, const float* loss,
+                                        int32_t n_leaves, int64_t n_rays, double* q, double* p, double* r,
+                                        float* prob) {
+  if (!hits || !trained || !loss || n_leaves < 1 || n_rays < 0 || !q || !p || !r || !prob)
+    return NBVH_ERR_INVALID_ARG;
+  // q of a hit leaf that no ray trained: the mean q of the trained leaves
+  double q_sum = 0.0;
+  int64_t q_n = 0;
+  for (int32_t i = 0; i < n_leaves; ++i)
+    if (trained[i] > 0) {
+      q_sum += double(loss[i]) / double(trained[i]);
+      ++q_n;
+    }
+  const double q_mean = q_n > 0 ? q_sum / double(q_n) : 1.0;
+  const double denom = double(std::max<int64_t>(1, n_rays));
+  double r_max = -HUGE_VAL;
+  for (int32_t i = 0; i < n_leaves; ++i) {
+    q[i] = trained[i] > 0 ? double(loss[i]) / double(trained[i]) : q_mean;
+    p[i] = double(hits[i]) / denom;
+    r[i] = (hits[i] > 0 && q[i] > 0.0) ? 2.0 * std::log(q[i]) + std::log(p[i]) : -HUGE_VAL;
+    if (std::isfinite(r[i])) r_max = std::max(r_max, r[i]);
+  }
+  if (!std::isfinite(r_max)) r_max = 0.0;
+  for (int32_t i = 0; i < n_leaves; ++i)
+    prob[i] = float(std::isfinite(r[i]) ? std::max(std::exp(r[i] - r_max), 0.005) : 0.005);
+  return NBVH_OK;
+}
+
+extern "C" nbvh_status nbvh_refine_cut(const nbvh_node* base_nodes, int32_t n_base_nodes, const int32_t* cut,
+                                       int32_t n_cut, const double* r, const float* prob, int32_t k_splits,
+                                       int32_t* new_cut, float* new_prob, int32_t cap, int32_t* n_new) {
+  if (!base_nodes || n_base_nodes < 1 || !cut || n_cut < 1 || !r || !prob || k_splits < 0 || !new_cut ||
+      !new_prob || !n_new)
+    return NBVH_ERR_INVALID_ARG;
+  // splittable: an internal base reference with a finite ranking
+  std::vector<int32_t> cand;
+  for (int32_t i = 0; i < n_cut; ++i) {
+    if (cut[i] < -n_base_nodes - 1 || cut[i] >= n_base_nodes) return NBVH_ERR_INVALID_ARG;
+    if (cut[i] >= 0 && std::isfinite(r[i])) cand.push_back(i);
+  }
+  std::stable_sort(cand.begin(), cand.end(), [&](int32_t a, int32_t b) { return r[a] > r[b]; });
+  const size_t k = std::min(size_t(k_splits), cand.size());
+  std::vector<uint8_t> chosen(size_t(n_cut), 0);
+  for (size_t i = 0; i < k; ++i) chosen[size_t(cand[i])] = 1;
+  int32_t m = 0;
+  auto put = [&](int32_t ref, float pr) {
+    if (m < cap) {
+      new_cut[m] = ref;
+      new_prob[m] = pr;
+    }
+    ++m;
+  };
+  for (int32_t i = 0; i < n_cut; ++i) {
+    if (!chosen[size_t(i)]) {
+      put(cut[i], prob[i]);
+      continue;
+    }
+    const nbvh_node& nd = base_nodes[cut[i]];
+    put(nd.child0, 1.0f);  // a new leaf has no statistics yet: it trains with probability 1
+    if (nd.child1 != 0x7fffffff) put(nd.child1, 1.0f);
+  }
+  *n_new = m;
+  return m <= cap ? NBVH_OK : NBVH_ERR_WORKSPACE_TOO_SMALL;
+}

@@ -1,5 +1,5 @@
-// Internal device helpers of the neural ray query library (sm_103a).
-// Single translation unit: nbvh_lib.cu includes every kernel file after this.
+// Internal device helpers of the neural ray query library (sm_103a), included
+// by every CUDA translation unit of the library.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -21,9 +21,30 @@ constexpr int kTraverseStack = 64;
 
 // Host-side count of kernel launches made by this library (nbvh_lib.cu).
 void count_launches(int64_t n);
+// Multiprocessors of the current device (nbvh_lib.cu).
+int sm_count();
 
-// Per-process device status word (first error wins; read+cleared by the host).
+// Device status word, one per translation unit of the library (first error
+// wins). Each unit registers a reader at load time; nbvh_get_device_status
+// reads and clears them all.
+using StatusReader = cudaError_t (*)(int* value);
+void register_status_reader(StatusReader fn);
+
+namespace {
 __device__ int g_status = 0;
+
+cudaError_t read_clear_status(int* value) {
+  cudaError_t e = cudaMemcpyFromSymbol(value, g_status, sizeof(int));
+  if (e != cudaSuccess) return e;
+  const int zero = 0;
+  return cudaMemcpyToSymbol(g_status, &zero, sizeof(int));
+}
+
+struct StatusRegistration {
+  StatusRegistration() { register_status_reader(&read_clear_status); }
+};
+StatusRegistration g_status_registration;
+}  // namespace
 
 __device__ __forceinline__ void set_status(int code) { atomicCAS(&g_status, 0, code); }
 

@@ -1,5 +1,7 @@
-// Device entry points of the C ABI (include/nbvh.h). Single CUDA translation
-// unit: the kernels live in the included headers.
+// Device entry points of the C ABI (include/nbvh.h). The heavy kernel
+// families (the fused evaluation kernels, the training kernels) are
+// instantiated in their own translation units (tu_*.cu) and reached through
+// launch.h; the small kernels live in the headers included here.
 #include <algorithm>
 #include <atomic>
 #include <cmath>
@@ -9,19 +11,41 @@
 
 #include "nbvh_host.h"
 #include "nbvh_internal.cuh"
+#include "launch.h"
 #include "traverse.cuh"
-#include "eval_plain.cuh"
-#include "eval_tc.cuh"
 #include "bounce.cuh"
 #include "tri_blas.cuh"
 #include "probe.cuh"
-#include "train.cuh"
-#include "train_tc.cuh"
 
 namespace nbvh {
 
 std::atomic<int64_t> g_launches{0};
 void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 148;
+  }
+  return n;
+}
+
+// Status words of the translation units (nbvh_internal.cuh).
+std::vector<StatusReader>& status_readers() {
+  static std::vector<StatusReader> v;
+  return v;
+}
+std::mutex& status_mu() {
+  static std::mutex m;
+  return m;
+}
+void register_status_reader(StatusReader fn) {
+  std::lock_guard<std::mutex> lk(status_mu());
+  status_readers().push_back(fn);
+}
 
 namespace {
 
@@ -56,69 +80,6 @@ bool make_grid(const nbvh_model_desc* d, GridParams& gp) {
   return true;
 }
 
-int sm_count() {
-  static int n = 0;
-  if (n == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 148;
-  }
-  return n;
-}
-
-// ---------------------------------------------------------------- plain dispatch
-template <typename T, int F, int W, bool WAVE>
-cudaError_t launch_plain_twf(const EvalArgs& a, int64_t n_items_max, cudaStream_t s) {
-  auto kern = eval_plain_kernel<T, F, W, WAVE>;
-  const size_t smem = plain_smem_bytes(a.gp.n_inputs, W, a.n_hidden, a.n_out);
-  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  if (e != cudaSuccess) return e;
-  int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kPlainThreads, smem);
-  if (e != cudaSuccess) return e;
-  if (occ < 1) occ = 1;
-  int64_t tiles = (n_items_max + kPlainTM - 1) / kPlainTM;
-  int64_t grid = int64_t(sm_count()) * occ;
-  if (tiles < grid) grid = tiles;
-  if (grid < 1) return cudaSuccess;
-  kern<<<unsigned(grid), kPlainThreads, smem, s>>>(a);
-  count_launches(1);
-  return cudaGetLastError();
-}
-
-template <typename T, int F, bool WAVE>
-cudaError_t launch_plain_tf(const EvalArgs& a, int64_t n, cudaStream_t s) {
-  switch (a.width) {
-    case 16: return launch_plain_twf<T, F, 16, WAVE>(a, n, s);
-    case 32: return launch_plain_twf<T, F, 32, WAVE>(a, n, s);
-    case 64: return launch_plain_twf<T, F, 64, WAVE>(a, n, s);
-    case 128: return launch_plain_twf<T, F, 128, WAVE>(a, n, s);
-  }
-  return cudaErrorInvalidValue;
-}
-
-template <typename T, bool WAVE>
-cudaError_t launch_plain_t(int F, const EvalArgs& a, int64_t n, cudaStream_t s) {
-  switch (F) {
-    case 1: return launch_plain_tf<T, 1, WAVE>(a, n, s);
-    case 2: return launch_plain_tf<T, 2, WAVE>(a, n, s);
-    case 4: return launch_plain_tf<T, 4, WAVE>(a, n, s);
-    case 8: return launch_plain_tf<T, 8, WAVE>(a, n, s);
-  }
-  return cudaErrorInvalidValue;
-}
-
-template <bool WAVE>
-cudaError_t launch_plain(const nbvh_model_desc* d, const EvalArgs& a, int64_t n, cudaStream_t s) {
-  switch (d->table_prec) {
-    case NBVH_FP32: return launch_plain_t<float, WAVE>(d->n_features, a, n, s);
-    case NBVH_FP16: return launch_plain_t<__half, WAVE>(d->n_features, a, n, s);
-    case NBVH_BF16: return launch_plain_t<__nv_bfloat16, WAVE>(d->n_features, a, n, s);
-  }
-  return cudaErrorInvalidValue;
-}
 
 template <typename T>
 cudaError_t launch_encode_t(int F, const GridParams& gp, const void* table, RayPtrs r, const int32_t* seg_ray,
@@ -156,10 +117,86 @@ nbvh_status status_of(cudaError_t e) {
   return NBVH_ERR_CUDA;
 }
 
-cudaError_t launch_eval(const nbvh_model_desc* d, const EvalArgs& a, bool wave, int64_t n, cudaStream_t s) {
-  if (d->mlp_prec == NBVH_FP32) return wave ? launch_plain<true>(d, a, n, s) : launch_plain<false>(d, a, n, s);
-  return wave ? launch_tc<1>(d, a, n, s) : launch_tc<0>(d, a, n, s);
+template <int MODE>
+cudaError_t launch_tc(const nbvh_model_desc* d, const EvalArgs& a, int64_t n, const TcPlan& pl, cudaStream_t s) {
+  switch (d->table_prec) {
+    case NBVH_FP32: return launch_tc_tm<float, MODE>(d, a, n, pl, s);
+    case NBVH_FP16: return launch_tc_tm<__half, MODE>(d, a, n, pl, s);
+    case NBVH_BF16: return launch_tc_tm<__nv_bfloat16, MODE>(d, a, n, pl, s);
+  }
+  return cudaErrorInvalidValue;
 }
+
+template <bool WAVE>
+cudaError_t launch_plain(const nbvh_model_desc* d, const EvalArgs& a, int64_t n, cudaStream_t s) {
+  switch (d->table_prec) {
+    case NBVH_FP32: return launch_plain_t<float, WAVE>(d->n_features, a, n, s);
+    case NBVH_FP16: return launch_plain_t<__half, WAVE>(d->n_features, a, n, s);
+    case NBVH_BF16: return launch_plain_t<__nv_bfloat16, WAVE>(d->n_features, a, n, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// Options: the caller's, or the defaults.
+nbvh_query_options default_options() {
+  nbvh_query_options o;
+  std::memset(&o, 0, sizeof(o));
+  o.schedule = NBVH_SCHEDULE_PERSISTENT;
+  o.patience_cycles = 4000;
+  o.traverse_block = 128;
+  o.eval_threads = 0;
+  o.w1_mode = NBVH_W1_AUTO;
+  return o;
+}
+
+bool options_valid(const nbvh_query_options& o) {
+  return (o.schedule == NBVH_SCHEDULE_WAVES || o.schedule == NBVH_SCHEDULE_PERSISTENT) && o.patience_cycles >= 0 &&
+         o.patience_cycles <= (int64_t(1) << 40) &&
+         (o.traverse_block == 64 || o.traverse_block == 128 || o.traverse_block == 256) &&
+         (o.eval_threads == 0 || o.eval_threads == 256 || o.eval_threads == 512) && o.w1_mode >= NBVH_W1_AUTO &&
+         o.w1_mode <= NBVH_W1_STREAMED;
+}
+
+// The evaluation kernels can run this model with these options (checked on
+// the host before anything is enqueued).
+bool eval_stageable(const nbvh_model_desc* d, const nbvh_query_options& o) {
+  if (d->mlp_prec == NBVH_FP32)
+    return plain_chunk_samples(d->n_samples, d->n_levels * d->n_features, d->width, d->n_hidden, d->n_out) >= 0;
+  return tc_plan(d, o.eval_threads, o.w1_mode).ok;
+}
+
+// The evaluation's plan for desc under options o; with a streamed plan the
+// first layer's 16-bit image is written into `image` (once per call, before
+// the evaluation launches) and a.w1_image points at it.
+cudaError_t prepare_eval(const nbvh_model_desc* d, EvalArgs& a, const nbvh_query_options& o, void* image,
+                         TcPlan* plan, cudaStream_t s) {
+  std::memset(plan, 0, sizeof(*plan));
+  a.w1_image = nullptr;
+  if (d->mlp_prec == NBVH_FP32) return cudaSuccess;
+  *plan = tc_plan(d, o.eval_threads, o.w1_mode);
+  if (!plan->ok) return cudaErrorInvalidConfiguration;
+  if (plan->stream) {
+    if (!image) return cudaErrorInvalidConfiguration;
+    cudaError_t e = launch_w1_image(d, a.mlp, image, s);
+    if (e != cudaSuccess) return e;
+    a.w1_image = image;
+  }
+  return cudaSuccess;
+}
+
+// One evaluation launch of MODE (0 list, 1 query wave or persistent, 2
+// training forward) after prepare_eval.
+template <int MODE>
+cudaError_t launch_eval(const nbvh_model_desc* d, const EvalArgs& a, int64_t n, const TcPlan& plan, cudaStream_t s) {
+  if (d->mlp_prec == NBVH_FP32) {
+    if constexpr (MODE == 2) return cudaErrorInvalidValue;
+    else return launch_plain<MODE == 1>(d, a, n, s);
+  }
+  return launch_tc<MODE>(d, a, n, plan, s);
+}
+
+// Bytes of the first-layer image an evaluation of desc may need.
+size_t image_bytes(const nbvh_model_desc* d) { return d->mlp_prec == NBVH_FP32 ? 0 : tc_image_bytes(d); }
 
 // ---------------------------------------------------------------- bookkeeping
 struct StageEvents {
@@ -189,6 +226,7 @@ struct QueryWs {
   float* seg_t0;
   float* seg_t1;
   int32_t* queue[2];
+  void* image;  // the streamed first-layer image (FP16/BF16 models)
   size_t bytes;
 };
 
@@ -199,7 +237,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 int32_t pq_base(int32_t max_segs) { return int32_t(align256(sizeof(int32_t) * size_t(max_segs + 2)) / 4); }
 size_t counters_bytes(int32_t max_segs) { return size_t(pq_base(max_segs)) * 4 + 4 * 128; }
 
-QueryWs carve_query(void* base, int64_t n, int32_t max_segs) {
+QueryWs carve_query(void* base, int64_t n, int32_t max_segs, size_t image = 0) {
   QueryWs w;
   char* p = static_cast<char*>(base);
   size_t off = 0;
@@ -216,25 +254,19 @@ QueryWs carve_query(void* base, int64_t n, int32_t max_segs) {
   // the two wave queues, or (persistent query) one ring of n 64-bit items
   w.queue[0] = reinterpret_cast<int32_t*>(take(2 * sizeof(int32_t) * size_t(n)));
   w.queue[1] = w.queue[0] ? w.queue[0] + n : nullptr;
+  w.image = image ? take(image) : nullptr;
   w.bytes = off;
   return w;
 }
 
-
-
-// Evaluation schedule of the tensor-core query (nbvh_set_query_schedule).
-std::atomic<int32_t> g_schedule{NBVH_SCHEDULE_PERSISTENT};
-std::atomic<int64_t> g_patience{4000};
-std::atomic<int32_t> g_traverse_block{128};  // threads per traversal CTA (64, 128 or 256)
-
-PQueue pq_of(const QueryWs& w, int32_t max_segs) {
+PQueue pq_of(const QueryWs& w, int32_t max_segs, int64_t patience) {
   int32_t* c = w.counters + pq_base(max_segs);
   PQueue q;
   q.head = reinterpret_cast<unsigned long long*>(c);
   q.reserved = reinterpret_cast<unsigned long long*>(c + 32);
   q.retired = reinterpret_cast<unsigned long long*>(c + 64);
   q.tiles = reinterpret_cast<unsigned int*>(c + 96);
-  q.patience = g_patience.load();
+  q.patience = patience;
   q.ring = reinterpret_cast<unsigned long long*>(w.queue[0]);
   return q;
 }
@@ -246,8 +278,8 @@ PQueue pq_of(const QueryWs& w, int32_t max_segs) {
 cudaError_t launch_query_stages(const nbvh_model_desc* desc, const GridParams& gp, const void* table,
                                 const float* mlp, const nbvh_node* nodes, const nbvh_rays& rays, int32_t max_segs,
                                 const nbvh_hits& out, const QueryWs& w, bool merge, int32_t* inst_out,
-                                int32_t inst_id, cudaEvent_t after_traverse, cudaStream_t s,
-                                const int32_t* list = nullptr, const int32_t* list_count = nullptr) {
+                                int32_t inst_id, const nbvh_query_options& o, cudaEvent_t after_traverse,
+                                cudaStream_t s, const int32_t* list = nullptr, const int32_t* list_count = nullptr) {
   TraverseOut to;
   std::memset(&to, 0, sizeof(to));
   to.seg_count = w.seg_count;
@@ -260,14 +292,14 @@ cudaError_t launch_query_stages(const nbvh_model_desc* desc, const GridParams& g
   to.hits = out;
   to.merge = merge ? 1 : 0;
   to.reverse_inside = (desc->flags & NBVH_FLAG_REVERSE_INSIDE) ? 1 : 0;
-  const bool persistent = desc->mlp_prec != NBVH_FP32 && g_schedule.load() == NBVH_SCHEDULE_PERSISTENT;
+  const bool persistent = desc->mlp_prec != NBVH_FP32 && o.schedule == NBVH_SCHEDULE_PERSISTENT;
   if (persistent) {
     to.queue0 = nullptr;
     to.ring0 = reinterpret_cast<unsigned long long*>(w.queue[0]);
     cudaError_t me = cudaMemsetAsync(w.queue[0], 0xff, 8 * size_t(rays.n), s);  // empty ring
     if (me != cudaSuccess) return me;
   }
-  const int tb = g_traverse_block.load();
+  const int tb = o.traverse_block;
   if (list) {  // only the listed rays (grid-stride over the device-side count)
     const int64_t blocks = std::min<int64_t>((rays.n + 255) / 256, int64_t(sm_count()) * 8);
     traverse_list_kernel<<<unsigned(std::max<int64_t>(blocks, 1)), 256, 0, s>>>(nodes, ray_ptrs(rays), rays.n,
@@ -289,14 +321,17 @@ cudaError_t launch_query_stages(const nbvh_model_desc* desc, const GridParams& g
   a.inst_out = inst_out;
   a.inst_id = inst_id;
   a.max_segs = max_segs;
+  TcPlan plan;
+  e = prepare_eval(desc, a, o, w.image, &plan, s);
+  if (e != cudaSuccess) return e;
   if (persistent) {
     // one launch drains a queue of (slot, ray) items
-    a.pq = pq_of(w, max_segs);
+    a.pq = pq_of(w, max_segs, o.patience_cycles);
     pq_init_kernel<<<1, 1, 0, s>>>(w.counters, a.pq);
     count_launches(1);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return launch_eval(desc, a, true, rays.n, s);
+    return launch_eval<1>(desc, a, rays.n, plan, s);
   }
   for (int wv = 0; wv < max_segs; ++wv) {
     a.wave = wv;
@@ -304,7 +339,7 @@ cudaError_t launch_query_stages(const nbvh_model_desc* desc, const GridParams& g
     a.qlen = w.counters + wv;
     a.next_queue = w.queue[(wv + 1) & 1];
     a.next_qlen = w.counters + wv + 1;
-    e = launch_eval(desc, a, true, rays.n, s);
+    e = launch_eval<1>(desc, a, rays.n, plan, s);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -352,45 +387,105 @@ extern "C" nbvh_status nbvh_encode(const nbvh_model_desc* desc, const void* tabl
   return status_of(e);
 }
 
+extern "C" nbvh_status nbvh_query_options_default(nbvh_query_options* opt) {
+  if (!opt) return NBVH_ERR_INVALID_ARG;
+  *opt = default_options();
+  return NBVH_OK;
+}
+
+extern "C" nbvh_status nbvh_eval_plan(const nbvh_model_desc* desc, const nbvh_query_options* opt,
+                                      int32_t* threads, int32_t* w1_streamed, int32_t* smem_bytes,
+                                      int32_t* tmem_cols) {
+  if (!nbvh_host::desc_valid(desc) || !threads || !w1_streamed || !smem_bytes || !tmem_cols)
+    return NBVH_ERR_INVALID_ARG;
+  const nbvh_query_options o = opt ? *opt : default_options();
+  if (!options_valid(o)) return NBVH_ERR_INVALID_ARG;
+  if (!eval_stageable(desc, o)) return NBVH_ERR_UNSUPPORTED;
+  if (desc->mlp_prec == NBVH_FP32) {
+    const int LF = desc->n_levels * desc->n_features;
+    const int cs = plain_chunk_samples(desc->n_samples, LF, desc->width, desc->n_hidden, desc->n_out);
+    *threads = kPlainThreads;
+    *w1_streamed = cs > 0 ? 1 : 0;
+    *smem_bytes = int32_t(plain_smem_bytes((cs > 0 ? cs : desc->n_samples) * LF, desc->width, desc->n_hidden,
+                                           desc->n_out));
+    *tmem_cols = 0;
+    return NBVH_OK;
+  }
+  const TcPlan pl = tc_plan(desc, o.eval_threads, o.w1_mode);
+  *threads = pl.threads;
+  *w1_streamed = pl.stream ? 1 : 0;
+  *smem_bytes = int32_t(pl.smem);
+  *tmem_cols = int32_t(pl.ncols);
+  return NBVH_OK;
+}
+
+extern "C" nbvh_status nbvh_eval_workspace_size(const nbvh_model_desc* desc, size_t* bytes) {
+  if (!nbvh_host::desc_valid(desc) || !bytes) return NBVH_ERR_INVALID_ARG;
+  *bytes = image_bytes(desc);
+  return NBVH_OK;
+}
+
 extern "C" nbvh_status nbvh_eval_segments(const nbvh_model_desc* desc, const void* table, const float* mlp,
                                           nbvh_rays rays, const int32_t* seg_ray, const float* t0,
-                                          const float* t1, int64_t n_seg, float* out, void* stream) {
+                                          const float* t1, int64_t n_seg, float* out,
+                                          const nbvh_query_options* opt, void* workspace, size_t ws_bytes,
+                                          void* stream) {
   if (!nbvh_host::desc_valid(desc) || !table || !mlp || !rays_valid(rays) || n_seg < 0)
     return NBVH_ERR_INVALID_ARG;
+  const nbvh_query_options o = opt ? *opt : default_options();
+  if (!options_valid(o)) return NBVH_ERR_INVALID_ARG;
   if (n_seg == 0) return NBVH_OK;
   if (!seg_ray || !t0 || !t1 || !out) return NBVH_ERR_INVALID_ARG;
+  if (workspace && (reinterpret_cast<uintptr_t>(workspace) & 255) != 0) return NBVH_ERR_INVALID_ARG;
+  if (ws_bytes < image_bytes(desc) || (image_bytes(desc) > 0 && !workspace)) return NBVH_ERR_WORKSPACE_TOO_SMALL;
   GridParams gp;
   if (!make_grid(desc, gp)) return NBVH_ERR_INVALID_ARG;
+  if (!eval_stageable(desc, o)) return NBVH_ERR_UNSUPPORTED;
   EvalArgs a = base_args(desc, gp, table, mlp, rays);
   a.seg_ray = seg_ray;
   a.list_t0 = t0;
   a.list_t1 = t1;
   a.n_items = n_seg;
   a.out = out;
-  return status_of(launch_eval(desc, a, false, n_seg, as_stream(stream)));
+  cudaStream_t s = as_stream(stream);
+  TcPlan plan;
+  cudaError_t e = prepare_eval(desc, a, o, workspace, &plan, s);
+  if (e == cudaSuccess) e = launch_eval<0>(desc, a, n_seg, plan, s);
+  return status_of(e);
 }
 
 extern "C" nbvh_status nbvh_query_workspace_size(const nbvh_model_desc* desc, int64_t n_rays, int32_t max_segs,
                                                  size_t* bytes) {
   if (!nbvh_host::desc_valid(desc) || n_rays < 0 || max_segs < 1 || !bytes) return NBVH_ERR_INVALID_ARG;
-  *bytes = carve_query(nullptr, n_rays, max_segs).bytes;
+  *bytes = carve_query(nullptr, n_rays, max_segs, image_bytes(desc)).bytes;
   return NBVH_OK;
 }
 
 extern "C" nbvh_status nbvh_query_rays(const nbvh_model_desc* desc, const void* table, const float* mlp,
                                        const nbvh_node* nodes, int32_t n_nodes, nbvh_rays rays, int32_t max_segs,
                                        nbvh_hits out, void* workspace, size_t ws_bytes, void* stream) {
+  return nbvh_query_rays_opt(desc, table, mlp, nodes, n_nodes, rays, max_segs, out, workspace, ws_bytes, nullptr,
+                             stream);
+}
+
+extern "C" nbvh_status nbvh_query_rays_opt(const nbvh_model_desc* desc, const void* table, const float* mlp,
+                                           const nbvh_node* nodes, int32_t n_nodes, nbvh_rays rays,
+                                           int32_t max_segs, nbvh_hits out, void* workspace, size_t ws_bytes,
+                                           const nbvh_query_options* opt, void* stream) {
   if (!nbvh_host::desc_valid(desc) || !table || !mlp || !nodes || n_nodes < 1 || !rays_valid(rays) ||
       max_segs < 1 || max_segs > 4096)
     return NBVH_ERR_INVALID_ARG;
+  const nbvh_query_options o = opt ? *opt : default_options();
+  if (!options_valid(o)) return NBVH_ERR_INVALID_ARG;
   if (rays.n == 0) return NBVH_OK;
   if (rays.n > (int64_t(1) << 31) - 1) return NBVH_ERR_INVALID_ARG;
   if (!out.hit || !out.t || !out.nx || !out.ny || !out.nz || !out.leaf || !workspace) return NBVH_ERR_INVALID_ARG;
   if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0) return NBVH_ERR_INVALID_ARG;
-  QueryWs w = carve_query(workspace, rays.n, max_segs);
+  QueryWs w = carve_query(workspace, rays.n, max_segs, image_bytes(desc));
   if (ws_bytes < w.bytes) return NBVH_ERR_WORKSPACE_TOO_SMALL;
   GridParams gp;
   if (!make_grid(desc, gp)) return NBVH_ERR_INVALID_ARG;
+  if (!eval_stageable(desc, o)) return NBVH_ERR_UNSUPPORTED;  // before anything is enqueued
   cudaStream_t s = as_stream(stream);
   cudaError_t e = cudaMemsetAsync(w.counters, 0, counters_bytes(max_segs), s);
   if (e != cudaSuccess) return NBVH_ERR_CUDA;
@@ -407,7 +502,7 @@ extern "C" nbvh_status nbvh_query_rays(const nbvh_model_desc* desc, const void* 
   }
   const bool timed = ev.e0 && ev.e1 && ev.e2;
   if (timed) cudaEventRecord(ev.e0, s);
-  e = launch_query_stages(desc, gp, table, mlp, nodes, rays, max_segs, out, w, false, nullptr, 0,
+  e = launch_query_stages(desc, gp, table, mlp, nodes, rays, max_segs, out, w, false, nullptr, 0, o,
                           timed ? ev.e1 : nullptr, s);
   if (e != cudaSuccess) return status_of(e);
   if (timed) {
@@ -415,22 +510,6 @@ extern "C" nbvh_status nbvh_query_rays(const nbvh_model_desc* desc, const void* 
     std::lock_guard<std::mutex> lk(g_timing_mu);
     g_pending.push_back(ev);
   }
-  return NBVH_OK;
-}
-
-extern "C" nbvh_status nbvh_set_query_schedule(int32_t schedule, int64_t patience_cycles) {
-  if ((schedule != NBVH_SCHEDULE_WAVES && schedule != NBVH_SCHEDULE_PERSISTENT) || patience_cycles < 0 ||
-      patience_cycles > (int64_t(1) << 40))
-    return NBVH_ERR_INVALID_ARG;
-  g_schedule.store(schedule);
-  g_patience.store(patience_cycles);
-  return NBVH_OK;
-}
-
-extern "C" nbvh_status nbvh_get_query_schedule(int32_t* schedule, int64_t* patience_cycles) {
-  if (!schedule || !patience_cycles) return NBVH_ERR_INVALID_ARG;
-  *schedule = g_schedule.load();
-  *patience_cycles = g_patience.load();
   return NBVH_OK;
 }
 
@@ -544,6 +623,17 @@ TriBlasArgs tri_args(const nbvh_tri_blas& b, const nbvh_rays& rays, const nbvh_h
   return a;
 }
 
+size_t image_bytes(const nbvh_model_desc* d);
+
+// The largest first-layer image of the neural instances (the passes run one
+// after the other on the caller's stream and share the region).
+size_t hybrid_image_bytes(const nbvh_instance* inst, int32_t n_inst) {
+  size_t m = 0;
+  for (int i = 0; i < n_inst; ++i)
+    if (inst[i].kind == NBVH_BLAS_NEURAL) m = std::max(m, image_bytes(&inst[i].desc));
+  return m;
+}
+
 int32_t hybrid_max_segs(const nbvh_instance* inst, int32_t n_inst) {
   int32_t m = 0;
   for (int i = 0; i < n_inst; ++i)
@@ -595,7 +685,7 @@ HybridWs carve_hybrid(void* base, const nbvh_instance* inst, int32_t n_inst, int
   int32_t n_neural = 0;
   for (int i = 0; i < n_inst; ++i) n_neural += inst[i].kind == NBVH_BLAS_NEURAL;
   const int32_t ms = std::max(hybrid_max_segs(inst, n_inst), 1);
-  h.q = carve_query(base, n, ms);
+  h.q = carve_query(base, n, ms, hybrid_image_bytes(inst, n_inst));
   char* p = static_cast<char*>(base);
   size_t off = h.q.bytes;
   h.lists = p ? reinterpret_cast<int32_t*>(p + off) : nullptr;
@@ -615,8 +705,10 @@ extern "C" nbvh_status nbvh_hybrid_workspace_size(const nbvh_instance* inst, int
 
 extern "C" nbvh_status nbvh_hybrid_trace(const nbvh_instance* inst, int32_t n_inst, nbvh_rays rays,
                                          nbvh_hits out, int32_t* out_inst, void* workspace, size_t ws_bytes,
-                                         void* stream) {
+                                         const nbvh_query_options* opt, void* stream) {
   if (!instances_valid(inst, n_inst) || !rays_valid(rays)) return NBVH_ERR_INVALID_ARG;
+  const nbvh_query_options o = opt ? *opt : default_options();
+  if (!options_valid(o)) return NBVH_ERR_INVALID_ARG;
   if (rays.n == 0) return NBVH_OK;
   if (!hits_valid(out) || !out_inst || !workspace || rays.n > (int64_t(1) << 31) - 1) return NBVH_ERR_INVALID_ARG;
   if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0) return NBVH_ERR_INVALID_ARG;
@@ -625,6 +717,8 @@ extern "C" nbvh_status nbvh_hybrid_trace(const nbvh_instance* inst, int32_t n_in
   std::vector<GridParams> gps(static_cast<size_t>(n_inst));
   for (int i = 0; i < n_inst; ++i)
     if (inst[i].kind == NBVH_BLAS_NEURAL && !make_grid(&inst[i].desc, gps[i])) return NBVH_ERR_INVALID_ARG;
+  for (int i = 0; i < n_inst; ++i)  // before anything is enqueued
+    if (inst[i].kind == NBVH_BLAS_NEURAL && !eval_stageable(&inst[i].desc, o)) return NBVH_ERR_UNSUPPORTED;
   cudaStream_t s = as_stream(stream);
   hits_clear_kernel<<<unsigned((rays.n + 255) / 256), 256, 0, s>>>(out, out_inst, rays.n);
   count_launches(1);
@@ -670,9 +764,9 @@ extern "C" nbvh_status nbvh_hybrid_trace(const nbvh_instance* inst, int32_t n_in
     const int32_t k = cull_slot[i];
     e = cudaMemsetAsync(hw.q.counters, 0, counters_bytes(x.max_segs), s);
     if (e != cudaSuccess) return NBVH_ERR_CUDA;
-    QueryWs wi = carve_query(workspace, rays.n, x.max_segs);
+    QueryWs wi = carve_query(workspace, rays.n, x.max_segs, hybrid_image_bytes(inst, n_inst));
     e = launch_query_stages(&x.desc, gps[i], x.table, x.mlp, x.nodes, rays, x.max_segs, out, wi, true, out_inst, i,
-                            nullptr, s, hw.lists + size_t(k) * size_t(rays.n), hw.counts + k);
+                            o, nullptr, s, hw.lists + size_t(k) * size_t(rays.n), hw.counts + k);
     if (e != cudaSuccess) return status_of(e);
   }
   return NBVH_OK;
@@ -697,18 +791,13 @@ extern "C" nbvh_status nbvh_autotune_query(const nbvh_model_desc* desc, const vo
     if (e0) cudaEventDestroy(e0);
     return NBVH_ERR_CUDA;
   }
-  const int32_t old_sched = g_schedule.load(), old_block = g_traverse_block.load();
-  const int64_t old_pat = g_patience.load();
   // one candidate: warm-up, then the median of reps timed queries
   auto time_it = [&](nbvh_tune_result& r) -> nbvh_status {
-    g_schedule.store(r.schedule);
-    g_patience.store(r.patience_cycles);
-    g_traverse_block.store(r.traverse_block);
     std::vector<float> ms;
     for (int i = 0; i <= reps; ++i) {
       if (cudaEventRecord(e0, s) != cudaSuccess) return NBVH_ERR_CUDA;
-      const nbvh_status st = nbvh_query_rays(desc, table, mlp, nodes, n_nodes, rays, max_segs, out, workspace,
-                                             ws_bytes, stream);
+      const nbvh_status st = nbvh_query_rays_opt(desc, table, mlp, nodes, n_nodes, rays, max_segs, out, workspace,
+                                                 ws_bytes, &r.opt, stream);
       if (st != NBVH_OK) return st;
       if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return NBVH_ERR_CUDA;
       float t = 0.0f;
@@ -720,49 +809,64 @@ extern "C" nbvh_status nbvh_autotune_query(const nbvh_model_desc* desc, const vo
     return NBVH_OK;
   };
   std::vector<nbvh_tune_result> cand;
-  const bool tc = desc->mlp_prec != NBVH_FP32;
-  cand.push_back({NBVH_SCHEDULE_WAVES, 0, 128, 0.0f});
-  if (tc)
-    for (int64_t p : {int64_t(0), int64_t(1000), int64_t(4000), int64_t(16000), int64_t(64000)})
-      cand.push_back({NBVH_SCHEDULE_PERSISTENT, p, 128, 0.0f});
   nbvh_status st = NBVH_OK;
-  for (auto& c : cand)
-    if ((st = time_it(c)) != NBVH_OK) break;
-  if (st == NBVH_OK) {
-    nbvh_tune_result b = cand[0];
-    for (const auto& c : cand)
-      if (c.ms < b.ms) b = c;
-    for (int32_t tb : {64, 256}) {  // traversal block size under the best schedule
-      nbvh_tune_result c = b;
-      c.traverse_block = tb;
-      if ((st = time_it(c)) != NBVH_OK) break;
-      cand.push_back(c);
-      if (c.ms < b.ms) b = c;
+  nbvh_tune_result b;
+  b.opt = default_options();
+  b.ms = 0.0f;
+  bool have = false;
+  // times c (skipping shapes the kernels cannot stage) and keeps the faster
+  auto consider = [&](nbvh_tune_result c) {
+    if (st != NBVH_OK || !eval_stageable(desc, c.opt)) return;
+    if ((st = time_it(c)) != NBVH_OK) return;
+    cand.push_back(c);
+    if (!have || c.ms < b.ms) {
+      b = c;
+      have = true;
     }
-    if (st == NBVH_OK) {
-      *best = b;
-      g_schedule.store(b.schedule);
-      g_patience.store(b.patience_cycles);
-      g_traverse_block.store(b.traverse_block);
+  };
+  const bool tc = desc->mlp_prec != NBVH_FP32;
+  {  // stage 1: schedule
+    nbvh_tune_result c;
+    c.opt = default_options();
+    c.ms = 0.0f;
+    c.opt.schedule = NBVH_SCHEDULE_WAVES;
+    c.opt.patience_cycles = 0;
+    consider(c);
+    if (tc)
+      for (int64_t p : {int64_t(0), int64_t(1000), int64_t(4000), int64_t(16000), int64_t(64000)}) {
+        c.opt.schedule = NBVH_SCHEDULE_PERSISTENT;
+        c.opt.patience_cycles = p;
+        consider(c);
+      }
+  }
+  if (tc && have) {  // stage 2: evaluation CTA shape and first-layer placement
+    const nbvh_tune_result base = b;
+    for (int32_t th : {256, 512})
+      for (int32_t wm : {NBVH_W1_RESIDENT, NBVH_W1_STREAMED}) {
+        const TcPlan cur = tc_plan(desc, base.opt.eval_threads, base.opt.w1_mode);
+        if (th == cur.threads && (wm == NBVH_W1_STREAMED) == cur.stream) continue;  // timed in stage 1
+        nbvh_tune_result c = base;
+        c.opt.eval_threads = th;
+        c.opt.w1_mode = wm;
+        consider(c);
+      }
+  }
+  if (have) {  // stage 3: traversal CTA size
+    const nbvh_tune_result base = b;
+    for (int32_t tb : {64, 256}) {
+      nbvh_tune_result c = base;
+      c.opt.traverse_block = tb;
+      consider(c);
     }
   }
-  if (st != NBVH_OK) {
-    g_schedule.store(old_sched);
-    g_patience.store(old_pat);
-    g_traverse_block.store(old_block);
-  }
+  if (st == NBVH_OK && !have) st = NBVH_ERR_UNSUPPORTED;
+  if (st == NBVH_OK) *best = b;
   const int32_t k = std::min<int32_t>(all_cap, int32_t(cand.size()));
   for (int32_t i = 0; i < k; ++i) all[i] = cand[size_t(i)];
   *n_all = int32_t(cand.size());
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return st;
-}
-
-extern "C" nbvh_status nbvh_set_traverse_block(int32_t threads) {
-  if (threads != 64 && threads != 128 && threads != 256) return NBVH_ERR_INVALID_ARG;
-  g_traverse_block.store(threads);
-  return NBVH_OK;
 }
 
 // ---------------------------------------------------------------- measurement utility
@@ -805,24 +909,53 @@ extern "C" nbvh_status nbvh_probe_l2_gather(const void* table, int64_t n_entries
 
 extern "C" nbvh_status nbvh_get_device_status(void* stream) {
   if (cudaStreamSynchronize(as_stream(stream)) != cudaSuccess) return NBVH_ERR_CUDA;
-  int v = 0;
-  if (cudaMemcpyFromSymbol(&v, g_status, sizeof(int)) != cudaSuccess) return NBVH_ERR_CUDA;
-  const int zero = 0;
-  if (cudaMemcpyToSymbol(g_status, &zero, sizeof(int)) != cudaSuccess) return NBVH_ERR_CUDA;
-  return static_cast<nbvh_status>(v);
+  std::vector<StatusReader> readers;
+  {
+    std::lock_guard<std::mutex> lk(status_mu());
+    readers = status_readers();
+  }
+  int first = 0;
+  for (StatusReader r : readers) {  // every unit's word is read and cleared
+    int v = 0;
+    if (r(&v) != cudaSuccess) return NBVH_ERR_CUDA;
+    if (first == 0) first = v;
+  }
+  return static_cast<nbvh_status>(first);
 }
 
 // ---------------------------------------------------------------- built-in scratch
 // Scratch of nbvh_query_rays_static: a fixed array in device memory, so that
 // callers who cannot allocate still get a query. Host code must not pass the
 // symbol itself to a kernel (on the host it names a stand-in, not the device
-// array); the device address comes from cudaGetSymbolAddress, once per device.
+// array); the device address comes from cudaGetSymbolAddress with the device
+// current, looked up once per device and context: a context created anew
+// after cudaDeviceReset loads the module again, so its address is looked up
+// again.
 namespace nbvh {
 namespace {
 static __device__ __align__(256) unsigned char g_static_scratch[NBVH_STATIC_SCRATCH_BYTES];
 constexpr int kMaxDevices = 64;
+struct StaticAddr {
+  void* ctx;   // the context the address belongs to
+  void* addr;  // the array's device address in it
+};
 std::mutex g_static_mu;
-void* g_static_addr[kMaxDevices] = {};
+StaticAddr g_static_addr[kMaxDevices] = {};
+
+// The calling thread's current context (driver entry point fetched through
+// the runtime, so the library does not link the driver library itself).
+cudaError_t current_context(void** ctx) {
+  using GetCurrent = int (*)(void**);
+  static GetCurrent fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    const cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !p) return cudaErrorSymbolNotFound;
+    fn = reinterpret_cast<GetCurrent>(p);
+  }
+  return fn(ctx) == 0 ? cudaSuccess : cudaErrorDeviceUninitialized;
+}
 }  // namespace
 }  // namespace nbvh
 
@@ -836,15 +969,20 @@ extern "C" nbvh_status nbvh_query_rays_static(const nbvh_model_desc* desc, const
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return NBVH_ERR_CUDA;
   if (dev < 0 || dev >= kMaxDevices) return NBVH_ERR_UNSUPPORTED;
+  void* ctx = nullptr;  // NULL until the runtime has made a context current on this thread
+  if (current_context(&ctx) != cudaSuccess) return NBVH_ERR_CUDA;
   void* base = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_static_mu);
-    if (!g_static_addr[dev]) {
-      void* p = nullptr;
+    StaticAddr& sa = g_static_addr[dev];
+    if (!sa.addr || !ctx || sa.ctx != ctx) {
+      void* p = nullptr;  // the lookup also makes the device's primary context current
       if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) return NBVH_ERR_CUDA;
-      g_static_addr[dev] = p;
+      if (current_context(&ctx) != cudaSuccess || !ctx) return NBVH_ERR_CUDA;
+      sa.addr = p;
+      sa.ctx = ctx;
     }
-    base = g_static_addr[dev];
+    base = sa.addr;
   }
   return nbvh_query_rays(desc, table, mlp, nodes, n_nodes, rays, max_segs, out, base,
                          size_t(NBVH_STATIC_SCRATCH_BYTES), stream);
@@ -854,24 +992,37 @@ extern "C" nbvh_status nbvh_query_rays_static(const nbvh_model_desc* desc, const
 namespace nbvh {
 namespace {
 
+// Training workspace. Per-ray arrays hold the whole batch of n rays; the
+// activations the backward reads (features, hidden activations, their
+// gradients) hold one chunk of `chunk` rays. chunk = n stores the whole
+// batch's activations; a smaller chunk is the recompute mode: the forward
+// runs chunk by chunk keeping only the per-ray outputs (raw outputs, dL/d(raw),
+// loss terms), and the backward runs the forward of each chunk again to
+// rebuild its activations before differentiating it.
 struct TrainWs {
   int32_t* n_valid;
-  double* loss;
+  float* loss;                       // the step's loss when the caller passes no loss_out
+  float* partial;                    // loss reduction partial sums
   float* rays[8];
   int32_t* leaf;
   float *t0, *t1;
   uint8_t* hit;
   float *depth, *nx, *ny, *nz;
-  float *ar, *ag, *ab;  // albedo labels, carved for n_out >= 8 only
-  TrainBuffers buf;
-  uint16_t *X16, *H16, *dZ16;  // tensor-core path: 16-bit operands (X16 feature-major)
-  uint16_t* dZT0;              // first layer's dZ, neuron-major
-  int64_t ld;                  // row stride of X16 and dZT0
+  float *ar, *ag, *ab;               // albedo labels, carved for n_out >= 8 only
+  float *O, *G, *loss_seg;           // per ray (or item): raw outputs, dL/d(raw), loss terms
+  int64_t chunk;                     // rays per activation chunk
+  float *X, *H, *dZ;                 // FP32 path: features [c][K], H and dZ [n_hidden][c][W]
+  uint16_t *X16, *H16, *dZ16;        // tensor-core path: 16-bit operands (X16 feature-major)
+  uint16_t* dZT0;                    // first layer's dZ, neuron-major
+  int64_t ld;                        // row stride of X16 and dZT0
+  void* image;                       // streamed first-layer image
   int32_t *counts, *cursor, *order;  // rays grouped by trained leaf (training step)
   size_t bytes;
 };
 
-TrainWs carve_train(void* base, const nbvh_model_desc* d, int64_t n, int32_t n_leaves = 0) {
+constexpr int kLossBlocks = 256;
+
+TrainWs carve_train(void* base, const nbvh_model_desc* d, int64_t n, int32_t n_leaves, int64_t chunk) {
   TrainWs w;
   std::memset(&w, 0, sizeof(w));
   char* p = static_cast<char*>(base);
@@ -883,9 +1034,11 @@ TrainWs carve_train(void* base, const nbvh_model_desc* d, int64_t n, int32_t n_l
   };
   const size_t K = size_t(d->n_samples) * d->n_levels * d->n_features;
   const size_t Wd = size_t(d->width), nh = size_t(d->n_hidden), no = size_t(d->n_out), N = size_t(n);
+  const size_t C = size_t(std::min<int64_t>(std::max<int64_t>(chunk, 1), n));
   char* small = take(256);
   w.n_valid = reinterpret_cast<int32_t*>(small);
-  w.loss = reinterpret_cast<double*>(small ? small + 16 : nullptr);
+  w.loss = reinterpret_cast<float*>(small ? small + 16 : nullptr);
+  w.partial = reinterpret_cast<float*>(take(4 * kLossBlocks));
   for (int k = 0; k < 8; ++k) w.rays[k] = reinterpret_cast<float*>(take(4 * N));
   w.leaf = reinterpret_cast<int32_t*>(take(4 * N));
   w.t0 = reinterpret_cast<float*>(take(4 * N));
@@ -900,18 +1053,23 @@ TrainWs carve_train(void* base, const nbvh_model_desc* d, int64_t n, int32_t n_l
     w.ag = reinterpret_cast<float*>(take(4 * N));
     w.ab = reinterpret_cast<float*>(take(4 * N));
   }
-  w.buf.X = reinterpret_cast<float*>(take(4 * N * K));
-  w.buf.H = reinterpret_cast<float*>(take(4 * nh * N * Wd));
-  w.buf.O = reinterpret_cast<float*>(take(4 * N * no));
-  w.buf.G = reinterpret_cast<float*>(take(4 * N * no));
-  w.buf.loss_seg = reinterpret_cast<float*>(take(4 * N));
-  w.buf.dZ = reinterpret_cast<float*>(take(4 * nh * N * Wd));
-  const size_t Kp = (K + 15) & ~size_t(15);
-  w.ld = int64_t((N + 63) & ~size_t(63));
-  w.X16 = reinterpret_cast<uint16_t*>(take(2 * size_t(w.ld) * Kp));
-  w.dZT0 = reinterpret_cast<uint16_t*>(take(2 * size_t(w.ld) * Wd));
-  w.H16 = reinterpret_cast<uint16_t*>(take(2 * nh * N * Wd));
-  w.dZ16 = reinterpret_cast<uint16_t*>(take(2 * nh * N * Wd));
+  w.O = reinterpret_cast<float*>(take(4 * N * no));
+  w.G = reinterpret_cast<float*>(take(4 * N * no));
+  w.loss_seg = reinterpret_cast<float*>(take(4 * N));
+  w.chunk = int64_t(C);
+  if (d->mlp_prec == NBVH_FP32) {
+    w.X = reinterpret_cast<float*>(take(4 * C * K));
+    w.H = reinterpret_cast<float*>(take(4 * nh * C * Wd));
+    w.dZ = reinterpret_cast<float*>(take(4 * nh * C * Wd));
+  } else {
+    const size_t Kp = (K + 15) & ~size_t(15);
+    w.ld = int64_t((C + 63) & ~size_t(63));
+    w.X16 = reinterpret_cast<uint16_t*>(take(2 * size_t(w.ld) * Kp));
+    w.dZT0 = reinterpret_cast<uint16_t*>(take(2 * size_t(w.ld) * Wd));
+    w.H16 = reinterpret_cast<uint16_t*>(take(2 * nh * C * Wd));
+    w.dZ16 = reinterpret_cast<uint16_t*>(take(2 * nh * C * Wd));
+    w.image = take(image_bytes(d));
+  }
   if (n_leaves > 0) {
     w.counts = reinterpret_cast<int32_t*>(take(4 * size_t(n_leaves)));
     w.cursor = reinterpret_cast<int32_t*>(take(4 * (size_t(n_leaves) + 1)));
@@ -921,46 +1079,31 @@ TrainWs carve_train(void* base, const nbvh_model_desc* d, int64_t n, int32_t n_l
   return w;
 }
 
-template <typename T, int F, int W>
-cudaError_t launch_train_plain(bool backward, const TrainArgs& a, cudaStream_t s) {
-  const size_t smem = backward ? train_bwd_smem(a.gp.n_inputs, W, a.n_hidden, a.n_out)
-                               : train_fwd_smem(a.gp.n_inputs, W, a.n_hidden, a.n_out);
-  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
-  auto kern = backward ? train_backward_plain<T, F, W> : train_forward_plain<T, F, W>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  if (e != cudaSuccess) return e;
-  int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kPlainThreads, smem);
-  if (e != cudaSuccess) return e;
-  const int64_t tiles = (a.n + kPlainTM - 1) / kPlainTM;
-  int64_t grid = int64_t(sm_count()) * (occ < 1 ? 1 : occ);
-  if (tiles < grid) grid = tiles;
-  if (grid < 1) return cudaSuccess;
-  kern<<<unsigned(grid), kPlainThreads, smem, s>>>(a);
-  count_launches(1);
-  return cudaGetLastError();
+// Rays per activation chunk for a workspace of ws_bytes: the whole batch when
+// its activations fit, else the largest multiple of 128 rays whose chunk does
+// (0: not even 128 fit).
+int64_t train_chunk(const nbvh_model_desc* d, int64_t n, int32_t n_leaves, size_t ws_bytes) {
+  if (carve_train(nullptr, d, n, n_leaves, n).bytes <= ws_bytes) return n;
+  int64_t lo = 0, hi = (n - 1) / kTcM;  // chunk = 128 k, k in [1, hi]
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) / 2;
+    if (carve_train(nullptr, d, n, n_leaves, mid * kTcM).bytes <= ws_bytes)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo * kTcM;
 }
 
-template <typename T, int F>
-cudaError_t launch_train_tf(bool bwd, int W, const TrainArgs& a, cudaStream_t s) {
-  switch (W) {
-    case 16: return launch_train_plain<T, F, 16>(bwd, a, s);
-    case 32: return launch_train_plain<T, F, 32>(bwd, a, s);
-    case 64: return launch_train_plain<T, F, 64>(bwd, a, s);
-    case 128: return launch_train_plain<T, F, 128>(bwd, a, s);
-  }
-  return cudaErrorInvalidValue;
-}
-
-template <typename T>
-cudaError_t launch_train_t(bool bwd, const nbvh_model_desc* d, const TrainArgs& a, cudaStream_t s) {
-  switch (d->n_features) {
-    case 1: return launch_train_tf<T, 1>(bwd, d->width, a, s);
-    case 2: return launch_train_tf<T, 2>(bwd, d->width, a, s);
-    case 4: return launch_train_tf<T, 4>(bwd, d->width, a, s);
-    case 8: return launch_train_tf<T, 8>(bwd, d->width, a, s);
-  }
-  return cudaErrorInvalidValue;
+// The training kernels can run this model (checked before anything is enqueued).
+bool train_stageable(const nbvh_model_desc* d) {
+  const int K = d->n_samples * d->n_levels * d->n_features, W = d->width;
+  if (d->mlp_prec == NBVH_FP32)
+    return train_fwd_smem(K, W, d->n_hidden, d->n_out) <= kSmemMax &&
+           train_bwd_smem(K, W, d->n_hidden, d->n_out) <= kSmemMax;
+  if (W != 32 && W != 64 && W != 128) return false;
+  const TcBwdLayout bl = tc_bwd_layout(K, W, d->n_hidden);
+  return tc_plan(d, 0, NBVH_W1_AUTO).ok && bl.total <= kSmemMax && bl.ncols <= 512;
 }
 
 cudaError_t launch_train(bool bwd, const nbvh_model_desc* d, const TrainArgs& a, cudaStream_t s) {
@@ -975,71 +1118,6 @@ cudaError_t launch_train(bool bwd, const nbvh_model_desc* d, const TrainArgs& a,
 bool scene_valid(const nbvh_train_scene* sc) {
   return sc && sc->nodes && sc->n_nodes >= 1 && sc->leaf_box && sc->n_leaves >= 1 && sc->tris && sc->tri_perm &&
          sc->leaf_range;
-}
-
-TrainArgs train_args(const nbvh_model_desc* d, const GridParams& gp, const void* table, const float* mlp,
-                     const nbvh_rays& rays, const int32_t* leaf, const float* t0, const float* t1,
-                     const TrainWs& w) {
-  TrainArgs a;
-  std::memset(&a, 0, sizeof(a));
-  a.gp = gp;
-  a.table = table;
-  a.mlp = mlp;
-  a.n_hidden = d->n_hidden;
-  a.width = d->width;
-  a.n_out = d->n_out;
-  a.rays = ray_ptrs(rays);
-  a.leaf = leaf;
-  a.t0 = t0;
-  a.t1 = t1;
-  a.n = rays.n;
-  a.buf = w.buf;
-  a.loss_scale = 1.0f;
-  return a;
-}
-
-template <int F, int W>
-cudaError_t launch_bwd_tc_fw(bool bf16, const TcBwdArgs& a, cudaStream_t s) {
-  const TcBwdLayout lay = tc_bwd_layout(a.gp.n_inputs, W, a.n_hidden);
-  if (lay.total > 227 * 1024 || lay.ncols > 512) return cudaErrorInvalidConfiguration;
-  auto kern = bf16 ? train_backward_tc<F, W, true> : train_backward_tc<F, W, false>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(lay.total));
-  if (e != cudaSuccess) return e;
-  constexpr int threads = bwd_threads<W>();
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, lay.total);
-  if (e != cudaSuccess) return e;
-  // co-resident CTAs must fit the SM's 512 TMEM columns together
-  per_sm = std::min(per_sm, int(512 / lay.ncols));
-  if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  const int64_t tiles = (a.n + kTcM - 1) / kTcM;
-  int64_t grid = int64_t(sm_count()) * per_sm;
-  if (tiles < grid) grid = tiles;
-  if (grid < 1) return cudaSuccess;
-  kern<<<unsigned(grid), threads, lay.total, s>>>(a);
-  count_launches(1);
-  return cudaGetLastError();
-}
-
-template <int F>
-cudaError_t launch_bwd_tc_f(bool bf16, int W, const TcBwdArgs& a, cudaStream_t s) {
-  switch (W) {
-    case 32: return launch_bwd_tc_fw<F, 32>(bf16, a, s);
-    case 64: return launch_bwd_tc_fw<F, 64>(bf16, a, s);
-    case 128: return launch_bwd_tc_fw<F, 128>(bf16, a, s);
-  }
-  return cudaErrorInvalidConfiguration;
-}
-
-cudaError_t launch_bwd_tc(const nbvh_model_desc* d, const TcBwdArgs& a, cudaStream_t s) {
-  const bool bf16 = d->mlp_prec == NBVH_BF16;
-  switch (d->n_features) {
-    case 1: return launch_bwd_tc_f<1>(bf16, d->width, a, s);
-    case 2: return launch_bwd_tc_f<2>(bf16, d->width, a, s);
-    case 4: return launch_bwd_tc_f<4>(bf16, d->width, a, s);
-    case 8: return launch_bwd_tc_f<8>(bf16, d->width, a, s);
-  }
-  return cudaErrorInvalidValue;
 }
 
 template <typename TZ, typename TA>
@@ -1061,31 +1139,6 @@ template <typename TZ, typename TA>
 cudaError_t launch_wg_any(const TZ* dZ, int ldz, int n_o, const TA* A, int lda, int n_j, int64_t n, float* dW,
                           float* db, cudaStream_t s) {
   return launch_wg_strided<TZ, TA>(dZ, ldz, 1, n_o, A, lda, 1, n_j, n, dW, db, s);
-}
-
-template <int W>
-cudaError_t launch_wg_tc_w(bool bf16, const WgTcArgs& a, cudaStream_t s) {
-  const uint32_t smem = wg_tc_smem(a.Kp, W);
-  if (smem > 227 * 1024 || wg_tc_tiles(a.Kp) * W > 512) return cudaErrorInvalidConfiguration;
-  auto kern = bf16 ? weight_grad_tc<W, true> : weight_grad_tc<W, false>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  if (e != cudaSuccess) return e;
-  const int64_t chunks = (a.n + kWgTcItems - 1) / kWgTcItems;
-  int64_t grid = sm_count();
-  if (chunks < grid) grid = chunks;
-  if (grid < 1) return cudaSuccess;
-  kern<<<unsigned(grid), kWgTcThreads, smem, s>>>(a);
-  count_launches(1);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_wg_tc(bool bf16, int W, const WgTcArgs& a, cudaStream_t s) {
-  switch (W) {
-    case 32: return launch_wg_tc_w<32>(bf16, a, s);
-    case 64: return launch_wg_tc_w<64>(bf16, a, s);
-    case 128: return launch_wg_tc_w<128>(bf16, a, s);
-  }
-  return cudaErrorInvalidConfiguration;
 }
 
 // Weight gradients of the tensor-core path from its 16-bit stored operands.
@@ -1119,6 +1172,163 @@ cudaError_t weight_grads_16(const nbvh_model_desc* d, const TrainWs& w, const fl
 cudaError_t launch_weight_grad(const float* dZ, int n_o, const float* A, int n_j, int64_t n, float* dW, float* db,
                                cudaStream_t s) {
   return launch_wg_any<float, float>(dZ, n_o, n_o, A, n_j, n_j, n, dW, db, s);
+}
+
+// One chunk of a training batch: items [i0, i0 + c). With `order` the items
+// map to rays through order[i0 ..] and the ray arrays stay whole; without it
+// item i is ray i and the ray arrays are offset.
+struct Chunk {
+  nbvh_rays rays;
+  const int32_t* leaf;
+  const float *t0, *t1;
+  const int32_t* order;
+  int64_t i0, c;
+};
+
+Chunk chunk_of(const nbvh_rays& rays, const int32_t* leaf, const float* t0, const float* t1, const int32_t* order,
+               int64_t i0, int64_t c) {
+  Chunk k;
+  k.rays = rays;
+  k.leaf = leaf;
+  k.t0 = t0;
+  k.t1 = t1;
+  k.order = order ? order + i0 : nullptr;
+  k.i0 = i0;
+  k.c = c;
+  if (!order) {
+    const float** f[8] = {&k.rays.ox, &k.rays.oy, &k.rays.oz, &k.rays.dx, &k.rays.dy, &k.rays.dz, &k.rays.tmin,
+                          &k.rays.tmax};
+    for (auto* q : f) *q += i0;
+    k.leaf += i0;
+    k.t0 += i0;
+    k.t1 += i0;
+  }
+  k.rays.n = c;
+  return k;
+}
+
+// Forward of one chunk into the workspace's activation buffers; with labels
+// (lab.hit set) also the loss terms and dL/d(raw) of its items.
+cudaError_t forward_chunk(const nbvh_model_desc* d, const GridParams& gp, const void* table, const float* mlp,
+                          const Chunk& k, const Labels& lab, const int32_t* n_valid, float loss_scale,
+                          const float* loss_scale_dev, const TrainWs& w, const TcPlan& plan, const void* image,
+                          cudaStream_t s) {
+  const int no = d->n_out;
+  if (d->mlp_prec == NBVH_FP32) {
+    TrainArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.gp = gp;
+    a.table = table;
+    a.mlp = mlp;
+    a.n_hidden = d->n_hidden;
+    a.width = d->width;
+    a.n_out = no;
+    a.rays = ray_ptrs(k.rays);
+    a.leaf = k.leaf;
+    a.t0 = k.t0;
+    a.t1 = k.t1;
+    a.n = k.c;
+    a.buf = TrainBuffers{w.X, w.H, w.O + k.i0 * no, w.G + k.i0 * no, w.loss_seg + k.i0, w.dZ};
+    a.lab = lab;
+    a.n_valid = n_valid;
+    a.loss_scale = loss_scale;
+    a.loss_scale_dev = loss_scale_dev;
+    return launch_train(false, d, a, s);
+  }
+  EvalArgs a = base_args(d, gp, table, mlp, k.rays);
+  a.list_t0 = k.t0;
+  a.list_t1 = k.t1;
+  a.n_items = k.c;
+  a.w1_image = image;
+  a.tr.leaf = k.leaf;
+  a.tr.order = k.order;
+  a.tr.X16 = w.X16;
+  a.tr.ld = w.ld;
+  a.tr.H16 = w.H16;
+  a.tr.O = w.O + k.i0 * no;
+  a.tr.G = w.G + k.i0 * no;
+  a.tr.loss_seg = w.loss_seg + k.i0;
+  a.tr.lab = lab;
+  a.tr.n_valid = n_valid;
+  a.tr.loss_scale = loss_scale;
+  a.tr.loss_scale_dev = loss_scale_dev;
+  return launch_tc<2>(d, a, k.c, plan, s);
+}
+
+// Backward of one chunk whose activations are in the workspace: MLP adjoint,
+// scatter into the table gradient, weight gradients (all accumulate).
+cudaError_t backward_chunk(const nbvh_model_desc* d, const GridParams& gp, const void* table, const float* mlp,
+                           const Chunk& k, const float* G, float* grad_table, float* grad_mlp, const TrainWs& w,
+                           cudaStream_t s) {
+  const int no = d->n_out;
+  const float* Gk = G + k.i0 * no;
+  if (d->mlp_prec != NBVH_FP32) {
+    TcBwdArgs b;
+    std::memset(&b, 0, sizeof(b));
+    b.gp = gp;
+    b.mlp = mlp;
+    b.n_hidden = d->n_hidden;
+    b.n_out = no;
+    b.rays = ray_ptrs(k.rays);
+    b.leaf = k.leaf;
+    b.order = k.order;
+    b.t0 = k.t0;
+    b.t1 = k.t1;
+    b.n = k.c;
+    b.G = Gk;
+    b.H16 = w.H16;
+    b.dZ16 = w.dZ16;
+    b.dZT0 = w.dZT0;
+    b.ld = w.ld;
+    b.grad_table = grad_table;
+    cudaError_t e = launch_bwd_tc(d, b, s);
+    if (e != cudaSuccess) return e;
+    return d->mlp_prec == NBVH_BF16 ? weight_grads_16<__nv_bfloat16>(d, w, Gk, k.c, grad_mlp, s)
+                                    : weight_grads_16<__half>(d, w, Gk, k.c, grad_mlp, s);
+  }
+  TrainArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.gp = gp;
+  a.table = table;
+  a.mlp = mlp;
+  a.n_hidden = d->n_hidden;
+  a.width = d->width;
+  a.n_out = no;
+  a.rays = ray_ptrs(k.rays);
+  a.leaf = k.leaf;
+  a.t0 = k.t0;
+  a.t1 = k.t1;
+  a.n = k.c;
+  a.buf = TrainBuffers{w.X, w.H, nullptr, const_cast<float*>(Gk), nullptr, w.dZ};
+  a.grad_table = grad_table;
+  cudaError_t e = launch_train(true, d, a, s);
+  if (e != cudaSuccess) return e;
+  // weight gradients, parameter order: W0 [W][K], b0, (W_h [W][W], b_h)*, Wo [n_out][W], bo
+  const int K = gp.n_inputs, Wd = d->width, nh = d->n_hidden;
+  const int64_t c = k.c;
+  size_t off = 0;
+  e = launch_weight_grad(w.dZ, Wd, w.X, K, c, grad_mlp + off, grad_mlp + off + size_t(Wd) * K, s);
+  off += size_t(Wd) * K + Wd;
+  for (int h = 1; h < nh && e == cudaSuccess; ++h) {
+    e = launch_weight_grad(w.dZ + size_t(h) * c * Wd, Wd, w.H + size_t(h - 1) * c * Wd, Wd, c, grad_mlp + off,
+                           grad_mlp + off + size_t(Wd) * Wd, s);
+    off += size_t(Wd) * Wd + Wd;
+  }
+  if (e == cudaSuccess)
+    e = launch_weight_grad(Gk, no, w.H + size_t(nh - 1) * c * Wd, Wd, c, grad_mlp + off,
+                           grad_mlp + off + size_t(no) * Wd, s);
+  return e;
+}
+
+// The batch loss in FP32: compensated per-thread sums, then pairwise trees
+// (two launches, no atomics: the result does not depend on scheduling).
+cudaError_t launch_loss(const float* term, int64_t n, const int32_t* n_valid, float* partial, float* out,
+                        cudaStream_t s) {
+  const int blocks = int(std::min<int64_t>(kLossBlocks, std::max<int64_t>(1, (n + 255) / 256)));
+  loss_partial_kernel<<<blocks, 256, 0, s>>>(term, n, partial);
+  loss_final_kernel<<<1, 256, 0, s>>>(partial, blocks, n_valid, out);
+  count_launches(2);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -1178,7 +1388,17 @@ extern "C" nbvh_status nbvh_train_labels(nbvh_rays rays, const int32_t* leaf, co
 extern "C" nbvh_status nbvh_train_workspace_size(const nbvh_model_desc* desc, int64_t n, int32_t n_leaves,
                                                  size_t* bytes) {
   if (!nbvh_host::desc_valid(desc) || n < 0 || n_leaves < 0 || !bytes) return NBVH_ERR_INVALID_ARG;
-  *bytes = carve_train(nullptr, desc, n, n_leaves).bytes;
+  *bytes = carve_train(nullptr, desc, n, n_leaves, n).bytes;
+  return NBVH_OK;
+}
+
+extern "C" nbvh_status nbvh_train_workspace_budget(const nbvh_model_desc* desc, int64_t n, int32_t n_leaves,
+                                                   size_t max_bytes, size_t* bytes, int64_t* chunk) {
+  if (!nbvh_host::desc_valid(desc) || n < 1 || n_leaves < 0 || !bytes || !chunk) return NBVH_ERR_INVALID_ARG;
+  const int64_t c = train_chunk(desc, n, n_leaves, max_bytes);
+  if (c <= 0) return NBVH_ERR_WORKSPACE_TOO_SMALL;
+  *chunk = c;
+  *bytes = carve_train(nullptr, desc, n, n_leaves, c).bytes;
   return NBVH_OK;
 }
 
@@ -1187,19 +1407,78 @@ namespace {
 nbvh_status forward_train_impl(const nbvh_model_desc* desc, const void* table, const float* mlp, nbvh_rays rays,
                                const int32_t* leaf, const float* t0, const float* t1, nbvh_labels labels,
                                const int32_t* n_valid, float loss_scale, const float* loss_scale_dev,
-                               float* raw_out, double* loss_out, void* workspace, size_t ws_bytes, void* stream,
-                               const int32_t* order, int32_t n_leaves);
+                               float* raw_out, float* loss_out, void* workspace, size_t ws_bytes, void* stream,
+                               const int32_t* order, int32_t n_leaves) {
+  if (!nbvh_host::desc_valid(desc) || !table || !mlp || !rays_valid(rays)) return NBVH_ERR_INVALID_ARG;
+  if (rays.n == 0) return NBVH_OK;
+  if (!leaf || !t0 || !t1 || !workspace || (reinterpret_cast<uintptr_t>(workspace) & 255) ||
+      (labels.hit && (!labels.depth || !labels.nx || !labels.ny || !labels.nz || !n_valid)) ||
+      (labels.ar && (!labels.ag || !labels.ab)) || !(loss_scale > 0.0f) || rays.n > (int64_t(1) << 31) - 1)
+    return NBVH_ERR_INVALID_ARG;
+  const int64_t chunk = train_chunk(desc, rays.n, n_leaves, ws_bytes);
+  if (chunk <= 0) return NBVH_ERR_WORKSPACE_TOO_SMALL;
+  TrainWs w = carve_train(workspace, desc, rays.n, n_leaves, chunk);
+  GridParams gp;
+  if (!make_grid(desc, gp)) return NBVH_ERR_INVALID_ARG;
+  if (!train_stageable(desc)) return NBVH_ERR_UNSUPPORTED;
+  cudaStream_t s = as_stream(stream);
+  const Labels lab{labels.hit, labels.depth, labels.nx, labels.ny, labels.nz, labels.ar, labels.ag, labels.ab};
+  EvalArgs pa = base_args(desc, gp, table, mlp, rays);
+  TcPlan plan;
+  cudaError_t e = prepare_eval(desc, pa, default_options(), w.image, &plan, s);
+  for (int64_t i0 = 0; i0 < rays.n && e == cudaSuccess; i0 += chunk)
+    e = forward_chunk(desc, gp, table, mlp, chunk_of(rays, leaf, t0, t1, order, i0, std::min(chunk, rays.n - i0)),
+                      lab, n_valid, loss_scale, loss_scale_dev, w, plan, pa.w1_image, s);
+  if (e != cudaSuccess) return status_of(e);
+  if (raw_out) {
+    e = cudaMemcpyAsync(raw_out, w.O, sizeof(float) * size_t(rays.n) * desc->n_out, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return NBVH_ERR_CUDA;
+  }
+  if (labels.hit && loss_out) e = launch_loss(w.loss_seg, rays.n, n_valid, w.partial, loss_out, s);
+  return status_of(e);
+}
+
 nbvh_status backward_impl(const nbvh_model_desc* desc, const void* table, const float* mlp, nbvh_rays rays,
                           const int32_t* leaf, const float* t0, const float* t1, const float* grad_out,
                           float* grad_table, float* grad_mlp, void* workspace, size_t ws_bytes, void* stream,
-                          const int32_t* order, int32_t n_leaves);
+                          const int32_t* order, int32_t n_leaves) {
+  if (!nbvh_host::desc_valid(desc) || !table || !mlp || !rays_valid(rays)) return NBVH_ERR_INVALID_ARG;
+  if (rays.n == 0) return NBVH_OK;
+  if (!leaf || !t0 || !t1 || !grad_table || !grad_mlp || !workspace ||
+      (reinterpret_cast<uintptr_t>(workspace) & 255) || rays.n > (int64_t(1) << 31) - 1)
+    return NBVH_ERR_INVALID_ARG;
+  const int64_t chunk = train_chunk(desc, rays.n, n_leaves, ws_bytes);
+  if (chunk <= 0) return NBVH_ERR_WORKSPACE_TOO_SMALL;
+  TrainWs w = carve_train(workspace, desc, rays.n, n_leaves, chunk);
+  GridParams gp;
+  if (!make_grid(desc, gp)) return NBVH_ERR_INVALID_ARG;
+  if (!train_stageable(desc)) return NBVH_ERR_UNSUPPORTED;
+  cudaStream_t s = as_stream(stream);
+  const float* G = grad_out ? grad_out : w.G;
+  const bool recompute = chunk < rays.n;
+  EvalArgs pa = base_args(desc, gp, table, mlp, rays);
+  TcPlan plan;
+  cudaError_t e = cudaSuccess;
+  if (recompute) e = prepare_eval(desc, pa, default_options(), w.image, &plan, s);
+  const Labels none{};
+  for (int64_t i0 = 0; i0 < rays.n && e == cudaSuccess; i0 += chunk) {
+    const Chunk k = chunk_of(rays, leaf, t0, t1, order, i0, std::min(chunk, rays.n - i0));
+    // recompute mode: this chunk's activations again (no labels: the loss
+    // terms and dL/d(raw) of the first forward stay as they are)
+    if (recompute)
+      e = forward_chunk(desc, gp, table, mlp, k, none, nullptr, 1.0f, nullptr, w, plan, pa.w1_image, s);
+    if (e == cudaSuccess) e = backward_chunk(desc, gp, table, mlp, k, G, grad_table, grad_mlp, w, s);
+  }
+  return status_of(e);
+}
+
 }  // namespace
 }  // namespace nbvh
 
 extern "C" nbvh_status nbvh_forward_train(const nbvh_model_desc* desc, const void* table, const float* mlp,
                                           nbvh_rays rays, const int32_t* leaf, const float* t0, const float* t1,
                                           nbvh_labels labels, const int32_t* n_valid, float loss_scale,
-                                          const float* loss_scale_dev, float* raw_out, double* loss_out,
+                                          const float* loss_scale_dev, float* raw_out, float* loss_out,
                                           void* workspace, size_t ws_bytes, void* stream) {
   return forward_train_impl(desc, table, mlp, rays, leaf, t0, t1, labels, n_valid, loss_scale, loss_scale_dev,
                             raw_out, loss_out, workspace, ws_bytes, stream, nullptr, 0);
@@ -1213,129 +1492,20 @@ extern "C" nbvh_status nbvh_backward(const nbvh_model_desc* desc, const void* ta
                        stream, nullptr, 0);
 }
 
-namespace nbvh {
-namespace {
-nbvh_status forward_train_impl(const nbvh_model_desc* desc, const void* table, const float* mlp, nbvh_rays rays,
-                               const int32_t* leaf, const float* t0, const float* t1, nbvh_labels labels,
-                               const int32_t* n_valid, float loss_scale, const float* loss_scale_dev,
-                               float* raw_out, double* loss_out, void* workspace, size_t ws_bytes, void* stream,
-                               const int32_t* order, int32_t n_leaves) {
-  if (!nbvh_host::desc_valid(desc) || !table || !mlp || !rays_valid(rays)) return NBVH_ERR_INVALID_ARG;
-  if (rays.n == 0) return NBVH_OK;
-  if (!leaf || !t0 || !t1 || !workspace || (reinterpret_cast<uintptr_t>(workspace) & 255) ||
-      (labels.hit && (!labels.depth || !labels.nx || !labels.ny || !labels.nz || !n_valid)) ||
-      (labels.ar && (!labels.ag || !labels.ab)) ||
-      !(loss_scale > 0.0f))
-    return NBVH_ERR_INVALID_ARG;
-  TrainWs w = carve_train(workspace, desc, rays.n, n_leaves);
-  if (ws_bytes < w.bytes) return NBVH_ERR_WORKSPACE_TOO_SMALL;
-  GridParams gp;
-  if (!make_grid(desc, gp)) return NBVH_ERR_INVALID_ARG;
-  cudaStream_t s = as_stream(stream);
-  cudaError_t e;
-  if (desc->mlp_prec == NBVH_FP32) {
-    TrainArgs a = train_args(desc, gp, table, mlp, rays, leaf, t0, t1, w);
-    a.lab = Labels{labels.hit, labels.depth, labels.nx, labels.ny, labels.nz, labels.ar, labels.ag, labels.ab};
-    a.n_valid = n_valid;
-    a.loss_scale = loss_scale;
-    a.loss_scale_dev = loss_scale_dev;
-    e = launch_train(false, desc, a, s);
-  } else {
-    EvalArgs a = base_args(desc, gp, table, mlp, rays);
-    a.list_t0 = t0;
-    a.list_t1 = t1;
-    a.n_items = rays.n;
-    a.tr.leaf = leaf;
-    a.tr.order = order;
-    a.tr.X16 = w.X16;
-    a.tr.ld = w.ld;
-    a.tr.H16 = w.H16;
-    a.tr.O = w.buf.O;
-    a.tr.G = w.buf.G;
-    a.tr.loss_seg = w.buf.loss_seg;
-    a.tr.lab = Labels{labels.hit, labels.depth, labels.nx, labels.ny, labels.nz, labels.ar, labels.ag, labels.ab};
-    a.tr.n_valid = n_valid;
-    a.tr.loss_scale = loss_scale;
-    a.tr.loss_scale_dev = loss_scale_dev;
-    e = launch_tc<2>(desc, a, rays.n, s);
-  }
-  if (e != cudaSuccess) return status_of(e);
-  if (raw_out) {
-    e = cudaMemcpyAsync(raw_out, w.buf.O, sizeof(float) * size_t(rays.n) * desc->n_out, cudaMemcpyDeviceToDevice, s);
-    if (e != cudaSuccess) return NBVH_ERR_CUDA;
-  }
-  if (labels.hit && loss_out) {
-    if (cudaMemsetAsync(loss_out, 0, sizeof(double), s) != cudaSuccess) return NBVH_ERR_CUDA;
-    loss_reduce_kernel<<<unsigned(sm_count()), 256, 0, s>>>(w.buf.loss_seg, rays.n, n_valid, loss_out);
-    count_launches(1);
-    e = cudaGetLastError();
-  }
-  return status_of(e);
-}
-
-nbvh_status backward_impl(const nbvh_model_desc* desc, const void* table, const float* mlp, nbvh_rays rays,
-                          const int32_t* leaf, const float* t0, const float* t1, const float* grad_out,
-                          float* grad_table, float* grad_mlp, void* workspace, size_t ws_bytes, void* stream,
-                          const int32_t* order, int32_t n_leaves) {
-  if (!nbvh_host::desc_valid(desc) || !table || !mlp || !rays_valid(rays)) return NBVH_ERR_INVALID_ARG;
-  if (rays.n == 0) return NBVH_OK;
-  if (!leaf || !t0 || !t1 || !grad_table || !grad_mlp || !workspace ||
+extern "C" nbvh_status nbvh_loss_fp64(const nbvh_model_desc* desc, int64_t n, const int32_t* n_valid,
+                                      const void* workspace, size_t ws_bytes, double* loss_out, void* stream) {
+  if (!nbvh_host::desc_valid(desc) || n < 1 || !n_valid || !workspace || !loss_out ||
       (reinterpret_cast<uintptr_t>(workspace) & 255))
     return NBVH_ERR_INVALID_ARG;
-  TrainWs w = carve_train(workspace, desc, rays.n, n_leaves);
-  if (ws_bytes < w.bytes) return NBVH_ERR_WORKSPACE_TOO_SMALL;
-  GridParams gp;
-  if (!make_grid(desc, gp)) return NBVH_ERR_INVALID_ARG;
+  const int64_t chunk = train_chunk(desc, n, 0, ws_bytes);
+  if (chunk <= 0) return NBVH_ERR_WORKSPACE_TOO_SMALL;
+  const TrainWs w = carve_train(const_cast<void*>(workspace), desc, n, 0, chunk);
   cudaStream_t s = as_stream(stream);
-  if (desc->mlp_prec != NBVH_FP32) {
-    TcBwdArgs b;
-    std::memset(&b, 0, sizeof(b));
-    b.gp = gp;
-    b.mlp = mlp;
-    b.n_hidden = desc->n_hidden;
-    b.n_out = desc->n_out;
-    b.rays = ray_ptrs(rays);
-    b.leaf = leaf;
-    b.order = order;
-    b.t0 = t0;
-    b.t1 = t1;
-    b.n = rays.n;
-    b.G = grad_out ? grad_out : w.buf.G;
-    b.H16 = w.H16;
-    b.dZ16 = w.dZ16;
-    b.dZT0 = w.dZT0;
-    b.ld = w.ld;
-    b.grad_table = grad_table;
-    cudaError_t e = launch_bwd_tc(desc, b, s);
-    if (e != cudaSuccess) return status_of(e);
-    e = desc->mlp_prec == NBVH_BF16 ? weight_grads_16<__nv_bfloat16>(desc, w, b.G, rays.n, grad_mlp, s)
-                                    : weight_grads_16<__half>(desc, w, b.G, rays.n, grad_mlp, s);
-    return status_of(e);
-  }
-  TrainArgs a = train_args(desc, gp, table, mlp, rays, leaf, t0, t1, w);
-  if (grad_out) a.buf.G = const_cast<float*>(grad_out);
-  a.grad_table = grad_table;
-  cudaError_t e = launch_train(true, desc, a, s);
-  if (e != cudaSuccess) return status_of(e);
-  // weight gradients, parameter order: W0 [W][K], b0, (W_h [W][W], b_h)*, Wo [n_out][W], bo
-  const int K = gp.n_inputs, Wd = desc->width, nh = desc->n_hidden, no = desc->n_out;
-  const int64_t n = rays.n;
-  size_t off = 0;
-  e = launch_weight_grad(w.buf.dZ, Wd, w.buf.X, K, n, grad_mlp + off, grad_mlp + off + size_t(Wd) * K, s);
-  off += size_t(Wd) * K + Wd;
-  for (int h = 1; h < nh && e == cudaSuccess; ++h) {
-    e = launch_weight_grad(w.buf.dZ + size_t(h) * n * Wd, Wd, w.buf.H + size_t(h - 1) * n * Wd, Wd, n,
-                           grad_mlp + off, grad_mlp + off + size_t(Wd) * Wd, s);
-    off += size_t(Wd) * Wd + Wd;
-  }
-  if (e == cudaSuccess)
-    e = launch_weight_grad(a.buf.G, no, w.buf.H + size_t(nh - 1) * n * Wd, Wd, n, grad_mlp + off,
-                           grad_mlp + off + size_t(no) * Wd, s);
-  return status_of(e);
+  if (cudaMemsetAsync(loss_out, 0, sizeof(double), s) != cudaSuccess) return NBVH_ERR_CUDA;
+  loss_fd_fp64_kernel<<<unsigned(sm_count()), 256, 0, s>>>(w.loss_seg, n, n_valid, loss_out);
+  count_launches(1);
+  return status_of(cudaGetLastError());
 }
-
-}  // namespace
-}  // namespace nbvh
 
 extern "C" nbvh_status nbvh_adam(const nbvh_model_desc* desc, const nbvh_optim* opt, int64_t step, float lr,
                                  float beta1, float beta2, float eps, int32_t dynamic_scale, void* stream) {
@@ -1382,7 +1552,7 @@ extern "C" nbvh_status nbvh_adam(const nbvh_model_desc* desc, const nbvh_optim* 
 
 extern "C" nbvh_status nbvh_train_step(const nbvh_model_desc* desc, const nbvh_optim* opt,
                                        const nbvh_train_scene* scene, int32_t mode, int64_t batch, uint64_t seed,
-                                       int64_t step, float lr, double* loss_out, void* workspace, size_t ws_bytes,
+                                       int64_t step, float lr, float* loss_out, void* workspace, size_t ws_bytes,
                                        void* stream) {
   return nbvh_train_step_weighted(desc, opt, scene, mode, batch, seed, step, lr, nullptr, nullptr, loss_out,
                                   workspace, ws_bytes, stream);
@@ -1391,14 +1561,16 @@ extern "C" nbvh_status nbvh_train_step(const nbvh_model_desc* desc, const nbvh_o
 extern "C" nbvh_status nbvh_train_step_weighted(const nbvh_model_desc* desc, const nbvh_optim* opt,
                                                 const nbvh_train_scene* scene, int32_t mode, int64_t batch,
                                                 uint64_t seed, int64_t step, float lr, const float* leaf_prob,
-                                                const nbvh_leaf_stats* stats, double* loss_out, void* workspace,
+                                                const nbvh_leaf_stats* stats, float* loss_out, void* workspace,
                                                 size_t ws_bytes, void* stream) {
   if (!nbvh_host::desc_valid(desc) || !opt || !scene_valid(scene) || batch < 1 || step < 1 || !workspace ||
       (reinterpret_cast<uintptr_t>(workspace) & 255) || batch > (int64_t(1) << 31) - 1)
     return NBVH_ERR_INVALID_ARG;
   if (stats && (!stats->hits || !stats->trained || !stats->loss)) return NBVH_ERR_INVALID_ARG;
-  TrainWs w = carve_train(workspace, desc, batch, scene->n_leaves);
-  if (ws_bytes < w.bytes) return NBVH_ERR_WORKSPACE_TOO_SMALL;
+  const int64_t chunk = train_chunk(desc, batch, scene->n_leaves, ws_bytes);
+  if (chunk <= 0) return NBVH_ERR_WORKSPACE_TOO_SMALL;
+  if (!train_stageable(desc)) return NBVH_ERR_UNSUPPORTED;
+  TrainWs w = carve_train(workspace, desc, batch, scene->n_leaves, chunk);
   cudaStream_t s = as_stream(stream);
   if (cudaMemsetAsync(w.n_valid, 0, 256, s) != cudaSuccess) return NBVH_ERR_CUDA;
   if (cudaMemsetAsync(w.counts, 0, 4 * size_t(scene->n_leaves), s) != cudaSuccess) return NBVH_ERR_CUDA;
@@ -1434,9 +1606,10 @@ extern "C" nbvh_status nbvh_train_step_weighted(const nbvh_model_desc* desc, con
                           nullptr, loss_out ? loss_out : w.loss, workspace, ws_bytes, stream, order,
                           scene->n_leaves);
   if (st != NBVH_OK) return st;
-  if (stats) {
-    leaf_loss_kernel<<<unsigned((batch + 255) / 256), 256, 0, s>>>(w.buf.loss_seg, batch, w.leaf, order,
-                                                                    stats->trained, stats->loss);
+  if (stats) {  // per-leaf sums over each leaf's contiguous range of the grouped order
+    leaf_loss_kernel<<<unsigned((scene->n_leaves + 7) / 8), 256, 0, s>>>(
+        w.loss_seg, w.order, order != nullptr ? 1 : 0, w.counts, w.cursor, scene->n_leaves, stats->trained,
+        stats->loss);
     count_launches(1);
     if (cudaGetLastError() != cudaSuccess) return NBVH_ERR_CUDA;
   }

@@ -18,7 +18,7 @@ __device__ __forceinline__ uint32_t probe_mix(uint32_t x) {
 // kProbeLoads independent 4-byte loads per thread per iteration at positions
 // masked to the table (n_entries a power of two), summed so none is dropped.
 constexpr int kProbeLoads = 16;
-__global__ void __launch_bounds__(1024) probe_gather_kernel(const uint32_t* __restrict__ tab, uint32_t mask,
+static __global__ void __launch_bounds__(1024) probe_gather_kernel(const uint32_t* __restrict__ tab, uint32_t mask,
                                                             int iters, uint32_t* __restrict__ sink) {
   uint32_t s = probe_mix(blockIdx.x * blockDim.x + threadIdx.x + 12345u);
   uint32_t acc = 0;

@@ -95,7 +95,7 @@ __device__ __forceinline__ int first_leaf_dev(const nbvh_node* __restrict__ node
   return best;
 }
 
-__global__ void __launch_bounds__(128) train_rays_kernel(TrainRayArgs a) {
+static __global__ void __launch_bounds__(128) train_rays_kernel(TrainRayArgs a) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
   const uint4 r = philox4x32_10(make_uint4(uint32_t(i), a.step_lo, a.step_hi, 0u), a.k0, a.k1);
@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(128) train_rays_kernel(TrainRayArgs a) {
 // With `order` (rays grouped by leaf) the lanes of a warp mostly share one
 // leaf: the triangle loop is warp-uniform and its loads are broadcasts. With
 // `leaf_tris` the leaf's triangles are read contiguously.
-__global__ void __launch_bounds__(128) labels_kernel(RayPtrs rays, const int32_t* __restrict__ leaf,
+static __global__ void __launch_bounds__(128) labels_kernel(RayPtrs rays, const int32_t* __restrict__ leaf,
                                                      const float* __restrict__ t0, const float* __restrict__ t1,
                                                      int64_t n, const float* __restrict__ tris,
                                                      const int32_t* __restrict__ tri_perm,
@@ -573,7 +573,7 @@ inline size_t train_bwd_smem(int K, int W, int nh, int n_out) {
 constexpr int kWgTile = 32;
 constexpr int kWgChunk = 2048;
 
-__global__ void __launch_bounds__(256) weight_grad_kernel(const float* __restrict__ dZ, int n_o,
+static __global__ void __launch_bounds__(256) weight_grad_kernel(const float* __restrict__ dZ, int n_o,
                                                           const float* __restrict__ A, int n_j, int64_t n,
                                                           float* __restrict__ dW, float* __restrict__ db) {
   __shared__ float sz[32][kWgTile + 1];
@@ -623,7 +623,7 @@ struct AdamState {
   int32_t* applied;    // device scalar: 1 when the last step was applied
 };
 
-__global__ void grad_check_kernel(const float* __restrict__ g, int64_t n, int32_t* bad) {
+static __global__ void grad_check_kernel(const float* __restrict__ g, int64_t n, int32_t* bad) {
   int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   bool ok = true;
@@ -658,7 +658,7 @@ __global__ void adam_kernel(float* __restrict__ master, T* __restrict__ work, fl
   }
 }
 
-__global__ void loss_scale_update_kernel(AdamState st, int32_t dynamic) {
+static __global__ void loss_scale_update_kernel(AdamState st, int32_t dynamic) {
   const bool bad = *st.bad != 0;
   *st.applied = bad ? 0 : 1;
   if (dynamic) {
@@ -673,19 +673,61 @@ __global__ void loss_scale_update_kernel(AdamState st, int32_t dynamic) {
   *st.bad = 0;
 }
 
-// Sum of per-segment loss terms in FP64 divided by the valid count (the batch
-// loss); also used by the finite-difference gradient check.
-// (*out must be zero before the launch; blocks add their partial sums.)
-__global__ void loss_reduce_kernel(const float* __restrict__ term, int64_t n, const int32_t* n_valid,
-                                   double* out) {
+// The batch loss in FP32 (sum of the per-segment terms over the valid count):
+// each thread sums its grid-stride share with compensated (Kahan) summation,
+// blocks reduce pairwise in shared memory into partial[blockIdx.x], and one
+// block reduces the partials the same way. No atomics, so the value does not
+// depend on scheduling.
+__device__ __forceinline__ void kahan_add(float& sum, float& comp, float x) {
+  const float y = __fsub_rn(x, comp);
+  const float t = __fadd_rn(sum, y);
+  comp = __fsub_rn(__fsub_rn(t, sum), y);
+  sum = t;
+}
+
+__device__ __forceinline__ float block_pairwise_sum(float v, float* sm) {
+  sm[threadIdx.x] = v;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (int(threadIdx.x) < w) sm[threadIdx.x] = __fadd_rn(sm[threadIdx.x], sm[threadIdx.x + w]);
+    __syncthreads();
+  }
+  return sm[0];
+}
+
+static __global__ void __launch_bounds__(256) loss_partial_kernel(const float* __restrict__ term, int64_t n,
+                                                                  float* __restrict__ partial) {
+  __shared__ float sm[256];
+  float sum = 0.0f, comp = 0.0f;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    kahan_add(sum, comp, term[i]);
+  const float b = block_pairwise_sum(sum, sm);
+  if (threadIdx.x == 0) partial[blockIdx.x] = b;
+}
+
+static __global__ void __launch_bounds__(256) loss_final_kernel(const float* __restrict__ partial, int nb,
+                                                                const int32_t* __restrict__ n_valid,
+                                                                float* __restrict__ out) {
+  __shared__ float sm[256];
+  float sum = 0.0f, comp = 0.0f;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) kahan_add(sum, comp, partial[i]);
+  const float b = block_pairwise_sum(sum, sm);
+  if (threadIdx.x == 0) *out = b / float(max(1, *n_valid));
+}
+
+// The same loss with FP64 accumulation, for the finite-difference gradient
+// check only (nbvh_loss_fp64): central differences subtract two nearly equal
+// losses. (*out must be zero before the launch; blocks add their sums.)
+static __global__ void loss_fd_fp64_kernel(const float* __restrict__ term, int64_t n, const int32_t* n_valid,
+                                           double* out) {
   __shared__ double sm[256];
   double acc = 0.0;
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
     acc += double(term[i]);
   sm[threadIdx.x] = acc;
   __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (int(threadIdx.x) < w) sm[threadIdx.x] += sm[threadIdx.x + w];
     __syncthreads();
   }
   if (threadIdx.x == 0) atomicAdd(out, sm[0] / double(max(1, *n_valid)));
@@ -695,14 +737,14 @@ __global__ void loss_reduce_kernel(const float* __restrict__ term, int64_t n, co
 // Rays grouped by trained leaf (counting sort): order[] lists the training rays
 // leaf by leaf, then the rays that train nothing.
 // ---------------------------------------------------------------------------
-__global__ void leaf_hist_kernel(const int32_t* __restrict__ leaf, int64_t n, int32_t* counts) {
+static __global__ void leaf_hist_kernel(const int32_t* __restrict__ leaf, int64_t n, int32_t* counts) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i < n && leaf[i] >= 0) atomicAdd(counts + leaf[i], 1);
 }
 
 // Exclusive scan of n_leaves counts into cursor[0..n_leaves]; cursor[n_leaves]
 // is the number of training rays (where the rays without a leaf start).
-__global__ void __launch_bounds__(1024) leaf_scan_kernel(const int32_t* __restrict__ counts, int n_leaves,
+static __global__ void __launch_bounds__(1024) leaf_scan_kernel(const int32_t* __restrict__ counts, int n_leaves,
                                                          int32_t* cursor) {
   __shared__ int32_t part[1024];
   const int per = (n_leaves + blockDim.x - 1) / blockDim.x;
@@ -725,7 +767,7 @@ __global__ void __launch_bounds__(1024) leaf_scan_kernel(const int32_t* __restri
   if (threadIdx.x == blockDim.x - 1) cursor[n_leaves] = part[threadIdx.x];
 }
 
-__global__ void leaf_scatter_kernel(const int32_t* __restrict__ leaf, int64_t n, int n_leaves, int32_t* cursor,
+static __global__ void leaf_scatter_kernel(const int32_t* __restrict__ leaf, int64_t n, int n_leaves, int32_t* cursor,
                                     int32_t* order) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -745,7 +787,7 @@ namespace nbvh {
 // key = seed words, counter (ray, step low, step high, 3), u = top 24 bits
 // * 2^-24, trained iff u < prob[leaf]); a rejected ray trains nothing.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) leaf_select_kernel(int32_t* __restrict__ leaf, int64_t n, uint32_t k0,
+static __global__ void __launch_bounds__(256) leaf_select_kernel(int32_t* __restrict__ leaf, int64_t n, uint32_t k0,
                                                           uint32_t k1, uint32_t step_lo, uint32_t step_hi,
                                                           const float* __restrict__ prob, uint32_t* hits,
                                                           int32_t* n_valid) {
@@ -763,19 +805,74 @@ __global__ void __launch_bounds__(256) leaf_select_kernel(int32_t* __restrict__ 
   }
 }
 
-// Per-leaf sums of the trained rays' loss terms (entry i of the forward's
-// term buffer belongs to ray order[i], or to ray i without an order).
-__global__ void __launch_bounds__(256) leaf_loss_kernel(const float* __restrict__ term, int64_t n,
-                                                        const int32_t* __restrict__ leaf,
-                                                        const int32_t* __restrict__ order, uint32_t* trained,
-                                                        double* loss) {
-  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int64_t r = order ? int64_t(order[i]) : i;
-  const int lf = leaf[r];
-  if (lf < 0) return;
-  atomicAdd(trained + lf, 1u);
-  atomicAdd(loss + lf, double(term[i]));
+// Per-leaf sums of the trained rays' loss terms, one warp per leaf over the
+// leaf's contiguous range of the grouped order (after leaf_scatter_kernel,
+// cursor[l] is the range's end and counts[l] its length). The term of order
+// position i is term[i] (by_item: the tensor-core forward stores terms by
+// item) or term[order[i]] (by ray). Compensated per-lane sums, then a
+// pairwise warp reduction; one lane adds the leaf's sum and count (FP32).
+static __global__ void __launch_bounds__(256) leaf_loss_kernel(const float* __restrict__ term,
+                                                               const int32_t* __restrict__ order, int by_item,
+                                                               const int32_t* __restrict__ counts,
+                                                               const int32_t* __restrict__ cursor, int n_leaves,
+                                                               uint32_t* trained, float* loss) {
+  const int l = int(blockIdx.x) * (blockDim.x >> 5) + int(threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (l >= n_leaves) return;
+  const int cnt = counts[l];
+  const int end = cursor[l], start = end - cnt;
+  float sum = 0.0f, comp = 0.0f;
+  for (int i = start + lane; i < end; i += 32) kahan_add(sum, comp, term[by_item ? i : order[i]]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sum = __fadd_rn(sum, __shfl_xor_sync(0xffffffffu, sum, o));
+  if (lane == 0 && cnt > 0) {
+    trained[l] += uint32_t(cnt);
+    loss[l] = __fadd_rn(loss[l], sum);
+  }
+}
+
+// ---------------------------------------------------------------- launch
+template <typename T, int F, int W>
+cudaError_t launch_train_plain(bool backward, const TrainArgs& a, cudaStream_t s) {
+  const size_t smem = backward ? train_bwd_smem(a.gp.n_inputs, W, a.n_hidden, a.n_out)
+                               : train_fwd_smem(a.gp.n_inputs, W, a.n_hidden, a.n_out);
+  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+  auto kern = backward ? train_backward_plain<T, F, W> : train_forward_plain<T, F, W>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kPlainThreads, smem);
+  if (e != cudaSuccess) return e;
+  const int64_t tiles = (a.n + kPlainTM - 1) / kPlainTM;
+  int64_t grid = int64_t(sm_count()) * (occ < 1 ? 1 : occ);
+  if (tiles < grid) grid = tiles;
+  if (grid < 1) return cudaSuccess;
+  kern<<<unsigned(grid), kPlainThreads, smem, s>>>(a);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template <typename T, int F>
+cudaError_t launch_train_tf(bool bwd, int W, const TrainArgs& a, cudaStream_t s) {
+  switch (W) {
+    case 16: return launch_train_plain<T, F, 16>(bwd, a, s);
+    case 32: return launch_train_plain<T, F, 32>(bwd, a, s);
+    case 64: return launch_train_plain<T, F, 64>(bwd, a, s);
+    case 128: return launch_train_plain<T, F, 128>(bwd, a, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// The FP32 training kernels of one table type (one translation unit each).
+template <typename T>
+cudaError_t launch_train_t(bool bwd, const nbvh_model_desc* d, const TrainArgs& a, cudaStream_t s) {
+  switch (d->n_features) {
+    case 1: return launch_train_tf<T, 1>(bwd, d->width, a, s);
+    case 2: return launch_train_tf<T, 2>(bwd, d->width, a, s);
+    case 4: return launch_train_tf<T, 4>(bwd, d->width, a, s);
+    case 8: return launch_train_tf<T, 8>(bwd, d->width, a, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace nbvh

@@ -193,7 +193,7 @@ __device__ __forceinline__ void queue_first(const TraverseOut& out, bool want, i
 }
 
 // One thread per ray.
-__global__ void __launch_bounds__(256) traverse_kernel(const nbvh_node* __restrict__ nodes,
+static __global__ void __launch_bounds__(256) traverse_kernel(const nbvh_node* __restrict__ nodes,
                                                        RayPtrs rays, int64_t n, TraverseOut out) {
   const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const bool active = r < n;
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(256) traverse_kernel(const nbvh_node* __restri
 
 // The rays list[0 .. *list_count) only (hybrid hierarchy: the rays whose
 // interval meets the instance's root boxes); grid-stride, warp-uniform loop.
-__global__ void __launch_bounds__(256) traverse_list_kernel(const nbvh_node* __restrict__ nodes, RayPtrs rays,
+static __global__ void __launch_bounds__(256) traverse_list_kernel(const nbvh_node* __restrict__ nodes, RayPtrs rays,
                                                             int64_t n, const int32_t* __restrict__ list,
                                                             const int32_t* __restrict__ list_count,
                                                             TraverseOut out) {
@@ -273,7 +273,7 @@ __device__ __forceinline__ bool root_maybe(const float* __restrict__ box, const 
   return en <= ex + slack * (fabsf(ex) + fabsf(en)) + 1e-30f;
 }
 
-__global__ void __launch_bounds__(256) tlas_cull_kernel(RayPtrs rays, int64_t n, const float* __restrict__ best_t,
+static __global__ void __launch_bounds__(256) tlas_cull_kernel(RayPtrs rays, int64_t n, const float* __restrict__ best_t,
                                                         CullArgs c) {
   constexpr int kWarps = 256 / 32;
   __shared__ int s_cnt[kMaxInstances], s_base[kMaxInstances];

@@ -78,7 +78,7 @@ __device__ __forceinline__ bool clip_box_robust(const RayR& r, float tmax, float
 // The traversal visits the nearer child first and skips boxes whose
 // conservative clip to [tmin, best] is empty (inclusive, so equal-t candidates
 // survive).
-__global__ void __launch_bounds__(128) tri_trace_kernel(TriBlasArgs a) {
+static __global__ void __launch_bounds__(128) tri_trace_kernel(TriBlasArgs a) {
   const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (r >= a.n) return;
   const float ox = a.rays.ox[r], oy = a.rays.oy[r], oz = a.rays.oz[r];
@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(128) tri_trace_kernel(TriBlasArgs a) {
 }
 
 // Empty hit records (hit 0, t +inf, leaf -1, instance -1) before the merges.
-__global__ void __launch_bounds__(256) hits_clear_kernel(nbvh_hits h, int32_t* inst_out, int64_t n) {
+static __global__ void __launch_bounds__(256) hits_clear_kernel(nbvh_hits h, int32_t* inst_out, int64_t n) {
   const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (r >= n) return;
   h.hit[r] = 0;

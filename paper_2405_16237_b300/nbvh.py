@@ -94,8 +94,13 @@ class LeafStats(ctypes.Structure):
     _fields_ = [("hits", c_void_p), ("trained", c_void_p), ("loss", c_void_p)]
 
 
+class QueryOptions(ctypes.Structure):
+    _fields_ = [("schedule", c_int32), ("patience_cycles", c_int64), ("traverse_block", c_int32),
+                ("eval_threads", c_int32), ("w1_mode", c_int32)]
+
+
 class TuneResult(ctypes.Structure):
-    _fields_ = [("schedule", c_int32), ("patience_cycles", c_int64), ("traverse_block", c_int32), ("ms", c_float)]
+    _fields_ = [("opt", QueryOptions), ("ms", c_float)]
 
 
 class TriBlas(ctypes.Structure):
@@ -125,15 +130,18 @@ _SIGS = {
                                 c_void_p]),
     "nbvh_encode": (c_int32, [POINTER(ModelDesc), c_void_p, Rays, c_void_p, c_void_p, c_void_p, c_int64,
                               c_void_p, c_void_p]),
+    "nbvh_query_options_default": (c_int32, [POINTER(QueryOptions)]),
+    "nbvh_eval_workspace_size": (c_int32, [POINTER(ModelDesc), POINTER(c_size_t)]),
+    "nbvh_eval_plan": (c_int32, [POINTER(ModelDesc), POINTER(QueryOptions), POINTER(c_int32), POINTER(c_int32),
+                                 POINTER(c_int32), POINTER(c_int32)]),
     "nbvh_eval_segments": (c_int32, [POINTER(ModelDesc), c_void_p, c_void_p, Rays, c_void_p, c_void_p, c_void_p,
-                                     c_int64, c_void_p, c_void_p]),
+                                     c_int64, c_void_p, POINTER(QueryOptions), c_void_p, c_size_t, c_void_p]),
     "nbvh_query_workspace_size": (c_int32, [POINTER(ModelDesc), c_int64, c_int32, POINTER(c_size_t)]),
     "nbvh_query_rays": (c_int32, [POINTER(ModelDesc), c_void_p, c_void_p, c_void_p, c_int32, Rays, c_int32,
                                   Hits, c_void_p, c_size_t, c_void_p]),
+    "nbvh_query_rays_opt": (c_int32, [POINTER(ModelDesc), c_void_p, c_void_p, c_void_p, c_int32, Rays, c_int32,
+                                      Hits, c_void_p, c_size_t, POINTER(QueryOptions), c_void_p]),
     "nbvh_bounce_rays": (c_int32, [Rays, Hits, ctypes.c_uint64, RaysOut, c_void_p]),
-    "nbvh_set_query_schedule": (c_int32, [c_int32, c_int64]),
-    "nbvh_get_query_schedule": (c_int32, [POINTER(c_int32), POINTER(c_int64)]),
-    "nbvh_set_traverse_block": (c_int32, [c_int32]),
     "nbvh_autotune_query": (c_int32, [POINTER(ModelDesc), c_void_p, c_void_p, c_void_p, c_int32, Rays, c_int32, Hits,
                                       c_void_p, c_size_t, c_int32, POINTER(TuneResult), POINTER(TuneResult), c_int32,
                                       POINTER(c_int32), c_void_p]),
@@ -147,6 +155,9 @@ _SIGS = {
                                   c_void_p, c_void_p, c_void_p, c_void_p]),
     "nbvh_train_labels": (c_int32, [Rays, c_void_p, c_void_p, c_void_p, POINTER(TrainScene), Labels, c_void_p]),
     "nbvh_train_workspace_size": (c_int32, [POINTER(ModelDesc), c_int64, c_int32, POINTER(c_size_t)]),
+    "nbvh_train_workspace_budget": (c_int32, [POINTER(ModelDesc), c_int64, c_int32, c_size_t, POINTER(c_size_t),
+                                              POINTER(c_int64)]),
+    "nbvh_loss_fp64": (c_int32, [POINTER(ModelDesc), c_int64, c_void_p, c_void_p, c_size_t, c_void_p, c_void_p]),
     "nbvh_forward_train": (c_int32, [POINTER(ModelDesc), c_void_p, c_void_p, Rays, c_void_p, c_void_p, c_void_p,
                                      Labels, c_void_p, c_float, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t,
                                      c_void_p]),
@@ -161,6 +172,10 @@ _SIGS = {
                                            c_void_p, c_size_t, c_void_p]),
     "nbvh_build_cut": (c_int32, [c_void_p, c_int32, c_void_p, c_int32, c_void_p, c_int32, c_double, c_float,
                                  c_void_p, c_int32, POINTER(c_int32), c_void_p, c_void_p, c_void_p]),
+    "nbvh_rank_leaves": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int64, c_void_p, c_void_p, c_void_p,
+                                   c_void_p]),
+    "nbvh_refine_cut": (c_int32, [c_void_p, c_int32, c_void_p, c_int32, c_void_p, c_void_p, c_int32, c_void_p,
+                                  c_void_p, c_int32, POINTER(c_int32)]),
     "nbvh_graph_begin": (c_int32, [c_void_p]),
     "nbvh_graph_end": (c_int32, [c_void_p, POINTER(c_void_p)]),
     "nbvh_graph_launch": (c_int32, [c_void_p, c_void_p]),
@@ -170,7 +185,7 @@ _SIGS = {
     "nbvh_trace_triangles": (c_int32, [POINTER(TriBlas), Rays, Hits, c_void_p]),
     "nbvh_hybrid_workspace_size": (c_int32, [POINTER(Instance), c_int32, c_int64, POINTER(c_size_t)]),
     "nbvh_hybrid_trace": (c_int32, [POINTER(Instance), c_int32, Rays, Hits, c_void_p, c_void_p, c_size_t,
-                                    c_void_p]),
+                                    POINTER(QueryOptions), c_void_p]),
     "nbvh_probe_l2_gather": (c_int32, [c_void_p, c_int64, c_void_p, POINTER(c_double), c_void_p]),
     "nbvh_get_device_status": (c_int32, [c_void_p]),
 }
@@ -378,13 +393,37 @@ def encode(desc: ModelDesc, table, rays: dict, seg_ray, t0, t1, out=None):
     return out
 
 
-def eval_segments(desc: ModelDesc, table, mlp, rays: dict, seg_ray, t0, t1, out=None):
+def eval_plan(desc: ModelDesc, options=None):
+    """nbvh_eval_plan: the evaluation's launch plan as a dict, or None when
+    the kernels cannot run this model under these options."""
+    th, st, sm, tm = c_int32(), c_int32(), c_int32(), c_int32()
+    code = lib().nbvh_eval_plan(ctypes.byref(desc), _opt_ref(options), ctypes.byref(th), ctypes.byref(st),
+                                ctypes.byref(sm), ctypes.byref(tm))
+    if code == 7:
+        return None
+    _check(code, "eval_plan")
+    return {"threads": th.value, "w1_streamed": bool(st.value), "smem_bytes": sm.value, "tmem_cols": tm.value}
+
+
+def eval_workspace_size(desc: ModelDesc) -> int:
+    b = c_size_t()
+    _check(lib().nbvh_eval_workspace_size(ctypes.byref(desc), ctypes.byref(b)), "eval_workspace_size")
+    return b.value
+
+
+def eval_segments(desc: ModelDesc, table, mlp, rays: dict, seg_ray, t0, t1, out=None, options=None, workspace=None):
     torch = _torch()
     n = seg_ray.numel()
     if out is None:
         out = torch.empty((n, desc.n_out), dtype=torch.float32, device=seg_ray.device)
+    need = eval_workspace_size(desc)
+    if workspace is None and need > 0:
+        workspace = new_workspace(need, seg_ray.device)
+    base = aligned_ptr(workspace) if workspace is not None else None
+    avail = workspace.numel() - (base - workspace.data_ptr()) if workspace is not None else 0
     _check(lib().nbvh_eval_segments(ctypes.byref(desc), _ptr(table), _ptr(mlp), rays_struct(rays), _ptr(seg_ray),
-                                    _ptr(t0), _ptr(t1), n, _ptr(out), _stream()), "eval_segments")
+                                    _ptr(t0), _ptr(t1), n, _ptr(out), _opt_ref(options),
+                                    c_void_p(base) if base else None, avail, _stream()), "eval_segments")
     return out
 
 
@@ -405,8 +444,42 @@ def aligned_ptr(ws) -> int:
     return (p + 255) & ~255
 
 
+SCHEDULE_WAVES, SCHEDULE_PERSISTENT = 0, 1
+W1_AUTO, W1_RESIDENT, W1_STREAMED = 0, 1, 2
+
+
+def query_options(**kw) -> QueryOptions:
+    """nbvh_query_options_default with the given fields replaced (schedule,
+    patience_cycles, traverse_block, eval_threads, w1_mode)."""
+    o = QueryOptions()
+    _check(lib().nbvh_query_options_default(ctypes.byref(o)), "query_options_default")
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def options_dict(o: QueryOptions) -> dict:
+    return {"schedule": ["waves", "persistent"][o.schedule], "patience_cycles": o.patience_cycles,
+            "traverse_block": o.traverse_block, "eval_threads": o.eval_threads,
+            "w1_mode": ["auto", "resident", "streamed"][o.w1_mode]}
+
+
+def options_from_dict(d: dict) -> QueryOptions:
+    return query_options(schedule=["waves", "persistent"].index(d["schedule"]), patience_cycles=d["patience_cycles"],
+                         traverse_block=d["traverse_block"], eval_threads=d["eval_threads"],
+                         w1_mode=["auto", "resident", "streamed"].index(d["w1_mode"]))
+
+
+def _opt_ref(options):
+    if options is None:
+        return None
+    if isinstance(options, dict):
+        options = options_from_dict(options)
+    return ctypes.byref(options)
+
+
 def query_rays(desc: ModelDesc, table, mlp, nodes, n_nodes: int, rays: dict, max_segs: int, out=None,
-               workspace=None):
+               workspace=None, options=None):
     n = rays["ox"].numel()
     if out is None:
         out = new_hits(n, rays["ox"].device, albedo=desc.n_out >= 8)
@@ -415,9 +488,9 @@ def query_rays(desc: ModelDesc, table, mlp, nodes, n_nodes: int, rays: dict, max
         workspace = new_workspace(need, rays["ox"].device)
     base = aligned_ptr(workspace)
     avail = workspace.numel() - (base - workspace.data_ptr())
-    _check(lib().nbvh_query_rays(ctypes.byref(desc), _ptr(table), _ptr(mlp), _ptr(nodes), n_nodes,
-                                 rays_struct(rays), max_segs, hits_struct(out), c_void_p(base), avail, _stream()),
-           "query_rays")
+    _check(lib().nbvh_query_rays_opt(ctypes.byref(desc), _ptr(table), _ptr(mlp), _ptr(nodes), n_nodes,
+                                     rays_struct(rays), max_segs, hits_struct(out), c_void_p(base), avail,
+                                     _opt_ref(options), _stream()), "query_rays")
     return out
 
 
@@ -444,41 +517,26 @@ def bounce_rays(rays: dict, hits: dict, seed: int, out=None):
     return out
 
 
-SCHEDULE_WAVES, SCHEDULE_PERSISTENT = 0, 1
-
-
-def set_query_schedule(schedule: int, patience_cycles: int = 4000):
-    _check(lib().nbvh_set_query_schedule(schedule, patience_cycles), "set_query_schedule")
-
-
-def get_query_schedule():
-    a, b = c_int32(), c_int64()
-    _check(lib().nbvh_get_query_schedule(ctypes.byref(a), ctypes.byref(b)), "get_query_schedule")
-    return a.value, b.value
-
-
-def set_traverse_block(threads: int):
-    _check(lib().nbvh_set_traverse_block(threads), "set_traverse_block")
-
-
 def _tune_dict(r: TuneResult) -> dict:
-    return {"schedule": ["waves", "persistent"][r.schedule], "patience_cycles": r.patience_cycles,
-            "traverse_block": r.traverse_block, "ms": r.ms}
+    d = options_dict(r.opt)
+    d["ms"] = r.ms
+    return d
 
 
 def autotune_query(desc: ModelDesc, table, mlp, nodes, n_nodes: int, rays: dict, max_segs: int, out=None,
                    workspace=None, reps: int = 3):
-    """nbvh_autotune_query: times the query under each candidate schedule and
-    keeps the fastest (process-wide). Returns (best, [all candidates])."""
+    """nbvh_autotune_query: times the query under each candidate option set
+    and returns (best, [all candidates]) as dicts (options_from_dict turns
+    one back into options); the library keeps no state."""
     n = rays["ox"].numel()
     if out is None:
-        out = new_hits(n, rays["ox"].device)
+        out = new_hits(n, rays["ox"].device, albedo=desc.n_out >= 8)
     if workspace is None:
         workspace = new_workspace(query_workspace_size(desc, n, max_segs), rays["ox"].device)
     base = aligned_ptr(workspace)
     avail = workspace.numel() - (base - workspace.data_ptr())
     best = TuneResult()
-    cap = 16
+    cap = 32
     arr = (TuneResult * cap)()
     n_all = c_int32()
     _check(lib().nbvh_autotune_query(ctypes.byref(desc), _ptr(table), _ptr(mlp), _ptr(nodes), n_nodes,
@@ -606,6 +664,28 @@ def train_workspace_size(desc: ModelDesc, n: int, n_leaves: int = 0) -> int:
     _check(lib().nbvh_train_workspace_size(ctypes.byref(desc), n, n_leaves, ctypes.byref(b)),
            "train_workspace_size")
     return b.value
+
+
+def train_workspace_budget(desc: ModelDesc, n: int, n_leaves: int, max_bytes: int):
+    """(bytes, rays per activation chunk) of a training workspace within
+    max_bytes: the stored mode (chunk = n) when it fits, else recompute mode."""
+    b, c = c_size_t(), c_int64()
+    _check(lib().nbvh_train_workspace_budget(ctypes.byref(desc), n, n_leaves, max_bytes, ctypes.byref(b),
+                                             ctypes.byref(c)), "train_workspace_budget")
+    return b.value, c.value
+
+
+def workspace_bytes(workspace) -> int:
+    """Usable bytes of a workspace tensor from its 256-byte aligned start."""
+    base = aligned_ptr(workspace)
+    return workspace.numel() - (base - workspace.data_ptr())
+
+
+def loss_fp64(desc: ModelDesc, n: int, n_valid, workspace, out):
+    """nbvh_loss_fp64: the last forward's loss with FP64 accumulation (the
+    finite-difference check's reduction); out: device float64 scalar."""
+    _check(lib().nbvh_loss_fp64(ctypes.byref(desc), n, _ptr(n_valid), c_void_p(aligned_ptr(workspace)),
+                                workspace_bytes(workspace), _ptr(out), _stream()), "loss_fp64")
 
 
 def forward_train(desc: ModelDesc, table, mlp, rays: dict, leaf, t0, t1, workspace, labels=None, n_valid=None,
@@ -800,7 +880,7 @@ def hybrid_workspace_size(instances, n_rays: int) -> int:
     return b.value
 
 
-def hybrid_trace(instances, rays: dict, out=None, inst_out=None, workspace=None):
+def hybrid_trace(instances, rays: dict, out=None, inst_out=None, workspace=None, options=None):
     """Closest hit over the instances of the two-level hierarchy
     (nbvh_hybrid_trace). Returns (hits, instance index per ray)."""
     torch = _torch()
@@ -818,7 +898,7 @@ def hybrid_trace(instances, rays: dict, out=None, inst_out=None, workspace=None)
     base = aligned_ptr(workspace)
     avail = workspace.numel() - (base - workspace.data_ptr())
     _check(lib().nbvh_hybrid_trace(arr, len(arr), rays_struct(rays), hits_struct(out), _ptr(inst_out),
-                                   c_void_p(base), avail, _stream()), "hybrid_trace")
+                                   c_void_p(base), avail, _opt_ref(options), _stream()), "hybrid_trace")
     return out, inst_out
 
 
@@ -871,7 +951,7 @@ def base_children(base: dict, ref: int):
 def train_step_weighted(desc: ModelDesc, opt, scene, mode: int, batch: int, seed: int, step: int, lr: float,
                         workspace, leaf_prob=None, stats=None, loss_out=None):
     """nbvh_train_step_weighted. stats: dict of device tensors hits (int32),
-    trained (int32), loss (float64), n_leaves entries each, accumulated."""
+    trained (int32), loss (float32), n_leaves entries each, accumulated."""
     base = aligned_ptr(workspace)
     avail = workspace.numel() - (base - workspace.data_ptr())
     st = None
@@ -886,24 +966,37 @@ def train_step_weighted(desc: ModelDesc, opt, scene, mode: int, batch: int, seed
 
 
 def node_rank(hits, trained, loss, n_rays):
-    """Sec. 5.1 "Node error": q = mean training loss of the leaf, p = fraction of
-    the training rays that hit it, ranking r = 2 log q + log p; the training
-    probability of Sec. 5.2, read as max(exp(r - r_max), 0.005) (the ranking's
-    linear-domain ratio q^2 p / max q^2 p). A leaf no ray hit gets r = -inf; a
-    leaf hit but never trained takes the mean q of the trained ones."""
-    hits = np.asarray(hits, np.float64)
-    trained = np.asarray(trained, np.float64)
-    loss = np.asarray(loss, np.float64)
-    q = np.where(trained > 0, loss / np.maximum(trained, 1.0), np.nan)
-    qm = np.nanmean(q) if np.any(trained > 0) else 1.0
-    q = np.where(np.isnan(q), qm, q)
-    p = hits / max(1.0, float(n_rays))
-    with np.errstate(divide="ignore"):
-        r = np.where((hits > 0) & (q > 0), 2.0 * np.log(np.maximum(q, 1e-300)) + np.log(np.maximum(p, 1e-300)),
-                     -np.inf)
-    rmax = np.max(r) if np.any(np.isfinite(r)) else 0.0
-    prob = np.where(np.isfinite(r), np.maximum(np.exp(r - rmax), 0.005), 0.005)
+    """nbvh_rank_leaves (Sec. 5.1 "Node error", Sec. 5.2 training
+    probability): per leaf q, p, the ranking r and the training probability."""
+    n = len(hits)
+    h = np.ascontiguousarray(hits, np.uint32)
+    t = np.ascontiguousarray(trained, np.uint32)
+    l = np.ascontiguousarray(loss, np.float32)
+    q, p, r = (np.zeros(n, np.float64) for _ in range(3))
+    prob = np.zeros(n, np.float32)
+    _check(lib().nbvh_rank_leaves(h.ctypes.data_as(c_void_p), t.ctypes.data_as(c_void_p), l.ctypes.data_as(c_void_p),
+                                  n, int(n_rays), q.ctypes.data_as(c_void_p), p.ctypes.data_as(c_void_p),
+                                  r.ctypes.data_as(c_void_p), prob.ctypes.data_as(c_void_p)), "rank_leaves")
     return q, p, r, prob
+
+
+def refine_cut(base: dict, cut, r, prob, k_splits: int):
+    """nbvh_refine_cut (Sec. 5.1): the cut with its k_splits best-ranked
+    splittable leaves replaced by their base children, and every new leaf's
+    training probability. Returns (new cut, new probabilities)."""
+    cut = np.ascontiguousarray(cut, np.int32)
+    r = np.ascontiguousarray(r, np.float64)
+    prob = np.ascontiguousarray(prob, np.float32)
+    cap = 2 * len(cut)
+    out = np.zeros(cap, np.int32)
+    out_p = np.zeros(cap, np.float32)
+    m = c_int32()
+    nodes = np.ascontiguousarray(base["nodes"])
+    _check(lib().nbvh_refine_cut(nodes.ctypes.data_as(c_void_p), base["n_nodes"], cut.ctypes.data_as(c_void_p),
+                                 len(cut), r.ctypes.data_as(c_void_p), prob.ctypes.data_as(c_void_p), int(k_splits),
+                                 out.ctypes.data_as(c_void_p), out_p.ctypes.data_as(c_void_p), cap, ctypes.byref(m)),
+           "refine_cut")
+    return out[:m.value].tolist(), out_p[:m.value].tolist()
 
 
 def optimize_cut(tris, desc: ModelDesc, opt, n_target: int, *, base_max_leaf: int = 16, iters: int = 50,
@@ -934,7 +1027,7 @@ def optimize_cut(tris, desc: ModelDesc, opt, n_target: int, *, base_max_leaf: in
     history = []
     ws = None
     ws_leaves = -1
-    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
 
     lods = []  # registered (leaves, scene), coarse to fine
     lod_rng = np.random.default_rng(seed ^ 0x10D)
@@ -951,7 +1044,7 @@ def optimize_cut(tris, desc: ModelDesc, opt, n_target: int, *, base_max_leaf: in
         n = len(cut)
         stats = {"hits": torch.zeros(n, dtype=torch.int32, device="cuda"),
                  "trained": torch.zeros(n, dtype=torch.int32, device="cuda"),
-                 "loss": torch.zeros(n, dtype=torch.float64, device="cuda")}
+                 "loss": torch.zeros(n, dtype=torch.float32, device="cuda")}
         pdev = torch.as_tensor(np.asarray(prob, np.float32)).cuda() if prob is not None else None
         for _ in range(n_iters):
             k = int(lod_rng.integers(0, len(lods) + 1)) if lods else len(lods)
@@ -978,22 +1071,12 @@ def optimize_cut(tris, desc: ModelDesc, opt, n_target: int, *, base_max_leaf: in
         q, p, r, pr = node_rank(h, t, l, batch * iters)
         history.append({"leaves": len(cut), "iters": iters, "loss": float(loss.item()),
                         "mean_q": float(np.sum(l) / max(1, np.sum(t)))})
-        refs = lv["leaf_ref"]
-        cand = [i for i in range(len(refs)) if refs[i] >= 0 and np.isfinite(r[i])]
-        cand.sort(key=lambda i: (-r[i], i))
-        k = min(int(splits), n_target - len(cut), len(cand))
+        k = min(int(splits), n_target - len(cut))
         if k <= 0:
             break
-        chosen = set(cand[:k])
-        new_cut, new_prob = [], []
-        for i, ref in enumerate(refs):
-            if i in chosen:
-                ch = base_children(base, int(ref))
-                new_cut += ch
-                new_prob += [1.0] * len(ch)
-            else:
-                new_cut.append(int(ref))
-                new_prob.append(float(pr[i]))
+        new_cut, new_prob = refine_cut(base, lv["leaf_ref"], r, pr, k)
+        if len(new_cut) == len(cut):
+            break  # nothing left to split
         cut, prob = new_cut, new_prob
         iters = int(math.ceil(iters * factor))
         splits = int(math.ceil(splits * factor))

@@ -105,7 +105,7 @@ def test_albedo_forward_loss_and_gradients_fp32():
     dv, h = _batch8(b)
     n = len(h["leaf"])
     ws = B.new_workspace(B.train_workspace_size(b.desc, n))
-    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
     raw = B.forward_train(b.desc, b.table, b.mlp, dv["rays"], dv["leaf"], dv["t0"], dv["t1"], ws,
                           labels=dv["lab"], n_valid=dv["n_valid"], loss_out=loss)
     g_tab = torch.zeros((b.layout["total"], b.case.model.n_features), dtype=torch.float32, device="cuda")
@@ -152,7 +152,7 @@ def test_albedo_tensor_core_gradients_match_half_precision_oracle(mp):
     n = len(h["leaf"])
     ws = B.new_workspace(B.train_workspace_size(desc, n))
     scale = 1024.0
-    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
     B.forward_train(desc, b.table, b.mlp, dv["rays"], dv["leaf"], dv["t0"], dv["t1"], ws,
                     labels=dv["lab"], n_valid=dv["n_valid"], loss_scale=scale, loss_out=loss)
     g_tab = torch.zeros((b.layout["total"], b.case.model.n_features), dtype=torch.float32, device="cuda")
@@ -178,13 +178,9 @@ def test_albedo_query_parity(mp, schedule):
     _torch()
     b = built8()
     desc = b.with_prec(mp)
-    old = B.get_query_schedule()
-    B.set_query_schedule(schedule, 0)
-    try:
-        h = {k: v.cpu().numpy() for k, v in
-             B.query_rays(desc, b.table, b.mlp, b.nodes, b.leaves["n_nodes"], b.rays, 24).items()}
-    finally:
-        B.set_query_schedule(*old)
+    opt = B.query_options(schedule=schedule, patience_cycles=0)
+    h = {k: v.cpu().numpy() for k, v in
+         B.query_rays(desc, b.table, b.mlp, b.nodes, b.leaves["n_nodes"], b.rays, 24, options=opt).items()}
     assert B.device_status() == 0 and "ar" in h
     res = b.oracle_query()
     n = len(h["hit"])
@@ -271,7 +267,7 @@ def test_albedo_training_learns():
         return float(np.mean(np.abs(a[both] - gt_alb[both]))), int(both.sum())
 
     before, _ = albedo_error()
-    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
     for step in range(1, 1201):
         B.train_step(desc, opt, scene, B.TRAIN_PROBED_MIX, batch, 7, step, 1e-2, ws, loss_out=loss)
     assert B.device_status() == 0 and np.isfinite(float(loss.item()))

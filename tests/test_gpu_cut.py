@@ -47,7 +47,7 @@ def test_weighted_step_selection_and_leaf_statistics():
     prob[4] = 1.0
     stats = {"hits": torch.zeros(n_leaves, dtype=torch.int32, device="cuda"),
              "trained": torch.zeros(n_leaves, dtype=torch.int32, device="cuda"),
-             "loss": torch.zeros(n_leaves, dtype=torch.float64, device="cuda")}
+             "loss": torch.zeros(n_leaves, dtype=torch.float32, device="cuda")}
     ws = B.new_workspace(B.train_workspace_size(desc, n, n_leaves))
     B.train_step_weighted(desc, opt, scene, B.TRAIN_PROBED_MIX, n, seed, step, 1e-2, ws,
                           leaf_prob=torch.as_tensor(prob).cuda(), stats=stats)
@@ -80,8 +80,8 @@ def test_unweighted_step_equals_plain_step():
     _, _, _, _, _, _, _, opt_b, _ = _setup()
     n = 2048
     ws = B.new_workspace(B.train_workspace_size(desc, n, len(leaves["leaf_lo"])))
-    la = torch.zeros(1, dtype=torch.float64, device="cuda")
-    lb = torch.zeros(1, dtype=torch.float64, device="cuda")
+    la = torch.zeros(1, dtype=torch.float32, device="cuda")
+    lb = torch.zeros(1, dtype=torch.float32, device="cuda")
     B.train_step(desc, opt_a, scene, B.TRAIN_PROBED_MIX, n, 9, 1, 1e-2, ws, loss_out=la)
     B.train_step_weighted(desc, opt_b, scene, B.TRAIN_PROBED_MIX, n, 9, 1, 1e-2, ws, loss_out=lb)
     assert B.device_status() == 0

@@ -46,11 +46,10 @@ def test_empty_and_ragged_ray_sets(mp, schedule):
     torch = _torch()
     b = built()
     desc = b.with_prec(mp)
-    old = B.get_query_schedule()
-    B.set_query_schedule(schedule, 0)
-    try:
+    opt = B.query_options(schedule=schedule, patience_cycles=0)
+    if True:
         empty = {k: v[:0] for k, v in B.to_device_rays(b.case.rays).items()}
-        out = B.query_rays(desc, b.table, b.mlp, b.nodes, b.leaves["n_nodes"], empty, 8)
+        out = B.query_rays(desc, b.table, b.mlp, b.nodes, b.leaves["n_nodes"], empty, 8, options=opt)
         assert out["hit"].numel() == 0
         rng = np.random.default_rng(3)
         n_all = len(b.case.rays["ox"])
@@ -58,7 +57,8 @@ def test_empty_and_ragged_ray_sets(mp, schedule):
             idx = np.sort(rng.choice(n_all, n, replace=False))
             rays = _sub(b.case.rays, idx)
             res = O.query(rays, b.oleaves, b.table_host, b.layers, b.olayout, b.case.model.n_samples)
-            h = _np(B.query_rays(desc, b.table, b.mlp, b.nodes, b.leaves["n_nodes"], B.to_device_rays(rays), 24))
+            h = _np(B.query_rays(desc, b.table, b.mlp, b.nodes, b.leaves["n_nodes"], B.to_device_rays(rays), 24,
+                                 options=opt))
             ok = ~ambiguous_rays(res, n)
             if mp == B.FP32:
                 assert np.array_equal(h["hit"][ok].astype(bool), res["hit"][ok].astype(bool))
@@ -66,8 +66,6 @@ def test_empty_and_ragged_ray_sets(mp, schedule):
                 assert np.all(np.abs(h["t"][hh] - res["t"][hh]) <= 1e-5 * np.abs(res["t"][hh]))
             else:
                 assert np.mean(h["hit"][ok].astype(bool) == res["hit"][ok].astype(bool)) >= (0.99 if n > 100 else 0.0)
-    finally:
-        B.set_query_schedule(*old)
     assert B.device_status() == 0
 
 
@@ -152,28 +150,83 @@ def test_one_ray_training_step():
     scene = B.DeviceScene(b.case.tris, b.leaves)
     opt = B.Optimizer(b.with_prec(B.FP32), b.table.clone(), b.mlp.clone())
     ws = B.new_workspace(B.train_workspace_size(b.with_prec(B.FP32), 1, scene.n_leaves))
-    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
     for step in range(1, 6):
         B.train_step(b.with_prec(B.FP32), opt, scene, B.TRAIN_PROBED_MIX, 1, 21, step, 1e-2, ws, loss_out=loss)
         assert np.isfinite(loss.item())
     assert B.device_status() == 0
 
 
-@pytest.mark.parametrize("mp", [B.FP32, B.FP16])
-def test_inputs_beyond_the_kernels_report_unsupported(mp):
-    """N * L * F = 1024 is a valid descriptor (<= NBVH_MAX_INPUTS) that neither
-    MLP kernel stages (the first layer's weights or features exceed shared
-    memory or TMEM): the query returns NBVH_ERR_UNSUPPORTED and the device
-    status stays clean."""
+@pytest.mark.parametrize("mp", [B.FP32, B.FP16, B.BF16])
+@pytest.mark.parametrize("shape", [(32, 16, 2), (16, 16, 8)])
+def test_wide_first_layer_matches_oracle(mp, shape):
+    """First layers of N * L * F = 1024 and 2048 inputs (up to NBVH_MAX_INPUTS)
+    run through both MLP kernels, which take them in chunks (the tensor-core
+    kernel 128 inputs at a time, its 16-bit weights resident in shared memory
+    or streamed by bulk copies). Raw outputs of 1,500 segments against the
+    oracle: FP32 <= 1e-5 relative (each output's RMS as the floor); FP16/BF16
+    hit agreement >= 99.9 % on the segments the format resolves, depth
+    <= 2e-3, mean normal error <= 1 degree. The query gives the same bits under
+    every evaluation shape and weight placement."""
     from dataclasses import replace
+    from test_gpu_query import RAW_AGREEMENT, _angle_deg, hit_agreement
     torch = _torch()
+    n_samples, n_levels, n_features = shape
     case = make_case("random_tris_c0", 1.0, 2.0)
-    model = replace(case.model, n_samples=32, n_levels=16, n_features=2, log2_table=12, width=64)
-    b = Built(replace(case, model=model))
+    model = replace(case.model, n_samples=n_samples, n_levels=n_levels, n_features=n_features, log2_table=12,
+                    width=64)
+    rng = np.random.default_rng(11)
+    idx = np.sort(rng.choice(len(case.rays["ox"]), 1200, replace=False))
+    b = Built(replace(case, model=model, table_prec=B.FP32 if mp == B.FP32 else B.FP16,
+                      rays=_sub(case.rays, idx)))
+    seg = O.ray_segments(b.case.rays, b.oleaves["leaf_lo"], b.oleaves["leaf_hi"])
+    S = min(len(seg["ray"]), 1500)
+    assert S > 500
+    t0 = seg["t0"][:S].astype(np.float32)
+    t1 = seg["t1"][:S].astype(np.float32)
+    sr = torch.as_tensor(seg["ray"][:S].astype(np.int32)).cuda()
+    o, d, _, _ = O.rays_od(b.case.rays)
+    rr = seg["ray"][:S]
+    _, ref = O.eval_segments(o[rr], d[rr], t0.astype(np.float64), t1.astype(np.float64), b.table_host,
+                             b.layers, b.olayout, b.oleaves["frame"]["model_centre"],
+                             b.oleaves["frame"]["model_extent"], n_samples)
     desc = b.with_prec(mp)
-    B.device_status()  # clear the status word
-    with pytest.raises(B.NBVHError) as err:
-        B.query_rays(desc, b.table, b.mlp, b.nodes, b.leaves["n_nodes"], b.rays, 64)
-    assert err.value.code == 7  # NBVH_ERR_UNSUPPORTED
-    torch.cuda.synchronize()
+    shapes = [None] if mp == B.FP32 else [B.query_options(eval_threads=t, w1_mode=w)
+                                           for t in (256, 512) for w in (B.W1_RESIDENT, B.W1_STREAMED)]
+    outs = []
+    for opt in shapes:
+        if opt is not None and not _stageable(desc, opt):
+            continue
+        outs.append(B.eval_segments(desc, b.table, b.mlp, b.rays, sr, torch.as_tensor(t0).cuda(),
+                                    torch.as_tensor(t1).cuda(), options=opt).cpu().numpy())
     assert B.device_status() == 0
+    assert len(outs) >= (1 if mp == B.FP32 else 2)
+    for got in outs[1:]:
+        assert np.array_equal(got, outs[0])  # evaluation shape changes no bit
+    got = outs[0]
+    if mp == B.FP32:
+        scale_j = np.sqrt(np.mean(ref ** 2, axis=0))
+        assert (np.abs(got - ref) / (np.abs(ref) + scale_j)).max() <= 1e-5
+    else:
+        raw_agree, resolved = hit_agreement(got[:, 0], ref[:, 0], mp)
+        assert resolved >= 0.999, (raw_agree, resolved)
+        dg = t0 + O.sigmoid(got[:, 1]) * (t1 - t0)
+        dr = t0 + O.sigmoid(ref[:, 1]) * (t1 - t0)
+        assert np.max(np.abs(dg - dr)) <= 2e-3
+        assert np.mean(_angle_deg(got[:, 2:5], ref[:, 2:5])) <= 1.0
+    # the whole query: every shape gives the same records
+    res = {}
+    for opt in shapes:
+        if opt is not None and not _stageable(desc, opt):
+            continue
+        h = B.query_rays(desc, b.table, b.mlp, b.nodes, b.leaves["n_nodes"], b.rays, 32, options=opt)
+        res[None if opt is None else (opt.eval_threads, opt.w1_mode)] = h
+    first = next(iter(res.values()))
+    for h in res.values():
+        for k in first:
+            assert torch.equal(h[k], first[k]), k
+    assert B.device_status() == 0
+
+
+def _stageable(desc, opt) -> bool:
+    return B.eval_plan(desc, opt) is not None

@@ -166,14 +166,9 @@ def test_hybrid_schedules_agree():
     ground, assets = small_hybrid_scene(3)
     hb = HybridBuilt(ground, assets, B.BF16, table_prec=B.BF16)
     rays = B.to_device_rays(hybrid_rays(40, 800))
-    old = B.get_query_schedule()
-    try:
-        B.set_query_schedule(B.SCHEDULE_WAVES, 0)
-        hw, iw = B.hybrid_trace(hb.instances, rays)
-        B.set_query_schedule(B.SCHEDULE_PERSISTENT, 4000)
-        hp, ip = B.hybrid_trace(hb.instances, rays)
-    finally:
-        B.set_query_schedule(*old)
+    hw, iw = B.hybrid_trace(hb.instances, rays, options=B.query_options(schedule=B.SCHEDULE_WAVES))
+    hp, ip = B.hybrid_trace(hb.instances, rays, options=B.query_options(schedule=B.SCHEDULE_PERSISTENT,
+                                                                         eval_threads=512))
     assert B.device_status() == 0
     for k in hw:
         assert torch.equal(hw[k], hp[k]), k

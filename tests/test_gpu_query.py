@@ -343,16 +343,12 @@ def test_persistent_schedule_equals_waves(mp, patience):
     b = built("icosphere_l6", 1.0, 2.0)
     rays = B.to_device_rays(W.mixed_rays(6000, seed=W.SEED_BASE + 31, radius=0.6))
     desc = b.with_prec(mp)
-    old = B.get_query_schedule()
-    try:
-        B.set_query_schedule(B.SCHEDULE_WAVES, 0)
-        hw = B.query_rays(desc, b.table, b.mlp, b.nodes, b.leaves["n_nodes"], rays, 24)
-        B.set_query_schedule(B.SCHEDULE_PERSISTENT, patience)
-        ws = B.new_workspace(B.query_workspace_size(desc, rays["ox"].numel(), 24))
-        hp = B.query_rays(desc, b.table, b.mlp, b.nodes, b.leaves["n_nodes"], rays, 24, workspace=ws)
-        segs, launches = B.query_stats(ws, rays["ox"].numel(), 24)
-    finally:
-        B.set_query_schedule(*old)
+    hw = B.query_rays(desc, b.table, b.mlp, b.nodes, b.leaves["n_nodes"], rays, 24,
+                      options=B.query_options(schedule=B.SCHEDULE_WAVES))
+    ws = B.new_workspace(B.query_workspace_size(desc, rays["ox"].numel(), 24))
+    hp = B.query_rays(desc, b.table, b.mlp, b.nodes, b.leaves["n_nodes"], rays, 24, workspace=ws,
+                      options=B.query_options(schedule=B.SCHEDULE_PERSISTENT, patience_cycles=patience))
+    segs, launches = B.query_stats(ws, rays["ox"].numel(), 24)
     assert B.device_status() == 0
     for k in hw:
         assert torch.equal(hw[k], hp[k]), k
@@ -362,31 +358,35 @@ def test_persistent_schedule_equals_waves(mp, patience):
 
 @pytest.mark.parametrize("mp", [B.FP16, B.FP32])
 def test_autotuner_times_candidates_and_keeps_results(mp):
-    """nbvh_autotune_query: every candidate is timed, the fastest is set
-    process-wide and returned, and the hit records equal the untuned query's
-    bit for bit (the schedule changes only the order of evaluation)."""
+    """nbvh_autotune_query: the schedules (and for FP16/BF16 the evaluation
+    CTA shapes and first-layer placements, then traversal CTA sizes) are each
+    timed; the fastest is returned, nothing is kept in the library, and every
+    candidate's options give hit records equal to the default query's bit for
+    bit (the options change only the order and shape of evaluation)."""
     torch = _torch()
     b = built("icosphere_l6", 1.0, 2.0)
     desc = b.with_prec(mp)
     rays = B.to_device_rays(W.mixed_rays(5000, seed=W.SEED_BASE + 32, radius=0.6))
-    old = B.get_query_schedule()
-    try:
-        ref = B.query_rays(desc, b.table, b.mlp, b.nodes, b.leaves["n_nodes"], rays, 24)
-        best, cands = B.autotune_query(desc, b.table, b.mlp, b.nodes, b.leaves["n_nodes"], rays, 24, reps=2)
-        got = B.query_rays(desc, b.table, b.mlp, b.nodes, b.leaves["n_nodes"], rays, 24)
-        now = B.get_query_schedule()
-    finally:
-        B.set_query_schedule(*old)
-        B.set_traverse_block(128)
+    ref = B.query_rays(desc, b.table, b.mlp, b.nodes, b.leaves["n_nodes"], rays, 24)
+    best, cands = B.autotune_query(desc, b.table, b.mlp, b.nodes, b.leaves["n_nodes"], rays, 24, reps=2)
     assert B.device_status() == 0
     n_sched = 6 if mp != B.FP32 else 1
-    assert len(cands) == n_sched + 2
+    n_shape = 3 if mp != B.FP32 else 0
+    assert len(cands) == n_sched + n_shape + 2
     assert {c["schedule"] for c in cands} == ({"waves", "persistent"} if mp != B.FP32 else {"waves"})
+    if mp != B.FP32:
+        # stage 1 runs the automatic shape (256 threads, resident weights for
+        # this model); stage 2 the three others
+        shapes = {(c["eval_threads"], c["w1_mode"]) for c in cands}
+        assert {(256, "streamed"), (512, "resident"), (512, "streamed")} <= shapes
     assert all(c["ms"] > 0 for c in cands)
     assert best["ms"] == min(c["ms"] for c in cands)
-    assert now == (1 if best["schedule"] == "persistent" else 0, best["patience_cycles"])
-    for k in ref:
-        assert torch.equal(ref[k], got[k]), k
+    for c in cands:
+        got = B.query_rays(desc, b.table, b.mlp, b.nodes, b.leaves["n_nodes"], rays, 24,
+                           options=B.options_from_dict(c))
+        for k in ref:
+            assert torch.equal(ref[k], got[k]), (c, k)
+    assert B.device_status() == 0
 
 
 def _surface_rays(tris, n, seed):

@@ -121,7 +121,7 @@ def test_forward_loss_and_gradients_fp32():
     dv, h = _batch(b)
     n = len(h["leaf"])
     ws = B.new_workspace(B.train_workspace_size(b.desc, n))
-    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
     raw = B.forward_train(b.desc, b.table, b.mlp, dv["rays"], dv["leaf"], dv["t0"], dv["t1"], ws,
                           labels=dv["lab"], n_valid=dv["n_valid"], loss_out=loss)
     g_tab = torch.zeros((b.layout["total"], b.case.model.n_features), dtype=torch.float32, device="cuda")
@@ -179,7 +179,8 @@ def test_fd_gradient_check_fp64_reduction():
 
     def L_of(table, mlp):
         B.forward_train(b.desc, table, mlp, dv["rays"], dv["leaf"], dv["t0"], dv["t1"], ws, labels=dv["lab"],
-                        n_valid=dv["n_valid"], loss_out=loss)
+                        n_valid=dv["n_valid"])
+        B.loss_fp64(b.desc, n, dv["n_valid"], ws, loss)  # the check's FP64 reduction
         return float(loss.item())
 
     L_of(b.table, b.mlp)
@@ -288,7 +289,7 @@ def test_training_gains_over_untrained_and_box_proxy():
         return np.mean(hit == gt_hit), (np.median(np.abs(t[both] - gt[both])) if both.any() else np.inf)
 
     untrained = evaluate(b.table, b.mlp)
-    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
     for step in range(1, 401):
         B.train_step(desc, opt, scene, B.TRAIN_PROBED_MIX, batch, 1234, step, 1e-2, ws, loss_out=loss)
     assert B.device_status() == 0
@@ -322,7 +323,7 @@ def test_tensor_core_gradients_match_oracle(mp):
     dv, h = _batch(b, n=2000, seed=81)
     n = len(h["leaf"])
     ws = B.new_workspace(B.train_workspace_size(desc, n))
-    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
     scale = 1024.0
     raw = B.forward_train(desc, b.table, b.mlp, dv["rays"], dv["leaf"], dv["t0"], dv["t1"], ws,
                           labels=dv["lab"], n_valid=dv["n_valid"], loss_scale=scale, loss_out=loss)
@@ -424,7 +425,7 @@ def test_tensor_core_training_learns():
         return np.mean(hh["hit"].cpu().numpy().astype(bool) == gt_hit)
 
     before = agreement()
-    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
     for step in range(1, 401):
         B.train_step(desc, opt, scene, B.TRAIN_PROBED_MIX, batch, 99, step, 1e-2, ws, loss_out=loss)
     assert B.device_status() == 0

@@ -184,19 +184,119 @@ def test_tri_blas_single_leaf_and_bad_arguments():
         B.build_tri_blas(bad, 4)
 
 
-def test_schedule_and_tuner_arguments_checked_on_host():
-    """Invalid schedule settings and autotuner arguments are rejected before
-    any device work (no GPU needed)."""
+def test_query_options_checked_on_host():
+    """nbvh_query_options_default gives the documented defaults; invalid
+    options and autotuner arguments are rejected before any device work (no
+    GPU needed: zero rays return before the first CUDA call)."""
     L = B.lib()
-    assert L.nbvh_set_query_schedule(7, 0) == 1
-    assert L.nbvh_set_query_schedule(1, -5) == 1
-    assert L.nbvh_set_traverse_block(100) == 1
+    o = B.query_options()
+    assert (o.schedule, o.patience_cycles, o.traverse_block, o.eval_threads, o.w1_mode) == (1, 4000, 128, 0, 0)
+    desc = _desc(W.C1.model, B.FP16, B.FP16)
+    fake = ctypes.c_void_p(1 << 20)
+    rays = B.Rays()
+    rays.n = 0
+    hits = B.Hits()
+    for bad in (dict(schedule=7), dict(patience_cycles=-5), dict(traverse_block=100), dict(eval_threads=384),
+                dict(w1_mode=3)):
+        assert L.nbvh_query_rays_opt(ctypes.byref(desc), fake, fake, fake, 1, rays, 8, hits, fake, 1 << 30,
+                                     ctypes.byref(B.query_options(**bad)), None) == 1, bad
+    assert L.nbvh_query_rays_opt(ctypes.byref(desc), fake, fake, fake, 1, rays, 8, hits, fake, 1 << 30,
+                                 ctypes.byref(B.query_options()), None) == 0
     best = B.TuneResult()
     n_all = ctypes.c_int32()
     assert L.nbvh_autotune_query(None, None, None, None, 0, B.Rays(), 8, B.Hits(), None, 0, 1, ctypes.byref(best),
                                  None, 0, ctypes.byref(n_all), None) == 1
-    s, p = B.get_query_schedule()
-    assert s in (0, 1) and p >= 0
+
+
+def test_unsupported_query_enqueues_nothing():
+    """A valid descriptor with options the kernels cannot run (256-thread
+    evaluation CTAs at width 128) returns NBVH_ERR_UNSUPPORTED from the host
+    check, before any launch: the library's launch count does not move and no
+    CUDA call is made (this runs without a GPU)."""
+    L = B.lib()
+    from dataclasses import replace
+    desc = _desc(replace(W.C1.model, width=128), B.FP16, B.FP16)
+    fake = ctypes.c_void_p(1 << 20)
+    rays = B.Rays()
+    for k in ("ox", "oy", "oz", "dx", "dy", "dz", "tmin", "tmax"):
+        setattr(rays, k, 1 << 20)
+    rays.n = 1000
+    hits = B.Hits()
+    for k in B.HIT_KEYS:
+        setattr(hits, k, 1 << 20)
+    n0 = B.launch_count()
+    st = L.nbvh_query_rays_opt(ctypes.byref(desc), fake, fake, fake, 1, rays, 8, hits, ctypes.c_void_p(1 << 20),
+                               1 << 40, ctypes.byref(B.query_options(eval_threads=256)), None)
+    assert st == 7 and B.launch_count() == n0
+
+
+def test_rank_leaves_matches_oracle():
+    """nbvh_rank_leaves (Sec. 5.1 node error, Sec. 5.2 training probability)
+    against the oracle's node_rank on random statistics with unhit and
+    untrained leaves."""
+    rng = np.random.default_rng(17)
+    n = 300
+    hits = rng.integers(0, 500, n).astype(np.uint32)
+    hits[rng.choice(n, 30, replace=False)] = 0
+    trained = np.minimum(hits, rng.integers(0, 400, n)).astype(np.uint32)
+    trained[rng.choice(n, 20, replace=False)] = 0
+    loss = (trained * rng.uniform(0.01, 2.0, n)).astype(np.float32)
+    n_rays = int(hits.sum()) + 1000
+    q, p, r, prob = B.node_rank(hits, trained, loss, n_rays)
+    oq, op, orr, oprob = O.node_rank(hits.astype(np.int64), trained.astype(np.int64), loss.astype(np.float64), n_rays)
+    assert np.allclose(q, oq, rtol=1e-14, atol=0) and np.allclose(p, op, rtol=1e-15, atol=0)
+    fin = np.isfinite(orr)
+    assert np.array_equal(np.isfinite(r), fin) and np.allclose(r[fin], orr[fin], rtol=1e-13, atol=1e-13)
+    assert np.array_equal(prob, oprob.astype(np.float32))
+    assert (prob[~fin] == np.float32(0.005)).all() and prob.max() == 1.0
+
+
+def test_refine_cut_matches_oracle_split():
+    """nbvh_refine_cut against the oracle's split_cut on a real SAH base BVH:
+    the k best-ranked splittable leaves become their children (ties to the
+    lower index), new leaves train with probability 1, others keep theirs."""
+    tris = np.concatenate([W.ground_heightfield(10, amplitude=0.05), W.scene_icosphere(level=2, radius=0.3)])
+    base = _base(tris)
+    nodes = B.node_array({"nodes": base["nodes"]})
+
+    def children(ref):
+        if ref < 0:
+            return []
+        nd = nodes[ref]
+        return [int(nd["child0"])] + ([int(nd["child1"])] if int(nd["child1"]) != 0x7fffffff else [])
+
+    rng = np.random.default_rng(5)
+    cut = [0]
+    for _ in range(6):
+        r = rng.normal(size=len(cut))
+        r[rng.uniform(size=len(cut)) < 0.2] = -np.inf
+        r[rng.integers(0, len(cut))] = r.max() if np.isfinite(r).any() else 0.0  # a tie
+        prob = rng.uniform(0.005, 1.0, len(cut)).astype(np.float32)
+        k = int(rng.integers(1, 4))
+        new_cut, new_prob = B.refine_cut(base, cut, r, prob, k)
+        assert new_cut == O.split_cut(cut, r, k, children)
+        kept = {c: float(p) for c, p in zip(cut, prob)}
+        for c, p in zip(new_cut, new_prob):
+            assert p == (kept[c] if c in kept else 1.0)
+        cut = new_cut
+
+
+def test_train_workspace_budget_picks_recompute_below_the_stored_size():
+    """nbvh_train_workspace_budget: the stored size when it fits (chunk = n),
+    else the largest 128-ray multiple whose activation chunk fits (recompute
+    mode, smaller than stored), else NBVH_ERR_WORKSPACE_TOO_SMALL."""
+    for mp in (B.FP32, B.FP16):
+        desc = _desc(W.C1.model, B.FP16, mp)
+        n = 1 << 18
+        stored = B.train_workspace_size(desc, n, 2048)
+        b, c = B.train_workspace_budget(desc, n, 2048, stored)
+        assert (b, c) == (stored, n)
+        b2, c2 = B.train_workspace_budget(desc, n, 2048, stored // 3)
+        assert c2 < n and c2 % 128 == 0 and b2 <= stored // 3
+        b3, c3 = B.train_workspace_budget(desc, n, 2048, b2 + 1)
+        assert c3 == c2  # the largest chunk that fits
+        with pytest.raises(B.NBVHError):
+            B.train_workspace_budget(desc, n, 2048, 1 << 20)
 
 
 def _base(tris, max_leaf=8):

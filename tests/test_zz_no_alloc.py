@@ -18,15 +18,12 @@ pytestmark = pytest.mark.gpu
 
 
 def _compare(got, ref):
-    for k in ("hit", "leaf"):
-        assert np.array_equal(got[k].cpu().numpy(), ref[k].cpu().numpy()), k
-    hit = ref["hit"].cpu().numpy().astype(bool)
-    for k in ("t", "nx", "ny", "nz"):
-        g = got[k].cpu().numpy()[hit]
-        r = ref[k].cpu().numpy()[hit]
-        # the same kernels on the same inputs: within the FP32 path's 1e-5
-        assert np.all(np.abs(g - r) <= 1e-5 * np.maximum(1.0, np.abs(r))), k
-    assert np.all(np.isinf(got["t"].cpu().numpy()[~hit]))
+    # the same kernels on the same inputs (a row's result does not depend on
+    # where it is evaluated), so any difference would be state left in the
+    # shared scratch: bit-for-bit equality
+    import torch
+    for k in ref:
+        assert torch.equal(got[k], ref[k]), k
 
 
 @pytest.mark.parametrize("mlp_prec", [B.FP32, B.FP16])
@@ -39,10 +36,17 @@ def test_static_scratch_query_matches_workspace_query(mlp_prec):
     ref = B.query_rays(desc, b.table, b.mlp, b.nodes, b.leaves["n_nodes"], b.rays, max_segs)
     assert B.device_status() == 0
     assert ref["hit"].cpu().numpy().sum() > 0
-    for _ in range(2):
-        got = B.query_rays_static(desc, b.table, b.mlp, b.nodes, b.leaves["n_nodes"], b.rays, max_segs)
-        assert B.device_status() == 0
-        _compare(got, ref)
+    outs = [B.new_hits(b.rays["ox"].numel()) for _ in range(2)]  # allocated before the calls
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for out in outs:
+        B.query_rays_static(desc, b.table, b.mlp, b.nodes, b.leaves["n_nodes"], b.rays, max_segs, out=out)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0  # the calls allocated no device memory
+    assert B.device_status() == 0
+    for out in outs:
+        _compare(out, ref)
 
 
 def test_static_scratch_rejects_oversized_requests():
