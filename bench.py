@@ -60,6 +60,8 @@ def parse():
     p.add_argument("--no-albedo", action="store_true", help="skip the albedo-head measurement")
     p.add_argument("--no-autotune", action="store_true",
                    help="keep the library's default query schedule (no autotuning before the timed region)")
+    p.add_argument("--primary", default="1920x1080",
+                   help="primary image of the icosphere workload (smaller only for profiling captures)")
     p.add_argument("--quick", action="store_true",
                    help="time the FP16 tensor-core form only (no other forms, no e2e, no CPU baseline)")
     return p.parse_args()
@@ -113,10 +115,11 @@ def barrier(world: int):
 
 
 # ---------------------------------------------------------------------------- workload
-def make_scene():
+def make_scene(primary="1920x1080"):
     from paper_2405_16237_b300 import workloads as W
     tris = W.scene_icosphere(level=8)
-    return W.C1, tris, W.camera_rays(1920, 1080)
+    w, h = (int(x) for x in primary.split("x"))
+    return W.C1, tris, W.camera_rays(w, h)
 
 
 class GpuWorkload:
@@ -903,7 +906,7 @@ def time_hybrid(args, world):
 def main():
     args = parse()
     world, rank, local = dist_init(args.gpus)
-    spec, tris, rays_np = make_scene()
+    spec, tris, rays_np = make_scene(args.primary)
 
     if args.impl == "reference":
         if rank != 0:

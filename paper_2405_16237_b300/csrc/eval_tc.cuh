@@ -170,23 +170,25 @@ struct OpType<true> {
 };
 
 // ---------------------------------------------------------------- tile geometry
-// The first layer runs over the features in K chunks of kKC = 128 (64 TMEM
-// columns). A sample's L*F features are padded to a multiple of 8 (one
-// "item": 8 features = 4 TMEM columns, one tcgen05.st); the padded input has
+// A sample's L*F features are padded to a multiple of 8 (one "item": 8
+// features = 4 TMEM columns, one tcgen05.st); the padded input has
 // KP = N * LFp features rounded up to 16 (one MMA K step) and the first
-// layer's weights carry zero rows for the padding. While the tensor cores
-// multiply chunk r, the gather fills chunk r + 1 into the other of two TMEM
-// buffers, so the feature footprint is 128 columns whatever K is.
-constexpr int kKC = 128;
+// layer's weights carry zero rows for the padding. When the whole padded
+// input fits the CTA's TMEM next to the accumulator and the hidden
+// activations, the first layer runs as one round (one barrier per tile).
+// Otherwise it runs over K chunks of KC features through two TMEM buffers:
+// while the tensor cores multiply chunk r, the gather fills chunk r + 1 into
+// the other buffer, so the feature footprint is bounded whatever K is.
 constexpr int kItemF = 8;
-constexpr int kChunkItems = kKC / kItemF;
 
 // TMEM column plan (one 32-bit column holds two 16-bit operand elements):
-//   [0, W)             FP32 accumulator D of the current layer (the output
-//                      layer uses its first 16 columns)
-//   [W, W + W/2)       hidden activations H, the next layer's A operand
-//   [2W, 2W + 128)     two 64-column feature chunk buffers, the first layer's
-//                      A operand
+//   [0, W)                  FP32 accumulator D of the current layer (the
+//                           output layer uses its first 16 columns)
+//   [W, W + W/2)            hidden activations H, the next layer's A operand
+//   [2W, 2W + NB * KC/2)    NB feature buffers of KC features, the first
+//                           layer's A operand
+// A CTA of 256 threads keeps to 256 columns (two CTAs share an SM), one of
+// 512 threads may use all 512.
 // Shared memory: the first layer's weights as chunk-sized B operands (all R
 // chunks resident, or two buffers that bulk copies refill from a prepared
 // 16-bit image in global memory), the hidden and output weights, two row
@@ -196,9 +198,11 @@ struct TcLayout {
   int IPS;                   // items per sample (LFp / 8)
   int NI;                    // items per row (N * IPS)
   int KP;                    // padded input width (N * LFp rounded up to 16)
-  int R;                     // K chunks
+  int KC;                    // features per chunk (a multiple of 64)
+  int NB;                    // TMEM feature buffers (1: one round; 2: double buffered)
+  int R;                     // chunks (rounds per tile)
   uint32_t col_h, col_a, ncols;
-  uint32_t chunk_bytes;      // one W x 128 chunk of the first layer's weights
+  uint32_t chunk_bytes;      // one W x KC chunk of the first layer's weights
   uint32_t w1_off;           // resident: R chunks; streamed: 2 chunk buffers
   uint32_t wh_off;           // (n_hidden - 1) x W x W
   uint32_t wo_off;           // 16 x W
@@ -209,20 +213,31 @@ struct TcLayout {
 
 constexpr uint32_t kRowBytes = 12 * 4;  // per row: ray, t0, t1, slot, best t, next t0, origin, direction
 
-__host__ __device__ inline TcLayout tc_layout(int L, int F, int N, int W, int n_hidden, bool stream) {
+__host__ __device__ inline TcLayout tc_layout(int L, int F, int N, int W, int n_hidden, bool stream, int threads) {
   TcLayout T;
   T.LFp = (L * F + kItemF - 1) / kItemF * kItemF;
   T.IPS = T.LFp / kItemF;
   T.NI = N * T.IPS;
   T.KP = (N * T.LFp + 15) & ~15;
-  T.R = (T.KP + kKC - 1) / kKC;
   T.col_h = uint32_t(W);
   T.col_a = uint32_t(2 * W);
-  const uint32_t used = T.col_a + uint32_t(kKC);
+  const int budget = threads == 256 ? 256 : 512;
+  const int avail = budget - 2 * W;         // columns for the feature buffers
+  const int kp64 = (T.KP + 63) & ~63;
+  if (kp64 / 2 <= avail) {
+    T.NB = 1;
+    T.KC = kp64;
+  } else {
+    T.NB = 2;
+    T.KC = 2 * (avail / 2 / 32 * 32);
+    if (T.KC < 64) T.KC = 64;  // no valid plan has so few columns (tc_plan rejects it)
+  }
+  T.R = (T.KP + T.KC - 1) / T.KC;
+  const uint32_t used = T.col_a + uint32_t(T.NB * T.KC / 2);
   uint32_t nc = 32;
   while (nc < used) nc <<= 1;
   T.ncols = nc;
-  T.chunk_bytes = uint32_t(W) * kKC * 2;
+  T.chunk_bytes = uint32_t(W) * uint32_t(T.KC) * 2;
   uint32_t off = 0;
   auto take = [&](uint32_t bytes) {
     const uint32_t o = off;
@@ -245,12 +260,12 @@ __host__ __device__ inline int padded_feature(int c, int L, int F, int N, int LF
 }
 
 // Element (row n, padded column c) of the first layer's weights in the chunked
-// B-operand layout: chunk c / 128, then the K-major core-matrix layout of a
-// W x 128 operand.
-__host__ __device__ inline uint32_t w1_chunk_offset(int n, int c, uint32_t chunk_bytes) {
-  const int r = c / kKC, cc = c - r * kKC;
-  return uint32_t(r) * chunk_bytes +
-         uint32_t((n >> 3) * (kKC * 16) + (cc >> 3) * 128 + (n & 7) * 16 + (cc & 7) * 2);
+// B-operand layout: chunk c / KC, then the K-major core-matrix layout of a
+// W x KC operand.
+__host__ __device__ inline uint32_t w1_chunk_offset(int n, int c, const TcLayout& T) {
+  const int r = c / T.KC, cc = c - r * T.KC;
+  return uint32_t(r) * T.chunk_bytes +
+         uint32_t((n >> 3) * (T.KC * 16) + (cc >> 3) * 128 + (n & 7) * 16 + (cc & 7) * 2);
 }
 
 // D[tmem] (+)= A[tmem] * B[smem]^T (A from tensor memory, kind::f16).
@@ -635,11 +650,11 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 template <bool BF16>
 __device__ __forceinline__ void put_w1(uint8_t* dst, const float* __restrict__ W1, int i, int W, int K, int L, int F,
                                        int N, const TcLayout& T) {
-  const int cols = T.R * kKC;
+  const int cols = T.R * T.KC;
   const int n = i / cols, c = i - n * cols;
   const int f = padded_feature(c, L, F, N, T.LFp);
   const float v = f >= 0 ? __ldg(W1 + size_t(n) * K + f) : 0.0f;
-  *reinterpret_cast<typename OpType<BF16>::T*>(dst + w1_chunk_offset(n, c, T.chunk_bytes)) = OpType<BF16>::one(v);
+  *reinterpret_cast<typename OpType<BF16>::T*>(dst + w1_chunk_offset(n, c, T)) = OpType<BF16>::one(v);
 }
 
 // Streamed first-layer weights: the 16-bit chunked image the kernel's bulk
@@ -647,7 +662,7 @@ __device__ __forceinline__ void put_w1(uint8_t* dst, const float* __restrict__ W
 template <bool BF16>
 __global__ void __launch_bounds__(256) w1_image_kernel(const float* __restrict__ W1, int W, int K, int L, int F, int N,
                                                        TcLayout T, uint8_t* __restrict__ img) {
-  const int total = W * T.R * kKC;
+  const int total = W * T.R * T.KC;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x)
     put_w1<BF16>(img, W1, i, W, K, L, F, N, T);
 }
@@ -726,7 +741,6 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) eval_tc_kernel(EvalArgs
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   constexpr int kGroups = NT / 128;
-  constexpr int IPG = kChunkItems / kGroups;  // items per warp group and chunk
   constexpr int LPC = 8 / F;                  // levels per item
   constexpr int kCols = W / kGroups;          // accumulator columns per thread in hidden epilogues
   static_assert(kCols % 8 == 0 || kCols == 4 || kCols == 8, "epilogue column split");
@@ -735,7 +749,9 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) eval_tc_kernel(EvalArgs
   const int N = a.gp.n_samples;
   const int n_out = a.n_out;
   const bool stream = a.w1_image != nullptr;
-  const TcLayout lay = tc_layout(L, F, N, W, a.n_hidden, stream);
+  const TcLayout lay = tc_layout(L, F, N, W, a.n_hidden, stream, NT);
+  const int CI = lay.KC / kItemF;   // items per chunk
+  const int IPG = CI / kGroups;     // items per warp group and chunk
   uint8_t* sW1 = smem + lay.w1_off;
   uint8_t* sWh = smem + lay.wh_off;
   uint8_t* sWo = smem + lay.wo_off;
@@ -774,7 +790,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) eval_tc_kernel(EvalArgs
   const float* W1 = a.mlp;
   const float* b1 = W1 + size_t(W) * K;
   if (!stream)
-    for (int i = threadIdx.x; i < W * lay.R * kKC; i += NT) put_w1<BF16>(sW1, W1, i, W, K, L, F, N, lay);
+    for (int i = threadIdx.x; i < W * lay.R * lay.KC; i += NT) put_w1<BF16>(sW1, W1, i, W, K, L, F, N, lay);
   const float* p = b1 + W;
   for (int h = 1; h < a.n_hidden; ++h) {
     stage_weights<BF16>(sWh + size_t(h - 1) * W * W * 2, p, W, W, W, W);
@@ -877,26 +893,28 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) eval_tc_kernel(EvalArgs
       }
     };
 
-    // ---- layer 1 over K chunks: gather chunk r into buffer g & 1 while the
+    // ---- layer 1 over K chunks: gather chunk r into buffer g % NB while the
     // tensor cores multiply chunk r - 1
     for (int r = 0; r < lay.R; ++r, ++g) {
-      const int b = int(g & 1u);
-      if (g >= 2) {  // buffer b was read by the MMAs of round g - 2
-        const bool ok = mbar_wait(mma_done + b, ((g - 2) >> 1) & 1u);
-        if (__syncthreads_or(!ok || s_fail)) {
-          failed = true;
-          break;
-        }
+      const int b = lay.NB == 1 ? 0 : int(g & 1u);  // TMEM feature buffer
+      const int wbuf = int(g & 1u);                 // streamed weight buffer
+      if (g >= uint32_t(lay.NB)) {
+        // this round's buffers were read by the MMAs of round g - NB (their
+        // completion implies every earlier round's): each thread waits for it
+        // itself, a failed wait shows at the next barrier
+        const uint32_t gw = g - uint32_t(lay.NB);
+        if (!mbar_wait(mma_done + (gw & 1u), (gw >> 1) & 1u)) s_fail = 1;
         tc_fence_after();
       }
       if (stream && threadIdx.x == 0 && !s_fail) {  // after a failed wait no further copy is issued
-        mbar_expect_tx(w_full + b, lay.chunk_bytes);
-        bulk_g2s(sW1 + size_t(b) * lay.chunk_bytes,
-                 static_cast<const uint8_t*>(a.w1_image) + size_t(r) * lay.chunk_bytes, lay.chunk_bytes, w_full + b);
-        tma_pending[b] = g;
+        mbar_expect_tx(w_full + wbuf, lay.chunk_bytes);
+        bulk_g2s(sW1 + size_t(wbuf) * lay.chunk_bytes,
+                 static_cast<const uint8_t*>(a.w1_image) + size_t(r) * lay.chunk_bytes, lay.chunk_bytes,
+                 w_full + wbuf);
+        tma_pending[wbuf] = g;
       }
-      const uint32_t t_buf = t_row + lay.col_a + uint32_t(b * (kKC / 2));
-      const int it_begin = r * kChunkItems + cgroup * IPG;  // this warp group's first item
+      const uint32_t t_buf = t_row + lay.col_a + uint32_t(b * (lay.KC / 2));
+      const int it_begin = r * CI + cgroup * IPG;  // this warp group's first item
       const int c_begin = cgroup * IPG * 4;                   // its first column in the buffer
       if constexpr (kSplitX) {
         // Lanes i and i ^ 16 share cells: lane i loads the four corners with
@@ -907,7 +925,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) eval_tc_kernel(EvalArgs
         const int r0 = quarter * 32 + (lane & 15), r1 = r0 + 16;
         const bool v0 = rb.ray[r0] >= 0, v1 = rb.ray[r1] >= 0;
         float p0[3] = {0.0f, 0.0f, 0.0f}, p1[3] = {0.0f, 0.0f, 0.0f};
-        if (L == 16 && lay.IPS == 4 && IPG % 4 == 0) {
+        if (L == 16 && lay.IPS == 4 && IPG % 4 == 0 && it_begin % 4 == 0) {
           // whole samples per warp group, the 16 levels unrolled
 #pragma unroll 1
           for (int s = 0; s < IPG / 4; ++s) {
@@ -990,19 +1008,19 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) eval_tc_kernel(EvalArgs
         tc_fence_after();
         bool ok = !s_fail;
         if (stream && ok) {
-          ok = mbar_wait(w_full + b, (g >> 1) & 1u);
-          if (ok) tma_pending[b] = ~0u;
+          ok = mbar_wait(w_full + wbuf, (g >> 1) & 1u);
+          if (ok) tma_pending[wbuf] = ~0u;
         }
         if (ok) {
-          const int steps = min(kKC, lay.KP - r * kKC) / 16;
-          const uint32_t wb = smem_u32(sW1 + size_t(stream ? b : r) * lay.chunk_bytes);
+          const int steps = min(lay.KC, lay.KP - r * lay.KC) / 16;
+          const uint32_t wb = smem_u32(sW1 + size_t(stream ? wbuf : r) * lay.chunk_bytes);
           for (int j = 0; j < steps; ++j)
-            mma_f16_ts(tmem, tmem + lay.col_a + uint32_t(b * (kKC / 2) + 8 * j),
-                       smem_desc(wb + j * 256, 128, kKC * 16), idesc_h, (r > 0 || j > 0) ? 1u : 0u);
+            mma_f16_ts(tmem, tmem + lay.col_a + uint32_t(b * (lay.KC / 2) + 8 * j),
+                       smem_desc(wb + j * 256, 128, uint32_t(lay.KC) * 16), idesc_h, (r > 0 || j > 0) ? 1u : 0u);
         } else {
           s_fail = 1;
         }
-        mma_commit(mma_done + b);  // also when nothing was issued: keeps the phases in step
+        mma_commit(mma_done + (g & 1u));  // also when nothing was issued: keeps the phases in step
       }
     }
     if (failed) break;
@@ -1198,11 +1216,11 @@ inline TcPlan tc_plan(const nbvh_model_desc* d, int threads_opt, int w1_mode) {
   std::memset(&p, 0, sizeof(p));
   const int W = d->width;
   if (W < 32 || W > 128 || d->n_out > 16) return p;
-  const TcLayout res = tc_layout(d->n_levels, d->n_features, d->n_samples, W, d->n_hidden, false);
-  const TcLayout str = tc_layout(d->n_levels, d->n_features, d->n_samples, W, d->n_hidden, true);
-  p.threads = threads_opt != 0 ? threads_opt : (W <= 64 ? 256 : 512);
+  p.threads = threads_opt != 0 ? threads_opt : 512;
   if (p.threads != 256 && p.threads != 512) return p;
   if (p.threads == 256 && W > 64) return p;
+  const TcLayout res = tc_layout(d->n_levels, d->n_features, d->n_samples, W, d->n_hidden, false, p.threads);
+  const TcLayout str = tc_layout(d->n_levels, d->n_features, d->n_samples, W, d->n_hidden, true, p.threads);
   const uint32_t budget = p.threads == 256 ? kSmemHalf : kSmemMax;
   if (w1_mode == NBVH_W1_RESIDENT) p.stream = false;
   else if (w1_mode == NBVH_W1_STREAMED) p.stream = true;
@@ -1211,14 +1229,20 @@ inline TcPlan tc_plan(const nbvh_model_desc* d, int threads_opt, int w1_mode) {
   p.smem = T.total;
   p.ncols = T.ncols;
   p.image_bytes = size_t(T.R) * T.chunk_bytes;
-  p.ok = T.total <= kSmemMax && T.ncols <= 512;
+  p.ok = T.total <= kSmemMax && T.ncols <= uint32_t(p.threads == 256 ? 256 : 512);
   return p;
 }
 
-// Bytes of the streamed first-layer image of any plan of this model.
+// Bytes of the streamed first-layer image of any plan of this model (the
+// chunking depends on the CTA size).
 inline size_t tc_image_bytes(const nbvh_model_desc* d) {
-  const TcLayout T = tc_layout(d->n_levels, d->n_features, d->n_samples, d->width, d->n_hidden, true);
-  return size_t(T.R) * T.chunk_bytes;
+  size_t m = 0;
+  for (int th : {256, 512}) {
+    if (th == 256 && d->width > 64) continue;
+    const TcLayout T = tc_layout(d->n_levels, d->n_features, d->n_samples, d->width, d->n_hidden, true, th);
+    m = std::max(m, size_t(T.R) * T.chunk_bytes);
+  }
+  return m;
 }
 
 template <typename T, int F, int W, int MODE, int NT>
@@ -1279,10 +1303,11 @@ cudaError_t launch_tc_tm(const nbvh_model_desc* d, const EvalArgs& a, int64_t n,
 }
 
 // The prepared image of the first layer's weights (plan with stream set).
-inline cudaError_t launch_w1_image(const nbvh_model_desc* d, const float* mlp, void* img, cudaStream_t s) {
-  const TcLayout T = tc_layout(d->n_levels, d->n_features, d->n_samples, d->width, d->n_hidden, true);
+inline cudaError_t launch_w1_image(const nbvh_model_desc* d, const float* mlp, int threads, void* img,
+                                   cudaStream_t s) {
+  const TcLayout T = tc_layout(d->n_levels, d->n_features, d->n_samples, d->width, d->n_hidden, true, threads);
   const int K = d->n_samples * d->n_levels * d->n_features;
-  const int total = d->width * T.R * kKC;
+  const int total = d->width * T.R * T.KC;
   const unsigned grid = unsigned(std::min(1024, (total + 255) / 256));
   if (d->mlp_prec == NBVH_BF16)
     w1_image_kernel<true><<<grid, 256, 0, s>>>(mlp, d->width, K, d->n_levels, d->n_features, d->n_samples, T,

@@ -177,7 +177,7 @@ cudaError_t prepare_eval(const nbvh_model_desc* d, EvalArgs& a, const nbvh_query
   if (!plan->ok) return cudaErrorInvalidConfiguration;
   if (plan->stream) {
     if (!image) return cudaErrorInvalidConfiguration;
-    cudaError_t e = launch_w1_image(d, a.mlp, image, s);
+    cudaError_t e = launch_w1_image(d, a.mlp, plan->threads, image, s);
     if (e != cudaSuccess) return e;
     a.w1_image = image;
   }
