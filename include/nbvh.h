@@ -215,7 +215,16 @@ nbvh_status nbvh_encode(const nbvh_model_desc* desc, const void* table, nbvh_ray
  *                   16-bit image in the workspace and streamed through two
  *                   shared-memory buffers, 128 inputs at a time, by bulk
  *                   copies; NBVH_W1_AUTO: resident when it fits the CTA's
- *                   shared-memory budget, else streamed. */
+ *                   shared-memory budget, else streamed.
+ *  wait_spins       persistent schedule: polling rounds (each with a short
+ *                   sleep) before a queue wait gives up and records
+ *                   NBVH_ERR_TIMEOUT; 0 = the default (about a second).
+ *  test_phantom_items  test hook, 0 otherwise: the persistent queue announces
+ *                   this many extra items (0 .. 1024) that nothing ever
+ *                   writes, so the waits for them run out; the query then
+ *                   returns with NBVH_ERR_TIMEOUT in the device status (it
+ *                   never traps or spins unbounded) and the records of the
+ *                   rays are not defined. */
 #define NBVH_SCHEDULE_WAVES 0
 #define NBVH_SCHEDULE_PERSISTENT 1
 #define NBVH_W1_AUTO 0
@@ -227,6 +236,8 @@ typedef struct {
   int32_t traverse_block;
   int32_t eval_threads;
   int32_t w1_mode;
+  int64_t wait_spins;
+  int32_t test_phantom_items;
 } nbvh_query_options;
 
 /* Host. The defaults: persistent schedule, patience 4000 cycles, traversal

@@ -310,6 +310,39 @@ def normalize_points(p, centre, extent):
     return np.clip(x, 0.0, 1.0)
 
 
+def _fma32(a, b, c):
+    """float32 fused multiply-add: the product of two float32 values is exact
+    in float64, so one rounding of the float64 sum to float32 is the fused
+    result (up to a double rounding of probability ~2^-29)."""
+    return (np.asarray(a, np.float32).astype(F64) * np.asarray(b, np.float32).astype(F64)
+            + np.asarray(c, np.float32).astype(F64)).astype(np.float32)
+
+
+def sample_grid_f32(o, d, t0, t1, n_samples: int, centre, extent):
+    """Grid coordinates of the stratified samples as the reduced-precision
+    (FP16/BF16 tensor-core) form computes them: float32 throughout, one
+    rounding per fused step. u_k = (k + 1/2)/N, t_k = fma(u_k, t1 - t0, t0),
+    xhat = clamp(fma(fma(t_k, d, o) - c, 1/E, 1/2), 0, 1), 1/E rounded to
+    float32. (Reading: the paper runs its model in half precision, Sec. 6; a
+    half-precision oracle that models those operands also takes the form's
+    float32 positions, since at the finest levels, resolution ~7,000, a float32
+    position error is of the order of a 16-bit feature's rounding.) Shapes as
+    sample_points; returns float64 arrays of float32 values."""
+    f32 = np.float32
+    o = np.asarray(o, f32)
+    d = np.asarray(d, f32)
+    t0 = np.asarray(t0, f32)
+    t1 = np.asarray(t1, f32)
+    u = (np.arange(n_samples, dtype=f32) + f32(0.5)) / f32(n_samples)
+    dt = (t1 - t0).astype(f32)
+    t = _fma32(u[None, :], dt[:, None], t0[:, None])
+    p = _fma32(t[..., None], d[:, None, :], o[:, None, :])
+    q = (p - np.asarray(centre, f32)).astype(f32)
+    inv = f32(1.0) / f32(extent)
+    x = _fma32(q, inv, f32(0.5))
+    return np.clip(x, f32(0.0), f32(1.0)).astype(F64)
+
+
 # ============================================================================
 # S3: multi-resolution hash-grid encoding (Sec. 3, Sec. 4, Fig. 3)
 # ============================================================================
@@ -813,13 +846,19 @@ def encode_backward(x, g_feat, n_entries: int, n_features: int, layout):
 
 
 def forward_backward(o, d, t0, t1, valid, y_hit, y_depth, y_normal, table, layers, layout,
-                     centre, extent, n_samples: int, rnd=None, scale: float = 1.0, y_albedo=None):
+                     centre, extent, n_samples: int, rnd=None, scale: float = 1.0, y_albedo=None,
+                     positions: str = "f64"):
     """Loss of a batch of segments and its exact gradient with respect to every
     table entry and MLP weight/bias. Returns (L, dtable, [(dW, db)], raw).
     ``rnd``/``scale``: half-precision MLP operands (``mlp_forward``,
-    ``mlp_backward``); the encoding and the table gradient stay exact."""
-    p = sample_points(o, d, t0, t1, n_samples)
-    x = normalize_points(p, centre, extent)
+    ``mlp_backward``); the encoding and the table gradient stay exact.
+    ``positions``: "f64" (exact sample points) or "f32" (sample_grid_f32, the
+    reduced-precision form's float32 positions)."""
+    if positions == "f32":
+        x = sample_grid_f32(o, d, t0, t1, n_samples, centre, extent)
+    else:
+        p = sample_points(o, d, t0, t1, n_samples)
+        x = normalize_points(p, centre, extent)
     feat = encode(x, table, layout)
     raw, acts, pre = mlp_forward(feat, layers, rnd)
     L, _ = loss(raw, y_hit, y_depth, y_normal, valid, y_albedo)

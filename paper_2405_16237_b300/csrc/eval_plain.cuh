@@ -90,6 +90,7 @@ struct PQueue {
   unsigned long long* retired;   // items resolved
   unsigned int* tiles;           // tiles claimed (statistics)
   long long patience;            // cycles a CTA waits for a full tile before taking a partial one
+  long long spin_limit;          // polling rounds before a queue wait gives up (NBVH_ERR_TIMEOUT)
   unsigned long long* ring;      // [n_rays] items; nullptr: one launch per segment slot instead
 };
 

@@ -331,7 +331,7 @@ __device__ __forceinline__ uint32_t pack2(float a, float b) {
 }
 
 // ---------------------------------------------------------------- persistent query queue
-constexpr long long kPqSpinLimit = 1LL << 22;      // bounded waits (~1 s with the back-off below)
+constexpr long long kPqSpinLimit = 1LL << 22;      // default bound of the queue waits (~1 s with the back-off below)
 constexpr unsigned long long kPqEmpty = ~0ull;     // an empty ring entry
 
 __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
@@ -372,7 +372,7 @@ __device__ __forceinline__ void red_release_add_u64(unsigned long long* p, unsig
 // be queued.
 __device__ __forceinline__ int pq_claim(const PQueue& q, unsigned long long* start) {
   const long long t0 = clock64();
-  for (long long spin = 0; spin < kPqSpinLimit; ++spin) {
+  for (long long spin = 0; spin < q.spin_limit; ++spin) {
     const unsigned long long retired = ld_relaxed_u64(q.retired);
     const unsigned long long head = ld_relaxed_u64(q.head);
     const unsigned long long res = ld_relaxed_u64(q.reserved);
@@ -422,7 +422,7 @@ __device__ __forceinline__ int pq_try_claim(const PQueue& q, unsigned long long*
 // record reads after it. Returns kPqEmpty if the wait gave up.
 __device__ __forceinline__ unsigned long long pq_take(const PQueue& q, unsigned long long p, unsigned long long n) {
   unsigned long long* e = q.ring + p % n;
-  for (long long spin = 0; spin < kPqSpinLimit; ++spin) {
+  for (long long spin = 0; spin < q.spin_limit; ++spin) {
     const unsigned long long v = exch_acquire_u64(e, kPqEmpty);
     if (v != kPqEmpty) return v;
     __nanosleep(32);
@@ -435,7 +435,7 @@ __device__ __forceinline__ unsigned long long pq_take(const PQueue& q, unsigned 
 __device__ __forceinline__ bool pq_put(const PQueue& q, unsigned long long p, unsigned long long n,
                                        unsigned long long item) {
   unsigned long long* e = q.ring + p % n;
-  for (long long spin = 0; spin < kPqSpinLimit; ++spin) {
+  for (long long spin = 0; spin < q.spin_limit; ++spin) {
     if (cas_release_u64(e, kPqEmpty, item) == kPqEmpty) return true;
     __nanosleep(32);
   }
@@ -545,8 +545,10 @@ __device__ __forceinline__ bool pq_resolve(const EvalArgs& a, int ray, int sl, f
 }
 
 // The traversal queued the first items at ring positions [0, *qlen0).
-static __global__ void pq_init_kernel(const int32_t* __restrict__ qlen0, PQueue q) {
-  *q.reserved = (unsigned long long)(*qlen0);
+// phantom > 0 (a test hook) announces that many further items that nothing
+// ever writes, so that the waits for them run out.
+static __global__ void pq_init_kernel(const int32_t* __restrict__ qlen0, PQueue q, int32_t phantom) {
+  *q.reserved = (unsigned long long)(*qlen0) + (unsigned long long)(phantom > 0 ? phantom : 0);
 }
 
 // The four corners of the cell of level l at (x, y, z) whose x offset is xb:

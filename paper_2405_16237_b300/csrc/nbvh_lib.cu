@@ -146,6 +146,8 @@ nbvh_query_options default_options() {
   o.traverse_block = 128;
   o.eval_threads = 0;
   o.w1_mode = NBVH_W1_AUTO;
+  o.wait_spins = 0;
+  o.test_phantom_items = 0;
   return o;
 }
 
@@ -154,7 +156,8 @@ bool options_valid(const nbvh_query_options& o) {
          o.patience_cycles <= (int64_t(1) << 40) &&
          (o.traverse_block == 64 || o.traverse_block == 128 || o.traverse_block == 256) &&
          (o.eval_threads == 0 || o.eval_threads == 256 || o.eval_threads == 512) && o.w1_mode >= NBVH_W1_AUTO &&
-         o.w1_mode <= NBVH_W1_STREAMED;
+         o.w1_mode <= NBVH_W1_STREAMED && o.wait_spins >= 0 && o.wait_spins <= (int64_t(1) << 40) &&
+         o.test_phantom_items >= 0 && o.test_phantom_items <= 1024;
 }
 
 // The evaluation kernels can run this model with these options (checked on
@@ -259,7 +262,7 @@ QueryWs carve_query(void* base, int64_t n, int32_t max_segs, size_t image = 0) {
   return w;
 }
 
-PQueue pq_of(const QueryWs& w, int32_t max_segs, int64_t patience) {
+PQueue pq_of(const QueryWs& w, int32_t max_segs, int64_t patience, int64_t spin_limit) {
   int32_t* c = w.counters + pq_base(max_segs);
   PQueue q;
   q.head = reinterpret_cast<unsigned long long*>(c);
@@ -267,6 +270,7 @@ PQueue pq_of(const QueryWs& w, int32_t max_segs, int64_t patience) {
   q.retired = reinterpret_cast<unsigned long long*>(c + 64);
   q.tiles = reinterpret_cast<unsigned int*>(c + 96);
   q.patience = patience;
+  q.spin_limit = spin_limit > 0 ? spin_limit : kPqSpinLimit;
   q.ring = reinterpret_cast<unsigned long long*>(w.queue[0]);
   return q;
 }
@@ -326,8 +330,8 @@ cudaError_t launch_query_stages(const nbvh_model_desc* desc, const GridParams& g
   if (e != cudaSuccess) return e;
   if (persistent) {
     // one launch drains a queue of (slot, ray) items
-    a.pq = pq_of(w, max_segs, o.patience_cycles);
-    pq_init_kernel<<<1, 1, 0, s>>>(w.counters, a.pq);
+    a.pq = pq_of(w, max_segs, o.patience_cycles, o.wait_spins);
+    pq_init_kernel<<<1, 1, 0, s>>>(w.counters, a.pq, o.test_phantom_items);
     count_launches(1);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -1207,6 +1211,15 @@ Chunk chunk_of(const nbvh_rays& rays, const int32_t* leaf, const float* t0, cons
   return k;
 }
 
+// The labels of a chunk's rays: indexed by ray, so offset with the ray
+// arrays when the chunk's items are rays i0 .. i0 + c (no order).
+Labels labels_at(const Labels& lab, const Chunk& k) {
+  if (k.order || !lab.hit) return lab;
+  const int64_t o = k.i0;
+  auto at = [&](const float* p) { return p ? p + o : nullptr; };
+  return Labels{lab.hit + o, at(lab.depth), at(lab.nx), at(lab.ny), at(lab.nz), at(lab.ar), at(lab.ag), at(lab.ab)};
+}
+
 // Forward of one chunk into the workspace's activation buffers; with labels
 // (lab.hit set) also the loss terms and dL/d(raw) of its items.
 cudaError_t forward_chunk(const nbvh_model_desc* d, const GridParams& gp, const void* table, const float* mlp,
@@ -1229,7 +1242,7 @@ cudaError_t forward_chunk(const nbvh_model_desc* d, const GridParams& gp, const 
     a.t1 = k.t1;
     a.n = k.c;
     a.buf = TrainBuffers{w.X, w.H, w.O + k.i0 * no, w.G + k.i0 * no, w.loss_seg + k.i0, w.dZ};
-    a.lab = lab;
+    a.lab = labels_at(lab, k);
     a.n_valid = n_valid;
     a.loss_scale = loss_scale;
     a.loss_scale_dev = loss_scale_dev;
@@ -1248,7 +1261,7 @@ cudaError_t forward_chunk(const nbvh_model_desc* d, const GridParams& gp, const 
   a.tr.O = w.O + k.i0 * no;
   a.tr.G = w.G + k.i0 * no;
   a.tr.loss_seg = w.loss_seg + k.i0;
-  a.tr.lab = lab;
+  a.tr.lab = labels_at(lab, k);
   a.tr.n_valid = n_valid;
   a.tr.loss_scale = loss_scale;
   a.tr.loss_scale_dev = loss_scale_dev;

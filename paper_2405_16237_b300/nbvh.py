@@ -96,7 +96,8 @@ class LeafStats(ctypes.Structure):
 
 class QueryOptions(ctypes.Structure):
     _fields_ = [("schedule", c_int32), ("patience_cycles", c_int64), ("traverse_block", c_int32),
-                ("eval_threads", c_int32), ("w1_mode", c_int32)]
+                ("eval_threads", c_int32), ("w1_mode", c_int32), ("wait_spins", c_int64),
+                ("test_phantom_items", c_int32)]
 
 
 class TuneResult(ctypes.Structure):

@@ -162,7 +162,9 @@ class HybridBuilt:
     oracle's description of the same instances."""
 
     def __init__(self, ground, assets, mlp_prec: int, table_prec: int = B.BF16, table_scale: float = 1.0,
-                 gain: float = 2.0, max_segs: int = 16):
+                 gain: float = 2.0, max_segs: int = 16, train_steps: int = 0):
+        """train_steps > 0: each asset's model is first trained on its own
+        triangles with the library's FP16 training step (2^13 rays a step)."""
         import torch
         self.ground = ground
         self.blas = B.build_tri_blas(ground, 4)
@@ -178,11 +180,21 @@ class HybridBuilt:
             tab = W.init_table(lay["total"], a.model.n_features, 500 + k, table_scale)
             t = torch.as_tensor(tab)
             t = t.to(torch.bfloat16) if table_prec == B.BF16 else (t.half() if table_prec == B.FP16 else t)
-            table_host = t.float().numpy().astype(np.float64)
             table = t.cuda()
             layers = W.init_mlp(a.model.mlp_dims(), 600 + k, gain=gain)
             mlp = torch.as_tensor(B.pack_mlp(layers)).cuda()
             nodes = torch.as_tensor(lv["nodes"]).cuda()
+            if train_steps > 0:
+                d16 = B.model_desc(a.model, table_prec, B.FP16, info["centre"], info["extent"])
+                scene = B.DeviceScene(a.tris, lv)
+                opt = B.Optimizer(d16, table.float().clone(), mlp.clone(), loss_scale=32768.0)
+                ws = B.new_workspace(B.train_workspace_size(d16, 1 << 13, scene.n_leaves))
+                for step in range(1, train_steps + 1):
+                    B.train_step(d16, opt, scene, B.TRAIN_PROBED_MIX, 1 << 13, 900 + k, step, 1e-2, ws)
+                table = opt.table.clone()
+                mlp = opt.mlp.clone()
+                layers = unpack_mlp(mlp.cpu().numpy(), a.model.mlp_dims())
+            table_host = table.float().cpu().numpy().astype(np.float64)
             self.keep += [table, mlp, nodes]
             self.instances.append(B.neural_instance(desc, table, mlp, nodes, lv["n_nodes"], max_segs))
             self.oinstances.append({"kind": "neural", "leaves": O.build_leaves(a.tris, a.n_leaves, 1e-4),
@@ -210,3 +222,45 @@ def hybrid_ambiguous(ref, n_rays, rel=1e-5):
             close = np.isfinite(T[:, 1]) & (T[:, 1] - T[:, 0] <= rel * np.maximum(1.0, np.abs(T[:, 0])))
         amb |= close
     return amb
+
+
+# ---------------------------------------------------------------- trained weights
+def unpack_mlp(flat, dims):
+    """The library's flat MLP parameters as [(W [out, in], b [out])]."""
+    flat = np.asarray(flat, np.float32)
+    layers, off = [], 0
+    for i in range(len(dims) - 1):
+        w = flat[off:off + dims[i + 1] * dims[i]].reshape(dims[i + 1], dims[i])
+        off += dims[i + 1] * dims[i]
+        bias = flat[off:off + dims[i + 1]]
+        off += dims[i + 1]
+        layers.append((w.copy(), bias.copy()))
+    return layers
+
+
+class Trained:
+    """A case's model after `steps` of the library's own FP16 training step
+    (probed-mix rays of its scene, 2^14 per step, lr 1e-2, dynamic loss
+    scale). Trained networks put most logits far from zero, as a query meets
+    them in use; the table stays in the case's storage precision."""
+
+    def __init__(self, b: Built, steps: int = 300, batch: int = 1 << 14, seed: int = 7):
+        import torch
+        desc = b.with_prec(B.FP16)
+        scene = B.DeviceScene(b.case.tris, b.leaves)
+        opt = B.Optimizer(desc, b.table.float().clone(), b.mlp.clone(), loss_scale=32768.0)
+        ws = B.new_workspace(B.train_workspace_size(desc, batch, scene.n_leaves))
+        for step in range(1, steps + 1):
+            B.train_step(desc, opt, scene, B.TRAIN_PROBED_MIX, batch, seed, step, 1e-2, ws)
+        torch.cuda.synchronize()
+        assert B.device_status() == 0
+        self.b = b
+        self.table = opt.table.clone()
+        self.table_host = self.table.float().cpu().numpy().astype(np.float64)
+        self.mlp = opt.mlp.clone()
+        self.layers = unpack_mlp(self.mlp.cpu().numpy(), b.case.model.mlp_dims())
+
+    def oracle_query(self, rays=None):
+        b = self.b
+        return O.query(b.case.rays if rays is None else rays, b.oleaves, self.table_host, self.layers, b.olayout,
+                       b.case.model.n_samples)

@@ -230,3 +230,26 @@ def test_wide_first_layer_matches_oracle(mp, shape):
 
 def _stageable(desc, opt) -> bool:
     return B.eval_plan(desc, opt) is not None
+
+
+def test_queue_wait_runs_out_and_reports_timeout():
+    """A bounded device wait that runs out: the persistent queue is told of
+    items that nothing ever writes (the test hook test_phantom_items, a flag
+    nothing sets), with a short wait limit. The query returns, the device
+    status reads NBVH_ERR_TIMEOUT (no trap, no fault, no endless spin), and the
+    context stays usable: the next query with the default options gives the
+    same records as before and a clean status."""
+    torch = _torch()
+    b = built()
+    desc = b.with_prec(B.FP16)
+    B.device_status()
+    ref = B.query_rays(desc, b.table, b.mlp, b.nodes, b.leaves["n_nodes"], b.rays, 24)
+    assert B.device_status() == 0
+    stalled = B.query_options(schedule=B.SCHEDULE_PERSISTENT, wait_spins=2000, test_phantom_items=7)
+    B.query_rays(desc, b.table, b.mlp, b.nodes, b.leaves["n_nodes"], b.rays, 24, options=stalled)
+    torch.cuda.synchronize()
+    assert B.device_status() == 6  # NBVH_ERR_TIMEOUT
+    again = B.query_rays(desc, b.table, b.mlp, b.nodes, b.leaves["n_nodes"], b.rays, 24)
+    assert B.device_status() == 0
+    for k in ref:
+        assert torch.equal(ref[k], again[k]), k

@@ -81,12 +81,13 @@ def test_hybrid_trace_fp32_matches_oracle():
 
 @pytest.mark.parametrize("mp", [B.FP16, B.BF16])
 def test_hybrid_trace_tensor_core_matches_oracle(mp):
-    """BF16 tables, FP16/BF16 tensor-core MLPs: winning instance agreement
-    >= 99.5%, depth <= 2e-3 and mean normal error <= 1 degree where both sides
-    pick the same instance and leaf."""
+    """BF16 tables, FP16/BF16 tensor-core MLPs, each asset's network trained
+    by the library (200 FP16 steps): winning instance agreement >= 99.9 %,
+    depth <= 2e-3 and mean normal error <= 1 degree where both sides pick the
+    same instance and leaf."""
     _torch()
     ground, assets = small_hybrid_scene(3)
-    hb = HybridBuilt(ground, assets, mp, table_prec=B.BF16)
+    hb = HybridBuilt(ground, assets, mp, table_prec=B.BF16, table_scale=1e-4, gain=1.0, train_steps=200)
     rays = hybrid_rays(40, 800)
     h, inst = B.hybrid_trace(hb.instances, B.to_device_rays(rays))
     assert B.device_status() == 0
@@ -94,7 +95,7 @@ def test_hybrid_trace_tensor_core_matches_oracle(mp):
     inst = inst.cpu().numpy()
     ref = O.hybrid_trace(rays, hb.oinstances)
     agree = np.mean(inst == ref["inst"])
-    assert agree >= 0.995, agree
+    assert agree >= 0.999, agree
     same = (inst == ref["inst"]) & (h["leaf"] == ref["leaf"]) & ref["hit"].astype(bool)
     assert same.sum() > 500
     assert np.max(np.abs(h["t"][same] - ref["t"][same])) <= 2e-3

@@ -431,3 +431,110 @@ def test_tensor_core_training_learns():
     assert B.device_status() == 0
     after = agreement()
     assert np.isfinite(float(loss.item())) and after > before + 0.05, (before, after)
+
+
+# ---------------------------------------------------------------- the benchmarked model (C1/C2)
+def c1_built(scale=0.5, gain=2.0):
+    """The model of the full-size icosphere workload and its training step
+    (16 levels, F = 2, 2^20-entry hashed levels, 16 samples: N * F = 32,
+    three 64-wide hidden layers) on a level-6 icosphere."""
+    key = ("c1", scale, gain)
+    if key not in _CACHE:
+        _torch()
+        b = Built(make_case("icosphere_l6", scale, gain))
+        b.scene = B.DeviceScene(b.case.tris, b.leaves)
+        _CACHE[key] = b
+    return _CACHE[key]
+
+
+@pytest.mark.parametrize("mp", [B.FP32, B.FP16, B.BF16])
+def test_benchmarked_model_forward_and_gradients_match_oracle(mp):
+    """Forward, loss and gradients of the benchmarked training model through
+    the kernels the training bench runs (FP16/BF16: the tensor-core forward
+    at width 64, train_backward_tc<2, 64> with level-major scatter (N * F =
+    32) and the tensor-core first-layer weight gradient; FP32: the CUDA-core
+    forward and backward). FP32 against the exact oracle: raw outputs and the
+    loss <= 1e-5 relative, gradients <= 1e-5 of the largest entry. FP16/BF16
+    against the oracle run with the same 16-bit operand rounding and loss
+    scale: table gradient median per-entry error <= 1e-4, 90th percentile
+    <= 1e-3, relative L2 <= 1e-2 for table and MLP, MLP median <= 1e-3."""
+    torch = _torch()
+    b = c1_built()
+    desc = b.with_prec(mp)
+    dv, h = _batch(b, n=1500, seed=91)
+    n = len(h["leaf"])
+    ws = B.new_workspace(B.train_workspace_size(desc, n))
+    scale = 1.0 if mp == B.FP32 else 1024.0
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    raw = B.forward_train(desc, b.table, b.mlp, dv["rays"], dv["leaf"], dv["t0"], dv["t1"], ws, labels=dv["lab"],
+                          n_valid=dv["n_valid"], loss_scale=scale, loss_out=loss)
+    g_tab = torch.zeros((b.layout["total"], b.case.model.n_features), dtype=torch.float32, device="cuda")
+    g_mlp = torch.zeros_like(b.mlp)
+    B.backward(desc, b.table, b.mlp, dv["rays"], dv["leaf"], dv["t0"], dv["t1"], ws, g_tab, g_mlp)
+    assert B.device_status() == 0
+    fr = b.oleaves["frame"]
+    v = h["valid"]
+    assert v.sum() > 500
+    if mp == B.FP32:
+        L, ref_tab, ref_layers, ref_raw = _oracle_fb(b, h)
+        r = raw.cpu().numpy()[v]
+        scale_j = np.sqrt(np.mean(ref_raw[v] ** 2, axis=0))
+        assert np.max(np.abs(r - ref_raw[v]) / (np.abs(ref_raw[v]) + scale_j)) <= 1e-5
+        assert abs(float(loss.item()) - L) <= 1e-5 * abs(L)
+        gt = g_tab.cpu().numpy()
+        assert np.max(np.abs(gt - ref_tab)) <= 1e-5 * np.max(np.abs(ref_tab))
+        ref_m = B.pack_mlp([(dw, db) for dw, db in ref_layers])
+        assert np.max(np.abs(g_mlp.cpu().numpy() - ref_m)) <= 1e-5 * np.max(np.abs(ref_m))
+        return
+    _, ref_tab, ref_layers, _ = O.forward_backward(h["o"], h["d"], h["t0"], h["t1"], v, h["yh"], h["yd"], h["yn"],
+                                                   b.table_host, b.layers, b.olayout, fr["model_centre"],
+                                                   fr["model_extent"], b.case.model.n_samples,
+                                                   rnd=_half_round(mp), scale=scale)
+    gt, rt = g_tab.cpu().numpy().ravel() / scale, ref_tab.ravel()
+    gm, rm = g_mlp.cpu().numpy() / scale, B.pack_mlp(ref_layers).astype(np.float64)
+    et, em = _entry_err(gt, rt), _entry_err(gm, rm)
+    l2t = np.linalg.norm(gt - rt) / np.linalg.norm(rt)
+    l2m = np.linalg.norm(gm - rm) / np.linalg.norm(rm)
+    stats = (np.median(et), np.percentile(et, 90), l2t, np.median(em), l2m)
+    assert np.median(et) <= 1e-4 and np.percentile(et, 90) <= 1e-3 and l2t <= 1e-2, stats
+    assert np.median(em) <= 1e-3 and l2m <= 1e-2, stats
+
+
+@pytest.mark.parametrize("mp", [B.FP32, B.FP16])
+def test_recompute_mode_equals_stored_mode(mp):
+    """A workspace a third of the stored size selects recompute mode (the
+    activations of one chunk of rays at a time, rebuilt in the backward). Raw
+    outputs and the loss are the same bits (every row is evaluated the same
+    way wherever it sits); the gradients differ only by FP32 summation order
+    (float atomics and split-K sums): relative L2 <= 1e-6 and every entry
+    within 1e-6 of the largest."""
+    torch = _torch()
+    b = c1_built()
+    desc = b.with_prec(mp)
+    dv, h = _batch(b, n=3000, seed=93)
+    n = len(h["leaf"])
+    stored = B.train_workspace_size(desc, n)
+    small, chunk = B.train_workspace_budget(desc, n, 0, stored // 3)
+    assert chunk < n and small < stored
+
+    def run(nbytes):
+        ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        if ws.data_ptr() % 256:
+            ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+        raw = B.forward_train(desc, b.table, b.mlp, dv["rays"], dv["leaf"], dv["t0"], dv["t1"], ws,
+                              labels=dv["lab"], n_valid=dv["n_valid"], loss_scale=1024.0, loss_out=loss)
+        g_tab = torch.zeros((b.layout["total"], b.case.model.n_features), dtype=torch.float32, device="cuda")
+        g_mlp = torch.zeros_like(b.mlp)
+        B.backward(desc, b.table, b.mlp, dv["rays"], dv["leaf"], dv["t0"], dv["t1"], ws, g_tab, g_mlp)
+        assert B.workspace_bytes(ws) < stored or nbytes >= stored
+        return raw, loss, g_tab, g_mlp
+
+    ra, la, ta, ma = run(stored)
+    rb, lb, tb, mb = run(small)
+    assert B.device_status() == 0
+    assert torch.equal(ra, rb) and torch.equal(la, lb)
+    for x, y in ((ta, tb), (ma, mb)):
+        x, y = x.double(), y.double()
+        assert float((x - y).norm() / x.norm()) <= 1e-6
+        assert float((x - y).abs().max()) <= 1e-6 * float(x.abs().max())

@@ -990,3 +990,30 @@ def test_cut_leaves_rejects_an_incomplete_cut():
     tris, nodes, rng, perm = _hand_base()
     with pytest.raises(ValueError):
         O.cut_leaves(tris, nodes, rng, perm, [2, ~0], 0.0, 10.0)   # base leaf 1 below no reference
+
+
+def test_sample_grid_f32_hand_example_and_rounding_bound():
+    """sample_grid_f32: a hand example whose every step is exact in float32
+    (t_k = 1.25, 1.75, 2.25, 2.75; x = t/8 + 1/2, y = 2t/8 + 1/2 clamped), and
+    on random inputs every coordinate within 3 float32 ulps of the exact
+    float64 value of the same formula (a dropped term or a wrong operand
+    would be far off)."""
+    o = np.array([[0.0, 0.0, 0.0]])
+    d = np.array([[1.0, 2.0, 0.0]])
+    x = O.sample_grid_f32(o, d, np.array([1.0]), np.array([3.0]), 4, np.zeros(3), 8.0)
+    assert x[0, :, 0].tolist() == [0.65625, 0.71875, 0.78125, 0.84375]
+    assert x[0, :, 1].tolist() == [0.8125, 0.9375, 1.0, 1.0]
+    assert x[0, :, 2].tolist() == [0.5, 0.5, 0.5, 0.5]
+    rng = np.random.default_rng(3)
+    n = 2000
+    o = rng.uniform(-1, 1, (n, 3)).astype(np.float32)
+    d = rng.normal(size=(n, 3)).astype(np.float32)
+    t0 = rng.uniform(0, 1, n).astype(np.float32)
+    t1 = (t0 + rng.uniform(0, 1, n)).astype(np.float32)
+    c = np.array([0.1, -0.2, 0.05], np.float32)
+    E = np.float32(3.0)
+    g32 = O.sample_grid_f32(o, d, t0, t1, 16, c, E)
+    ref = O.normalize_points(O.sample_points(o, d, t0, t1, 16), c, E)
+    inside = (ref > 1e-3) & (ref < 1 - 1e-3)
+    ulp = np.spacing(np.abs(ref).astype(np.float32)).astype(np.float64)
+    assert np.all(np.abs(g32 - ref)[inside] <= 3 * ulp[inside] + 2e-7)
