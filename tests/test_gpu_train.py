@@ -489,7 +489,7 @@ def test_benchmarked_model_forward_and_gradients_match_oracle(mp):
     _, ref_tab, ref_layers, _ = O.forward_backward(h["o"], h["d"], h["t0"], h["t1"], v, h["yh"], h["yd"], h["yn"],
                                                    b.table_host, b.layers, b.olayout, fr["model_centre"],
                                                    fr["model_extent"], b.case.model.n_samples,
-                                                   rnd=_half_round(mp), scale=scale)
+                                                   rnd=_half_round(mp), scale=scale, positions="f32")
     gt, rt = g_tab.cpu().numpy().ravel() / scale, ref_tab.ravel()
     gm, rm = g_mlp.cpu().numpy() / scale, B.pack_mlp(ref_layers).astype(np.float64)
     et, em = _entry_err(gt, rt), _entry_err(gm, rm)
