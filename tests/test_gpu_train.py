@@ -455,9 +455,13 @@ def test_benchmarked_model_forward_and_gradients_match_oracle(mp):
     32) and the tensor-core first-layer weight gradient; FP32: the CUDA-core
     forward and backward). FP32 against the exact oracle: raw outputs and the
     loss <= 1e-5 relative, gradients <= 1e-5 of the largest entry. FP16/BF16
-    against the oracle run with the same 16-bit operand rounding and loss
-    scale: table gradient median per-entry error <= 1e-4, 90th percentile
-    <= 1e-3, relative L2 <= 1e-2 for table and MLP, MLP median <= 1e-3."""
+    against the oracle run with the same 16-bit operand rounding, loss scale
+    and float32 sample positions (sample_grid_f32: at the finest level a
+    float32 position error is of the order of a 16-bit feature's rounding and
+    flips ReLU masks of near-zero pre-activations, each moving a whole ray's
+    contribution; with exact positions the MLP gradients differ by 1-4 %):
+    table gradient median per-entry error <= 1e-4, 90th percentile <= 1e-3,
+    relative L2 <= 1e-2 for table and MLP, MLP median <= 1e-3."""
     torch = _torch()
     b = c1_built()
     desc = b.with_prec(mp)
