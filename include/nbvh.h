@@ -216,6 +216,15 @@ nbvh_status nbvh_encode(const nbvh_model_desc* desc, const void* table, nbvh_ray
  *                   shared-memory buffers, 128 inputs at a time, by bulk
  *                   copies; NBVH_W1_AUTO: resident when it fits the CTA's
  *                   shared-memory budget, else streamed.
+ *  eval_pipeline    persistent FP16/BF16 schedule: NBVH_PIPELINE_PHASES runs
+ *                   each tile in CTA-wide phases (all warps gather, then the
+ *                   MLP, resolve and claim); NBVH_PIPELINE_WARP_SPECIALISED
+ *                   gives four warps the claims, MMAs, epilogues and resolves
+ *                   and twelve the gather, handing work over through
+ *                   mbarriers, so the next tile is gathered while the last
+ *                   one is finished (hidden width 32 or 64, first layer
+ *                   resident, L * F a multiple of 16; else UNSUPPORTED);
+ *                   NBVH_PIPELINE_AUTO: warp-specialised where it applies.
  *  wait_spins       persistent schedule: polling rounds (each with a short
  *                   sleep) before a queue wait gives up and records
  *                   NBVH_ERR_TIMEOUT; 0 = the default (about a second).
@@ -230,12 +239,16 @@ nbvh_status nbvh_encode(const nbvh_model_desc* desc, const void* table, nbvh_ray
 #define NBVH_W1_AUTO 0
 #define NBVH_W1_RESIDENT 1
 #define NBVH_W1_STREAMED 2
+#define NBVH_PIPELINE_AUTO 0
+#define NBVH_PIPELINE_PHASES 1
+#define NBVH_PIPELINE_WARP_SPECIALISED 2
 typedef struct {
   int32_t schedule;
   int64_t patience_cycles;
   int32_t traverse_block;
   int32_t eval_threads;
   int32_t w1_mode;
+  int32_t eval_pipeline;
   int64_t wait_spins;
   int32_t test_phantom_items;
 } nbvh_query_options;
@@ -244,14 +257,15 @@ typedef struct {
  * CTAs of 128 threads, automatic evaluation CTA shape and weight placement. */
 nbvh_status nbvh_query_options_default(nbvh_query_options* opt);
 
-/* Host. The evaluation kernel's launch plan for desc under opt (NULL = the
+/* Host. The query evaluation's launch plan for desc under opt (NULL = the
  * defaults): threads per CTA, whether the first layer's weights are streamed
  * (1) or resident (0), dynamic shared memory bytes and TMEM columns per CTA
  * (0 for the FP32 form, whose CTAs use no TMEM; for it *threads is the CTA
- * size and *w1_streamed says whether the first layer is taken in chunks).
+ * size and *w1_streamed says whether the first layer is taken in chunks), and
+ * the pipeline (NBVH_PIPELINE_PHASES or NBVH_PIPELINE_WARP_SPECIALISED).
  * NBVH_ERR_UNSUPPORTED when the kernels cannot run this combination. */
 nbvh_status nbvh_eval_plan(const nbvh_model_desc* desc, const nbvh_query_options* opt, int32_t* threads,
-                           int32_t* w1_streamed, int32_t* smem_bytes, int32_t* tmem_cols);
+                           int32_t* w1_streamed, int32_t* smem_bytes, int32_t* tmem_cols, int32_t* pipeline);
 
 /* Host. Workspace bytes of nbvh_eval_segments for desc (the streamed
  * first-layer image of the FP16/BF16 form; may be 0). */
@@ -325,10 +339,11 @@ typedef struct {
  * caller's own inputs under candidate options and returns the fastest in
  * *best (nothing is stored in the library). The search runs in stages, each
  * keeping the best so far: (1) waves, and for FP16/BF16 the persistent
- * schedule with patience 0, 1000, 4000, 16000 and 64000 cycles; (2) for
- * FP16/BF16 the evaluation CTA shape, 256 and 512 threads (256 only for
- * width <= 64) times resident and streamed first-layer weights, where the
- * model stages them; (3) traversal CTAs of 64, 128 and 256 threads. Each
+ * schedule with patience 0, 1000, 4000, 16000 and 64000 cycles (automatic
+ * pipeline and shape); (2) for FP16/BF16 the other evaluation pipeline and
+ * the phase kernel's CTA shapes, 256 and 512 threads (256 only for width
+ * <= 64) times resident and streamed first-layer weights, where the model
+ * stages them; (3) traversal CTAs of 64, 128 and 256 threads. Each
  * candidate runs once untimed and reps times timed (CUDA events on the
  * stream, median). The first all_cap candidates with their times go to
  * all[], their count to *n_all. Every candidate gives the same hit records

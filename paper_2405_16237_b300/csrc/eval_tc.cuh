@@ -207,6 +207,7 @@ struct TcLayout {
   uint32_t wh_off;           // (n_hidden - 1) x W x W
   uint32_t wo_off;           // 16 x W
   uint32_t row_off;          // two row buffers
+  uint32_t raw_off;          // raw outputs of a tile's rows (persistent query resolve)
   uint32_t bar_off;          // mbarriers + TMEM base address
   uint32_t total;
 };
@@ -248,6 +249,7 @@ __host__ __device__ inline TcLayout tc_layout(int L, int F, int N, int W, int n_
   T.wh_off = take(uint32_t(n_hidden - 1) * W * W * 2);
   T.wo_off = take(16u * W * 2);
   T.row_off = take(2 * kTcM * kRowBytes);
+  T.raw_off = take(kTcM * 8 * 4);
   T.bar_off = take(64);
   T.total = off + 128;  // slack for base alignment
   return T;
@@ -542,6 +544,50 @@ __device__ __forceinline__ bool pq_resolve(const EvalArgs& a, int ray, int sl, f
     write_albedo(a, ray, raw);
   }
   return next_t0 < best;
+}
+
+// Resolve the rows of one claimed item in slot order: row `row` holds the
+// item (slot s of its ray) and, in a partial tile, rows row + c, row + 2c, ...
+// hold the ray's next segments s + 1, s + 2, ... (lookahead rows staged while
+// they started before the ray's best t). The closest predicted hit over them
+// (ties to the earlier slot) updates the ray's record, evaluation stopping
+// at the first row that starts at or beyond the best t so far. *last = the
+// last slot evaluated. Returns whether the segment after it is queued (it
+// starts before the best t). raw: the tile's raw outputs, 8 per row.
+__device__ __forceinline__ bool pq_resolve_rows(const EvalArgs& a, const RowBuf& rb, const float* raw, int row, int c,
+                                                int* last) {
+  const int ray = rb.ray[row];
+  const size_t nr = size_t(a.n_rays);
+  float best = rb.best[row];
+  int win = -1, l = rb.slot[row];
+  SegResult w;
+  w.hit = false;
+  w.t = w.nx = w.ny = w.nz = 0.0f;
+  for (int j = row, m = 0; j < kTcM; j += c, ++m) {
+    if (m > 0 && (rb.ray[j] != ray || !(fminf(rb.t0[j], rb.t1[j]) < best))) break;
+    SegResult s = decode_segment(raw + j * 8, rb.t0[j], rb.t1[j]);
+    if (s.hit && rb.t0[j] > rb.t1[j]) s.hit = s.t > a.rays.tmin[ray] && s.t <= a.rays.tmax[ray];  // reversed chord
+    if (s.hit && s.t < best) {
+      best = s.t;
+      win = j;
+      w = s;
+    }
+    l = rb.slot[j];
+  }
+  if (win >= 0) {
+    a.hits.t[ray] = w.t;
+    a.hits.hit[ray] = 1;
+    a.hits.nx[ray] = w.nx;
+    a.hits.ny[ray] = w.ny;
+    a.hits.nz[ray] = w.nz;
+    a.hits.leaf[ray] = a.seg_leaf[size_t(rb.slot[win]) * nr + size_t(ray)];
+    if (a.inst_out) a.inst_out[ray] = a.inst_id;
+    write_albedo(a, ray, raw + win * 8);
+  }
+  *last = l;
+  if (l + 1 >= a.seg_count[ray]) return false;
+  const size_t qn = size_t(l + 1) * nr + size_t(ray);
+  return fminf(a.seg_t0[qn], a.seg_t1[qn]) < best;
 }
 
 // The traversal queued the first items at ring positions [0, *qlen0).
@@ -854,6 +900,33 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) eval_tc_kernel(EvalArgs
           put_row(rb, a.rays, threadIdx.x, -1, 0.0f, 0.0f);
       }
       __syncthreads();
+      if (ccount < kTcM) {
+        // A partial tile (the queue runs shallow): the empty rows take the
+        // claimed rays' next segments (row c + (e - 1) c + i: item i's e-th
+        // next slot) while they start before the ray's best t, so a ray's
+        // chain of segments advances several slots per tile.
+        if (threadIdx.x >= ccount && threadIdx.x < kTcM) {
+          const int j = int(threadIdx.x) - ccount;
+          const int i = j % ccount, e = j / ccount + 1;
+          const int ray = rb.ray[i];
+          int sl = -1;
+          float t0 = 0.0f, t1 = 0.0f;
+          if (ray >= 0) {
+            sl = rb.slot[i] + e;
+            if (sl < a.seg_count[ray]) {
+              const size_t q = size_t(sl) * size_t(a.n_rays) + size_t(ray);
+              t0 = a.seg_t0[q];
+              t1 = a.seg_t1[q];
+              if (!(fminf(t0, t1) < rb.best[i])) sl = -1;
+            } else {
+              sl = -1;
+            }
+          }
+          put_row(rb, a.rays, threadIdx.x, sl >= 0 ? ray : -1, t0, t1);
+          rb.slot[threadIdx.x] = sl;
+        }
+        __syncthreads();
+      }
     } else if (!persistent) {
       if (threadIdx.x < kTcM) {
         const int64_t i = tile * kTcM + threadIdx.x;
@@ -1100,10 +1173,19 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) eval_tc_kernel(EvalArgs
         const int ray = rb.ray[row];
         if constexpr (MODE == 1) {
           if (persistent) {
-            // the row's ray id stays in the row buffer only if its next segment is queued
-            const bool push = ray >= 0 && pq_resolve(a, ray, rb.slot[row], rb.best[row], rb.next[row], raw,
-                                                     rb.t0[row], rb.t1[row]);
+            // each item's thread resolves its rows (the item and its
+            // lookahead rows) in slot order; the row's ray id stays in the row
+            // buffer only if the ray's next segment is queued, its slot
+            // becomes the last one evaluated
+            float* rawbuf = reinterpret_cast<float*>(smem + lay.raw_off);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) rawbuf[row * 8 + j] = raw[j];
+            asm volatile("bar.sync 3, 128;" ::: "memory");
+            int last = rb.slot[row];
+            const bool push = row < ccount && ray >= 0 && pq_resolve_rows(a, rb, rawbuf, row, ccount, &last);
+            asm volatile("bar.sync 3, 128;" ::: "memory");
             rb.ray[row] = push ? ray : -1;
+            rb.slot[row] = last;
           } else {
             wave_resolve(a, ray >= 0, ray, raw, rb.t0[row], rb.t1[row]);
           }

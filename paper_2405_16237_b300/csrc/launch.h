@@ -3,6 +3,7 @@
 // not instantiate the kernels itself.
 #pragma once
 #include "eval_tc.cuh"
+#include "eval_ws.cuh"
 #include "train_tc.cuh"
 
 namespace nbvh {
@@ -18,7 +19,8 @@ namespace nbvh {
                                                  cudaStream_t);                                                   \
   extern template cudaError_t launch_plain_t<T, false>(int, const EvalArgs&, int64_t, cudaStream_t);              \
   extern template cudaError_t launch_plain_t<T, true>(int, const EvalArgs&, int64_t, cudaStream_t);               \
-  extern template cudaError_t launch_train_t<T>(bool, const nbvh_model_desc*, const TrainArgs&, cudaStream_t);
+  extern template cudaError_t launch_train_t<T>(bool, const nbvh_model_desc*, const TrainArgs&, cudaStream_t);     \
+  extern template cudaError_t launch_ws_t<T>(const nbvh_model_desc*, const EvalArgs&, cudaStream_t);
 NBVH_EXTERN_TABLE_TYPES(NBVH_EXTERN_TC)
 #undef NBVH_EXTERN_TC
 #undef NBVH_EXTERN_TABLE_TYPES

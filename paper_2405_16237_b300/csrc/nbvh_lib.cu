@@ -146,6 +146,7 @@ nbvh_query_options default_options() {
   o.traverse_block = 128;
   o.eval_threads = 0;
   o.w1_mode = NBVH_W1_AUTO;
+  o.eval_pipeline = NBVH_PIPELINE_AUTO;
   o.wait_spins = 0;
   o.test_phantom_items = 0;
   return o;
@@ -156,16 +157,40 @@ bool options_valid(const nbvh_query_options& o) {
          o.patience_cycles <= (int64_t(1) << 40) &&
          (o.traverse_block == 64 || o.traverse_block == 128 || o.traverse_block == 256) &&
          (o.eval_threads == 0 || o.eval_threads == 256 || o.eval_threads == 512) && o.w1_mode >= NBVH_W1_AUTO &&
-         o.w1_mode <= NBVH_W1_STREAMED && o.wait_spins >= 0 && o.wait_spins <= (int64_t(1) << 40) &&
+         o.w1_mode <= NBVH_W1_STREAMED && o.eval_pipeline >= NBVH_PIPELINE_AUTO &&
+         o.eval_pipeline <= NBVH_PIPELINE_WARP_SPECIALISED && o.wait_spins >= 0 && o.wait_spins <= (int64_t(1) << 40) &&
          o.test_phantom_items >= 0 && o.test_phantom_items <= 1024;
 }
 
+// Whether a query with these options runs the warp-specialised persistent
+// kernel: asked for, or automatic where it applies (the automatic CTA shape
+// and weight placement).
+bool use_ws(const nbvh_model_desc* d, const nbvh_query_options& o) {
+  if (d->mlp_prec == NBVH_FP32 || o.schedule != NBVH_SCHEDULE_PERSISTENT) return false;
+  if (o.eval_pipeline == NBVH_PIPELINE_WARP_SPECIALISED) return true;
+  return o.eval_pipeline == NBVH_PIPELINE_AUTO && (o.eval_threads == 0 || o.eval_threads == 512) &&
+         o.w1_mode != NBVH_W1_STREAMED && ws_supported(d);
+}
+
 // The evaluation kernels can run this model with these options (checked on
-// the host before anything is enqueued).
-bool eval_stageable(const nbvh_model_desc* d, const nbvh_query_options& o) {
+// the host before anything is enqueued). query: the options' schedule and
+// pipeline apply (a segment list always runs the phase kernel).
+bool eval_stageable(const nbvh_model_desc* d, const nbvh_query_options& o, bool query = true) {
   if (d->mlp_prec == NBVH_FP32)
     return plain_chunk_samples(d->n_samples, d->n_levels * d->n_features, d->width, d->n_hidden, d->n_out) >= 0;
+  if (query && o.eval_pipeline == NBVH_PIPELINE_WARP_SPECIALISED)
+    return o.schedule == NBVH_SCHEDULE_PERSISTENT && ws_supported(d);
+  if (query && use_ws(d, o)) return true;
   return tc_plan(d, o.eval_threads, o.w1_mode).ok;
+}
+
+cudaError_t launch_ws(const nbvh_model_desc* d, const EvalArgs& a, cudaStream_t s) {
+  switch (d->table_prec) {
+    case NBVH_FP32: return launch_ws_t<float>(d, a, s);
+    case NBVH_FP16: return launch_ws_t<__half>(d, a, s);
+    case NBVH_BF16: return launch_ws_t<__nv_bfloat16>(d, a, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
 // The evaluation's plan for desc under options o; with a streamed plan the
@@ -325,9 +350,13 @@ cudaError_t launch_query_stages(const nbvh_model_desc* desc, const GridParams& g
   a.inst_out = inst_out;
   a.inst_id = inst_id;
   a.max_segs = max_segs;
+  const bool ws = persistent && use_ws(desc, o);
   TcPlan plan;
-  e = prepare_eval(desc, a, o, w.image, &plan, s);
-  if (e != cudaSuccess) return e;
+  std::memset(&plan, 0, sizeof(plan));
+  if (!ws) {
+    e = prepare_eval(desc, a, o, w.image, &plan, s);
+    if (e != cudaSuccess) return e;
+  }
   if (persistent) {
     // one launch drains a queue of (slot, ray) items
     a.pq = pq_of(w, max_segs, o.patience_cycles, o.wait_spins);
@@ -335,7 +364,7 @@ cudaError_t launch_query_stages(const nbvh_model_desc* desc, const GridParams& g
     count_launches(1);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return launch_eval<1>(desc, a, rays.n, plan, s);
+    return ws ? launch_ws(desc, a, s) : launch_eval<1>(desc, a, rays.n, plan, s);
   }
   for (int wv = 0; wv < max_segs; ++wv) {
     a.wave = wv;
@@ -399,8 +428,8 @@ extern "C" nbvh_status nbvh_query_options_default(nbvh_query_options* opt) {
 
 extern "C" nbvh_status nbvh_eval_plan(const nbvh_model_desc* desc, const nbvh_query_options* opt,
                                       int32_t* threads, int32_t* w1_streamed, int32_t* smem_bytes,
-                                      int32_t* tmem_cols) {
-  if (!nbvh_host::desc_valid(desc) || !threads || !w1_streamed || !smem_bytes || !tmem_cols)
+                                      int32_t* tmem_cols, int32_t* pipeline) {
+  if (!nbvh_host::desc_valid(desc) || !threads || !w1_streamed || !smem_bytes || !tmem_cols || !pipeline)
     return NBVH_ERR_INVALID_ARG;
   const nbvh_query_options o = opt ? *opt : default_options();
   if (!options_valid(o)) return NBVH_ERR_INVALID_ARG;
@@ -413,6 +442,16 @@ extern "C" nbvh_status nbvh_eval_plan(const nbvh_model_desc* desc, const nbvh_qu
     *smem_bytes = int32_t(plain_smem_bytes((cs > 0 ? cs : desc->n_samples) * LF, desc->width, desc->n_hidden,
                                            desc->n_out));
     *tmem_cols = 0;
+    *pipeline = NBVH_PIPELINE_PHASES;
+    return NBVH_OK;
+  }
+  if (use_ws(desc, o)) {
+    const WsLayout L = ws_layout(desc->n_levels, desc->n_features, desc->n_samples, desc->width, desc->n_hidden);
+    *threads = kWsThreads;
+    *w1_streamed = 0;
+    *smem_bytes = int32_t(L.total);
+    *tmem_cols = 512;
+    *pipeline = NBVH_PIPELINE_WARP_SPECIALISED;
     return NBVH_OK;
   }
   const TcPlan pl = tc_plan(desc, o.eval_threads, o.w1_mode);
@@ -420,6 +459,7 @@ extern "C" nbvh_status nbvh_eval_plan(const nbvh_model_desc* desc, const nbvh_qu
   *w1_streamed = pl.stream ? 1 : 0;
   *smem_bytes = int32_t(pl.smem);
   *tmem_cols = int32_t(pl.ncols);
+  *pipeline = NBVH_PIPELINE_PHASES;
   return NBVH_OK;
 }
 
@@ -444,7 +484,7 @@ extern "C" nbvh_status nbvh_eval_segments(const nbvh_model_desc* desc, const voi
   if (ws_bytes < image_bytes(desc) || (image_bytes(desc) > 0 && !workspace)) return NBVH_ERR_WORKSPACE_TOO_SMALL;
   GridParams gp;
   if (!make_grid(desc, gp)) return NBVH_ERR_INVALID_ARG;
-  if (!eval_stageable(desc, o)) return NBVH_ERR_UNSUPPORTED;
+  if (!eval_stageable(desc, o, false)) return NBVH_ERR_UNSUPPORTED;
   EvalArgs a = base_args(desc, gp, table, mlp, rays);
   a.seg_ray = seg_ray;
   a.list_t0 = t0;
@@ -843,13 +883,21 @@ extern "C" nbvh_status nbvh_autotune_query(const nbvh_model_desc* desc, const vo
         consider(c);
       }
   }
-  if (tc && have) {  // stage 2: evaluation CTA shape and first-layer placement
+  if (tc && have) {  // stage 2: pipeline, evaluation CTA shape and first-layer placement
     const nbvh_tune_result base = b;
+    const bool pers = base.opt.schedule == NBVH_SCHEDULE_PERSISTENT;
+    const bool base_ws = use_ws(desc, base.opt);
+    const TcPlan cur = tc_plan(desc, base.opt.eval_threads, base.opt.w1_mode);
+    if (pers && !base_ws && ws_supported(desc)) {
+      nbvh_tune_result c = base;
+      c.opt.eval_pipeline = NBVH_PIPELINE_WARP_SPECIALISED;
+      consider(c);
+    }
     for (int32_t th : {256, 512})
       for (int32_t wm : {NBVH_W1_RESIDENT, NBVH_W1_STREAMED}) {
-        const TcPlan cur = tc_plan(desc, base.opt.eval_threads, base.opt.w1_mode);
-        if (th == cur.threads && (wm == NBVH_W1_STREAMED) == cur.stream) continue;  // timed in stage 1
+        if (!base_ws && th == cur.threads && (wm == NBVH_W1_STREAMED) == cur.stream) continue;  // timed in stage 1
         nbvh_tune_result c = base;
+        c.opt.eval_pipeline = NBVH_PIPELINE_PHASES;
         c.opt.eval_threads = th;
         c.opt.w1_mode = wm;
         consider(c);

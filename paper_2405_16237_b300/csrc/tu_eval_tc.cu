@@ -3,6 +3,7 @@
 // 0 segment list, 1 query, 2 training forward). The build compiles this file
 // once per combination so the instantiations compile in parallel.
 #include "eval_tc.cuh"
+#include "eval_ws.cuh"
 
 namespace nbvh {
 #if NBVH_TU_TABLE == 0
@@ -14,4 +15,7 @@ using TableT = __nv_bfloat16;
 #endif
 template cudaError_t launch_tc_tm<TableT, NBVH_TU_MODE>(const nbvh_model_desc*, const EvalArgs&, int64_t,
                                                         const TcPlan&, cudaStream_t);
+#if NBVH_TU_MODE == 1
+template cudaError_t launch_ws_t<TableT>(const nbvh_model_desc*, const EvalArgs&, cudaStream_t);
+#endif
 }  // namespace nbvh

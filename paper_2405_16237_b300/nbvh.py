@@ -96,8 +96,8 @@ class LeafStats(ctypes.Structure):
 
 class QueryOptions(ctypes.Structure):
     _fields_ = [("schedule", c_int32), ("patience_cycles", c_int64), ("traverse_block", c_int32),
-                ("eval_threads", c_int32), ("w1_mode", c_int32), ("wait_spins", c_int64),
-                ("test_phantom_items", c_int32)]
+                ("eval_threads", c_int32), ("w1_mode", c_int32), ("eval_pipeline", c_int32),
+                ("wait_spins", c_int64), ("test_phantom_items", c_int32)]
 
 
 class TuneResult(ctypes.Structure):
@@ -134,7 +134,7 @@ _SIGS = {
     "nbvh_query_options_default": (c_int32, [POINTER(QueryOptions)]),
     "nbvh_eval_workspace_size": (c_int32, [POINTER(ModelDesc), POINTER(c_size_t)]),
     "nbvh_eval_plan": (c_int32, [POINTER(ModelDesc), POINTER(QueryOptions), POINTER(c_int32), POINTER(c_int32),
-                                 POINTER(c_int32), POINTER(c_int32)]),
+                                 POINTER(c_int32), POINTER(c_int32), POINTER(c_int32)]),
     "nbvh_eval_segments": (c_int32, [POINTER(ModelDesc), c_void_p, c_void_p, Rays, c_void_p, c_void_p, c_void_p,
                                      c_int64, c_void_p, POINTER(QueryOptions), c_void_p, c_size_t, c_void_p]),
     "nbvh_query_workspace_size": (c_int32, [POINTER(ModelDesc), c_int64, c_int32, POINTER(c_size_t)]),
@@ -397,13 +397,14 @@ def encode(desc: ModelDesc, table, rays: dict, seg_ray, t0, t1, out=None):
 def eval_plan(desc: ModelDesc, options=None):
     """nbvh_eval_plan: the evaluation's launch plan as a dict, or None when
     the kernels cannot run this model under these options."""
-    th, st, sm, tm = c_int32(), c_int32(), c_int32(), c_int32()
+    th, st, sm, tm, pl = c_int32(), c_int32(), c_int32(), c_int32(), c_int32()
     code = lib().nbvh_eval_plan(ctypes.byref(desc), _opt_ref(options), ctypes.byref(th), ctypes.byref(st),
-                                ctypes.byref(sm), ctypes.byref(tm))
+                                ctypes.byref(sm), ctypes.byref(tm), ctypes.byref(pl))
     if code == 7:
         return None
     _check(code, "eval_plan")
-    return {"threads": th.value, "w1_streamed": bool(st.value), "smem_bytes": sm.value, "tmem_cols": tm.value}
+    return {"threads": th.value, "w1_streamed": bool(st.value), "smem_bytes": sm.value, "tmem_cols": tm.value,
+            "pipeline": PIPELINES[pl.value]}
 
 
 def eval_workspace_size(desc: ModelDesc) -> int:
@@ -447,6 +448,8 @@ def aligned_ptr(ws) -> int:
 
 SCHEDULE_WAVES, SCHEDULE_PERSISTENT = 0, 1
 W1_AUTO, W1_RESIDENT, W1_STREAMED = 0, 1, 2
+PIPELINE_AUTO, PIPELINE_PHASES, PIPELINE_WARP_SPECIALISED = 0, 1, 2
+PIPELINES = ("auto", "phases", "warp_specialised")
 
 
 def query_options(**kw) -> QueryOptions:
@@ -462,13 +465,14 @@ def query_options(**kw) -> QueryOptions:
 def options_dict(o: QueryOptions) -> dict:
     return {"schedule": ["waves", "persistent"][o.schedule], "patience_cycles": o.patience_cycles,
             "traverse_block": o.traverse_block, "eval_threads": o.eval_threads,
-            "w1_mode": ["auto", "resident", "streamed"][o.w1_mode]}
+            "w1_mode": ["auto", "resident", "streamed"][o.w1_mode], "eval_pipeline": PIPELINES[o.eval_pipeline]}
 
 
 def options_from_dict(d: dict) -> QueryOptions:
     return query_options(schedule=["waves", "persistent"].index(d["schedule"]), patience_cycles=d["patience_cycles"],
                          traverse_block=d["traverse_block"], eval_threads=d["eval_threads"],
-                         w1_mode=["auto", "resident", "streamed"].index(d["w1_mode"]))
+                         w1_mode=["auto", "resident", "streamed"].index(d["w1_mode"]),
+                         eval_pipeline=PIPELINES.index(d.get("eval_pipeline", "auto")))
 
 
 def _opt_ref(options):

@@ -447,6 +447,26 @@ def c1_built(scale=0.5, gain=2.0):
     return _CACHE[key]
 
 
+def _decided_rays(b, h, mp, tau=1e-3):
+    """Rays whose gradient no rounding-level difference can change by a
+    discrete step: every hidden pre-activation of the oracle's reduced-
+    precision model (16-bit operands, float32 positions) lies more than tau
+    times its layer's RMS from zero (a ReLU mask flip moves the ray's whole
+    contribution) and the depth and normal L1 terms lie more than tau from
+    their kinks."""
+    fr = b.oleaves["frame"]
+    x = O.sample_grid_f32(h["o"], h["d"], h["t0"], h["t1"], b.case.model.n_samples, fr["model_centre"],
+                          fr["model_extent"])
+    raw, _, pre = O.mlp_forward(O.encode(x, b.table_host, b.olayout), b.layers, _half_round(mp))
+    v = h["valid"].copy()
+    for z in pre[:-1]:
+        rms = np.sqrt(np.mean(z[v] ** 2))
+        v &= np.min(np.abs(z), axis=1) > tau * rms
+    v &= np.abs(O.sigmoid(raw[:, 1]) - h["yd"]) > tau
+    v &= np.min(np.abs(raw[:, 2:5] - h["yn"]), axis=1) > tau
+    return v
+
+
 @pytest.mark.parametrize("mp", [B.FP32, B.FP16, B.BF16])
 def test_benchmarked_model_forward_and_gradients_match_oracle(mp):
     """Forward, loss and gradients of the benchmarked training model through
@@ -456,16 +476,24 @@ def test_benchmarked_model_forward_and_gradients_match_oracle(mp):
     forward and backward). FP32 against the exact oracle: raw outputs and the
     loss <= 1e-5 relative, gradients <= 1e-5 of the largest entry. FP16/BF16
     against the oracle run with the same 16-bit operand rounding, loss scale
-    and float32 sample positions (sample_grid_f32: at the finest level a
-    float32 position error is of the order of a 16-bit feature's rounding and
-    flips ReLU masks of near-zero pre-activations, each moving a whole ray's
-    contribution; with exact positions the MLP gradients differ by 1-4 %):
-    table gradient median per-entry error <= 1e-4, 90th percentile <= 1e-3,
+    and float32 sample positions (sample_grid_f32), on the rays whose
+    gradient is decided (_decided_rays: ~85 %; the others are dropped on both
+    sides). A ReLU mask flipped by a rounding-level difference moves a whole
+    ray's contribution: with every ray kept, a handful of flips among the
+    288,000 hidden units changes the MLP gradients by 1-4 %. Bounds: table
+    gradient median per-entry error <= 1e-4, 90th percentile <= 1e-3,
     relative L2 <= 1e-2 for table and MLP, MLP median <= 1e-3."""
     torch = _torch()
     b = c1_built()
     desc = b.with_prec(mp)
-    dv, h = _batch(b, n=1500, seed=91)
+    dv, h = _batch(b, n=2500, seed=91)
+    if mp != B.FP32:
+        keep = _decided_rays(b, h, mp)
+        assert keep.sum() > 0.7 * h["valid"].sum()
+        leaf = np.where(keep, h["leaf"], -1).astype(np.int32)
+        h = dict(h, leaf=leaf, valid=keep)
+        dv = dict(dv, leaf=torch.as_tensor(leaf).cuda(),
+                  n_valid=torch.tensor([int(keep.sum())], dtype=torch.int32, device="cuda"))
     n = len(h["leaf"])
     ws = B.new_workspace(B.train_workspace_size(desc, n))
     scale = 1.0 if mp == B.FP32 else 1024.0
