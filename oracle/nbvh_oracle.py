@@ -359,12 +359,21 @@ def grid_index(c, res: int, dense: bool, T: int):
     return (h & np.uint64(T - 1)).astype(np.int64)
 
 
-def level_corners(x, res: int):
+def level_corners(x, res: int, f32: bool = False):
     """Cell and trilinear corner weights of points x [..., 3] in [0,1] at
     resolution ``res``: cell = min(floor(x*res), res - 1), frac = x*res - cell.
     Returns (corners [..., 8, 3] int64, weights [..., 8]); corner bit b of the
-    corner number selects +1 along axis b."""
-    pos = np.asarray(x, F64) * res
+    corner number selects +1 along axis b.
+
+    ``f32``: the reduced-precision form's grid coordinates: x (float32) * res
+    rounded once to float32, then cell and frac from that value (frac exact).
+    (Reading, as for sample_grid_f32: at resolution ~7,000 the float32
+    rounding of x * res moves frac by up to ~2e-4, of the order of a 16-bit
+    feature's rounding, so a half-precision oracle takes the form's value.)"""
+    if f32:
+        pos = (np.asarray(x, np.float32) * np.float32(res)).astype(np.float32).astype(F64)
+    else:
+        pos = np.asarray(x, F64) * res
     cell = np.minimum(np.floor(pos), res - 1).astype(np.int64)
     frac = pos - cell
     corners, weights = [], []
@@ -378,21 +387,23 @@ def level_corners(x, res: int):
     return np.stack(corners, -2), np.stack(weights, -1)
 
 
-def encode(x, table, layout):
+def encode(x, table, layout, f32: bool = False):
     """Features of points x [S, N, 3] (grid coords): for each sample k, level l
     and feature f, the trilinear interpolation of the 8 surrounding vertices'
     table entries. Concatenation order index = k*L*F + l*F + f, i.e. samples in
     ray order (Sec. 4: the order encodes the ray's direction).
-    ``table`` [total, F] (any float dtype, upcast). Returns [S, N*L*F]."""
-    tab = np.asarray(table).astype(F64)
+    ``table`` [total, F] (any float dtype; the gathered entries are upcast
+    exactly). ``f32``: float32 grid coordinates (level_corners). Returns
+    [S, N*L*F]."""
+    tab = np.asarray(table)
     S, N, _ = x.shape
     L = len(layout["res"])
     F = tab.shape[1]
     out = np.zeros((S, N, L, F))
     for l in range(L):
-        corners, w = level_corners(x, int(layout["res"][l]))
+        corners, w = level_corners(x, int(layout["res"][l]), f32)
         idx = grid_index(corners, int(layout["res"][l]), bool(layout["dense"][l]), layout["T"])
-        vals = tab[layout["offset"][l] + idx]            # [S, N, 8, F]
+        vals = tab[layout["offset"][l] + idx].astype(F64)  # [S, N, 8, F]
         out[:, :, l, :] = np.sum(w[..., None] * vals, axis=2)
     return out.reshape(S, N * L * F)
 
@@ -828,7 +839,7 @@ def mlp_backward(g_out, acts, pre, layers, rnd=None, scale: float = 1.0):
     return g, grads
 
 
-def encode_backward(x, g_feat, n_entries: int, n_features: int, layout):
+def encode_backward(x, g_feat, n_entries: int, n_features: int, layout, f32: bool = False):
     """Adjoint of ``encode``: every (sample, level, corner) adds
     weight * dL/dfeature into its table entry (collisions accumulate)."""
     S, N, _ = x.shape
@@ -837,7 +848,7 @@ def encode_backward(x, g_feat, n_entries: int, n_features: int, layout):
     g = np.asarray(g_feat, F64).reshape(S, N, L, F)
     out = np.zeros((n_entries, F))
     for l in range(L):
-        corners, w = level_corners(x, int(layout["res"][l]))
+        corners, w = level_corners(x, int(layout["res"][l]), f32)
         idx = grid_index(corners, int(layout["res"][l]), bool(layout["dense"][l]), layout["T"])
         rows = (layout["offset"][l] + idx).reshape(-1)
         contrib = (w[..., None] * g[:, :, l, None, :]).reshape(-1, F)
@@ -852,20 +863,22 @@ def forward_backward(o, d, t0, t1, valid, y_hit, y_depth, y_normal, table, layer
     table entry and MLP weight/bias. Returns (L, dtable, [(dW, db)], raw).
     ``rnd``/``scale``: half-precision MLP operands (``mlp_forward``,
     ``mlp_backward``); the encoding and the table gradient stay exact.
-    ``positions``: "f64" (exact sample points) or "f32" (sample_grid_f32, the
-    reduced-precision form's float32 positions)."""
-    if positions == "f32":
+    ``positions``: "f64" (exact sample points) or "f32" (the reduced-precision
+    form's float32 positions, sample_grid_f32, and grid coordinates,
+    level_corners(f32=True))."""
+    f32 = positions == "f32"
+    if f32:
         x = sample_grid_f32(o, d, t0, t1, n_samples, centre, extent)
     else:
         p = sample_points(o, d, t0, t1, n_samples)
         x = normalize_points(p, centre, extent)
-    feat = encode(x, table, layout)
+    feat = encode(x, table, layout, f32)
     raw, acts, pre = mlp_forward(feat, layers, rnd)
     L, _ = loss(raw, y_hit, y_depth, y_normal, valid, y_albedo)
     g = loss_grad(raw, y_hit, y_depth, y_normal, valid, y_albedo)
     g_feat, g_layers = mlp_backward(g, acts, pre, layers, rnd, scale)
     tab = np.asarray(table)
-    g_tab = encode_backward(x, g_feat, tab.shape[0], tab.shape[1], layout)
+    g_tab = encode_backward(x, g_feat, tab.shape[0], tab.shape[1], layout, f32)
     return L, g_tab, g_layers, raw
 
 

@@ -1017,3 +1017,43 @@ def test_sample_grid_f32_hand_example_and_rounding_bound():
     inside = (ref > 1e-3) & (ref < 1 - 1e-3)
     ulp = np.spacing(np.abs(ref).astype(np.float32)).astype(np.float64)
     assert np.all(np.abs(g32 - ref)[inside] <= 3 * ulp[inside] + 2e-7)
+
+
+def _round_f32(v: float) -> float:
+    """Round a Python float to the nearest float32 (ties to even) through the
+    IEEE single format of the struct module."""
+    import struct
+    return struct.unpack("<f", struct.pack("<f", v))[0]
+
+
+def test_level_corners_f32_grid_coordinates():
+    """level_corners(f32=True): p = x * res rounded once to float32 (the exact
+    double product of two float32 values, rounded through struct), cell =
+    min(floor(p), res - 1), frac = p - cell. Hand values: x = 0.1 (float32)
+    at res 7006 gives p = 700.6000366..., x = 0.5 at res 7006 is exact (3503),
+    and x = 1 clamps to the last cell with frac 1. Random points: frac within
+    half a float32 ulp of p of the float64 form, and weights summing to 1."""
+    x32 = np.float32(0.1)
+    p = _round_f32(float(x32) * 7006.0)
+    assert p != float(x32) * 7006.0 and abs(p - float(x32) * 7006.0) <= 2.0 ** -15
+    pts = np.array([[float(x32), 0.5, 1.0]])
+    c32, w32 = O.level_corners(pts, 7006, f32=True)
+    c64, w64 = O.level_corners(pts, 7006)
+    assert c32[0, 0].tolist() == [700, 3503, 7005] == c64[0, 0].tolist()
+    fx = p - 700.0
+    # corner 1 (+x): weight fx * (1 - 0) * (1 - 1) = 0; corner 7 (+x,+y,+z): fx * 0 * 1
+    # corner 5 (+x, +z): fx * (1 - fy) * fz with fy = 0, fz = 1
+    assert w32[0, 5] == fx and w32[0, 4] == 1.0 - fx
+    assert abs(w64[0, 5] - (float(x32) * 7006.0 - 700.0)) < 1e-12 and w64[0, 5] != w32[0, 5]
+    rng = np.random.default_rng(5)
+    x = rng.uniform(0, 1, (3000, 3)).astype(np.float32).astype(np.float64)
+    for res in (16, 81, 1383, 7006):
+        c32, w32 = O.level_corners(x, res, f32=True)
+        c64, w64 = O.level_corners(x, res)
+        pos = x * res
+        half_ulp = 0.5 * np.spacing(pos.astype(np.float32)).astype(np.float64)
+        same = np.all(c32 == c64, axis=(-1, -2))
+        assert same.mean() > 0.99
+        f32 = (np.asarray(x, np.float32) * np.float32(res)).astype(np.float64) - c32[:, 0, :]
+        assert np.all(np.abs(f32 - (pos - c64[:, 0, :]))[same] <= half_ulp[same] + 1e-12)
+        assert np.allclose(w32.sum(-1), 1.0, atol=1e-12)
