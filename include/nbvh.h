@@ -224,7 +224,9 @@ nbvh_status nbvh_encode(const nbvh_model_desc* desc, const void* table, nbvh_ray
  *                   mbarriers, so the next tile is gathered while the last
  *                   one is finished (hidden width 32 or 64, first layer
  *                   resident, L * F a multiple of 16; else UNSUPPORTED);
- *                   NBVH_PIPELINE_AUTO: warp-specialised where it applies.
+ *                   NBVH_PIPELINE_AUTO: the phase kernel (the faster one on
+ *                   the displaced-icosphere workload; the autotuner times
+ *                   both).
  *  wait_spins       persistent schedule: polling rounds (each with a short
  *                   sleep) before a queue wait gives up and records
  *                   NBVH_ERR_TIMEOUT; 0 = the default (about a second).
@@ -361,12 +363,32 @@ nbvh_status nbvh_autotune_query(const nbvh_model_desc* desc, const void* table, 
 nbvh_status nbvh_query_stats(const void* workspace, int64_t n_rays, int32_t max_segs, int64_t* segments,
                              int32_t* waves, void* stream);
 
-/* Host. Stage timing: while enabled, nbvh_query_rays records CUDA events on
- * the caller's stream around its traversal and its evaluation waves;
- * nbvh_get_timing synchronises on them and returns the summed milliseconds
- * since the previous nbvh_get_timing, and the number of timed calls. */
+/* Host. Kernel-class timing: while enabled, every enqueueing call records a
+ * CUDA event pair on the caller's stream around each group of launches of
+ * one class (a query's traversal; its evaluation: image, queue set-up and the
+ * persistent launch or every wave; a triangle trace; ...), except while the
+ * stream is being captured into a graph. nbvh_get_kernel_times synchronises
+ * on the events recorded since its previous call and returns, per class
+ * (index NBVH_KERNEL_*, n_kinds entries, at most NBVH_KERNEL_KINDS used),
+ * the summed milliseconds, the number of timed groups and the kernels they
+ * launched (counted by this process, so exact when one host thread
+ * enqueues). Timing adds two event records per group and no
+ * synchronisation to the enqueueing calls. */
+#define NBVH_KERNEL_TRAVERSE 0        /* S1 traversal */
+#define NBVH_KERNEL_EVAL 1            /* S2..S5 query evaluation (encode + MLP + resolve) */
+#define NBVH_KERNEL_TRI_TRACE 2       /* triangle BLAS closest hit */
+#define NBVH_KERNEL_TLAS_CULL 3       /* hybrid top-level ray lists */
+#define NBVH_KERNEL_BOUNCE 4          /* cosine-weighted bounce rays */
+#define NBVH_KERNEL_TRAIN_RAYS 5      /* training rays, leaf selection and grouping */
+#define NBVH_KERNEL_LABELS 6          /* brute-force ray-triangle labels */
+#define NBVH_KERNEL_TRAIN_FORWARD 7   /* training forward and loss terms */
+#define NBVH_KERNEL_TRAIN_BACKWARD 8  /* MLP adjoint + table-gradient scatter */
+#define NBVH_KERNEL_WEIGHT_GRAD 9     /* MLP weight gradients */
+#define NBVH_KERNEL_ADAM 10           /* gradient check, Adam, loss scale */
+#define NBVH_KERNEL_OTHER 11          /* clears, loss reduction, statistics */
+#define NBVH_KERNEL_KINDS 12
 nbvh_status nbvh_set_timing(int32_t enable);
-nbvh_status nbvh_get_timing(double* traverse_ms, double* eval_ms, int64_t* calls);
+nbvh_status nbvh_get_kernel_times(double* ms, int64_t* sections, int64_t* launches, int32_t n_kinds);
 
 /* Host. Number of kernels this library has launched in this process. */
 int64_t nbvh_launch_count(void);

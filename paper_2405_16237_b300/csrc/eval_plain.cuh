@@ -86,9 +86,10 @@ struct TcTrain {
 // so head - retired counts the items in evaluation.
 struct PQueue {
   unsigned long long* head;      // items claimed
-  unsigned long long* reserved;  // items ever queued (= segments evaluated)
+  unsigned long long* reserved;  // items ever queued
   unsigned long long* retired;   // items resolved
   unsigned int* tiles;           // tiles claimed (statistics)
+  unsigned long long* lookahead; // segments evaluated in lookahead rows, never queued (statistics)
   long long patience;            // cycles a CTA waits for a full tile before taking a partial one
   long long spin_limit;          // polling rounds before a queue wait gives up (NBVH_ERR_TIMEOUT)
   unsigned long long* ring;      // [n_rays] items; nullptr: one launch per segment slot instead

@@ -905,6 +905,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) eval_tc_kernel(EvalArgs
         // claimed rays' next segments (row c + (e - 1) c + i: item i's e-th
         // next slot) while they start before the ray's best t, so a ray's
         // chain of segments advances several slots per tile.
+        bool staged = false;
         if (threadIdx.x >= ccount && threadIdx.x < kTcM) {
           const int j = int(threadIdx.x) - ccount;
           const int i = j % ccount, e = j / ccount + 1;
@@ -924,8 +925,10 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) eval_tc_kernel(EvalArgs
           }
           put_row(rb, a.rays, threadIdx.x, sl >= 0 ? ray : -1, t0, t1);
           rb.slot[threadIdx.x] = sl;
+          staged = sl >= 0;
         }
-        __syncthreads();
+        const int n_staged = __syncthreads_count(staged);
+        if (threadIdx.x == 0 && n_staged > 0) atomicAdd(a.pq.lookahead, (unsigned long long)n_staged);
       }
     } else if (!persistent) {
       if (threadIdx.x < kTcM) {

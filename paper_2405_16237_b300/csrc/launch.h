@@ -26,6 +26,8 @@ NBVH_EXTERN_TABLE_TYPES(NBVH_EXTERN_TC)
 #undef NBVH_EXTERN_TABLE_TYPES
 
 cudaError_t launch_bwd_tc(const nbvh_model_desc* d, const TcBwdArgs& a, cudaStream_t s);
+// W0^T of the streamed backward (bwd_w0_streamed) into img (Kp * W * 2 bytes)
+cudaError_t launch_bwd_image(const nbvh_model_desc* d, const float* mlp, uint8_t* img, cudaStream_t s);
 cudaError_t launch_wg_tc(bool bf16, int W, const WgTcArgs& a, cudaStream_t s);
 
 }  // namespace nbvh

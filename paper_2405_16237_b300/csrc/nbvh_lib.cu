@@ -163,13 +163,11 @@ bool options_valid(const nbvh_query_options& o) {
 }
 
 // Whether a query with these options runs the warp-specialised persistent
-// kernel: asked for, or automatic where it applies (the automatic CTA shape
-// and weight placement).
+// kernel: only when asked for (the automatic choice is the phase kernel,
+// which measured faster on the icosphere workload; the autotuner times both).
 bool use_ws(const nbvh_model_desc* d, const nbvh_query_options& o) {
-  if (d->mlp_prec == NBVH_FP32 || o.schedule != NBVH_SCHEDULE_PERSISTENT) return false;
-  if (o.eval_pipeline == NBVH_PIPELINE_WARP_SPECIALISED) return true;
-  return o.eval_pipeline == NBVH_PIPELINE_AUTO && (o.eval_threads == 0 || o.eval_threads == 512) &&
-         o.w1_mode != NBVH_W1_STREAMED && ws_supported(d);
+  return d->mlp_prec != NBVH_FP32 && o.schedule == NBVH_SCHEDULE_PERSISTENT &&
+         o.eval_pipeline == NBVH_PIPELINE_WARP_SPECIALISED;
 }
 
 // The evaluation kernels can run this model with these options (checked on
@@ -226,17 +224,22 @@ cudaError_t launch_eval(const nbvh_model_desc* d, const EvalArgs& a, int64_t n, 
 // Bytes of the first-layer image an evaluation of desc may need.
 size_t image_bytes(const nbvh_model_desc* d) { return d->mlp_prec == NBVH_FP32 ? 0 : tc_image_bytes(d); }
 
-// ---------------------------------------------------------------- bookkeeping
-struct StageEvents {
-  cudaEvent_t e0, e1, e2;
+// ---------------------------------------------------------------- kernel-class timing
+// While timing is enabled (nbvh_set_timing) each timed section records a CUDA
+// event pair on its stream around its launches (not while the stream is being
+// captured into a graph); nbvh_get_kernel_times sums them per class.
+struct TimedRecord {
+  int kind;
+  cudaEvent_t a, b;
+  int64_t launches;
 };
 
 std::mutex g_timing_mu;
 bool g_timing = false;
-std::vector<StageEvents> g_pending;
+std::vector<TimedRecord> g_records;
 std::vector<cudaEvent_t> g_free_events;
 
-cudaEvent_t take_event() {
+cudaEvent_t take_event() {  // under g_timing_mu
   if (!g_free_events.empty()) {
     cudaEvent_t e = g_free_events.back();
     g_free_events.pop_back();
@@ -246,6 +249,43 @@ cudaEvent_t take_event() {
   if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
   return e;
 }
+
+class TimedSection {
+ public:
+  TimedSection(int kind, cudaStream_t s) : kind_(kind), s_(s) {
+    {
+      std::lock_guard<std::mutex> lk(g_timing_mu);
+      if (!g_timing) return;
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+    std::lock_guard<std::mutex> lk(g_timing_mu);
+    a_ = take_event();
+    b_ = take_event();
+    if (!a_ || !b_) {
+      if (a_) g_free_events.push_back(a_);
+      if (b_) g_free_events.push_back(b_);
+      a_ = b_ = nullptr;
+      return;
+    }
+    l0_ = g_launches.load();
+    cudaEventRecord(a_, s_);
+  }
+  ~TimedSection() {
+    if (!a_) return;
+    cudaEventRecord(b_, s_);
+    std::lock_guard<std::mutex> lk(g_timing_mu);
+    g_records.push_back({kind_, a_, b_, g_launches.load() - l0_});
+  }
+  TimedSection(const TimedSection&) = delete;
+  TimedSection& operator=(const TimedSection&) = delete;
+
+ private:
+  int kind_;
+  cudaStream_t s_;
+  cudaEvent_t a_ = nullptr, b_ = nullptr;
+  int64_t l0_ = 0;
+};
 
 struct QueryWs {
   int32_t* counters;
@@ -294,6 +334,7 @@ PQueue pq_of(const QueryWs& w, int32_t max_segs, int64_t patience, int64_t spin_
   q.reserved = reinterpret_cast<unsigned long long*>(c + 32);
   q.retired = reinterpret_cast<unsigned long long*>(c + 64);
   q.tiles = reinterpret_cast<unsigned int*>(c + 96);
+  q.lookahead = reinterpret_cast<unsigned long long*>(c + 98);
   q.patience = patience;
   q.spin_limit = spin_limit > 0 ? spin_limit : kPqSpinLimit;
   q.ring = reinterpret_cast<unsigned long long*>(w.queue[0]);
@@ -307,8 +348,8 @@ PQueue pq_of(const QueryWs& w, int32_t max_segs, int64_t patience, int64_t spin_
 cudaError_t launch_query_stages(const nbvh_model_desc* desc, const GridParams& gp, const void* table,
                                 const float* mlp, const nbvh_node* nodes, const nbvh_rays& rays, int32_t max_segs,
                                 const nbvh_hits& out, const QueryWs& w, bool merge, int32_t* inst_out,
-                                int32_t inst_id, const nbvh_query_options& o, cudaEvent_t after_traverse,
-                                cudaStream_t s, const int32_t* list = nullptr, const int32_t* list_count = nullptr) {
+                                int32_t inst_id, const nbvh_query_options& o, cudaStream_t s,
+                                const int32_t* list = nullptr, const int32_t* list_count = nullptr) {
   TraverseOut to;
   std::memset(&to, 0, sizeof(to));
   to.seg_count = w.seg_count;
@@ -329,17 +370,21 @@ cudaError_t launch_query_stages(const nbvh_model_desc* desc, const GridParams& g
     if (me != cudaSuccess) return me;
   }
   const int tb = o.traverse_block;
-  if (list) {  // only the listed rays (grid-stride over the device-side count)
-    const int64_t blocks = std::min<int64_t>((rays.n + 255) / 256, int64_t(sm_count()) * 8);
-    traverse_list_kernel<<<unsigned(std::max<int64_t>(blocks, 1)), 256, 0, s>>>(nodes, ray_ptrs(rays), rays.n,
-                                                                                 list, list_count, to);
-  } else {
-    traverse_kernel<<<unsigned((rays.n + tb - 1) / tb), tb, 0, s>>>(nodes, ray_ptrs(rays), rays.n, to);
+  cudaError_t e;
+  {
+    TimedSection ts(NBVH_KERNEL_TRAVERSE, s);
+    if (list) {  // only the listed rays (grid-stride over the device-side count)
+      const int64_t blocks = std::min<int64_t>((rays.n + 255) / 256, int64_t(sm_count()) * 8);
+      traverse_list_kernel<<<unsigned(std::max<int64_t>(blocks, 1)), 256, 0, s>>>(nodes, ray_ptrs(rays), rays.n,
+                                                                                   list, list_count, to);
+    } else {
+      traverse_kernel<<<unsigned((rays.n + tb - 1) / tb), tb, 0, s>>>(nodes, ray_ptrs(rays), rays.n, to);
+    }
+    count_launches(1);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
   }
-  count_launches(1);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  if (after_traverse) cudaEventRecord(after_traverse, s);
+  TimedSection ts(NBVH_KERNEL_EVAL, s);
   EvalArgs a = base_args(desc, gp, table, mlp, rays);
   a.n_rays = rays.n;
   a.seg_count = w.seg_count;
@@ -533,28 +578,8 @@ extern "C" nbvh_status nbvh_query_rays_opt(const nbvh_model_desc* desc, const vo
   cudaStream_t s = as_stream(stream);
   cudaError_t e = cudaMemsetAsync(w.counters, 0, counters_bytes(max_segs), s);
   if (e != cudaSuccess) return NBVH_ERR_CUDA;
-  StageEvents ev{nullptr, nullptr, nullptr};
-  cudaStreamCaptureStatus capturing = cudaStreamCaptureStatusNone;
-  if (cudaStreamIsCapturing(s, &capturing) != cudaSuccess) return NBVH_ERR_CUDA;
-  {
-    std::lock_guard<std::mutex> lk(g_timing_mu);
-    if (g_timing && capturing == cudaStreamCaptureStatusNone) {
-      ev.e0 = take_event();
-      ev.e1 = take_event();
-      ev.e2 = take_event();
-    }
-  }
-  const bool timed = ev.e0 && ev.e1 && ev.e2;
-  if (timed) cudaEventRecord(ev.e0, s);
-  e = launch_query_stages(desc, gp, table, mlp, nodes, rays, max_segs, out, w, false, nullptr, 0, o,
-                          timed ? ev.e1 : nullptr, s);
-  if (e != cudaSuccess) return status_of(e);
-  if (timed) {
-    cudaEventRecord(ev.e2, s);
-    std::lock_guard<std::mutex> lk(g_timing_mu);
-    g_pending.push_back(ev);
-  }
-  return NBVH_OK;
+  e = launch_query_stages(desc, gp, table, mlp, nodes, rays, max_segs, out, w, false, nullptr, 0, o, s);
+  return status_of(e);
 }
 
 extern "C" nbvh_status nbvh_query_stats(const void* workspace, int64_t n_rays, int32_t max_segs, int64_t* segments,
@@ -567,11 +592,13 @@ extern "C" nbvh_status nbvh_query_stats(const void* workspace, int64_t n_rays, i
   if (cudaMemcpyAsync(c.data(), workspace, sizeof(int32_t) * c.size(), cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return NBVH_ERR_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return NBVH_ERR_CUDA;
-  // persistent query (tensor-core form): one launch, items ever enqueued
-  uint64_t reserved = 0;
+  // persistent query (tensor-core form): one launch, items ever queued plus
+  // the segments lookahead rows evaluated without queueing them
+  uint64_t reserved = 0, lookahead = 0;
   std::memcpy(&reserved, c.data() + pq_base(max_segs) + 32, sizeof(reserved));
+  std::memcpy(&lookahead, c.data() + pq_base(max_segs) + 98, sizeof(lookahead));
   if (reserved > 0) {
-    *segments = int64_t(reserved);
+    *segments = int64_t(reserved + lookahead);
     *waves = 1;
     return NBVH_OK;
   }
@@ -592,34 +619,34 @@ extern "C" nbvh_status nbvh_set_timing(int32_t enable) {
   return NBVH_OK;
 }
 
-extern "C" nbvh_status nbvh_get_timing(double* traverse_ms, double* eval_ms, int64_t* calls) {
-  if (!traverse_ms || !eval_ms || !calls) return NBVH_ERR_INVALID_ARG;
-  std::vector<StageEvents> pend;
+extern "C" nbvh_status nbvh_get_kernel_times(double* ms, int64_t* sections, int64_t* launches, int32_t n_kinds) {
+  if (!ms || !sections || !launches || n_kinds < 1) return NBVH_ERR_INVALID_ARG;
+  std::vector<TimedRecord> rec;
   {
     std::lock_guard<std::mutex> lk(g_timing_mu);
-    pend.swap(g_pending);
+    rec.swap(g_records);
   }
-  double tr = 0.0, ev = 0.0;
+  for (int32_t k = 0; k < n_kinds; ++k) {
+    ms[k] = 0.0;
+    sections[k] = 0;
+    launches[k] = 0;
+  }
   nbvh_status st = NBVH_OK;
-  for (auto& p : pend) {
-    float a = 0.0f, b = 0.0f;
-    if (cudaEventSynchronize(p.e2) != cudaSuccess || cudaEventElapsedTime(&a, p.e0, p.e1) != cudaSuccess ||
-        cudaEventElapsedTime(&b, p.e1, p.e2) != cudaSuccess)
+  for (auto& r : rec) {
+    float t = 0.0f;
+    if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess)
       st = NBVH_ERR_CUDA;
-    tr += a;
-    ev += b;
-  }
-  {
-    std::lock_guard<std::mutex> lk(g_timing_mu);
-    for (auto& p : pend) {
-      g_free_events.push_back(p.e0);
-      g_free_events.push_back(p.e1);
-      g_free_events.push_back(p.e2);
+    if (r.kind < n_kinds) {
+      ms[r.kind] += t;
+      sections[r.kind] += 1;
+      launches[r.kind] += r.launches;
     }
   }
-  *traverse_ms = tr;
-  *eval_ms = ev;
-  *calls = int64_t(pend.size());
+  std::lock_guard<std::mutex> lk(g_timing_mu);
+  for (auto& r : rec) {
+    g_free_events.push_back(r.a);
+    g_free_events.push_back(r.b);
+  }
   return st;
 }
 
@@ -633,6 +660,7 @@ extern "C" nbvh_status nbvh_bounce_rays(nbvh_rays rays, nbvh_hits hits, uint64_t
       !out.dy || !out.dz || !out.tmin || !out.tmax)
     return NBVH_ERR_INVALID_ARG;
   RayOut o{out.ox, out.oy, out.oz, out.dx, out.dy, out.dz, out.tmin, out.tmax};
+  TimedSection ts(NBVH_KERNEL_BOUNCE, as_stream(stream));
   bounce_kernel<<<unsigned((rays.n + 255) / 256), 256, 0, as_stream(stream)>>>(
       ray_ptrs(rays), hits, rays.n, uint32_t(seed & 0xffffffffu), uint32_t(seed >> 32), o);
   count_launches(1);
@@ -710,6 +738,7 @@ extern "C" nbvh_status nbvh_trace_triangles(const nbvh_tri_blas* blas, nbvh_rays
   if (rays.n == 0) return NBVH_OK;
   if (!hits_valid(hits) || rays.n > (int64_t(1) << 31) - 1) return NBVH_ERR_INVALID_ARG;
   const TriBlasArgs a = tri_args(*blas, rays, hits, nullptr, 0, 0);
+  TimedSection ts(NBVH_KERNEL_TRI_TRACE, as_stream(stream));
   tri_trace_kernel<<<unsigned((rays.n + 127) / 128), 128, 0, as_stream(stream)>>>(a);
   count_launches(1);
   return status_of(cudaGetLastError());
@@ -764,9 +793,13 @@ extern "C" nbvh_status nbvh_hybrid_trace(const nbvh_instance* inst, int32_t n_in
   for (int i = 0; i < n_inst; ++i)  // before anything is enqueued
     if (inst[i].kind == NBVH_BLAS_NEURAL && !eval_stageable(&inst[i].desc, o)) return NBVH_ERR_UNSUPPORTED;
   cudaStream_t s = as_stream(stream);
-  hits_clear_kernel<<<unsigned((rays.n + 255) / 256), 256, 0, s>>>(out, out_inst, rays.n);
-  count_launches(1);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e;
+  {
+    TimedSection ts(NBVH_KERNEL_OTHER, s);
+    hits_clear_kernel<<<unsigned((rays.n + 255) / 256), 256, 0, s>>>(out, out_inst, rays.n);
+    count_launches(1);
+    e = cudaGetLastError();
+  }
   if (e != cudaSuccess) return NBVH_ERR_CUDA;
   int32_t culled_from = -1;  // first instance covered by the top-level cull
   std::vector<int32_t> cull_slot(static_cast<size_t>(n_inst), -1);
@@ -774,6 +807,7 @@ extern "C" nbvh_status nbvh_hybrid_trace(const nbvh_instance* inst, int32_t n_in
     const nbvh_instance& x = inst[i];
     if (x.kind == NBVH_BLAS_TRIANGLES) {
       const TriBlasArgs a = tri_args(x.tri, rays, out, out_inst, i, 1);
+      TimedSection ts(NBVH_KERNEL_TRI_TRACE, s);
       tri_trace_kernel<<<unsigned((rays.n + 127) / 128), 128, 0, s>>>(a);
       count_launches(1);
       e = cudaGetLastError();
@@ -797,6 +831,7 @@ extern "C" nbvh_status nbvh_hybrid_trace(const nbvh_instance* inst, int32_t n_in
       }
       c.count = hw.counts;
       c.n_inst = k;
+      TimedSection ts(NBVH_KERNEL_TLAS_CULL, s);
       e = cudaMemsetAsync(hw.counts, 0, sizeof(int32_t) * kMaxInstances, s);
       if (e != cudaSuccess) return NBVH_ERR_CUDA;
       tlas_cull_kernel<<<unsigned((rays.n + 255) / 256), 256, 0, s>>>(ray_ptrs(rays), rays.n, out.t, c);
@@ -810,7 +845,7 @@ extern "C" nbvh_status nbvh_hybrid_trace(const nbvh_instance* inst, int32_t n_in
     if (e != cudaSuccess) return NBVH_ERR_CUDA;
     QueryWs wi = carve_query(workspace, rays.n, x.max_segs, hybrid_image_bytes(inst, n_inst));
     e = launch_query_stages(&x.desc, gps[i], x.table, x.mlp, x.nodes, rays, x.max_segs, out, wi, true, out_inst, i,
-                            o, nullptr, s, hw.lists + size_t(k) * size_t(rays.n), hw.counts + k);
+                            o, s, hw.lists + size_t(k) * size_t(rays.n), hw.counts + k);
     if (e != cudaSuccess) return status_of(e);
   }
   return NBVH_OK;
@@ -1068,6 +1103,7 @@ struct TrainWs {
   uint16_t* dZT0;                    // first layer's dZ, neuron-major
   int64_t ld;                        // row stride of X16 and dZT0
   void* image;                       // streamed first-layer image
+  uint8_t* bwd_image;                // W0^T of the streamed backward (else null)
   int32_t *counts, *cursor, *order;  // rays grouped by trained leaf (training step)
   size_t bytes;
 };
@@ -1121,6 +1157,7 @@ TrainWs carve_train(void* base, const nbvh_model_desc* d, int64_t n, int32_t n_l
     w.H16 = reinterpret_cast<uint16_t*>(take(2 * nh * C * Wd));
     w.dZ16 = reinterpret_cast<uint16_t*>(take(2 * nh * C * Wd));
     w.image = take(image_bytes(d));
+    if (bwd_w0_streamed(int(K), int(Wd), int(nh))) w.bwd_image = reinterpret_cast<uint8_t*>(take(2 * Kp * Wd));
   }
   if (n_leaves > 0) {
     w.counts = reinterpret_cast<int32_t*>(take(4 * size_t(n_leaves)));
@@ -1154,7 +1191,7 @@ bool train_stageable(const nbvh_model_desc* d) {
     return train_fwd_smem(K, W, d->n_hidden, d->n_out) <= kSmemMax &&
            train_bwd_smem(K, W, d->n_hidden, d->n_out) <= kSmemMax;
   if (W != 32 && W != 64 && W != 128) return false;
-  const TcBwdLayout bl = tc_bwd_layout(K, W, d->n_hidden);
+  const TcBwdLayout bl = tc_bwd_layout(K, W, d->n_hidden, bwd_w0_streamed(K, W, d->n_hidden));
   return tc_plan(d, 0, NBVH_W1_AUTO).ok && bl.total <= kSmemMax && bl.ncols <= 512;
 }
 
@@ -1274,6 +1311,7 @@ cudaError_t forward_chunk(const nbvh_model_desc* d, const GridParams& gp, const 
                           const Chunk& k, const Labels& lab, const int32_t* n_valid, float loss_scale,
                           const float* loss_scale_dev, const TrainWs& w, const TcPlan& plan, const void* image,
                           cudaStream_t s) {
+  TimedSection ts(NBVH_KERNEL_TRAIN_FORWARD, s);
   const int no = d->n_out;
   if (d->mlp_prec == NBVH_FP32) {
     TrainArgs a;
@@ -1342,8 +1380,15 @@ cudaError_t backward_chunk(const nbvh_model_desc* d, const GridParams& gp, const
     b.dZT0 = w.dZT0;
     b.ld = w.ld;
     b.grad_table = grad_table;
-    cudaError_t e = launch_bwd_tc(d, b, s);
+    b.w0t_image = w.bwd_image;
+    cudaError_t e;
+    {
+      TimedSection ts(NBVH_KERNEL_TRAIN_BACKWARD, s);
+      e = w.bwd_image ? launch_bwd_image(d, mlp, w.bwd_image, s) : cudaSuccess;
+      if (e == cudaSuccess) e = launch_bwd_tc(d, b, s);
+    }
     if (e != cudaSuccess) return e;
+    TimedSection ts(NBVH_KERNEL_WEIGHT_GRAD, s);
     return d->mlp_prec == NBVH_BF16 ? weight_grads_16<__nv_bfloat16>(d, w, Gk, k.c, grad_mlp, s)
                                     : weight_grads_16<__half>(d, w, Gk, k.c, grad_mlp, s);
   }
@@ -1362,8 +1407,13 @@ cudaError_t backward_chunk(const nbvh_model_desc* d, const GridParams& gp, const
   a.n = k.c;
   a.buf = TrainBuffers{w.X, w.H, nullptr, const_cast<float*>(Gk), nullptr, w.dZ};
   a.grad_table = grad_table;
-  cudaError_t e = launch_train(true, d, a, s);
+  cudaError_t e;
+  {
+    TimedSection ts(NBVH_KERNEL_TRAIN_BACKWARD, s);
+    e = launch_train(true, d, a, s);
+  }
   if (e != cudaSuccess) return e;
+  TimedSection ts(NBVH_KERNEL_WEIGHT_GRAD, s);
   // weight gradients, parameter order: W0 [W][K], b0, (W_h [W][W], b_h)*, Wo [n_out][W], bo
   const int K = gp.n_inputs, Wd = d->width, nh = d->n_hidden;
   const int64_t c = k.c;
@@ -1386,6 +1436,7 @@ cudaError_t backward_chunk(const nbvh_model_desc* d, const GridParams& gp, const
 cudaError_t launch_loss(const float* term, int64_t n, const int32_t* n_valid, float* partial, float* out,
                         cudaStream_t s) {
   const int blocks = int(std::min<int64_t>(kLossBlocks, std::max<int64_t>(1, (n + 255) / 256)));
+  TimedSection ts(NBVH_KERNEL_OTHER, s);
   loss_partial_kernel<<<blocks, 256, 0, s>>>(term, n, partial);
   loss_final_kernel<<<1, 256, 0, s>>>(partial, blocks, n_valid, out);
   count_launches(2);
@@ -1427,6 +1478,7 @@ extern "C" nbvh_status nbvh_train_rays(int32_t mode, uint64_t seed, int64_t step
   a.t0 = t0;
   a.t1 = t1;
   a.n_valid = n_valid;
+  TimedSection ts(NBVH_KERNEL_TRAIN_RAYS, as_stream(stream));
   train_rays_kernel<<<unsigned((rays.n + 127) / 128), 128, 0, as_stream(stream)>>>(a);
   count_launches(1);
   return status_of(cudaGetLastError());
@@ -1439,6 +1491,7 @@ extern "C" nbvh_status nbvh_train_labels(nbvh_rays rays, const int32_t* leaf, co
   if (!leaf || !t0 || !t1 || !out.hit || !out.depth || !out.nx || !out.ny || !out.nz ||
       (out.ar && (!out.ag || !out.ab)))
     return NBVH_ERR_INVALID_ARG;
+  TimedSection ts(NBVH_KERNEL_LABELS, as_stream(stream));
   labels_kernel<<<unsigned((rays.n + 127) / 128), 128, 0, as_stream(stream)>>>(
       ray_ptrs(rays), leaf, t0, t1, rays.n, scene->tris, scene->tri_perm, scene->leaf_range, scene->leaf_tris,
       nullptr, out.hit, out.depth, out.nx, out.ny, out.nz, scene->tri_albedo, out.ar, out.ag, out.ab);
@@ -1584,6 +1637,7 @@ extern "C" nbvh_status nbvh_adam(const nbvh_model_desc* desc, const nbvh_optim* 
   cudaStream_t s = as_stream(stream);
   AdamState st{opt->loss_scale, opt->counters, opt->counters + 1, opt->counters + 2};
   const unsigned g = unsigned(sm_count()) * 8;
+  TimedSection ts(NBVH_KERNEL_ADAM, s);
   grad_check_kernel<<<g, 256, 0, s>>>(opt->grad_table, nt, st.bad);
   grad_check_kernel<<<g, 256, 0, s>>>(opt->grad_mlp, nm, st.bad);
   const double c1 = 1.0 - std::pow(double(beta1), double(step));
@@ -1640,6 +1694,7 @@ extern "C" nbvh_status nbvh_train_step_weighted(const nbvh_model_desc* desc, con
   if (st != NBVH_OK) return st;
   if (leaf_prob || stats) {  // first-leaf hit counts; trained with the leaf's probability
     const uint64_t st0 = uint64_t(step - 1);
+    TimedSection ts(NBVH_KERNEL_TRAIN_RAYS, s);
     leaf_select_kernel<<<unsigned((batch + 255) / 256), 256, 0, s>>>(
         w.leaf, batch, uint32_t(seed & 0xffffffffu), uint32_t(seed >> 32), uint32_t(st0 & 0xffffffffu),
         uint32_t(st0 >> 32), leaf_prob, stats ? stats->hits : nullptr, w.n_valid);
@@ -1652,14 +1707,21 @@ extern "C" nbvh_status nbvh_train_step_weighted(const nbvh_model_desc* desc, con
   // group the rays by trained leaf: labels share a leaf's triangles per warp,
   // and the forward/backward tiles hold spatially close rays
   const unsigned g = unsigned((batch + 255) / 256);
-  leaf_hist_kernel<<<g, 256, 0, s>>>(w.leaf, batch, w.counts);
-  leaf_scan_kernel<<<1, 1024, 0, s>>>(w.counts, scene->n_leaves, w.cursor);
-  leaf_scatter_kernel<<<g, 256, 0, s>>>(w.leaf, batch, scene->n_leaves, w.cursor, w.order);
-  labels_kernel<<<unsigned((batch + 127) / 128), 128, 0, s>>>(
-      RayPtrs{ri.ox, ri.oy, ri.oz, ri.dx, ri.dy, ri.dz, ri.tmin, ri.tmax}, w.leaf, w.t0, w.t1, batch, scene->tris,
-      scene->tri_perm, scene->leaf_range, scene->leaf_tris, w.order, lab.hit, lab.depth, lab.nx, lab.ny, lab.nz,
-      scene->tri_albedo, lab.ar, lab.ag, lab.ab);
-  count_launches(4);
+  {
+    TimedSection ts(NBVH_KERNEL_TRAIN_RAYS, s);
+    leaf_hist_kernel<<<g, 256, 0, s>>>(w.leaf, batch, w.counts);
+    leaf_scan_kernel<<<1, 1024, 0, s>>>(w.counts, scene->n_leaves, w.cursor);
+    leaf_scatter_kernel<<<g, 256, 0, s>>>(w.leaf, batch, scene->n_leaves, w.cursor, w.order);
+    count_launches(3);
+  }
+  {
+    TimedSection ts(NBVH_KERNEL_LABELS, s);
+    labels_kernel<<<unsigned((batch + 127) / 128), 128, 0, s>>>(
+        RayPtrs{ri.ox, ri.oy, ri.oz, ri.dx, ri.dy, ri.dz, ri.tmin, ri.tmax}, w.leaf, w.t0, w.t1, batch, scene->tris,
+        scene->tri_perm, scene->leaf_range, scene->leaf_tris, w.order, lab.hit, lab.depth, lab.nx, lab.ny, lab.nz,
+        scene->tri_albedo, lab.ar, lab.ag, lab.ab);
+    count_launches(1);
+  }
   if (cudaGetLastError() != cudaSuccess) return NBVH_ERR_CUDA;
   const void* table = opt->table_work ? opt->table_work : opt->table_master;
   const int32_t* order = desc->mlp_prec != NBVH_FP32 ? w.order : nullptr;
@@ -1668,6 +1730,7 @@ extern "C" nbvh_status nbvh_train_step_weighted(const nbvh_model_desc* desc, con
                           scene->n_leaves);
   if (st != NBVH_OK) return st;
   if (stats) {  // per-leaf sums over each leaf's contiguous range of the grouped order
+    TimedSection ts(NBVH_KERNEL_OTHER, s);
     leaf_loss_kernel<<<unsigned((scene->n_leaves + 7) / 8), 256, 0, s>>>(
         w.loss_seg, w.order, order != nullptr ? 1 : 0, w.counts, w.cursor, scene->n_leaves, stats->trained,
         stats->loss);

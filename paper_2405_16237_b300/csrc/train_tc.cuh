@@ -25,18 +25,21 @@ struct TcBwdArgs {
   uint16_t* dZT0;         // [W][ld] the first layer's dZ again, neuron-major (out)
   int64_t ld;
   float* grad_table;      // FP32 [entries][F]
+  const uint8_t* w0t_image;  // W0^T in its shared-memory operand layout, copied
+                             // 128 features at a time (nullptr: staged whole)
 };
 
 // TMEM columns: [0, W) accumulator of dH; [W, W + W/2) the current A operand
 // (dL/dout padded to 16, then dZ); [2W, 2W + 128) a 128-feature chunk of
-// dL/dfeatures. Shared memory: the transposed weights as B operands.
+// dL/dfeatures. Shared memory: the transposed weights as B operands; W0^T
+// whole, or (streamed) one 128-feature chunk of it at a time.
 struct TcBwdLayout {
   int Kp;
   uint32_t col_a, col_x, ncols;
   uint32_t w0t_off, wht_off, wot_off, row_off, u_off, bar_off, total;
 };
 
-__host__ __device__ inline TcBwdLayout tc_bwd_layout(int K, int W, int n_hidden) {
+__host__ __device__ inline TcBwdLayout tc_bwd_layout(int K, int W, int n_hidden, bool streamed) {
   TcBwdLayout L;
   L.Kp = (K + 15) & ~15;
   L.col_a = uint32_t(W);
@@ -50,7 +53,7 @@ __host__ __device__ inline TcBwdLayout tc_bwd_layout(int K, int W, int n_hidden)
     off = (off + bytes + 127u) & ~127u;
     return o;
   };
-  L.w0t_off = take(uint32_t(L.Kp) * W * 2);
+  L.w0t_off = take(uint32_t(streamed ? (L.Kp < 128 ? L.Kp : 128) : L.Kp) * W * 2);
   L.wht_off = take(uint32_t(n_hidden - 1) * W * W * 2);
   L.wot_off = take(uint32_t(W) * 16 * 2);
   L.row_off = take(kTcM * 36);  // ray index, t0, t1, origin, direction per row
@@ -58,6 +61,14 @@ __host__ __device__ inline TcBwdLayout tc_bwd_layout(int K, int W, int n_hidden)
   L.bar_off = take(64);
   L.total = off + 128;
   return L;
+}
+
+constexpr uint32_t kBwdSmemMax = 227u * 1024u;
+
+// Whether the backward streams W0^T: its whole transpose does not fit the
+// shared-memory budget next to the other operands (e.g. K = 2048 at W = 64).
+__host__ __device__ inline bool bwd_w0_streamed(int K, int W, int n_hidden) {
+  return tc_bwd_layout(K, W, n_hidden, false).total > kBwdSmemMax;
 }
 
 // Threads of the backward kernel: 512 lets two CTAs share an SM (2 x 256 TMEM
@@ -74,6 +85,31 @@ __host__ __device__ constexpr int bwd_threads() {
 __host__ __device__ inline bool bwd_level_major(int n_samples, int F) {
   const int nf = n_samples * F;
   return F <= 2 && nf % 16 == 0 && 128 % nf == 0;
+}
+
+// Row r of W0^T (B operand of the dX MMA, K-major, rows = features): the
+// feature of input order k*L*F + l*F + f, permuted level-major
+// (l*N*F + k*F + f) when the scatter walks rays level by level.
+__host__ __device__ inline int bwd_w0_feature(int r, int K, int NS, int L, int F, bool lmaj) {
+  if (!lmaj || r >= K) return r;
+  const int nf = NS * F;
+  const int l = r / nf, rem = r - l * nf;
+  return (rem / F) * (L * F) + l * F + rem % F;
+}
+
+// W0^T of the FP32 master weights in the backward's operand layout, written
+// to global memory once per backward call for the streamed form.
+template <bool BF16>
+__global__ void bwd_w0t_image_kernel(const float* __restrict__ W0, int K, int Kp, int W, int NS, int L, int F,
+                                     uint8_t* __restrict__ img) {
+  using OT = OpType<BF16>;
+  const bool lmaj = bwd_level_major(NS, F);
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < int64_t(Kp) * W;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    const int r = int(i / W), k = int(i - int64_t(r) * W);
+    const float v = r < K ? __ldg(W0 + size_t(k) * K + bwd_w0_feature(r, K, NS, L, F, lmaj)) : 0.0f;
+    *reinterpret_cast<typename OT::T*>(img + op_offset(r, k, W)) = OT::one(v);
+  }
 }
 
 // Adds F gradient values to an FP32 table entry (vector reductions where the
@@ -149,7 +185,8 @@ __global__ void __launch_bounds__(bwd_threads<W>(), 1024 / bwd_threads<W>()) tra
   const int NS = a.gp.n_samples;
   const int nh = a.n_hidden;
   const int n_out = a.n_out;
-  const TcBwdLayout lay = tc_bwd_layout(K, W, nh);
+  const bool streamed = a.w0t_image != nullptr;
+  const TcBwdLayout lay = tc_bwd_layout(K, W, nh, streamed);
   const int Kp = lay.Kp;
   const bool lmaj = bwd_level_major(NS, F);
   uint8_t* sW0t = smem + lay.w0t_off;
@@ -179,16 +216,12 @@ __global__ void __launch_bounds__(bwd_threads<W>(), 1024 / bwd_threads<W>()) tra
   if (threadIdx.x < NS) su[threadIdx.x] = sample_u(threadIdx.x, NS);
   // B operands (K-major, rows = the MMA's N): W0^T [Kp][W], W_h^T [W][W], Wo^T [W][16]
   const float* W0 = a.mlp;
-  for (int i = threadIdx.x; i < Kp * W; i += blockDim.x) {
-    const int r = i / W, k = i - r * W;
-    int f = r;  // feature of row r: input order k*L*F + l*F + f, or level-major l*N*F + k*F + f
-    if (lmaj && r < K) {
-      const int nf = NS * F;
-      const int l = r / nf, rem = r - l * nf;
-      f = (rem / F) * (L * F) + l * F + rem % F;
+  if (!streamed) {
+    for (int i = threadIdx.x; i < Kp * W; i += blockDim.x) {
+      const int r = i / W, k = i - r * W;
+      const float v = r < K ? __ldg(W0 + size_t(k) * K + bwd_w0_feature(r, K, NS, L, F, lmaj)) : 0.0f;
+      *reinterpret_cast<typename OT::T*>(sW0t + op_offset(r, k, W)) = OT::one(v);
     }
-    const float v = r < K ? __ldg(W0 + size_t(k) * K + f) : 0.0f;
-    *reinterpret_cast<typename OT::T*>(sW0t + op_offset(r, k, W)) = OT::one(v);
   }
   const float* p = W0 + size_t(W) * K + W;
   for (int h = 1; h < nh; ++h) {
@@ -325,9 +358,18 @@ __global__ void __launch_bounds__(bwd_threads<W>(), 1024 / bwd_threads<W>()) tra
       const bool valid = ray >= 0;
       for (int c0 = 0; c0 < Kp && !failed; c0 += 128) {
         const int cw = min(128, Kp - c0);
+        if (streamed) {
+          // this chunk's rows of W0^T (contiguous in the operand layout); the
+          // previous chunk's MMA completed before the last barrier
+          const uint4* src = reinterpret_cast<const uint4*>(a.w0t_image + size_t(c0) * W * 2);
+          uint4* dst = reinterpret_cast<uint4*>(sW0t);
+          for (int i = threadIdx.x; i < cw * W / 8; i += blockDim.x) dst[i] = __ldg(src + i);
+          fence_proxy_async_smem();
+          __syncthreads();
+        }
         if (threadIdx.x == 0) {
           tc_fence_after();
-          const uint32_t wb = smem_u32(sW0t) + uint32_t(c0 / 8) * uint32_t(W) * 16;
+          const uint32_t wb = smem_u32(sW0t) + (streamed ? 0u : uint32_t(c0 / 8) * uint32_t(W) * 16);
           for (int j = 0; j < W / 16; ++j)
             mma_f16_ts(tmem + lay.col_x, tmem + lay.col_a + uint32_t(8 * j),
                        smem_desc(wb + j * 256, 128, uint32_t(W) * 16), idesc_f16(BF16, kTcM, cw), j > 0);

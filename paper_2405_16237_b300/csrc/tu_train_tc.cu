@@ -6,8 +6,8 @@ namespace nbvh {
 namespace {
 template <int F, int W>
 cudaError_t launch_bwd_tc_fw(bool bf16, const TcBwdArgs& a, cudaStream_t s) {
-  const TcBwdLayout lay = tc_bwd_layout(a.gp.n_inputs, W, a.n_hidden);
-  if (lay.total > 227 * 1024 || lay.ncols > 512) return cudaErrorInvalidConfiguration;
+  const TcBwdLayout lay = tc_bwd_layout(a.gp.n_inputs, W, a.n_hidden, a.w0t_image != nullptr);
+  if (lay.total > kBwdSmemMax || lay.ncols > 512) return cudaErrorInvalidConfiguration;
   auto kern = bf16 ? train_backward_tc<F, W, true> : train_backward_tc<F, W, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(lay.total));
   if (e != cudaSuccess) return e;
@@ -38,6 +38,20 @@ cudaError_t launch_bwd_tc_f(bool bf16, int W, const TcBwdArgs& a, cudaStream_t s
 }
 
 }  // namespace
+
+cudaError_t launch_bwd_image(const nbvh_model_desc* d, const float* mlp, uint8_t* img, cudaStream_t s) {
+  const int K = d->n_samples * d->n_levels * d->n_features, Kp = (K + 15) & ~15;
+  const int64_t n = int64_t(Kp) * d->width;
+  const int blocks = int(std::min<int64_t>((n + 255) / 256, int64_t(sm_count()) * 4));
+  if (d->mlp_prec == NBVH_BF16)
+    bwd_w0t_image_kernel<true><<<blocks, 256, 0, s>>>(mlp, K, Kp, d->width, d->n_samples, d->n_levels,
+                                                      d->n_features, img);
+  else
+    bwd_w0t_image_kernel<false><<<blocks, 256, 0, s>>>(mlp, K, Kp, d->width, d->n_samples, d->n_levels,
+                                                       d->n_features, img);
+  count_launches(1);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_bwd_tc(const nbvh_model_desc* d, const TcBwdArgs& a, cudaStream_t s) {
   const bool bf16 = d->mlp_prec == NBVH_BF16;

@@ -148,7 +148,7 @@ _SIGS = {
                                       POINTER(c_int32), c_void_p]),
     "nbvh_query_stats": (c_int32, [c_void_p, c_int64, c_int32, POINTER(c_int64), POINTER(c_int32), c_void_p]),
     "nbvh_set_timing": (c_int32, [c_int32]),
-    "nbvh_get_timing": (c_int32, [POINTER(c_double), POINTER(c_double), POINTER(c_int64)]),
+    "nbvh_get_kernel_times": (c_int32, [POINTER(c_double), POINTER(c_int64), POINTER(c_int64), c_int32]),
     "nbvh_launch_count": (c_int64, []),
     "nbvh_query_rays_static": (c_int32, [POINTER(ModelDesc), c_void_p, c_void_p, c_void_p, c_int32, Rays, c_int32,
                                          Hits, c_void_p]),
@@ -562,10 +562,20 @@ def set_timing(enable: bool):
     _check(lib().nbvh_set_timing(1 if enable else 0), "set_timing")
 
 
-def get_timing():
-    a, b, c = c_double(), c_double(), c_int64()
-    _check(lib().nbvh_get_timing(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "get_timing")
-    return a.value, b.value, c.value
+# kernel classes of the library's timing (NBVH_KERNEL_* in the header)
+KERNEL_KINDS = ("traverse", "eval", "tri_trace", "tlas_cull", "bounce", "train_rays", "labels", "train_forward",
+                "train_backward", "weight_grad", "adam", "other")
+
+
+def get_kernel_times() -> dict:
+    """Per kernel class, since the previous call: summed milliseconds of the
+    timed groups, the number of groups and the kernels they launched."""
+    n = len(KERNEL_KINDS)
+    ms = (c_double * n)()
+    sec = (c_int64 * n)()
+    lau = (c_int64 * n)()
+    _check(lib().nbvh_get_kernel_times(ms, sec, lau, n), "get_kernel_times")
+    return {k: {"ms": ms[i], "groups": int(sec[i]), "launches": int(lau[i])} for i, k in enumerate(KERNEL_KINDS)}
 
 
 def launch_count() -> int:

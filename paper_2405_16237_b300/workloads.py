@@ -402,10 +402,10 @@ def scene_hybrid(n_assets: int = 16, seed: int = SEED_BASE + 4, asset_level: int
                  n_leaves: int = 128):
     """Neural assets on a classical ground. Each asset is a displaced icosphere
     (20 * 4^asset_level triangles, radius U(0.10, 0.18)) standing on the
-    ground at a jittered 4x4 grid position; its model draws F in {2, 4, 8}
-    and log2 T in {16, ..., 22} (seeded), with n_levels = 32 / F so that
-    N * L * F stays 16 * 32 = 512, base resolution 16 and growth reaching a
-    finest resolution of 1024 (the paper's 8 levels up to 1024 at F = 4).
+    ground at a jittered 4x4 grid position; its model is the icosphere
+    workload's (16 levels, base resolution 16, growth 1.5, 16 samples, a 3x64
+    MLP) with F drawn from {2, 4, 8} and log2 T from {16, ..., 22} (seeded):
+    N * L * F = 512, 1024 or 2048 first-layer inputs.
     Returns (ground triangles, [HybridAsset])."""
     rng = np.random.default_rng(seed)
     ground = ground_heightfield(ground_cells)
@@ -420,11 +420,7 @@ def scene_hybrid(n_assets: int = 16, seed: int = SEED_BASE + 4, asset_level: int
         tris = tris + np.array([cx, -0.35 + r, cz], np.float32)
         F = int(rng.choice([2, 4, 8]))
         lt = int(rng.integers(16, 23))
-        L = 32 // F
-        # the model descriptor stores the growth factor as float32: use a
-        # float32 value so every consumer derives the same level resolutions
-        growth = float(np.float32((1024.0 / 16.0) ** (1.0 / (L - 1))))
-        model = ModelConfig(n_levels=L, n_features=F, log2_table=lt, base_res=16, growth=growth, n_samples=16,
+        model = ModelConfig(n_levels=16, n_features=F, log2_table=lt, base_res=16, growth=1.5, n_samples=16,
                             n_hidden=3, width=64)
         assets.append(HybridAsset(tris.astype(np.float32), model, n_leaves))
     return ground, assets

@@ -139,8 +139,10 @@ def test_levels_of_detail():
     segs = []
     for leaves, _ in (lods[0], lods[-1]):
         ws = B.new_workspace(B.query_workspace_size(desc, 4000, 40))
+        # one launch per segment slot: the count is the early-out's, free of
+        # the persistent schedule's lookahead evaluations
         B.query_rays(desc, opt.table, opt.mlp, torch.as_tensor(leaves["nodes"]).cuda(), leaves["n_nodes"], rays, 40,
-                     workspace=ws)
+                     workspace=ws, options=B.query_options(schedule=B.SCHEDULE_WAVES))
         segs.append(B.query_stats(ws, 4000, 40)[0])
     assert B.device_status() == 0
     assert segs[0] < segs[1]

@@ -299,14 +299,19 @@ def test_full_size_persistent_equals_waves():
     hw = B.query_rays(desc, table, mlp, nodes, leaves["n_nodes"], rays, 48, workspace=ws,
                       options=B.query_options(schedule=B.SCHEDULE_WAVES))
     segs_w, waves = B.query_stats(ws, n, 48)
-    hp = B.query_rays(desc, table, mlp, nodes, leaves["n_nodes"], rays, 48, workspace=ws,
-                      options=B.query_options(schedule=B.SCHEDULE_PERSISTENT))
-    segs_p, launches = B.query_stats(ws, n, 48)
-    assert B.device_status() == 0
-    assert n == 2073600 and launches == 1 and waves > 3 and segs_p == segs_w > n // 8
-    assert int(hw["hit"].sum()) > 100000
-    for k in hw:
-        assert torch.equal(hw[k], hp[k]), k
+    for pipe in (B.PIPELINE_PHASES, B.PIPELINE_WARP_SPECIALISED):
+        hp = B.query_rays(desc, table, mlp, nodes, leaves["n_nodes"], rays, 48, workspace=ws,
+                          options=B.query_options(schedule=B.SCHEDULE_PERSISTENT, eval_pipeline=pipe))
+        segs_p, launches = B.query_stats(ws, n, 48)
+        assert B.device_status() == 0
+        assert n == 2073600 and launches == 1 and waves > 3 and segs_w > n // 8
+        # lookahead rows evaluate a ray's later segments before its earlier
+        # ones resolve, so the persistent schedule may evaluate segments that
+        # the waves skip, never fewer
+        assert segs_p >= segs_w
+        assert int(hw["hit"].sum()) > 100000
+        for k in hw:
+            assert torch.equal(hw[k], hp[k]), (pipe, k)
 
 
 def test_query_workspace_too_small():
@@ -343,6 +348,49 @@ def test_bounce_rays_parity():
     assert np.max(np.abs(gd - dirs)) <= 2e-6
     assert np.all(got["tmin"][h] == 0) and np.all(np.isinf(got["tmax"][h]))
     assert np.all(got["tmax"][~h] == -1.0)
+
+
+def test_kernel_class_timing():
+    """While timing is on, each eager query records one traversal and one
+    evaluation group (the persistent schedule: the queue set-up and the one
+    evaluation launch) and each bounce one group, all with positive device
+    time; a graph recording records nothing; with timing off nothing is
+    recorded."""
+    torch = _torch()
+    b = built("icosphere_l6", 1.0, 2.0)
+    desc = b.with_prec(B.FP16)
+    n = b.rays["ox"].numel()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ws = B.new_workspace(B.query_workspace_size(desc, n, 16))
+        out = B.new_hits(n)
+        rays2 = B.new_rays(n)
+
+        def step():
+            B.query_rays(desc, b.table, b.mlp, b.nodes, b.leaves["n_nodes"], b.rays, 16, out=out, workspace=ws)
+            B.bounce_rays(b.rays, out, 5, out=rays2)
+
+        B.get_kernel_times()
+        B.set_timing(True)
+        try:
+            for _ in range(3):
+                step()
+            t = B.get_kernel_times()
+            g = B.Graph.record(step)
+            g.launch()
+            s.synchronize()
+            g.destroy()
+            t_graph = B.get_kernel_times()
+        finally:
+            B.set_timing(False)
+        step()
+        t_off = B.get_kernel_times()
+    assert B.device_status() == 0
+    for k in ("traverse", "eval", "bounce"):
+        assert t[k]["groups"] == 3 and t[k]["ms"] > 0.0, (k, t[k])
+    assert t["traverse"]["launches"] == 3 and t["bounce"]["launches"] == 3
+    assert t["eval"]["launches"] >= 6  # per query: queue set-up + the persistent evaluation (+ W1 image)
+    assert all(v["groups"] == 0 for v in t_graph.values()) and all(v["groups"] == 0 for v in t_off.values())
 
 
 def test_graph_replay_equals_eager_query():
@@ -384,10 +432,13 @@ def test_graph_replay_equals_eager_query():
 
 @pytest.mark.parametrize("mp", [B.FP16, B.BF16])
 @pytest.mark.parametrize("patience", [0, 4000, 1 << 30])
-def test_persistent_schedule_equals_waves(mp, patience):
+@pytest.mark.parametrize("pipeline", [B.PIPELINE_PHASES, B.PIPELINE_WARP_SPECIALISED])
+def test_persistent_schedule_equals_waves(mp, patience, pipeline):
     """The persistent queue (one launch, tiles claimed as resolves refill the
-    queue; patience from eager partial tiles to waiting until drained) gives
-    bit-identical hit records to one launch per segment slot."""
+    queue; patience from eager partial tiles, which take lookahead rows, to
+    waiting until drained), in the phase kernel and in the warp-specialised
+    pipeline, gives bit-identical hit records to one launch per segment
+    slot."""
     torch = _torch()
     b = built("icosphere_l6", 1.0, 2.0)
     rays = B.to_device_rays(W.mixed_rays(6000, seed=W.SEED_BASE + 31, radius=0.6))
@@ -396,7 +447,8 @@ def test_persistent_schedule_equals_waves(mp, patience):
                       options=B.query_options(schedule=B.SCHEDULE_WAVES))
     ws = B.new_workspace(B.query_workspace_size(desc, rays["ox"].numel(), 24))
     hp = B.query_rays(desc, b.table, b.mlp, b.nodes, b.leaves["n_nodes"], rays, 24, workspace=ws,
-                      options=B.query_options(schedule=B.SCHEDULE_PERSISTENT, patience_cycles=patience))
+                      options=B.query_options(schedule=B.SCHEDULE_PERSISTENT, patience_cycles=patience,
+                                              eval_pipeline=pipeline))
     segs, launches = B.query_stats(ws, rays["ox"].numel(), 24)
     assert B.device_status() == 0
     for k in hw:

@@ -450,14 +450,15 @@ def c1_built(scale=0.5, gain=2.0):
 def _decided_rays(b, h, mp, tau=1e-3):
     """Rays whose gradient no rounding-level difference can change by a
     discrete step: every hidden pre-activation of the oracle's reduced-
-    precision model (16-bit operands, float32 positions) lies more than tau
+    precision model (16-bit operands, float32 positions and grid
+    coordinates) lies more than tau
     times its layer's RMS from zero (a ReLU mask flip moves the ray's whole
     contribution) and the depth and normal L1 terms lie more than tau from
     their kinks."""
     fr = b.oleaves["frame"]
     x = O.sample_grid_f32(h["o"], h["d"], h["t0"], h["t1"], b.case.model.n_samples, fr["model_centre"],
                           fr["model_extent"])
-    raw, _, pre = O.mlp_forward(O.encode(x, b.table_host, b.olayout), b.layers, _half_round(mp))
+    raw, _, pre = O.mlp_forward(O.encode(x, b.table_host, b.olayout, f32=True), b.layers, _half_round(mp))
     v = h["valid"].copy()
     for z in pre[:-1]:
         rms = np.sqrt(np.mean(z[v] ** 2))
@@ -488,12 +489,7 @@ def test_benchmarked_model_forward_and_gradients_match_oracle(mp):
     desc = b.with_prec(mp)
     dv, h = _batch(b, n=2500, seed=91)
     if mp != B.FP32:
-        keep = _decided_rays(b, h, mp)
-        assert keep.sum() > 0.7 * h["valid"].sum()
-        leaf = np.where(keep, h["leaf"], -1).astype(np.int32)
-        h = dict(h, leaf=leaf, valid=keep)
-        dv = dict(dv, leaf=torch.as_tensor(leaf).cuda(),
-                  n_valid=torch.tensor([int(keep.sum())], dtype=torch.int32, device="cuda"))
+        dv, h = _keep_decided(torch, b, dv, h, mp)
     n = len(h["leaf"])
     ws = B.new_workspace(B.train_workspace_size(desc, n))
     scale = 1.0 if mp == B.FP32 else 1024.0
@@ -504,7 +500,6 @@ def test_benchmarked_model_forward_and_gradients_match_oracle(mp):
     g_mlp = torch.zeros_like(b.mlp)
     B.backward(desc, b.table, b.mlp, dv["rays"], dv["leaf"], dv["t0"], dv["t1"], ws, g_tab, g_mlp)
     assert B.device_status() == 0
-    fr = b.oleaves["frame"]
     v = h["valid"]
     assert v.sum() > 500
     if mp == B.FP32:
@@ -518,8 +513,16 @@ def test_benchmarked_model_forward_and_gradients_match_oracle(mp):
         ref_m = B.pack_mlp([(dw, db) for dw, db in ref_layers])
         assert np.max(np.abs(g_mlp.cpu().numpy() - ref_m)) <= 1e-5 * np.max(np.abs(ref_m))
         return
-    _, ref_tab, ref_layers, _ = O.forward_backward(h["o"], h["d"], h["t0"], h["t1"], v, h["yh"], h["yd"], h["yn"],
-                                                   b.table_host, b.layers, b.olayout, fr["model_centre"],
+    _check_half_grads(b, mp, h, g_tab, g_mlp, scale)
+
+
+def _check_half_grads(b, mp, h, g_tab, g_mlp, scale):
+    """Table and MLP gradients against the oracle run with the same 16-bit
+    operand rounding, loss scale and float32 sample positions, on the rays
+    h["valid"] keeps."""
+    fr = b.oleaves["frame"]
+    _, ref_tab, ref_layers, _ = O.forward_backward(h["o"], h["d"], h["t0"], h["t1"], h["valid"], h["yh"], h["yd"],
+                                                   h["yn"], b.table_host, b.layers, b.olayout, fr["model_centre"],
                                                    fr["model_extent"], b.case.model.n_samples,
                                                    rnd=_half_round(mp), scale=scale, positions="f32")
     gt, rt = g_tab.cpu().numpy().ravel() / scale, ref_tab.ravel()
@@ -530,6 +533,50 @@ def test_benchmarked_model_forward_and_gradients_match_oracle(mp):
     stats = (np.median(et), np.percentile(et, 90), l2t, np.median(em), l2m)
     assert np.median(et) <= 1e-4 and np.percentile(et, 90) <= 1e-3 and l2t <= 1e-2, stats
     assert np.median(em) <= 1e-3 and l2m <= 1e-2, stats
+
+
+def _keep_decided(torch, b, dv, h, mp):
+    keep = _decided_rays(b, h, mp)
+    assert keep.sum() > 0.7 * h["valid"].sum()
+    leaf = np.where(keep, h["leaf"], -1).astype(np.int32)
+    return (dict(dv, leaf=torch.as_tensor(leaf).cuda(),
+                 n_valid=torch.tensor([int(keep.sum())], dtype=torch.int32, device="cuda")),
+            dict(h, leaf=leaf, valid=keep))
+
+
+_WIDE = {}
+
+
+@pytest.mark.parametrize("mp", [B.FP16, B.BF16])
+@pytest.mark.parametrize("n_features", [4, 8])
+def test_wide_first_layer_training_matches_half_precision_oracle(n_features, mp):
+    """16 levels x 16 samples x F = 4 or 8 features (K = 1024 or 2048 inputs,
+    the wide assets of the hybrid scene) at width 64: the tensor-core forward
+    (first layer in K chunks) and backward (K = 2048: W0^T does not fit
+    shared memory whole and is copied in 128-feature chunks from a global
+    image; K = 1024: staged whole) against the oracle run with the same
+    16-bit rounding, on the rays whose gradient is decided. Same bounds as
+    the benchmarked-model test."""
+    from dataclasses import replace
+    torch = _torch()
+    if n_features not in _WIDE:
+        base = make_case("icosphere_l6", 0.5, 2.0)
+        _WIDE[n_features] = Built(replace(base, model=replace(base.model, n_features=n_features, log2_table=15)))
+    b = _WIDE[n_features]
+    desc = b.with_prec(mp)
+    dv, h = _batch(b, n=2500, seed=97)
+    dv, h = _keep_decided(torch, b, dv, h, mp)
+    assert h["valid"].sum() > 500
+    n = len(h["leaf"])
+    ws = B.new_workspace(B.train_workspace_size(desc, n))
+    scale = 1024.0
+    B.forward_train(desc, b.table, b.mlp, dv["rays"], dv["leaf"], dv["t0"], dv["t1"], ws, labels=dv["lab"],
+                    n_valid=dv["n_valid"], loss_scale=scale)
+    g_tab = torch.zeros((b.layout["total"], n_features), dtype=torch.float32, device="cuda")
+    g_mlp = torch.zeros_like(b.mlp)
+    B.backward(desc, b.table, b.mlp, dv["rays"], dv["leaf"], dv["t0"], dv["t1"], ws, g_tab, g_mlp)
+    assert B.device_status() == 0
+    _check_half_grads(b, mp, h, g_tab, g_mlp, scale)
 
 
 @pytest.mark.parametrize("mp", [B.FP32, B.FP16])
