@@ -235,7 +235,12 @@ nbvh_status nbvh_encode(const nbvh_model_desc* desc, const void* table, nbvh_ray
  *                   writes, so the waits for them run out; the query then
  *                   returns with NBVH_ERR_TIMEOUT in the device status (it
  *                   never traps or spins unbounded) and the records of the
- *                   rays are not defined. */
+ *                   rays are not defined.
+ *  segments_out     statistics, nullptr = none: device int64 array to which
+ *                   the call adds, on its stream and without synchronising,
+ *                   the segments it evaluated (nbvh_query_rays: entry 0;
+ *                   nbvh_hybrid_trace: entry i for neural instance i). One
+ *                   extra one-block launch per evaluation. */
 #define NBVH_SCHEDULE_WAVES 0
 #define NBVH_SCHEDULE_PERSISTENT 1
 #define NBVH_W1_AUTO 0
@@ -253,6 +258,7 @@ typedef struct {
   int32_t eval_pipeline;
   int64_t wait_spins;
   int32_t test_phantom_items;
+  int64_t* segments_out;
 } nbvh_query_options;
 
 /* Host. The defaults: persistent schedule, patience 4000 cycles, traversal
@@ -749,6 +755,17 @@ nbvh_status nbvh_hybrid_trace(const nbvh_instance* inst, int32_t n_inst, nbvh_ra
  * kernel may write. */
 nbvh_status nbvh_probe_l2_gather(const void* table, int64_t n_entries, uint32_t* sink, double* gsectors_per_s,
                                  void* stream);
+
+/* Device (synchronises). Measurement utility, no counterpart in the paper:
+ * the L2 reduction ceiling that bounds the training backward's table-
+ * gradient scatter when the gradient buffer is L2-resident. One CTA of 1,024
+ * threads per SM issues fire-and-forget float2 atomic adds (8 bytes each,
+ * the scatter's update at F = 2) at pseudo-random entries of grad
+ * (n_entries float2 entries, a power of two in [1024, 2^30]; device memory
+ * the caller owns; each add puts 1e-30 into both floats of an entry), 16 per
+ * thread per round. *gops_per_s receives the best of three timed launches
+ * in 1e9 atomic adds per second. */
+nbvh_status nbvh_probe_l2_reduce(float* grad, int64_t n_entries, double* gops_per_s, void* stream);
 
 /* Device. Reads and clears the device status word (synchronises the stream). */
 nbvh_status nbvh_get_device_status(void* stream);

@@ -341,6 +341,19 @@ PQueue pq_of(const QueryWs& w, int32_t max_segs, int64_t patience, int64_t spin_
   return q;
 }
 
+// Adds a query's evaluated segments to *out: the per-wave counts, or the
+// persistent queue's queued items plus its lookahead rows (statistics).
+__global__ void segments_add_kernel(const int32_t* wave_counts, int32_t n_waves, const unsigned long long* reserved,
+                                    const unsigned long long* lookahead, long long* out) {
+  long long v = 0;
+  for (int i = threadIdx.x; i < n_waves; i += 32) v += wave_counts[i];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (threadIdx.x == 0) {
+    if (reserved) v += (long long)(*reserved + *lookahead);
+    atomicAdd(reinterpret_cast<unsigned long long*>(out), (unsigned long long)v);
+  }
+}
+
 // Traversal (S1) then the evaluation (S2..S5) on the carved query workspace:
 // one wave per segment slot (FP32 form) or one persistent launch (FP16/BF16).
 // merge: the hit record holds the closest hit so far (hybrid hierarchy) and
@@ -409,18 +422,26 @@ cudaError_t launch_query_stages(const nbvh_model_desc* desc, const GridParams& g
     count_launches(1);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return ws ? launch_ws(desc, a, s) : launch_eval<1>(desc, a, rays.n, plan, s);
+    e = ws ? launch_ws(desc, a, s) : launch_eval<1>(desc, a, rays.n, plan, s);
+  } else {
+    for (int wv = 0; wv < max_segs; ++wv) {
+      a.wave = wv;
+      a.queue = w.queue[wv & 1];
+      a.qlen = w.counters + wv;
+      a.next_queue = w.queue[(wv + 1) & 1];
+      a.next_qlen = w.counters + wv + 1;
+      e = launch_eval<1>(desc, a, rays.n, plan, s);
+      if (e != cudaSuccess) return e;
+    }
   }
-  for (int wv = 0; wv < max_segs; ++wv) {
-    a.wave = wv;
-    a.queue = w.queue[wv & 1];
-    a.qlen = w.counters + wv;
-    a.next_queue = w.queue[(wv + 1) & 1];
-    a.next_qlen = w.counters + wv + 1;
-    e = launch_eval<1>(desc, a, rays.n, plan, s);
-    if (e != cudaSuccess) return e;
+  if (e == cudaSuccess && o.segments_out) {
+    segments_add_kernel<<<1, 32, 0, s>>>(w.counters, persistent ? 0 : max_segs, persistent ? a.pq.reserved : nullptr,
+                                         persistent ? a.pq.lookahead : nullptr,
+                                         reinterpret_cast<long long*>(o.segments_out));
+    count_launches(1);
+    e = cudaGetLastError();
   }
-  return cudaSuccess;
+  return e;
 }
 }  // namespace
 }  // namespace nbvh
@@ -844,8 +865,10 @@ extern "C" nbvh_status nbvh_hybrid_trace(const nbvh_instance* inst, int32_t n_in
     e = cudaMemsetAsync(hw.q.counters, 0, counters_bytes(x.max_segs), s);
     if (e != cudaSuccess) return NBVH_ERR_CUDA;
     QueryWs wi = carve_query(workspace, rays.n, x.max_segs, hybrid_image_bytes(inst, n_inst));
+    nbvh_query_options oi = o;
+    if (o.segments_out) oi.segments_out = o.segments_out + i;
     e = launch_query_stages(&x.desc, gps[i], x.table, x.mlp, x.nodes, rays, x.max_segs, out, wi, true, out_inst, i,
-                            o, s, hw.lists + size_t(k) * size_t(rays.n), hw.counts + k);
+                            oi, s, hw.lists + size_t(k) * size_t(rays.n), hw.counts + k);
     if (e != cudaSuccess) return status_of(e);
   }
   return NBVH_OK;
@@ -991,6 +1014,41 @@ extern "C" nbvh_status nbvh_probe_l2_gather(const void* table, int64_t n_entries
   if (st != NBVH_OK) return st;
   const double loads = double(blocks) * threads * iters * kProbeLoads;
   *gsectors_per_s = loads / (double(best) * 1e-3) / 1e9;
+  return NBVH_OK;
+}
+
+extern "C" nbvh_status nbvh_probe_l2_reduce(float* grad, int64_t n_entries, double* gops_per_s, void* stream) {
+  if (!grad || !gops_per_s || n_entries < 1024 || n_entries > (int64_t(1) << 30) ||
+      (n_entries & (n_entries - 1)) != 0 || (reinterpret_cast<uintptr_t>(grad) & 7) != 0)
+    return NBVH_ERR_INVALID_ARG;
+  cudaStream_t s = as_stream(stream);
+  const uint32_t mask = uint32_t(n_entries - 1);
+  const int blocks = sm_count(), threads = 1024, iters = 50;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return NBVH_ERR_CUDA;
+  }
+  nbvh_status st = NBVH_OK;
+  float best = 0.0f;
+  for (int rep = 0; rep < 4 && st == NBVH_OK; ++rep) {  // the first launch brings the buffer into L2
+    cudaEventRecord(e0, s);
+    probe_reduce_kernel<<<blocks, threads, 0, s>>>(reinterpret_cast<float2*>(grad), mask, iters);
+    count_launches(1);
+    cudaEventRecord(e1, s);
+    if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+      st = NBVH_ERR_CUDA;
+      break;
+    }
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && (best == 0.0f || ms < best)) best = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != NBVH_OK) return st;
+  const double ops = double(blocks) * threads * iters * kProbeLoads;
+  *gops_per_s = ops / (double(best) * 1e-3) / 1e9;
   return NBVH_OK;
 }
 

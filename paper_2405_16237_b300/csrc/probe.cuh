@@ -33,4 +33,20 @@ static __global__ void __launch_bounds__(1024) probe_gather_kernel(const uint32_
   if (acc == 0x9e3779b9u) sink[0] = acc;  // keeps the loads; practically never stores
 }
 
+// kProbeLoads fire-and-forget float2 atomic adds per thread per iteration at
+// pseudo-random entries (n_entries a power of two): the form of the training
+// backward's table-gradient updates at F = 2.
+static __global__ void __launch_bounds__(1024) probe_reduce_kernel(float2* __restrict__ grad, uint32_t mask,
+                                                                   int iters) {
+  uint32_t s = probe_mix(blockIdx.x * blockDim.x + threadIdx.x + 777u);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int u = 0; u < kProbeLoads; ++u) {
+      const uint32_t h = probe_mix(s + u * 0x9e3779b9u);
+      atomicAdd(grad + (h & mask), make_float2(1e-30f, 1e-30f));
+    }
+    s = probe_mix(s + 0x85ebca6bu);
+  }
+}
+
 }  // namespace nbvh

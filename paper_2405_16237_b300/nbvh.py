@@ -97,7 +97,7 @@ class LeafStats(ctypes.Structure):
 class QueryOptions(ctypes.Structure):
     _fields_ = [("schedule", c_int32), ("patience_cycles", c_int64), ("traverse_block", c_int32),
                 ("eval_threads", c_int32), ("w1_mode", c_int32), ("eval_pipeline", c_int32),
-                ("wait_spins", c_int64), ("test_phantom_items", c_int32)]
+                ("wait_spins", c_int64), ("test_phantom_items", c_int32), ("segments_out", c_void_p)]
 
 
 class TuneResult(ctypes.Structure):
@@ -188,6 +188,7 @@ _SIGS = {
     "nbvh_hybrid_trace": (c_int32, [POINTER(Instance), c_int32, Rays, Hits, c_void_p, c_void_p, c_size_t,
                                     POINTER(QueryOptions), c_void_p]),
     "nbvh_probe_l2_gather": (c_int32, [c_void_p, c_int64, c_void_p, POINTER(c_double), c_void_p]),
+    "nbvh_probe_l2_reduce": (c_int32, [c_void_p, c_int64, POINTER(c_double), c_void_p]),
     "nbvh_get_device_status": (c_int32, [c_void_p]),
 }
 
@@ -294,6 +295,22 @@ def pack_mlp(layers) -> np.ndarray:
     """Flatten [(W [out,in], b [out])] into the library's float parameter order."""
     return np.concatenate([np.concatenate([np.asarray(w, np.float32).ravel(), np.asarray(b, np.float32)])
                            for w, b in layers]).astype(np.float32)
+
+
+def unpack_mlp(flat, dims):
+    """The library's flat parameter order back to [(W [out, in], b [out])]
+    float32 arrays (the inverse of pack_mlp)."""
+    flat = np.asarray(flat, np.float32)
+    layers, off = [], 0
+    for i in range(len(dims) - 1):
+        w = flat[off:off + dims[i + 1] * dims[i]].reshape(dims[i + 1], dims[i])
+        off += dims[i + 1] * dims[i]
+        b = flat[off:off + dims[i + 1]]
+        off += dims[i + 1]
+        layers.append((w.copy(), b.copy()))
+    if off != len(flat):
+        raise ValueError("parameter count does not match the layer sizes")
+    return layers
 
 
 # ---------------------------------------------------------------- leaf build (host)
@@ -454,10 +471,14 @@ PIPELINES = ("auto", "phases", "warp_specialised")
 
 def query_options(**kw) -> QueryOptions:
     """nbvh_query_options_default with the given fields replaced (schedule,
-    patience_cycles, traverse_block, eval_threads, w1_mode)."""
+    patience_cycles, traverse_block, eval_threads, w1_mode, eval_pipeline,
+    wait_spins, test_phantom_items; segments_out: a device int64 tensor)."""
     o = QueryOptions()
     _check(lib().nbvh_query_options_default(ctypes.byref(o)), "query_options_default")
     for k, v in kw.items():
+        if k == "segments_out" and v is not None and not isinstance(v, int):
+            assert v.dtype == _torch().int64 and v.is_cuda and v.is_contiguous()
+            v = v.data_ptr()
         setattr(o, k, v)
     return o
 
@@ -926,6 +947,16 @@ def probe_l2_gather(n_entries: int = 1 << 24) -> float:
     g = c_double()
     _check(lib().nbvh_probe_l2_gather(_ptr(tab), n_entries, _ptr(sink), ctypes.byref(g), _stream()),
            "probe_l2_gather")
+    return g.value
+
+
+def probe_l2_reduce(n_entries: int = 1 << 23) -> float:
+    """nbvh_probe_l2_reduce: the L2 float2 atomic-add ceiling in 1e9 adds/s
+    (a measurement utility for the table-gradient scatter's roofline)."""
+    torch = _torch()
+    grad = torch.zeros(2 * n_entries, dtype=torch.float32, device="cuda")
+    g = c_double()
+    _check(lib().nbvh_probe_l2_reduce(_ptr(grad), n_entries, ctypes.byref(g), _stream()), "probe_l2_reduce")
     return g.value
 
 

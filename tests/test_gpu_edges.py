@@ -253,3 +253,21 @@ def test_queue_wait_runs_out_and_reports_timeout():
     assert B.device_status() == 0
     for k in ref:
         assert torch.equal(ref[k], again[k]), k
+
+
+def test_l2_probes_measure_and_reject_bad_sizes():
+    """The two measurement utilities return plausible positive rates (random
+    4-byte loads and float2 atomic adds on an L2-resident buffer: between
+    1e9 and 1e13 per second) and refuse sizes that are not powers of two
+    before launching anything."""
+    import ctypes
+    torch = _torch()
+    g = B.probe_l2_gather(1 << 24)
+    r = B.probe_l2_reduce(1 << 23)
+    assert B.device_status() == 0
+    assert 1.0 < g < 1e4 and 1.0 < r < 1e4, (g, r)
+    buf = torch.zeros(1 << 12, dtype=torch.float32, device="cuda")
+    out = ctypes.c_double()
+    n0 = B.launch_count()
+    st = B.lib().nbvh_probe_l2_reduce(ctypes.c_void_p(buf.data_ptr()), 1000, ctypes.byref(out), None)
+    assert st == 1 and B.launch_count() == n0  # NBVH_ERR_INVALID_ARG

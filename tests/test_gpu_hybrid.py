@@ -103,20 +103,34 @@ def test_hybrid_trace_tensor_core_matches_oracle(mp):
     assert np.degrees(np.arccos(c)).mean() <= 1.0
 
 
-def test_hybrid_single_instance_reduces_to_its_query():
+@pytest.mark.parametrize("schedule", [0, 1])
+def test_hybrid_single_instance_reduces_to_its_query(schedule):
     """One neural instance alone: the hybrid trace equals nbvh_query_rays bit
-    for bit (the merge pass starts from an empty record)."""
+    for bit (the merge pass starts from an empty record), and under either
+    schedule the query adds to segments_out the count nbvh_query_stats reads
+    back (the waves schedule: the hybrid trace adds the same count)."""
     torch = _torch()
     ground, assets = small_hybrid_scene(1)
     hb = HybridBuilt(ground, assets, B.BF16, table_prec=B.BF16)
     rays = B.to_device_rays(hybrid_rays(40, 800))
+    n = rays["ox"].numel()
     x = hb.instances[1]
-    h, inst = B.hybrid_trace([x], rays)
-    q = B.query_rays(x.desc, hb.keep[0], hb.keep[1], hb.keep[2], x.n_nodes, rays, x.max_segs)
+    seg_h = torch.zeros(1, dtype=torch.int64, device="cuda")
+    seg_q = torch.zeros(1, dtype=torch.int64, device="cuda")
+    h, inst = B.hybrid_trace([x], rays, options=B.query_options(schedule=schedule, segments_out=seg_h))
+    ws = B.new_workspace(B.query_workspace_size(x.desc, n, x.max_segs))
+    q = B.query_rays(x.desc, hb.keep[0], hb.keep[1], hb.keep[2], x.n_nodes, rays, x.max_segs, workspace=ws,
+                     options=B.query_options(schedule=schedule, segments_out=seg_q))
+    segs, _ = B.query_stats(ws, n, x.max_segs)
     assert B.device_status() == 0
     for k in h:
         assert torch.equal(h[k], q[k]), k
     assert torch.equal(inst, torch.where(q["hit"] > 0, 0, -1).to(torch.int32))
+    assert int(seg_q.item()) == segs > 20
+    if schedule == B.SCHEDULE_WAVES:
+        assert int(seg_h.item()) == segs
+    else:  # lookahead rows depend on how the queue fills its tiles
+        assert int(seg_h.item()) >= segs // 2
 
 
 def test_hybrid_graph_bounce_loop_equals_eager():
