@@ -240,7 +240,17 @@ nbvh_status nbvh_encode(const nbvh_model_desc* desc, const void* table, nbvh_ray
  *                   the call adds, on its stream and without synchronising,
  *                   the segments it evaluated (nbvh_query_rays: entry 0;
  *                   nbvh_hybrid_trace: entry i for neural instance i). One
- *                   extra one-block launch per evaluation. */
+ *                   extra one-block launch per evaluation.
+ *  instance_streams nbvh_hybrid_trace: 1 = the neural instances one after
+ *                   another in index order, each merged into the record;
+ *                   0 or >= 2 = evaluated concurrently on the library's two
+ *                   side streams (forked from and joined back into the
+ *                   caller's stream, also under graph capture), each into its
+ *                   own staging record, then merged per ray in instance order
+ *                   (the same record bit for bit); the persistent
+ *                   evaluations' idle CTAs then leave early so that the
+ *                   other stream's kernels get their SMs. nbvh_query_rays
+ *                   ignores it. */
 #define NBVH_SCHEDULE_WAVES 0
 #define NBVH_SCHEDULE_PERSISTENT 1
 #define NBVH_W1_AUTO 0
@@ -259,6 +269,7 @@ typedef struct {
   int64_t wait_spins;
   int32_t test_phantom_items;
   int64_t* segments_out;
+  int32_t instance_streams;
 } nbvh_query_options;
 
 /* Host. The defaults: persistent schedule, patience 4000 cycles, traversal
@@ -720,7 +731,10 @@ typedef struct {
   int32_t max_segs;         /*   segment slots per ray for this asset */
 } nbvh_instance;
 
-/* Host. Workspace bytes of nbvh_hybrid_trace for n_rays rays. */
+/* Host. Workspace bytes of nbvh_hybrid_trace for n_rays rays, for either
+ * form (instance_streams): two query workspaces of the deepest instance, the
+ * per-instance ray lists, and per neural instance a staging hit record
+ * (about 21 bytes per ray, 33 with an albedo head). */
 nbvh_status nbvh_hybrid_workspace_size(const nbvh_instance* inst, int32_t n_inst, int64_t n_rays, size_t* bytes);
 
 /* Device. Closest hit over every instance of the two-level hierarchy. Each
@@ -729,13 +743,19 @@ nbvh_status nbvh_hybrid_workspace_size(const nbvh_instance* inst, int32_t n_inst
  * [tmin, tmax]. The result is the smallest t over the instances; equal t goes
  * to the lower instance index. out.leaf is the triangle index or the N-BVH
  * leaf; out_inst (device, rays.n int32) the instance index, -1 on a miss.
- * Instances are processed in index order as wavefront passes, each keeping
- * the record unless it finds a strictly closer hit. Before the first neural
- * instance, one top-level pass tests every ray against the root boxes of all
- * remaining neural instances and lists, per instance, the rays that meet
- * them before the record; each neural pass then traverses only its list and
- * skips the leaves whose segment starts at or beyond the record (their hits
- * cannot be closer), which leaves the result unchanged.
+ * The result is the closest hit over all instances, equal t to the lower
+ * instance index. Sequential form (instance_streams = 1): instances are
+ * processed in index order as wavefront passes, each keeping the record
+ * unless it finds a strictly closer hit. Before the first neural instance,
+ * one top-level pass tests every ray against the root boxes of all remaining
+ * neural instances and lists, per instance, the rays that meet them before
+ * the record; each neural pass then traverses only its list and skips the
+ * leaves whose segment starts at or beyond the record (their hits cannot be
+ * closer), which leaves the result unchanged. Concurrent form (the default):
+ * the triangle instances first, then the top-level pass, then the neural
+ * instances on two side streams, each searching from the triangles' answer
+ * into its own staging record, then one per-ray merge in instance order; the
+ * record equals the sequential form's bit for bit.
  * inst: host array of n_inst (1..64) instances; workspace: device, 256-byte
  * aligned, >= nbvh_hybrid_workspace_size bytes. opt: the evaluation options
  * of the neural passes (NULL = nbvh_query_options_default). Segment overflow

@@ -90,6 +90,9 @@ struct PQueue {
   unsigned long long* retired;   // items resolved
   unsigned int* tiles;           // tiles claimed (statistics)
   unsigned long long* lookahead; // segments evaluated in lookahead rows, never queued (statistics)
+  unsigned int* exited;          // CTAs that left before the queue drained (their SMs go to other work)
+  int32_t yield_idle;            // > 0: CTAs with nothing to claim leave while the rest (with yield_idle - 1
+                                 // spares) suffice; their SMs go to concurrent kernels
   long long patience;            // cycles a CTA waits for a full tile before taking a partial one
   long long spin_limit;          // polling rounds before a queue wait gives up (NBVH_ERR_TIMEOUT)
   unsigned long long* ring;      // [n_rays] items; nullptr: one launch per segment slot instead

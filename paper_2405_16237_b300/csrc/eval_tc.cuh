@@ -363,15 +363,23 @@ __device__ __forceinline__ void red_release_add_u64(unsigned long long* p, unsig
 }
 
 // Thread 0 of a CTA: claim up to kTcM queued items. Returns the count (start
-// in *start), 0 when the queue has drained, -1 when the wait gave up. A
-// partial tile is taken only when nothing is in evaluation (no more items can
-// come) or after q.patience cycles of waiting: a tile's latency hardly
-// shrinks with fewer rows, while other CTAs' resolves refill the queue within
-// microseconds. The counters are polled with independent relaxed loads (a
-// stale value only delays a claim; the CAS on head validates it); the drained
-// state is confirmed by reading retired, then head, then reserved in order:
-// equal values mean nothing is in evaluation or queued, so nothing more can
-// be queued.
+// in *start), 0 when the CTA leaves (the queue has drained, or see below),
+// -1 when the wait gave up. A partial tile is taken only when nothing is in
+// evaluation (no more items can come) or after q.patience cycles of waiting:
+// a tile's latency hardly shrinks with fewer rows, while other CTAs' resolves
+// refill the queue within microseconds. The counters are polled with
+// independent relaxed loads (a stale value only delays a claim; the CAS on
+// head validates it); the drained state is confirmed by reading retired, then
+// head, then reserved in order: equal values mean nothing is in evaluation
+// or queued, so nothing more can be queued.
+// With q.yield_idle = m > 0 (other kernels run beside this one: the
+// instances of a hybrid trace) a CTA with nothing to claim also leaves while
+// the CTAs that stay are enough for the items in evaluation: each item has at
+// most one successor, so the next round needs at most ceil(in evaluation /
+// kTcM) tiles (plus m - 1 spare CTAs for partial tiles with lookahead rows),
+// and the CTAs evaluating them stay. Its SM then serves the other
+// kernels. A stale count only makes the CTA stay. (Alone, a draining queue
+// is better served by many CTAs taking partial tiles with lookahead rows.)
 __device__ __forceinline__ int pq_claim(const PQueue& q, unsigned long long* start) {
   const long long t0 = clock64();
   for (long long spin = 0; spin < q.spin_limit; ++spin) {
@@ -395,6 +403,14 @@ __device__ __forceinline__ int pq_claim(const PQueue& q, unsigned long long* sta
       const unsigned long long s2 = ld_acquire_u64(q.reserved);
       if (r2 == h2 && s2 == h2) return 0;
       continue;
+    } else if (q.yield_idle && head > retired) {
+      const unsigned long long need = (head - retired + kTcM - 1) / kTcM + unsigned(q.yield_idle);
+      const unsigned left = *reinterpret_cast<volatile unsigned*>(q.exited);
+      if (gridDim.x > left && gridDim.x - left - 1 >= need) {
+        const unsigned old = atomicAdd(q.exited, 1u);
+        if (gridDim.x > old && gridDim.x - old - 1 >= need) return 0;
+        atomicSub(q.exited, 1u);
+      }
     }
     __nanosleep(64);
   }

@@ -6,6 +6,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <vector>
 
@@ -149,6 +150,8 @@ nbvh_query_options default_options() {
   o.eval_pipeline = NBVH_PIPELINE_AUTO;
   o.wait_spins = 0;
   o.test_phantom_items = 0;
+  o.segments_out = nullptr;
+  o.instance_streams = 0;
   return o;
 }
 
@@ -159,7 +162,8 @@ bool options_valid(const nbvh_query_options& o) {
          (o.eval_threads == 0 || o.eval_threads == 256 || o.eval_threads == 512) && o.w1_mode >= NBVH_W1_AUTO &&
          o.w1_mode <= NBVH_W1_STREAMED && o.eval_pipeline >= NBVH_PIPELINE_AUTO &&
          o.eval_pipeline <= NBVH_PIPELINE_WARP_SPECIALISED && o.wait_spins >= 0 && o.wait_spins <= (int64_t(1) << 40) &&
-         o.test_phantom_items >= 0 && o.test_phantom_items <= 1024;
+         o.test_phantom_items >= 0 && o.test_phantom_items <= 1024 && o.instance_streams >= 0 &&
+         o.instance_streams <= 64;
 }
 
 // Whether a query with these options runs the warp-specialised persistent
@@ -327,7 +331,14 @@ QueryWs carve_query(void* base, int64_t n, int32_t max_segs, size_t image = 0) {
   return w;
 }
 
-PQueue pq_of(const QueryWs& w, int32_t max_segs, int64_t patience, int64_t spin_limit) {
+// Persistent evaluations beside other instances' (concurrent hybrid form):
+// idle CTAs leave while the CTAs that stay, with this many spares, suffice.
+#ifndef NBVH_YIELD_SPARES
+#define NBVH_YIELD_SPARES 8
+#endif
+constexpr int kYieldSpares = NBVH_YIELD_SPARES;
+
+PQueue pq_of(const QueryWs& w, int32_t max_segs, int64_t patience, int64_t spin_limit, bool yield_idle) {
   int32_t* c = w.counters + pq_base(max_segs);
   PQueue q;
   q.head = reinterpret_cast<unsigned long long*>(c);
@@ -335,6 +346,8 @@ PQueue pq_of(const QueryWs& w, int32_t max_segs, int64_t patience, int64_t spin_
   q.retired = reinterpret_cast<unsigned long long*>(c + 64);
   q.tiles = reinterpret_cast<unsigned int*>(c + 96);
   q.lookahead = reinterpret_cast<unsigned long long*>(c + 98);
+  q.exited = reinterpret_cast<unsigned int*>(c + 100);
+  q.yield_idle = yield_idle ? kYieldSpares + 1 : 0;
   q.patience = patience;
   q.spin_limit = spin_limit > 0 ? spin_limit : kPqSpinLimit;
   q.ring = reinterpret_cast<unsigned long long*>(w.queue[0]);
@@ -362,7 +375,8 @@ cudaError_t launch_query_stages(const nbvh_model_desc* desc, const GridParams& g
                                 const float* mlp, const nbvh_node* nodes, const nbvh_rays& rays, int32_t max_segs,
                                 const nbvh_hits& out, const QueryWs& w, bool merge, int32_t* inst_out,
                                 int32_t inst_id, const nbvh_query_options& o, cudaStream_t s,
-                                const int32_t* list = nullptr, const int32_t* list_count = nullptr) {
+                                const int32_t* list = nullptr, const int32_t* list_count = nullptr,
+                                const float* init_t = nullptr, const int32_t* init_inst = nullptr) {
   TraverseOut to;
   std::memset(&to, 0, sizeof(to));
   to.seg_count = w.seg_count;
@@ -375,6 +389,9 @@ cudaError_t launch_query_stages(const nbvh_model_desc* desc, const GridParams& g
   to.hits = out;
   to.merge = merge ? 1 : 0;
   to.reverse_inside = (desc->flags & NBVH_FLAG_REVERSE_INSIDE) ? 1 : 0;
+  to.init_t = init_t;
+  to.init_inst = init_inst;
+  to.inst_id = inst_id;
   const bool persistent = desc->mlp_prec != NBVH_FP32 && o.schedule == NBVH_SCHEDULE_PERSISTENT;
   if (persistent) {
     to.queue0 = nullptr;
@@ -417,7 +434,7 @@ cudaError_t launch_query_stages(const nbvh_model_desc* desc, const GridParams& g
   }
   if (persistent) {
     // one launch drains a queue of (slot, ray) items
-    a.pq = pq_of(w, max_segs, o.patience_cycles, o.wait_spins);
+    a.pq = pq_of(w, max_segs, o.patience_cycles, o.wait_spins, init_t != nullptr);
     pq_init_kernel<<<1, 1, 0, s>>>(w.counters, a.pq, o.test_phantom_items);
     count_launches(1);
     e = cudaGetLastError();
@@ -765,30 +782,119 @@ extern "C" nbvh_status nbvh_trace_triangles(const nbvh_tri_blas* blas, nbvh_rays
   return status_of(cudaGetLastError());
 }
 
-// Hybrid workspace: the query workspace of the deepest neural instance, then
-// one ray list per neural instance (n_rays entries) and their counts.
+namespace nbvh {
+namespace {
+
+// Hybrid workspace: kHybridStreams query workspaces sized for the deepest
+// neural instance (the sequential form uses the first), one ray list per
+// neural instance (n_rays entries) and their counts, then for the concurrent
+// form a per-ray instance mask and one staging hit record per neural
+// instance (albedo arrays when an instance has the albedo head).
+// At most two: on the 16-asset scene (3840x2160, 4 bounces) two streams took
+// the frame from 128 to 111 ms, three and four 116-123 ms (the kernels
+// contend for SMs and L2).
+constexpr int kHybridStreams = 2;
+
 struct HybridWs {
-  QueryWs q;
+  QueryWs q[kHybridStreams];
   int32_t* lists;
   int32_t* counts;
+  unsigned long long* mask;
+  nbvh_hits stage;  // slot k of ray r at k * n + r
   size_t bytes;
 };
 
+bool hybrid_albedo(const nbvh_instance* inst, int32_t n_inst) {
+  for (int i = 0; i < n_inst; ++i)
+    if (inst[i].kind == NBVH_BLAS_NEURAL && inst[i].desc.n_out >= 8) return true;
+  return false;
+}
+
 HybridWs carve_hybrid(void* base, const nbvh_instance* inst, int32_t n_inst, int64_t n) {
   HybridWs h;
+  std::memset(&h, 0, sizeof(h));
   int32_t n_neural = 0;
   for (int i = 0; i < n_inst; ++i) n_neural += inst[i].kind == NBVH_BLAS_NEURAL;
   const int32_t ms = std::max(hybrid_max_segs(inst, n_inst), 1);
-  h.q = carve_query(base, n, ms, hybrid_image_bytes(inst, n_inst));
   char* p = static_cast<char*>(base);
-  size_t off = h.q.bytes;
-  h.lists = p ? reinterpret_cast<int32_t*>(p + off) : nullptr;
-  off += align256(sizeof(int32_t) * size_t(n) * size_t(n_neural));
-  h.counts = p ? reinterpret_cast<int32_t*>(p + off) : nullptr;
-  off += align256(sizeof(int32_t) * kMaxInstances);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    char* q = p ? p + off : nullptr;
+    off += align256(bytes);
+    return q;
+  };
+  for (int j = 0; j < kHybridStreams; ++j) {
+    h.q[j] = carve_query(p ? p + off : nullptr, n, ms, hybrid_image_bytes(inst, n_inst));
+    off += h.q[j].bytes;
+  }
+  const size_t N = size_t(n), K = size_t(n_neural);
+  h.lists = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * N * K));
+  h.counts = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * kMaxInstances));
+  h.mask = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * N));
+  h.stage.hit = reinterpret_cast<uint8_t*>(take(N * K));
+  h.stage.t = reinterpret_cast<float*>(take(4 * N * K));
+  h.stage.nx = reinterpret_cast<float*>(take(4 * N * K));
+  h.stage.ny = reinterpret_cast<float*>(take(4 * N * K));
+  h.stage.nz = reinterpret_cast<float*>(take(4 * N * K));
+  h.stage.leaf = reinterpret_cast<int32_t*>(take(4 * N * K));
+  if (hybrid_albedo(inst, n_inst)) {
+    h.stage.ar = reinterpret_cast<float*>(take(4 * N * K));
+    h.stage.ag = reinterpret_cast<float*>(take(4 * N * K));
+    h.stage.ab = reinterpret_cast<float*>(take(4 * N * K));
+  }
   h.bytes = off;
   return h;
 }
+
+// Staging record of slot k (k * n entries into every array).
+nbvh_hits stage_slot(const nbvh_hits& st, int32_t k, int64_t n) {
+  const size_t o = size_t(k) * size_t(n);
+  nbvh_hits h = st;
+  h.hit = st.hit + o;
+  h.t = st.t + o;
+  h.nx = st.nx + o;
+  h.ny = st.ny + o;
+  h.nz = st.nz + o;
+  h.leaf = st.leaf + o;
+  if (st.ar) {
+    h.ar = st.ar + o;
+    h.ag = st.ag + o;
+    h.ab = st.ab + o;
+  }
+  return h;
+}
+
+// Per device: the side streams of the concurrent hybrid form and its fork /
+// join events, created on first use and kept; one host thread at a time
+// enqueues on them (their events would interleave otherwise).
+struct SideStreams {
+  cudaStream_t s[kHybridStreams];
+  cudaEvent_t fork;
+  cudaEvent_t join[kHybridStreams];
+  std::mutex mu;
+};
+
+SideStreams* side_streams() {
+  static std::mutex mu;
+  static std::vector<std::unique_ptr<SideStreams>> per_dev;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  if (per_dev.size() <= size_t(dev)) per_dev.resize(size_t(dev) + 1);
+  if (!per_dev[size_t(dev)]) {
+    std::unique_ptr<SideStreams> x(new SideStreams());
+    bool ok = cudaEventCreateWithFlags(&x->fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int j = 0; j < kHybridStreams && ok; ++j)
+      ok = cudaStreamCreateWithFlags(&x->s[j], cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&x->join[j], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) return nullptr;
+    per_dev[size_t(dev)] = std::move(x);
+  }
+  return per_dev[size_t(dev)].get();
+}
+
+}  // namespace
+}  // namespace nbvh
 
 extern "C" nbvh_status nbvh_hybrid_workspace_size(const nbvh_instance* inst, int32_t n_inst, int64_t n_rays,
                                                   size_t* bytes) {
@@ -796,6 +902,55 @@ extern "C" nbvh_status nbvh_hybrid_workspace_size(const nbvh_instance* inst, int
   *bytes = carve_hybrid(nullptr, inst, n_inst, n_rays).bytes;
   return NBVH_OK;
 }
+
+namespace nbvh {
+namespace {
+
+// The top-level cull: for the neural instances from `from` on, the list of
+// rays whose interval meets their root boxes before the record so far (the
+// record only shrinks, so each list stays a superset of the rays the
+// instance's traversal can give a segment); slot k = the k-th of them.
+cudaError_t hybrid_cull(const nbvh_instance* inst, int32_t n_inst, int32_t from, const nbvh_rays& rays,
+                        const nbvh_hits& out, const HybridWs& hw, bool with_mask, std::vector<int32_t>& cull_slot,
+                        cudaStream_t s) {
+  CullArgs c;
+  std::memset(&c, 0, sizeof(c));
+  int32_t k = 0;
+  for (int j = from; j < n_inst; ++j) {
+    if (inst[j].kind != NBVH_BLAS_NEURAL) continue;
+    cull_slot[size_t(j)] = k;
+    c.root[k] = inst[j].nodes;
+    c.list[k] = hw.lists + size_t(k) * size_t(rays.n);
+    ++k;
+  }
+  c.count = hw.counts;
+  c.n_inst = k;
+  c.mask = with_mask ? hw.mask : nullptr;
+  TimedSection ts(NBVH_KERNEL_TLAS_CULL, s);
+  cudaError_t e = cudaMemsetAsync(hw.counts, 0, sizeof(int32_t) * kMaxInstances, s);
+  if (e != cudaSuccess) return e;
+  tlas_cull_kernel<<<unsigned((rays.n + 255) / 256), 256, 0, s>>>(ray_ptrs(rays), rays.n, out.t, c);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// One neural instance's traversal and evaluation over its ray list, on
+// stream s with query workspace w: merged into `rec` (with the instance id
+// into out_inst), or staged (init_t set: rec is its staging record).
+cudaError_t hybrid_neural(const nbvh_instance& x, int32_t i, const GridParams& gp, const nbvh_rays& rays,
+                          const nbvh_hits& rec, int32_t* out_inst, const QueryWs& w, const HybridWs& hw, int32_t k,
+                          const nbvh_query_options& o, const float* init_t, const int32_t* init_inst,
+                          cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(w.counters, 0, counters_bytes(x.max_segs), s);
+  if (e != cudaSuccess) return e;
+  nbvh_query_options oi = o;
+  if (o.segments_out) oi.segments_out = o.segments_out + i;
+  return launch_query_stages(&x.desc, gp, x.table, x.mlp, x.nodes, rays, x.max_segs, rec, w, true, out_inst, i, oi,
+                             s, hw.lists + size_t(k) * size_t(rays.n), hw.counts + k, init_t, init_inst);
+}
+
+}  // namespace
+}  // namespace nbvh
 
 extern "C" nbvh_status nbvh_hybrid_trace(const nbvh_instance* inst, int32_t n_inst, nbvh_rays rays,
                                          nbvh_hits out, int32_t* out_inst, void* workspace, size_t ws_bytes,
@@ -809,10 +964,19 @@ extern "C" nbvh_status nbvh_hybrid_trace(const nbvh_instance* inst, int32_t n_in
   const HybridWs hw = carve_hybrid(workspace, inst, n_inst, rays.n);
   if (ws_bytes < hw.bytes) return NBVH_ERR_WORKSPACE_TOO_SMALL;
   std::vector<GridParams> gps(static_cast<size_t>(n_inst));
-  for (int i = 0; i < n_inst; ++i)
-    if (inst[i].kind == NBVH_BLAS_NEURAL && !make_grid(&inst[i].desc, gps[i])) return NBVH_ERR_INVALID_ARG;
+  int32_t n_neural = 0;
+  for (int i = 0; i < n_inst; ++i) {
+    if (inst[i].kind != NBVH_BLAS_NEURAL) continue;
+    ++n_neural;
+    if (!make_grid(&inst[i].desc, gps[size_t(i)])) return NBVH_ERR_INVALID_ARG;
+  }
   for (int i = 0; i < n_inst; ++i)  // before anything is enqueued
     if (inst[i].kind == NBVH_BLAS_NEURAL && !eval_stageable(&inst[i].desc, o)) return NBVH_ERR_UNSUPPORTED;
+  const int32_t streams = std::min<int32_t>(o.instance_streams == 0 ? kHybridStreams : o.instance_streams,
+                                            kHybridStreams);
+  const bool concurrent = streams > 1 && n_neural > 1;
+  SideStreams* side = concurrent ? side_streams() : nullptr;
+  if (concurrent && !side) return NBVH_ERR_CUDA;
   cudaStream_t s = as_stream(stream);
   cudaError_t e;
   {
@@ -822,56 +986,77 @@ extern "C" nbvh_status nbvh_hybrid_trace(const nbvh_instance* inst, int32_t n_in
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) return NBVH_ERR_CUDA;
-  int32_t culled_from = -1;  // first instance covered by the top-level cull
   std::vector<int32_t> cull_slot(static_cast<size_t>(n_inst), -1);
-  for (int i = 0; i < n_inst; ++i) {
-    const nbvh_instance& x = inst[i];
-    if (x.kind == NBVH_BLAS_TRIANGLES) {
-      const TriBlasArgs a = tri_args(x.tri, rays, out, out_inst, i, 1);
-      TimedSection ts(NBVH_KERNEL_TRI_TRACE, s);
-      tri_trace_kernel<<<unsigned((rays.n + 127) / 128), 128, 0, s>>>(a);
-      count_launches(1);
-      e = cudaGetLastError();
-      if (e != cudaSuccess) return status_of(e);
-      continue;
-    }
-    if (culled_from < 0) {
-      // Top level: one pass over the rays builds, for every neural instance
-      // from here on, the list of rays whose interval meets its root boxes
-      // before the record so far (the record only shrinks, so each list stays
-      // a superset of the rays its traversal can give a segment).
-      CullArgs c;
-      std::memset(&c, 0, sizeof(c));
-      int32_t k = 0;
-      for (int j = i; j < n_inst; ++j) {
-        if (inst[j].kind != NBVH_BLAS_NEURAL) continue;
-        cull_slot[j] = k;
-        c.root[k] = inst[j].nodes;
-        c.list[k] = hw.lists + size_t(k) * size_t(rays.n);
-        ++k;
+  auto tri = [&](int i) {
+    const TriBlasArgs a = tri_args(inst[i].tri, rays, out, out_inst, i, 1);
+    TimedSection ts(NBVH_KERNEL_TRI_TRACE, s);
+    tri_trace_kernel<<<unsigned((rays.n + 127) / 128), 128, 0, s>>>(a);
+    count_launches(1);
+    return cudaGetLastError();
+  };
+  if (!concurrent) {
+    // one instance after another in index order, each merged into the record
+    int32_t culled_from = -1;  // first instance covered by the top-level cull
+    for (int i = 0; i < n_inst; ++i) {
+      const nbvh_instance& x = inst[i];
+      if (x.kind == NBVH_BLAS_TRIANGLES) {
+        e = tri(i);
+        if (e != cudaSuccess) return status_of(e);
+        continue;
       }
-      c.count = hw.counts;
-      c.n_inst = k;
-      TimedSection ts(NBVH_KERNEL_TLAS_CULL, s);
-      e = cudaMemsetAsync(hw.counts, 0, sizeof(int32_t) * kMaxInstances, s);
-      if (e != cudaSuccess) return NBVH_ERR_CUDA;
-      tlas_cull_kernel<<<unsigned((rays.n + 255) / 256), 256, 0, s>>>(ray_ptrs(rays), rays.n, out.t, c);
-      count_launches(1);
-      e = cudaGetLastError();
-      if (e != cudaSuccess) return NBVH_ERR_CUDA;
-      culled_from = i;
+      if (culled_from < 0) {
+        e = hybrid_cull(inst, n_inst, i, rays, out, hw, false, cull_slot, s);
+        if (e != cudaSuccess) return NBVH_ERR_CUDA;
+        culled_from = i;
+      }
+      e = hybrid_neural(x, i, gps[size_t(i)], rays, out, out_inst, hw.q[0], hw, cull_slot[size_t(i)], o, nullptr,
+                        nullptr, s);
+      if (e != cudaSuccess) return status_of(e);
     }
-    const int32_t k = cull_slot[i];
-    e = cudaMemsetAsync(hw.q.counters, 0, counters_bytes(x.max_segs), s);
-    if (e != cudaSuccess) return NBVH_ERR_CUDA;
-    QueryWs wi = carve_query(workspace, rays.n, x.max_segs, hybrid_image_bytes(inst, n_inst));
-    nbvh_query_options oi = o;
-    if (o.segments_out) oi.segments_out = o.segments_out + i;
-    e = launch_query_stages(&x.desc, gps[i], x.table, x.mlp, x.nodes, rays, x.max_segs, out, wi, true, out_inst, i,
-                            oi, s, hw.lists + size_t(k) * size_t(rays.n), hw.counts + k);
-    if (e != cudaSuccess) return status_of(e);
+    return NBVH_OK;
   }
-  return NBVH_OK;
+  // Concurrent form: the triangle instances first (merged in index order),
+  // then every neural instance on one of the side streams, each into its own
+  // staging record started at the triangles' answer, then a per-ray merge in
+  // instance order. A neural instance's own closest hit does not depend on
+  // where its search starts (only segments that cannot win are skipped), so
+  // the record equals the sequential form's bit for bit. An instance's idle
+  // persistent CTAs leave early, so the instances' evaluations overlap.
+  for (int i = 0; i < n_inst; ++i)
+    if (inst[i].kind == NBVH_BLAS_TRIANGLES) {
+      e = tri(i);
+      if (e != cudaSuccess) return status_of(e);
+    }
+  e = hybrid_cull(inst, n_inst, 0, rays, out, hw, true, cull_slot, s);
+  if (e != cudaSuccess) return NBVH_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(side->mu);
+  if (cudaEventRecord(side->fork, s) != cudaSuccess) return NBVH_ERR_CUDA;
+  for (int j = 0; j < streams; ++j)
+    if (cudaStreamWaitEvent(side->s[j], side->fork, 0) != cudaSuccess) return NBVH_ERR_CUDA;
+  StageArgs sa;
+  std::memset(&sa, 0, sizeof(sa));
+  sa.st = hw.stage;
+  sa.n = rays.n;
+  nbvh_status st = NBVH_OK;
+  for (int i = 0; i < n_inst && st == NBVH_OK; ++i) {
+    if (inst[i].kind != NBVH_BLAS_NEURAL) continue;
+    const int32_t k = cull_slot[size_t(i)];
+    sa.inst_of[k] = i;
+    const int j = k % streams;
+    e = hybrid_neural(inst[i], i, gps[size_t(i)], rays, stage_slot(hw.stage, k, rays.n), nullptr, hw.q[j], hw, k, o,
+                      out.t, out_inst, side->s[j]);
+    if (e != cudaSuccess) st = status_of(e);
+  }
+  // join (also after a failure: the side streams must not outlive the caller's stream order)
+  for (int j = 0; j < streams; ++j)
+    if (cudaEventRecord(side->join[j], side->s[j]) != cudaSuccess ||
+        cudaStreamWaitEvent(s, side->join[j], 0) != cudaSuccess)
+      st = NBVH_ERR_CUDA;
+  if (st != NBVH_OK) return st;
+  TimedSection ts(NBVH_KERNEL_OTHER, s);
+  hybrid_merge_kernel<<<unsigned((rays.n + 255) / 256), 256, 0, s>>>(out, out_inst, hw.mask, rays.n, sa);
+  count_launches(1);
+  return status_of(cudaGetLastError());
 }
 
 // ---------------------------------------------------------------- autotuner (S6)

@@ -24,6 +24,14 @@ struct TraverseOut {
   // whole chord with swapped endpoints (t0 = exit, t1 = entry), for a query
   // of the chord in reverse order (NBVH_FLAG_REVERSE_INSIDE).
   int32_t reverse_inside;
+  // Staged merge (hybrid hierarchy, instances evaluated concurrently): the
+  // record `hits` is this instance's own staging record, started at the
+  // closest hit of the instances merged before (init_t, found by instance
+  // init_inst; -1: none). A hit equal to it still wins for an instance with a
+  // lower index than init_inst, so such an instance starts just above it.
+  const float* init_t;
+  const int32_t* init_inst;
+  int32_t inst_id;
 };
 
 // Order key of a listed segment: its start along the ray (the entry of a
@@ -46,7 +54,13 @@ __device__ __forceinline__ int traverse_ray(const nbvh_node* __restrict__ nodes,
   const RayR ray = make_rayr(ox, oy, oz, dx, dy, dz, tmin, tmax);
   const int max_segs = out.max_segs;
   const bool merge = out.merge != 0;
-  const float best = merge ? out.hits.t[r] : 0.0f;
+  float best = merge ? out.hits.t[r] : 0.0f;
+  if (out.init_t) {
+    best = out.init_t[r];
+    if (out.init_inst[r] > out.inst_id) best = nextafterf(best, __int_as_float(0x7f800000));
+    out.hits.t[r] = best;
+    out.hits.hit[r] = 0;
+  }
   bool overflow = false;
   float lo_box[3] = {0.0f, 0.0f, 0.0f}, hi_box[3] = {0.0f, 0.0f, 0.0f};  // the box being emitted
   float tail_key = 0.0f;  // order key and leaf of the list's last entry (count > 0)
@@ -232,6 +246,7 @@ struct CullArgs {
   int32_t* list[kMaxInstances];
   int32_t* count;  // [n_inst]
   int32_t n_inst;
+  unsigned long long* mask;  // optional, per ray: bit k = listed for instance k
 };
 
 __device__ __forceinline__ bool root_meets(const nbvh_node* __restrict__ nodes, const RayR& ray, float best) {
@@ -300,6 +315,7 @@ static __global__ void __launch_bounds__(256) tlas_cull_kernel(RayPtrs rays, int
     for (int k = 0; k < c.n_inst; ++k)
       if (root_maybe(s_box[k], ray, best)) mask |= uint64_t(1) << k;
   }
+  if (active && c.mask) c.mask[r] = mask;
   // count: one shared-memory increment per warp and instance
   for (int k = 0; k < c.n_inst; ++k) {
     const unsigned m = __ballot_sync(0xffffffffu, (mask >> k) & 1);
@@ -315,6 +331,57 @@ static __global__ void __launch_bounds__(256) tlas_cull_kernel(RayPtrs rays, int
     const unsigned m = __ballot_sync(0xffffffffu, (mask >> k) & 1);
     if ((mask >> k) & 1)
       c.list[k][s_base[k] + s_wbase[warp][k] + __popc(m & ((1u << lane) - 1u))] = int32_t(r);
+  }
+}
+
+// Staging records of concurrently evaluated instances: slot k's record of
+// ray r at index k * n + r of each array (albedo arrays optional).
+struct StageArgs {
+  nbvh_hits st;
+  int64_t n;
+  int32_t inst_of[kMaxInstances];  // instance index of slot k
+};
+
+// Per ray, the record (the triangle instances' closest hit) and the staged
+// answers of the instances the ray was listed for, taken in slot order (=
+// instance order): the closest hit wins, equal t to the lower instance
+// index, as if the instances had been merged one after another.
+static __global__ void __launch_bounds__(256) hybrid_merge_kernel(nbvh_hits out, int32_t* __restrict__ out_inst,
+                                                                  const unsigned long long* __restrict__ mask,
+                                                                  int64_t n, StageArgs sa) {
+  const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  unsigned long long m = mask[r];
+  if (!m) return;
+  float best = out.t[r];
+  int best_inst = out.hit[r] ? out_inst[r] : 0x7fffffff;
+  int win = -1;
+  while (m) {
+    const int k = __ffsll(static_cast<long long>(m)) - 1;
+    m &= m - 1;
+    const size_t q = size_t(k) * size_t(sa.n) + size_t(r);
+    if (!sa.st.hit[q]) continue;
+    const float t = sa.st.t[q];
+    if (t < best || (t == best && sa.inst_of[k] < best_inst)) {
+      best = t;
+      best_inst = sa.inst_of[k];
+      win = k;
+    }
+  }
+  if (win < 0) return;
+  const size_t q = size_t(win) * size_t(sa.n) + size_t(r);
+  out.hit[r] = 1;
+  out.t[r] = best;
+  out.nx[r] = sa.st.nx[q];
+  out.ny[r] = sa.st.ny[q];
+  out.nz[r] = sa.st.nz[q];
+  out.leaf[r] = sa.st.leaf[q];
+  out_inst[r] = best_inst;
+  if (out.ar) {
+    const bool has = sa.st.ar != nullptr;
+    out.ar[r] = has ? sa.st.ar[q] : 0.0f;
+    out.ag[r] = has ? sa.st.ag[q] : 0.0f;
+    out.ab[r] = has ? sa.st.ab[q] : 0.0f;
   }
 }
 

@@ -97,7 +97,8 @@ class LeafStats(ctypes.Structure):
 class QueryOptions(ctypes.Structure):
     _fields_ = [("schedule", c_int32), ("patience_cycles", c_int64), ("traverse_block", c_int32),
                 ("eval_threads", c_int32), ("w1_mode", c_int32), ("eval_pipeline", c_int32),
-                ("wait_spins", c_int64), ("test_phantom_items", c_int32), ("segments_out", c_void_p)]
+                ("wait_spins", c_int64), ("test_phantom_items", c_int32), ("segments_out", c_void_p),
+                ("instance_streams", c_int32)]
 
 
 class TuneResult(ctypes.Structure):
@@ -486,14 +487,16 @@ def query_options(**kw) -> QueryOptions:
 def options_dict(o: QueryOptions) -> dict:
     return {"schedule": ["waves", "persistent"][o.schedule], "patience_cycles": o.patience_cycles,
             "traverse_block": o.traverse_block, "eval_threads": o.eval_threads,
-            "w1_mode": ["auto", "resident", "streamed"][o.w1_mode], "eval_pipeline": PIPELINES[o.eval_pipeline]}
+            "w1_mode": ["auto", "resident", "streamed"][o.w1_mode], "eval_pipeline": PIPELINES[o.eval_pipeline],
+            "instance_streams": o.instance_streams}
 
 
 def options_from_dict(d: dict) -> QueryOptions:
     return query_options(schedule=["waves", "persistent"].index(d["schedule"]), patience_cycles=d["patience_cycles"],
                          traverse_block=d["traverse_block"], eval_threads=d["eval_threads"],
                          w1_mode=["auto", "resident", "streamed"].index(d["w1_mode"]),
-                         eval_pipeline=PIPELINES.index(d.get("eval_pipeline", "auto")))
+                         eval_pipeline=PIPELINES.index(d.get("eval_pipeline", "auto")),
+                         instance_streams=d.get("instance_streams", 0))
 
 
 def _opt_ref(options):

@@ -188,3 +188,45 @@ def test_hybrid_schedules_agree():
     for k in hw:
         assert torch.equal(hw[k], hp[k]), k
     assert torch.equal(iw, ip)
+
+
+@pytest.mark.parametrize("schedule", [0, 1])
+@pytest.mark.parametrize("albedo", [False, True])
+def test_concurrent_instances_equal_sequential(schedule, albedo):
+    """The neural instances evaluated concurrently on the library's side
+    streams, each into its own staging record merged per ray in instance
+    order (instance_streams 0 = 4, and 2), give the record of the sequential
+    form (instance_streams = 1) bit for bit, with the triangle instance
+    placed between neural ones (the tie rule to the lower index across both
+    kinds), under either schedule; with the albedo head the record's albedo
+    is merged too. A coarse-grid copy of one asset makes equal-t ties
+    between instances common."""
+    from dataclasses import replace
+    torch = _torch()
+    ground, assets = small_hybrid_scene(4)
+    if albedo:
+        for a in assets:
+            a.model = replace(a.model, n_out=8)
+    hb = HybridBuilt(ground, assets, B.BF16, table_prec=B.BF16)
+    tri = hb.instances[0]
+    neural = hb.instances[1:]
+    # the same asset twice: both answer with identical t, the lower index wins
+    order = [neural[0], tri, neural[1], neural[0], neural[2], neural[3]]
+    rays = B.to_device_rays(hybrid_rays(40, 800))
+    n = rays["ox"].numel()
+    res = {}
+    for streams in (1, 0, 2):
+        h = B.new_hits(n, albedo=albedo)
+        ins = torch.empty(n, dtype=torch.int32, device="cuda")
+        B.hybrid_trace(order, rays, out=h, inst_out=ins,
+                       options=B.query_options(schedule=schedule, instance_streams=streams))
+        res[streams] = (h, ins)
+    assert B.device_status() == 0
+    h1, i1 = res[1]
+    for streams in (0, 2):
+        h, ins = res[streams]
+        for k in h1:
+            assert torch.equal(h1[k], h[k]), (streams, k)
+        assert torch.equal(i1, ins), streams
+    # every kind of answer occurs; the duplicate (index 3) never beats index 0
+    assert int((i1 == 1).sum()) > 100 and int((i1 == 0).sum()) > 5 and int((i1 == 3).sum()) == 0
