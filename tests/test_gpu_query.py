@@ -518,7 +518,7 @@ def _surface_rays(tris, n, seed):
 def test_reverse_inside_query_matches_oracle(mp):
     """NBVH_FLAG_REVERSE_INSIDE on rays that start on the surface: segment
     lists with the reversed chords first (endpoints exact), FP32 results equal
-    to the oracle's on unambiguous rays, FP16 within tolerance."""
+    to the oracle's on unambiguous rays, FP16 hit agreement >= 99.9 % there."""
     torch = _torch()
     b = built("icosphere_l6", 1.0, 2.0)
     rays = _surface_rays(b.case.tris, 3000, 12)
@@ -549,8 +549,8 @@ def test_reverse_inside_query_matches_oracle(mp):
         hh = ok & res["hit"].astype(bool)
         assert hh.sum() > 100
         assert np.all(np.abs(h["t"][hh] - res["t"][hh]) <= 1e-5 * np.maximum(np.abs(res["t"][hh]), 1e-3))
-    else:
-        assert np.mean(h["hit"].astype(bool) == res["hit"].astype(bool)) >= 0.995
+    else:  # >= 99.9 % on the rays whose answer is not within rounding of a flip
+        assert np.mean((h["hit"].astype(bool) == res["hit"].astype(bool))[~amb]) >= 0.999
     # the chords themselves: the traversal step of the query lists the same swapped segments
     plain = O.ray_segments(rays, b.oleaves["leaf_lo"], b.oleaves["leaf_hi"])
     assert not np.array_equal(plain["t0"], seg["t0"])
