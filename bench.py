@@ -1075,7 +1075,8 @@ def time_icosphere(args, world, rank, wl, flush, pool, clocks_cb):
     del second, sets
     out = {"workload": wl.spec.name, "value": world * rays_step / (ms16 * 1e-3) / 1e6, "unit": "Mrays/s",
            "ms_per_step": ms16, "steps": steps, "rays_per_step": rays_step, "primary_rays": wl.n,
-           "bounce_rays": rays_step - wl.n, "segments_per_step": seg_step, "listed_segments_per_step": listed,
+           "bounce_rays": rays_step - wl.n, "segments_per_step": seg_step, "segments_primary": seg1,
+           "segments_bounce": seg2, "listed_segments_per_step": listed,
            "gpu_launches_per_step": launches16, "dtype": "f16 table, f16 tensor-core MLP",
            "fp32_plain": {"value": world * rays_step / (ms32 * 1e-3) / 1e6, "ms_per_step": ms32},
            "bf16_tc": {"value": world * rays_step / (msbf * 1e-3) / 1e6, "ms_per_step": msbf},
