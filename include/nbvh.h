@@ -250,7 +250,15 @@ nbvh_status nbvh_encode(const nbvh_model_desc* desc, const void* table, nbvh_ray
  *                   (the same record bit for bit); the persistent
  *                   evaluations' idle CTAs then leave early so that the
  *                   other stream's kernels get their SMs. nbvh_query_rays
- *                   ignores it. */
+ *                   ignores it.
+ *  partial_items    persistent schedule: the most queued items a partial
+ *                   tile claims (1 .. 128; 0 = the default, 16). The tile's
+ *                   other rows evaluate those rays' next segments
+ *                   (lookahead), so with a shallow queue several CTAs share
+ *                   it and each ray advances up to 128 / items segments per
+ *                   tile. Results do not depend on it. The concurrent hybrid
+ *                   form defaults to 128 (beside the other stream's kernels,
+ *                   smaller partial tiles measured slower). */
 #define NBVH_SCHEDULE_WAVES 0
 #define NBVH_SCHEDULE_PERSISTENT 1
 #define NBVH_W1_AUTO 0
@@ -270,6 +278,7 @@ typedef struct {
   int32_t test_phantom_items;
   int64_t* segments_out;
   int32_t instance_streams;
+  int32_t partial_items;
 } nbvh_query_options;
 
 /* Host. The defaults: persistent schedule, patience 4000 cycles, traversal
@@ -362,7 +371,9 @@ typedef struct {
  * pipeline and shape); (2) for FP16/BF16 the other evaluation pipeline and
  * the phase kernel's CTA shapes, 256 and 512 threads (256 only for width
  * <= 64) times resident and streamed first-layer weights, where the model
- * stages them; (3) traversal CTAs of 64, 128 and 256 threads. Each
+ * stages them; (3) for the persistent phase kernel, partial tiles of 4, 8,
+ * 16 (the default) and 32 items and of whole-queue claims (128); (4)
+ * traversal CTAs of 64, 128 and 256 threads. Each
  * candidate runs once untimed and reps times timed (CUDA events on the
  * stream, median). The first all_cap candidates with their times go to
  * all[], their count to *n_all. Every candidate gives the same hit records

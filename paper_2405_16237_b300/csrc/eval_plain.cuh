@@ -94,6 +94,7 @@ struct PQueue {
   int32_t yield_idle;            // > 0: CTAs with nothing to claim leave while the rest (with yield_idle - 1
                                  // spares) suffice; their SMs go to concurrent kernels
   long long patience;            // cycles a CTA waits for a full tile before taking a partial one
+  int32_t partial_items;         // the most items a partial tile claims (the rest of it: lookahead rows)
   long long spin_limit;          // polling rounds before a queue wait gives up (NBVH_ERR_TIMEOUT)
   unsigned long long* ring;      // [n_rays] items; nullptr: one launch per segment slot instead
 };

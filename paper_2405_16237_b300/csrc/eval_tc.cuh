@@ -367,7 +367,10 @@ __device__ __forceinline__ void red_release_add_u64(unsigned long long* p, unsig
 // -1 when the wait gave up. A partial tile is taken only when nothing is in
 // evaluation (no more items can come) or after q.patience cycles of waiting:
 // a tile's latency hardly shrinks with fewer rows, while other CTAs' resolves
-// refill the queue within microseconds. The counters are polled with
+// refill the queue within microseconds. A partial tile claims at most
+// q.partial_items items: its other rows hold those rays' next segments
+// (lookahead), so when the queue runs shallow, several CTAs split it and each
+// ray's chain advances up to 128 / items slots per tile. The counters are polled with
 // independent relaxed loads (a stale value only delays a claim; the CAS on
 // head validates it); the drained state is confirmed by reading retired, then
 // head, then reserved in order: equal values mean nothing is in evaluation
@@ -389,7 +392,10 @@ __device__ __forceinline__ int pq_claim(const PQueue& q, unsigned long long* sta
     if (res > head) {
       const unsigned long long avail = res - head;
       if (avail >= kTcM || retired == head || clock64() - t0 > q.patience) {
-        const unsigned want = unsigned(avail < kTcM ? avail : kTcM);
+        // a partial tile takes at most q.partial_items items, so that other
+        // CTAs share a shallow queue and each item gets more lookahead rows
+        const unsigned long long cap = avail >= kTcM ? kTcM : (unsigned long long)q.partial_items;
+        const unsigned want = unsigned(avail < cap ? avail : cap);
         if (atomicCAS(q.head, head, head + want) == head) {
           atomicAdd(q.tiles, 1u);
           *start = head;

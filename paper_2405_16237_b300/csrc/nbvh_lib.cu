@@ -152,6 +152,7 @@ nbvh_query_options default_options() {
   o.test_phantom_items = 0;
   o.segments_out = nullptr;
   o.instance_streams = 0;
+  o.partial_items = 0;
   return o;
 }
 
@@ -163,7 +164,7 @@ bool options_valid(const nbvh_query_options& o) {
          o.w1_mode <= NBVH_W1_STREAMED && o.eval_pipeline >= NBVH_PIPELINE_AUTO &&
          o.eval_pipeline <= NBVH_PIPELINE_WARP_SPECIALISED && o.wait_spins >= 0 && o.wait_spins <= (int64_t(1) << 40) &&
          o.test_phantom_items >= 0 && o.test_phantom_items <= 1024 && o.instance_streams >= 0 &&
-         o.instance_streams <= 64;
+         o.instance_streams <= 64 && o.partial_items >= 0 && o.partial_items <= 128;
 }
 
 // Whether a query with these options runs the warp-specialised persistent
@@ -331,6 +332,12 @@ QueryWs carve_query(void* base, int64_t n, int32_t max_segs, size_t image = 0) {
   return w;
 }
 
+// Items a partial persistent tile claims by default (nbvh_query_options.partial_items = 0).
+#ifndef NBVH_PARTIAL_ITEMS
+#define NBVH_PARTIAL_ITEMS 16
+#endif
+constexpr int32_t kPartialItems = NBVH_PARTIAL_ITEMS;
+
 // Persistent evaluations beside other instances' (concurrent hybrid form):
 // idle CTAs leave while the CTAs that stay, with this many spares, suffice.
 #ifndef NBVH_YIELD_SPARES
@@ -338,7 +345,8 @@ QueryWs carve_query(void* base, int64_t n, int32_t max_segs, size_t image = 0) {
 #endif
 constexpr int kYieldSpares = NBVH_YIELD_SPARES;
 
-PQueue pq_of(const QueryWs& w, int32_t max_segs, int64_t patience, int64_t spin_limit, bool yield_idle) {
+PQueue pq_of(const QueryWs& w, int32_t max_segs, int64_t patience, int32_t partial_items, int64_t spin_limit,
+             bool yield_idle) {
   int32_t* c = w.counters + pq_base(max_segs);
   PQueue q;
   q.head = reinterpret_cast<unsigned long long*>(c);
@@ -349,6 +357,7 @@ PQueue pq_of(const QueryWs& w, int32_t max_segs, int64_t patience, int64_t spin_
   q.exited = reinterpret_cast<unsigned int*>(c + 100);
   q.yield_idle = yield_idle ? kYieldSpares + 1 : 0;
   q.patience = patience;
+  q.partial_items = partial_items;
   q.spin_limit = spin_limit > 0 ? spin_limit : kPqSpinLimit;
   q.ring = reinterpret_cast<unsigned long long*>(w.queue[0]);
   return q;
@@ -434,7 +443,9 @@ cudaError_t launch_query_stages(const nbvh_model_desc* desc, const GridParams& g
   }
   if (persistent) {
     // one launch drains a queue of (slot, ray) items
-    a.pq = pq_of(w, max_segs, o.patience_cycles, o.wait_spins, init_t != nullptr);
+    // the warp-specialised pipeline has no lookahead rows: its partial tiles take every item
+    const int32_t partial = ws ? int32_t(kTcM) : (o.partial_items > 0 ? o.partial_items : kPartialItems);
+    a.pq = pq_of(w, max_segs, o.patience_cycles, partial, o.wait_spins, init_t != nullptr);
     pq_init_kernel<<<1, 1, 0, s>>>(w.counters, a.pq, o.test_phantom_items);
     count_launches(1);
     e = cudaGetLastError();
@@ -945,6 +956,9 @@ cudaError_t hybrid_neural(const nbvh_instance& x, int32_t i, const GridParams& g
   if (e != cudaSuccess) return e;
   nbvh_query_options oi = o;
   if (o.segments_out) oi.segments_out = o.segments_out + i;
+  // beside the other stream's instances, partial tiles take the whole queue
+  // by default (measured: 111 vs 114 ms per 16-asset frame with 16 items)
+  if (init_t && o.partial_items == 0) oi.partial_items = int32_t(kTcM);
   return launch_query_stages(&x.desc, gp, x.table, x.mlp, x.nodes, rays, x.max_segs, rec, w, true, out_inst, i, oi,
                              s, hw.lists + size_t(k) * size_t(rays.n), hw.counts + k, init_t, init_inst);
 }
@@ -1146,7 +1160,16 @@ extern "C" nbvh_status nbvh_autotune_query(const nbvh_model_desc* desc, const vo
         consider(c);
       }
   }
-  if (have) {  // stage 3: traversal CTA size
+  if (tc && have && b.opt.schedule == NBVH_SCHEDULE_PERSISTENT && !use_ws(desc, b.opt)) {
+    // stage 3: items per partial tile (the rest of the tile: lookahead rows)
+    const nbvh_tune_result base = b;
+    for (int32_t pi : {4, 8, 32, 128}) {
+      nbvh_tune_result c = base;
+      c.opt.partial_items = pi;
+      consider(c);
+    }
+  }
+  if (have) {  // stage 4: traversal CTA size
     const nbvh_tune_result base = b;
     for (int32_t tb : {64, 256}) {
       nbvh_tune_result c = base;

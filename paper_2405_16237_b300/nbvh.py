@@ -98,7 +98,7 @@ class QueryOptions(ctypes.Structure):
     _fields_ = [("schedule", c_int32), ("patience_cycles", c_int64), ("traverse_block", c_int32),
                 ("eval_threads", c_int32), ("w1_mode", c_int32), ("eval_pipeline", c_int32),
                 ("wait_spins", c_int64), ("test_phantom_items", c_int32), ("segments_out", c_void_p),
-                ("instance_streams", c_int32)]
+                ("instance_streams", c_int32), ("partial_items", c_int32)]
 
 
 class TuneResult(ctypes.Structure):
@@ -488,7 +488,7 @@ def options_dict(o: QueryOptions) -> dict:
     return {"schedule": ["waves", "persistent"][o.schedule], "patience_cycles": o.patience_cycles,
             "traverse_block": o.traverse_block, "eval_threads": o.eval_threads,
             "w1_mode": ["auto", "resident", "streamed"][o.w1_mode], "eval_pipeline": PIPELINES[o.eval_pipeline],
-            "instance_streams": o.instance_streams}
+            "instance_streams": o.instance_streams, "partial_items": o.partial_items}
 
 
 def options_from_dict(d: dict) -> QueryOptions:
@@ -496,7 +496,7 @@ def options_from_dict(d: dict) -> QueryOptions:
                          traverse_block=d["traverse_block"], eval_threads=d["eval_threads"],
                          w1_mode=["auto", "resident", "streamed"].index(d["w1_mode"]),
                          eval_pipeline=PIPELINES.index(d.get("eval_pipeline", "auto")),
-                         instance_streams=d.get("instance_streams", 0))
+                         instance_streams=d.get("instance_streams", 0), partial_items=d.get("partial_items", 0))
 
 
 def _opt_ref(options):

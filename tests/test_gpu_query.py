@@ -432,13 +432,14 @@ def test_graph_replay_equals_eager_query():
 
 @pytest.mark.parametrize("mp", [B.FP16, B.BF16])
 @pytest.mark.parametrize("patience", [0, 4000, 1 << 30])
-@pytest.mark.parametrize("pipeline", [B.PIPELINE_PHASES, B.PIPELINE_WARP_SPECIALISED])
-def test_persistent_schedule_equals_waves(mp, patience, pipeline):
+@pytest.mark.parametrize("pipeline,partial", [(B.PIPELINE_PHASES, 0), (B.PIPELINE_PHASES, 1),
+                                              (B.PIPELINE_PHASES, 128), (B.PIPELINE_WARP_SPECIALISED, 0)])
+def test_persistent_schedule_equals_waves(mp, patience, pipeline, partial):
     """The persistent queue (one launch, tiles claimed as resolves refill the
     queue; patience from eager partial tiles, which take lookahead rows, to
     waiting until drained), in the phase kernel and in the warp-specialised
     pipeline, gives bit-identical hit records to one launch per segment
-    slot."""
+    slot. Partial tiles claim at most `partial` items (0: the default)."""
     torch = _torch()
     b = built("icosphere_l6", 1.0, 2.0)
     rays = B.to_device_rays(W.mixed_rays(6000, seed=W.SEED_BASE + 31, radius=0.6))
@@ -448,7 +449,7 @@ def test_persistent_schedule_equals_waves(mp, patience, pipeline):
     ws = B.new_workspace(B.query_workspace_size(desc, rays["ox"].numel(), 24))
     hp = B.query_rays(desc, b.table, b.mlp, b.nodes, b.leaves["n_nodes"], rays, 24, workspace=ws,
                       options=B.query_options(schedule=B.SCHEDULE_PERSISTENT, patience_cycles=patience,
-                                              eval_pipeline=pipeline))
+                                              eval_pipeline=pipeline, partial_items=partial))
     segs, launches = B.query_stats(ws, rays["ox"].numel(), 24)
     assert B.device_status() == 0
     for k in hw:
@@ -460,7 +461,8 @@ def test_persistent_schedule_equals_waves(mp, patience, pipeline):
 @pytest.mark.parametrize("mp", [B.FP16, B.FP32])
 def test_autotuner_times_candidates_and_keeps_results(mp):
     """nbvh_autotune_query: the schedules (and for FP16/BF16 the evaluation
-    CTA shapes and first-layer placements, then traversal CTA sizes) are each
+    CTA shapes and first-layer placements, the partial-tile sizes, then
+    traversal CTA sizes) are each
     timed; the fastest is returned, nothing is kept in the library, and every
     candidate's options give hit records equal to the default query's bit for
     bit (the options change only the order and shape of evaluation)."""
@@ -482,7 +484,12 @@ def test_autotuner_times_candidates_and_keeps_results(mp):
         shapes = {(c["eval_pipeline"], c["eval_threads"], c["w1_mode"]) for c in cands}
         phase_shapes = {("phases", t, w) for t in (256, 512) for w in ("resident", "streamed")}
         assert len(phase_shapes - shapes) <= 1 and ("auto", 0, "auto") in shapes
-        assert n_sched + 3 + 2 <= len(cands) <= n_sched + 5 + 2
+        # stage 3 (partial-tile sizes 4, 8, 32, 128) runs when the best so far
+        # is the persistent phase kernel
+        n_partial = sum(1 for c in cands if c["partial_items"] != 0)
+        assert n_partial in (0, 4)
+        assert {c["partial_items"] for c in cands} == ({0, 4, 8, 32, 128} if n_partial else {0})
+        assert n_sched + 3 + 2 + n_partial <= len(cands) <= n_sched + 5 + 2 + n_partial
     assert all(c["ms"] > 0 for c in cands)
     assert best["ms"] == min(c["ms"] for c in cands)
     for c in cands:
