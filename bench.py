@@ -1222,7 +1222,7 @@ def time_latency(args, world, flush):
 
 
 # ---------------------------------------------------------------------------- uneven segments (S6)
-def time_uneven(args, world, flush):
+def time_uneven(args, world, flush, pool=None):
     """64 displaced sphere clusters (1k-200k triangles each) in one 8,192-leaf
     N-BVH; 4,194,304 rays (60% from a camera, 40% sphere chords) with 1-40
     segments each; the icosphere model in FP16. The autotuner picks the
@@ -1273,7 +1273,22 @@ def time_uneven(args, world, flush):
     segs, _ = B.query_stats(ws, n, ms_max)
     ms = dist_max(total, world) / args.uneven_steps
     hit = cnt > 0
+    cpu = None
+    if pool is not None:
+        from oracle import nbvh_oracle as O
+        rng = np.random.default_rng(SEED + 7)
+        idx = np.sort(rng.choice(n, size=min(args.accuracy_rays, n), replace=False))
+        inst = [{"kind": "neural", "leaves": O.build_leaves(tris, spec.n_leaves, spec.inflate_rel),
+                 "table": table.float().cpu().numpy(),
+                 "layers": B.unpack_mlp(mlp.cpu().numpy(), cfg.mlp_dims()),
+                 "layout": O.level_layout(cfg.n_levels, cfg.base_res, cfg.growth, cfg.log2_table),
+                 "n_samples": cfg.n_samples}]
+        _, wall = pool.run(pool.add_job("query", inst), W.subset(rays_np, idx))
+        cpu = {"value": len(idx) / wall / 1e6, "unit": "Mrays/s", "cores": pool.n, "kind": "oracle",
+               "sample": f"{len(idx)} seeded rays of the 4,194,304 (every segment evaluated), {pool.n} "
+                         f"single-threaded processes, {wall:.1f} s wall"}
     return {"workload": spec.name, "value": world * n / (ms * 1e-3) / 1e6, "unit": "Mrays/s", "ms_per_query": ms,
+            "cpu_baseline": cpu,
             "rays": n, "triangles": int(len(tris)), "segments_per_ray": {
                 "max": int(cnt.max()), "mean_of_rays_with_segments": float(cnt[hit].mean()),
                 "rays_with_segments": int(hit.sum()), "p99": float(np.percentile(cnt[hit], 99))},
@@ -1614,7 +1629,7 @@ def run_gpu(args, world, rank):
                                  "ms_per_step": line["icosphere"]["ms_per_step"], "config": {
                                      "workload": spec.name}})
             if only == "all":
-                line["uneven"] = time_uneven(args, world, flush) if args.uneven_steps > 0 else None
+                line["uneven"] = time_uneven(args, world, flush, pool) if args.uneven_steps > 0 else None
                 line["cut_optimization"] = time_cut(args, world) if args.cut_steps > 0 else None
                 line["levels_of_detail"] = time_lod(args, world, flush) if args.lod_steps > 0 else None
                 line["albedo_head"] = time_albedo(args, world, wl, flush) if not args.no_albedo else None
