@@ -84,7 +84,7 @@ def parse():
                    help="keep the library's default query options (no autotuning before the timed region)")
     p.add_argument("--primary", default="1920x1080",
                    help="primary image of the icosphere workload (smaller only for profiling captures)")
-    p.add_argument("--only", default="all", choices=["all", "hybrid", "icosphere", "train", "latency"],
+    p.add_argument("--only", default="all", choices=["all", "hybrid", "icosphere", "train", "latency", "uneven"],
                    help="run one workload only, without CPU baselines (profiling captures)")
     return p.parse_args()
 
@@ -1638,6 +1638,8 @@ def run_gpu(args, world, rank):
             torch.cuda.empty_cache()
         if only in ("all", "latency"):
             line["latency_4096_rays"] = time_latency(args, world, Flusher())
+        if only == "uneven":
+            line["uneven"] = time_uneven(args, world, Flusher())
         if B.device_status() != 0:
             raise RuntimeError("device status at the end of the run")
     finally:

@@ -371,8 +371,8 @@ typedef struct {
  * pipeline and shape); (2) for FP16/BF16 the other evaluation pipeline and
  * the phase kernel's CTA shapes, 256 and 512 threads (256 only for width
  * <= 64) times resident and streamed first-layer weights, where the model
- * stages them; (3) for the persistent phase kernel, partial tiles of 4, 8,
- * 16 (the default) and 32 items and of whole-queue claims (128); (4)
+ * stages them; (3) from the fastest persistent phase-kernel candidate,
+ * partial tiles of 4, 8, 32 and 128 items (16 is the default); (4)
  * traversal CTAs of 64, 128 and 256 threads. Each
  * candidate runs once untimed and reps times timed (CUDA events on the
  * stream, median). The first all_cap candidates with their times go to

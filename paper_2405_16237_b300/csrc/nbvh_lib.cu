@@ -1160,9 +1160,19 @@ extern "C" nbvh_status nbvh_autotune_query(const nbvh_model_desc* desc, const vo
         consider(c);
       }
   }
-  if (tc && have && b.opt.schedule == NBVH_SCHEDULE_PERSISTENT && !use_ws(desc, b.opt)) {
+  // the fastest persistent phase-kernel candidate so far (stage 3 starts
+  // from it even when waves lead: its partial tiles may change the order)
+  bool have_pers = false;
+  nbvh_tune_result best_pers;
+  std::memset(&best_pers, 0, sizeof(best_pers));
+  for (const nbvh_tune_result& c : cand)
+    if (c.opt.schedule == NBVH_SCHEDULE_PERSISTENT && !use_ws(desc, c.opt) && (!have_pers || c.ms < best_pers.ms)) {
+      best_pers = c;
+      have_pers = true;
+    }
+  if (tc && have_pers) {
     // stage 3: items per partial tile (the rest of the tile: lookahead rows)
-    const nbvh_tune_result base = b;
+    const nbvh_tune_result base = best_pers;
     for (int32_t pi : {4, 8, 32, 128}) {
       nbvh_tune_result c = base;
       c.opt.partial_items = pi;
