@@ -691,8 +691,7 @@ def hybrid_details(args, world, hw, flush, pool, oinst, frame_ms):
                        "dominant_kernel_class": dom,
                        "launches_per_frame": r.get("groups"), "ms_per_frame": r.get("ms"),
                        "bytes_per_frame": bytes_eval,
-                       "traffic": (traffic["dram_bytes_per_segment"] * float(seg[1:].sum()) / max(1.0, r["groups"])
-                                   if traffic and r else None)}
+                       "traffic": traffic["dram_bytes_per_launch"] if traffic else None}
     out["kernels"] = kernels
     out["segments_per_frame"] = {"total": int(seg[1:].sum()), "per_asset": per_asset}
 
@@ -1034,14 +1033,15 @@ def time_icosphere(args, world, rank, wl, flush, pool, clocks_cb):
                 "frac": ev.get("frac"), "peak_source": peak_kind,
                 "kernel": "eval_tc_kernel (query mode): gather + trilinear + tcgen05 MLP + resolve",
                 "bytes_per_segment": b_seg, "segments_per_step": seg_step,
-                "traffic": (traffic["dram_bytes_per_segment"] * seg_step / max(1.0, ev.get("groups", 1))
-                            if traffic else None),
+                "traffic": traffic["dram_bytes_per_launch"] if traffic else None,
+                "traffic_how": traffic["note"] if traffic else None,
                 "l2_gather": {
                     "ceiling_gsectors_s": l2_ceiling,
                     "how": "nbvh_probe_l2_gather: random 4-byte loads from a 64 MB L2-resident table, one "
                            "1024-thread CTA per SM, 16 loads in flight per thread",
                     "kernel_gsectors_s": (traffic["l2_sectors_per_segment"] * seg_step / (ev["ms"] * 1e-3) / 1e9
-                                          if traffic and ev else None)}}
+                                          if traffic and ev else None),
+                    "sectors_per_segment_from": "the committed 960x540 capture (profiles/traffic.json)"}}
     if roofline["l2_gather"]["kernel_gsectors_s"]:
         roofline["l2_gather"]["frac"] = roofline["l2_gather"]["kernel_gsectors_s"] / l2_ceiling
 
@@ -1080,7 +1080,8 @@ def time_icosphere(args, world, rank, wl, flush, pool, clocks_cb):
            "gpu_launches_per_step": launches16, "dtype": "f16 table, f16 tensor-core MLP",
            "fp32_plain": {"value": world * rays_step / (ms32 * 1e-3) / 1e6, "ms_per_step": ms32},
            "bf16_tc": {"value": world * rays_step / (msbf * 1e-3) / 1e6, "ms_per_step": msbf},
-           "network": "trained by the training measurement above",
+           "network": ("trained by the training measurement above" if "train" in args.__dict__.get("_ran", ())
+                       else "untrained (initial weights)"),
            "schedule": {"options": B.options_dict(wl.options), "plan": B.eval_plan(d16, wl.options),
                         "autotuner": {"best": tune_best, "candidates": tune_all}},
            "kernels": kernels, "roofline": roofline,
@@ -1620,8 +1621,10 @@ def run_gpu(args, world, rank):
             spec, tris, rays_np = make_scene(args.primary)
             wl = GpuWorkload(spec, tris, rays_np, args.max_segs)
             flush = Flusher()
+            args._ran = ()
             if args.train_steps > 0 and only in ("all", "train"):
                 line["train"] = train_icosphere(args, world, wl, flush)
+                args._ran = ("train",)
             if only in ("all", "icosphere"):
                 line["icosphere"] = time_icosphere(args, world, rank, wl, flush, pool, clocks_cb)
                 if not line.get("value"):
