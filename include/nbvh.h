@@ -490,9 +490,12 @@ nbvh_status nbvh_train_labels(nbvh_rays rays, const int32_t* leaf, const float* 
  * chunk's forward again to rebuild its activations before differentiating it
  * (the same gradients up to FP32 summation order). The calls choose the mode
  * from ws_bytes, so a forward and its backward must get the same ws_bytes.
- * Training supports first layers the kernels stage whole: N * L * F up to
- * about 768 at width 64 (FP16/BF16) and similar for FP32; larger models
- * return NBVH_ERR_UNSUPPORTED before anything is enqueued. */
+ * Training supports N * L * F up to 2048 at width 64 in FP16/BF16 (the
+ * forward chunks the first layer as the query does; the backward copies W0^T
+ * 128 features at a time when it does not fit shared memory whole). The FP32
+ * training kernels stage the first layer whole, which caps N * L * F at
+ * about 550 at width 64. Larger models return NBVH_ERR_UNSUPPORTED before
+ * anything is enqueued. */
 nbvh_status nbvh_train_workspace_size(const nbvh_model_desc* desc, int64_t n, int32_t n_leaves, size_t* bytes);
 
 /* Host. Memory budget of a training workspace: *bytes = the stored-mode size
