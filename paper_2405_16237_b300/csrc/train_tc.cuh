@@ -592,18 +592,36 @@ constexpr int kWgTcItems = 64;
 constexpr int kWgTcThreads = 256;
 
 __host__ __device__ inline int wg_tc_tiles(int Kp) { return (Kp + 127) / 128; }
-__host__ __device__ inline uint32_t wg_tc_smem(int Kp, int W) {
-  return uint32_t(wg_tc_tiles(Kp)) * 128 * kWgTcItems * 2 + uint32_t(W) * kWgTcItems * 2 + 128 + 128;
+// One stage: the features of 64 items ([Kp][64]) and their dZ0 ([W][64]).
+__host__ __device__ inline uint32_t wg_tc_stage_bytes(int Kp, int W) {
+  return uint32_t(wg_tc_tiles(Kp)) * 128 * kWgTcItems * 2 + uint32_t(W) * kWgTcItems * 2;
 }
+// Two stages (the next chunk copied in while the tensor cores take this one)
+// where they fit shared memory, else one.
+__host__ __device__ inline int wg_tc_stages(int Kp, int W) {
+  return 2 * wg_tc_stage_bytes(Kp, W) + 256 <= 227u * 1024u ? 2 : 1;
+}
+__host__ __device__ inline uint32_t wg_tc_smem(int Kp, int W) {
+  return uint32_t(wg_tc_stages(Kp, W)) * wg_tc_stage_bytes(Kp, W) + 128 + 128;
+}
+
+// 16 bytes global -> shared, asynchronous; bytes beyond src_bytes (0..16) are zero.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 template <int W, bool BF16>
 __global__ void __launch_bounds__(kWgTcThreads, 1) weight_grad_tc(WgTcArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   const int tiles = wg_tc_tiles(a.Kp);
-  uint8_t* sA = smem;
-  uint8_t* sB = smem + size_t(tiles) * 128 * kWgTcItems * 2;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sB + size_t(W) * kWgTcItems * 2);
+  const int stages = wg_tc_stages(a.Kp, W);
+  const uint32_t stage_bytes = wg_tc_stage_bytes(a.Kp, W);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + size_t(stages) * stage_bytes);
   uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bar + 1);
   const int64_t n_chunks = (a.n + kWgTcItems - 1) / kWgTcItems;
   if (int64_t(blockIdx.x) >= n_chunks) return;
@@ -626,34 +644,42 @@ __global__ void __launch_bounds__(kWgTcThreads, 1) weight_grad_tc(WgTcArgs a) {
   float bsum = 0.0f;  // thread t < W: sum of dZ0 over its neuron
   uint32_t phase = 0;
   bool failed = false, first = true;
-  // 16-byte pieces of a [rows][64 items] tile into the K-major core-matrix layout
+  // 16-byte pieces of a [rows][64 items] tile into the K-major core-matrix
+  // layout, copied asynchronously (zeros past the batch and past valid_rows)
   auto stage = [&](uint8_t* dst, const uint16_t* src, int rows, int valid_rows, int64_t c0) {
     for (int p = threadIdx.x; p < rows * 8; p += blockDim.x) {
       const int r = p >> 3, q = p & 7;
       const int64_t col = c0 + 8 * q;
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (r < valid_rows) {
-        const uint16_t* g = src + int64_t(r) * a.ld + col;
-        if (col + 8 <= a.n) {
-          v = *reinterpret_cast<const uint4*>(g);
-        } else {
-          uint16_t e[8];
-#pragma unroll
-          for (int t = 0; t < 8; ++t) e[t] = col + t < a.n ? g[t] : uint16_t(0);
-          v = make_uint4(e[0] | (uint32_t(e[1]) << 16), e[2] | (uint32_t(e[3]) << 16), e[4] | (uint32_t(e[5]) << 16),
-                         e[6] | (uint32_t(e[7]) << 16));
-        }
-      }
-      *reinterpret_cast<uint4*>(dst + op_offset(r, 8 * q, kWgTcItems)) = v;
+      const int64_t left = r < valid_rows ? a.n - col : 0;
+      const uint32_t bytes = left >= 8 ? 16u : (left > 0 ? uint32_t(left) * 2u : 0u);
+      const uint16_t* g = bytes ? src + int64_t(r) * a.ld + col : src;
+      cp_async16(dst + op_offset(r, 8 * q, kWgTcItems), g, bytes);
     }
   };
-  for (int64_t c = blockIdx.x; c < n_chunks && !failed; c += gridDim.x) {
+  auto issue = [&](int buf, int64_t c) {
+    uint8_t* sA = smem + size_t(buf) * stage_bytes;
+    uint8_t* sB = sA + size_t(tiles) * 128 * kWgTcItems * 2;
     const int64_t c0 = c * kWgTcItems;
     for (int t = 0; t < tiles; ++t)
       stage(sA + size_t(t) * 128 * kWgTcItems * 2, a.XT + int64_t(t) * 128 * a.ld, 128, min(128, a.K - 128 * t), c0);
     stage(sB, a.ZT, W, W, c0);
+    cp_async_commit();
+  };
+  issue(0, blockIdx.x);
+  int i = 0;
+  for (int64_t c = blockIdx.x; c < n_chunks && !failed; c += gridDim.x, ++i) {
+    const int b = stages == 2 ? (i & 1) : 0;
+    const int64_t cn = c + gridDim.x;
+    if (stages == 2 && cn < n_chunks) {
+      issue(b ^ 1, cn);  // its buffer's last MMA (the previous chunk) has completed
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
     fence_proxy_async_smem();
     __syncthreads();
+    uint8_t* sA = smem + size_t(b) * stage_bytes;
+    uint8_t* sB = sA + size_t(tiles) * 128 * kWgTcItems * 2;
     if (threadIdx.x < W) {
       for (int q = 0; q < kWgTcItems; ++q) {
         const uint16_t e = *reinterpret_cast<const uint16_t*>(sB + op_offset(threadIdx.x, q, kWgTcItems));
@@ -676,7 +702,9 @@ __global__ void __launch_bounds__(kWgTcThreads, 1) weight_grad_tc(WgTcArgs a) {
     phase ^= 1u;
     if (__syncthreads_or(!ok)) failed = true;
     tc_fence_after();
+    if (stages == 1 && cn < n_chunks && !failed) issue(0, cn);  // the buffer is free once the MMA completed
   }
+  cp_async_wait<0>();  // no copy left in flight into the freed buffers
   if (!failed && warp < 4) {
     const int q = warp;  // lane quarter
     const uint32_t t_row = tmem + (uint32_t(q * 32) << 16);
