@@ -801,9 +801,9 @@ namespace {
 // neural instance (n_rays entries) and their counts, then for the concurrent
 // form a per-ray instance mask and one staging hit record per neural
 // instance (albedo arrays when an instance has the albedo head).
-// At most two: on the 16-asset scene (3840x2160, 4 bounces) two streams took
-// the frame from 128 to 111 ms, three and four 116-123 ms (the kernels
-// contend for SMs and L2).
+// At most two: on the 16-asset scene (3840x2160, 4 bounces) one stream takes
+// 117 ms per frame, two 101, three and four 105 and 107 (the kernels contend
+// for SMs and L2).
 constexpr int kHybridStreams = 2;
 
 struct HybridWs {
