@@ -207,15 +207,17 @@ nbvh_status nbvh_encode(const nbvh_model_desc* desc, const void* table, nbvh_ray
  *                   tile before it takes fewer items (0 .. 2^40).
  *  traverse_block   threads per traversal CTA: 64, 128 or 256.
  *  eval_threads     FP16/BF16 evaluation CTA: 256 (two CTAs per SM, hidden
- *                   width <= 64), 512 (one CTA per SM), 0 = automatic (256
- *                   where the width allows).
+ *                   width <= 64), 512 (one CTA per SM), 0 = automatic (512).
  *  w1_mode          FP16/BF16 evaluation: where the first layer's weights
  *                   live. NBVH_W1_RESIDENT: converted into shared memory once
  *                   per CTA; NBVH_W1_STREAMED: converted once per call into a
  *                   16-bit image in the workspace and streamed through two
  *                   shared-memory buffers, 128 inputs at a time, by bulk
- *                   copies; NBVH_W1_AUTO: resident when it fits the CTA's
- *                   shared-memory budget, else streamed.
+ *                   copies; NBVH_W1_AUTO: streamed (on the mixed scene's
+ *                   per-instance launches the per-CTA conversion of resident
+ *                   weights cost 11 % of the frame; on one large launch the
+ *                   two placements tie). The training forward places its
+ *                   weights itself: resident when they fit.
  *  eval_pipeline    persistent FP16/BF16 schedule: NBVH_PIPELINE_PHASES runs
  *                   each tile in CTA-wide phases (all warps gather, then the
  *                   MLP, resolve and claim); NBVH_PIPELINE_WARP_SPECIALISED

@@ -1320,7 +1320,11 @@ struct TcPlan {
 constexpr uint32_t kSmemMax = 227 * 1024;       // per CTA
 constexpr uint32_t kSmemHalf = 113 * 1024;      // per CTA with two CTAs on an SM
 
-inline TcPlan tc_plan(const nbvh_model_desc* d, int threads_opt, int w1_mode) {
+// w1_mode NBVH_W1_AUTO: streamed for a query (query = true: on the mixed
+// scene's many per-instance launches the per-CTA conversion of resident
+// weights cost 11 % of the frame; on one large launch the two tie), else
+// resident when it fits the CTA's budget.
+inline TcPlan tc_plan(const nbvh_model_desc* d, int threads_opt, int w1_mode, bool query = true) {
   TcPlan p;
   std::memset(&p, 0, sizeof(p));
   const int W = d->width;
@@ -1333,7 +1337,7 @@ inline TcPlan tc_plan(const nbvh_model_desc* d, int threads_opt, int w1_mode) {
   const uint32_t budget = p.threads == 256 ? kSmemHalf : kSmemMax;
   if (w1_mode == NBVH_W1_RESIDENT) p.stream = false;
   else if (w1_mode == NBVH_W1_STREAMED) p.stream = true;
-  else p.stream = res.total > budget;
+  else p.stream = query || res.total > budget;
   const TcLayout& T = p.stream ? str : res;
   p.smem = T.total;
   p.ncols = T.ncols;

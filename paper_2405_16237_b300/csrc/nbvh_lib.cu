@@ -200,11 +200,11 @@ cudaError_t launch_ws(const nbvh_model_desc* d, const EvalArgs& a, cudaStream_t 
 // first layer's 16-bit image is written into `image` (once per call, before
 // the evaluation launches) and a.w1_image points at it.
 cudaError_t prepare_eval(const nbvh_model_desc* d, EvalArgs& a, const nbvh_query_options& o, void* image,
-                         TcPlan* plan, cudaStream_t s) {
+                         TcPlan* plan, cudaStream_t s, bool query = true) {
   std::memset(plan, 0, sizeof(*plan));
   a.w1_image = nullptr;
   if (d->mlp_prec == NBVH_FP32) return cudaSuccess;
-  *plan = tc_plan(d, o.eval_threads, o.w1_mode);
+  *plan = tc_plan(d, o.eval_threads, o.w1_mode, query);
   if (!plan->ok) return cudaErrorInvalidConfiguration;
   if (plan->stream) {
     if (!image) return cudaErrorInvalidConfiguration;
@@ -1468,7 +1468,7 @@ bool train_stageable(const nbvh_model_desc* d) {
            train_bwd_smem(K, W, d->n_hidden, d->n_out) <= kSmemMax;
   if (W != 32 && W != 64 && W != 128) return false;
   const TcBwdLayout bl = tc_bwd_layout(K, W, d->n_hidden, bwd_w0_streamed(K, W, d->n_hidden));
-  return tc_plan(d, 0, NBVH_W1_AUTO).ok && bl.total <= kSmemMax && bl.ncols <= 512;
+  return tc_plan(d, 0, NBVH_W1_AUTO, false).ok && bl.total <= kSmemMax && bl.ncols <= 512;
 }
 
 cudaError_t launch_train(bool bwd, const nbvh_model_desc* d, const TrainArgs& a, cudaStream_t s) {
@@ -1815,7 +1815,7 @@ nbvh_status forward_train_impl(const nbvh_model_desc* desc, const void* table, c
   const Labels lab{labels.hit, labels.depth, labels.nx, labels.ny, labels.nz, labels.ar, labels.ag, labels.ab};
   EvalArgs pa = base_args(desc, gp, table, mlp, rays);
   TcPlan plan;
-  cudaError_t e = prepare_eval(desc, pa, default_options(), w.image, &plan, s);
+  cudaError_t e = prepare_eval(desc, pa, default_options(), w.image, &plan, s, false);
   for (int64_t i0 = 0; i0 < rays.n && e == cudaSuccess; i0 += chunk)
     e = forward_chunk(desc, gp, table, mlp, chunk_of(rays, leaf, t0, t1, order, i0, std::min(chunk, rays.n - i0)),
                       lab, n_valid, loss_scale, loss_scale_dev, w, plan, pa.w1_image, s);
@@ -1849,7 +1849,7 @@ nbvh_status backward_impl(const nbvh_model_desc* desc, const void* table, const 
   EvalArgs pa = base_args(desc, gp, table, mlp, rays);
   TcPlan plan;
   cudaError_t e = cudaSuccess;
-  if (recompute) e = prepare_eval(desc, pa, default_options(), w.image, &plan, s);
+  if (recompute) e = prepare_eval(desc, pa, default_options(), w.image, &plan, s, false);
   const Labels none{};
   for (int64_t i0 = 0; i0 < rays.n && e == cudaSuccess; i0 += chunk) {
     const Chunk k = chunk_of(rays, leaf, t0, t1, order, i0, std::min(chunk, rays.n - i0));
