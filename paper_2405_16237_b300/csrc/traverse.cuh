@@ -261,26 +261,36 @@ __device__ __forceinline__ bool root_meets(const nbvh_node* __restrict__ nodes, 
   return h0 || h1;
 }
 
-// The ray against the root's bounding box grown on every side by
-// g = 1e-3 of its size + 1e-4 (1 + |lo| + |hi|), the interval ends compared
-// with a relative slack of 1e-5. A "false" is conservative: these slab values
-// and the traversal's exactly rounded ones differ by a few ulps of
-// (b - o) / d, far less than g / |d|, so a ray this rejects fails the
-// traversal's root test (root_meets) too. A direction component too small for
-// a finite reciprocal passes.
-__device__ __forceinline__ bool root_maybe(const float* __restrict__ box, const RayR& ray, float best) {
-  float en = ray.tmin, ex = fminf(ray.tmax, best);
-  const float slack = 1e-5f;
+// The root's bounding box grown on every side by g = 1e-3 of its size +
+// 1e-4 (1 + |lo| + |hi|) (computed once per CTA into gbox: lo - g, hi + g).
+__device__ __forceinline__ void grow_box(const float* box, float* gbox) {
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     const float lo = box[i], hi = box[3 + i];
     const float g = 1e-3f * (hi - lo) + 1e-4f * (1.0f + fabsf(lo) + fabsf(hi));
-    if (ray.d[i] != 0.0f && !isfinite(ray.inv[i])) return true;
+    gbox[i] = lo - g;
+    gbox[3 + i] = hi + g;
+  }
+}
+
+// The ray against a grown root box (grow_box), the interval ends compared with
+// a relative slack of 1e-5; ex0 = min(tmax, the ray's record). A "false" is
+// conservative: these slab values and the traversal's exactly rounded ones
+// differ by a few ulps of (b - o) / d, far less than g / |d|, so a ray this
+// rejects fails the traversal's root test (root_meets) too. A ray with a
+// direction component too small for a finite reciprocal passes every box
+// (the caller's check).
+__device__ __forceinline__ bool root_maybe(const float* __restrict__ gbox, const RayR& ray, float ex0) {
+  float en = ray.tmin, ex = ex0;
+  const float slack = 1e-5f;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const float glo = gbox[i], ghi = gbox[3 + i];
     if (ray.d[i] == 0.0f) {
-      if (ray.o[i] < lo - g || ray.o[i] > hi + g) return false;
+      if (ray.o[i] < glo || ray.o[i] > ghi) return false;
     } else {
-      const float ta = (lo - g - ray.o[i]) * ray.inv[i];
-      const float tb = (hi + g - ray.o[i]) * ray.inv[i];
+      const float ta = (glo - ray.o[i]) * ray.inv[i];
+      const float tb = (ghi - ray.o[i]) * ray.inv[i];
       en = fmaxf(en, fminf(ta, tb));
       ex = fminf(ex, fmaxf(ta, tb));
     }
@@ -293,15 +303,17 @@ static __global__ void __launch_bounds__(256) tlas_cull_kernel(RayPtrs rays, int
   constexpr int kWarps = 256 / 32;
   __shared__ int s_cnt[kMaxInstances], s_base[kMaxInstances];
   __shared__ int s_wbase[kWarps][kMaxInstances];  // a warp's offset within the block's share
-  __shared__ float s_box[kMaxInstances][6];       // root bounding boxes
+  __shared__ float s_box[kMaxInstances][6];       // grown root bounding boxes
   for (int k = threadIdx.x; k < c.n_inst; k += blockDim.x) {
     s_cnt[k] = 0;
     const nbvh_node* nd = c.root[k];
     const bool two = nd->child1 != kNodeNone;
+    float box[6];
     for (int j = 0; j < 3; ++j) {
-      s_box[k][j] = two ? fminf(nd->lo0[j], nd->lo1[j]) : nd->lo0[j];
-      s_box[k][3 + j] = two ? fmaxf(nd->hi0[j], nd->hi1[j]) : nd->hi0[j];
+      box[j] = two ? fminf(nd->lo0[j], nd->lo1[j]) : nd->lo0[j];
+      box[3 + j] = two ? fmaxf(nd->hi0[j], nd->hi1[j]) : nd->hi0[j];
     }
+    grow_box(box, s_box[k]);
   }
   __syncthreads();
   const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -312,8 +324,16 @@ static __global__ void __launch_bounds__(256) tlas_cull_kernel(RayPtrs rays, int
     const RayR ray = make_rayr(rays.ox[r], rays.oy[r], rays.oz[r], rays.dx[r], rays.dy[r], rays.dz[r],
                                rays.tmin[r], rays.tmax[r]);
     const float best = best_t[r];
-    for (int k = 0; k < c.n_inst; ++k)
-      if (root_maybe(s_box[k], ray, best)) mask |= uint64_t(1) << k;
+    bool tiny = false;  // a direction component too small for a finite reciprocal
+#pragma unroll
+    for (int i = 0; i < 3; ++i) tiny |= ray.d[i] != 0.0f && !isfinite(ray.inv[i]);
+    if (tiny) {
+      mask = c.n_inst >= 64 ? ~uint64_t(0) : (uint64_t(1) << c.n_inst) - 1;
+    } else {
+      const float ex0 = fminf(ray.tmax, best);
+      for (int k = 0; k < c.n_inst; ++k)
+        if (root_maybe(s_box[k], ray, ex0)) mask |= uint64_t(1) << k;
+    }
   }
   if (active && c.mask) c.mask[r] = mask;
   // count: one shared-memory increment per warp and instance
