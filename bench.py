@@ -930,15 +930,18 @@ def train_rooflines(kt, wl, batch, n_leaves, scene):
            "scatter": {"issued_adds_per_ray": issued, "algorithmic_adds_per_ray": algo, "valid_fraction": valid}}
     spec = {
         "train_rays": ("hbm", batch * (32 + 12 + 12), "GB/s", "per ray 32 B ray + leaf, t0, t1 + 12 B grouping"),
-        "train_forward": ("hbm", batch * (K // cfg.n_features * 8 * cfg.n_features * 2 + K * 2 + nh * W_ * 2 + 44),
+        "train_forward": ("hbm", batch * (K // cfg.n_features * 8 * cfg.n_features * 2 + K * 2 + nh * W_ * 2
+                                          + (nh - 1) * W_ * 2 + 44),
                           "GB/s", "per ray the gather (N*L*8 corners*F*2 B) + stored features (K*2 B) + hidden "
-                                  "activations (n_hidden*W*2 B) + outputs, dL/draw, loss term (44 B)"),
+                                  "activations (n_hidden*W*2 B) and the neuron-major copies of those feeding a "
+                                  "hidden layer ((n_hidden-1)*W*2 B) + outputs, dL/draw, loss term (44 B)"),
         "train_backward": ("l2_atomic", batch * issued, "Gadds/s",
                            "float2 table-gradient adds the kernel issues per training ray (the method's N*L*8 "
                            "corner updates per valid ray, merged along the ray: scatter) against "
                            "nbvh_probe_l2_reduce"),
-        "weight_grad": ("hbm", batch * (K * 2 + 2 * nh * W_ * 2 + W_ * 2 + 5 * 4), "GB/s",
-                        "per ray features (K*2 B), dZ and H (2*n_hidden*W*2 B), neuron-major dZ0, dL/draw"),
+        "weight_grad": ("hbm", batch * (K * 2 + 2 * nh * W_ * 2 + cfg.n_out * 4), "GB/s",
+                        "per ray the operands read: features (K*2 B), each layer's dZ and input activations "
+                        "(2*n_hidden*W*2 B), dL/draw (n_out*4 B)"),
         "adam": ("hbm", (n_params_tab + n_params_mlp) * 30, "GB/s",
                  "per parameter 30 B (master, gradient, two moments read; master, moments, 16-bit copy written; "
                  "gradient cleared)"),

@@ -66,6 +66,8 @@ struct TcTrain {
   uint16_t* X16;      // [Kp][ld] feature-major (one row per feature, items along it)
   int64_t ld;         // row stride of X16 (items, rounded up to 64)
   uint16_t* H16;      // [n_hidden][n][W]
+  uint16_t* HT16;     // [n_hidden - 1][W][ld] the hidden activations that feed a hidden
+                      // layer again, neuron-major (nullptr: not stored)
   float* O;           // [n][n_out]
   float* G;           // [n][n_out]
   float* loss_seg;    // [n]

@@ -1162,6 +1162,14 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) eval_tc_kernel(EvalArgs
             uint32_t* hdst = reinterpret_cast<uint32_t*>(a.tr.H16 + (size_t(h) * size_t(n_items) + size_t(grow)) * W + c0);
 #pragma unroll
             for (int i = 0; i < kCols / 2; ++i) hdst[i] = pk[i];
+            if (a.tr.HT16 && h + 1 < a.n_hidden) {  // the next hidden layer's weight gradient reads it neuron-major
+              uint16_t* hT = a.tr.HT16 + (size_t(h) * W + c0) * size_t(xld) + size_t(grow);
+#pragma unroll
+              for (int i = 0; i < kCols / 2; ++i) {
+                hT[size_t(2 * i) * size_t(xld)] = uint16_t(pk[i] & 0xffffu);
+                hT[size_t(2 * i + 1) * size_t(xld)] = uint16_t(pk[i] >> 16);
+              }
+            }
           }
         }
         tmem_st_wait();

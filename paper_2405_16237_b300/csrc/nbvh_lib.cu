@@ -1375,9 +1375,10 @@ struct TrainWs {
   float *O, *G, *loss_seg;           // per ray (or item): raw outputs, dL/d(raw), loss terms
   int64_t chunk;                     // rays per activation chunk
   float *X, *H, *dZ;                 // FP32 path: features [c][K], H and dZ [n_hidden][c][W]
-  uint16_t *X16, *H16, *dZ16;        // tensor-core path: 16-bit operands (X16 feature-major)
-  uint16_t* dZT0;                    // first layer's dZ, neuron-major
-  int64_t ld;                        // row stride of X16 and dZT0
+  uint16_t *X16, *H16;              // tensor-core path: 16-bit operands (X16 feature-major)
+  uint16_t* HT16;                    // [n_hidden - 1][W][ld] H of the layers feeding a hidden layer, neuron-major
+  uint16_t* dZT;                     // [n_hidden][W][ld] every layer's dZ, neuron-major
+  int64_t ld;                        // row stride of X16, HT16 and dZT
   void* image;                       // streamed first-layer image
   uint8_t* bwd_image;                // W0^T of the streamed backward (else null)
   int32_t *counts, *cursor, *order;  // rays grouped by trained leaf (training step)
@@ -1429,9 +1430,9 @@ TrainWs carve_train(void* base, const nbvh_model_desc* d, int64_t n, int32_t n_l
     const size_t Kp = (K + 15) & ~size_t(15);
     w.ld = int64_t((C + 63) & ~size_t(63));
     w.X16 = reinterpret_cast<uint16_t*>(take(2 * size_t(w.ld) * Kp));
-    w.dZT0 = reinterpret_cast<uint16_t*>(take(2 * size_t(w.ld) * Wd));
+    w.dZT = reinterpret_cast<uint16_t*>(take(2 * size_t(w.ld) * Wd * nh));
     w.H16 = reinterpret_cast<uint16_t*>(take(2 * nh * C * Wd));
-    w.dZ16 = reinterpret_cast<uint16_t*>(take(2 * nh * C * Wd));
+    if (nh > 1) w.HT16 = reinterpret_cast<uint16_t*>(take(2 * size_t(w.ld) * Wd * (nh - 1)));
     w.image = take(image_bytes(d));
     if (bwd_w0_streamed(int(K), int(Wd), int(nh))) w.bwd_image = reinterpret_cast<uint8_t*>(take(2 * Kp * Wd));
   }
@@ -1506,31 +1507,62 @@ cudaError_t launch_wg_any(const TZ* dZ, int ldz, int n_o, const TA* A, int lda, 
   return launch_wg_strided<TZ, TA>(dZ, ldz, 1, n_o, A, lda, 1, n_j, n, dW, db, s);
 }
 
-// Weight gradients of the tensor-core path from its 16-bit stored operands.
+// Output-layer weight gradients (weight_grad_out) over n items: blocks of
+// about n / (4 per SM) items each.
+template <typename TA>
+cudaError_t launch_wg_out(const float* G, int n_o, const TA* H, int W, int64_t n, float* dW, float* db,
+                          cudaStream_t s) {
+  if (n_o > 16 || W > 128 || W < 8 || W % 8 != 0 || (reinterpret_cast<uintptr_t>(H) & 15) != 0)
+    return launch_wg_any<float, TA>(G, n_o, n_o, H, W, W, n, dW, db, s);
+  const int64_t want = int64_t(sm_count()) * 4;
+  const int64_t chunk = std::max<int64_t>((n + want - 1) / want, 64);
+  const int64_t grid = (n + chunk - 1) / chunk;
+  if (grid < 1) return cudaSuccess;
+  if (n_o <= 4)
+    weight_grad_out<TA, 4><<<unsigned(grid), 256, 0, s>>>(G, n_o, H, W, n, chunk, dW, db);
+  else if (n_o <= 8)
+    weight_grad_out<TA, 8><<<unsigned(grid), 256, 0, s>>>(G, n_o, H, W, n, chunk, dW, db);
+  else
+    weight_grad_out<TA, 16><<<unsigned(grid), 256, 0, s>>>(G, n_o, H, W, n, chunk, dW, db);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// Weight gradients of the tensor-core path from its 16-bit stored operands:
+// the first and hidden layers on the tensor cores (features, activations and
+// pre-activation gradients stored neuron-major, the batch contiguous), the
+// output layer from the FP32 dL/d(raw) and the item-major last activations.
+// Shapes beyond the tensor-core kernel's TMEM/shared-memory budget use the
+// CUDA-core reduction on the same operands.
 template <typename T16>
 cudaError_t weight_grads_16(const nbvh_model_desc* d, const TrainWs& w, const float* G, int64_t n, float* grad_mlp,
                             cudaStream_t s) {
   const int K = d->n_samples * d->n_levels * d->n_features, Kp = (K + 15) & ~15;
   const int Wd = d->width, nh = d->n_hidden, no = d->n_out;
+  const bool bf16 = std::is_same<T16, __nv_bfloat16>::value;
   const T16* X = reinterpret_cast<const T16*>(w.X16);
   const T16* H = reinterpret_cast<const T16*>(w.H16);
-  const T16* Z = reinterpret_cast<const T16*>(w.dZ16);
+  const T16* HT = reinterpret_cast<const T16*>(w.HT16);
+  const T16* ZT = reinterpret_cast<const T16*>(w.dZT);
+  const size_t lz = size_t(Wd) * size_t(w.ld);  // one layer of dZT / HT16
   size_t off = 0;
-  // first layer: tensor cores (both operands stored with the batch contiguous);
-  // shapes beyond their TMEM/shared-memory budget use the CUDA-core reduction
-  WgTcArgs ta{w.X16, w.dZT0, n, w.ld, K, Kp, grad_mlp, grad_mlp + size_t(Wd) * K};
-  cudaError_t e = launch_wg_tc(std::is_same<T16, __nv_bfloat16>::value, Wd, ta, s);
+  WgTcArgs ta{w.X16, w.dZT, n, w.ld, K, Kp, grad_mlp, grad_mlp + size_t(Wd) * K};
+  cudaError_t e = launch_wg_tc(bf16, Wd, ta, s);
   if (e == cudaErrorInvalidConfiguration)
-    e = launch_wg_strided<T16, T16>(Z, Wd, 1, Wd, X, 1, w.ld, K, n, grad_mlp, grad_mlp + size_t(Wd) * K, s);
+    e = launch_wg_strided<T16, T16>(ZT, 1, w.ld, Wd, X, 1, w.ld, K, n, grad_mlp, grad_mlp + size_t(Wd) * K, s);
   off += size_t(Wd) * K + Wd;
   for (int h = 1; h < nh && e == cudaSuccess; ++h) {
-    e = launch_wg_any<T16, T16>(Z + size_t(h) * n * Wd, Wd, Wd, H + size_t(h - 1) * n * Wd, Wd, Wd, n,
-                                grad_mlp + off, grad_mlp + off + size_t(Wd) * Wd, s);
+    float* dW = grad_mlp + off;
+    float* db = dW + size_t(Wd) * Wd;
+    WgTcArgs th{w.HT16 + (h - 1) * lz, w.dZT + h * lz, n, w.ld, Wd, Wd, dW, db};
+    e = launch_wg_tc(bf16, Wd, th, s);
+    if (e == cudaErrorInvalidConfiguration)
+      e = launch_wg_strided<T16, T16>(ZT + h * lz, 1, w.ld, Wd, HT + (h - 1) * lz, 1, w.ld, Wd, n, dW, db, s);
     off += size_t(Wd) * Wd + Wd;
   }
   if (e == cudaSuccess)
-    e = launch_wg_any<float, T16>(G, no, no, H + size_t(nh - 1) * n * Wd, Wd, Wd, n, grad_mlp + off,
-                                  grad_mlp + off + size_t(no) * Wd, s);
+    e = launch_wg_out<T16>(G, no, H + size_t(nh - 1) * n * Wd, Wd, n, grad_mlp + off, grad_mlp + off + size_t(no) * Wd,
+                           s);
   return e;
 }
 
@@ -1620,6 +1652,7 @@ cudaError_t forward_chunk(const nbvh_model_desc* d, const GridParams& gp, const 
   a.tr.X16 = w.X16;
   a.tr.ld = w.ld;
   a.tr.H16 = w.H16;
+  a.tr.HT16 = w.HT16;
   a.tr.O = w.O + k.i0 * no;
   a.tr.G = w.G + k.i0 * no;
   a.tr.loss_seg = w.loss_seg + k.i0;
@@ -1652,8 +1685,7 @@ cudaError_t backward_chunk(const nbvh_model_desc* d, const GridParams& gp, const
     b.n = k.c;
     b.G = Gk;
     b.H16 = w.H16;
-    b.dZ16 = w.dZ16;
-    b.dZT0 = w.dZT0;
+    b.dZT = w.dZT;
     b.ld = w.ld;
     b.grad_table = grad_table;
     b.w0t_image = w.bwd_image;

@@ -21,8 +21,7 @@ struct TcBwdArgs {
   int64_t n;
   const float* G;         // [n][n_out] dL/d(raw), times the loss scale (by item)
   const uint16_t* H16;    // [n_hidden][n][W] hidden activations of the forward
-  uint16_t* dZ16;         // [n_hidden][n][W] pre-activation gradients (out)
-  uint16_t* dZT0;         // [W][ld] the first layer's dZ again, neuron-major (out)
+  uint16_t* dZT;          // [n_hidden][W][ld] pre-activation gradients, neuron-major (out)
   int64_t ld;
   float* grad_table;      // FP32 [entries][F]
   const uint8_t* w0t_image;  // W0^T in its shared-memory operand layout, copied
@@ -326,16 +325,12 @@ __global__ void __launch_bounds__(bwd_threads<W>(), 1024 / bwd_threads<W>()) tra
 #pragma unroll
         for (int i = 0; i < kCols / 2; ++i) pk[i] = pack2<BF16>(v[2 * i], v[2 * i + 1]);
         tmem_st_cols<kCols / 2>(t_row + lay.col_a + uint32_t(c0 / 2), pk);
-        if (grow < a.n) {
-          uint32_t* zdst = reinterpret_cast<uint32_t*>(a.dZ16 + (size_t(h) * size_t(a.n) + size_t(grow)) * W + c0);
+        if (grow < a.n) {  // neuron-major, as the weight gradients read it
+          uint16_t* zT = a.dZT + (int64_t(h) * W + c0) * a.ld + grow;
 #pragma unroll
-          for (int i = 0; i < kCols / 2; ++i) zdst[i] = pk[i];
-          if (h == 0) {
-#pragma unroll
-            for (int i = 0; i < kCols / 2; ++i) {
-              a.dZT0[int64_t(c0 + 2 * i) * a.ld + grow] = uint16_t(pk[i] & 0xffffu);
-              a.dZT0[int64_t(c0 + 2 * i + 1) * a.ld + grow] = uint16_t(pk[i] >> 16);
-            }
+          for (int i = 0; i < kCols / 2; ++i) {
+            zT[int64_t(2 * i) * a.ld] = uint16_t(pk[i] & 0xffffu);
+            zT[int64_t(2 * i + 1) * a.ld] = uint16_t(pk[i] >> 16);
           }
         }
         tmem_st_wait();
@@ -572,12 +567,80 @@ __global__ void __launch_bounds__(256) weight_grad_tiled(const TZ* __restrict__ 
   }
 }
 
+// Output-layer weight gradients (n_o <= NO outputs, NO = 4, 8 or 16, width
+// W <= 128 a multiple of 8, rows of H 16-byte aligned): dW[o][j] += sum_i G[i][o] H[i][j], db[o] += sum_i G[i][o], G
+// FP32 [n][n_o], H 16-bit [n][W]. A block takes a chunk of the items, 64 at a
+// time: the tile's G and H rows are contiguous, so all threads copy them into
+// shared memory with independent coalesced loads; then thread t takes column
+// j = t % W of rows t / W, t / W + 256 / W, ... for all outputs at once.
+constexpr int kWgOutItems = 64;
+template <typename TA, int NO>
+__global__ void __launch_bounds__(256) weight_grad_out(const float* __restrict__ G, int n_o,
+                                                       const TA* __restrict__ H, int W, int64_t n, int64_t chunk,
+                                                       float* __restrict__ dW, float* __restrict__ db) {
+  __shared__ __align__(16) float sg[kWgOutItems][NO];
+  __shared__ float sh[kWgOutItems][128];
+  const int64_t i0 = int64_t(blockIdx.x) * chunk;
+  const int64_t i1 = min(n, i0 + chunk);
+  const int groups = 256 / W;
+  const int j = threadIdx.x % W, g = threadIdx.x / W;
+  const int pieces = W / 8;  // 16-byte pieces per row (W a multiple of 8)
+  const int c8 = threadIdx.x % pieces, r8 = threadIdx.x / pieces, rstep = 256 / pieces;
+  const bool active = g < groups;
+  float acc[NO];
+#pragma unroll
+  for (int o = 0; o < NO; ++o) acc[o] = 0.0f;
+  float bacc = 0.0f;
+  for (int64_t ib = i0; ib < i1; ib += kWgOutItems) {
+    const int cnt = int(min(int64_t(kWgOutItems), i1 - ib));
+    for (int e = threadIdx.x; e < kWgOutItems * NO; e += 256) {
+      const int r = e / NO, o = e - (e / NO) * NO;
+      sg[r][o] = (r < cnt && o < n_o) ? __ldg(G + (ib + r) * n_o + o) : 0.0f;
+    }
+    // 16-byte pieces (8 entries) of the tile's rows
+    for (int r = r8; r < kWgOutItems; r += rstep) {
+      float v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      if (r < cnt) {
+        const uint4 q = __ldg(reinterpret_cast<const uint4*>(H + (ib + r) * W + 8 * c8));
+        const TA* e = reinterpret_cast<const TA*>(&q);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = to_f(e[k]);
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) sh[r][8 * c8 + k] = v[k];
+    }
+    __syncthreads();
+    if (active) {
+      for (int r = g; r < cnt; r += groups) {
+        const float h = sh[r][j];
+#pragma unroll
+        for (int o = 0; o < NO; o += 4) {
+          const float4 gv = *reinterpret_cast<const float4*>(&sg[r][o]);
+          acc[o] = fmaf(gv.x, h, acc[o]);
+          acc[o + 1] = fmaf(gv.y, h, acc[o + 1]);
+          acc[o + 2] = fmaf(gv.z, h, acc[o + 2]);
+          acc[o + 3] = fmaf(gv.w, h, acc[o + 3]);
+        }
+      }
+    }
+    if (threadIdx.x < n_o)
+      for (int r = 0; r < cnt; ++r) bacc += sg[r][threadIdx.x];
+    __syncthreads();
+  }
+  if (active) {
+#pragma unroll
+    for (int o = 0; o < NO; ++o)
+      if (o < n_o) atomicAdd(dW + o * W + j, acc[o]);
+  }
+  if (threadIdx.x < n_o) atomicAdd(db + threadIdx.x, bacc);
+}
+
 // ---------------------------------------------------------------------------
 // First-layer weight gradient on the tensor cores: dW0^T [Kp x W] =
 // X^T [Kp x n] * dZ0 [n x W], K = the batch, split over CTAs. Both operands are
 // stored with the batch contiguous (feature-major features, neuron-major dZ0),
 // so both tiles are K-major. Each CTA accumulates its 128-feature tiles in TMEM
-// over its chunks of 64 items, then adds them into the FP32 gradient.
+// over its chunks of items, then adds them into the FP32 gradient.
 // ---------------------------------------------------------------------------
 struct WgTcArgs {
   const uint16_t* XT;  // [Kp][ld]
@@ -588,21 +651,27 @@ struct WgTcArgs {
   float* db;           // [W]
 };
 
-constexpr int kWgTcItems = 64;
 constexpr int kWgTcThreads = 256;
 
 __host__ __device__ inline int wg_tc_tiles(int Kp) { return (Kp + 127) / 128; }
-// One stage: the features of 64 items ([Kp][64]) and their dZ0 ([W][64]).
-__host__ __device__ inline uint32_t wg_tc_stage_bytes(int Kp, int W) {
-  return uint32_t(wg_tc_tiles(Kp)) * 128 * kWgTcItems * 2 + uint32_t(W) * kWgTcItems * 2;
+// One stage: the features of `it` items ([Kp][it]) and their dZ ([W][it]).
+__host__ __device__ inline uint32_t wg_tc_stage_bytes(int Kp, int W, int it) {
+  return uint32_t(wg_tc_tiles(Kp)) * 128 * uint32_t(it) * 2 + uint32_t(W) * uint32_t(it) * 2;
 }
-// Two stages (the next chunk copied in while the tensor cores take this one)
-// where they fit shared memory, else one.
+// Items per stage: the most of 256, 128 and 64 whose two stages (the next
+// chunk copied in while the tensor cores take this one) fit shared memory;
+// few features (a hidden layer's 64) take long chunks, so that each copy and
+// MMA round carries enough work.
+__host__ __device__ inline int wg_tc_items(int Kp, int W) {
+  for (int it = 256; it > 64; it /= 2)
+    if (2 * wg_tc_stage_bytes(Kp, W, it) + 256 <= 227u * 1024u) return it;
+  return 64;
+}
 __host__ __device__ inline int wg_tc_stages(int Kp, int W) {
-  return 2 * wg_tc_stage_bytes(Kp, W) + 256 <= 227u * 1024u ? 2 : 1;
+  return 2 * wg_tc_stage_bytes(Kp, W, wg_tc_items(Kp, W)) + 256 <= 227u * 1024u ? 2 : 1;
 }
 __host__ __device__ inline uint32_t wg_tc_smem(int Kp, int W) {
-  return uint32_t(wg_tc_stages(Kp, W)) * wg_tc_stage_bytes(Kp, W) + 128 + 128;
+  return uint32_t(wg_tc_stages(Kp, W)) * wg_tc_stage_bytes(Kp, W, wg_tc_items(Kp, W)) + 128 + 128;
 }
 
 // 16 bytes global -> shared, asynchronous; bytes beyond src_bytes (0..16) are zero.
@@ -619,11 +688,12 @@ __global__ void __launch_bounds__(kWgTcThreads, 1) weight_grad_tc(WgTcArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   const int tiles = wg_tc_tiles(a.Kp);
+  const int it = wg_tc_items(a.Kp, W);  // items per chunk
   const int stages = wg_tc_stages(a.Kp, W);
-  const uint32_t stage_bytes = wg_tc_stage_bytes(a.Kp, W);
+  const uint32_t stage_bytes = wg_tc_stage_bytes(a.Kp, W, it);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + size_t(stages) * stage_bytes);
   uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bar + 1);
-  const int64_t n_chunks = (a.n + kWgTcItems - 1) / kWgTcItems;
+  const int64_t n_chunks = (a.n + it - 1) / it;
   if (int64_t(blockIdx.x) >= n_chunks) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint32_t ncols = 32;
@@ -644,24 +714,25 @@ __global__ void __launch_bounds__(kWgTcThreads, 1) weight_grad_tc(WgTcArgs a) {
   float bsum = 0.0f;  // thread t < W: sum of dZ0 over its neuron
   uint32_t phase = 0;
   bool failed = false, first = true;
-  // 16-byte pieces of a [rows][64 items] tile into the K-major core-matrix
+  // 16-byte pieces of a [rows][it items] tile into the K-major core-matrix
   // layout, copied asynchronously (zeros past the batch and past valid_rows)
+  const int ppr = it / 8;  // pieces per row
   auto stage = [&](uint8_t* dst, const uint16_t* src, int rows, int valid_rows, int64_t c0) {
-    for (int p = threadIdx.x; p < rows * 8; p += blockDim.x) {
-      const int r = p >> 3, q = p & 7;
+    for (int p = threadIdx.x; p < rows * ppr; p += blockDim.x) {
+      const int r = p / ppr, q = p - r * ppr;
       const int64_t col = c0 + 8 * q;
       const int64_t left = r < valid_rows ? a.n - col : 0;
       const uint32_t bytes = left >= 8 ? 16u : (left > 0 ? uint32_t(left) * 2u : 0u);
       const uint16_t* g = bytes ? src + int64_t(r) * a.ld + col : src;
-      cp_async16(dst + op_offset(r, 8 * q, kWgTcItems), g, bytes);
+      cp_async16(dst + op_offset(r, 8 * q, it), g, bytes);
     }
   };
   auto issue = [&](int buf, int64_t c) {
     uint8_t* sA = smem + size_t(buf) * stage_bytes;
-    uint8_t* sB = sA + size_t(tiles) * 128 * kWgTcItems * 2;
-    const int64_t c0 = c * kWgTcItems;
+    uint8_t* sB = sA + size_t(tiles) * 128 * it * 2;
+    const int64_t c0 = c * it;
     for (int t = 0; t < tiles; ++t)
-      stage(sA + size_t(t) * 128 * kWgTcItems * 2, a.XT + int64_t(t) * 128 * a.ld, 128, min(128, a.K - 128 * t), c0);
+      stage(sA + size_t(t) * 128 * it * 2, a.XT + int64_t(t) * 128 * a.ld, 128, min(128, a.K - 128 * t), c0);
     stage(sB, a.ZT, W, W, c0);
     cp_async_commit();
   };
@@ -679,19 +750,19 @@ __global__ void __launch_bounds__(kWgTcThreads, 1) weight_grad_tc(WgTcArgs a) {
     fence_proxy_async_smem();
     __syncthreads();
     uint8_t* sA = smem + size_t(b) * stage_bytes;
-    uint8_t* sB = sA + size_t(tiles) * 128 * kWgTcItems * 2;
+    uint8_t* sB = sA + size_t(tiles) * 128 * it * 2;
     if (threadIdx.x < W) {
-      for (int q = 0; q < kWgTcItems; ++q) {
-        const uint16_t e = *reinterpret_cast<const uint16_t*>(sB + op_offset(threadIdx.x, q, kWgTcItems));
+      for (int q = 0; q < it; ++q) {
+        const uint16_t e = *reinterpret_cast<const uint16_t*>(sB + op_offset(threadIdx.x, q, it));
         bsum += from16<BF16>(e);
       }
     }
     if (threadIdx.x == 0) {
       tc_fence_after();
-      const uint32_t sbo = uint32_t(kWgTcItems) * 16;
+      const uint32_t sbo = uint32_t(it) * 16;
       for (int t = 0; t < tiles; ++t) {
-        const uint32_t aa = smem_u32(sA + size_t(t) * 128 * kWgTcItems * 2);
-        for (int kk = 0; kk < kWgTcItems / 16; ++kk)
+        const uint32_t aa = smem_u32(sA + size_t(t) * 128 * it * 2);
+        for (int kk = 0; kk < it / 16; ++kk)
           mma_f16(tmem + uint32_t(t * W), smem_desc(aa + kk * 256, 128, sbo), smem_desc(smem_u32(sB) + kk * 256, 128, sbo),
                   idesc, (first && kk == 0) ? 0u : 1u);
       }

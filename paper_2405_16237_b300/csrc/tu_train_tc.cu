@@ -73,7 +73,8 @@ cudaError_t launch_wg_tc_w(bool bf16, const WgTcArgs& a, cudaStream_t s) {
   auto kern = bf16 ? weight_grad_tc<W, true> : weight_grad_tc<W, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
-  const int64_t chunks = (a.n + kWgTcItems - 1) / kWgTcItems;
+  const int it = wg_tc_items(a.Kp, W);
+  const int64_t chunks = (a.n + it - 1) / it;
   int64_t grid = sm_count();
   if (chunks < grid) grid = chunks;
   if (grid < 1) return cudaSuccess;
