@@ -79,13 +79,17 @@ struct TcTrain {
 
 // Persistent query queue (tensor-core query kernel, one launch for all
 // segments of all rays). An item is (segment slot << 32 | ray) in a ring of
-// n_rays 64-bit entries (position p at p % n_rays; an empty entry holds all
-// ones). A ray has at most one item queued or in evaluation, so at most
-// n_rays items are ever alive and position p has been taken before p + n_rays
-// is reserved. Producers reserve positions and write each item into its
-// entry; consumers claim positions [head, reserved) and take each item as soon
-// as it is there; a tile retires its items after queueing their successors,
-// so head - retired counts the items in evaluation.
+// R 64-bit entries (position p at p % R; an empty entry holds all ones), R =
+// the items the traversal queued (*qlen0, at least 1). Only those rays ever
+// get items and a ray has at most one item queued or in evaluation, so at most
+// R items are ever alive and position p has been taken before p + R is
+// reserved. The traversal's first items fill entries [0, R), so the ring
+// needs no clearing: every later position finds its entry emptied by the
+// consumer of the position R before it. Producers reserve positions and write
+// each item into its entry; consumers claim positions [head, reserved) and
+// take each item as soon as it is there; a tile retires its items after
+// queueing their successors, so head - retired counts the items in
+// evaluation.
 struct PQueue {
   unsigned long long* head;      // items claimed
   unsigned long long* reserved;  // items ever queued
@@ -99,7 +103,14 @@ struct PQueue {
   int32_t partial_items;         // the most items a partial tile claims (the rest of it: lookahead rows)
   long long spin_limit;          // polling rounds before a queue wait gives up (NBVH_ERR_TIMEOUT)
   unsigned long long* ring;      // [n_rays] items; nullptr: one launch per segment slot instead
+  const int32_t* qlen0;          // the traversal's queued items: the ring's size R
 };
+
+// The ring's size R (read by any thread; the traversal wrote it before the launch).
+__device__ __forceinline__ unsigned long long pq_ring_n(const PQueue& q) {
+  const int32_t n0 = __ldg(q.qlen0);
+  return n0 > 0 ? (unsigned long long)n0 : 1ull;
+}
 
 // Everything a segment-evaluation kernel needs. Two modes:
 //  - list mode  (queue == nullptr): item i is segment (seg_ray[i], t0[i], t1[i]),

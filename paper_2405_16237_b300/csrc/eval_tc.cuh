@@ -519,17 +519,19 @@ __device__ __forceinline__ void row_point(const GridParams& gp, const RowBuf& b,
 
 // Stage row r of a claimed tile (item at ring position p): the ray, its
 // segment's interval, its best t and its next segment's t0. Returns the ray
-// (-1 if the wait gave up).
+// (-1 if the wait gave up, or the entry holds no item of this query: only
+// announced items that nothing writes, the test hook, can find one).
 __device__ __forceinline__ int pq_stage(const EvalArgs& a, unsigned long long p, int r, const RowBuf& b) {
   const size_t nr = size_t(a.n_rays);
-  const unsigned long long it = pq_take(a.pq, p, nr);
+  const unsigned long long it = pq_take(a.pq, p, pq_ring_n(a.pq));
   int ray = -1;
   float t0 = 0.0f, t1 = 0.0f;
-  if (it == kPqEmpty) {
+  const uint32_t iray = uint32_t(it), isl = uint32_t(it >> 32);
+  if (it == kPqEmpty || iray >= uint32_t(a.n_rays) || isl >= uint32_t(a.max_segs)) {
     set_status(NBVH_ERR_TIMEOUT);
   } else {
-    ray = int(uint32_t(it));
-    const int sl = int(it >> 32);
+    ray = int(iray);
+    const int sl = int(isl);
     b.slot[r] = sl;
     const size_t q = size_t(sl) * nr + size_t(ray);
     t0 = a.seg_t0[q];
@@ -1284,7 +1286,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) eval_tc_kernel(EvalArgs
         base = __shfl_sync(0xffffffffu, base, 0);
         if (pray >= 0) {
           const unsigned long long item = (unsigned long long)(rb.slot[threadIdx.x] + 1) << 32 | uint32_t(pray);
-          if (!pq_put(a.pq, base + __popc(m & ((1u << lane) - 1u)), (unsigned long long)a.n_rays, item))
+          if (!pq_put(a.pq, base + __popc(m & ((1u << lane) - 1u)), pq_ring_n(a.pq), item))
             set_status(NBVH_ERR_TIMEOUT);
         }
         asm volatile("bar.sync 2, 128;" ::: "memory");

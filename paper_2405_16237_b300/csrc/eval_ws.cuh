@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) eval_ws_kernel(EvalArgs a) {
       base = __shfl_sync(0xffffffffu, base, 0);
       if (push) {
         const unsigned long long item = (unsigned long long)(rb.slot[row] + 1) << 32 | uint32_t(ray);
-        if (!pq_put(a.pq, base + __popc(msk & ((1u << lane) - 1u)), (unsigned long long)a.n_rays, item))
+        if (!pq_put(a.pq, base + __popc(msk & ((1u << lane) - 1u)), pq_ring_n(a.pq), item))
           set_status(NBVH_ERR_TIMEOUT);
       }
       tc_fence_before();

@@ -360,6 +360,7 @@ PQueue pq_of(const QueryWs& w, int32_t max_segs, int64_t patience, int32_t parti
   q.partial_items = partial_items;
   q.spin_limit = spin_limit > 0 ? spin_limit : kPqSpinLimit;
   q.ring = reinterpret_cast<unsigned long long*>(w.queue[0]);
+  q.qlen0 = w.counters;  // the traversal's queue length
   return q;
 }
 
@@ -404,9 +405,7 @@ cudaError_t launch_query_stages(const nbvh_model_desc* desc, const GridParams& g
   const bool persistent = desc->mlp_prec != NBVH_FP32 && o.schedule == NBVH_SCHEDULE_PERSISTENT;
   if (persistent) {
     to.queue0 = nullptr;
-    to.ring0 = reinterpret_cast<unsigned long long*>(w.queue[0]);
-    cudaError_t me = cudaMemsetAsync(w.queue[0], 0xff, 8 * size_t(rays.n), s);  // empty ring
-    if (me != cudaSuccess) return me;
+    to.ring0 = reinterpret_cast<unsigned long long*>(w.queue[0]);  // fills entries [0, qlen0): see PQueue
   }
   const int tb = o.traverse_block;
   cudaError_t e;
