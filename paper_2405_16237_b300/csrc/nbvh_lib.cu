@@ -1949,24 +1949,31 @@ extern "C" nbvh_status nbvh_adam(const nbvh_model_desc* desc, const nbvh_optim* 
   grad_check_kernel<<<g, 256, 0, s>>>(opt->grad_mlp, nm, st.bad);
   const double c1 = 1.0 - std::pow(double(beta1), double(step));
   const double c2 = 1.0 - std::pow(double(beta2), double(step));
+  auto a16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+  const bool vt = a16(opt->table_master) && a16(opt->grad_table) && a16(opt->table_m) && a16(opt->table_v) &&
+                  (reinterpret_cast<uintptr_t>(opt->table_work) & 15) == 0;
+  const bool vm = a16(opt->mlp) && a16(opt->grad_mlp) && a16(opt->mlp_m) && a16(opt->mlp_v);
+  auto table_adam = [&](auto tag) {
+    using T = decltype(tag);
+    T* work = static_cast<T*>(opt->table_work);
+    if (vt)
+      adam_kernel<T, true><<<g, 256, 0, s>>>(opt->table_master, work, opt->grad_table, opt->table_m, opt->table_v, nt,
+                                             lr, beta1, beta2, eps, float(c1), float(c2), st);
+    else
+      adam_kernel<T, false><<<g, 256, 0, s>>>(opt->table_master, work, opt->grad_table, opt->table_m, opt->table_v,
+                                              nt, lr, beta1, beta2, eps, float(c1), float(c2), st);
+  };
   switch (desc->table_prec) {
-    case NBVH_FP16:
-      adam_kernel<__half><<<g, 256, 0, s>>>(opt->table_master, static_cast<__half*>(opt->table_work),
-                                           opt->grad_table, opt->table_m, opt->table_v, nt, lr, beta1, beta2, eps,
-                                           float(c1), float(c2), st);
-      break;
-    case NBVH_BF16:
-      adam_kernel<__nv_bfloat16><<<g, 256, 0, s>>>(opt->table_master, static_cast<__nv_bfloat16*>(opt->table_work),
-                                                   opt->grad_table, opt->table_m, opt->table_v, nt, lr, beta1, beta2,
-                                                   eps, float(c1), float(c2), st);
-      break;
-    default:
-      adam_kernel<float><<<g, 256, 0, s>>>(opt->table_master, static_cast<float*>(opt->table_work), opt->grad_table,
-                                          opt->table_m, opt->table_v, nt, lr, beta1, beta2, eps, float(c1), float(c2),
-                                          st);
+    case NBVH_FP16: table_adam(__half()); break;
+    case NBVH_BF16: table_adam(__nv_bfloat16()); break;
+    default: table_adam(float()); break;
   }
-  adam_kernel<float><<<g, 256, 0, s>>>(opt->mlp, nullptr, opt->grad_mlp, opt->mlp_m, opt->mlp_v, nm, lr, beta1,
-                                      beta2, eps, float(c1), float(c2), st);
+  if (vm)
+    adam_kernel<float, true><<<g, 256, 0, s>>>(opt->mlp, nullptr, opt->grad_mlp, opt->mlp_m, opt->mlp_v, nm, lr, beta1,
+                                               beta2, eps, float(c1), float(c2), st);
+  else
+    adam_kernel<float, false><<<g, 256, 0, s>>>(opt->mlp, nullptr, opt->grad_mlp, opt->mlp_m, opt->mlp_v, nm, lr,
+                                                beta1, beta2, eps, float(c1), float(c2), st);
   loss_scale_update_kernel<<<1, 1, 0, s>>>(st, dynamic_scale);
   count_launches(5);
   return status_of(cudaGetLastError());

@@ -623,36 +623,87 @@ struct AdamState {
   int32_t* applied;    // device scalar: 1 when the last step was applied
 };
 
+// Sets *bad when a gradient is not finite (g 16-byte aligned: four at a time).
 static __global__ void grad_check_kernel(const float* __restrict__ g, int64_t n, int32_t* bad) {
-  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   bool ok = true;
-  for (; i < n; i += stride) ok &= isfinite(g[i]);
+  const bool vec = (reinterpret_cast<uintptr_t>(g) & 15) == 0;
+  const int64_t head = vec ? (n & ~int64_t(3)) : 0;
+  for (int64_t q = tid; q < head / 4; q += stride) {
+    const float4 x = reinterpret_cast<const float4*>(g)[q];
+    ok &= isfinite(x.x) && isfinite(x.y) && isfinite(x.z) && isfinite(x.w);
+  }
+  for (int64_t i = head + tid; i < n; i += stride) ok &= isfinite(g[i]);
   if (!__all_sync(0xffffffffu, ok) && (threadIdx.x & 31) == 0) atomicExch(bad, 1);
 }
 
+// One Adam update of one parameter (the gradient unscaled by the loss scale).
+__device__ __forceinline__ float adam_update(float g, float& m, float& v, float p, float lr, float b1, float b2,
+                                             float eps, float c1, float c2) {
+  const float mi = b1 * m + (1.0f - b1) * g;
+  const float vi = b2 * v + (1.0f - b2) * g * g;
+  m = mi;
+  v = vi;
+  return p - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
 template <typename T>
+__device__ __forceinline__ T adam_work(float p) {
+  if constexpr (std::is_same<T, __half>::value) return __float2half_rn(p);
+  else if constexpr (std::is_same<T, __nv_bfloat16>::value) return __float2bfloat16_rn(p);
+  else return p;
+}
+
+// Adam over n parameters, four at a time (VEC: every pointer 16-byte aligned,
+// the 16-bit working copy 8-byte aligned; the last n % 4 one at a time), the
+// working copy refreshed and the gradient cleared. A step whose gradient was
+// not finite only clears it.
+template <typename T, bool VEC>
 __global__ void adam_kernel(float* __restrict__ master, T* __restrict__ work, float* __restrict__ grad,
                             float* __restrict__ m, float* __restrict__ v, int64_t n, float lr, float b1, float b2,
                             float eps, float c1, float c2, AdamState st) {
   const bool skip = *st.bad != 0;
   const float inv_scale = 1.0f / *st.loss_scale;
-  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-  for (; i < n; i += stride) {
+  int64_t head = 0;  // parameters [0, head) go four at a time
+  if constexpr (VEC) {
+    head = n & ~int64_t(3);
+    for (int64_t q = tid; q < head / 4; q += stride) {
+      float4* g4 = reinterpret_cast<float4*>(grad) + q;
+      if (!skip) {
+        const float4 g = *g4;
+        float4 mm = reinterpret_cast<const float4*>(m)[q];
+        float4 vv = reinterpret_cast<const float4*>(v)[q];
+        float4 p = reinterpret_cast<const float4*>(master)[q];
+        p.x = adam_update(g.x * inv_scale, mm.x, vv.x, p.x, lr, b1, b2, eps, c1, c2);
+        p.y = adam_update(g.y * inv_scale, mm.y, vv.y, p.y, lr, b1, b2, eps, c1, c2);
+        p.z = adam_update(g.z * inv_scale, mm.z, vv.z, p.z, lr, b1, b2, eps, c1, c2);
+        p.w = adam_update(g.w * inv_scale, mm.w, vv.w, p.w, lr, b1, b2, eps, c1, c2);
+        reinterpret_cast<float4*>(m)[q] = mm;
+        reinterpret_cast<float4*>(v)[q] = vv;
+        reinterpret_cast<float4*>(master)[q] = p;
+        if (work) {
+          if constexpr (std::is_same<T, float>::value) {
+            reinterpret_cast<float4*>(work)[q] = p;
+          } else {
+            T w4[4] = {adam_work<T>(p.x), adam_work<T>(p.y), adam_work<T>(p.z), adam_work<T>(p.w)};
+            reinterpret_cast<uint2*>(work)[q] = *reinterpret_cast<const uint2*>(w4);
+          }
+        }
+      }
+      *g4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+  }
+  for (int64_t i = head + tid; i < n; i += stride) {
     if (!skip) {
-      const float g = grad[i] * inv_scale;
-      const float mi = b1 * m[i] + (1.0f - b1) * g;
-      const float vi = b2 * v[i] + (1.0f - b2) * g * g;
+      float mi = m[i], vi = v[i];
+      const float p = adam_update(grad[i] * inv_scale, mi, vi, master[i], lr, b1, b2, eps, c1, c2);
       m[i] = mi;
       v[i] = vi;
-      const float p = master[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
       master[i] = p;
-      if (work) {
-        if constexpr (std::is_same<T, __half>::value) work[i] = __float2half_rn(p);
-        else if constexpr (std::is_same<T, __nv_bfloat16>::value) work[i] = __float2bfloat16_rn(p);
-        else work[i] = p;
-      }
+      if (work) work[i] = adam_work<T>(p);
     }
     grad[i] = 0.0f;
   }
