@@ -260,7 +260,11 @@ nbvh_status nbvh_encode(const nbvh_model_desc* desc, const void* table, nbvh_ray
  *                   it and each ray advances up to 128 / items segments per
  *                   tile. Results do not depend on it. The concurrent hybrid
  *                   form defaults to 128 (beside the other stream's kernels,
- *                   smaller partial tiles measured slower). */
+ *                   smaller partial tiles measured slower). A query whose
+ *                   traversal queues fewer than 128 items per evaluation CTA
+ *                   spreads them over all CTAs at once: each claim takes at
+ *                   most max(32, queued / CTAs) items, the tile's other rows
+ *                   holding lookahead segments. */
 #define NBVH_SCHEDULE_WAVES 0
 #define NBVH_SCHEDULE_PERSISTENT 1
 #define NBVH_W1_AUTO 0

@@ -104,6 +104,7 @@ struct PQueue {
   long long spin_limit;          // polling rounds before a queue wait gives up (NBVH_ERR_TIMEOUT)
   unsigned long long* ring;      // [n_rays] items; nullptr: one launch per segment slot instead
   const int32_t* qlen0;          // the traversal's queued items: the ring's size R
+  int32_t split;                 // > 0: a claim takes at most max(split, ceil(R / CTAs)) items (see pq_full)
 };
 
 // The ring's size R (read by any thread; the traversal wrote it before the launch).

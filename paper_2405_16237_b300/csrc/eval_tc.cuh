@@ -383,18 +383,32 @@ __device__ __forceinline__ void red_release_add_u64(unsigned long long* p, unsig
 // and the CTAs evaluating them stay. Its SM then serves the other
 // kernels. A stale count only makes the CTA stay. (Alone, a draining queue
 // is better served by many CTAs taking partial tiles with lookahead rows.)
+// Items a claim takes at once: a full tile, or with q.split > 0 at most
+// max(q.split, ceil(R / CTAs)) (R: the traversal's queue length). A short
+// queue then spreads over all the CTAs at once, each tile's other rows
+// holding the same rays' next segments (lookahead), instead of a few CTAs
+// taking full tiles one segment per ray.
+__device__ __forceinline__ unsigned long long pq_full(const PQueue& q) {
+  if (q.split <= 0) return kTcM;
+  const int32_t n0 = __ldg(q.qlen0);
+  const unsigned long long per = (unsigned long long)(n0 > 0 ? n0 : 0) / gridDim.x + 1ull;
+  const unsigned long long f = per > (unsigned long long)q.split ? per : (unsigned long long)q.split;
+  return f < kTcM ? f : kTcM;
+}
+
 __device__ __forceinline__ int pq_claim(const PQueue& q, unsigned long long* start) {
   const long long t0 = clock64();
+  const unsigned long long full = pq_full(q);
   for (long long spin = 0; spin < q.spin_limit; ++spin) {
     const unsigned long long retired = ld_relaxed_u64(q.retired);
     const unsigned long long head = ld_relaxed_u64(q.head);
     const unsigned long long res = ld_relaxed_u64(q.reserved);
     if (res > head) {
       const unsigned long long avail = res - head;
-      if (avail >= kTcM || retired == head || clock64() - t0 > q.patience) {
+      if (avail >= full || retired == head || clock64() - t0 > q.patience) {
         // a partial tile takes at most q.partial_items items, so that other
         // CTAs share a shallow queue and each item gets more lookahead rows
-        const unsigned long long cap = avail >= kTcM ? kTcM : (unsigned long long)q.partial_items;
+        const unsigned long long cap = avail >= full ? full : (unsigned long long)q.partial_items;
         const unsigned want = unsigned(avail < cap ? avail : cap);
         if (atomicCAS(q.head, head, head + want) == head) {
           atomicAdd(q.tiles, 1u);
