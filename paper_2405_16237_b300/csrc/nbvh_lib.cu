@@ -1522,18 +1522,13 @@ cudaError_t launch_wg_any(const TZ* dZ, int ldz, int n_o, const TA* A, int lda, 
 template <typename TA>
 cudaError_t launch_wg_out(const float* G, int n_o, const TA* H, int W, int64_t n, float* dW, float* db,
                           cudaStream_t s) {
-  if (n_o > 16 || W > 128 || W < 8 || W % 8 != 0 || (reinterpret_cast<uintptr_t>(H) & 15) != 0)
+  if (n_o > 8 || W > 128 || W < 8 || W % 8 != 0 || (reinterpret_cast<uintptr_t>(H) & 15) != 0)
     return launch_wg_any<float, TA>(G, n_o, n_o, H, W, W, n, dW, db, s);
   const int64_t want = int64_t(sm_count()) * 4;
   const int64_t chunk = std::max<int64_t>((n + want - 1) / want, 64);
   const int64_t grid = (n + chunk - 1) / chunk;
   if (grid < 1) return cudaSuccess;
-  if (n_o <= 4)
-    weight_grad_out<TA, 4><<<unsigned(grid), 256, 0, s>>>(G, n_o, H, W, n, chunk, dW, db);
-  else if (n_o <= 8)
-    weight_grad_out<TA, 8><<<unsigned(grid), 256, 0, s>>>(G, n_o, H, W, n, chunk, dW, db);
-  else
-    weight_grad_out<TA, 16><<<unsigned(grid), 256, 0, s>>>(G, n_o, H, W, n, chunk, dW, db);
+  weight_grad_out<TA, 8><<<unsigned(grid), 256, 0, s>>>(G, n_o, H, W, n, chunk, dW, db);  // n_out is 5..8
   count_launches(1);
   return cudaGetLastError();
 }

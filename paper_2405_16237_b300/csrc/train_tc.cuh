@@ -567,7 +567,7 @@ __global__ void __launch_bounds__(256) weight_grad_tiled(const TZ* __restrict__ 
   }
 }
 
-// Output-layer weight gradients (n_o <= NO outputs, NO = 4, 8 or 16, width
+// Output-layer weight gradients (n_o <= NO outputs, NO a multiple of 4, width
 // W <= 128 a multiple of 8, rows of H 16-byte aligned): dW[o][j] += sum_i G[i][o] H[i][j], db[o] += sum_i G[i][o], G
 // FP32 [n][n_o], H 16-bit [n][W]. A block takes a chunk of the items, 64 at a
 // time: the tile's G and H rows are contiguous, so all threads copy them into
