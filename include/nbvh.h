@@ -209,15 +209,16 @@ nbvh_status nbvh_encode(const nbvh_model_desc* desc, const void* table, nbvh_ray
  *  eval_threads     FP16/BF16 evaluation CTA: 256 (two CTAs per SM, hidden
  *                   width <= 64), 512 (one CTA per SM), 0 = automatic (512).
  *  w1_mode          FP16/BF16 evaluation: where the first layer's weights
- *                   live. NBVH_W1_RESIDENT: converted into shared memory once
- *                   per CTA; NBVH_W1_STREAMED: converted once per call into a
- *                   16-bit image in the workspace and streamed through two
- *                   shared-memory buffers, 128 inputs at a time, by bulk
- *                   copies; NBVH_W1_AUTO: streamed (on the mixed scene's
- *                   per-instance launches the per-CTA conversion of resident
- *                   weights cost 11 % of the frame; on one large launch the
- *                   two placements tie). The training forward places its
- *                   weights itself: resident when they fit.
+ *                   live. Both forms convert them once per call into a 16-bit
+ *                   image in the workspace. NBVH_W1_RESIDENT: each CTA copies
+ *                   the whole image into shared memory at its start;
+ *                   NBVH_W1_STREAMED: streamed through two shared-memory
+ *                   buffers, 128 inputs at a time, by bulk copies;
+ *                   NBVH_W1_AUTO: streamed (resident weights take up to
+ *                   128 KB of the SM's shared L1, which the mixed scene's
+ *                   gather needed: 11 % slower there; 1.7 % faster on the
+ *                   icosphere query). The training forward places its weights
+ *                   itself: resident when they fit.
  *  eval_pipeline    persistent FP16/BF16 schedule: NBVH_PIPELINE_PHASES runs
  *                   each tile in CTA-wide phases (all warps gather, then the
  *                   MLP, resolve and claim); NBVH_PIPELINE_WARP_SPECIALISED

@@ -148,6 +148,8 @@ struct EvalArgs {
   int32_t inst_id;
   PQueue pq;          // tensor-core query: persistent queue (when pq.ring is set)
   const void* w1_image;  // tensor-core kernel: streamed first-layer weights (nullptr: resident)
+  const void* w1_copy;   // resident plan: the same 16-bit image, bulk-copied whole by each CTA
+                         // (nullptr: each CTA converts the FP32 weights)
   int32_t chunk_samples; // FP32 kernel: samples per first-layer chunk (0: all, weights resident)
   // training forward (tensor-core kernel, list of one segment per ray)
   TcTrain tr;

@@ -875,8 +875,16 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) eval_tc_kernel(EvalArgs
   // when they stay resident).
   const float* W1 = a.mlp;
   const float* b1 = W1 + size_t(W) * K;
-  if (!stream)
+  if (!stream && a.w1_copy) {  // resident from the prepared image: bulk copies, waited for below
+    if (threadIdx.x == 0) {
+      const uint32_t bytes = uint32_t(lay.R) * lay.chunk_bytes;
+      mbar_expect_tx(w_full, bytes);
+      for (uint32_t o = 0; o < bytes; o += 32768u)
+        bulk_g2s(sW1 + o, static_cast<const uint8_t*>(a.w1_copy) + o, min(32768u, bytes - o), w_full);
+    }
+  } else if (!stream) {
     for (int i = threadIdx.x; i < W * lay.R * lay.KC; i += NT) put_w1<BF16>(sW1, W1, i, W, K, L, F, N, lay);
+  }
   const float* p = b1 + W;
   for (int h = 1; h < a.n_hidden; ++h) {
     stage_weights<BF16>(sWh + size_t(h - 1) * W * W * 2, p, W, W, W, W);
@@ -903,6 +911,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) eval_tc_kernel(EvalArgs
   uint32_t g = 0;             // first-layer chunk rounds so far (buffer g & 1)
   uint32_t tma_pending[2] = {~0u, ~0u};  // thread 0: round of a streamed copy not yet seen complete
   bool failed = false;
+  if (!stream && a.w1_copy && !mbar_wait(w_full, 0)) failed = true;  // the resident image copy
   constexpr bool kSplitX = F == 2 && sizeof(T) == 2;  // 4-byte entries: x-corner lane split
 
   int cur = 0;  // persistent query: the row buffer of the tile being evaluated
@@ -1344,10 +1353,11 @@ struct TcPlan {
 constexpr uint32_t kSmemMax = 227 * 1024;       // per CTA
 constexpr uint32_t kSmemHalf = 113 * 1024;      // per CTA with two CTAs on an SM
 
-// w1_mode NBVH_W1_AUTO: streamed for a query (query = true: on the mixed
-// scene's many per-instance launches the per-CTA conversion of resident
-// weights cost 11 % of the frame; on one large launch the two tie), else
-// resident when it fits the CTA's budget.
+// w1_mode NBVH_W1_AUTO: streamed for a query (query = true), else resident
+// when it fits the CTA's budget. Resident weights (64-128 KB at K = 512-1024)
+// take that much of the SM's shared L1: the mixed scene's gather-bound
+// instances ran 11 % slower with them, while the icosphere query runs 1.7 %
+// faster (its autotuner times both placements).
 inline TcPlan tc_plan(const nbvh_model_desc* d, int threads_opt, int w1_mode, bool query = true) {
   TcPlan p;
   std::memset(&p, 0, sizeof(p));

@@ -196,13 +196,16 @@ cudaError_t launch_ws(const nbvh_model_desc* d, const EvalArgs& a, cudaStream_t 
   return cudaErrorInvalidValue;
 }
 
-// The evaluation's plan for desc under options o; with a streamed plan the
-// first layer's 16-bit image is written into `image` (once per call, before
-// the evaluation launches) and a.w1_image points at it.
+// The evaluation's plan for desc under options o. The first layer's 16-bit
+// image is written into `image` (once per call, before the evaluation
+// launches): a streamed plan's CTAs copy it chunk by chunk (a.w1_image), a
+// resident plan's copy it whole at their start (a.w1_copy); without an image
+// buffer a resident plan's CTAs convert the FP32 weights themselves.
 cudaError_t prepare_eval(const nbvh_model_desc* d, EvalArgs& a, const nbvh_query_options& o, void* image,
                          TcPlan* plan, cudaStream_t s, bool query = true) {
   std::memset(plan, 0, sizeof(*plan));
   a.w1_image = nullptr;
+  a.w1_copy = nullptr;
   if (d->mlp_prec == NBVH_FP32) return cudaSuccess;
   *plan = tc_plan(d, o.eval_threads, o.w1_mode, query);
   if (!plan->ok) return cudaErrorInvalidConfiguration;
@@ -211,6 +214,10 @@ cudaError_t prepare_eval(const nbvh_model_desc* d, EvalArgs& a, const nbvh_query
     cudaError_t e = launch_w1_image(d, a.mlp, plan->threads, image, s);
     if (e != cudaSuccess) return e;
     a.w1_image = image;
+  } else if (image) {
+    cudaError_t e = launch_w1_image(d, a.mlp, plan->threads, image, s);
+    if (e != cudaSuccess) return e;
+    a.w1_copy = image;
   }
   return cudaSuccess;
 }
