@@ -214,11 +214,13 @@ nbvh_status nbvh_encode(const nbvh_model_desc* desc, const void* table, nbvh_ray
  *                   the whole image into shared memory at its start;
  *                   NBVH_W1_STREAMED: streamed through two shared-memory
  *                   buffers, 128 inputs at a time, by bulk copies;
- *                   NBVH_W1_AUTO: streamed (resident weights take up to
- *                   128 KB of the SM's shared L1, which the mixed scene's
- *                   gather needed: 11 % slower there; 1.7 % faster on the
- *                   icosphere query). The training forward places its weights
- *                   itself: resident when they fit.
+ *                   NBVH_W1_AUTO: resident when the layer's image is at
+ *                   most 64 KB (N * L * F <= 512 at width 64), else streamed:
+ *                   resident weights take their size out of the SM's
+ *                   unified L1 / shared memory, which the gather uses (128 KB
+ *                   resident made the mixed scene 11 % slower; 64 KB resident
+ *                   made the queries 1-5 % faster). The training forward
+ *                   keeps them resident whenever they fit.
  *  eval_pipeline    persistent FP16/BF16 schedule: NBVH_PIPELINE_PHASES runs
  *                   each tile in CTA-wide phases (all warps gather, then the
  *                   MLP, resolve and claim); NBVH_PIPELINE_WARP_SPECIALISED

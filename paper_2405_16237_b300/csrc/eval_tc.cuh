@@ -1353,11 +1353,13 @@ struct TcPlan {
 constexpr uint32_t kSmemMax = 227 * 1024;       // per CTA
 constexpr uint32_t kSmemHalf = 113 * 1024;      // per CTA with two CTAs on an SM
 
-// w1_mode NBVH_W1_AUTO: streamed for a query (query = true), else resident
-// when it fits the CTA's budget. Resident weights (64-128 KB at K = 512-1024)
-// take that much of the SM's shared L1: the mixed scene's gather-bound
-// instances ran 11 % slower with them, while the icosphere query runs 1.7 %
-// faster (its autotuner times both placements).
+// w1_mode NBVH_W1_AUTO: resident when it fits the CTA's budget, except that a
+// query streams a first layer of more than kResidentW1Max bytes. Resident
+// weights take their size out of the SM's unified L1 / shared memory: with
+// the 128 KB layers (K = 1024) resident the mixed scene ran 11 % slower,
+// while 64 KB layers (K = 512) resident made the icosphere query 1.7 %, the
+// sphere-cluster query 4.6 % and the mixed scene 1 % faster.
+constexpr size_t kResidentW1Max = 64 * 1024;
 inline TcPlan tc_plan(const nbvh_model_desc* d, int threads_opt, int w1_mode, bool query = true) {
   TcPlan p;
   std::memset(&p, 0, sizeof(p));
@@ -1371,7 +1373,7 @@ inline TcPlan tc_plan(const nbvh_model_desc* d, int threads_opt, int w1_mode, bo
   const uint32_t budget = p.threads == 256 ? kSmemHalf : kSmemMax;
   if (w1_mode == NBVH_W1_RESIDENT) p.stream = false;
   else if (w1_mode == NBVH_W1_STREAMED) p.stream = true;
-  else p.stream = query || res.total > budget;
+  else p.stream = (query && size_t(res.R) * res.chunk_bytes > kResidentW1Max) || res.total > budget;
   const TcLayout& T = p.stream ? str : res;
   p.smem = T.total;
   p.ncols = T.ncols;
