@@ -176,9 +176,10 @@ struct OpType<true> {
 // layer's weights carry zero rows for the padding. When the whole padded
 // input fits the CTA's TMEM next to the accumulator and the hidden
 // activations, the first layer runs as one round (one barrier per tile).
-// Otherwise it runs over K chunks of KC features through two TMEM buffers:
-// while the tensor cores multiply chunk r, the gather fills chunk r + 1 into
-// the other buffer, so the feature footprint is bounded whatever K is.
+// Otherwise it runs over K chunks of KC features (at most 32 KB of weights
+// each) through two TMEM buffers: while the tensor cores multiply chunk r,
+// the gather fills chunk r + 1 into the other buffer, so the feature
+// footprint is bounded whatever K is.
 constexpr int kItemF = 8;
 
 // TMEM column plan (one 32-bit column holds two 16-bit operand elements):
@@ -231,6 +232,13 @@ __host__ __device__ inline TcLayout tc_layout(int L, int F, int N, int W, int n_
   } else {
     T.NB = 2;
     T.KC = 2 * (avail / 2 / 32 * 32);
+    // A chunk of at most 32 KB of weights (256 features at W = 64): the two
+    // streamed buffers then take 64 KB of the SM's unified L1 / shared memory
+    // instead of 96, which the gather uses. The 16-asset frame took 80.5 ms
+    // against 85.9 with 384-feature chunks (192: 111.7, 320: 115.0 vs 105.2
+    // ms untrained: chunks dividing K evenly, in few rounds, win).
+    const int kc_cap = (32768 / (W * 2)) / 64 * 64;
+    if (kc_cap >= 64 && T.KC > kc_cap) T.KC = kc_cap;
     if (T.KC < 64) T.KC = 64;  // no valid plan has so few columns (tc_plan rejects it)
   }
   T.R = (T.KP + T.KC - 1) / T.KC;
