@@ -652,6 +652,7 @@ struct WgTcArgs {
 };
 
 constexpr int kWgTcThreads = 256;
+constexpr int kWgIssuer = kWgTcThreads - 32;  // the thread that issues the MMAs (W <= 128 < kWgIssuer)
 
 __host__ __device__ inline int wg_tc_tiles(int Kp) { return (Kp + 127) / 128; }
 // One stage: the features of `it` items ([Kp][it]) and their dZ ([W][it]).
@@ -667,8 +668,11 @@ __host__ __device__ inline int wg_tc_items(int Kp, int W) {
     if (2 * wg_tc_stage_bytes(Kp, W, it) + 256 <= 227u * 1024u) return it;
   return 64;
 }
+// Stages: three where they fit (two chunks in flight while the tensor cores
+// take a third: the 512-feature first layer at W = 64), else two, else one.
 __host__ __device__ inline int wg_tc_stages(int Kp, int W) {
-  return 2 * wg_tc_stage_bytes(Kp, W, wg_tc_items(Kp, W)) + 256 <= 227u * 1024u ? 2 : 1;
+  const uint32_t b = wg_tc_stage_bytes(Kp, W, wg_tc_items(Kp, W));
+  return 3 * b + 256 <= 227u * 1024u ? 3 : (2 * b + 256 <= 227u * 1024u ? 2 : 1);
 }
 __host__ __device__ inline uint32_t wg_tc_smem(int Kp, int W) {
   return uint32_t(wg_tc_stages(Kp, W)) * wg_tc_stage_bytes(Kp, W, wg_tc_items(Kp, W)) + 128 + 128;
@@ -685,6 +689,7 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 
 template <int W, bool BF16>
 __global__ void __launch_bounds__(kWgTcThreads, 1) weight_grad_tc(WgTcArgs a) {
+  static_assert(W < kWgIssuer, "the MMA issuer is not a bias thread");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   const int tiles = wg_tc_tiles(a.Kp);
@@ -736,13 +741,21 @@ __global__ void __launch_bounds__(kWgTcThreads, 1) weight_grad_tc(WgTcArgs a) {
     stage(sB, a.ZT, W, W, c0);
     cp_async_commit();
   };
-  issue(0, blockIdx.x);
-  int i = 0;
-  for (int64_t c = blockIdx.x; c < n_chunks && !failed; c += gridDim.x, ++i) {
-    const int b = stages == 2 ? (i & 1) : 0;
-    const int64_t cn = c + gridDim.x;
-    if (stages == 2 && cn < n_chunks) {
-      issue(b ^ 1, cn);  // its buffer's last MMA (the previous chunk) has completed
+  // this CTA's chunks: blockIdx.x + j * gridDim.x for j < mine; chunk j sits
+  // in buffer j % stages
+  const int64_t mine = (n_chunks - 1 - blockIdx.x) / gridDim.x + 1;
+  for (int j = 0; j < max(stages - 1, 1) && j < mine; ++j) issue(j, blockIdx.x + int64_t(j) * gridDim.x);
+  for (int64_t i = 0; i < mine && !failed; ++i) {
+    const int b = int(i % stages);
+    const int64_t ahead = i + stages - 1;
+    // the chunk stages - 1 ahead goes into the buffer of chunk i - 1, whose
+    // MMAs have completed
+    if (stages > 1 && ahead < mine) issue(int(ahead % stages), blockIdx.x + ahead * gridDim.x);
+    // chunk i has landed once at most the groups committed after it are pending
+    const int64_t newer = min(int64_t(stages - 1), mine - 1 - i);
+    if (newer >= 2) {
+      cp_async_wait<2>();
+    } else if (newer == 1) {
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
@@ -757,7 +770,7 @@ __global__ void __launch_bounds__(kWgTcThreads, 1) weight_grad_tc(WgTcArgs a) {
         bsum += from16<BF16>(e);
       }
     }
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == kWgIssuer) {  // not one of the bias threads (t < W), so the MMAs start at once
       tc_fence_after();
       const uint32_t sbo = uint32_t(it) * 16;
       for (int t = 0; t < tiles; ++t) {
@@ -773,7 +786,8 @@ __global__ void __launch_bounds__(kWgTcThreads, 1) weight_grad_tc(WgTcArgs a) {
     phase ^= 1u;
     if (__syncthreads_or(!ok)) failed = true;
     tc_fence_after();
-    if (stages == 1 && cn < n_chunks && !failed) issue(0, cn);  // the buffer is free once the MMA completed
+    if (stages == 1 && i + 1 < mine && !failed)  // the buffer is free once the MMA completed
+      issue(0, blockIdx.x + (i + 1) * gridDim.x);
   }
   cp_async_wait<0>();  // no copy left in flight into the freed buffers
   if (!failed && warp < 4) {
