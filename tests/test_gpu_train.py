@@ -617,3 +617,46 @@ def test_recompute_mode_equals_stored_mode(mp):
         x, y = x.double(), y.double()
         assert float((x - y).norm() / x.norm()) <= 1e-6
         assert float((x - y).abs().max()) <= 1e-6 * float(x.abs().max())
+
+
+@pytest.mark.parametrize("mp", [B.FP16, B.BF16])
+def test_pipelined_weight_gradients_equal_sum_of_pieces(mp):
+    """The weight-gradient kernels with several chunks per CTA (37,925 rays:
+    593 chunks of 64 for the 512-feature first layer on 148 CTAs, so every
+    CTA cycles its three copy stages and the last chunk is ragged) against
+    the same rays in pieces of 9,024 (one chunk per CTA). Gradients are
+    linear in the rays and each piece is normalised by the whole batch's
+    valid count, so the sums agree up to FP32 summation order: relative L2
+    and every entry within 1e-5 of the largest. Raw outputs are the same
+    bits (each row is evaluated the same way wherever it sits)."""
+    torch = _torch()
+    b = c1_built()
+    desc = b.with_prec(mp)
+    n = 4 * 148 * 64 + 37
+    rays, leaf, t0, t1, n_valid = B.train_rays(B.TRAIN_PROBED_MIX, 2024, 1, b.scene, n)
+    lab = B.train_labels(rays, leaf, t0, t1, b.scene)
+    assert int(n_valid.item()) > n // 2
+
+    def run(bounds):
+        g_tab = torch.zeros((b.layout["total"], b.case.model.n_features), dtype=torch.float32, device="cuda")
+        g_mlp = torch.zeros_like(b.mlp)
+        raws = []
+        for lo, hi in bounds:  # lo a multiple of 64: every slice stays 256-byte aligned
+            r = {k: v[lo:hi] for k, v in rays.items()}
+            lb = {k: v[lo:hi] for k, v in lab.items()}
+            ws = B.new_workspace(B.train_workspace_size(desc, hi - lo))
+            raws.append(B.forward_train(desc, b.table, b.mlp, r, leaf[lo:hi], t0[lo:hi], t1[lo:hi], ws, labels=lb,
+                                        n_valid=n_valid, loss_scale=1024.0))
+            B.backward(desc, b.table, b.mlp, r, leaf[lo:hi], t0[lo:hi], t1[lo:hi], ws, g_tab, g_mlp)
+        return torch.cat(raws), g_tab, g_mlp
+
+    piece = 141 * 64
+    ra, ta, ma = run([(0, n)])
+    rb, tb, mb = run([(lo, min(n, lo + piece)) for lo in range(0, n, piece)])
+    assert B.device_status() == 0
+    assert torch.equal(ra, rb)
+    for x, y in ((ta, tb), (ma, mb)):
+        x, y = x.double(), y.double()
+        assert float(x.abs().max()) > 0
+        assert float((x - y).norm() / x.norm()) <= 1e-5
+        assert float((x - y).abs().max()) <= 1e-5 * float(x.abs().max())
