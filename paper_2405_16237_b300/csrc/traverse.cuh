@@ -321,25 +321,33 @@ static __global__ void __launch_bounds__(256) tlas_cull_kernel(RayPtrs rays, int
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint64_t mask = 0;  // instances whose root the ray meets
   if (active) {
-    const RayR ray = make_rayr(rays.ox[r], rays.oy[r], rays.oz[r], rays.dx[r], rays.dy[r], rays.dz[r],
-                               rays.tmin[r], rays.tmax[r]);
-    const float best = best_t[r];
-    bool tiny = false;  // a direction component too small for a finite reciprocal
+    const float tmin = rays.tmin[r], tmax = rays.tmax[r];
+    const float ex0 = fminf(tmax, best_t[r]);
+    // tmin > ex0: an empty interval (a ray a bounce pass retired, or one the
+    // triangles closed before tmin), which no instance's traversal gives a
+    // segment: its root test needs an entry >= tmin below tmax and the record
+    if (!(tmin > ex0)) {
+      const RayR ray = make_rayr(rays.ox[r], rays.oy[r], rays.oz[r], rays.dx[r], rays.dy[r], rays.dz[r], tmin,
+                                 tmax);
+      bool tiny = false;  // a direction component too small for a finite reciprocal
 #pragma unroll
-    for (int i = 0; i < 3; ++i) tiny |= ray.d[i] != 0.0f && !isfinite(ray.inv[i]);
-    if (tiny) {
-      mask = c.n_inst >= 64 ? ~uint64_t(0) : (uint64_t(1) << c.n_inst) - 1;
-    } else {
-      const float ex0 = fminf(ray.tmax, best);
-      for (int k = 0; k < c.n_inst; ++k)
-        if (root_maybe(s_box[k], ray, ex0)) mask |= uint64_t(1) << k;
+      for (int i = 0; i < 3; ++i) tiny |= ray.d[i] != 0.0f && !isfinite(ray.inv[i]);
+      if (tiny) {
+        mask = c.n_inst >= 64 ? ~uint64_t(0) : (uint64_t(1) << c.n_inst) - 1;
+      } else {
+        for (int k = 0; k < c.n_inst; ++k)
+          if (root_maybe(s_box[k], ray, ex0)) mask |= uint64_t(1) << k;
+      }
     }
   }
   if (active && c.mask) c.mask[r] = mask;
+  const bool any = __any_sync(0xffffffffu, mask != 0);  // warps with nothing to list skip both loops
   // count: one shared-memory increment per warp and instance
-  for (int k = 0; k < c.n_inst; ++k) {
-    const unsigned m = __ballot_sync(0xffffffffu, (mask >> k) & 1);
-    if (m && lane == 0) s_wbase[warp][k] = atomicAdd(&s_cnt[k], __popc(m));
+  if (any) {
+    for (int k = 0; k < c.n_inst; ++k) {
+      const unsigned m = __ballot_sync(0xffffffffu, (mask >> k) & 1);
+      if (m && lane == 0) s_wbase[warp][k] = atomicAdd(&s_cnt[k], __popc(m));
+    }
   }
   __syncthreads();
   // reserve: one global increment per block and instance
@@ -347,10 +355,12 @@ static __global__ void __launch_bounds__(256) tlas_cull_kernel(RayPtrs rays, int
     s_base[k] = s_cnt[k] > 0 ? atomicAdd(c.count + k, s_cnt[k]) : 0;
   __syncthreads();
   // write
-  for (int k = 0; k < c.n_inst; ++k) {
-    const unsigned m = __ballot_sync(0xffffffffu, (mask >> k) & 1);
-    if ((mask >> k) & 1)
-      c.list[k][s_base[k] + s_wbase[warp][k] + __popc(m & ((1u << lane) - 1u))] = int32_t(r);
+  if (any) {
+    for (int k = 0; k < c.n_inst; ++k) {
+      const unsigned m = __ballot_sync(0xffffffffu, (mask >> k) & 1);
+      if ((mask >> k) & 1)
+        c.list[k][s_base[k] + s_wbase[warp][k] + __popc(m & ((1u << lane) - 1u))] = int32_t(r);
+    }
   }
 }
 

@@ -85,13 +85,13 @@ static __global__ void __launch_bounds__(128) tri_trace_kernel(TriBlasArgs a) {
   const float dx = a.rays.dx[r], dy = a.rays.dy[r], dz = a.rays.dz[r];
   const float tmin = a.rays.tmin[r], tmax = a.rays.tmax[r];
   const float prev = a.merge ? a.hits.t[r] : __int_as_float(0x7f800000);
-  RayR ray = make_rayr(ox, oy, oz, dx, dy, dz, tmin, fminf(tmax, prev));
-  float best = ray.tmax;
+  float best = fminf(tmax, prev);
   int bid = 0x7fffffff;  // caller index of the best triangle
   int bj = -1;           // its leaf-order position
   if (!(tmin <= best)) {
-    bj = -1;
+    bj = -1;  // an empty interval (a ray a bounce pass retired): no reciprocals needed
   } else {
+    RayR ray = make_rayr(ox, oy, oz, dx, dy, dz, tmin, best);
     int stack[kTraverseStack];
     int sp = 0;
     int cur = 0;
